@@ -1,0 +1,173 @@
+"""CPU oracle for frequent-itemset mining -- test infrastructure.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It never imports the GPU package and the GPU
+package never imports it; the C code in ``fim_oracle.c`` shares nothing with
+the CUDA sources.  See ``fim_oracle.c`` for the cited definitions.
+
+Functions return results as ``(set_offsets u64[n+1], set_items u32[...],
+supports u32[n])`` sorted canonically: items ascending inside a set, sets in
+the thesis's lexicographic order (Ch. 9), counts exact.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fim_oracle.c")
+_LIB = os.path.join(_HERE, "libfimoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile fim_oracle.c with gcc (plain C, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            u32, u64, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            for name in ("oracle_eclat", "oracle_bruteforce", "oracle_apriori"):
+                f = getattr(lib, name)
+                f.restype = ctypes.c_int
+                f.argtypes = [P, P, u32, u32, u32, PP]
+            lib.oracle_result_free.restype = None
+            lib.oracle_result_free.argtypes = [P]
+            lib.oracle_result_sort.restype = ctypes.c_int
+            lib.oracle_result_sort.argtypes = [P]
+            lib.oracle_result_n_sets.restype = u64
+            lib.oracle_result_n_sets.argtypes = [P]
+            lib.oracle_result_n_items.restype = u64
+            lib.oracle_result_n_items.argtypes = [P]
+            lib.oracle_result_copy.restype = None
+            lib.oracle_result_copy.argtypes = [P, P, P, P]
+            lib.oracle_check.restype = ctypes.c_int
+            lib.oracle_check.argtypes = [P, P, u32, u32, u32, u64, P, P, P, u64, ctypes.POINTER(u64)]
+            lib.oracle_item_order.restype = ctypes.c_int
+            lib.oracle_item_order.argtypes = [P, P, u32, u32, u32, P, ctypes.POINTER(u32)]
+            lib.oracle_class_costs.restype = ctypes.c_int
+            lib.oracle_class_costs.argtypes = [P, P, u32, u32, u32, dbl, dbl, u64, P, P, ctypes.POINTER(u32),
+                                               ctypes.POINTER(u64)]
+            lib.oracle_splitmix64_at.restype = u64
+            lib.oracle_splitmix64_at.argtypes = [u64, u64]
+            _lib = lib
+    return _lib
+
+
+def _csr(offsets, items):
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+    items = np.ascontiguousarray(items, dtype=np.uint32)
+    if items.size == 0:
+        items = np.zeros(1, dtype=np.uint32)
+    return offsets, items
+
+
+def _run(fname, offsets, items, N, minsup):
+    lib = _load()
+    offsets, items = _csr(offsets, items)
+    D = offsets.size - 1
+    h = ctypes.c_void_p()
+    rc = getattr(lib, fname)(offsets.ctypes.data, items.ctypes.data, D, N, minsup, ctypes.byref(h))
+    if rc != 0:
+        raise ValueError(f"{fname} failed with code {rc}")
+    try:
+        if lib.oracle_result_sort(h) != 0:
+            raise MemoryError("oracle sort failed")
+        n = lib.oracle_result_n_sets(h)
+        ni = lib.oracle_result_n_items(h)
+        so = np.empty(n + 1, dtype=np.uint64)
+        si = np.empty(max(ni, 1), dtype=np.uint32)
+        sp = np.empty(max(n, 1), dtype=np.uint32)
+        lib.oracle_result_copy(h, so.ctypes.data, si.ctypes.data, sp.ctypes.data)
+        return so, si[:ni], sp[:n]
+    finally:
+        lib.oracle_result_free(h)
+
+
+def eclat(offsets, items, N: int, minsup: int):
+    """O1: Eclat-DFS over sorted tidlists (App. B.3.2)."""
+    return _run("oracle_eclat", offsets, items, N, minsup)
+
+
+def bruteforce(offsets, items, N: int, minsup: int):
+    """O2: every non-empty subset, counted by scanning (N <= 20)."""
+    return _run("oracle_bruteforce", offsets, items, N, minsup)
+
+
+def apriori(offsets, items, N: int, minsup: int):
+    """O3: level-wise Apriori (App. B.1)."""
+    return _run("oracle_apriori", offsets, items, N, minsup)
+
+
+CHECK_CODES = {
+    0: "ok", 1: "support differs from recount", 2: "support below minsup", 3: "parent missing or smaller support",
+    4: "frequent extension missing", 5: "singleton missing or wrong", 6: "duplicate or malformed set",
+}
+
+
+def check(offsets, items, N: int, minsup: int, set_offsets, set_items, supports, stride: int = 1):
+    """O4: certificate check of an output; returns (code, bad_index); code 0 = exact."""
+    lib = _load()
+    offsets, items = _csr(offsets, items)
+    so = np.ascontiguousarray(set_offsets, dtype=np.uint64)
+    si = np.ascontiguousarray(set_items, dtype=np.uint32)
+    sp = np.ascontiguousarray(supports, dtype=np.uint32)
+    if si.size == 0:
+        si = np.zeros(1, dtype=np.uint32)
+    if sp.size == 0:
+        sp = np.zeros(1, dtype=np.uint32)
+    bad = ctypes.c_uint64(0)
+    rc = lib.oracle_check(offsets.ctypes.data, items.ctypes.data, offsets.size - 1, N, minsup, so.size - 1,
+                          so.ctypes.data, si.ctypes.data, sp.ctypes.data, stride, ctypes.byref(bad))
+    if rc < 0:
+        raise MemoryError("oracle check failed to allocate")
+    return rc, bad.value
+
+
+def item_order(offsets, items, N: int, prefilter_minsup: int = 0):
+    """Kept items (support >= prefilter) by ascending support, ties by id."""
+    lib = _load()
+    offsets, items = _csr(offsets, items)
+    out = np.empty(max(N, 1), dtype=np.uint32)
+    nk = ctypes.c_uint32(0)
+    rc = lib.oracle_item_order(offsets.ctypes.data, items.ctypes.data, offsets.size - 1, N, prefilter_minsup,
+                               out.ctypes.data, ctypes.byref(nk))
+    if rc != 0:
+        raise ValueError(f"item_order failed {rc}")
+    return out[: nk.value]
+
+
+def class_costs(offsets, items, N: int, prefilter_minsup: int, sample_rate: float, rel_minsup: float, seed: int):
+    """Sample-based relative class sizes and their LPT order; returns (cost f64[N_f], order u32[N_f], |F_s|)."""
+    lib = _load()
+    offsets, items = _csr(offsets, items)
+    cost = np.zeros(max(N, 1), dtype=np.float64)
+    order = np.zeros(max(N, 1), dtype=np.uint32)
+    nk = ctypes.c_uint32(0)
+    nfs = ctypes.c_uint64(0)
+    rc = lib.oracle_class_costs(offsets.ctypes.data, items.ctypes.data, offsets.size - 1, N, prefilter_minsup,
+                                sample_rate, rel_minsup, seed, cost.ctypes.data, order.ctypes.data, ctypes.byref(nk),
+                                ctypes.byref(nfs))
+    if rc != 0:
+        raise ValueError(f"class_costs failed {rc}")
+    return cost[: nk.value], order[: nk.value], nfs.value
+
+
+def splitmix64_at(seed: int, k: int) -> int:
+    """k-th output (0-based) of SplitMix64 started at state ``seed``."""
+    return _load().oracle_splitmix64_at(seed, k)

@@ -1,0 +1,302 @@
+"""Pins of the CPU oracle against facts fixed by the thesis and by mathematics.
+
+Nothing here uses the GPU path.  Every check compares the oracle with
+something other than itself: values printed in the thesis's worked examples,
+closed forms, brute force over all subsets, an independent level-wise miner,
+library-free recounts, and the published SplitMix64 stream.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_05038_gb300 import synth
+
+
+def csr(txs):
+    off = np.zeros(len(txs) + 1, dtype=np.uint32)
+    items = []
+    for i, t in enumerate(txs):
+        items.extend(sorted(set(t)))
+        off[i + 1] = len(items)
+    return off, np.array(items, dtype=np.uint32)
+
+
+def as_dict(res):
+    so, si, sp = res
+    return {tuple(int(v) for v in si[so[i]:so[i + 1]]): int(sp[i]) for i in range(len(sp))}
+
+
+def brute_dict(txs, N, minsup):
+    """Definition written out in Python: all non-empty subsets of the items present."""
+    sets = [frozenset(t) for t in txs]
+    present = sorted(set().union(*sets)) if sets else []
+    out = {}
+    for k in range(1, len(present) + 1):
+        for c in itertools.combinations(present, k):
+            s = sum(1 for t in sets if t.issuperset(c))
+            if s >= minsup:
+                out[c] = s
+    return out
+
+
+# ---------------------------------------------------------------- golden examples
+
+@pytest.mark.parametrize("miner", [oracle.eclat, oracle.bruteforce, oracle.apriori])
+def test_eclat_worked_example(golden, miner):
+    """App. B.3.2: the 23 frequent itemsets and supports printed by the Eclat example."""
+    minsup, txs, rows = golden("eclat_example.txt")
+    off, items = csr(txs)
+    got = as_dict(miner(off, items, 6, minsup))
+    want = {s: v for f, s, v in rows if f == "F"}
+    assert len(want) == 23
+    assert got == want
+    for f, s, v in rows:
+        if f == "I":
+            assert v < minsup and s not in got
+
+
+@pytest.mark.parametrize("miner", [oracle.eclat, oracle.bruteforce, oracle.apriori])
+def test_apriori_worked_example_corrected(golden, miner):
+    """App. B.1 example database with its printed errors corrected (11 frequent itemsets)."""
+    minsup, txs, rows = golden("apriori_example.txt")
+    off, items = csr(txs)
+    got = as_dict(miner(off, items, 6, minsup))
+    want = {s: v for f, s, v in rows if f == "F"}
+    assert len(want) == 11
+    assert got == want
+
+
+def test_golden_supports_by_python_definition(golden):
+    """The fixtures themselves agree with the definition of support (Ch. 2)."""
+    for name in ("eclat_example.txt", "apriori_example.txt"):
+        minsup, txs, rows = golden(name)
+        sets = [set(t) for t in txs]
+        for f, s, v in rows:
+            assert sum(1 for t in sets if set(s) <= t) == v
+            assert (v >= minsup) == (f == "F")
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("k", [1, 3, 7, 12])
+def test_identical_transactions(k):
+    """D identical transactions of k items: 2^k - 1 frequent itemsets, each with support D."""
+    D = 37
+    off, items = csr([list(range(2, 2 + k))] * D)
+    for miner in (oracle.eclat, oracle.apriori):
+        got = as_dict(miner(off, items, k + 4, D))
+        assert len(got) == 2 ** k - 1
+        assert set(got.values()) == {D}
+
+
+def test_disjoint_singletons():
+    """Transactions of one item each: only singletons can be frequent."""
+    N = 9
+    txs = [[t % N] for t in range(100)]
+    off, items = csr(txs)
+    got = as_dict(oracle.eclat(off, items, N, 1))
+    assert all(len(s) == 1 for s in got)
+    assert got == {(i,): sum(1 for t in range(100) if t % N == i) for i in range(N)}
+
+
+def test_minsup_above_D_is_empty():
+    w = synth.make_workload("tiny", D=500)
+    for miner in (oracle.eclat, oracle.apriori):
+        so, si, sp = miner(w["offsets"], w["items"], w["N"], 501)
+        assert len(sp) == 0
+
+
+def test_minsup_zero_rejected():
+    off, items = csr([[1, 2]])
+    with pytest.raises(ValueError):
+        oracle.eclat(off, items, 3, 0)
+
+
+def test_item_out_of_range_rejected():
+    off, items = csr([[1, 7]])
+    with pytest.raises(ValueError):
+        oracle.eclat(off, items, 5, 1)
+
+
+def test_two_item_bernoulli_pair_count():
+    """Two items in a Bernoulli pattern: supp({0,1}) is the number of rows holding both."""
+    rng = np.random.default_rng(5)
+    a = rng.random(3000) < 0.6
+    b = rng.random(3000) < 0.45
+    txs = [[0] * int(x) + [1] * int(y) for x, y in zip(a, b)]
+    off, items = csr(txs)
+    got = as_dict(oracle.eclat(off, items, 2, 1))
+    assert got[(0,)] == int(a.sum()) and got[(1,)] == int(b.sum())
+    assert got[(0, 1)] == int((a & b).sum())
+
+
+def test_duplicate_items_count_once():
+    """Set semantics (Def. Transaction): a repeated item inside a transaction counts once."""
+    off = np.array([0, 4, 6], dtype=np.uint32)
+    items = np.array([1, 1, 2, 2, 1, 1], dtype=np.uint32)
+    got = as_dict(oracle.eclat(off, items, 3, 1))
+    assert got == {(1,): 2, (2,): 1, (1, 2): 1}
+
+
+def test_empty_transactions_count_toward_D():
+    off, items = csr([[], [1, 2], [], [1]])
+    got = as_dict(oracle.eclat(off, items, 3, 2))
+    assert got == {(1,): 2}
+
+
+# ---------------------------------------------------------------- brute force / independent miners
+
+@pytest.mark.parametrize("seed", range(12))
+def test_eclat_equals_bruteforce_tiny(seed):
+    rng = np.random.default_rng(100 + seed)
+    N = int(rng.integers(3, 15))
+    D = int(rng.integers(1, 400))
+    dens = rng.uniform(0.1, 0.7)
+    txs = [list(np.nonzero(rng.random(N) < dens)[0]) for _ in range(D)]
+    off, items = csr(txs)
+    for minsup in sorted({1, 2, max(1, D // 10), max(1, D // 3)}):
+        e = as_dict(oracle.eclat(off, items, N, minsup))
+        b = as_dict(oracle.bruteforce(off, items, N, minsup))
+        a = as_dict(oracle.apriori(off, items, N, minsup))
+        assert e == b == a
+
+
+def test_bruteforce_equals_python_definition():
+    rng = np.random.default_rng(7)
+    txs = [list(np.nonzero(rng.random(8) < 0.4)[0]) for _ in range(60)]
+    off, items = csr(txs)
+    for minsup in (1, 3, 9):
+        assert as_dict(oracle.bruteforce(off, items, 8, minsup)) == brute_dict(txs, 8, minsup)
+
+
+@pytest.mark.parametrize("name,D", [("tiny", 3000), ("dense_deep", 2000)])
+def test_eclat_equals_apriori_workloads(name, D):
+    w = synth.make_workload(name, D=D)
+    ms = synth.abs_minsup(w["rel_minsup"], D)
+    e = oracle.eclat(w["offsets"], w["items"], w["N"], ms)
+    a = oracle.apriori(w["offsets"], w["items"], w["N"], ms)
+    for x, y in zip(e, a):
+        assert np.array_equal(x, y)
+    assert len(e[2]) > 50
+
+
+def test_singletons_equal_histogram():
+    w = synth.make_workload("sparse_mid", D=20000)
+    so, si, sp = oracle.eclat(w["offsets"], w["items"], w["N"], 30)
+    hist = np.bincount(w["items"], minlength=w["N"])  # generator writes distinct items per transaction
+    single = {int(si[so[i]]): int(sp[i]) for i in range(len(sp)) if so[i + 1] - so[i] == 1}
+    assert single == {i: int(c) for i, c in enumerate(hist) if c >= 30}
+
+
+def test_anti_monotone_along_prefixes():
+    """Thm. 2.1 on an Eclat output: every set's prefix (minus last item) is output with >= support."""
+    w = synth.make_workload("tiny", D=4000)
+    d = as_dict(oracle.eclat(w["offsets"], w["items"], w["N"], 40))
+    for s, v in d.items():
+        if len(s) > 1:
+            assert d[s[:-1]] >= v
+            for drop in range(len(s)):
+                sub = s[:drop] + s[drop + 1:]
+                assert d[sub] >= v
+
+
+# ---------------------------------------------------------------- certificate checker
+
+def test_check_accepts_exact_and_rejects_planted_mistakes():
+    w = synth.make_workload("tiny", D=3000)
+    ms = 30
+    off, items, N = w["offsets"], w["items"], w["N"]
+    so, si, sp = oracle.eclat(off, items, N, ms)
+    assert oracle.check(off, items, N, ms, so, si, sp)[0] == 0
+    # wrong count
+    sp2 = sp.copy()
+    big = int(np.argmax(np.diff(so.astype(np.int64))))
+    sp2[big] += 1
+    assert oracle.check(off, items, N, ms, so, si, sp2)[0] in (1, 3)
+    # dropped deepest set (its parent then misses a frequent extension)
+    keep = np.ones(len(sp), dtype=bool)
+    keep[big] = False
+    so3 = np.concatenate([[0], np.cumsum(np.diff(so.astype(np.int64))[keep])]).astype(np.uint64)
+    si3 = np.concatenate([si[so[i]:so[i + 1]] for i in range(len(sp)) if keep[i]])
+    assert oracle.check(off, items, N, ms, so3, si3, sp[keep])[0] == 4
+    # dropped singleton
+    k1 = [i for i in range(len(sp)) if so[i + 1] - so[i] == 1][3]
+    keep = np.ones(len(sp), dtype=bool)
+    keep[k1] = False
+    so4 = np.concatenate([[0], np.cumsum(np.diff(so.astype(np.int64))[keep])]).astype(np.uint64)
+    si4 = np.concatenate([si[so[i]:so[i + 1]] for i in range(len(sp)) if keep[i]])
+    assert oracle.check(off, items, N, ms, so4, si4, sp[keep])[0] in (3, 5)
+
+
+# ---------------------------------------------------------------- counter-based generator
+
+def test_splitmix64_published_stream():
+    """SplitMix64 from state 1234567 (reference outputs of Steele et al.'s generator)."""
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423]
+    assert synth.splitmix64_stream(1234567, 3) == want
+    assert [oracle.splitmix64_at(1234567, k) for k in range(3)] == want
+
+
+# ---------------------------------------------------------------- class-cost estimate
+
+def _sample_brute_costs(txs, N, prefilter, rate, rel, seed):
+    """Estimate written out independently: sample by SplitMix64, brute-force mine, tally by first rank."""
+    D = len(txs)
+    supp = np.zeros(N, dtype=np.int64)
+    for t in txs:
+        for i in set(t):
+            supp[i] += 1
+    kept = [i for i in range(N) if supp[i] >= prefilter]
+    kept.sort(key=lambda i: (supp[i], i))
+    rank = {it: r for r, it in enumerate(kept)}
+    m = max(1, math.ceil(rate * D))
+    ms = max(1, math.ceil(rel * m))
+    sample = []
+    for k in range(m):
+        x = oracle.splitmix64_at(seed, k)
+        sample.append([i for i in txs[((x >> 32) * D) >> 32] if i in rank])
+    fs = brute_dict(sample, N, ms)
+    cnt = np.zeros(len(kept), dtype=np.int64)
+    for s in fs:
+        cnt[min(rank[i] for i in s)] += 1
+    cost = cnt / len(fs) if fs else cnt.astype(float)
+    return cost, len(fs)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 99])
+def test_class_costs_match_independent_restatement(seed):
+    rng = np.random.default_rng(seed + 40)
+    N, D = 10, 300
+    txs = [list(np.nonzero(rng.random(N) < rng.uniform(0.2, 0.6))[0]) for _ in range(D)]
+    off, items = csr(txs)
+    for prefilter, rate, rel in ((0, 0.2, 0.1), (20, 0.5, 0.05), (0, 1.0, 0.3)):
+        cost, order, nfs = oracle.class_costs(off, items, N, prefilter, rate, rel, seed)
+        want, nfs2 = _sample_brute_costs(txs, N, prefilter, rate, rel, seed)
+        assert nfs == nfs2
+        assert np.array_equal(cost, want)
+        keys = sorted(range(len(cost)), key=lambda r: (-cost[r], r))
+        assert list(order) == keys
+
+
+def test_sample_support_within_chernoff_bound():
+    """Sec. 6.1: with |D_s| >= ln(2/delta)/(2 eps^2), singleton relative supports err by <= eps w.p. >= 1-delta.
+
+    A 10,000-row sample gives eps = 0.0136 at delta = 0.05; over 40 items and fixed
+    seeds, the observed error stays inside the bound for at least 95% of items."""
+    w = synth.make_workload("tiny", D=20000)
+    off, items = w["offsets"], w["items"]
+    D, N = 20000, w["N"]
+    full = np.bincount(items, minlength=N) / D
+    m = 10000
+    eps = math.sqrt(math.log(2 / 0.05) / (2 * m))
+    assert abs(eps - 0.0136) < 1e-3
+    for seed in (3, 4):
+        idx = np.array([(oracle.splitmix64_at(seed, k) >> 32) * D >> 32 for k in range(m)], dtype=np.int64)
+        cnt = np.zeros(N)
+        for t in idx:
+            cnt[items[off[t]:off[t + 1]]] += 1
+        err = np.abs(cnt / m - full)
+        assert np.mean(err <= eps) >= 0.95
