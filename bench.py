@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 vertical-bitmap Eclat hot path.
+
+One step = the whole hot path on one synthetic database resident in HBM:
+build the vertical bitmaps (item counts + bitmap build), the 1%-sample
+class-cost estimate (sample build + sample mining + tally), and the mining of
+every frequent itemset (pair kernel, level-2 compaction, persistent DFS),
+results left in device memory.
+
+Prints one JSON line.  `value` is the algorithmic AND+popcount throughput of
+the mining in GB/s (bytes of all tidset intersections) over the
+whole step time; `itemsets_per_s` is |F| over the same time.  `e2e` repeats the
+step through the C ABI with host buffers (pinned CSR in, itemsets out).
+`--impl reference` times the CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2108_05038_gb300 import synth  # noqa: E402
+
+METRIC = "tidset AND+popc GB/s"
+WORKLOAD = "sparse_mid"
+SAMPLE_RATE = 0.01
+EST_SEED = 1
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_desc(w):
+    return (f"{WORKLOAD}: pattern-embedded D={w['D']:,} N={w['N']:,} TL={w['TL']} PL={w['PL']} npat={w['npat']} "
+            f"uniform items, seed {w['seed']}, minsup {w['minsup']} ({w['rel_minsup'] * 100:.2f}%), 64-bit words")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2108_05038_gb300 import fim
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = synth.make_workload(WORKLOAD)
+    D, N, minsup, rel = w["D"], w["N"], w["minsup"], w["rel_minsup"]
+    stream = torch.cuda.current_stream()
+    d_off = torch.from_numpy(w["offsets"].astype(np.int32)).cuda()
+    d_items = torch.from_numpy(w["items"].astype(np.int32)).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(collect_times=False):
+        db = fim.build_vertical_db_device(d_off, d_items, D, N, 64, 0, stream=stream)
+        db.estimate_class_costs(SAMPLE_RATE, rel, EST_SEED)
+        res = db.mine(minsup, result_on_device=True, collect_times=collect_times)
+        st = res.stats
+        res.free()
+        db.free()
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, bytes_alg, n_sets = 0.0, 0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = None
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)  # write 512 MB: the 129 MB L2 holds nothing of the previous step
+        e0.record(stream)
+        stats = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        bytes_alg += stats["bytes_algorithmic"]
+        n_sets += stats["n_frequent"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+
+    # dominant kernel: live CUDA-event timing of each launch inside the library
+    pair_ms, dfs_ms, reps = [], [], max(3, args.steps)
+    for _ in range(reps):
+        flush.fill_(1)
+        st = step(collect_times=True)
+        pair_ms.append(st["ms_pair_kernel"])
+        dfs_ms.append(st["ms_dfs_kernel"])
+    pair_avg = sum(pair_ms) / len(pair_ms)
+    dfs_avg = sum(dfs_ms) / len(dfs_ms)
+
+    # end to end through the C ABI with host buffers (pinned CSR in, itemsets out)
+    h_off = torch.from_numpy(w["offsets"]).pin_memory()
+    h_items = torch.from_numpy(w["items"]).pin_memory()
+    e2e_s, d2h = 0.0, 0
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        db = fim.build_vertical_db(h_off.numpy(), h_items.numpy(), N, 64, 0, stream=stream)
+        db.estimate_class_costs(SAMPLE_RATE, rel, EST_SEED)
+        res = db.mine(minsup)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_s += t1 - t0
+            d2h = res.set_offsets.nbytes + res.set_items.nbytes + res.supports.nbytes
+        db.free()
+    h2d = int(w["offsets"].nbytes + w["items"].nbytes)
+
+    # max over ranks
+    per_rank = torch.tensor([total_ms, bytes_alg, n_sets, e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        gathered = [torch.zeros_like(per_rank) for _ in range(world)]
+        dist.all_gather(gathered, per_rank)
+        allv = torch.stack(gathered).cpu().numpy()
+    else:
+        allv = per_rank.cpu().numpy()[None, :]
+    max_ms = float(allv[:, 0].max())
+    tot_bytes = float(allv[:, 1].sum())
+    tot_sets = float(allv[:, 2].sum())
+    max_e2e = float(allv[:, 3].max())
+
+    out = None
+    if rank == 0:
+        value = tot_bytes / (max_ms * 1e-3) / 1e9
+        peaks = {}
+        pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk_path):
+            peaks = json.load(open(pk_path))
+        sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        # integer pipe: 64 lanes/clk/SM, two slots (AND, POPC) per 32-bit word pair
+        alu_peak_gword = 64 / 2 * num_sms * sm_max_mhz * 1e6 / 1e9
+        words = stats["n_pair_intersections"] * ((D + 31) // 32)
+        achieved_gword = words / (pair_avg * 1e-3) / 1e9
+        launches = 2 + (3 + 5) + 5  # build (2), estimate (3 + engine), mine (engine: pair, 3 level-2, dfs)
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_desc(w), "sample_rate": SAMPLE_RATE,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "512 MB buffer written between timed steps"},
+            "itemsets_per_s": round(tot_sets / (max_ms * 1e-3), 1),
+            "n_frequent": int(stats["n_frequent"]),
+            "breakdown_ms": {"pair_kernel": round(pair_avg, 4), "dfs_kernel": round(dfs_avg, 4),
+                             "step": round(max_ms / args.steps, 4)},
+            "roofline": {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
+                         "peak": round(alu_peak_gword, 1), "unit": "Gword/s", "frac": round(achieved_gword / alu_peak_gword, 4),
+                         "traffic": None,
+                         "peak_source": "derived: 64 integer lanes/clk/SM / 2 ops per word x SMs x max SM clock"},
+            "e2e": {"value": round(tot_bytes / max_e2e / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": round(max_e2e / args.steps * 1e3, 3)},
+            "gpu_launches": launches * args.steps,
+            "clocks": clk,
+            "wall_s": round(wall, 3),
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, stats["bytes_algorithmic"])
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(w, bytes_alg_per_step):
+    """The oracle as it stands, on the host, on the same workload (one full mine, single thread)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    so, si, sp = oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"])
+    dt = time.perf_counter() - t0
+    return {"value": round(bytes_alg_per_step / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full oracle Eclat mine of {WORKLOAD} ({len(sp)} itemsets) in {dt:.2f} s; GB/s counts "
+                      f"the bitmap path's algorithmic bytes for the same answer",
+            "itemsets_per_s": round(len(sp) / dt, 1)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores, same workload and metric."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+
+    w = synth.make_workload(WORKLOAD)
+    # algorithmic bytes of the bitmap path for this workload, computed from the oracle's own output
+    so, si, sp = oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"])
+    order = oracle.item_order(w["offsets"], w["items"], w["N"], 0)
+    item_rank = np.zeros(w["N"], dtype=np.int64)
+    item_rank[order] = np.arange(len(order))
+    I, C, M = bitmap_work(so, si, item_rank)
+    bytes_alg = (I + C + M) * ((w["D"] + 63) // 64 * 8)
+    for _ in range(args.warmup):
+        oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"])
+    dt = time.perf_counter() - t0
+    value = bytes_alg * args.steps / dt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_desc(w)},
+            "itemsets_per_s": round(len(sp) * args.steps / dt, 1),
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"full oracle Eclat mine of {WORKLOAD} per step"},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def bitmap_work(so, si, item_rank):
+    """Work of the bitmap Eclat for a given output, from the output alone.
+
+    Classes are formed in row order (ascending support, ties by id).  With k_P =
+    number of frequent itemsets P u {e}, e after P's last item:
+    intersections I = n1(n1-1)/2 + sum_{|P|>=1} k_P(k_P-1)/2, class nodes with
+    candidates C = (n1-1) + sum_{|P|>=1} (k_P-1)+, materialised prefixes
+    M = #{X : |X| >= 2, k_X >= 2}.  Algorithmic bytes = (I + C + M) x row bytes."""
+    groups = {}
+    n1 = 0
+    for k in range(len(so) - 1):
+        s = tuple(sorted(int(item_rank[v]) for v in si[so[k]:so[k + 1]]))
+        if len(s) == 1:
+            n1 += 1
+        else:
+            groups[s[:-1]] = groups.get(s[:-1], 0) + 1
+    I = n1 * (n1 - 1) // 2 + sum(k * (k - 1) // 2 for k in groups.values())
+    C = max(n1 - 1, 0) + sum(max(k - 1, 0) for k in groups.values())
+    M = sum(1 for p, k in groups.items() if len(p) >= 2 and k >= 2)
+    return I, C, M
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

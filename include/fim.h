@@ -1,0 +1,192 @@
+/*
+ * fim.h -- C ABI of the GB300 frequent-itemset miner (vertical-bitmap Eclat).
+ *
+ * The method is the depth-first Eclat of R. Kessl, "Parallel algorithms for
+ * mining of frequent itemsets" (thesis, 2011; arXiv 2108.05038), App. B.3:
+ * supports are counted by intersecting transaction-id lists (here: bitmaps,
+ * AND + popcount) over prefix-based equivalence classes (PBECs, Sec. 2.4) and
+ * pruned at the minimum support.  The thesis's sample-based estimate of the
+ * size of a PBEC (Sec. 6.2, Phase 2 in Sec. 8.2) orders the prefix classes
+ * across the persistent CTAs of one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns fim_status; nothing aborts, throws across the ABI or
+ *    traps the device.  On error the output handle is left NULL and
+ *    fim_last_error() (thread local) describes the cause.
+ *  - Input buffers are copied; the caller keeps ownership of its buffers.
+ *    Objects returned through `out` handles are owned by the library until
+ *    the matching *_free call.
+ *  - Device work runs on the CUDA stream given to fim_build_vertical_db*
+ *    (NULL = the legacy default stream).  Calls that return host data
+ *    synchronise that stream before returning.
+ *  - A fim_db may be used by one thread at a time.
+ */
+#ifndef FIM_H_
+#define FIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fim_db fim_db;         /* device bitmaps + item relabel map + CSR copy for sampling */
+typedef struct fim_result fim_result; /* frequent itemsets in CSR form (host or device memory)      */
+
+typedef enum {
+  FIM_OK = 0,
+  FIM_ERR_INVALID = 1,         /* bad argument (NULL pointer, size, item id >= N, minsup 0 ...)  */
+  FIM_ERR_OOM = 2,             /* a device or host allocation failed                            */
+  FIM_ERR_OUTPUT_OVERFLOW = 3, /* fixed output capacity too small; needed sizes are reported   */
+  FIM_ERR_CUDA = 4,            /* a CUDA runtime call failed                                    */
+  FIM_ERR_TIMEOUT = 5          /* a bounded device-side wait ran out (no progress)              */
+} fim_status;
+
+/* Order in which the prefix classes enter the persistent kernel's queue. */
+typedef enum {
+  FIM_ORDER_ESTIMATE = 0, /* longest first by the sample estimate (LPT, Sec. 8.2); falls back to
+                             FIM_ORDER_UNIFORM when fim_estimate_class_costs was never called  */
+  FIM_ORDER_UNIFORM = 1   /* class order = item order (ascending support)                      */
+} fim_class_order;
+
+/* Counters of one fim_mine call (filled when fim_mine_opts.stats != NULL). */
+typedef struct {
+  uint64_t n_frequent;           /* |F|: frequent itemsets written                                */
+  uint64_t n_items_out;          /* sum of |X| over F                                             */
+  uint32_t n_frequent_items;     /* frequent singletons (rows taking part in this mine)            */
+  uint32_t max_len;              /* longest frequent itemset                                       */
+  uint64_t n_intersections;      /* AND+popcount operand pairs evaluated, all levels               */
+  uint64_t n_pair_intersections; /* of which in the level-2 pair kernel (i < j pairs)              */
+  uint64_t n_classes;            /* class nodes expanded by the persistent DFS kernel              */
+  uint64_t n_queue_entries;      /* level-3 prefix classes put in the persistent queue             */
+  uint64_t n_donations;          /* subclasses handed from a busy CTA to idle CTAs                 */
+  uint64_t bytes_algorithmic;    /* algorithmic bytes of all intersections (see DESIGN measurement) */
+  uint64_t bytes_pair_kernel;    /* algorithmic bytes of the pair kernel                           */
+  uint64_t bytes_dfs_kernel;     /* algorithmic bytes of the DFS kernel                            */
+  uint32_t words_per_row;        /* 32-bit words per bitmap row, padded (row stride)               */
+  uint32_t grid_ctas;            /* persistent CTAs launched                                       */
+  uint32_t threads_per_cta;
+  uint32_t vec_per_lane;         /* 16-byte loads per lane per piece                               */
+  float ms_pair_kernel;          /* CUDA-event time of the pair kernel (collect_times = 1)         */
+  float ms_dfs_kernel;           /* CUDA-event time of the persistent DFS kernel                   */
+  float ms_device_total;         /* CUDA-event time from the first to the last mining kernel       */
+  float reserved_f;
+} fim_mine_stats;
+
+typedef struct {
+  uint32_t struct_size;        /* set to sizeof(fim_mine_opts); 0 = treat as defaults            */
+  uint32_t class_order;        /* fim_class_order                                                 */
+  uint32_t reserved0;          /* must be 0                                                       */
+  uint32_t threads_per_cta;    /* persistent DFS CTA size: 0 = default, else 128/256/512          */
+  uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece: 0 = default, 1,2,4,8     */
+  uint32_t ctas_per_sm;        /* 0 = as many as fit                                              */
+  uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 1)          */
+  uint32_t result_on_device;   /* 1 = keep the result in device memory (no D2H copy)              */
+  uint32_t collect_times;      /* 1 = record CUDA events around the kernels (stats.ms_*)          */
+  uint32_t reserved_u;
+  uint64_t out_capacity_sets;  /* 0 = automatic (grow and retry); else fixed capacity             */
+  uint64_t out_capacity_items; /* idem, total items over all sets                                 */
+  uint64_t spin_limit;         /* idle-CTA polling rounds without progress before FIM_ERR_TIMEOUT;
+                                  0 = default (a few s)                                            */
+  /* outputs */
+  uint64_t out_needed_sets;    /* on FIM_ERR_OUTPUT_OVERFLOW: capacities that would have sufficed */
+  uint64_t out_needed_items;
+  fim_mine_stats* stats;       /* optional                                                        */
+} fim_mine_opts;
+
+/* Fill *opts with the defaults (struct_size set, all options default). */
+void fim_mine_opts_init(fim_mine_opts* opts);
+
+/*
+ * Build the vertical representation (Def. "Transaction id list" and the
+ * vertical representation of Ch. 2; first step of Eclat-DFS, App. B.3.2).
+ *
+ * tx_offsets[D+1], tx_items[tx_offsets[D]]: horizontal database in CSR form,
+ * HOST memory; transaction t holds tx_items[tx_offsets[t] .. tx_offsets[t+1]).
+ * Items are ids < N in any order; a repeated id inside a transaction counts
+ * once (set semantics, Def. "Transaction").  Empty transactions are allowed
+ * and count toward D.
+ * word_bits: 32 or 64, the nominal bitmap word; the bit layout in memory is
+ * the same for both on a little-endian GPU (bit t of row f sits in byte
+ * t/8, bit t%8), so it only decides how W is reported.
+ * prefilter_minsup: items with support < prefilter_minsup get no row (0 keeps
+ * every item).  Kept items are relabelled 0..N_f-1 by ascending support, ties
+ * by ascending id (the ascending-support order of App. B.4.2); every later
+ * mine must use minsup >= prefilter_minsup.
+ * Errors: FIM_ERR_INVALID (NULL pointers, D == 0, N == 0, word_bits not 32/64,
+ * offsets not non-decreasing, an item >= N), FIM_ERR_OOM, FIM_ERR_CUDA.
+ */
+fim_status fim_build_vertical_db(const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D, uint32_t N,
+                                 uint32_t word_bits, uint32_t prefilter_minsup, void* cuda_stream, fim_db** out);
+
+/* Same as fim_build_vertical_db with tx_offsets / tx_items in DEVICE memory
+ * (read on cuda_stream; the library copies what it keeps). */
+fim_status fim_build_vertical_db_device(const uint32_t* d_tx_offsets, const uint32_t* d_tx_items, uint32_t D,
+                                        uint32_t N, uint32_t word_bits, uint32_t prefilter_minsup,
+                                        void* cuda_stream, fim_db** out);
+
+/* Sizes of a built database: transactions, item base, kept rows, 32-bit words
+ * per padded row, nominal word bits, device bytes held.  Any pointer may be NULL. */
+fim_status fim_db_info(const fim_db* db, uint32_t* D, uint32_t* N, uint32_t* n_rows, uint32_t* words_per_row,
+                       uint32_t* word_bits, uint64_t* device_bytes);
+
+/* Relabel map: rank_item[r] = original id of row r, supports[r] = its support
+ * (both arrays of n_rows entries, host memory; either may be NULL). */
+fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports);
+
+/*
+ * Sample-based estimate of the relative size of every one-item-prefix class
+ * [r | {g : g after r}] (Def. "Relative size of a PBEC", Sec. 2.4; estimate
+ * of Sec. 6.2 used by Phase 2, Sec. 8.2).
+ * A sample D_s of m = ceil(sample_rate * D) transactions is drawn with
+ * replacement (Sec. 6.1): draw k takes transaction ((x_k >> 32) * D) >> 32,
+ * x_k = k-th output of SplitMix64 started at state `seed`.  D_s (kept items
+ * only) is mined on the GPU at minsup_s = max(1, ceil(rel_minsup * m)) and
+ * cost_out[r] = |{X in F_s : the lowest row of X is r}| / |F_s| (0 when F_s is
+ * empty).  order_out = rows by descending cost, ties by ascending row (the
+ * LPT order, Sec. 8.2).  Both arrays have n_rows entries (host memory).
+ * The estimate is kept in the db and orders the classes of later fim_mine
+ * calls (FIM_ORDER_ESTIMATE); it never changes their output.
+ * Errors: FIM_ERR_INVALID (sample_rate not in (0,1], rel_minsup not in [0,1],
+ * NULL outputs), FIM_ERR_OOM, FIM_ERR_CUDA, FIM_ERR_TIMEOUT.
+ */
+fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
+                                    double* cost_out, uint32_t* order_out);
+
+/* Number of frequent itemsets found in the sample by the last estimate. */
+fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, uint32_t* sample_rows,
+                                    uint32_t* sample_minsup);
+
+/*
+ * Mine every frequent itemset F = { X != {} : supp(X) >= minsup_abs }
+ * (Def. "Frequent itemset", Ch. 2) with exact supports, by Eclat over the
+ * db's bitmaps (App. B.3.2): level 2 by the tiled pair kernel, deeper levels
+ * by the persistent DFS kernel over the level-3 prefix classes.
+ * minsup_abs >= max(1, prefilter_minsup) (0 is rejected: every subset would be
+ * frequent).  opts may be NULL (defaults).  The result lists each frequent
+ * itemset once with original item ids ascending inside the set; the order of
+ * the sets is unspecified.
+ * Errors: FIM_ERR_INVALID, FIM_ERR_OOM, FIM_ERR_CUDA, FIM_ERR_TIMEOUT,
+ * FIM_ERR_OUTPUT_OVERFLOW (only with a fixed capacity; opts->out_needed_*
+ * then hold the sizes that would have sufficed).
+ */
+fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_result** out);
+
+/* CSR view of a result: n_sets sets; set k holds set_items[set_offsets[k] ..
+ * set_offsets[k+1]) with supports[k].  Pointers stay valid until
+ * fim_result_free; they are device pointers iff *on_device is 1 (on_device may
+ * be NULL). */
+fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,
+                           const uint32_t** set_items, const uint32_t** supports, int* on_device);
+
+void fim_result_free(fim_result* res);
+void fim_db_free(fim_db* db);
+const char* fim_status_str(fim_status s);
+/* Description of the last error on the calling thread ("" if none). */
+const char* fim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIM_H_ */

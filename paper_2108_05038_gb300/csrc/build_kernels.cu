@@ -1,0 +1,168 @@
+// Vertical-database kernels: item counting (K1), bitmap build (K2), the
+// database sample of the class-cost estimate, row popcounts and the tally of
+// sample itemsets per one-item-prefix class.
+//
+// Vertical representation (Ch. 2, Def. "Transaction id list"): row r holds the
+// tidlist of item rank_item[r] as a bitmap, bit t of the row set iff
+// transaction t contains the item.  Bits past D stay zero.
+#include "fim_internal.cuh"
+
+namespace fim {
+namespace {
+
+constexpr uint32_t kSmemHistMax = 12288;  // items counted in shared memory (48 KB)
+
+// K1: item supports with set semantics.  One thread per transaction; an item
+// counts once per transaction (a repeat is detected by scanning the earlier
+// positions of the same transaction).  Also validates ids and offsets and
+// records the longest transaction (distinct items).
+__global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
+                             uint32_t N, uint32_t* __restrict__ cnt, uint32_t* err, uint32_t* max_len) {
+  extern __shared__ uint32_t hist[];
+  const bool use_smem = N <= kSmemHistMax;
+  if (use_smem) {
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+  }
+  uint32_t local_max = 0, local_err = 0;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D; t += gridDim.x * blockDim.x) {
+    uint32_t b = off[t], e = off[t + 1];
+    if (e < b) { local_err |= DEV_ERR_OFFSETS; continue; }
+    uint32_t distinct = 0;
+    for (uint32_t k = b; k < e; ++k) {
+      uint32_t it = items[k];
+      if (it >= N) { local_err |= DEV_ERR_ITEM_RANGE; continue; }
+      bool dup = false;
+      for (uint32_t q = b; q < k && !dup; ++q) dup = items[q] == it;
+      if (dup) continue;
+      ++distinct;
+      if (use_smem) atomicAdd(&hist[it], 1u);
+      else atomicAdd(&cnt[it], 1u);
+    }
+    local_max = max(local_max, distinct);
+  }
+  if (local_err) atomicOr(err, local_err);
+  if (local_max) atomicMax(max_len, local_max);
+  if (use_smem) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+      if (hist[i]) atomicAdd(&cnt[i], hist[i]);
+  }
+}
+
+// K2: scatter transaction bits into the item-major bitmap rows of kept items.
+__global__ void k_bitmap_build(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
+                               const int32_t* __restrict__ item_rank, uint32_t* __restrict__ bits, uint32_t stride) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D; t += gridDim.x * blockDim.x) {
+    const uint32_t bit = 1u << (t & 31), word = t >> 5;
+    for (uint32_t k = off[t]; k < off[t + 1]; ++k) {
+      int32_t r = item_rank[items[k]];
+      if (r >= 0) atomicOr(&bits[(size_t)r * stride + word], bit);
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  // k-th output of SplitMix64 (Steele, Lea, Flood 2014) started at state `seed`
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Database sample D_s drawn with replacement (Sec. 6.1): sample row k is
+// transaction ((x_k >> 32) * D) >> 32; its kept items are set in bit k of the
+// sample bitmap rows (same row order as the full database).
+__global__ void k_sample_build(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
+                               const int32_t* __restrict__ item_rank, uint64_t seed, uint32_t m,
+                               uint32_t* __restrict__ sbits, uint32_t sstride) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    uint64_t x = splitmix64_at(seed, k);
+    uint32_t t = (uint32_t)(((x >> 32) * (uint64_t)D) >> 32);
+    const uint32_t bit = 1u << (k & 31), word = k >> 5;
+    for (uint32_t q = off[t]; q < off[t + 1]; ++q) {
+      int32_t r = item_rank[items[q]];
+      if (r >= 0) atomicOr(&sbits[(size_t)r * sstride + word], bit);
+    }
+  }
+}
+
+// supp[r] = popcount of row r (one CTA per row).
+__global__ void k_row_popcount(const uint32_t* __restrict__ bits, uint32_t stride, uint32_t* __restrict__ supp) {
+  const uint4* row = reinterpret_cast<const uint4*>(bits + (size_t)blockIdx.x * stride);
+  uint32_t s = 0;
+  for (uint32_t i = threadIdx.x; i < stride / 4; i += blockDim.x) {
+    uint4 v = row[i];
+    s += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+  }
+  s = __reduce_add_sync(0xffffffffu, s);
+  __shared__ uint32_t wsum[32];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) tot += wsum[w];
+    supp[blockIdx.x] = tot;
+  }
+}
+
+// tally[r] += 1 for every itemset whose lowest row (rank) is r.
+__global__ void k_tally_min_rank(const uint64_t* __restrict__ set_off, const uint32_t* __restrict__ set_items,
+                                 uint64_t n_sets, const int32_t* __restrict__ item_rank,
+                                 unsigned long long* __restrict__ tally) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_sets; s += (uint64_t)gridDim.x * blockDim.x) {
+    int32_t best = 0x7fffffff;
+    for (uint64_t q = set_off[s]; q < set_off[s + 1]; ++q) best = min(best, item_rank[set_items[q]]);
+    if (best >= 0 && best != 0x7fffffff) atomicAdd(&tally[best], 1ull);
+  }
+}
+
+uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t cap = 152 * 32) {
+  uint64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (uint32_t)g;
+}
+
+}  // namespace
+
+cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t* cnt,
+                              uint32_t* err, uint32_t* max_len, cudaStream_t st) {
+  const uint32_t threads = 256;
+  size_t smem = N <= kSmemHistMax ? (size_t)N * 4 : 0;
+  // with a shared histogram every CTA flushes N counters: keep the grid modest
+  uint32_t grid = grid_for(D, threads, N <= kSmemHistMax ? 152 * 4 : 152 * 32);
+  k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, err, max_len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
+                                uint32_t* bits, uint32_t stride, cudaStream_t st) {
+  const uint32_t threads = 256;
+  k_bitmap_build<<<grid_for(D, threads), threads, 0, st>>>(off, items, D, item_rank, bits, stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
+                                uint64_t seed, uint32_t m, uint32_t* sbits, uint32_t sstride, cudaStream_t st) {
+  const uint32_t threads = 256;
+  k_sample_build<<<grid_for(m, threads), threads, 0, st>>>(off, items, D, item_rank, seed, m, sbits, sstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t n_rows, uint32_t* supp,
+                                cudaStream_t st) {
+  if (n_rows == 0) return cudaSuccess;
+  k_row_popcount<<<n_rows, 256, 0, st>>>(bits, stride, supp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tally_min_rank(const uint64_t* set_off, const uint32_t* set_items, uint64_t n_sets,
+                                  const int32_t* item_rank, unsigned long long* tally, cudaStream_t st) {
+  if (n_sets == 0) return cudaSuccess;
+  const uint32_t threads = 256;
+  k_tally_min_rank<<<grid_for(n_sets, threads), threads, 0, st>>>(set_off, set_items, n_sets, item_rank, tally);
+  return cudaGetLastError();
+}
+
+}  // namespace fim

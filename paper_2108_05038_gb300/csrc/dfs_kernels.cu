@@ -1,0 +1,661 @@
+// Level-2 survivors, the persistent prefix-class queue, and K4: the persistent
+// depth-first Eclat kernel.
+//
+// Eclat-DFS-Computation (App. B.3.2), restated for bitmaps: a class node is a
+// prefix X with its bitmap t(X) and an ordered candidate list E; its step
+// counts c_e = popc(t(X) & t({e})) for every e in E (support of X u {e} from
+// two generating subsets, App. B.3.1), keeps the survivors S = {e : c_e >=
+// minsup}, outputs X u {e} for e in S, and expands the children
+// [X u {s_k} | s_{k+1} ...] (the PBEC split of Sec. 2.4).  t(X u {s}) is
+// materialised only for children that have children themselves.
+//
+// Level 2 comes from the pair kernel.  The classes with two-item prefixes
+// [(i, s_m) | S_i after s_m] form the static queue of the persistent kernel,
+// grouped by their top class [i] and ordered by the queue order of the top
+// classes (LPT on the sample estimate, Sec. 8.2, or the item order).  Each
+// persistent CTA pops a class and runs its whole subtree depth first with a
+// private stack (the tidlist cache C of Prepare-Tidlists, Ch. 9, holds one
+// prefix bitmap per depth).  When CTAs run idle, busy CTAs hand them the
+// next unexpanded child of their shallowest open frame through a bounded
+// pool (the dynamic load balancing of the thesis's Phase 1, restated for a
+// device work queue); a counter of unfinished entries detects termination.
+#include "fim_internal.cuh"
+
+namespace fim {
+namespace {
+
+constexpr uint32_t kCandBatch = 1024;  // candidates counted per pass (shared-memory counters)
+constexpr uint32_t kSlotHeader = 4;    // pool slot: state, xlen, ncand, spare
+enum : uint32_t { SLOT_FREE = 0, SLOT_BUSY = 1, SLOT_READY = 2 };
+
+// Exclusive block-wide scan of a 0/1 flag.  wtot: 33 shared words.  Returns
+// this thread's position among the set flags; *total = number of set flags.
+// Contains two barriers; the caller must barrier before reusing wtot.
+__device__ __forceinline__ uint32_t block_flag_scan(bool flag, uint32_t* wtot, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t ballot = __ballot_sync(0xffffffffu, flag);
+  const uint32_t wpos = __popc(ballot & ((1u << lane) - 1u));
+  if (lane == 0) wtot[warp] = __popc(ballot);
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < nw ? wtot[lane] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += u;
+    }
+    if (lane < nw) wtot[lane] = incl - v;
+    if (lane == 31) wtot[32] = incl;
+  }
+  __syncthreads();
+  *total = wtot[32];
+  return wtot[warp] + wpos;
+}
+
+// ---------------------------------------------------------------------------
+// level-2 post-processing
+
+__global__ void k_surv_count(const uint32_t* __restrict__ C2, uint32_t n1, uint32_t minsup,
+                             uint32_t* __restrict__ scnt) {
+  const uint32_t i = blockIdx.x;
+  uint32_t c = 0;
+  for (uint32_t j = i + 1 + threadIdx.x; j < n1; j += blockDim.x) c += C2[(size_t)i * n1 + j] >= minsup;
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ uint32_t ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += ws[w];
+    scnt[i] = t;
+  }
+}
+
+// One CTA: survivor offsets (row order), entry offsets (queue order), totals,
+// and the initial state of the control block.
+__global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t* __restrict__ row_order, uint32_t n1,
+                              uint32_t* __restrict__ soff, uint32_t* __restrict__ eoff, uint64_t cap_sets,
+                              uint64_t cap_items, DevCtrl* ctrl) {
+  __shared__ uint32_t wtot[33];
+  uint32_t carry_s = 0, carry_e = 0;
+  for (uint32_t base = 0; base < n1; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t vs = i < n1 ? scnt[i] : 0u;
+    uint32_t q_row = i < n1 ? row_order[i] : 0u;
+    uint32_t cq = i < n1 ? scnt[q_row] : 0u;
+    uint32_t ve = cq > 0 ? cq - 1 : 0u;
+    // two inclusive warp scans, then across warps
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t a = vs, b = ve;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t ua = __shfl_up_sync(0xffffffffu, a, o), ub = __shfl_up_sync(0xffffffffu, b, o);
+      if (lane >= (uint32_t)o) { a += ua; b += ub; }
+    }
+    __shared__ uint32_t wa[32], wb[32];
+    if (lane == 31) { wa[warp] = a; wb[warp] = b; }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t x = lane < nw ? wa[lane] : 0u, y = lane < nw ? wb[lane] : 0u;
+      uint32_t xi = x, yi = y;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t ux = __shfl_up_sync(0xffffffffu, xi, o), uy = __shfl_up_sync(0xffffffffu, yi, o);
+        if (lane >= (uint32_t)o) { xi += ux; yi += uy; }
+      }
+      if (lane < nw) { wa[lane] = xi - x; wb[lane] = yi - y; }
+      if (lane == 31) { wtot[0] = xi; wtot[1] = yi; }
+    }
+    __syncthreads();
+    if (i < n1) {
+      soff[i] = carry_s + wa[warp] + a - vs;
+      eoff[i] = carry_e + wb[warp] + b - ve;
+    }
+    carry_s += wtot[0];
+    carry_e += wtot[1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    soff[n1] = carry_s;
+    eoff[n1] = carry_e;
+    const unsigned long long P = carry_s;
+    const unsigned long long sets = n1 + P, items = n1 + 2 * P;
+    ctrl->packed = (sets << 32) | items;
+    ctrl->sets_total = sets;
+    ctrl->items_total = items;
+    ctrl->n_pairs = carry_s;
+    ctrl->n_entries = carry_e;
+    ctrl->pending = carry_e;
+    ctrl->queue_head = 0;
+    ctrl->max_len = n1 > 0 ? (P > 0 ? 2u : 1u) : 0u;
+    if (sets > cap_sets || items > cap_items) ctrl->err |= DEV_ERR_OVERFLOW;
+  }
+}
+
+// One CTA per queue position q (row i = row_order[q]): survivors of row i in
+// ascending column order, the pair records, the singleton record of row i and
+// the queue entries (i, m) of its two-item prefix classes.
+__global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint32_t minsup,
+                              const uint32_t* __restrict__ frows, const uint32_t* __restrict__ row_supp,
+                              const uint32_t* __restrict__ rank_item, const uint32_t* __restrict__ row_order,
+                              const uint32_t* __restrict__ scnt, const uint32_t* __restrict__ soff,
+                              const uint32_t* __restrict__ eoff, uint32_t* __restrict__ sitems,
+                              uint2* __restrict__ entries, uint64_t* __restrict__ out_off,
+                              uint32_t* __restrict__ out_items, uint32_t* __restrict__ out_supp, uint64_t cap_sets,
+                              uint64_t cap_items) {
+  __shared__ uint32_t wtot[33];
+  const uint32_t q = blockIdx.x;
+  const uint32_t i = row_order[q];
+  const uint32_t id_i = rank_item[frows[i]];
+  if (threadIdx.x == 0 && i < cap_sets && i < cap_items) {
+    out_off[i] = i;
+    out_items[i] = id_i;
+    out_supp[i] = row_supp[i];
+  }
+  const uint32_t ne = scnt[i] > 0 ? scnt[i] - 1 : 0u;
+  for (uint32_t m = threadIdx.x; m < ne; m += blockDim.x) entries[eoff[q] + m] = make_uint2(i, m);
+  uint32_t pos0 = 0;
+  for (uint32_t base = i + 1; base < n1; base += blockDim.x) {
+    uint32_t j = base + threadIdx.x;
+    uint32_t c = j < n1 ? C2[(size_t)i * n1 + j] : 0u;
+    bool f = j < n1 && c >= minsup;
+    uint32_t tot;
+    uint32_t pos = block_flag_scan(f, wtot, &tot);
+    if (f) {
+      uint32_t k = soff[i] + pos0 + pos;
+      sitems[k] = j;
+      uint64_t rec = (uint64_t)n1 + k, it = (uint64_t)n1 + 2ull * k;
+      if (rec < cap_sets && it + 2 <= cap_items) {
+        uint32_t id_j = rank_item[frows[j]];
+        out_off[rec] = it;
+        out_items[it] = min(id_i, id_j);
+        out_items[it + 1] = max(id_i, id_j);
+        out_supp[rec] = c;
+      }
+    }
+    pos0 += tot;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: persistent DFS
+
+struct Ctl {
+  uint32_t kind;      // 0 exit, 1 static entry, 2 pool slot
+  uint32_t a, b;      // entry (row, m) or slot index
+  uint32_t action;    // 0 pop, 1 child, 2 donate
+  uint32_t s;         // child item
+  uint32_t nc;        // child candidates
+  uint32_t cand_off;  // offset of the child's candidates in the frame list
+  uint32_t fd;        // frame to donate from
+  int32_t depth;
+  uint32_t xlen0;     // prefix length of the entry's root node
+  uint32_t nsurv;
+  uint32_t slot;
+  unsigned long long base;
+};
+
+struct DfsArgs {
+  DfsLaunch p;
+  uint32_t stride4;
+  uint32_t nseg;       // pieces per candidate row
+  uint32_t max_len;    // itemset length bound (entries of xs)
+};
+
+template <int VEC>
+__device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, const uint4* pre, uint32_t base4,
+                                               uint32_t stride4, bool pre_global) {
+  uint32_t s = 0;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    uint32_t w = base4 + v * 32;
+    if (w < stride4) {
+      uint4 a = __ldg(row + w);
+      uint4 b = pre_global ? __ldcg(pre + w) : pre[w];
+      s += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+    }
+  }
+  return s;
+}
+
+// Counts the candidates of one class node against its prefix bitmap, writes
+// the survivors (frow indices, candidate order) to out_list and one output
+// record per survivor.  All threads of the CTA call it; returns the survivor
+// count (same value in every thread).
+template <int VEC>
+__device__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32_t* wtot, const uint32_t* xid,
+                                 const uint32_t* pre, bool pre_global, const uint32_t* cand, bool cand_global,
+                                 uint32_t nc, uint32_t* out_list, uint32_t out_cap, uint32_t xlen,
+                                 unsigned long long& stat_inter) {
+  const DfsLaunch& p = A.p;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
+  uint32_t nsurv = 0;
+  if (threadIdx.x == 0) stat_inter += nc;
+  for (uint32_t b0 = 0; b0 < nc; b0 += kCandBatch) {
+    const uint32_t nb = min(kCandBatch, nc - b0);
+    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    const uint32_t total = nb * A.nseg;
+    for (uint32_t pc = warp; pc < total; pc += nw) {
+      const uint32_t k = pc / A.nseg, g = pc - k * A.nseg;
+      const uint32_t idx = cand_global ? __ldcg(cand + b0 + k) : cand[b0 + k];
+      const uint4* row = reinterpret_cast<const uint4*>(p.bits + (size_t)p.frows[idx] * p.stride);
+      uint32_t s = piece_popc<VEC>(row, pre4, g * 32 * VEC + lane, A.stride4, pre_global);
+      s = __reduce_add_sync(0xffffffffu, s);
+      if (lane == 0 && s) atomicAdd(&cnt[k], s);
+    }
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+      const uint32_t k = c0 + threadIdx.x;
+      const uint32_t ck = k < nb ? cnt[k] : 0u;
+      const bool f = k < nb && ck >= p.minsup;
+      uint32_t tot;
+      const uint32_t pos = block_flag_scan(f, wtot, &tot);
+      if (threadIdx.x == 0 && tot) {
+        const unsigned long long sets = tot, items = (unsigned long long)tot * (xlen + 1);
+        C.base = atomicAdd((unsigned long long*)&p.ctrl->packed, (sets << 32) | items);
+        atomicAdd((unsigned long long*)&p.ctrl->sets_total, sets);
+        atomicAdd((unsigned long long*)&p.ctrl->items_total, items);
+        atomicMax(&p.ctrl->max_len, xlen + 1);
+      }
+      __syncthreads();
+      if (f) {
+        const uint32_t idx = cand_global ? __ldcg(cand + b0 + k) : cand[b0 + k];
+        const uint32_t o = nsurv + pos;
+        if (o < out_cap) out_list[o] = idx;
+        else atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+        const uint64_t rec = (C.base >> 32) + pos;
+        const uint64_t it0 = (C.base & 0xffffffffull) + (uint64_t)pos * (xlen + 1);
+        if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
+          const uint32_t v = p.rank_item[p.frows[idx]];
+          uint32_t* dst = p.out_items + it0;
+          uint32_t q = 0;
+          bool placed = false;
+          for (uint32_t x = 0; x < xlen; ++x) {
+            const uint32_t u = xid[x];
+            if (!placed && v < u) { dst[q++] = v; placed = true; }
+            dst[q++] = u;
+          }
+          if (!placed) dst[q] = v;
+          p.out_off[rec] = it0;
+          p.out_supp[rec] = ck;
+        } else {
+          atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
+        }
+      }
+      nsurv += tot;
+      __syncthreads();
+    }
+  }
+  return nsurv;
+}
+
+// sorted original ids of xs[0..len) into xid (ids are distinct)
+__device__ __forceinline__ void build_xid(const DfsLaunch& p, const uint32_t* xs, uint32_t len, uint32_t* xid) {
+  for (uint32_t k = threadIdx.x; k < len; k += blockDim.x) {
+    const uint32_t v = p.rank_item[p.frows[xs[k]]];
+    uint32_t r = 0;
+    for (uint32_t q = 0; q < len; ++q) r += p.rank_item[p.frows[xs[q]]] < v;
+    xid[r] = v;
+  }
+}
+
+template <int VEC, bool PSMEM>
+__global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
+  const DfsLaunch& p = A.p;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ Ctl C;
+  __shared__ uint32_t wtot[33];
+  // dynamic shared memory: [prefix stride words (PSMEM)] [cnt kCandBatch] [f_n maxd+1] [f_cur maxd+1] [xs L+1] [xid L+1]
+  uint32_t* sp = smem;
+  uint32_t* spre = PSMEM ? sp : nullptr;
+  if (PSMEM) sp += p.stride;
+  uint32_t* cnt = sp; sp += kCandBatch;
+  uint32_t* f_n = sp; sp += p.maxd + 1;
+  uint32_t* f_cur = sp; sp += p.maxd + 1;
+  uint32_t* xs = sp; sp += A.max_len + 1;
+  uint32_t* xid = sp;
+
+  const uint32_t per_depth = p.stride + ((p.n1 + 3u) & ~3u);
+  uint32_t* arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
+#define slot_pre(d) (arena + (size_t)(d) * per_depth)
+#define slot_list(d) (arena + (size_t)(d) * per_depth + p.stride)
+  const uint32_t list_cap = p.n1;
+  const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
+
+  unsigned long long st_inter = 0, st_frames = 0, st_don = 0;
+  bool static_done = false;
+  uint32_t rot = blockIdx.x;
+  unsigned int last_progress = 0;
+
+  for (;;) {
+    // ---------------- acquire a class ----------------
+    if (threadIdx.x == 0) {
+      C.kind = 0;
+      if (!static_done) {
+        uint32_t e = atomicAdd(&p.ctrl->queue_head, 1u);
+        if (e < p.ctrl->n_entries) {
+          uint2 en = p.entries[e];
+          C.kind = 1; C.a = en.x; C.b = en.y;
+        } else {
+          static_done = true;
+        }
+      }
+      if (C.kind == 0 && p.donate) {
+        bool idle = false;
+        unsigned long long spins = 0;
+        uint32_t backoff = 64;
+        for (;;) {
+          if (*(volatile uint32_t*)&p.ctrl->n_ready > 0) {
+            for (uint32_t t = 0; t < p.pool_slots; ++t) {
+              uint32_t g = (rot + t) % p.pool_slots;
+              uint32_t* st = p.pool + (size_t)g * p.pool_slot_words;
+              if (*(volatile uint32_t*)st == SLOT_READY && atomicCAS(st, SLOT_READY, SLOT_BUSY) == SLOT_READY) {
+                __threadfence();
+                atomicSub(&p.ctrl->n_ready, 1u);
+                C.kind = 2; C.slot = g; rot = g + 1;
+                break;
+              }
+            }
+            if (C.kind == 2) break;
+          }
+          if (*(volatile uint32_t*)&p.ctrl->pending == 0) break;
+          if (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_TIMEOUT) break;
+          if (!idle) { atomicAdd(&p.ctrl->n_idle, 1u); idle = true; }
+          __nanosleep(backoff);
+          if (backoff < 2048) backoff <<= 1;
+          unsigned int prog = *(volatile unsigned int*)&p.ctrl->n_nodes;
+          if (prog != last_progress) { last_progress = prog; spins = 0; }
+          if (++spins > p.spin_limit) { atomicOr(&p.ctrl->err, DEV_ERR_TIMEOUT); break; }
+        }
+        if (idle) atomicSub(&p.ctrl->n_idle, 1u);
+      }
+    }
+    __syncthreads();
+    if (C.kind == 0) break;
+
+    // ---------------- root node of the class ----------------
+    const uint32_t* cand;
+    uint32_t nc;
+    bool cand_global;
+    const uint32_t* pre;
+    bool pre_global;
+    uint32_t* slotp = nullptr;
+    if (C.kind == 1) {
+      const uint32_t i = C.a, m = C.b;
+      const uint32_t s = p.sitems[p.soff[i] + m];
+      cand = p.sitems + p.soff[i] + m + 1;
+      nc = p.scnt[i] - m - 1;
+      cand_global = false;
+      if (threadIdx.x == 0) { xs[0] = i; xs[1] = s; C.xlen0 = 2; }
+      const uint4* r1 = bits4 + (size_t)p.frows[i] * A.stride4;
+      const uint4* r2 = bits4 + (size_t)p.frows[s] * A.stride4;
+      uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(0));
+      for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
+        uint4 a = __ldg(r1 + w), b = __ldg(r2 + w);
+        dst[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+      }
+      pre = PSMEM ? spre : slot_pre(0);
+      pre_global = false;
+    } else {
+      slotp = p.pool + (size_t)C.slot * p.pool_slot_words;
+      const uint32_t xl = __ldcg(slotp + 1);
+      nc = __ldcg(slotp + 2);
+      for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) xs[k] = __ldcg(slotp + kSlotHeader + k);
+      if (threadIdx.x == 0) C.xlen0 = xl;
+      cand = slotp + kSlotHeader + A.max_len;
+      cand_global = true;
+      const uint32_t* spref = slotp + (p.pool_slot_words - p.stride);
+      if (PSMEM) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(spref);
+        uint4* d4 = reinterpret_cast<uint4*>(spre);
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = __ldcg(s4 + w);
+        pre = spre;
+        pre_global = false;
+      } else {
+        pre = spref;
+        pre_global = true;
+      }
+    }
+    __syncthreads();
+    build_xid(p, xs, C.xlen0, xid);
+    __syncthreads();
+    const uint32_t xlen0 = C.xlen0;
+    uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, pre, pre_global, cand, cand_global, nc, slot_list(0),
+                                    list_cap, xlen0, st_inter);
+    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&p.ctrl->n_nodes, 1ull);
+    if (ns >= 2) {
+      // materialise the root prefix into the stack (it is in shared memory or the pool)
+      if (PSMEM || C.kind == 2) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(pre);
+        uint4* d4 = reinterpret_cast<uint4*>(slot_pre(0));
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = pre_global ? __ldcg(s4 + w) : s4[w];
+      }
+      if (threadIdx.x == 0) { f_n[0] = ns; f_cur[0] = 0; C.depth = 0; ++st_frames; }
+    } else if (threadIdx.x == 0) {
+      C.depth = -1;
+    }
+    __syncthreads();
+    if (C.kind == 2 && threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(slotp, SLOT_FREE);
+    }
+
+    // ---------------- depth-first expansion ----------------
+    uint32_t donate_cool = 0;
+    for (;;) {
+      __syncthreads();  // every thread has read the previous decision
+      if (threadIdx.x == 0) {
+        const int32_t d = C.depth;
+        C.action = 0;
+        if (d < 0) {
+          C.action = 4;  // class done
+        } else {
+          bool want = false;
+          if (p.donate && donate_cool == 0) {
+            const uint32_t idle = *(volatile uint32_t*)&p.ctrl->n_idle;
+            const uint32_t ready = *(volatile uint32_t*)&p.ctrl->n_ready;
+            want = idle > ready;
+          }
+          if (donate_cool) --donate_cool;
+          if (want) {
+            for (int32_t fd = 0; fd <= d; ++fd)
+              if (f_n[fd] - 1 - f_cur[fd] >= 2) { C.action = 2; C.fd = fd; break; }
+          }
+          if (C.action == 2) {
+            C.slot = 0xffffffffu;
+            for (uint32_t t = 0; t < p.pool_slots; ++t) {
+              uint32_t g = (rot + t) % p.pool_slots;
+              uint32_t* st = p.pool + (size_t)g * p.pool_slot_words;
+              if (*(volatile uint32_t*)st == SLOT_FREE && atomicCAS(st, SLOT_FREE, SLOT_BUSY) == SLOT_FREE) {
+                C.slot = g; rot = g + 1; break;
+              }
+            }
+            if (C.slot == 0xffffffffu) {
+              C.action = 0;  // pool full: expand locally
+              donate_cool = 64;
+            } else {
+              const uint32_t fd = C.fd, k = f_cur[fd];
+              C.s = slot_list(fd)[k];
+              C.cand_off = k + 1;
+              C.nc = f_n[fd] - k - 1;
+              f_cur[fd] = k + 1;
+            }
+          }
+          if (C.action == 0) {
+            if (f_cur[d] + 1 >= f_n[d]) {
+              C.depth = d - 1;
+              C.action = 3;  // frame exhausted
+            } else if ((uint32_t)(d + 1) > p.maxd) {
+              atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+              C.depth = -1;
+              C.action = 3;
+            } else {
+              const uint32_t k = f_cur[d];
+              C.action = 1;
+              C.s = slot_list(d)[k];
+              C.cand_off = k + 1;
+              C.nc = f_n[d] - k - 1;
+              f_cur[d] = k + 1;
+              xs[xlen0 + d] = C.s;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t action = C.action;
+      if (action == 4) break;
+      if (action == 3) continue;
+      if (action == 2) {
+        // hand the child [X_fd u {s} | rest of frame fd] to an idle CTA
+        const uint32_t fd = C.fd, s = C.s, ncd = C.nc, coff = C.cand_off, gslot = C.slot;
+        uint32_t* sl = p.pool + (size_t)gslot * p.pool_slot_words;
+        const uint32_t xl = xlen0 + fd + 1;
+        if (threadIdx.x == 0) { sl[1] = xl; sl[2] = ncd; }
+        for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) sl[kSlotHeader + k] = k + 1 < xl ? xs[k] : s;
+        const uint32_t* src_list = slot_list(fd) + coff;
+        for (uint32_t k = threadIdx.x; k < ncd; k += blockDim.x) sl[kSlotHeader + A.max_len + k] = src_list[k];
+        const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(fd));
+        const uint4* r4 = bits4 + (size_t)p.frows[s] * A.stride4;
+        uint4* d4 = reinterpret_cast<uint4*>(sl + (p.pool_slot_words - p.stride));
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
+          uint4 a = a4[w], b = __ldg(r4 + w);
+          d4[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          atomicAdd(&p.ctrl->pending, 1u);
+          __threadfence();
+          atomicExch(sl, SLOT_READY);
+          atomicAdd(&p.ctrl->n_ready, 1u);
+          ++st_don;
+        }
+        continue;
+      }
+      // action 1: expand the child [X_d u {s} | rest of frame d]
+      const int32_t d = C.depth;
+      const uint32_t s = C.s, ncc = C.nc, coff = C.cand_off;
+      const uint32_t xl = xlen0 + d + 1;  // prefix length of the child
+      {
+        const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(d));
+        const uint4* r4 = bits4 + (size_t)p.frows[s] * A.stride4;
+        uint4* d4 = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(d + 1));
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
+          uint4 a = a4[w], b = __ldg(r4 + w);
+          d4[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+        }
+      }
+      build_xid(p, xs, xl, xid);
+      __syncthreads();
+      uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : slot_pre(d + 1), false,
+                                      slot_list(d) + coff, false, ncc, slot_list(d + 1), list_cap, xl, st_inter);
+      if (threadIdx.x == 0) atomicAdd((unsigned long long*)&p.ctrl->n_nodes, 1ull);
+      if (n2 >= 2) {
+        if (PSMEM) {
+          const uint4* s4 = reinterpret_cast<const uint4*>(spre);
+          uint4* d4 = reinterpret_cast<uint4*>(slot_pre(d + 1));
+          for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = s4[w];
+        }
+        if (threadIdx.x == 0) { f_n[d + 1] = n2; f_cur[d + 1] = 0; C.depth = d + 1; ++st_frames; }
+      }
+    }
+    // class finished
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicSub(&p.ctrl->pending, 1u);
+    }
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd((unsigned long long*)&p.ctrl->n_intersections, st_inter);
+    atomicAdd((unsigned long long*)&p.ctrl->n_frames, st_frames);
+    atomicAdd((unsigned long long*)&p.ctrl->n_donations, st_don);
+  }
+#undef slot_pre
+#undef slot_list
+}
+
+template <int VEC, bool PSMEM>
+cudaError_t launch_dfs_t(const DfsArgs& a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_dfs<VEC, PSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dfs<VEC, PSMEM><<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool PSMEM>
+cudaError_t launch_dfs_vec(const DfsArgs& a, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
+                           cudaStream_t st) {
+  switch (vec) {
+    case 1: return launch_dfs_t<1, PSMEM>(a, grid, threads, smem, st);
+    case 2: return launch_dfs_t<2, PSMEM>(a, grid, threads, smem, st);
+    case 8: return launch_dfs_t<8, PSMEM>(a, grid, threads, smem, st);
+    default: return launch_dfs_t<4, PSMEM>(a, grid, threads, smem, st);
+  }
+}
+
+template <int VEC, bool PSMEM>
+cudaError_t occ_t(uint32_t threads, size_t smem, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(k_dfs<VEC, PSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs<VEC, PSMEM>, (int)threads, smem);
+}
+
+}  // namespace
+
+cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
+  if (p.n1 == 0) return cudaSuccess;
+  k_surv_count<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.scnt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_level2_scan<<<1, 1024, 0, st>>>(p.scnt, p.row_order, p.n1, p.soff, p.eoff, p.cap_sets, p.cap_items, p.ctrl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_level2_fill<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.frows, p.row_supp, p.rank_item, p.row_order, p.scnt,
+                                      p.soff, p.eoff, p.sitems, p.entries, p.out_off, p.out_items, p.out_supp,
+                                      p.cap_sets, p.cap_items);
+  return cudaGetLastError();
+}
+
+size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem) {
+  size_t words = (prefix_in_smem ? stride : 0) + kCandBatch + 2ull * (maxd + 1) + 2ull * (max_len + 1);
+  return words * sizeof(uint32_t);
+}
+
+bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd) {
+  return dfs_smem_bytes(stride, max_len, maxd, true) + sizeof(Ctl) + 33 * 4 + 256 <= smem_optin;
+}
+
+cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, int* out) {
+  if (prefix_in_smem) {
+    switch (vec) {
+      case 1: return occ_t<1, true>(threads, smem, out);
+      case 2: return occ_t<2, true>(threads, smem, out);
+      case 8: return occ_t<8, true>(threads, smem, out);
+      default: return occ_t<4, true>(threads, smem, out);
+    }
+  }
+  switch (vec) {
+    case 1: return occ_t<1, false>(threads, smem, out);
+    case 2: return occ_t<2, false>(threads, smem, out);
+    case 8: return occ_t<8, false>(threads, smem, out);
+    default: return occ_t<4, false>(threads, smem, out);
+  }
+}
+
+cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
+                       bool prefix_in_smem, uint32_t max_len, cudaStream_t st) {
+  DfsArgs a;
+  a.p = p;
+  a.stride4 = p.stride / 4;
+  const uint32_t segw4 = 32u * vec;  // 16-byte vectors per piece
+  a.nseg = (a.stride4 + segw4 - 1) / segw4;
+  a.max_len = max_len;
+  if (prefix_in_smem) return launch_dfs_vec<true>(a, grid, threads, vec, smem, st);
+  return launch_dfs_vec<false>(a, grid, threads, vec, smem, st);
+}
+
+}  // namespace fim

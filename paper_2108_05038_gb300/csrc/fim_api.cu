@@ -1,0 +1,689 @@
+// C ABI of the miner (include/fim.h): database build, sample-based class-cost
+// estimate, mining engine orchestration and result handling.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fim_internal.cuh"
+
+namespace fim {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+fim_status fail(fim_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+fim_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FIM_ERR_OOM : FIM_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+
+fim_status Workspace::get(int slot, size_t nbytes, void** out) {
+  if ((int)bufs.size() <= slot) bufs.resize(slot + 1);
+  DevBuf& b = bufs[slot];
+  if (nbytes == 0) nbytes = 16;
+  if (b.cap < nbytes) {
+    if (b.ptr) {
+      cudaFreeAsync(b.ptr, stream);
+      bytes -= b.cap;
+      b.ptr = nullptr;
+      b.cap = 0;
+    }
+    size_t cap = nbytes + nbytes / 4 + 256;
+    cudaError_t e = cudaMallocAsync(&b.ptr, cap, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.ptr = nullptr;
+      return cuda_fail(e, "workspace allocation");
+    }
+    b.cap = cap;
+    bytes += cap;
+  }
+  *out = b.ptr;
+  return FIM_OK;
+}
+
+void Workspace::release() {
+  for (auto& b : bufs)
+    if (b.ptr) cudaFreeAsync(b.ptr, stream);
+  bufs.clear();
+  bytes = 0;
+}
+
+template <typename T>
+static fim_status ws_get(Workspace& ws, int slot, size_t count, T** out) {
+  void* p = nullptr;
+  FIM_TRY(ws.get(slot, count * sizeof(T), &p));
+  *out = static_cast<T*>(p);
+  return FIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mining engine
+
+static uint32_t clamp_threads(uint32_t t) {
+  if (t == 128 || t == 256 || t == 512) return t;
+  return 512;
+}
+static uint32_t clamp_vec(uint32_t v) {
+  if (v == 1 || v == 2 || v == 4 || v == 8) return v;
+  return 4;
+}
+
+fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg,
+                       EngineOutput* out, fim_mine_stats* stats) {
+  cudaStream_t st = ws.stream;
+  const uint32_t n1 = in.n1;
+  *out = EngineOutput{};
+  if (stats) {
+    stats->n_frequent_items = n1;
+    stats->words_per_row = in.stride;
+  }
+  DevCtrl* d_ctrl = nullptr;
+  FIM_TRY(ws_get(ws, WS_CTRL, 1, &d_ctrl));
+  FIM_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(DevCtrl), st));
+
+  uint64_t cap_sets = cfg.cap_sets, cap_items = cfg.cap_items;
+  if (cap_sets == 0) cap_sets = std::max<uint64_t>((uint64_t)1 << 18, 8ull * n1 + 64);
+  if (cap_items == 0) cap_items = cap_sets * 6;
+  const uint64_t kMaxCap = 0xfffffff0ull;
+  cap_sets = std::min(cap_sets, kMaxCap);
+  cap_items = std::min(cap_items, kMaxCap);
+
+  if (n1 == 0) {
+    uint64_t* d_off = nullptr;
+    FIM_TRY(ws_get(ws, WS_OUT_OFF, 1, &d_off));
+    FIM_CUDA(cudaMemsetAsync(d_off, 0, sizeof(uint64_t), st));
+    out->d_off = d_off;
+    FIM_TRY(ws_get(ws, WS_OUT_ITEMS, 1, &out->d_items));
+    FIM_TRY(ws_get(ws, WS_OUT_SUPP, 1, &out->d_supp));
+    return FIM_OK;
+  }
+
+  // device copies of the row lists
+  uint32_t *d_frows = nullptr, *d_rsupp = nullptr, *d_order = nullptr;
+  FIM_TRY(ws_get(ws, WS_FROWS, n1, &d_frows));
+  FIM_TRY(ws_get(ws, WS_ROWSUPP, n1, &d_rsupp));
+  FIM_TRY(ws_get(ws, WS_ROWORDER, n1, &d_order));
+  FIM_CUDA(cudaMemcpyAsync(d_frows, in.frows.data(), n1 * 4ull, cudaMemcpyHostToDevice, st));
+  FIM_CUDA(cudaMemcpyAsync(d_rsupp, in.row_supp.data(), n1 * 4ull, cudaMemcpyHostToDevice, st));
+  FIM_CUDA(cudaMemcpyAsync(d_order, in.row_order.data(), n1 * 4ull, cudaMemcpyHostToDevice, st));
+
+  const uint64_t npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
+  uint32_t *d_C2 = nullptr, *d_scnt = nullptr, *d_soff = nullptr, *d_sitems = nullptr;
+  uint2* d_entries = nullptr;
+  FIM_TRY(ws_get(ws, WS_C2, (size_t)n1 * n1, &d_C2));
+  FIM_TRY(ws_get(ws, WS_SCNT, n1, &d_scnt));
+  FIM_TRY(ws_get(ws, WS_SOFF, 2ull * (n1 + 1), &d_soff));
+  FIM_TRY(ws_get(ws, WS_SITEMS, npairs_max + 1, &d_sitems));
+  FIM_TRY(ws_get(ws, WS_ENTRIES, npairs_max + 1, &d_entries));
+  uint32_t* d_eoff = d_soff + (n1 + 1);
+
+  // DFS geometry
+  const uint32_t L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
+  const uint32_t maxd = std::max<uint32_t>(1, L - 2);
+  const uint32_t threads = clamp_threads(cfg.threads);
+  const uint32_t vec = clamp_vec(cfg.vec);
+  const bool psmem = dfs_prefix_fits(in.stride, db->smem_optin, L, maxd);
+  const size_t smem = dfs_smem_bytes(in.stride, L, maxd, psmem);
+  int occ = 0;
+  FIM_CUDA(dfs_max_ctas_per_sm(threads, vec, smem, psmem, &occ));
+  if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
+  uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
+  const uint32_t grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);
+  const uint64_t per_depth = (uint64_t)in.stride + ((n1 + 3u) & ~3u);
+  const uint64_t arena_cta_words = per_depth * (maxd + 1);
+  uint32_t* d_arena = nullptr;
+  FIM_TRY(ws_get(ws, WS_ARENA, arena_cta_words * grid, &d_arena));
+  const uint32_t pool_slots = cfg.donate ? std::max<uint32_t>(8, grid) : 0;
+  const uint64_t pool_slot_words = (((uint64_t)kDfsSlotHeader + L + n1 + 3) & ~3ull) + in.stride;
+  uint32_t* d_pool = nullptr;
+  if (pool_slots) {
+    FIM_TRY(ws_get(ws, WS_POOL, pool_slot_words * pool_slots, &d_pool));
+    FIM_CUDA(cudaMemset2DAsync(d_pool, pool_slot_words * 4, 0, 16, pool_slots, st));
+  }
+
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (cfg.collect_times) {
+    for (auto& e : ev) FIM_CUDA(cudaEventCreate(&e));
+  }
+  auto destroy_events = [&]() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    uint64_t *d_off = nullptr;
+    uint32_t *d_items = nullptr, *d_supp = nullptr;
+    fim_status s;
+    if ((s = ws_get(ws, WS_OUT_OFF, cap_sets + 1, &d_off)) != FIM_OK ||
+        (s = ws_get(ws, WS_OUT_ITEMS, cap_items, &d_items)) != FIM_OK ||
+        (s = ws_get(ws, WS_OUT_SUPP, cap_sets, &d_supp)) != FIM_OK) {
+      destroy_events();
+      return s;
+    }
+    cudaError_t ce = cudaSuccess;
+    if (attempt > 0) ce = cudaMemsetAsync(d_ctrl, 0, sizeof(DevCtrl), st);
+    if (ev[0]) cudaEventRecord(ev[0], st);
+    uint32_t ksplit = 0;
+    if (ce == cudaSuccess) {
+      PairLaunch pl{in.bits, in.stride, d_frows, n1, d_C2, 0};
+      ce = launch_pair_counts(pl, db->num_sms, st, &ksplit);
+    }
+    if (ev[1]) cudaEventRecord(ev[1], st);
+    if (ce == cudaSuccess) {
+      LevelLaunch ll{d_C2, n1, in.minsup, d_frows, d_rsupp, in.d_rank_item, d_order, d_scnt, d_soff, d_eoff,
+                     d_sitems, d_entries, d_off, d_items, d_supp, cap_sets, cap_items, d_ctrl};
+      ce = launch_level2(ll, st);
+    }
+    if (ev[2]) cudaEventRecord(ev[2], st);
+    if (ce == cudaSuccess && n1 >= 3) {
+      DfsLaunch dl{};
+      dl.bits = in.bits;
+      dl.stride = in.stride;
+      dl.frows = d_frows;
+      dl.n1 = n1;
+      dl.minsup = in.minsup;
+      dl.rank_item = in.d_rank_item;
+      dl.soff = d_soff;
+      dl.scnt = d_scnt;
+      dl.sitems = d_sitems;
+      dl.entries = d_entries;
+      dl.arena = d_arena;
+      dl.arena_cta_words = arena_cta_words;
+      dl.maxd = maxd;
+      dl.pool = d_pool;
+      dl.pool_slots = pool_slots;
+      dl.pool_slot_words = pool_slot_words;
+      dl.out_off = d_off;
+      dl.out_items = d_items;
+      dl.out_supp = d_supp;
+      dl.cap_sets = cap_sets;
+      dl.cap_items = cap_items;
+      dl.ctrl = d_ctrl;
+      dl.spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
+      dl.donate = cfg.donate;
+      ce = launch_dfs(dl, grid, threads, vec, smem, psmem, L, st);
+    }
+    if (ev[3]) cudaEventRecord(ev[3], st);
+    if (ce != cudaSuccess) {
+      destroy_events();
+      return cuda_fail(ce, "mining kernels");
+    }
+    DevCtrl h{};
+    ce = cudaMemcpyAsync(&h, d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      destroy_events();
+      return cuda_fail(ce, "mining kernels (sync)");
+    }
+    if (h.err & DEV_ERR_TIMEOUT) {
+      destroy_events();
+      return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
+    }
+    if (h.err & DEV_ERR_DEPTH) {
+      destroy_events();
+      return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
+    }
+    const bool overflow = h.sets_total > cap_sets || h.items_total > cap_items;
+    if (overflow) {
+      if (cfg.fixed_capacity || attempt == 1) {
+        out->ctrl = h;
+        destroy_events();
+        set_error("output capacity exceeded");
+        return FIM_ERR_OUTPUT_OVERFLOW;
+      }
+      cap_sets = std::min<uint64_t>(kMaxCap, h.sets_total + h.sets_total / 16 + 16);
+      cap_items = std::min<uint64_t>(kMaxCap, h.items_total + h.items_total / 16 + 16);
+      if (h.sets_total > kMaxCap || h.items_total > kMaxCap) {
+        out->ctrl = h;
+        destroy_events();
+        return fail(FIM_ERR_OUTPUT_OVERFLOW, "result exceeds 2^32 sets or items");
+      }
+      continue;
+    }
+    const uint64_t fin = h.items_total;
+    FIM_CUDA(cudaMemcpyAsync(d_off + h.sets_total, &fin, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    out->n_sets = h.sets_total;
+    out->n_items = h.items_total;
+    out->d_off = d_off;
+    out->d_items = d_items;
+    out->d_supp = d_supp;
+    out->ctrl = h;
+    if (stats) {
+      const uint64_t rb = in.bytes_per_row_alg;
+      stats->n_frequent = h.sets_total;
+      stats->n_items_out = h.items_total;
+      stats->max_len = h.max_len;
+      stats->n_pair_intersections = npairs_max;
+      stats->n_intersections = npairs_max + h.n_intersections;
+      stats->n_classes = h.n_nodes;
+      stats->n_queue_entries = h.n_entries;
+      stats->n_donations = h.n_donations;
+      // sibling operand per intersection + one prefix read per class + materialised prefixes
+      stats->bytes_pair_kernel = npairs_max * rb + (uint64_t)(n1 - 1) * rb;
+      stats->bytes_dfs_kernel = h.n_intersections * rb + h.n_nodes * rb + h.n_frames * rb;
+      stats->bytes_algorithmic = stats->bytes_pair_kernel + stats->bytes_dfs_kernel;
+      stats->grid_ctas = n1 >= 3 ? grid : 0;
+      stats->threads_per_cta = threads;
+      stats->vec_per_lane = vec;
+      if (cfg.collect_times) {
+        cudaStreamSynchronize(st);
+        cudaEventElapsedTime(&stats->ms_pair_kernel, ev[0], ev[1]);
+        cudaEventElapsedTime(&stats->ms_dfs_kernel, ev[2], ev[3]);
+        cudaEventElapsedTime(&stats->ms_device_total, ev[0], ev[3]);
+      }
+    }
+    destroy_events();
+    return FIM_OK;
+  }
+  destroy_events();
+  return fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity exceeded");
+}
+
+// ---------------------------------------------------------------------------
+// database build
+
+static fim_status db_init(fim_db* db, uint32_t D, uint32_t N, uint32_t word_bits, uint32_t prefilter,
+                          void* stream) {
+  db->D = D;
+  db->N = N;
+  db->word_bits = word_bits;
+  db->prefilter = prefilter;
+  db->stream = static_cast<cudaStream_t>(stream);
+  db->ws.stream = db->stream;
+  FIM_CUDA(cudaGetDevice(&db->device));
+  FIM_CUDA(cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->device));
+  int optin = 0;
+  FIM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, db->device));
+  db->smem_optin = (size_t)optin;
+  db->W32 = (D + 31) / 32;
+  db->stride = ((db->W32 + 31) / 32) * 32;
+  return FIM_OK;
+}
+
+template <typename T>
+static fim_status dev_alloc(fim_db* db, T** p, size_t count) {
+  size_t bytes = std::max<size_t>(16, count * sizeof(T));
+  cudaError_t e = cudaMallocAsync((void**)p, bytes, db->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return cuda_fail(e, "device allocation");
+  }
+  db->device_bytes += bytes;
+  return FIM_OK;
+}
+
+// Items counted (K1), rows relabelled on the host, bitmaps built (K2).
+static fim_status db_build_rows(fim_db* db) {
+  cudaStream_t st = db->stream;
+  const uint32_t N = db->N, D = db->D;
+  uint32_t *d_cnt = nullptr, *d_flags = nullptr;
+  FIM_TRY(ws_get(db->ws, WS_TALLY, (size_t)N + 2, &d_cnt));
+  d_flags = d_cnt + N;  // [err, max_len]
+  FIM_CUDA(cudaMemsetAsync(d_cnt, 0, ((size_t)N + 2) * 4, st));
+  FIM_CUDA(launch_item_count(db->d_tx_off, db->d_tx_items, D, N, d_cnt, d_flags, d_flags + 1, st));
+  std::vector<uint32_t> cnt((size_t)N + 2);
+  FIM_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, ((size_t)N + 2) * 4, cudaMemcpyDeviceToHost, st));
+  FIM_CUDA(cudaStreamSynchronize(st));
+  const uint32_t err = cnt[N];
+  if (err & DEV_ERR_ITEM_RANGE) return fail(FIM_ERR_INVALID, "an item id is >= N");
+  if (err & DEV_ERR_OFFSETS) return fail(FIM_ERR_INVALID, "tx_offsets is not non-decreasing");
+  db->max_tx_len = cnt[N + 1];
+  std::vector<uint32_t> kept;
+  kept.reserve(N);
+  for (uint32_t i = 0; i < N; ++i)
+    if (cnt[i] >= db->prefilter) kept.push_back(i);
+  std::stable_sort(kept.begin(), kept.end(), [&](uint32_t a, uint32_t b) { return cnt[a] < cnt[b]; });
+  db->n_rows = (uint32_t)kept.size();
+  db->rank_item = kept;
+  db->supp.resize(db->n_rows);
+  db->item_rank.assign(N, -1);
+  for (uint32_t r = 0; r < db->n_rows; ++r) {
+    db->supp[r] = cnt[kept[r]];
+    db->item_rank[kept[r]] = (int32_t)r;
+  }
+  FIM_TRY(dev_alloc(db, &db->d_item_rank, N));
+  FIM_TRY(dev_alloc(db, &db->d_rank_item, db->n_rows));
+  FIM_TRY(dev_alloc(db, &db->d_supp, db->n_rows));
+  FIM_TRY(dev_alloc(db, &db->d_bits, (size_t)db->n_rows * db->stride));
+  FIM_CUDA(cudaMemcpyAsync(db->d_item_rank, db->item_rank.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+  if (db->n_rows) {
+    FIM_CUDA(cudaMemcpyAsync(db->d_rank_item, db->rank_item.data(), (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
+    FIM_CUDA(cudaMemcpyAsync(db->d_supp, db->supp.data(), (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
+    FIM_CUDA(cudaMemsetAsync(db->d_bits, 0, (size_t)db->n_rows * db->stride * 4, st));
+    FIM_CUDA(launch_bitmap_build(db->d_tx_off, db->d_tx_items, D, db->d_item_rank, db->d_bits, db->stride, st));
+  }
+  FIM_CUDA(cudaStreamSynchronize(st));
+  return FIM_OK;
+}
+
+static fim_status build_common(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N,
+                               uint32_t word_bits, uint32_t prefilter, void* stream, bool device_input,
+                               fim_db** out) {
+  if (!out) return fail(FIM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!off || D == 0 || N == 0) return fail(FIM_ERR_INVALID, "tx_offsets NULL or D == 0 or N == 0");
+  if (word_bits != 32 && word_bits != 64) return fail(FIM_ERR_INVALID, "word_bits must be 32 or 64");
+  fim_db* db = new (std::nothrow) fim_db();
+  if (!db) return fail(FIM_ERR_OOM, "host allocation");
+  fim_status s = db_init(db, D, N, word_bits, prefilter, stream);
+  auto bail = [&](fim_status e) {
+    fim_db_free(db);
+    return e;
+  };
+  if (s != FIM_OK) return bail(s);
+  cudaStream_t st = db->stream;
+  uint32_t first = 0, last = 0;
+  if (device_input) {
+    cudaError_t e = cudaMemcpyAsync(&first, off, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last, off + D, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "reading tx_offsets"));
+  } else {
+    first = off[0];
+    for (uint32_t t = 0; t < D; ++t)
+      if (off[t + 1] < off[t]) return bail(fail(FIM_ERR_INVALID, "tx_offsets is not non-decreasing"));
+    last = off[D];
+  }
+  if (first != 0) return bail(fail(FIM_ERR_INVALID, "tx_offsets[0] must be 0"));
+  if (last > 0 && !items) return bail(fail(FIM_ERR_INVALID, "tx_items is NULL"));
+  db->nnz = last;
+  if ((s = dev_alloc(db, &db->d_tx_off, (size_t)D + 1)) != FIM_OK) return bail(s);
+  if ((s = dev_alloc(db, &db->d_tx_items, std::max<uint64_t>(1, db->nnz))) != FIM_OK) return bail(s);
+  const cudaMemcpyKind kind = device_input ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(db->d_tx_off, off, ((size_t)D + 1) * 4, kind, st);
+  if (e == cudaSuccess && db->nnz) e = cudaMemcpyAsync(db->d_tx_items, items, db->nnz * 4, kind, st);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "copying the CSR database"));
+  if ((s = db_build_rows(db)) != FIM_OK) return bail(s);
+  *out = db;
+  return FIM_OK;
+}
+
+static void rows_for_minsup(const fim_db* db, uint32_t minsup, EngineInput* in) {
+  // rows are sorted by ascending support: the frequent ones are a suffix
+  uint32_t r0 = (uint32_t)(std::lower_bound(db->supp.begin(), db->supp.end(), minsup) - db->supp.begin());
+  in->n1 = db->n_rows - r0;
+  in->frows.resize(in->n1);
+  in->row_supp.resize(in->n1);
+  for (uint32_t k = 0; k < in->n1; ++k) {
+    in->frows[k] = r0 + k;
+    in->row_supp[k] = db->supp[r0 + k];
+  }
+}
+
+static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
+  fim_mine_opts d;
+  fim_mine_opts_init(&d);
+  if (!o || o->struct_size == 0) o = &d;
+  c->threads = o->threads_per_cta ? o->threads_per_cta : 512;
+  c->vec = o->vec_per_lane ? o->vec_per_lane : 4;
+  c->ctas_per_sm = o->ctas_per_sm;
+  c->donate = o->donate;
+  c->spin_limit = o->spin_limit;
+  c->cap_sets = o->out_capacity_sets;
+  c->cap_items = o->out_capacity_items;
+  c->fixed_capacity = o->out_capacity_sets != 0 || o->out_capacity_items != 0;
+  if (c->fixed_capacity) {
+    if (!c->cap_sets) c->cap_sets = 1;
+    if (!c->cap_items) c->cap_items = 1;
+  }
+  c->collect_times = o->collect_times != 0;
+}
+
+}  // namespace fim
+
+using namespace fim;
+
+extern "C" {
+
+void fim_mine_opts_init(fim_mine_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(fim_mine_opts);
+  o->class_order = FIM_ORDER_ESTIMATE;
+  o->donate = 1;
+}
+
+const char* fim_status_str(fim_status s) {
+  switch (s) {
+    case FIM_OK: return "FIM_OK";
+    case FIM_ERR_INVALID: return "FIM_ERR_INVALID";
+    case FIM_ERR_OOM: return "FIM_ERR_OOM";
+    case FIM_ERR_OUTPUT_OVERFLOW: return "FIM_ERR_OUTPUT_OVERFLOW";
+    case FIM_ERR_CUDA: return "FIM_ERR_CUDA";
+    case FIM_ERR_TIMEOUT: return "FIM_ERR_TIMEOUT";
+  }
+  return "FIM_ERR_UNKNOWN";
+}
+
+const char* fim_last_error(void) { return g_last_error.c_str(); }
+
+fim_status fim_build_vertical_db(const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D, uint32_t N,
+                                 uint32_t word_bits, uint32_t prefilter_minsup, void* cuda_stream, fim_db** out) {
+  return build_common(tx_offsets, tx_items, D, N, word_bits, prefilter_minsup, cuda_stream, false, out);
+}
+
+fim_status fim_build_vertical_db_device(const uint32_t* d_tx_offsets, const uint32_t* d_tx_items, uint32_t D,
+                                        uint32_t N, uint32_t word_bits, uint32_t prefilter_minsup,
+                                        void* cuda_stream, fim_db** out) {
+  return build_common(d_tx_offsets, d_tx_items, D, N, word_bits, prefilter_minsup, cuda_stream, true, out);
+}
+
+fim_status fim_db_info(const fim_db* db, uint32_t* D, uint32_t* N, uint32_t* n_rows, uint32_t* words_per_row,
+                       uint32_t* word_bits, uint64_t* device_bytes) {
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (D) *D = db->D;
+  if (N) *N = db->N;
+  if (n_rows) *n_rows = db->n_rows;
+  if (words_per_row) *words_per_row = db->stride;
+  if (word_bits) *word_bits = db->word_bits;
+  if (device_bytes) *device_bytes = db->device_bytes + db->ws.bytes;
+  return FIM_OK;
+}
+
+fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports) {
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (rank_item && db->n_rows) std::memcpy(rank_item, db->rank_item.data(), db->n_rows * 4ull);
+  if (supports && db->n_rows) std::memcpy(supports, db->supp.data(), db->n_rows * 4ull);
+  return FIM_OK;
+}
+
+fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
+                                    double* cost_out, uint32_t* order_out) {
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (!(sample_rate > 0.0 && sample_rate <= 1.0)) return fail(FIM_ERR_INVALID, "sample_rate must be in (0, 1]");
+  if (!(rel_minsup >= 0.0 && rel_minsup <= 1.0)) return fail(FIM_ERR_INVALID, "rel_minsup must be in [0, 1]");
+  cudaStream_t st = db->stream;
+  const double md = std::ceil(sample_rate * (double)db->D);
+  const uint32_t m = md < 1.0 ? 1u : (uint32_t)md;
+  const double msd = std::ceil(rel_minsup * (double)m);
+  const uint32_t minsup_s = msd < 1.0 ? 1u : (uint32_t)msd;
+  const uint32_t sw = (m + 31) / 32, sstride = ((sw + 31) / 32) * 32;
+  const uint32_t R = db->n_rows;
+  uint32_t *d_sbits = nullptr, *d_ssupp = nullptr;
+  FIM_TRY(ws_get(db->ws, WS_SAMPLE_BITS, (size_t)std::max<uint32_t>(R, 1) * sstride, &d_sbits));
+  FIM_TRY(ws_get(db->ws, WS_SAMPLE_SUPP, std::max<uint32_t>(R, 1), &d_ssupp));
+  std::vector<uint32_t> ssupp(R);
+  if (R) {
+    FIM_CUDA(cudaMemsetAsync(d_sbits, 0, (size_t)R * sstride * 4, st));
+    FIM_CUDA(launch_sample_build(db->d_tx_off, db->d_tx_items, db->D, db->d_item_rank, seed, m, d_sbits, sstride, st));
+    FIM_CUDA(launch_row_popcount(d_sbits, sstride, R, d_ssupp, st));
+    FIM_CUDA(cudaMemcpyAsync(ssupp.data(), d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+    FIM_CUDA(cudaStreamSynchronize(st));
+  }
+  EngineInput in;
+  in.bits = d_sbits;
+  in.stride = sstride;
+  in.bytes_per_row_alg = (uint32_t)(((uint64_t)m + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
+  for (uint32_t r = 0; r < R; ++r)
+    if (ssupp[r] >= minsup_s) {
+      in.frows.push_back(r);
+      in.row_supp.push_back(ssupp[r]);
+    }
+  in.n1 = (uint32_t)in.frows.size();
+  in.row_order.resize(in.n1);
+  std::iota(in.row_order.begin(), in.row_order.end(), 0u);
+  in.d_rank_item = db->d_rank_item;
+  in.minsup = minsup_s;
+  in.max_len_bound = db->max_tx_len;
+  EngineConfig cfg;
+  cfg.donate = 1;
+  EngineOutput eo;
+  FIM_TRY(engine_mine(db, db->ws, in, cfg, &eo, nullptr));
+  std::vector<unsigned long long> tally(R, 0ull);
+  if (R) {
+    unsigned long long* d_tally = nullptr;
+    FIM_TRY(ws_get(db->ws, WS_TALLY, R, &d_tally));
+    FIM_CUDA(cudaMemsetAsync(d_tally, 0, (size_t)R * 8, st));
+    FIM_CUDA(launch_tally_min_rank(eo.d_off, eo.d_items, eo.n_sets, db->d_item_rank, d_tally, st));
+    FIM_CUDA(cudaMemcpyAsync(tally.data(), d_tally, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+    FIM_CUDA(cudaStreamSynchronize(st));
+  }
+  db->est_cost.assign(R, 0.0);
+  for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = eo.n_sets ? (double)tally[r] / (double)eo.n_sets : 0.0;
+  db->est_order.resize(R);
+  std::iota(db->est_order.begin(), db->est_order.end(), 0u);
+  std::stable_sort(db->est_order.begin(), db->est_order.end(),
+                   [&](uint32_t a, uint32_t b) { return db->est_cost[a] > db->est_cost[b]; });
+  db->has_estimate = true;
+  db->est_nfs = eo.n_sets;
+  db->est_m = m;
+  db->est_minsup = minsup_s;
+  if (cost_out && R) std::memcpy(cost_out, db->est_cost.data(), R * sizeof(double));
+  if (order_out && R) std::memcpy(order_out, db->est_order.data(), R * sizeof(uint32_t));
+  return FIM_OK;
+}
+
+fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, uint32_t* sample_rows,
+                                    uint32_t* sample_minsup) {
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (!db->has_estimate) return fail(FIM_ERR_INVALID, "no estimate computed");
+  if (n_sample_fis) *n_sample_fis = db->est_nfs;
+  if (sample_rows) *sample_rows = db->est_m;
+  if (sample_minsup) *sample_minsup = db->est_minsup;
+  return FIM_OK;
+}
+
+fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_result** out) {
+  if (!out) return fail(FIM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (minsup_abs == 0) return fail(FIM_ERR_INVALID, "minsup 0 makes every subset frequent");
+  if (minsup_abs < db->prefilter)
+    return fail(FIM_ERR_INVALID, "minsup below the prefilter support of the database");
+  if (opts && opts->struct_size != 0 && opts->struct_size != sizeof(fim_mine_opts))
+    return fail(FIM_ERR_INVALID, "fim_mine_opts.struct_size mismatch");
+  EngineInput in;
+  rows_for_minsup(db, minsup_abs, &in);
+  in.bits = db->d_bits;
+  in.stride = db->stride;
+  in.bytes_per_row_alg = (uint32_t)(((uint64_t)db->D + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
+  in.d_rank_item = db->d_rank_item;
+  in.minsup = minsup_abs;
+  in.max_len_bound = db->max_tx_len;
+  const uint32_t order = opts && opts->struct_size ? opts->class_order : (uint32_t)FIM_ORDER_ESTIMATE;
+  in.row_order.clear();
+  in.row_order.reserve(in.n1);
+  if (order == FIM_ORDER_ESTIMATE && db->has_estimate && in.n1) {
+    const uint32_t r0 = db->n_rows - in.n1;
+    for (uint32_t r : db->est_order)
+      if (r >= r0) in.row_order.push_back(r - r0);
+  } else {
+    for (uint32_t k = 0; k < in.n1; ++k) in.row_order.push_back(k);
+  }
+  EngineConfig cfg;
+  engine_config_from_opts(opts, &cfg);
+  fim_mine_stats local_stats{};
+  fim_mine_stats* stats = opts && opts->struct_size && opts->stats ? opts->stats : &local_stats;
+  std::memset(stats, 0, sizeof(*stats));
+  EngineOutput eo;
+  fim_status s = engine_mine(db, db->ws, in, cfg, &eo, stats);
+  if (s == FIM_ERR_OUTPUT_OVERFLOW && opts && opts->struct_size) {
+    opts->out_needed_sets = eo.ctrl.sets_total;
+    opts->out_needed_items = eo.ctrl.items_total;
+  }
+  if (s != FIM_OK) return s;
+  fim_result* res = new (std::nothrow) fim_result();
+  if (!res) return fail(FIM_ERR_OOM, "host allocation");
+  res->n_sets = eo.n_sets;
+  res->n_items = eo.n_items;
+  res->stream = db->stream;
+  cudaStream_t st = db->stream;
+  const bool on_dev = opts && opts->struct_size && opts->result_on_device;
+  cudaError_t e = cudaSuccess;
+  if (on_dev) {
+    res->on_device = 1;
+    e = cudaMallocAsync((void**)&res->d_off, (eo.n_sets + 1) * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&res->d_items, std::max<uint64_t>(1, eo.n_items) * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&res->d_supp, std::max<uint64_t>(1, eo.n_sets) * 4, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res->d_off, eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && eo.n_items)
+      e = cudaMemcpyAsync(res->d_items, eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && eo.n_sets)
+      e = cudaMemcpyAsync(res->d_supp, eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToDevice, st);
+  } else {
+    res->h_off.resize(eo.n_sets + 1);
+    res->h_items.resize(eo.n_items);
+    res->h_supp.resize(eo.n_sets);
+    e = cudaMemcpyAsync(res->h_off.data(), eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && eo.n_items)
+      e = cudaMemcpyAsync(res->h_items.data(), eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && eo.n_sets)
+      e = cudaMemcpyAsync(res->h_supp.data(), eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    fim_result_free(res);
+    return cuda_fail(e, "copying the result");
+  }
+  *out = res;
+  return FIM_OK;
+}
+
+fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,
+                           const uint32_t** set_items, const uint32_t** supports, int* on_device) {
+  if (!res) return fail(FIM_ERR_INVALID, "result is NULL");
+  if (n_sets) *n_sets = res->n_sets;
+  if (on_device) *on_device = res->on_device;
+  if (res->on_device) {
+    if (set_offsets) *set_offsets = res->d_off;
+    if (set_items) *set_items = res->d_items;
+    if (supports) *supports = res->d_supp;
+  } else {
+    if (set_offsets) *set_offsets = res->h_off.data();
+    if (set_items) *set_items = res->h_items.data();
+    if (supports) *supports = res->h_supp.data();
+  }
+  return FIM_OK;
+}
+
+void fim_result_free(fim_result* res) {
+  if (!res) return;
+  if (res->d_off) cudaFreeAsync(res->d_off, res->stream);
+  if (res->d_items) cudaFreeAsync(res->d_items, res->stream);
+  if (res->d_supp) cudaFreeAsync(res->d_supp, res->stream);
+  delete res;
+}
+
+void fim_db_free(fim_db* db) {
+  if (!db) return;
+  cudaStream_t st = db->stream;
+  db->ws.release();
+  void* ptrs[] = {db->d_bits, db->d_rank_item, db->d_item_rank, db->d_supp, db->d_tx_off, db->d_tx_items};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, st);
+  cudaStreamSynchronize(st);
+  delete db;
+}
+
+}  // extern "C"

@@ -1,0 +1,274 @@
+// Internal declarations shared by the CUDA translation units of the miner.
+// Nothing here is part of the C ABI (include/fim.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fim.h"
+
+namespace fim {
+
+// ---------------------------------------------------------------------------
+// error reporting
+
+void set_error(const std::string& msg);
+fim_status fail(fim_status s, const std::string& msg);
+fim_status cuda_fail(cudaError_t e, const char* what);
+
+#define FIM_CUDA(call)                                                  \
+  do {                                                                  \
+    cudaError_t e__ = (call);                                           \
+    if (e__ != cudaSuccess) return ::fim::cuda_fail(e__, #call);       \
+  } while (0)
+
+#define FIM_TRY(call)                          \
+  do {                                         \
+    fim_status s__ = (call);                   \
+    if (s__ != FIM_OK) return s__;             \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device-side error bits (uint32 flag word)
+
+enum : uint32_t {
+  DEV_ERR_ITEM_RANGE = 1u << 0,   // an item id >= N in the CSR
+  DEV_ERR_OFFSETS = 1u << 1,      // tx_offsets decreasing
+  DEV_ERR_DEPTH = 1u << 2,        // DFS deeper than the arena was sized for
+  DEV_ERR_TIMEOUT = 1u << 3,      // a bounded wait ran out
+  DEV_ERR_OVERFLOW = 1u << 4,     // output capacity exceeded (counts keep going)
+  DEV_ERR_POOL = 1u << 5,         // donation pool protocol violated
+};
+
+// ---------------------------------------------------------------------------
+// stream-ordered device buffers, grown on demand and reused across calls
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t cap = 0;
+};
+
+struct Workspace {
+  cudaStream_t stream = nullptr;
+  std::vector<DevBuf> bufs;
+  uint64_t bytes = 0;
+  // returns a buffer of at least `bytes` bytes in slot `slot` (contents undefined)
+  fim_status get(int slot, size_t bytes, void** out);
+  void release();
+};
+
+enum WsSlot {
+  WS_C2 = 0,
+  WS_SCNT,
+  WS_SOFF,
+  WS_SITEMS,
+  WS_ENTRIES,
+  WS_ROWORDER,
+  WS_FROWS,
+  WS_ROWSUPP,
+  WS_ARENA,
+  WS_OUT_OFF,
+  WS_OUT_ITEMS,
+  WS_OUT_SUPP,
+  WS_CTRL,
+  WS_POOL,
+  WS_SAMPLE_BITS,
+  WS_SAMPLE_SUPP,
+  WS_TALLY,
+  WS_COUNT
+};
+
+// small control block living in device memory (one per mining call)
+struct DevCtrl {
+  unsigned long long packed;       // (records << 32) | items reserved so far
+  unsigned long long items_total;  // exact items requested (for overflow reporting)
+  unsigned long long sets_total;   // exact sets requested
+  unsigned long long n_intersections;
+  unsigned long long n_nodes;
+  unsigned long long n_frames;     // prefixes materialised into the arena
+  unsigned long long n_donations;
+  uint32_t queue_head;             // next static queue entry
+  uint32_t n_entries;              // static queue length (written by the scan kernel)
+  uint32_t err;                    // DEV_ERR_* bits
+  uint32_t max_len;                // longest itemset emitted
+  uint32_t n_pairs;                // frequent pairs
+  uint32_t pending;                // unfinished queue entries (termination detection)
+  uint32_t n_idle;                 // CTAs waiting for work
+  uint32_t n_ready;                // donated entries waiting in the pool
+  uint32_t pad[4];
+};
+
+// ---------------------------------------------------------------------------
+// the database object (C ABI opaque type)
+
+}  // namespace fim
+
+struct fim_db {
+  uint32_t D = 0, N = 0, n_rows = 0;
+  uint32_t W32 = 0;      // ceil(D / 32): 32-bit words holding D bits
+  uint32_t stride = 0;   // padded 32-bit words per row (multiple of 32 = 128 bytes)
+  uint32_t word_bits = 64;
+  uint32_t prefilter = 0;
+  uint32_t max_tx_len = 0;  // longest transaction (distinct kept items)
+  uint64_t nnz = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+
+  uint32_t* d_bits = nullptr;       // n_rows * stride
+  uint32_t* d_rank_item = nullptr;  // n_rows
+  int32_t* d_item_rank = nullptr;   // N
+  uint32_t* d_supp = nullptr;       // n_rows
+  uint32_t* d_tx_off = nullptr;     // D + 1
+  uint32_t* d_tx_items = nullptr;   // nnz
+  uint64_t device_bytes = 0;
+
+  std::vector<uint32_t> rank_item, supp;
+  std::vector<int32_t> item_rank;
+
+  // last estimate (fim_estimate_class_costs)
+  bool has_estimate = false;
+  std::vector<double> est_cost;
+  std::vector<uint32_t> est_order;
+  uint64_t est_nfs = 0;
+  uint32_t est_m = 0, est_minsup = 0;
+
+  fim::Workspace ws;
+};
+
+struct fim_result {
+  uint64_t n_sets = 0;
+  uint64_t n_items = 0;
+  int on_device = 0;
+  std::vector<uint64_t> h_off;
+  std::vector<uint32_t> h_items, h_supp;
+  uint64_t* d_off = nullptr;
+  uint32_t* d_items = nullptr;
+  uint32_t* d_supp = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+namespace fim {
+
+// ---------------------------------------------------------------------------
+// mining engine (shared by fim_mine and the sample mining of the estimate)
+
+struct EngineInput {
+  const uint32_t* bits = nullptr;  // rows of `stride` words
+  uint32_t stride = 0;             // padded words per row
+  uint32_t bytes_per_row_alg = 0;  // W * w / 8: unpadded bytes of one row (algorithmic)
+  uint32_t n1 = 0;                 // frequent rows taking part
+  std::vector<uint32_t> frows;     // ascending row ids (host), n1 entries
+  std::vector<uint32_t> row_supp;  // support of each frequent row, n1 entries
+  std::vector<uint32_t> row_order; // queue order of the top classes (permutation of 0..n1-1)
+  const uint32_t* d_rank_item = nullptr;  // row -> original item id
+  uint32_t minsup = 1;
+  uint32_t max_len_bound = 2;      // upper bound on the length of a frequent itemset
+};
+
+struct EngineOutput {
+  uint64_t n_sets = 0, n_items = 0;
+  uint64_t* d_off = nullptr;   // workspace-owned
+  uint32_t* d_items = nullptr;
+  uint32_t* d_supp = nullptr;
+  DevCtrl ctrl{};
+};
+
+struct EngineConfig {
+  uint32_t threads = 512;
+  uint32_t vec = 4;
+  uint32_t ctas_per_sm = 0;
+  uint32_t donate = 1;
+  uint32_t dynamic_order = 0;
+  uint64_t spin_limit = 0;
+  uint64_t cap_sets = 0, cap_items = 0;  // 0 = automatic
+  bool fixed_capacity = false;
+  bool collect_times = false;
+};
+
+fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg,
+                       EngineOutput* out, fim_mine_stats* stats);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+
+cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t* cnt,
+                              uint32_t* err, uint32_t* max_len, cudaStream_t st);
+cudaError_t launch_bitmap_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
+                                uint32_t* bits, uint32_t stride, cudaStream_t st);
+cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
+                                uint64_t seed, uint32_t m, uint32_t* sbits, uint32_t sstride, cudaStream_t st);
+cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t n_rows, uint32_t* supp,
+                                cudaStream_t st);
+cudaError_t launch_tally_min_rank(const uint64_t* set_off, const uint32_t* set_items, uint64_t n_sets,
+                                  const int32_t* item_rank, unsigned long long* tally, cudaStream_t st);
+
+struct PairLaunch {
+  const uint32_t* bits;
+  uint32_t stride;
+  const uint32_t* frows;
+  uint32_t n1;
+  uint32_t* C2;  // n1 * n1
+  uint32_t ksplit;
+};
+cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used);
+
+struct LevelLaunch {
+  const uint32_t* C2;
+  uint32_t n1;
+  uint32_t minsup;
+  const uint32_t* frows;
+  const uint32_t* row_supp;
+  const uint32_t* rank_item;
+  const uint32_t* row_order;    // queue position -> row
+  uint32_t* scnt;               // n1 survivors per row
+  uint32_t* soff;               // n1 + 1 survivor offsets (natural row order)
+  uint32_t* eoff;               // n1 + 1 entry offsets (queue order)
+  uint32_t* sitems;             // survivors (frow indices)
+  uint2* entries;               // (row, m)
+  uint64_t* out_off;
+  uint32_t* out_items;
+  uint32_t* out_supp;
+  uint64_t cap_sets, cap_items;
+  DevCtrl* ctrl;
+};
+cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st);
+
+struct DfsLaunch {
+  const uint32_t* bits;
+  uint32_t stride;
+  const uint32_t* frows;
+  uint32_t n1;
+  uint32_t minsup;
+  const uint32_t* rank_item;
+  const uint32_t* soff;
+  const uint32_t* scnt;
+  const uint32_t* sitems;
+  const uint2* entries;
+  uint32_t* arena;
+  uint64_t arena_cta_words;
+  uint32_t maxd;
+  uint32_t* pool;           // donation pool (slots)
+  uint32_t pool_slots;
+  uint64_t pool_slot_words;
+  uint64_t* out_off;
+  uint32_t* out_items;
+  uint32_t* out_supp;
+  uint64_t cap_sets, cap_items;
+  DevCtrl* ctrl;
+  uint64_t spin_limit;
+  uint32_t donate;
+};
+// grid: number of persistent CTAs; threads: CTA size; vec: 16-byte loads per lane per piece
+cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
+                       bool prefix_in_smem, uint32_t max_len, cudaStream_t st);
+size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem);
+cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, int* out);
+bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd);
+constexpr uint32_t kDfsSlotHeader = 4;  // donation pool slot: state, xlen, ncand, spare
+
+}  // namespace fim

@@ -1,0 +1,167 @@
+// K5: level-2 supports of all pairs of frequent items by bitmap AND + popcount.
+//
+// supp({a,b}) = |t({a}) n t({b})| (App. B.3.1; Lemma and Corollary of Sec. 2.4)
+// for every pair of frequent rows i < j, i.e. the first DFS step of Eclat
+// (App. B.3.2) for all one-item prefix classes [i | {j > i}] at once.  The
+// n1 x n1 block of pair counts is a dense contraction over the transaction
+// bits, so it is tiled like a GEMM: a CTA owns a 64 x 64 tile of (i, j) pairs
+// (upper triangle only), stages 32-word slices of the 64 + 64 rows in shared
+// memory with cp.async (3-stage pipeline), and every thread accumulates a 4 x 4
+// micro-tile.  Each staged word is reused by 64 pairs, so the kernel is bound
+// by the integer pipe (AND + POPC per word pair), not by memory.  Long rows
+// are split along the word axis over grid.y (partial counts added atomically).
+#include "fim_internal.cuh"
+
+namespace fim {
+namespace {
+
+constexpr int kTile = 64;      // rows per tile side
+constexpr int kChunk = 32;     // words staged per row per pipeline stage
+constexpr int kRowPad = 36;    // padded shared-memory row (words): conflict-free 16-byte loads
+constexpr int kStages = 3;
+constexpr int kThreads = 256;
+constexpr size_t kSmemBytes = (size_t)kStages * 2 * kTile * kRowPad * sizeof(uint32_t);
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, uint32_t src_bytes) {
+  uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem_src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// acc += popc(a & b): AND and POPC on the integer pipe, the add as a
+// multiply-add by a runtime one so that it can issue on the FMA pipe.
+__device__ __forceinline__ void acc_and_popc(uint32_t& acc, uint32_t a, uint32_t b, uint32_t one) {
+  uint32_t p = __popc(a & b);
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(p), "r"(one));
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows, uint32_t n1,
+              uint32_t nb, uint32_t chunks_per_split, uint32_t nchunks, uint32_t* __restrict__ C2, uint32_t ksplit,
+              uint32_t one) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const uint32_t tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+
+  uint32_t t = blockIdx.x, bi = 0;
+  while (t >= nb - bi) { t -= nb - bi; ++bi; }
+  const uint32_t bj = bi + t;
+  const uint32_t i0 = bi * kTile, j0 = bj * kTile;
+  const uint32_t c_begin = blockIdx.y * chunks_per_split;
+  const uint32_t c_end = min(nchunks, c_begin + chunks_per_split);
+  if (c_begin >= c_end) return;
+
+  // four 16-byte copies per thread and stage: 64 A rows + 64 B rows x 8 vectors.
+  // Copy q moves vector (tid & 7) of tile row (tid >> 3) + 32 * (q & 1) of A (q < 2) or B.
+  const uint32_t lr = tid >> 3, lc = tid & 7;
+  const uint32_t* src[4];
+  uint32_t okmask = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t g = (q < 2 ? i0 : j0) + lr + 32 * (q & 1);
+    bool ok = g < n1;
+    okmask |= (ok ? 1u : 0u) << q;
+    src[q] = bits + (size_t)frows[ok ? g : 0] * stride + lc * 4;
+  }
+  auto load_stage = [&](uint32_t stage, uint32_t chunk) {
+    uint32_t* base = sm + stage * (2 * kTile * kRowPad);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t dst = ((q >> 1) * kTile + lr + 32 * (q & 1)) * kRowPad + lc * 4;
+      cp_async16(base + dst, src[q] + (size_t)chunk * kChunk, (okmask >> q) & 1u ? 16u : 0u);
+    }
+  };
+
+  uint32_t acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0;
+
+#pragma unroll
+  for (int s = 0; s < kStages - 1; ++s) {
+    if (c_begin + s < c_end) load_stage(s, c_begin + s);
+    cp_async_commit();
+  }
+  uint32_t stage = 0;
+  for (uint32_t c = c_begin; c < c_end; ++c) {
+    cp_async_wait<kStages - 2>();
+    __syncthreads();
+    {
+      uint32_t nc = c + kStages - 1;
+      uint32_t ns = stage + kStages - 1;
+      if (ns >= kStages) ns -= kStages;
+      if (nc < c_end) load_stage(ns, nc);
+      cp_async_commit();
+    }
+    const uint32_t* As = sm + stage * (2 * kTile * kRowPad);
+    const uint32_t* Bs = As + kTile * kRowPad;
+#pragma unroll 2
+    for (int kk = 0; kk < kChunk / 4; ++kk) {
+      uint4 b[4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) b[y] = *reinterpret_cast<const uint4*>(Bs + (tx + 16 * y) * kRowPad + kk * 4);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const uint4 a = *reinterpret_cast<const uint4*>(As + (ty + 16 * x) * kRowPad + kk * 4);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          acc_and_popc(acc[x][y], a.x, b[y].x, one);
+          acc_and_popc(acc[x][y], a.y, b[y].y, one);
+          acc_and_popc(acc[x][y], a.z, b[y].z, one);
+          acc_and_popc(acc[x][y], a.w, b[y].w, one);
+        }
+      }
+    }
+    stage = stage + 1 == kStages ? 0 : stage + 1;
+  }
+  cp_async_wait<0>();
+
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      uint32_t i = i0 + ty + 16 * x, j = j0 + tx + 16 * y;
+      if (i < j && j < n1) {
+        if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], acc[x][y]);
+        else C2[(size_t)i * n1 + j] = acc[x][y];
+      }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used) {
+  if (p.n1 < 2) { *ksplit_used = 0; return cudaSuccess; }
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_pair_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const uint32_t nb = (p.n1 + kTile - 1) / kTile;
+  const uint32_t tiles = nb * (nb + 1) / 2;
+  const uint32_t nchunks = p.stride / kChunk;  // stride is a multiple of 32 words
+  uint32_t ksplit = p.ksplit;
+  if (ksplit == 0) {
+    // enough CTAs for ~2 resident per SM, but at least 8 chunks (256 words) per split
+    uint32_t target = (uint32_t)num_sms * 2;
+    ksplit = (target + tiles - 1) / tiles;
+    uint32_t maxsplit = nchunks / 8 > 0 ? nchunks / 8 : 1;
+    if (ksplit > maxsplit) ksplit = maxsplit;
+    if (ksplit < 1) ksplit = 1;
+  }
+  uint32_t cps = (nchunks + ksplit - 1) / ksplit;
+  ksplit = (nchunks + cps - 1) / cps;
+  *ksplit_used = ksplit;
+  if (ksplit > 1) {
+    cudaError_t e = cudaMemsetAsync(p.C2, 0, (size_t)p.n1 * p.n1 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(tiles, ksplit);
+  k_pair_counts<<<grid, kThreads, kSmemBytes, st>>>(p.bits, p.stride, p.frows, p.n1, nb, cps, nchunks, p.C2, ksplit, 1u);
+  return cudaGetLastError();
+}
+
+}  // namespace fim

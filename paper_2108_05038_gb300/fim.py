@@ -1,0 +1,292 @@
+"""Python binding of the C ABI in include/fim.h (argument marshalling only).
+
+Every step of the mining path runs in libfimgpu.so; this module converts
+numpy/torch buffers to pointers, calls the entry point of the same name and
+turns the returned CSR arrays into numpy arrays.  There is no CPU fallback:
+if the library cannot be built or loaded, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+FIM_OK, FIM_ERR_INVALID, FIM_ERR_OOM, FIM_ERR_OUTPUT_OVERFLOW, FIM_ERR_CUDA, FIM_ERR_TIMEOUT = range(6)
+FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
+
+# every symbol declared in include/fim.h
+EXPORTED = [
+    "fim_mine_opts_init", "fim_build_vertical_db", "fim_build_vertical_db_device", "fim_db_info", "fim_db_rows",
+    "fim_estimate_class_costs", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
+    "fim_db_free", "fim_status_str", "fim_last_error",
+]
+
+
+class FimError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+STATUS_NAMES = {0: "FIM_OK", 1: "FIM_ERR_INVALID", 2: "FIM_ERR_OOM", 3: "FIM_ERR_OUTPUT_OVERFLOW", 4: "FIM_ERR_CUDA",
+                5: "FIM_ERR_TIMEOUT"}
+
+
+class MineStats(ctypes.Structure):
+    _fields_ = [
+        ("n_frequent", ctypes.c_uint64), ("n_items_out", ctypes.c_uint64), ("n_frequent_items", ctypes.c_uint32),
+        ("max_len", ctypes.c_uint32), ("n_intersections", ctypes.c_uint64), ("n_pair_intersections", ctypes.c_uint64),
+        ("n_classes", ctypes.c_uint64), ("n_queue_entries", ctypes.c_uint64), ("n_donations", ctypes.c_uint64),
+        ("bytes_algorithmic", ctypes.c_uint64), ("bytes_pair_kernel", ctypes.c_uint64),
+        ("bytes_dfs_kernel", ctypes.c_uint64), ("words_per_row", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
+        ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ms_pair_kernel", ctypes.c_float),
+        ("ms_dfs_kernel", ctypes.c_float), ("ms_device_total", ctypes.c_float), ("reserved_f", ctypes.c_float),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+
+
+class MineOpts(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("class_order", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+        ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+        ("donate", ctypes.c_uint32), ("result_on_device", ctypes.c_uint32), ("collect_times", ctypes.c_uint32),
+        ("reserved_u", ctypes.c_uint32), ("out_capacity_sets", ctypes.c_uint64),
+        ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("out_needed_sets", ctypes.c_uint64),
+        ("out_needed_items", ctypes.c_uint64), ("stats", ctypes.POINTER(MineStats)),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libfimgpu.so (building it first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_stale and (not os.path.exists(_build.LIB) or _build.stale()):
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise FimError(FIM_ERR_CUDA, "load", f"{_build.LIB} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(_build.LIB)
+        P, u32, u64, dbl = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        i32 = ctypes.c_int
+        lib.fim_mine_opts_init.restype = None
+        lib.fim_mine_opts_init.argtypes = [ctypes.POINTER(MineOpts)]
+        for name in ("fim_build_vertical_db", "fim_build_vertical_db_device"):
+            f = getattr(lib, name)
+            f.restype = i32
+            f.argtypes = [P, P, u32, u32, u32, u32, P, PP]
+        lib.fim_db_info.restype = i32
+        lib.fim_db_info.argtypes = [P] + [ctypes.POINTER(u32)] * 5 + [ctypes.POINTER(u64)]
+        lib.fim_db_rows.restype = i32
+        lib.fim_db_rows.argtypes = [P, P, P]
+        lib.fim_estimate_class_costs.restype = i32
+        lib.fim_estimate_class_costs.argtypes = [P, dbl, dbl, u64, P, P]
+        lib.fim_estimate_sample_size.restype = i32
+        lib.fim_estimate_sample_size.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.fim_mine.restype = i32
+        lib.fim_mine.argtypes = [P, u32, ctypes.POINTER(MineOpts), PP]
+        lib.fim_result_view.restype = i32
+        lib.fim_result_view.argtypes = [P, ctypes.POINTER(u64), PP, PP, PP, ctypes.POINTER(i32)]
+        lib.fim_result_free.restype = None
+        lib.fim_result_free.argtypes = [P]
+        lib.fim_db_free.restype = None
+        lib.fim_db_free.argtypes = [P]
+        lib.fim_status_str.restype = ctypes.c_char_p
+        lib.fim_status_str.argtypes = [i32]
+        lib.fim_last_error.restype = ctypes.c_char_p
+        lib.fim_last_error.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _check(lib, status: int, where: str):
+    if status != FIM_OK:
+        raise FimError(status, where, lib.fim_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Address of a numpy array, a torch tensor, or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Result:
+    """Frequent itemsets in CSR form; numpy arrays for host results."""
+
+    def __init__(self, lib, handle, stats: MineStats | None):
+        self._lib, self._h = lib, handle
+        n = ctypes.c_uint64()
+        po, pi, ps = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        dev = ctypes.c_int()
+        _check(lib, lib.fim_result_view(handle, ctypes.byref(n), ctypes.byref(po), ctypes.byref(pi), ctypes.byref(ps),
+                                        ctypes.byref(dev)), "fim_result_view")
+        self.n_sets = n.value
+        self.on_device = bool(dev.value)
+        self.stats = stats.as_dict() if stats is not None else None
+        self.device_ptrs = (po.value, pi.value, ps.value) if self.on_device else None
+        if not self.on_device:
+            off = np.ctypeslib.as_array((ctypes.c_uint64 * (self.n_sets + 1)).from_address(po.value)).copy()
+            n_items = int(off[-1]) if self.n_sets else 0
+            if n_items:
+                items = np.ctypeslib.as_array((ctypes.c_uint32 * n_items).from_address(pi.value)).copy()
+            else:
+                items = np.zeros(0, dtype=np.uint32)
+            if self.n_sets:
+                supp = np.ctypeslib.as_array((ctypes.c_uint32 * self.n_sets).from_address(ps.value)).copy()
+            else:
+                supp = np.zeros(0, dtype=np.uint32)
+            self.set_offsets, self.set_items, self.supports = off, items, supp
+            self.free()
+
+    def free(self):
+        if self._h:
+            self._lib.fim_result_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def as_dict(self):
+        """{itemset tuple: support} (host results)."""
+        so, si, sp = self.set_offsets, self.set_items, self.supports
+        return {tuple(int(v) for v in si[so[k]:so[k + 1]]): int(sp[k]) for k in range(self.n_sets)}
+
+
+class Database:
+    """A built vertical database (fim_db)."""
+
+    def __init__(self, lib, handle):
+        self._lib, self._h = lib, handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        vals = [ctypes.c_uint32() for _ in range(5)]
+        nbytes = ctypes.c_uint64()
+        _check(self._lib, self._lib.fim_db_info(self._h, *[ctypes.byref(v) for v in vals], ctypes.byref(nbytes)),
+               "fim_db_info")
+        D, N, rows, words, wb = (v.value for v in vals)
+        return dict(D=D, N=N, n_rows=rows, words_per_row=words, word_bits=wb, device_bytes=nbytes.value)
+
+    def rows(self):
+        n = self.info()["n_rows"]
+        ri = np.zeros(max(n, 1), dtype=np.uint32)
+        sp = np.zeros(max(n, 1), dtype=np.uint32)
+        _check(self._lib, self._lib.fim_db_rows(self._h, ri.ctypes.data, sp.ctypes.data), "fim_db_rows")
+        return ri[:n], sp[:n]
+
+    def estimate_class_costs(self, sample_rate: float, rel_minsup: float, seed: int):
+        n = self.info()["n_rows"]
+        cost = np.zeros(max(n, 1), dtype=np.float64)
+        order = np.zeros(max(n, 1), dtype=np.uint32)
+        _check(self._lib, self._lib.fim_estimate_class_costs(self._h, sample_rate, rel_minsup, seed, cost.ctypes.data,
+                                                             order.ctypes.data), "fim_estimate_class_costs")
+        return cost[:n], order[:n]
+
+    def estimate_sample_size(self):
+        nfs, rows, ms = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(self._lib, self._lib.fim_estimate_sample_size(self._h, ctypes.byref(nfs), ctypes.byref(rows),
+                                                             ctypes.byref(ms)), "fim_estimate_sample_size")
+        return nfs.value, rows.value, ms.value
+
+    def mine(self, minsup: int, class_order: str = "estimate", threads_per_cta: int = 0, vec_per_lane: int = 0,
+             ctas_per_sm: int = 0, donate: bool = True, result_on_device: bool = False, collect_times: bool = False,
+             out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True):
+        opts = MineOpts()
+        self._lib.fim_mine_opts_init(ctypes.byref(opts))
+        opts.class_order = {"estimate": FIM_ORDER_ESTIMATE, "uniform": FIM_ORDER_UNIFORM}[class_order]
+        opts.threads_per_cta = threads_per_cta
+        opts.vec_per_lane = vec_per_lane
+        opts.ctas_per_sm = ctas_per_sm
+        opts.donate = 1 if donate else 0
+        opts.result_on_device = 1 if result_on_device else 0
+        opts.collect_times = 1 if collect_times else 0
+        opts.out_capacity_sets = out_capacity_sets
+        opts.out_capacity_items = out_capacity_items
+        opts.spin_limit = spin_limit
+        st = MineStats() if stats else None
+        if st is not None:
+            opts.stats = ctypes.pointer(st)
+        h = ctypes.c_void_p()
+        status = self._lib.fim_mine(self._h, minsup, ctypes.byref(opts), ctypes.byref(h))
+        if status == FIM_ERR_OUTPUT_OVERFLOW:
+            err = FimError(status, "fim_mine", self._lib.fim_last_error().decode(errors="replace"))
+            err.needed = (opts.out_needed_sets, opts.out_needed_items)
+            raise err
+        _check(self._lib, status, "fim_mine")
+        return Result(self._lib, h.value, st)
+
+    def free(self):
+        if self._h:
+            self._lib.fim_db_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_vertical_db(tx_offsets, tx_items, N: int, word_bits: int = 64, prefilter_minsup: int = 0, stream=None):
+    """fim_build_vertical_db: host CSR (numpy uint32) -> Database."""
+    lib = load()
+    off = np.ascontiguousarray(tx_offsets, dtype=np.uint32)
+    it = np.ascontiguousarray(tx_items, dtype=np.uint32)
+    if it.size == 0:
+        it = np.zeros(1, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    _check(lib, lib.fim_build_vertical_db(off.ctypes.data, it.ctypes.data, off.size - 1, N, word_bits,
+                                          prefilter_minsup, _stream_handle(stream), ctypes.byref(h)),
+           "fim_build_vertical_db")
+    return Database(lib, h.value)
+
+
+def build_vertical_db_device(d_tx_offsets, d_tx_items, D: int, N: int, word_bits: int = 64,
+                             prefilter_minsup: int = 0, stream=None):
+    """fim_build_vertical_db_device: CSR already in device memory (torch tensors or raw pointers)."""
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib, lib.fim_build_vertical_db_device(_ptr(d_tx_offsets), _ptr(d_tx_items), D, N, word_bits,
+                                                 prefilter_minsup, _stream_handle(stream), ctypes.byref(h)),
+           "fim_build_vertical_db_device")
+    return Database(lib, h.value)
+
+
+def status_str(status: int) -> str:
+    return load().fim_status_str(status).decode()

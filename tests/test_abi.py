@@ -1,0 +1,69 @@
+"""The C ABI library builds for sm_103a, loads without a GPU, and exports every
+function that include/fim.h declares.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2108_05038_gb300 import _build, fim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "fim.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fim_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_parsed():
+    names = header_functions()
+    assert "fim_mine" in names and "fim_build_vertical_db" in names and "fim_estimate_class_costs" in names
+
+
+def test_library_builds_and_exports_header_symbols():
+    path = _build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    for name in header_functions():
+        assert hasattr(lib, name), f"{name} declared in include/fim.h but not exported"
+    assert sorted(fim.EXPORTED) == header_functions()
+
+
+def test_status_strings_without_gpu():
+    lib = fim.load()
+    assert lib.fim_status_str(0) == b"FIM_OK"
+    assert lib.fim_status_str(3) == b"FIM_ERR_OUTPUT_OVERFLOW"
+    assert lib.fim_last_error() == b""
+
+
+def test_opts_struct_layout_matches_header():
+    lib = fim.load()
+    o = fim.MineOpts()
+    lib.fim_mine_opts_init(ctypes.byref(o))
+    assert o.struct_size == ctypes.sizeof(fim.MineOpts)
+    assert o.donate == 1 and o.class_order == fim.FIM_ORDER_ESTIMATE
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    lib = fim.load()
+    h = ctypes.c_void_p()
+    # NULL offsets, D == 0 and bad word size are rejected before any device call
+    assert lib.fim_build_vertical_db(None, None, 0, 10, 64, 0, None, ctypes.byref(h)) == fim.FIM_ERR_INVALID
+    assert b"D == 0" in lib.fim_last_error()
+    off = (ctypes.c_uint32 * 2)(0, 0)
+    assert lib.fim_build_vertical_db(off, None, 1, 10, 16, 0, None, ctypes.byref(h)) == fim.FIM_ERR_INVALID
+    assert lib.fim_mine(None, 5, None, ctypes.byref(h)) == fim.FIM_ERR_INVALID
+    assert lib.fim_estimate_class_costs(None, 0.01, 0.1, 1, None, None) == fim.FIM_ERR_INVALID
+
+
+def test_no_oracle_import_in_product_path():
+    """The GPU package never imports the oracle (parity would be void otherwise)."""
+    pkg = os.path.join(ROOT, "paper_2108_05038_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".c", ".h")):
+                text = open(os.path.join(dirpath, f), errors="replace").read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "fim_oracle" not in text, f

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Counts are integers, so the bar is bit-exact: the same set of itemsets and the
+same supports.  The output order of the GPU is unspecified; sets are compared
+as canonical dictionaries (items ascending inside a set).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_05038_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2108_05038_gb300 import fim  # noqa: E402
+
+
+def csr(txs):
+    off = np.zeros(len(txs) + 1, dtype=np.uint32)
+    items = []
+    for i, t in enumerate(txs):
+        items.extend(sorted(set(int(v) for v in t)))
+        off[i + 1] = len(items)
+    return off, np.array(items, dtype=np.uint32)
+
+
+def odict(res):
+    so, si, sp = res
+    return {tuple(int(v) for v in si[so[k]:so[k + 1]]): int(sp[k]) for k in range(len(sp))}
+
+
+def gpu_mine(off, items, N, minsup, word_bits=64, prefilter=0, **kw):
+    db = fim.build_vertical_db(off, items, N, word_bits=word_bits, prefilter_minsup=prefilter)
+    try:
+        return db.mine(minsup, **kw)
+    finally:
+        db.free()
+
+
+def assert_same(got: dict, want: dict):
+    if got != want:
+        missing = [k for k in want if k not in got][:5]
+        extra = [k for k in got if k not in want][:5]
+        wrong = [(k, got[k], want[k]) for k in want if k in got and got[k] != want[k]][:5]
+        raise AssertionError(f"{len(got)} vs {len(want)} itemsets; missing {missing} extra {extra} wrong {wrong}")
+
+
+# ---------------------------------------------------------------- golden and tiny cases
+
+def test_eclat_worked_example_on_gpu(golden):
+    minsup, txs, rows = golden("eclat_example.txt")
+    off, items = csr(txs)
+    for wb in (32, 64):
+        got = gpu_mine(off, items, 6, minsup, word_bits=wb).as_dict()
+        assert_same(got, {s: v for f, s, v in rows if f == "F"})
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_tiny_vs_bruteforce(seed):
+    rng = np.random.default_rng(1000 + seed)
+    N = int(rng.integers(2, 15))
+    D = int(rng.integers(1, 700))
+    dens = rng.uniform(0.05, 0.8)
+    txs = [list(np.nonzero(rng.random(N) < dens)[0]) for _ in range(D)]
+    off, items = csr(txs)
+    for minsup in sorted({1, 2, max(1, D // 7), max(1, D // 2)}):
+        want = odict(oracle.bruteforce(off, items, N, minsup))
+        got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64).as_dict()
+        assert_same(got, want)
+
+
+@pytest.mark.parametrize("D", [1, 31, 32, 33, 63, 64, 65, 1000, 4096 + 37])
+def test_ragged_D(D):
+    """D not a multiple of the word / row padding: tail bits stay zero."""
+    rng = np.random.default_rng(D)
+    txs = [list(np.nonzero(rng.random(12) < 0.6)[0]) for _ in range(D)]
+    off, items = csr(txs)
+    minsup = max(1, D // 5)
+    assert_same(gpu_mine(off, items, 12, minsup).as_dict(), odict(oracle.eclat(off, items, 12, minsup)))
+
+
+def test_identical_transactions_closed_form():
+    k, D = 11, 300
+    off, items = csr([list(range(k))] * D)
+    got = gpu_mine(off, items, k, D).as_dict()
+    assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
+
+
+def test_degenerate_cases():
+    off, items = csr([[0], [1], [2], [0, 1]])
+    assert gpu_mine(off, items, 3, 5).n_sets == 0             # minsup > D: empty
+    assert gpu_mine(off, items, 3, 2).as_dict() == {(0,): 2, (1,): 2}  # {0,1} has support 1
+    off, items = csr([[], [], [4]])
+    assert gpu_mine(off, items, 5, 1).as_dict() == {(4,): 1}  # empty transactions count toward D
+    off, items = csr([[1, 2]] * 3)
+    assert gpu_mine(off, items, 3, 3).as_dict() == {(1,): 3, (2,): 3, (1, 2): 3}  # n1 = 2: no DFS launch
+
+
+def test_duplicate_items_count_once():
+    off = np.array([0, 4, 6], dtype=np.uint32)
+    items = np.array([1, 1, 2, 2, 1, 1], dtype=np.uint32)
+    assert gpu_mine(off, items, 3, 1).as_dict() == {(1,): 2, (2,): 1, (1, 2): 1}
+
+
+def test_invalid_inputs():
+    off, items = csr([[1, 7]])
+    with pytest.raises(fim.FimError) as e:
+        fim.build_vertical_db(off, items, 5)
+    assert e.value.status == fim.FIM_ERR_INVALID
+    off, items = csr([[1, 2]])
+    db = fim.build_vertical_db(off, items, 3)
+    with pytest.raises(fim.FimError) as e:
+        db.mine(0)
+    assert e.value.status == fim.FIM_ERR_INVALID
+    with pytest.raises(fim.FimError):
+        db.estimate_class_costs(0.0, 0.1, 1)
+    db.free()
+
+
+# ---------------------------------------------------------------- named workloads
+
+@pytest.mark.parametrize("name", ["tiny", "dense_deep", "dense_exact37"])
+def test_workload_full_size_exact(name):
+    w = synth.make_workload(name)
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
+    got = gpu_mine(w["offsets"], w["items"], w["N"], w["minsup"], word_bits=w["word_bits"]).as_dict()
+    assert_same(got, want)
+
+
+def test_sparse_mid_full_size_exact():
+    w = synth.make_workload("sparse_mid")
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
+    res = gpu_mine(w["offsets"], w["items"], w["N"], w["minsup"], word_bits=64)
+    assert_same(res.as_dict(), want)
+    st = res.stats
+    assert st["n_frequent"] == len(want)
+    assert st["n_pair_intersections"] == st["n_frequent_items"] * (st["n_frequent_items"] - 1) // 2
+
+
+@pytest.mark.parametrize("threads,vec,donate,order", [(128, 1, True, "uniform"), (256, 2, False, "uniform"),
+                                                        (512, 8, True, "estimate"), (512, 4, False, "estimate")])
+def test_launch_shapes_and_orders_identical(threads, vec, donate, order):
+    """Item order, class order, CTA shape and donation never change the output (Sec. 8.2)."""
+    w = synth.make_workload("dense_deep", D=20000)
+    ms = 12000
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    if order == "estimate":
+        db.estimate_class_costs(0.02, 0.6, 5)
+    got = db.mine(ms, class_order=order, threads_per_cta=threads, vec_per_lane=vec, donate=donate).as_dict()
+    db.free()
+    assert_same(got, want)
+
+
+def test_prefilter_and_device_input():
+    w = synth.make_workload("tiny", D=6000)
+    ms = 90
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    assert_same(gpu_mine(w["offsets"], w["items"], w["N"], ms, prefilter=50).as_dict(), want)
+    d_off = torch.from_numpy(w["offsets"].astype(np.int32)).cuda()
+    d_it = torch.from_numpy(w["items"].astype(np.int32)).cuda()
+    torch.cuda.synchronize()
+    db = fim.build_vertical_db_device(d_off, d_it, 6000, w["N"], 32, 0)
+    got = db.mine(ms).as_dict()
+    db.free()
+    assert_same(got, want)
+
+
+def test_fixed_capacity_overflow_then_retry():
+    w = synth.make_workload("tiny", D=5000)
+    ms = 50
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    with pytest.raises(fim.FimError) as e:
+        db.mine(ms, out_capacity_sets=100, out_capacity_items=150)
+    assert e.value.status == fim.FIM_ERR_OUTPUT_OVERFLOW
+    need_sets, need_items = e.value.needed
+    assert need_sets == len(want) and need_items == sum(len(k) for k in want)
+    got = db.mine(ms, out_capacity_sets=need_sets, out_capacity_items=need_items).as_dict()
+    db.free()
+    assert_same(got, want)
+
+
+def test_repeated_mines_reuse_workspace():
+    w = synth.make_workload("tiny", D=8000)
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    for ms in (400, 80, 200, 80):
+        assert_same(db.mine(ms).as_dict(), odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms)))
+    db.free()
+
+
+# ---------------------------------------------------------------- class-cost estimate
+
+@pytest.mark.parametrize("name,D,rate,rel,seed", [("tiny", 10000, 0.05, 0.01, 3), ("dense_deep", 20000, 0.01, 0.6, 9),
+                                                   ("sparse_mid", 50000, 0.02, 0.005, 1)])
+def test_estimate_matches_oracle(name, D, rate, rel, seed):
+    w = synth.make_workload(name, D=D)
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    cost, order = db.estimate_class_costs(rate, rel, seed)
+    nfs, m, ms = db.estimate_sample_size()
+    db.free()
+    ocost, oorder, onfs = oracle.class_costs(w["offsets"], w["items"], w["N"], 0, rate, rel, seed)
+    assert m == math.ceil(rate * D) and nfs == onfs
+    assert np.array_equal(cost, ocost)
+    assert np.array_equal(order, oorder)
+
+
+def test_row_order_matches_oracle():
+    w = synth.make_workload("sparse_mid", D=20000)
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], prefilter_minsup=3)
+    ri, sp = db.rows()
+    db.free()
+    assert np.array_equal(ri, oracle.item_order(w["offsets"], w["items"], w["N"], 3))
+    assert np.all(np.diff(sp.astype(np.int64)) >= 0)
+
+
+# ---------------------------------------------------------------- full-size large sparse (sampled certificate)
+
+@pytest.mark.slow
+def test_large_sparse_certificate():
+    """1M transactions x 10k items: the oracle's certificate on every 97th output set."""
+    w = synth.make_workload("large_sparse")
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=64)
+    db.estimate_class_costs(0.01, w["rel_minsup"], 3)
+    res = db.mine(w["minsup"])
+    db.free()
+    code, bad = oracle.check(w["offsets"], w["items"], w["N"], w["minsup"], res.set_offsets, res.set_items,
+                             res.supports, stride=97)
+    assert code == 0, (oracle.CHECK_CODES[code], bad)
