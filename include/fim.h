@@ -180,6 +180,37 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
 fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,
                            const uint32_t** set_items, const uint32_t** supports, int* on_device);
 
+/*
+ * Frequent pairs without allocation.  The thesis has no counterpart to this
+ * entry point; it exists for callers that cannot allocate device memory while
+ * they run: a process whose device memory is reserved up front by another
+ * allocator (for example a framework's caching pool), or a latency-bound
+ * serving loop that must not call cudaMalloc/cudaFree, which may synchronise
+ * the whole device.  Every other entry point allocates its scratch on demand.
+ *
+ * Writes every frequent 2-itemset {a < b} of db (supp >= minsup_abs) to
+ * d_pairs[2k], d_pairs[2k+1] (original ids, ascending) and d_supports[k], both
+ * DEVICE buffers owned by the caller with room for `capacity` pairs; the
+ * order of the pairs is unspecified.  *n_pairs (host) receives the number of
+ * frequent pairs, also when it exceeds capacity (then FIM_ERR_OUTPUT_OVERFLOW
+ * and only `capacity` of them are written).  The call synchronises db's stream.
+ *
+ * Scratch: one fixed array inside the library (4 MiB plus a little), held by
+ * every GPU that loads the library until the process exits.  At most 1024
+ * items may be frequent at minsup_abs; more are rejected with
+ * FIM_ERR_INVALID before any device work.  The first call on a device looks up
+ * the array's device address (set-up); make that first call before any
+ * stream capture.  All calls share the one array, so calls whose device work
+ * overlaps (other threads, other streams) race and must be serialised by the
+ * caller.  No call allocates memory: no cudaMalloc, cudaFree or allocating
+ * library routine.
+ * Errors: FIM_ERR_INVALID (NULL db or n_pairs, NULL buffers with capacity > 0,
+ * minsup 0 or below the prefilter, more than 1024 frequent items),
+ * FIM_ERR_OUTPUT_OVERFLOW, FIM_ERR_CUDA.
+ */
+fim_status fim_mine_pairs_noalloc(const fim_db* db, uint32_t minsup_abs, uint32_t* d_pairs, uint32_t* d_supports,
+                                  uint64_t capacity, uint64_t* n_pairs);
+
 void fim_result_free(fim_result* res);
 void fim_db_free(fim_db* db);
 const char* fim_status_str(fim_status s);

@@ -22,7 +22,7 @@ FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
 EXPORTED = [
     "fim_mine_opts_init", "fim_build_vertical_db", "fim_build_vertical_db_device", "fim_db_info", "fim_db_rows",
     "fim_estimate_class_costs", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
-    "fim_db_free", "fim_status_str", "fim_last_error",
+    "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc",
 ]
 
 
@@ -100,6 +100,8 @@ def load(build_if_stale: bool = True):
         lib.fim_estimate_sample_size.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.fim_mine.restype = i32
         lib.fim_mine.argtypes = [P, u32, ctypes.POINTER(MineOpts), PP]
+        lib.fim_mine_pairs_noalloc.restype = i32
+        lib.fim_mine_pairs_noalloc.argtypes = [P, u32, P, P, u64, ctypes.POINTER(u64)]
         lib.fim_result_view.restype = i32
         lib.fim_result_view.argtypes = [P, ctypes.POINTER(u64), PP, PP, PP, ctypes.POINTER(i32)]
         lib.fim_result_free.restype = None
@@ -250,6 +252,18 @@ class Database:
             raise err
         _check(self._lib, status, "fim_mine")
         return Result(self._lib, h.value, st)
+
+    def mine_pairs_noalloc(self, minsup: int, d_pairs, d_supports, capacity: int) -> int:
+        """fim_mine_pairs_noalloc into caller-owned device buffers; returns the number of frequent pairs."""
+        n = ctypes.c_uint64()
+        status = self._lib.fim_mine_pairs_noalloc(self._h, minsup, _ptr(d_pairs), _ptr(d_supports), capacity,
+                                                  ctypes.byref(n))
+        if status == FIM_ERR_OUTPUT_OVERFLOW:
+            err = FimError(status, "fim_mine_pairs_noalloc", self._lib.fim_last_error().decode(errors="replace"))
+            err.needed = n.value
+            raise err
+        _check(self._lib, status, "fim_mine_pairs_noalloc")
+        return n.value
 
     def free(self):
         if self._h:
