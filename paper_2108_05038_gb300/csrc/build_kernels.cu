@@ -117,6 +117,10 @@ __global__ void k_tally_min_rank(const uint64_t* __restrict__ set_off, const uin
   }
 }
 
+__global__ void k_iota(uint32_t* out, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
+}
+
 uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t cap = 152 * 32) {
   uint64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -147,6 +151,12 @@ cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint
                                 uint64_t seed, uint32_t m, uint32_t* sbits, uint32_t sstride, cudaStream_t st) {
   const uint32_t threads = 256;
   k_sample_build<<<grid_for(m, threads), threads, 0, st>>>(off, items, D, item_rank, seed, m, sbits, sstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_iota<<<grid_for(n, 256), 256, 0, st>>>(out, n);
   return cudaGetLastError();
 }
 

@@ -25,8 +25,6 @@ namespace fim {
 namespace {
 
 constexpr uint32_t kCandBatch = 1024;  // candidates counted per pass (shared-memory counters)
-constexpr uint32_t kSlotHeader = 4;    // pool slot: state, xlen, ncand, spare
-enum : uint32_t { SLOT_FREE = 0, SLOT_BUSY = 1, SLOT_READY = 2 };
 
 // Exclusive block-wide scan of a 0/1 flag.  wtot: 33 shared words.  Returns
 // this thread's position among the set flags; *total = number of set flags.
@@ -183,17 +181,17 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
 // K4: persistent DFS
 
 struct Ctl {
-  uint32_t kind;      // 0 exit, 1 static entry, 2 pool slot
-  uint32_t a, b;      // entry (row, m) or slot index
-  uint32_t action;    // 0 pop, 1 child, 2 donate
-  uint32_t s;         // child item
-  uint32_t nc;        // child candidates
-  uint32_t cand_off;  // offset of the child's candidates in the frame list
-  uint32_t fd;        // frame to donate from
+  uint32_t kind;      // 0 exit, 1 static entry, 2 donated class from the ring
+  uint32_t a, b;      // static entry (row index, m)
+  uint32_t action;    // 1 expand child, 2 donate child, 3 frame exhausted, 4 class done
+  uint32_t s_row, s_id;
+  uint32_t nc;        // candidates of the child
+  uint32_t cand_off;  // their offset (entries) in the frame's list
+  uint32_t fd;        // frame the donated child comes from
   int32_t depth;
-  uint32_t xlen0;     // prefix length of the entry's root node
-  uint32_t nsurv;
-  uint32_t slot;
+  uint32_t xlen0;     // prefix length of the class's root node
+  uint32_t slot;      // ring slot in use
+  uint32_t rpos;      // ring position of that slot
   unsigned long long base;
 };
 
@@ -201,8 +199,11 @@ struct DfsArgs {
   DfsLaunch p;
   uint32_t stride4;
   uint32_t nseg;       // pieces per candidate row
-  uint32_t max_len;    // itemset length bound (entries of xs)
+  uint32_t max_len;    // itemset length bound (entries of the path arrays)
 };
+
+// candidate list encodings
+enum : uint32_t { CAND_FROW = 0, CAND_PAIR = 1, CAND_PAIR_RING = 2 };
 
 template <int VEC>
 __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, const uint4* pre, uint32_t base4,
@@ -220,20 +221,25 @@ __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, co
   return s;
 }
 
+__device__ __forceinline__ uint32_t cand_row(const DfsLaunch& p, const uint32_t* cand, uint32_t mode, uint32_t k) {
+  if (mode == CAND_FROW) return p.frows[cand[k]];
+  if (mode == CAND_PAIR) return cand[2 * k];
+  return __ldcg(cand + 2 * k);
+}
+
 // Counts the candidates of one class node against its prefix bitmap, writes
-// the survivors (frow indices, candidate order) to out_list and one output
-// record per survivor.  All threads of the CTA call it; returns the survivor
-// count (same value in every thread).
+// the survivors as (row, id) pairs in candidate order to out_list, and one
+// output record per survivor.  All threads of the CTA call it; returns the
+// survivor count (same value in every thread).
 template <int VEC>
-__device__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32_t* wtot, const uint32_t* xid,
-                                 const uint32_t* pre, bool pre_global, const uint32_t* cand, bool cand_global,
-                                 uint32_t nc, uint32_t* out_list, uint32_t out_cap, uint32_t xlen,
-                                 unsigned long long& stat_inter) {
+__device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32_t* wtot,
+                                                 const uint32_t* xid, const uint32_t* pre, bool pre_global,
+                                                 const uint32_t* cand, uint32_t mode, uint32_t nc, uint32_t* out_list,
+                                                 uint32_t out_cap, uint32_t xlen) {
   const DfsLaunch& p = A.p;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
   uint32_t nsurv = 0;
-  if (threadIdx.x == 0) stat_inter += nc;
   for (uint32_t b0 = 0; b0 < nc; b0 += kCandBatch) {
     const uint32_t nb = min(kCandBatch, nc - b0);
     for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) cnt[k] = 0;
@@ -241,9 +247,9 @@ __device__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32
     const uint32_t total = nb * A.nseg;
     for (uint32_t pc = warp; pc < total; pc += nw) {
       const uint32_t k = pc / A.nseg, g = pc - k * A.nseg;
-      const uint32_t idx = cand_global ? __ldcg(cand + b0 + k) : cand[b0 + k];
-      const uint4* row = reinterpret_cast<const uint4*>(p.bits + (size_t)p.frows[idx] * p.stride);
-      uint32_t s = piece_popc<VEC>(row, pre4, g * 32 * VEC + lane, A.stride4, pre_global);
+      const uint32_t row = cand_row(p, cand, mode, b0 + k);
+      const uint4* rp = reinterpret_cast<const uint4*>(p.bits + (size_t)row * p.stride);
+      uint32_t s = piece_popc<VEC>(rp, pre4, g * 32 * VEC + lane, A.stride4, pre_global);
       s = __reduce_add_sync(0xffffffffu, s);
       if (lane == 0 && s) atomicAdd(&cnt[k], s);
     }
@@ -256,21 +262,26 @@ __device__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32
       const uint32_t pos = block_flag_scan(f, wtot, &tot);
       if (threadIdx.x == 0 && tot) {
         const unsigned long long sets = tot, items = (unsigned long long)tot * (xlen + 1);
-        C.base = atomicAdd((unsigned long long*)&p.ctrl->packed, (sets << 32) | items);
-        atomicAdd((unsigned long long*)&p.ctrl->sets_total, sets);
-        atomicAdd((unsigned long long*)&p.ctrl->items_total, items);
+        C.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+        atomicAdd(&p.ctrl->sets_total, sets);
+        atomicAdd(&p.ctrl->items_total, items);
         atomicMax(&p.ctrl->max_len, xlen + 1);
       }
       __syncthreads();
       if (f) {
-        const uint32_t idx = cand_global ? __ldcg(cand + b0 + k) : cand[b0 + k];
+        const uint32_t row = cand_row(p, cand, mode, b0 + k);
+        const uint32_t v = mode == CAND_FROW ? p.rank_item[row]
+                                             : (mode == CAND_PAIR ? cand[2 * (b0 + k) + 1] : __ldcg(cand + 2 * (b0 + k) + 1));
         const uint32_t o = nsurv + pos;
-        if (o < out_cap) out_list[o] = idx;
-        else atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+        if (o < out_cap) {
+          out_list[2 * o] = row;
+          out_list[2 * o + 1] = v;
+        } else {
+          atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+        }
         const uint64_t rec = (C.base >> 32) + pos;
         const uint64_t it0 = (C.base & 0xffffffffull) + (uint64_t)pos * (xlen + 1);
         if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
-          const uint32_t v = p.rank_item[p.frows[idx]];
           uint32_t* dst = p.out_items + it0;
           uint32_t q = 0;
           bool placed = false;
@@ -293,52 +304,101 @@ __device__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32
   return nsurv;
 }
 
-// sorted original ids of xs[0..len) into xid (ids are distinct)
-__device__ __forceinline__ void build_xid(const DfsLaunch& p, const uint32_t* xs, uint32_t len, uint32_t* xid) {
+// xid = the ids of the current path xidp[0..len) in ascending order (ids are distinct)
+__device__ __forceinline__ void sort_path_ids(const uint32_t* xidp, uint32_t len, uint32_t* xid) {
   for (uint32_t k = threadIdx.x; k < len; k += blockDim.x) {
-    const uint32_t v = p.rank_item[p.frows[xs[k]]];
+    const uint32_t v = xidp[k];
     uint32_t r = 0;
-    for (uint32_t q = 0; q < len; ++q) r += p.rank_item[p.frows[xs[q]]] < v;
+    for (uint32_t q = 0; q < len; ++q) r += xidp[q] < v;
     xid[r] = v;
   }
 }
 
+// Bounded MPMC ring over the pool slots (after D. Vyukov's bounded queue):
+// slot c carries a sequence word; a producer may fill slot (pos % cap) when
+// seq == pos and publishes it with seq = pos + 1; a consumer may take it when
+// seq == pos + 1 and frees it with seq = pos + cap.  Single thread callers.
+__device__ bool ring_claim_for_fill(const DfsLaunch& p, uint32_t* slot, uint32_t* rpos) {
+  uint32_t pos = *(volatile uint32_t*)&p.ctrl->ring_tail;
+  for (int tries = 0; tries < 64; ++tries) {
+    const uint32_t c = pos % p.pool_slots;
+    const uint32_t seq = *(volatile uint32_t*)(p.pool + (size_t)c * p.pool_slot_words);
+    const int32_t diff = (int32_t)(seq - pos);
+    if (diff == 0) {
+      const uint32_t old = atomicCAS(&p.ctrl->ring_tail, pos, pos + 1);
+      if (old == pos) { *slot = c; *rpos = pos; return true; }
+      pos = old;
+    } else if (diff < 0) {
+      return false;  // full
+    } else {
+      pos = *(volatile uint32_t*)&p.ctrl->ring_tail;
+    }
+  }
+  return false;
+}
+
+__device__ bool ring_take(const DfsLaunch& p, uint32_t* slot, uint32_t* rpos) {
+  uint32_t pos = *(volatile uint32_t*)&p.ctrl->ring_head;
+  for (int tries = 0; tries < 64; ++tries) {
+    const uint32_t c = pos % p.pool_slots;
+    const uint32_t seq = *(volatile uint32_t*)(p.pool + (size_t)c * p.pool_slot_words);
+    const int32_t diff = (int32_t)(seq - (pos + 1));
+    if (diff == 0) {
+      const uint32_t old = atomicCAS(&p.ctrl->ring_head, pos, pos + 1);
+      if (old == pos) { __threadfence(); *slot = c; *rpos = pos; return true; }
+      pos = old;
+    } else if (diff < 0) {
+      return false;  // empty
+    } else {
+      pos = *(volatile uint32_t*)&p.ctrl->ring_head;
+    }
+  }
+  return false;
+}
+
+__global__ void k_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < slots; c += gridDim.x * blockDim.x)
+    pool[(size_t)c * slot_words] = c;
+}
+
 template <int VEC, bool PSMEM>
-__global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
+__global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
   const DfsLaunch& p = A.p;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ Ctl C;
   __shared__ uint32_t wtot[33];
-  // dynamic shared memory: [prefix stride words (PSMEM)] [cnt kCandBatch] [f_n maxd+1] [f_cur maxd+1] [xs L+1] [xid L+1]
+  // dynamic shared memory: [prefix (PSMEM)] [cnt] [f_n] [f_cur] [xrow] [xidp] [xid]
   uint32_t* sp = smem;
   uint32_t* spre = PSMEM ? sp : nullptr;
   if (PSMEM) sp += p.stride;
   uint32_t* cnt = sp; sp += kCandBatch;
   uint32_t* f_n = sp; sp += p.maxd + 1;
   uint32_t* f_cur = sp; sp += p.maxd + 1;
-  uint32_t* xs = sp; sp += A.max_len + 1;
+  uint32_t* xrow = sp; sp += A.max_len + 1;
+  uint32_t* xidp = sp; sp += A.max_len + 1;
   uint32_t* xid = sp;
 
-  const uint32_t per_depth = p.stride + ((p.n1 + 3u) & ~3u);
-  uint32_t* arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
+  const uint64_t per_depth = dfs_arena_depth_words(p.stride, p.n1);
+  uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
 #define slot_pre(d) (arena + (size_t)(d) * per_depth)
 #define slot_list(d) (arena + (size_t)(d) * per_depth + p.stride)
   const uint32_t list_cap = p.n1;
   const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
+  const uint32_t L = A.max_len;
+  const uint64_t sw = p.pool_slot_words;
 
   unsigned long long st_inter = 0, st_frames = 0, st_don = 0;
   bool static_done = false;
-  uint32_t rot = blockIdx.x;
-  unsigned int last_progress = 0;
+  uint32_t idle_hint = 0, ready_hint = 0;  // last seen pool state (thread 0)
 
   for (;;) {
     // ---------------- acquire a class ----------------
     if (threadIdx.x == 0) {
       C.kind = 0;
       if (!static_done) {
-        uint32_t e = atomicAdd(&p.ctrl->queue_head, 1u);
+        const uint32_t e = atomicAdd(&p.ctrl->queue_head, 1u);
         if (e < p.ctrl->n_entries) {
-          uint2 en = p.entries[e];
+          const uint2 en = p.entries[e];
           C.kind = 1; C.a = en.x; C.b = en.y;
         } else {
           static_done = true;
@@ -347,28 +407,22 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
       if (C.kind == 0 && p.donate) {
         bool idle = false;
         unsigned long long spins = 0;
-        uint32_t backoff = 64;
+        uint32_t backoff = 32;
+        uint32_t last = *(volatile uint32_t*)&p.ctrl->progress;
         for (;;) {
-          if (*(volatile uint32_t*)&p.ctrl->n_ready > 0) {
-            for (uint32_t t = 0; t < p.pool_slots; ++t) {
-              uint32_t g = (rot + t) % p.pool_slots;
-              uint32_t* st = p.pool + (size_t)g * p.pool_slot_words;
-              if (*(volatile uint32_t*)st == SLOT_READY && atomicCAS(st, SLOT_READY, SLOT_BUSY) == SLOT_READY) {
-                __threadfence();
-                atomicSub(&p.ctrl->n_ready, 1u);
-                C.kind = 2; C.slot = g; rot = g + 1;
-                break;
-              }
-            }
-            if (C.kind == 2) break;
+          uint32_t slot, rpos;
+          if (ring_take(p, &slot, &rpos)) {
+            atomicSub(&p.ctrl->n_ready, 1u);
+            C.kind = 2; C.slot = slot; C.rpos = rpos;
+            break;
           }
           if (*(volatile uint32_t*)&p.ctrl->pending == 0) break;
           if (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_TIMEOUT) break;
           if (!idle) { atomicAdd(&p.ctrl->n_idle, 1u); idle = true; }
           __nanosleep(backoff);
-          if (backoff < 2048) backoff <<= 1;
-          unsigned int prog = *(volatile unsigned int*)&p.ctrl->n_nodes;
-          if (prog != last_progress) { last_progress = prog; spins = 0; }
+          if (backoff < 1024) backoff <<= 1;
+          const uint32_t prog = *(volatile uint32_t*)&p.ctrl->progress;
+          if (prog != last) { last = prog; spins = 0; }
           if (++spins > p.spin_limit) { atomicOr(&p.ctrl->err, DEV_ERR_TIMEOUT); break; }
         }
         if (idle) atomicSub(&p.ctrl->n_idle, 1u);
@@ -379,116 +433,111 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
 
     // ---------------- root node of the class ----------------
     const uint32_t* cand;
-    uint32_t nc;
-    bool cand_global;
+    uint32_t nc, mode;
     const uint32_t* pre;
-    bool pre_global;
+    bool pre_global = false;
     uint32_t* slotp = nullptr;
     if (C.kind == 1) {
       const uint32_t i = C.a, m = C.b;
-      const uint32_t s = p.sitems[p.soff[i] + m];
-      cand = p.sitems + p.soff[i] + m + 1;
+      const uint32_t base = p.soff[i];
+      const uint32_t si = p.sitems[base + m];
+      const uint32_t r1 = p.frows[i], r2 = p.frows[si];
+      cand = p.sitems + base + m + 1;
       nc = p.scnt[i] - m - 1;
-      cand_global = false;
-      if (threadIdx.x == 0) { xs[0] = i; xs[1] = s; C.xlen0 = 2; }
-      const uint4* r1 = bits4 + (size_t)p.frows[i] * A.stride4;
-      const uint4* r2 = bits4 + (size_t)p.frows[s] * A.stride4;
+      mode = CAND_FROW;
+      if (threadIdx.x == 0) { xrow[0] = r1; xidp[0] = p.rank_item[r1]; C.xlen0 = 2; }
+      if (threadIdx.x == 1) { xrow[1] = r2; xidp[1] = p.rank_item[r2]; }
+      const uint4* a4 = bits4 + (size_t)r1 * A.stride4;
+      const uint4* b4 = bits4 + (size_t)r2 * A.stride4;
       uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(0));
       for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-        uint4 a = __ldg(r1 + w), b = __ldg(r2 + w);
+        const uint4 a = __ldg(a4 + w), b = __ldg(b4 + w);
         dst[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
       }
       pre = PSMEM ? spre : slot_pre(0);
-      pre_global = false;
     } else {
-      slotp = p.pool + (size_t)C.slot * p.pool_slot_words;
+      slotp = p.pool + (size_t)C.slot * sw;
       const uint32_t xl = __ldcg(slotp + 1);
       nc = __ldcg(slotp + 2);
-      for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) xs[k] = __ldcg(slotp + kSlotHeader + k);
+      for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) {
+        xrow[k] = __ldcg(slotp + kDfsSlotHeader + k);
+        xidp[k] = __ldcg(slotp + kDfsSlotHeader + L + k);
+      }
       if (threadIdx.x == 0) C.xlen0 = xl;
-      cand = slotp + kSlotHeader + A.max_len;
-      cand_global = true;
-      const uint32_t* spref = slotp + (p.pool_slot_words - p.stride);
+      cand = slotp + kDfsSlotHeader + 2 * L;
+      mode = CAND_PAIR_RING;
+      const uint32_t* spref = slotp + (sw - p.stride);
       if (PSMEM) {
         const uint4* s4 = reinterpret_cast<const uint4*>(spref);
         uint4* d4 = reinterpret_cast<uint4*>(spre);
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = __ldcg(s4 + w);
         pre = spre;
-        pre_global = false;
       } else {
         pre = spref;
         pre_global = true;
       }
     }
     __syncthreads();
-    build_xid(p, xs, C.xlen0, xid);
-    __syncthreads();
     const uint32_t xlen0 = C.xlen0;
-    uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, pre, pre_global, cand, cand_global, nc, slot_list(0),
-                                    list_cap, xlen0, st_inter);
-    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&p.ctrl->n_nodes, 1ull);
+    sort_path_ids(xidp, xlen0, xid);
+    __syncthreads();
+    if (threadIdx.x == 0) st_inter += nc;
+    const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, pre, pre_global, cand, mode, nc, slot_list(0),
+                                          list_cap, xlen0);
     if (ns >= 2) {
-      // materialise the root prefix into the stack (it is in shared memory or the pool)
+      // the root prefix goes to depth slot 0 (it is in shared memory or in the ring slot)
       if (PSMEM || C.kind == 2) {
         const uint4* s4 = reinterpret_cast<const uint4*>(pre);
         uint4* d4 = reinterpret_cast<uint4*>(slot_pre(0));
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = pre_global ? __ldcg(s4 + w) : s4[w];
       }
-      if (threadIdx.x == 0) { f_n[0] = ns; f_cur[0] = 0; C.depth = 0; ++st_frames; }
-    } else if (threadIdx.x == 0) {
-      C.depth = -1;
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(&p.ctrl->n_nodes, 1ull);
+      atomicAdd(&p.ctrl->progress, 1u);
+      if (ns >= 2) { f_n[0] = ns; f_cur[0] = 0; C.depth = 0; ++st_frames; }
+      else C.depth = -1;
     }
     __syncthreads();
     if (C.kind == 2 && threadIdx.x == 0) {
       __threadfence();
-      atomicExch(slotp, SLOT_FREE);
+      atomicExch(slotp, C.rpos + p.pool_slots);  // free the ring slot
     }
 
     // ---------------- depth-first expansion ----------------
-    uint32_t donate_cool = 0;
+    uint32_t cool = 0;
     for (;;) {
       __syncthreads();  // every thread has read the previous decision
       if (threadIdx.x == 0) {
         const int32_t d = C.depth;
         C.action = 0;
         if (d < 0) {
-          C.action = 4;  // class done
+          C.action = 4;
         } else {
-          bool want = false;
-          if (p.donate && donate_cool == 0) {
-            const uint32_t idle = *(volatile uint32_t*)&p.ctrl->n_idle;
-            const uint32_t ready = *(volatile uint32_t*)&p.ctrl->n_ready;
-            want = idle > ready;
-          }
-          if (donate_cool) --donate_cool;
-          if (want) {
-            for (int32_t fd = 0; fd <= d; ++fd)
-              if (f_n[fd] - 1 - f_cur[fd] >= 2) { C.action = 2; C.fd = fd; break; }
-          }
-          if (C.action == 2) {
-            C.slot = 0xffffffffu;
-            for (uint32_t t = 0; t < p.pool_slots; ++t) {
-              uint32_t g = (rot + t) % p.pool_slots;
-              uint32_t* st = p.pool + (size_t)g * p.pool_slot_words;
-              if (*(volatile uint32_t*)st == SLOT_FREE && atomicCAS(st, SLOT_FREE, SLOT_BUSY) == SLOT_FREE) {
-                C.slot = g; rot = g + 1; break;
+          if (p.donate && cool == 0 && idle_hint > ready_hint) {
+            for (int32_t fd = 0; fd <= d; ++fd) {
+              if (f_n[fd] - 1 - f_cur[fd] >= 2) {
+                uint32_t slot, rpos;
+                if (ring_claim_for_fill(p, &slot, &rpos)) {
+                  const uint32_t k = f_cur[fd];
+                  C.action = 2; C.fd = fd; C.slot = slot; C.rpos = rpos;
+                  C.s_row = slot_list(fd)[2 * k];
+                  C.s_id = slot_list(fd)[2 * k + 1];
+                  C.cand_off = k + 1;
+                  C.nc = f_n[fd] - k - 1;
+                  f_cur[fd] = k + 1;
+                } else {
+                  cool = 32;
+                }
+                break;
               }
             }
-            if (C.slot == 0xffffffffu) {
-              C.action = 0;  // pool full: expand locally
-              donate_cool = 64;
-            } else {
-              const uint32_t fd = C.fd, k = f_cur[fd];
-              C.s = slot_list(fd)[k];
-              C.cand_off = k + 1;
-              C.nc = f_n[fd] - k - 1;
-              f_cur[fd] = k + 1;
-            }
           }
+          if (cool) --cool;
           if (C.action == 0) {
             if (f_cur[d] + 1 >= f_n[d]) {
               C.depth = d - 1;
-              C.action = 3;  // frame exhausted
+              C.action = 3;
             } else if ((uint32_t)(d + 1) > p.maxd) {
               atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
               C.depth = -1;
@@ -496,12 +545,18 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
             } else {
               const uint32_t k = f_cur[d];
               C.action = 1;
-              C.s = slot_list(d)[k];
+              C.s_row = slot_list(d)[2 * k];
+              C.s_id = slot_list(d)[2 * k + 1];
               C.cand_off = k + 1;
               C.nc = f_n[d] - k - 1;
               f_cur[d] = k + 1;
-              xs[xlen0 + d] = C.s;
+              xrow[xlen0 + d] = C.s_row;
+              xidp[xlen0 + d] = C.s_id;
             }
+          }
+          if (p.donate) {  // read now, used at the next decision
+            idle_hint = *(volatile uint32_t*)&p.ctrl->n_idle;
+            ready_hint = *(volatile uint32_t*)&p.ctrl->n_ready;
           }
         }
       }
@@ -511,18 +566,21 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
       if (action == 3) continue;
       if (action == 2) {
         // hand the child [X_fd u {s} | rest of frame fd] to an idle CTA
-        const uint32_t fd = C.fd, s = C.s, ncd = C.nc, coff = C.cand_off, gslot = C.slot;
-        uint32_t* sl = p.pool + (size_t)gslot * p.pool_slot_words;
+        const uint32_t fd = C.fd, ncd = C.nc, coff = C.cand_off;
+        uint32_t* sl = p.pool + (size_t)C.slot * sw;
         const uint32_t xl = xlen0 + fd + 1;
         if (threadIdx.x == 0) { sl[1] = xl; sl[2] = ncd; }
-        for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) sl[kSlotHeader + k] = k + 1 < xl ? xs[k] : s;
-        const uint32_t* src_list = slot_list(fd) + coff;
-        for (uint32_t k = threadIdx.x; k < ncd; k += blockDim.x) sl[kSlotHeader + A.max_len + k] = src_list[k];
+        for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) {
+          sl[kDfsSlotHeader + k] = k + 1 < xl ? xrow[k] : C.s_row;
+          sl[kDfsSlotHeader + L + k] = k + 1 < xl ? xidp[k] : C.s_id;
+        }
+        const uint32_t* src_list = slot_list(fd) + 2 * coff;
+        for (uint32_t k = threadIdx.x; k < 2 * ncd; k += blockDim.x) sl[kDfsSlotHeader + 2 * L + k] = src_list[k];
         const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(fd));
-        const uint4* r4 = bits4 + (size_t)p.frows[s] * A.stride4;
-        uint4* d4 = reinterpret_cast<uint4*>(sl + (p.pool_slot_words - p.stride));
+        const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
+        uint4* d4 = reinterpret_cast<uint4*>(sl + (sw - p.stride));
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          uint4 a = a4[w], b = __ldg(r4 + w);
+          const uint4 a = a4[w], b = __ldg(r4 + w);
           d4[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
         }
         __threadfence();
@@ -530,7 +588,7 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
         if (threadIdx.x == 0) {
           atomicAdd(&p.ctrl->pending, 1u);
           __threadfence();
-          atomicExch(sl, SLOT_READY);
+          atomicExch(sl, C.rpos + 1);  // publish
           atomicAdd(&p.ctrl->n_ready, 1u);
           ++st_don;
         }
@@ -538,29 +596,31 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
       }
       // action 1: expand the child [X_d u {s} | rest of frame d]
       const int32_t d = C.depth;
-      const uint32_t s = C.s, ncc = C.nc, coff = C.cand_off;
+      const uint32_t ncc = C.nc, coff = C.cand_off;
       const uint32_t xl = xlen0 + d + 1;  // prefix length of the child
       {
         const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(d));
-        const uint4* r4 = bits4 + (size_t)p.frows[s] * A.stride4;
+        const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
         uint4* d4 = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(d + 1));
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          uint4 a = a4[w], b = __ldg(r4 + w);
+          const uint4 a = a4[w], b = __ldg(r4 + w);
           d4[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
         }
       }
-      build_xid(p, xs, xl, xid);
+      sort_path_ids(xidp, xl, xid);
       __syncthreads();
-      uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : slot_pre(d + 1), false,
-                                      slot_list(d) + coff, false, ncc, slot_list(d + 1), list_cap, xl, st_inter);
-      if (threadIdx.x == 0) atomicAdd((unsigned long long*)&p.ctrl->n_nodes, 1ull);
-      if (n2 >= 2) {
-        if (PSMEM) {
-          const uint4* s4 = reinterpret_cast<const uint4*>(spre);
-          uint4* d4 = reinterpret_cast<uint4*>(slot_pre(d + 1));
-          for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = s4[w];
-        }
-        if (threadIdx.x == 0) { f_n[d + 1] = n2; f_cur[d + 1] = 0; C.depth = d + 1; ++st_frames; }
+      if (threadIdx.x == 0) st_inter += ncc;
+      const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : slot_pre(d + 1), false,
+                                            slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl);
+      if (n2 >= 2 && PSMEM) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(spre);
+        uint4* d4 = reinterpret_cast<uint4*>(slot_pre(d + 1));
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = s4[w];
+      }
+      if (threadIdx.x == 0) {
+        atomicAdd(&p.ctrl->n_nodes, 1ull);
+        atomicAdd(&p.ctrl->progress, 1u);
+        if (n2 >= 2) { f_n[d + 1] = n2; f_cur[d + 1] = 0; C.depth = d + 1; ++st_frames; }
       }
     }
     // class finished
@@ -570,9 +630,9 @@ __global__ void __launch_bounds__(512) k_dfs(const DfsArgs A) {
     }
   }
   if (threadIdx.x == 0) {
-    atomicAdd((unsigned long long*)&p.ctrl->n_intersections, st_inter);
-    atomicAdd((unsigned long long*)&p.ctrl->n_frames, st_frames);
-    atomicAdd((unsigned long long*)&p.ctrl->n_donations, st_don);
+    atomicAdd(&p.ctrl->n_intersections, st_inter);
+    atomicAdd(&p.ctrl->n_frames, st_frames);
+    atomicAdd(&p.ctrl->n_donations, st_don);
   }
 #undef slot_pre
 #undef slot_list
@@ -621,7 +681,7 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
 }
 
 size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem) {
-  size_t words = (prefix_in_smem ? stride : 0) + kCandBatch + 2ull * (maxd + 1) + 2ull * (max_len + 1);
+  size_t words = (prefix_in_smem ? stride : 0) + kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1);
   return words * sizeof(uint32_t);
 }
 
@@ -644,6 +704,12 @@ cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, boo
     case 8: return occ_t<8, false>(threads, smem, out);
     default: return occ_t<4, false>(threads, smem, out);
   }
+}
+
+cudaError_t launch_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words, cudaStream_t st) {
+  if (slots == 0) return cudaSuccess;
+  k_pool_init<<<(slots + 255) / 256, 256, 0, st>>>(pool, slots, slot_words);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,

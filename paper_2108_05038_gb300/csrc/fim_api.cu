@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -24,6 +25,109 @@ fim_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 // ---------------------------------------------------------------------------
+// device memory: one stream-ordered pool per device owned by the library, with
+// a release threshold high enough that freed blocks stay cached for the next
+// call instead of going back to the driver at every synchronisation
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaError_t lib_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e != cudaSuccess) return e;
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool;
+  cudaError_t e = lib_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+// ---------------------------------------------------------------------------
+// pinned host staging: blocks are cached process-wide so that building many
+// databases does not pay cudaMallocHost each time
+
+static std::mutex g_pinned_mu;
+static std::vector<std::pair<size_t, void*>> g_pinned_free;
+
+static cudaError_t pinned_acquire(size_t bytes, void** p, size_t* cap) {
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    size_t best = (size_t)-1;
+    for (size_t k = 0; k < g_pinned_free.size(); ++k)
+      if (g_pinned_free[k].first >= bytes && (best == (size_t)-1 || g_pinned_free[k].first < g_pinned_free[best].first))
+        best = k;
+    if (best != (size_t)-1) {
+      *p = g_pinned_free[best].second;
+      *cap = g_pinned_free[best].first;
+      g_pinned_free.erase(g_pinned_free.begin() + best);
+      return cudaSuccess;
+    }
+  }
+  *cap = bytes;
+  return cudaMallocHost(p, bytes);
+}
+
+static void pinned_release(void* p, size_t cap) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.emplace_back(cap, p);
+}
+
+}  // namespace fim
+
+// A region of the database's pinned staging buffer, valid until the next
+// synchronisation of its stream (callers reset the bump pointer after syncing).
+static fim_status stage_get(fim_db* db, size_t bytes, void** out) {
+  bytes = (bytes + 63) & ~(size_t)63;
+  if (db->stage_used + bytes > db->stage_cap) {
+    FIM_CUDA(cudaStreamSynchronize(db->stream));
+    db->stage_used = 0;
+    if (bytes > db->stage_cap) {
+      fim::pinned_release(db->stage, db->stage_cap);
+      db->stage = nullptr;
+      db->stage_cap = 0;
+      void* p = nullptr;
+      size_t cap = 0;
+      cudaError_t e = fim::pinned_acquire(std::max<size_t>(bytes, 1 << 16), &p, &cap);
+      if (e != cudaSuccess) return fim::cuda_fail(e, "pinned staging allocation");
+      db->stage = static_cast<uint8_t*>(p);
+      db->stage_cap = cap;
+    }
+  }
+  *out = db->stage + db->stage_used;
+  db->stage_used += bytes;
+  return FIM_OK;
+}
+
+static fim_status stream_sync(fim_db* db) {
+  FIM_CUDA(cudaStreamSynchronize(db->stream));
+  db->stage_used = 0;
+  return FIM_OK;
+}
+
+namespace fim {
+
+// ---------------------------------------------------------------------------
 // workspace
 
 fim_status Workspace::get(int slot, size_t nbytes, void** out) {
@@ -38,7 +142,7 @@ fim_status Workspace::get(int slot, size_t nbytes, void** out) {
       b.cap = 0;
     }
     size_t cap = nbytes + nbytes / 4 + 256;
-    cudaError_t e = cudaMallocAsync(&b.ptr, cap, stream);
+    cudaError_t e = dev_malloc_async(&b.ptr, cap, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       b.ptr = nullptr;
@@ -71,7 +175,7 @@ static fim_status ws_get(Workspace& ws, int slot, size_t count, T** out) {
 
 static uint32_t clamp_threads(uint32_t t) {
   if (t == 128 || t == 256 || t == 512) return t;
-  return 512;
+  return 256;
 }
 static uint32_t clamp_vec(uint32_t v) {
   if (v == 1 || v == 2 || v == 4 || v == 8) return v;
@@ -108,14 +212,21 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
     return FIM_OK;
   }
 
-  // device copies of the row lists
-  uint32_t *d_frows = nullptr, *d_rsupp = nullptr, *d_order = nullptr;
-  FIM_TRY(ws_get(ws, WS_FROWS, n1, &d_frows));
-  FIM_TRY(ws_get(ws, WS_ROWSUPP, n1, &d_rsupp));
-  FIM_TRY(ws_get(ws, WS_ROWORDER, n1, &d_order));
-  FIM_CUDA(cudaMemcpyAsync(d_frows, in.frows.data(), n1 * 4ull, cudaMemcpyHostToDevice, st));
-  FIM_CUDA(cudaMemcpyAsync(d_rsupp, in.row_supp.data(), n1 * 4ull, cudaMemcpyHostToDevice, st));
-  FIM_CUDA(cudaMemcpyAsync(d_order, in.row_order.data(), n1 * 4ull, cudaMemcpyHostToDevice, st));
+  // device copies of the row lists (uploaded through pinned staging unless given)
+  const uint32_t *d_frows = in.d_frows, *d_rsupp = in.d_row_supp, *d_order = in.identity_order ? db->d_iota : nullptr;
+  auto upload = [&](int slot, const std::vector<uint32_t>& v, const uint32_t** dst) -> fim_status {
+    uint32_t* d = nullptr;
+    void* h = nullptr;
+    FIM_TRY(ws_get(ws, slot, n1, &d));
+    FIM_TRY(stage_get(db, n1 * 4ull, &h));
+    std::memcpy(h, v.data(), n1 * 4ull);
+    FIM_CUDA(cudaMemcpyAsync(d, h, n1 * 4ull, cudaMemcpyHostToDevice, st));
+    *dst = d;
+    return FIM_OK;
+  };
+  if (!d_frows) FIM_TRY(upload(WS_FROWS, in.frows, &d_frows));
+  if (!d_rsupp) FIM_TRY(upload(WS_ROWSUPP, in.row_supp, &d_rsupp));
+  if (!d_order) FIM_TRY(upload(WS_ROWORDER, in.row_order, &d_order));
 
   const uint64_t npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
   uint32_t *d_C2 = nullptr, *d_scnt = nullptr, *d_soff = nullptr, *d_sitems = nullptr;
@@ -129,27 +240,22 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
 
   // DFS geometry
   const uint32_t L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
-  const uint32_t maxd = std::max<uint32_t>(1, L - 2);
+  const uint32_t maxd_full = std::max<uint32_t>(1, L - 2);
+  uint32_t maxd = std::min<uint32_t>(maxd_full, kDfsDepthHint);  // grown (and the mine redone) on overflow
   const uint32_t threads = clamp_threads(cfg.threads);
   const uint32_t vec = clamp_vec(cfg.vec);
-  const bool psmem = dfs_prefix_fits(in.stride, db->smem_optin, L, maxd);
-  const size_t smem = dfs_smem_bytes(in.stride, L, maxd, psmem);
+  const bool psmem = dfs_prefix_fits(in.stride, db->smem_optin, L, maxd_full);
+  const size_t smem = dfs_smem_bytes(in.stride, L, maxd_full, psmem);
   int occ = 0;
   FIM_CUDA(dfs_max_ctas_per_sm(threads, vec, smem, psmem, &occ));
   if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
   uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
   const uint32_t grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);
-  const uint64_t per_depth = (uint64_t)in.stride + ((n1 + 3u) & ~3u);
-  const uint64_t arena_cta_words = per_depth * (maxd + 1);
-  uint32_t* d_arena = nullptr;
-  FIM_TRY(ws_get(ws, WS_ARENA, arena_cta_words * grid, &d_arena));
+  const uint64_t per_depth = dfs_arena_depth_words(in.stride, n1);
   const uint32_t pool_slots = cfg.donate ? std::max<uint32_t>(8, grid) : 0;
-  const uint64_t pool_slot_words = (((uint64_t)kDfsSlotHeader + L + n1 + 3) & ~3ull) + in.stride;
+  const uint64_t pool_slot_words = dfs_pool_slot_words(in.stride, L, n1);
   uint32_t* d_pool = nullptr;
-  if (pool_slots) {
-    FIM_TRY(ws_get(ws, WS_POOL, pool_slot_words * pool_slots, &d_pool));
-    FIM_CUDA(cudaMemset2DAsync(d_pool, pool_slot_words * 4, 0, 16, pool_slots, st));
-  }
+  if (pool_slots) FIM_TRY(ws_get(ws, WS_POOL, pool_slot_words * pool_slots, &d_pool));
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   if (cfg.collect_times) {
@@ -160,18 +266,21 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
       if (e) cudaEventDestroy(e);
   };
 
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
     uint64_t *d_off = nullptr;
-    uint32_t *d_items = nullptr, *d_supp = nullptr;
+    uint32_t *d_items = nullptr, *d_supp = nullptr, *d_arena = nullptr;
+    const uint64_t arena_cta_words = per_depth * (maxd + 1);
     fim_status s;
     if ((s = ws_get(ws, WS_OUT_OFF, cap_sets + 1, &d_off)) != FIM_OK ||
         (s = ws_get(ws, WS_OUT_ITEMS, cap_items, &d_items)) != FIM_OK ||
-        (s = ws_get(ws, WS_OUT_SUPP, cap_sets, &d_supp)) != FIM_OK) {
+        (s = ws_get(ws, WS_OUT_SUPP, cap_sets, &d_supp)) != FIM_OK ||
+        (s = ws_get(ws, WS_ARENA, arena_cta_words * grid, &d_arena)) != FIM_OK) {
       destroy_events();
       return s;
     }
     cudaError_t ce = cudaSuccess;
     if (attempt > 0) ce = cudaMemsetAsync(d_ctrl, 0, sizeof(DevCtrl), st);
+    if (ce == cudaSuccess && pool_slots) ce = launch_pool_init(d_pool, pool_slots, pool_slot_words, st);
     if (ev[0]) cudaEventRecord(ev[0], st);
     uint32_t ksplit = 0;
     if (ce == cudaSuccess) {
@@ -219,23 +328,34 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
       return cuda_fail(ce, "mining kernels");
     }
     DevCtrl h{};
-    ce = cudaMemcpyAsync(&h, d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st);
+    void* hstage = nullptr;
+    if ((s = stage_get(db, sizeof(DevCtrl), &hstage)) != FIM_OK) {
+      destroy_events();
+      return s;
+    }
+    ce = cudaMemcpyAsync(hstage, d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
       destroy_events();
       return cuda_fail(ce, "mining kernels (sync)");
     }
+    std::memcpy(&h, hstage, sizeof(DevCtrl));
+    db->stage_used = 0;
     if (h.err & DEV_ERR_TIMEOUT) {
       destroy_events();
       return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
     }
     if (h.err & DEV_ERR_DEPTH) {
-      destroy_events();
-      return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
+      if (maxd >= maxd_full) {
+        destroy_events();
+        return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
+      }
+      maxd = maxd_full;  // deeper than the first arena: redo with the full bound
+      continue;
     }
     const bool overflow = h.sets_total > cap_sets || h.items_total > cap_items;
     if (overflow) {
-      if (cfg.fixed_capacity || attempt == 1) {
+      if (cfg.fixed_capacity || attempt == 3) {
         out->ctrl = h;
         destroy_events();
         set_error("output capacity exceeded");
@@ -250,8 +370,10 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
       }
       continue;
     }
-    const uint64_t fin = h.items_total;
-    FIM_CUDA(cudaMemcpyAsync(d_off + h.sets_total, &fin, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    void* hfin = nullptr;
+    FIM_TRY(stage_get(db, sizeof(uint64_t), &hfin));
+    *static_cast<uint64_t*>(hfin) = h.items_total;
+    FIM_CUDA(cudaMemcpyAsync(d_off + h.sets_total, hfin, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     out->n_sets = h.sets_total;
     out->n_items = h.items_total;
     out->d_off = d_off;
@@ -313,7 +435,7 @@ static fim_status db_init(fim_db* db, uint32_t D, uint32_t N, uint32_t word_bits
 template <typename T>
 static fim_status dev_alloc(fim_db* db, T** p, size_t count) {
   size_t bytes = std::max<size_t>(16, count * sizeof(T));
-  cudaError_t e = cudaMallocAsync((void**)p, bytes, db->stream);
+  cudaError_t e = dev_malloc_async((void**)p, bytes, db->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -332,9 +454,11 @@ static fim_status db_build_rows(fim_db* db) {
   d_flags = d_cnt + N;  // [err, max_len]
   FIM_CUDA(cudaMemsetAsync(d_cnt, 0, ((size_t)N + 2) * 4, st));
   FIM_CUDA(launch_item_count(db->d_tx_off, db->d_tx_items, D, N, d_cnt, d_flags, d_flags + 1, st));
-  std::vector<uint32_t> cnt((size_t)N + 2);
-  FIM_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, ((size_t)N + 2) * 4, cudaMemcpyDeviceToHost, st));
-  FIM_CUDA(cudaStreamSynchronize(st));
+  void* hcnt = nullptr;
+  FIM_TRY(stage_get(db, ((size_t)N + 2) * 4, &hcnt));
+  FIM_CUDA(cudaMemcpyAsync(hcnt, d_cnt, ((size_t)N + 2) * 4, cudaMemcpyDeviceToHost, st));
+  FIM_TRY(stream_sync(db));
+  std::vector<uint32_t> cnt(static_cast<uint32_t*>(hcnt), static_cast<uint32_t*>(hcnt) + N + 2);
   const uint32_t err = cnt[N];
   if (err & DEV_ERR_ITEM_RANGE) return fail(FIM_ERR_INVALID, "an item id is >= N");
   if (err & DEV_ERR_OFFSETS) return fail(FIM_ERR_INVALID, "tx_offsets is not non-decreasing");
@@ -356,14 +480,27 @@ static fim_status db_build_rows(fim_db* db) {
   FIM_TRY(dev_alloc(db, &db->d_rank_item, db->n_rows));
   FIM_TRY(dev_alloc(db, &db->d_supp, db->n_rows));
   FIM_TRY(dev_alloc(db, &db->d_bits, (size_t)db->n_rows * db->stride));
-  FIM_CUDA(cudaMemcpyAsync(db->d_item_rank, db->item_rank.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+  FIM_TRY(dev_alloc(db, &db->d_iota, db->n_rows));
+  {
+    void* h = nullptr;
+    FIM_TRY(stage_get(db, ((size_t)N + 2ull * db->n_rows) * 4, &h));
+    uint32_t* hu = static_cast<uint32_t*>(h);
+    std::memcpy(hu, db->item_rank.data(), (size_t)N * 4);
+    if (db->n_rows) {
+      std::memcpy(hu + N, db->rank_item.data(), (size_t)db->n_rows * 4);
+      std::memcpy(hu + N + db->n_rows, db->supp.data(), (size_t)db->n_rows * 4);
+    }
+    FIM_CUDA(cudaMemcpyAsync(db->d_item_rank, hu, (size_t)N * 4, cudaMemcpyHostToDevice, st));
+    if (db->n_rows) {
+      FIM_CUDA(cudaMemcpyAsync(db->d_rank_item, hu + N, (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
+      FIM_CUDA(cudaMemcpyAsync(db->d_supp, hu + N + db->n_rows, (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
+    }
+  }
+  FIM_CUDA(launch_iota(db->d_iota, db->n_rows, st));
   if (db->n_rows) {
-    FIM_CUDA(cudaMemcpyAsync(db->d_rank_item, db->rank_item.data(), (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
-    FIM_CUDA(cudaMemcpyAsync(db->d_supp, db->supp.data(), (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
     FIM_CUDA(cudaMemsetAsync(db->d_bits, 0, (size_t)db->n_rows * db->stride * 4, st));
     FIM_CUDA(launch_bitmap_build(db->d_tx_off, db->d_tx_items, D, db->d_item_rank, db->d_bits, db->stride, st));
   }
-  FIM_CUDA(cudaStreamSynchronize(st));
   return FIM_OK;
 }
 
@@ -385,10 +522,16 @@ static fim_status build_common(const uint32_t* off, const uint32_t* items, uint3
   cudaStream_t st = db->stream;
   uint32_t first = 0, last = 0;
   if (device_input) {
-    cudaError_t e = cudaMemcpyAsync(&first, off, 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&last, off + D, 4, cudaMemcpyDeviceToHost, st);
+    void* h = nullptr;
+    if ((s = stage_get(db, 8, &h)) != FIM_OK) return bail(s);
+    uint32_t* hu = static_cast<uint32_t*>(h);
+    cudaError_t e = cudaMemcpyAsync(hu, off, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hu + 1, off + D, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "reading tx_offsets"));
+    db->stage_used = 0;
+    first = hu[0];
+    last = hu[1];
   } else {
     first = off[0];
     for (uint32_t t = 0; t < D; ++t)
@@ -425,7 +568,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   fim_mine_opts d;
   fim_mine_opts_init(&d);
   if (!o || o->struct_size == 0) o = &d;
-  c->threads = o->threads_per_cta ? o->threads_per_cta : 512;
+  c->threads = o->threads_per_cta ? o->threads_per_cta : 256;
   c->vec = o->vec_per_lane ? o->vec_per_lane : 4;
   c->ctas_per_sm = o->ctas_per_sm;
   c->donate = o->donate;
@@ -518,8 +661,11 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
     FIM_CUDA(cudaMemsetAsync(d_sbits, 0, (size_t)R * sstride * 4, st));
     FIM_CUDA(launch_sample_build(db->d_tx_off, db->d_tx_items, db->D, db->d_item_rank, seed, m, d_sbits, sstride, st));
     FIM_CUDA(launch_row_popcount(d_sbits, sstride, R, d_ssupp, st));
-    FIM_CUDA(cudaMemcpyAsync(ssupp.data(), d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
-    FIM_CUDA(cudaStreamSynchronize(st));
+    void* h = nullptr;
+    FIM_TRY(stage_get(db, (size_t)R * 4, &h));
+    FIM_CUDA(cudaMemcpyAsync(h, d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+    FIM_TRY(stream_sync(db));
+    std::memcpy(ssupp.data(), h, (size_t)R * 4);
   }
   EngineInput in;
   in.bits = d_sbits;
@@ -533,6 +679,7 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
   in.n1 = (uint32_t)in.frows.size();
   in.row_order.resize(in.n1);
   std::iota(in.row_order.begin(), in.row_order.end(), 0u);
+  in.identity_order = true;
   in.d_rank_item = db->d_rank_item;
   in.minsup = minsup_s;
   in.max_len_bound = db->max_tx_len;
@@ -546,8 +693,11 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
     FIM_TRY(ws_get(db->ws, WS_TALLY, R, &d_tally));
     FIM_CUDA(cudaMemsetAsync(d_tally, 0, (size_t)R * 8, st));
     FIM_CUDA(launch_tally_min_rank(eo.d_off, eo.d_items, eo.n_sets, db->d_item_rank, d_tally, st));
-    FIM_CUDA(cudaMemcpyAsync(tally.data(), d_tally, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
-    FIM_CUDA(cudaStreamSynchronize(st));
+    void* h = nullptr;
+    FIM_TRY(stage_get(db, (size_t)R * 8, &h));
+    FIM_CUDA(cudaMemcpyAsync(h, d_tally, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+    FIM_TRY(stream_sync(db));
+    std::memcpy(tally.data(), h, (size_t)R * 8);
   }
   db->est_cost.assign(R, 0.0);
   for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = eo.n_sets ? (double)tally[r] / (double)eo.n_sets : 0.0;
@@ -590,6 +740,10 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
   in.bytes_per_row_alg = (uint32_t)(((uint64_t)db->D + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
   in.d_rank_item = db->d_rank_item;
   in.minsup = minsup_abs;
+  if (in.n1) {
+    in.d_frows = db->d_iota + (db->n_rows - in.n1);  // frequent rows are the suffix
+    in.d_row_supp = db->d_supp + (db->n_rows - in.n1);
+  }
   in.max_len_bound = db->max_tx_len;
   const uint32_t order = opts && opts->struct_size ? opts->class_order : (uint32_t)FIM_ORDER_ESTIMATE;
   in.row_order.clear();
@@ -600,6 +754,7 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
       if (r >= r0) in.row_order.push_back(r - r0);
   } else {
     for (uint32_t k = 0; k < in.n1; ++k) in.row_order.push_back(k);
+    in.identity_order = true;
   }
   EngineConfig cfg;
   engine_config_from_opts(opts, &cfg);
@@ -623,9 +778,9 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
   cudaError_t e = cudaSuccess;
   if (on_dev) {
     res->on_device = 1;
-    e = cudaMallocAsync((void**)&res->d_off, (eo.n_sets + 1) * 8, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&res->d_items, std::max<uint64_t>(1, eo.n_items) * 4, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&res->d_supp, std::max<uint64_t>(1, eo.n_sets) * 4, st);
+    e = dev_malloc_async((void**)&res->d_off, (eo.n_sets + 1) * 8, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_items, std::max<uint64_t>(1, eo.n_items) * 4, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_supp, std::max<uint64_t>(1, eo.n_sets) * 4, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(res->d_off, eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && eo.n_items)
       e = cudaMemcpyAsync(res->d_items, eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToDevice, st);
@@ -679,10 +834,11 @@ void fim_db_free(fim_db* db) {
   if (!db) return;
   cudaStream_t st = db->stream;
   db->ws.release();
-  void* ptrs[] = {db->d_bits, db->d_rank_item, db->d_item_rank, db->d_supp, db->d_tx_off, db->d_tx_items};
+  void* ptrs[] = {db->d_bits, db->d_rank_item, db->d_item_rank, db->d_supp, db->d_tx_off, db->d_tx_items, db->d_iota};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, st);
   cudaStreamSynchronize(st);
+  fim::pinned_release(db->stage, db->stage_cap);
   delete db;
 }
 

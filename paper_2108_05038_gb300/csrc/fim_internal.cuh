@@ -16,6 +16,8 @@ namespace fim {
 // error reporting
 
 void set_error(const std::string& msg);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st);
+struct fim_db_fwd;
 fim_status fail(fim_status s, const std::string& msg);
 fim_status cuda_fail(cudaError_t e, const char* what);
 
@@ -81,24 +83,38 @@ enum WsSlot {
   WS_COUNT
 };
 
-// small control block living in device memory (one per mining call)
-struct DevCtrl {
+// small control block living in device memory (one per mining call); fields
+// that are polled by idle CTAs and fields that every node updates live on
+// separate 128-byte lines
+struct alignas(128) DevCtrl {
+  // line 0: output reservation and counters updated by every node
   unsigned long long packed;       // (records << 32) | items reserved so far
   unsigned long long items_total;  // exact items requested (for overflow reporting)
   unsigned long long sets_total;   // exact sets requested
   unsigned long long n_intersections;
-  unsigned long long n_nodes;
   unsigned long long n_frames;     // prefixes materialised into the arena
   unsigned long long n_donations;
-  uint32_t queue_head;             // next static queue entry
-  uint32_t n_entries;              // static queue length (written by the scan kernel)
-  uint32_t err;                    // DEV_ERR_* bits
   uint32_t max_len;                // longest itemset emitted
   uint32_t n_pairs;                // frequent pairs
-  uint32_t pending;                // unfinished queue entries (termination detection)
-  uint32_t n_idle;                 // CTAs waiting for work
-  uint32_t n_ready;                // donated entries waiting in the pool
-  uint32_t pad[4];
+  uint32_t err;                    // DEV_ERR_* bits
+  uint32_t pad0[17];
+  // line 1: static queue
+  alignas(128) uint32_t queue_head;  // next static queue entry
+  uint32_t n_entries;                // static queue length (written by the scan kernel)
+  uint32_t pad1[30];
+  // line 2: termination and progress (polled)
+  alignas(128) uint32_t pending;     // unfinished queue entries
+  uint32_t progress;                 // nodes finished (any CTA), the no-progress timer's clock
+  uint32_t pad2[30];
+  // line 3: donation ring (Vyukov bounded MPMC queue over the pool slots)
+  alignas(128) uint32_t ring_head;
+  uint32_t ring_tail;
+  uint32_t n_idle;                   // CTAs waiting for work
+  uint32_t n_ready;                  // donated classes waiting in the ring
+  uint32_t pad3[28];
+  // line 4: node count (stats)
+  alignas(128) unsigned long long n_nodes;
+  uint32_t pad4[30];
 };
 
 // ---------------------------------------------------------------------------
@@ -138,6 +154,12 @@ struct fim_db {
   uint32_t est_m = 0, est_minsup = 0;
 
   fim::Workspace ws;
+
+  uint32_t* d_iota = nullptr;  // 0 .. n_rows-1 (frequent-row lists of the full database point into it)
+  // pinned host staging for small copies; regions are handed out by a bump
+  // pointer that is reset whenever the stream has been synchronised
+  uint8_t* stage = nullptr;
+  size_t stage_cap = 0, stage_used = 0;
 };
 
 struct fim_result {
@@ -159,6 +181,9 @@ namespace fim {
 
 struct EngineInput {
   const uint32_t* bits = nullptr;  // rows of `stride` words
+  const uint32_t* d_frows = nullptr;     // optional device copy of frows (else uploaded)
+  const uint32_t* d_row_supp = nullptr;  // optional device copy of row_supp (else uploaded)
+  bool identity_order = false;           // row_order is 0..n1-1 (d_frows-style device iota used)
   uint32_t stride = 0;             // padded words per row
   uint32_t bytes_per_row_alg = 0;  // W * w / 8: unpadded bytes of one row (algorithmic)
   uint32_t n1 = 0;                 // frequent rows taking part
@@ -179,7 +204,7 @@ struct EngineOutput {
 };
 
 struct EngineConfig {
-  uint32_t threads = 512;
+  uint32_t threads = 256;
   uint32_t vec = 4;
   uint32_t ctas_per_sm = 0;
   uint32_t donate = 1;
@@ -202,6 +227,7 @@ cudaError_t launch_bitmap_build(const uint32_t* off, const uint32_t* items, uint
                                 uint32_t* bits, uint32_t stride, cudaStream_t st);
 cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
                                 uint64_t seed, uint32_t m, uint32_t* sbits, uint32_t sstride, cudaStream_t st);
+cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t n_rows, uint32_t* supp,
                                 cudaStream_t st);
 cudaError_t launch_tally_min_rank(const uint64_t* set_off, const uint32_t* set_items, uint64_t n_sets,
@@ -267,8 +293,16 @@ struct DfsLaunch {
 cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
                        bool prefix_in_smem, uint32_t max_len, cudaStream_t st);
 size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem);
+cudaError_t launch_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words, cudaStream_t st);
 cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, int* out);
 bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd);
-constexpr uint32_t kDfsSlotHeader = 4;  // donation pool slot: state, xlen, ncand, spare
+constexpr uint32_t kDfsDepthHint = 8;  // DFS stack depth allocated first (grown on demand)
+constexpr uint32_t kDfsSlotHeader = 4;  // donation pool slot: sequence, xlen, ncand, spare
+// pool slot words for itemsets of up to max_len items and n1 candidates (prefix bitmap last)
+__host__ __device__ inline uint64_t dfs_pool_slot_words(uint32_t stride, uint32_t max_len, uint32_t n1) {
+  return (((uint64_t)kDfsSlotHeader + 2ull * max_len + 2ull * n1 + 3) & ~3ull) + stride;
+}
+// arena words per depth: one prefix bitmap + one (row, id) survivor list
+__host__ __device__ inline uint64_t dfs_arena_depth_words(uint32_t stride, uint32_t n1) { return (uint64_t)stride + ((2ull * n1 + 3) & ~3ull); }
 
 }  // namespace fim

@@ -8,8 +8,12 @@
 // (upper triangle only), stages 32-word slices of the 64 + 64 rows in shared
 // memory with cp.async (3-stage pipeline), and every thread accumulates a 4 x 4
 // micro-tile.  Each staged word is reused by 64 pairs, so the kernel is bound
-// by the integer pipe (AND + POPC per word pair), not by memory.  Long rows
-// are split along the word axis over grid.y (partial counts added atomically).
+// by the integer pipe (AND + POPC per word pair), not by memory.  Rows are
+// split along the word axis into (tile, word range) work items that a grid of
+// two CTAs per SM walks through (partial counts added atomically), which keeps
+// every SM busy until the last wave.
+#include <mutex>
+
 #include "fim_internal.cuh"
 
 namespace fim {
@@ -40,17 +44,19 @@ __device__ __forceinline__ void acc_and_popc(uint32_t& acc, uint32_t a, uint32_t
 __global__ void __launch_bounds__(kThreads, 2)
 k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows, uint32_t n1,
               uint32_t nb, uint32_t chunks_per_split, uint32_t nchunks, uint32_t* __restrict__ C2, uint32_t ksplit,
-              uint32_t one) {
+              uint32_t n_items, uint32_t one) {
   extern __shared__ __align__(16) uint32_t sm[];
   const uint32_t tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-
-  uint32_t t = blockIdx.x, bi = 0;
+  // persistent loop over work items (tile, word range); consecutive items share a tile
+  for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  uint32_t t = item / ksplit, bi = 0;
+  const uint32_t split = item - t * ksplit;
   while (t >= nb - bi) { t -= nb - bi; ++bi; }
   const uint32_t bj = bi + t;
   const uint32_t i0 = bi * kTile, j0 = bj * kTile;
-  const uint32_t c_begin = blockIdx.y * chunks_per_split;
+  const uint32_t c_begin = split * chunks_per_split;
   const uint32_t c_end = min(nchunks, c_begin + chunks_per_split);
-  if (c_begin >= c_end) return;
+  if (c_begin >= c_end) continue;
 
   // four 16-byte copies per thread and stage: 64 A rows + 64 B rows x 8 vectors.
   // Copy q moves vector (tid & 7) of tile row (tid >> 3) + 32 * (q & 1) of A (q < 2) or B.
@@ -117,6 +123,7 @@ k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t
     stage = stage + 1 == kStages ? 0 : stage + 1;
   }
   cp_async_wait<0>();
+  __syncthreads();  // the next item refills the stages
 
 #pragma unroll
   for (int x = 0; x < 4; ++x)
@@ -128,27 +135,29 @@ k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t
         else C2[(size_t)i * n1 + j] = acc[x][y];
       }
     }
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used) {
   if (p.n1 < 2) { *ksplit_used = 0; return cudaSuccess; }
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_pair_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   const uint32_t nb = (p.n1 + kTile - 1) / kTile;
   const uint32_t tiles = nb * (nb + 1) / 2;
   const uint32_t nchunks = p.stride / kChunk;  // stride is a multiple of 32 words
+  const uint32_t slots = (uint32_t)num_sms * 2;  // two resident CTAs per SM
   uint32_t ksplit = p.ksplit;
   if (ksplit == 0) {
-    // enough CTAs for ~2 resident per SM, but at least 8 chunks (256 words) per split
-    uint32_t target = (uint32_t)num_sms * 2;
-    ksplit = (target + tiles - 1) / tiles;
-    uint32_t maxsplit = nchunks / 8 > 0 ? nchunks / 8 : 1;
+    // enough (tile, word-range) items for >= 4 per resident CTA, each of >= 8 chunks (256 words)
+    const uint32_t want = 4 * slots;
+    ksplit = (want + tiles - 1) / tiles;
+    const uint32_t maxsplit = nchunks / 8 > 0 ? nchunks / 8 : 1;
     if (ksplit > maxsplit) ksplit = maxsplit;
     if (ksplit < 1) ksplit = 1;
   }
@@ -159,8 +168,10 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
     cudaError_t e = cudaMemsetAsync(p.C2, 0, (size_t)p.n1 * p.n1 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(tiles, ksplit);
-  k_pair_counts<<<grid, kThreads, kSmemBytes, st>>>(p.bits, p.stride, p.frows, p.n1, nb, cps, nchunks, p.C2, ksplit, 1u);
+  const uint32_t n_items = tiles * ksplit;
+  const uint32_t grid = n_items < slots ? n_items : slots;
+  k_pair_counts<<<grid, kThreads, kSmemBytes, st>>>(p.bits, p.stride, p.frows, p.n1, nb, cps, nchunks, p.C2, ksplit,
+                                                     n_items, 1u);
   return cudaGetLastError();
 }
 

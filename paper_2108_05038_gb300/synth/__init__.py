@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
     """Compile synth.c into libfimsynth.so next to it (gcc, -O2)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -63,6 +64,10 @@ def _load():
             lib.synth_copy.argtypes = [P, P, P]
             lib.synth_free.restype = None
             lib.synth_free.argtypes = [P]
+            lib.synth_exp.restype = dbl
+            lib.synth_exp.argtypes = [dbl]
+            lib.synth_log.restype = dbl
+            lib.synth_log.argtypes = [dbl]
             lib.synth_splitmix64_next.restype = u64
             lib.synth_splitmix64_next.argtypes = [ctypes.POINTER(u64)]
             _lib = lib
@@ -108,10 +113,18 @@ def splitmix64_stream(state: int, n: int):
     return [lib.synth_splitmix64_next(ctypes.byref(s)) for _ in range(n)]
 
 
+def csr_digest(offsets, items) -> str:
+    """SHA-256 of a CSR database (little-endian u32 offsets then items)."""
+    import hashlib
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(offsets, dtype="<u4").tobytes())
+    h.update(np.ascontiguousarray(items, dtype="<u4").tobytes())
+    return h.hexdigest()
+
+
 # ---------------------------------------------------------------------------
 # Named workloads.  Each returns a dict with the CSR arrays and the absolute
-# minimum support; ``scale`` shrinks D (and npat/N proportionally where noted)
-# for quick CPU-side runs without changing the laws.
+# minimum support; ``make_workload(name, D=...)`` keeps the laws and changes D.
 
 WORKLOADS = {
     "tiny": dict(kind="pattern", seed=0, D=10_000, N=100, TL=10.0, PL=4.0, npat=200, popularity="uniform",

@@ -9,6 +9,10 @@
  * Random numbers come from SplitMix64 (G. Steele, D. Lea, C. Flood, "Fast
  * splittable pseudorandom number generators", OOPSLA 2014), used as a
  * sequential stream per purpose; each stream is seeded from (seed, purpose).
+ * The only transcendental functions (exp, log) are computed here from IEEE
+ * additions, multiplications and divisions, and the file is compiled without
+ * floating-point contraction, so a seed gives the same database bit for bit on
+ * every IEEE-754 machine (x86-64 and aarch64 alike).
  *
  * Generators:
  *  - pattern-embedded ("Quest-like") databases: npat seed patterns with
@@ -24,12 +28,44 @@
  *  - dense fixed-length databases: exactly k distinct items per transaction,
  *    drawn without replacement with weights p_i as above.
  */
-#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define GAMMA64 0x9E3779B97F4A7C15ULL
+
+/* exp and log from basic IEEE operations only (no libm: its last-bit results
+ * differ between platforms).  ln 2 is split in a high part exact in 32 bits
+ * and a low part, as in Cody-Waite range reduction. */
+static const double LN2_HI = 6.93147180369123816490e-01;
+static const double LN2_LO = 1.90821492927058770002e-10;
+static double scale2(double x, int k) {
+  /* x * 2^k for |k| < 1000 by repeated exact scaling */
+  while (k > 60) { x *= 1152921504606846976.0; k -= 60; }
+  while (k < -60) { x *= 8.67361737988403547206e-19; k += 60; }
+  if (k >= 0) return x * (double)(1ULL << k);
+  return x / (double)(1ULL << (-k));
+}
+static double my_exp(double x) {
+  if (x < -700.0) return 0.0;
+  if (x > 700.0) x = 700.0;
+  double kd = x / (LN2_HI + LN2_LO);
+  int k = (int)(kd < 0 ? kd - 0.5 : kd + 0.5);
+  double r = (x - (double)k * LN2_HI) - (double)k * LN2_LO;   /* |r| <= ln2/2 */
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 30; ++n) { term = term * r / (double)n; sum += term; }
+  return scale2(sum, k);
+}
+static double my_log(double x) {
+  /* x > 0: x = m * 2^k with m in [1, 2); log m = 2 atanh((m-1)/(m+1)) */
+  int k = 0;
+  while (x >= 2.0) { x *= 0.5; ++k; }
+  while (x < 1.0) { x *= 2.0; --k; }
+  double z = (x - 1.0) / (x + 1.0), z2 = z * z, term = z, sum = 0.0;
+  for (int n = 1; n < 80; n += 2) { sum += term / (double)n; term *= z2; }
+  return 2.0 * sum + (double)k * LN2_HI + (double)k * LN2_LO;
+}
+static double my_pow(double b, double e) { return my_exp(e * my_log(b)); }
 
 typedef struct { uint64_t s; } rng_t;
 
@@ -55,7 +91,7 @@ static uint32_t rng_below(rng_t* r, uint32_t n) {
 }
 static uint32_t rng_poisson(rng_t* r, double lam) {
   /* sequential inversion; lam here is at most a few tens */
-  double u = rng_unit(r), p = exp(-lam), f = p;
+  double u = rng_unit(r), p = my_exp(-lam), f = p;
   uint32_t k = 0;
   while (u > f && k < 10000) {
     ++k;
@@ -80,7 +116,7 @@ static int pop_init(popularity_t* p, uint32_t n, int zipf, double s, uint64_t se
   p->perm = (uint32_t*)malloc(sizeof(uint32_t) * n);
   if (!p->cdf || !p->perm) return -1;
   double acc = 0.0;
-  for (uint32_t k = 0; k < n; ++k) { acc += pow((double)(k + 1), -s); p->cdf[k] = acc; }
+  for (uint32_t k = 0; k < n; ++k) { acc += my_pow((double)(k + 1), -s); p->cdf[k] = acc; }
   for (uint32_t k = 0; k < n; ++k) p->cdf[k] /= acc;
   p->cdf[n - 1] = 1.0;
   for (uint32_t k = 0; k < n; ++k) p->perm[k] = k;
@@ -183,7 +219,7 @@ synth_db* synth_pattern_db(uint64_t seed, uint32_t D, uint32_t N, double TL, dou
       }
       for (uint32_t k = pat_off[p]; k < pat_n; ++k) mark[pat_items[k]] = 0;
       pat_off[p + 1] = pat_n;
-      wsum += -log(rng_unit(&rp));
+      wsum += -my_log(rng_unit(&rp));
       pat_cdf[p] = wsum;
     }
     for (uint32_t p = 0; p < npat; ++p) pat_cdf[p] /= wsum;
@@ -281,6 +317,9 @@ synth_db* synth_dense_fixed(uint64_t seed, uint32_t D, uint32_t N, uint32_t k, d
 
 /* Raw SplitMix64 stream values, exposed so tests can pin this file's generator
  * against the published reference sequence. */
+double synth_exp(double x) { return my_exp(x); }
+double synth_log(double x) { return my_log(x); }
+
 uint64_t synth_splitmix64_next(uint64_t* state) {
   *state += GAMMA64;
   return mix64(*state);

@@ -4,11 +4,14 @@ Counts are integers, so the bar is bit-exact: the same set of itemsets and the
 same supports.  The output order of the GPU is unspecified; sets are compared
 as canonical dictionaries (items ascending inside a set).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
 
+import canon
 import oracle
 from paper_2108_05038_gb300 import synth
 
@@ -85,10 +88,12 @@ def test_ragged_D(D):
     assert_same(gpu_mine(off, items, 12, minsup).as_dict(), odict(oracle.eclat(off, items, 12, minsup)))
 
 
-def test_identical_transactions_closed_form():
-    k, D = 11, 300
-    off, items = csr([list(range(k))] * D)
-    got = gpu_mine(off, items, k, D).as_dict()
+@pytest.mark.parametrize("k", [11, 16])
+def test_identical_transactions_closed_form(k):
+    """2^k - 1 itemsets of support D; depth 14 exceeds the first DFS stack and forces the regrown retry."""
+    D = 300
+    off, items = csr([list(range(k))] * D + [[k]])
+    got = gpu_mine(off, items, k + 1, D).as_dict()
     assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
 
 
@@ -220,16 +225,31 @@ def test_row_order_matches_oracle():
     assert np.all(np.diff(sp.astype(np.int64)) >= 0)
 
 
-# ---------------------------------------------------------------- full-size large sparse (sampled certificate)
+# ---------------------------------------------------------------- full sizes against stored oracle digests
 
-@pytest.mark.slow
-def test_large_sparse_certificate():
-    """1M transactions x 10k items: the oracle's certificate on every 97th output set."""
-    w = synth.make_workload("large_sparse")
-    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=64)
+DIGESTS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "digests.json")))
+
+
+@pytest.mark.parametrize("name", sorted(DIGESTS))
+def test_full_size_digest(name):
+    """Every named workload at full size: the generated database is the one the oracle mined
+    (CSR SHA-256), and the GPU's canonical output hashes to the oracle's (tests/golden/make_digests.py)."""
+    ref = DIGESTS[name]
+    w = synth.make_workload(name)
+    assert synth.csr_digest(w["offsets"], w["items"]) == ref["csr_sha256"]
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=w["word_bits"])
     db.estimate_class_costs(0.01, w["rel_minsup"], 3)
     res = db.mine(w["minsup"])
     db.free()
+    assert canon.digest(res.set_offsets, res.set_items, res.supports) == ref["oracle"]
+
+
+def test_large_sparse_certificate():
+    """large_sparse at full size: the oracle's certificate (recount, parents, completeness) on sampled sets."""
+    w = synth.make_workload("large_sparse")
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=64)
+    res = db.mine(w["minsup"], class_order="uniform")
+    db.free()
     code, bad = oracle.check(w["offsets"], w["items"], w["N"], w["minsup"], res.set_offsets, res.set_items,
-                             res.supports, stride=97)
+                             res.supports, stride=20011)
     assert code == 0, (oracle.CHECK_CODES[code], bad)
