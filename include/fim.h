@@ -33,6 +33,8 @@ extern "C" {
 
 typedef struct fim_db fim_db;         /* device bitmaps + item relabel map + CSR copy for sampling */
 typedef struct fim_result fim_result; /* frequent itemsets in CSR form (host or device memory)      */
+typedef struct fim_plan fim_plan;     /* one (database, minsup) mine captured in a CUDA graph        */
+typedef struct fim_server fim_server; /* continuous-batching request loop over mining jobs           */
 
 typedef enum {
   FIM_OK = 0,
@@ -81,7 +83,7 @@ typedef struct {
   uint32_t threads_per_cta;    /* persistent DFS CTA size: 0 = default, else 128/256/512          */
   uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece: 0 = default, 1,2,4,8     */
   uint32_t ctas_per_sm;        /* 0 = as many as fit                                              */
-  uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 1)          */
+  uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 0)          */
   uint32_t result_on_device;   /* 1 = keep the result in device memory (no D2H copy)              */
   uint32_t collect_times;      /* 1 = record CUDA events around the kernels (stats.ms_*)          */
   uint32_t reserved_u;
@@ -179,6 +181,69 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
  * be NULL). */
 fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,
                            const uint32_t** set_items, const uint32_t** supports, int* on_device);
+
+/*
+ * Launch-shape autotuner for the persistent DFS kernel (CTA size, 16-byte
+ * loads per lane, CTAs per SM, donation).  Mines db at minsup_abs once per
+ * candidate shape (twice, best time of the kernels by CUDA events), writes
+ * the fastest shape into opts (threads_per_cta, vec_per_lane, ctas_per_sm,
+ * donate) and its time into *best_ms (may be NULL).  Results are cached per
+ * (row stride, frequent items, minsup, rows).  The output of a mine never
+ * depends on the shape.  opts must come from fim_mine_opts_init; its other
+ * fields (class order ...) are used for the trial mines.
+ * Errors: as fim_mine.
+ */
+fim_status fim_autotune(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, float* best_ms);
+
+/*
+ * Batched mining plan: every prefix class of (db, minsup_abs) fused into the
+ * device work of one mine (pair kernel, level-2 queue build, ONE persistent
+ * DFS launch over all classes in queue order, ordered by the estimate when
+ * one exists) and captured once in a CUDA graph.  Creation runs one eager
+ * mine to size the output and the DFS stack, then captures; the plan owns
+ * its buffers.  The plan uses db's stream, or a private stream when db was
+ * built on the legacy default stream (fim_plan_stream returns it).
+ * fim_plan_launch enqueues one replay (asynchronous); fim_plan_result waits
+ * for the last replay and returns its itemsets (host or device per
+ * opts->result_on_device; opts may be NULL; opts->stats receives counters).
+ * db must outlive the plan and stay unchanged.
+ * Errors: as fim_mine; FIM_ERR_INVALID for a result before any launch.
+ */
+fim_status fim_plan_create(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_plan** out);
+fim_status fim_plan_launch(fim_plan* plan);
+fim_status fim_plan_result(fim_plan* plan, fim_mine_opts* opts, fim_result** out);
+fim_status fim_plan_stream(const fim_plan* plan, void** cuda_stream);
+void fim_plan_free(fim_plan* plan);
+
+/*
+ * Serving: a request loop that admits mining jobs on different databases and
+ * minsups.  fim_server_create starts `slots` worker threads, each with its own
+ * CUDA stream on the current device; hbm_budget_bytes bounds the summed
+ * footprint estimate of the jobs in flight (0 = 80% of the free memory);
+ * ctas_per_sm caps each job's persistent CTAs per SM (0 = 1) so that
+ * concurrent jobs share the SMs.  fim_server_submit copies the host CSR
+ * database (as fim_build_vertical_db) and queues the job; jobs are admitted
+ * in arrival order when a slot is free and their footprint fits the budget
+ * left (a job larger than the budget runs alone), then run build (prefilter =
+ * minsup), the sample estimate when sample_rate > 0, and the mine; the
+ * database stays resident on the device until the result is copied out.
+ * fim_server_wait blocks until the job is done and returns its result (owned
+ * by the caller: fim_result_free), the latency from submission and the
+ * service time (either pointer may be NULL); each id can be waited once.
+ * The result of a job does not depend on the other jobs in flight.
+ * fim_server_free stops the workers after the jobs in flight; queued jobs
+ * that never started are dropped.
+ * Errors: FIM_ERR_INVALID (bad arguments, unknown id), FIM_ERR_CUDA, and the
+ * errors of the job's own build / estimate / mine (returned by wait).
+ */
+fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t ctas_per_sm, fim_server** out);
+fim_status fim_server_submit(fim_server* srv, const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D,
+                             uint32_t N, uint32_t minsup_abs, double sample_rate, uint64_t* job_id);
+fim_status fim_server_wait(fim_server* srv, uint64_t job_id, fim_result** out, double* latency_s,
+                           double* service_s);
+fim_status fim_server_stats(fim_server* srv, uint64_t* in_use_bytes, uint32_t* in_flight, uint32_t* peak_in_flight,
+                            uint64_t* queued);
+void fim_server_free(fim_server* srv);
 
 /*
  * Frequent pairs without allocation.  The thesis has no counterpart to this

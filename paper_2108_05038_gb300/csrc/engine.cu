@@ -1,0 +1,248 @@
+// Mining engine: one Eclat run over a set of frequent bitmap rows.
+//
+// prepare  - geometry of the persistent DFS, row lists on the device, fixed buffers
+// alloc    - output and DFS-stack buffers (grow when a run overflows them)
+// launch   - pair kernel, level-2 compaction and queue, persistent DFS: device
+//            work only, so the same sequence can be captured in a CUDA graph
+// finish   - read the control block, check the device-side error bits
+#include <algorithm>
+#include <cstring>
+
+#include "fim_internal.cuh"
+
+namespace fim {
+
+static uint32_t clamp_threads(uint32_t t) { return (t == 128 || t == 256 || t == 512) ? t : 256u; }
+static uint32_t clamp_vec(uint32_t v) { return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 4u; }
+static constexpr uint64_t kMaxCap = 0xfffffff0ull;
+
+fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg, EnginePlan* ep) {
+  cudaStream_t st = ws.stream;
+  *ep = EnginePlan{};
+  const uint32_t n1 = in.n1;
+  ep->n1 = n1;
+  ep->minsup = in.minsup;
+  ep->stride = in.stride;
+  ep->bytes_per_row_alg = in.bytes_per_row_alg;
+  ep->bits = in.bits;
+  ep->d_rank_item = in.d_rank_item;
+  ep->num_sms = db->num_sms;
+  ep->donate = cfg.donate;
+  ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
+  ep->fixed_capacity = cfg.fixed_capacity;
+  ep->cap_sets = cfg.cap_sets ? cfg.cap_sets : std::max<uint64_t>((uint64_t)1 << 18, 8ull * n1 + 64);
+  ep->cap_items = cfg.cap_items ? cfg.cap_items : ep->cap_sets * 6;
+  ep->cap_sets = std::min(ep->cap_sets, kMaxCap);
+  ep->cap_items = std::min(ep->cap_items, kMaxCap);
+  FIM_TRY(ws_get(ws, WS_CTRL, 1, &ep->d_ctrl));
+  if (n1 == 0) return FIM_OK;
+
+  // row lists (pinned-staged uploads unless the caller already has them on the device)
+  ep->d_frows = in.d_frows;
+  ep->d_rsupp = in.d_row_supp;
+  ep->d_order = in.identity_order ? db->d_iota : nullptr;
+  auto upload = [&](int slot, const std::vector<uint32_t>& v, const uint32_t** dst) -> fim_status {
+    uint32_t* d = nullptr;
+    void* h = nullptr;
+    FIM_TRY(ws_get(ws, slot, n1, &d));
+    FIM_TRY(stage_get(db, n1 * 4ull, &h));
+    std::memcpy(h, v.data(), n1 * 4ull);
+    FIM_CUDA(cudaMemcpyAsync(d, h, n1 * 4ull, cudaMemcpyHostToDevice, st));
+    *dst = d;
+    return FIM_OK;
+  };
+  if (!ep->d_frows) FIM_TRY(upload(WS_FROWS, in.frows, &ep->d_frows));
+  if (!ep->d_rsupp) FIM_TRY(upload(WS_ROWSUPP, in.row_supp, &ep->d_rsupp));
+  if (!ep->d_order) FIM_TRY(upload(WS_ROWORDER, in.row_order, &ep->d_order));
+
+  ep->npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
+  FIM_TRY(ws_get(ws, WS_C2, (size_t)n1 * n1, &ep->d_C2));
+  FIM_TRY(ws_get(ws, WS_SCNT, n1, &ep->d_scnt));
+  FIM_TRY(ws_get(ws, WS_SOFF, 2ull * (n1 + 1), &ep->d_soff));
+  FIM_TRY(ws_get(ws, WS_SITEMS, ep->npairs_max + 1, &ep->d_sitems));
+  FIM_TRY(ws_get(ws, WS_ENTRIES, ep->npairs_max + 1, &ep->d_entries));
+  ep->d_eoff = ep->d_soff + (n1 + 1);
+
+  // persistent DFS geometry: itemsets are no longer than the longest transaction
+  ep->L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
+  ep->maxd_full = std::max<uint32_t>(1, ep->L - 2);
+  ep->maxd = std::min<uint32_t>(ep->maxd_full, kDfsDepthHint);  // grown (and the run repeated) on demand
+  ep->threads = clamp_threads(cfg.threads);
+  ep->vec = clamp_vec(cfg.vec);
+  ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full);
+  ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem);
+  int occ = 0;
+  FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, &occ));
+  if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
+  const uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
+  ep->grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);
+  ep->per_depth = dfs_arena_depth_words(in.stride, n1);
+  ep->pool_slots = cfg.donate ? std::max<uint32_t>(8, ep->grid) : 0;
+  ep->pool_slot_words = dfs_pool_slot_words(in.stride, ep->L, n1);
+  if (ep->pool_slots) FIM_TRY(ws_get(ws, WS_POOL, ep->pool_slot_words * ep->pool_slots, &ep->d_pool));
+  if (cfg.collect_times)
+    for (auto& e : ep->ev) FIM_CUDA(cudaEventCreate(&e));
+  return FIM_OK;
+}
+
+fim_status engine_alloc(Workspace& ws, EnginePlan* ep) {
+  FIM_TRY(ws_get(ws, WS_OUT_OFF, ep->cap_sets + 1, &ep->d_off));
+  FIM_TRY(ws_get(ws, WS_OUT_ITEMS, std::max<uint64_t>(1, ep->cap_items), &ep->d_items));
+  FIM_TRY(ws_get(ws, WS_OUT_SUPP, std::max<uint64_t>(1, ep->cap_sets), &ep->d_supp));
+  if (ep->n1 >= 3) FIM_TRY(ws_get(ws, WS_ARENA, ep->per_depth * (ep->maxd + 1) * ep->grid, &ep->d_arena));
+  return FIM_OK;
+}
+
+cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
+  cudaError_t ce = cudaMemsetAsync(ep.d_ctrl, 0, sizeof(DevCtrl), st);
+  if (ce != cudaSuccess || ep.n1 == 0) return ce;
+  if (ep.pool_slots) {
+    ce = launch_pool_init(ep.d_pool, ep.pool_slots, ep.pool_slot_words, st);
+    if (ce != cudaSuccess) return ce;
+  }
+  if (ep.ev[0]) cudaEventRecord(ep.ev[0], st);
+  uint32_t ksplit = 0;
+  PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
+  ce = launch_pair_counts(pl, ep.num_sms, st, &ksplit);
+  if (ce != cudaSuccess) return ce;
+  if (ep.ev[1]) cudaEventRecord(ep.ev[1], st);
+  LevelLaunch ll{ep.d_C2, ep.n1, ep.minsup, ep.d_frows, ep.d_rsupp, ep.d_rank_item, ep.d_order, ep.d_scnt,
+                 ep.d_soff, ep.d_eoff, ep.d_sitems, ep.d_entries, ep.d_off, ep.d_items, ep.d_supp,
+                 ep.cap_sets, ep.cap_items, ep.d_ctrl};
+  ce = launch_level2(ll, st);
+  if (ce != cudaSuccess) return ce;
+  if (ep.ev[2]) cudaEventRecord(ep.ev[2], st);
+  if (ep.n1 >= 3) {
+    DfsLaunch dl{};
+    dl.bits = ep.bits;
+    dl.stride = ep.stride;
+    dl.frows = ep.d_frows;
+    dl.n1 = ep.n1;
+    dl.minsup = ep.minsup;
+    dl.rank_item = ep.d_rank_item;
+    dl.soff = ep.d_soff;
+    dl.scnt = ep.d_scnt;
+    dl.sitems = ep.d_sitems;
+    dl.entries = ep.d_entries;
+    dl.arena = ep.d_arena;
+    dl.arena_cta_words = ep.per_depth * (ep.maxd + 1);
+    dl.maxd = ep.maxd;
+    dl.pool = ep.d_pool;
+    dl.pool_slots = ep.pool_slots;
+    dl.pool_slot_words = ep.pool_slot_words;
+    dl.out_off = ep.d_off;
+    dl.out_items = ep.d_items;
+    dl.out_supp = ep.d_supp;
+    dl.cap_sets = ep.cap_sets;
+    dl.cap_items = ep.cap_items;
+    dl.ctrl = ep.d_ctrl;
+    dl.spin_limit = ep.spin_limit;
+    dl.donate = ep.donate;
+    ce = launch_dfs(dl, ep.grid, ep.threads, ep.vec, ep.smem, ep.psmem, ep.L, st);
+    if (ce != cudaSuccess) return ce;
+  }
+  if (ep.ev[3]) cudaEventRecord(ep.ev[3], st);
+  return cudaSuccess;
+}
+
+void engine_release_events(EnginePlan* ep) {
+  for (auto& e : ep->ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+}
+
+fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutput* out, fim_mine_stats* stats,
+                         bool* retry) {
+  *retry = false;
+  *out = EngineOutput{};
+  void* hstage = nullptr;
+  FIM_TRY(stage_get(db, sizeof(DevCtrl), &hstage));
+  FIM_CUDA(cudaMemcpyAsync(hstage, ep->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+  FIM_CUDA(cudaStreamSynchronize(st));
+  db->stage_used = 0;
+  DevCtrl h;
+  std::memcpy(&h, hstage, sizeof(DevCtrl));
+  out->ctrl = h;
+  if (h.err & DEV_ERR_TIMEOUT) return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
+  if (h.err & DEV_ERR_DEPTH) {
+    if (ep->maxd >= ep->maxd_full) return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
+    ep->maxd = ep->maxd_full;  // deeper than the first stack: repeat with the full bound
+    *retry = true;
+    return FIM_OK;
+  }
+  if (h.sets_total > ep->cap_sets || h.items_total > ep->cap_items) {
+    if (h.sets_total > kMaxCap || h.items_total > kMaxCap)
+      return fail(FIM_ERR_OUTPUT_OVERFLOW, "result exceeds 2^32 sets or items");
+    if (ep->fixed_capacity) return fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity exceeded");
+    ep->cap_sets = std::min<uint64_t>(kMaxCap, h.sets_total + h.sets_total / 16 + 16);
+    ep->cap_items = std::min<uint64_t>(kMaxCap, h.items_total + h.items_total / 16 + 16);
+    *retry = true;
+    return FIM_OK;
+  }
+  if (ep->d_off) {
+    void* hfin = nullptr;
+    FIM_TRY(stage_get(db, sizeof(uint64_t), &hfin));
+    *static_cast<uint64_t*>(hfin) = h.items_total;
+    FIM_CUDA(cudaMemcpyAsync(ep->d_off + h.sets_total, hfin, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  }
+  out->n_sets = h.sets_total;
+  out->n_items = h.items_total;
+  out->d_off = ep->d_off;
+  out->d_items = ep->d_items;
+  out->d_supp = ep->d_supp;
+  if (stats) {
+    const uint64_t rb = ep->bytes_per_row_alg;
+    const uint32_t n1 = ep->n1;
+    stats->n_frequent_items = n1;
+    stats->words_per_row = ep->stride;
+    stats->n_frequent = h.sets_total;
+    stats->n_items_out = h.items_total;
+    stats->max_len = h.max_len;
+    stats->n_pair_intersections = ep->npairs_max;
+    stats->n_intersections = ep->npairs_max + h.n_intersections;
+    stats->n_classes = h.n_nodes;
+    stats->n_queue_entries = h.n_entries;
+    stats->n_donations = h.n_donations;
+    // sibling operand per intersection + one prefix read per class node + materialised prefixes
+    stats->bytes_pair_kernel = ep->npairs_max * rb + (uint64_t)(n1 > 0 ? n1 - 1 : 0) * rb;
+    stats->bytes_dfs_kernel = h.n_intersections * rb + h.n_nodes * rb + h.n_frames * rb;
+    stats->bytes_algorithmic = stats->bytes_pair_kernel + stats->bytes_dfs_kernel;
+    stats->grid_ctas = n1 >= 3 ? ep->grid : 0;
+    stats->threads_per_cta = ep->threads;
+    stats->vec_per_lane = ep->vec;
+    if (ep->ev[0] && n1 > 0) {
+      cudaEventElapsedTime(&stats->ms_pair_kernel, ep->ev[0], ep->ev[1]);
+      cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);
+      cudaEventElapsedTime(&stats->ms_device_total, ep->ev[0], ep->ev[3]);
+    }
+  }
+  return FIM_OK;
+}
+
+fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg, EngineOutput* out,
+                       fim_mine_stats* stats, EnginePlan* plan_out) {
+  EnginePlan ep;
+  fim_status s = engine_prepare(db, ws, in, cfg, &ep);
+  for (int attempt = 0; s == FIM_OK && attempt < 4; ++attempt) {
+    if ((s = engine_alloc(ws, &ep)) != FIM_OK) break;
+    cudaError_t ce = engine_launch(ep, ws.stream);
+    if (ce != cudaSuccess) {
+      s = cuda_fail(ce, "mining kernels");
+      break;
+    }
+    bool retry = false;
+    s = engine_finish(db, ws.stream, &ep, out, stats, &retry);
+    if (s != FIM_OK || !retry) break;
+    if (attempt == 3) s = fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity still exceeded after regrowth");
+  }
+  if (plan_out && s == FIM_OK) {
+    *plan_out = ep;
+    for (auto& e : ep.ev) e = nullptr;  // events belong to the caller's copy now
+  }
+  engine_release_events(&ep);
+  return s;
+}
+
+}  // namespace fim

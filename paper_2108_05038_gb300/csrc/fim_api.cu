@@ -93,23 +93,21 @@ static void pinned_release(void* p, size_t cap) {
   g_pinned_free.emplace_back(cap, p);
 }
 
-}  // namespace fim
-
 // A region of the database's pinned staging buffer, valid until the next
 // synchronisation of its stream (callers reset the bump pointer after syncing).
-static fim_status stage_get(fim_db* db, size_t bytes, void** out) {
+fim_status stage_get(fim_db* db, size_t bytes, void** out) {
   bytes = (bytes + 63) & ~(size_t)63;
   if (db->stage_used + bytes > db->stage_cap) {
     FIM_CUDA(cudaStreamSynchronize(db->stream));
     db->stage_used = 0;
     if (bytes > db->stage_cap) {
-      fim::pinned_release(db->stage, db->stage_cap);
+      pinned_release(db->stage, db->stage_cap);
       db->stage = nullptr;
       db->stage_cap = 0;
       void* p = nullptr;
       size_t cap = 0;
-      cudaError_t e = fim::pinned_acquire(std::max<size_t>(bytes, 1 << 16), &p, &cap);
-      if (e != cudaSuccess) return fim::cuda_fail(e, "pinned staging allocation");
+      cudaError_t e = pinned_acquire(std::max<size_t>(bytes, 1 << 16), &p, &cap);
+      if (e != cudaSuccess) return cuda_fail(e, "pinned staging allocation");
       db->stage = static_cast<uint8_t*>(p);
       db->stage_cap = cap;
     }
@@ -119,13 +117,11 @@ static fim_status stage_get(fim_db* db, size_t bytes, void** out) {
   return FIM_OK;
 }
 
-static fim_status stream_sync(fim_db* db) {
+fim_status stream_sync(fim_db* db) {
   FIM_CUDA(cudaStreamSynchronize(db->stream));
   db->stage_used = 0;
   return FIM_OK;
 }
-
-namespace fim {
 
 // ---------------------------------------------------------------------------
 // workspace
@@ -162,254 +158,10 @@ void Workspace::release() {
   bytes = 0;
 }
 
-template <typename T>
-static fim_status ws_get(Workspace& ws, int slot, size_t count, T** out) {
-  void* p = nullptr;
-  FIM_TRY(ws.get(slot, count * sizeof(T), &p));
-  *out = static_cast<T*>(p);
-  return FIM_OK;
-}
 
 // ---------------------------------------------------------------------------
 // mining engine
 
-static uint32_t clamp_threads(uint32_t t) {
-  if (t == 128 || t == 256 || t == 512) return t;
-  return 256;
-}
-static uint32_t clamp_vec(uint32_t v) {
-  if (v == 1 || v == 2 || v == 4 || v == 8) return v;
-  return 4;
-}
-
-fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg,
-                       EngineOutput* out, fim_mine_stats* stats) {
-  cudaStream_t st = ws.stream;
-  const uint32_t n1 = in.n1;
-  *out = EngineOutput{};
-  if (stats) {
-    stats->n_frequent_items = n1;
-    stats->words_per_row = in.stride;
-  }
-  DevCtrl* d_ctrl = nullptr;
-  FIM_TRY(ws_get(ws, WS_CTRL, 1, &d_ctrl));
-  FIM_CUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(DevCtrl), st));
-
-  uint64_t cap_sets = cfg.cap_sets, cap_items = cfg.cap_items;
-  if (cap_sets == 0) cap_sets = std::max<uint64_t>((uint64_t)1 << 18, 8ull * n1 + 64);
-  if (cap_items == 0) cap_items = cap_sets * 6;
-  const uint64_t kMaxCap = 0xfffffff0ull;
-  cap_sets = std::min(cap_sets, kMaxCap);
-  cap_items = std::min(cap_items, kMaxCap);
-
-  if (n1 == 0) {
-    uint64_t* d_off = nullptr;
-    FIM_TRY(ws_get(ws, WS_OUT_OFF, 1, &d_off));
-    FIM_CUDA(cudaMemsetAsync(d_off, 0, sizeof(uint64_t), st));
-    out->d_off = d_off;
-    FIM_TRY(ws_get(ws, WS_OUT_ITEMS, 1, &out->d_items));
-    FIM_TRY(ws_get(ws, WS_OUT_SUPP, 1, &out->d_supp));
-    return FIM_OK;
-  }
-
-  // device copies of the row lists (uploaded through pinned staging unless given)
-  const uint32_t *d_frows = in.d_frows, *d_rsupp = in.d_row_supp, *d_order = in.identity_order ? db->d_iota : nullptr;
-  auto upload = [&](int slot, const std::vector<uint32_t>& v, const uint32_t** dst) -> fim_status {
-    uint32_t* d = nullptr;
-    void* h = nullptr;
-    FIM_TRY(ws_get(ws, slot, n1, &d));
-    FIM_TRY(stage_get(db, n1 * 4ull, &h));
-    std::memcpy(h, v.data(), n1 * 4ull);
-    FIM_CUDA(cudaMemcpyAsync(d, h, n1 * 4ull, cudaMemcpyHostToDevice, st));
-    *dst = d;
-    return FIM_OK;
-  };
-  if (!d_frows) FIM_TRY(upload(WS_FROWS, in.frows, &d_frows));
-  if (!d_rsupp) FIM_TRY(upload(WS_ROWSUPP, in.row_supp, &d_rsupp));
-  if (!d_order) FIM_TRY(upload(WS_ROWORDER, in.row_order, &d_order));
-
-  const uint64_t npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
-  uint32_t *d_C2 = nullptr, *d_scnt = nullptr, *d_soff = nullptr, *d_sitems = nullptr;
-  uint2* d_entries = nullptr;
-  FIM_TRY(ws_get(ws, WS_C2, (size_t)n1 * n1, &d_C2));
-  FIM_TRY(ws_get(ws, WS_SCNT, n1, &d_scnt));
-  FIM_TRY(ws_get(ws, WS_SOFF, 2ull * (n1 + 1), &d_soff));
-  FIM_TRY(ws_get(ws, WS_SITEMS, npairs_max + 1, &d_sitems));
-  FIM_TRY(ws_get(ws, WS_ENTRIES, npairs_max + 1, &d_entries));
-  uint32_t* d_eoff = d_soff + (n1 + 1);
-
-  // DFS geometry
-  const uint32_t L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
-  const uint32_t maxd_full = std::max<uint32_t>(1, L - 2);
-  uint32_t maxd = std::min<uint32_t>(maxd_full, kDfsDepthHint);  // grown (and the mine redone) on overflow
-  const uint32_t threads = clamp_threads(cfg.threads);
-  const uint32_t vec = clamp_vec(cfg.vec);
-  const bool psmem = dfs_prefix_fits(in.stride, db->smem_optin, L, maxd_full);
-  const size_t smem = dfs_smem_bytes(in.stride, L, maxd_full, psmem);
-  int occ = 0;
-  FIM_CUDA(dfs_max_ctas_per_sm(threads, vec, smem, psmem, &occ));
-  if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
-  uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
-  const uint32_t grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);
-  const uint64_t per_depth = dfs_arena_depth_words(in.stride, n1);
-  const uint32_t pool_slots = cfg.donate ? std::max<uint32_t>(8, grid) : 0;
-  const uint64_t pool_slot_words = dfs_pool_slot_words(in.stride, L, n1);
-  uint32_t* d_pool = nullptr;
-  if (pool_slots) FIM_TRY(ws_get(ws, WS_POOL, pool_slot_words * pool_slots, &d_pool));
-
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  if (cfg.collect_times) {
-    for (auto& e : ev) FIM_CUDA(cudaEventCreate(&e));
-  }
-  auto destroy_events = [&]() {
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-  };
-
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    uint64_t *d_off = nullptr;
-    uint32_t *d_items = nullptr, *d_supp = nullptr, *d_arena = nullptr;
-    const uint64_t arena_cta_words = per_depth * (maxd + 1);
-    fim_status s;
-    if ((s = ws_get(ws, WS_OUT_OFF, cap_sets + 1, &d_off)) != FIM_OK ||
-        (s = ws_get(ws, WS_OUT_ITEMS, cap_items, &d_items)) != FIM_OK ||
-        (s = ws_get(ws, WS_OUT_SUPP, cap_sets, &d_supp)) != FIM_OK ||
-        (s = ws_get(ws, WS_ARENA, arena_cta_words * grid, &d_arena)) != FIM_OK) {
-      destroy_events();
-      return s;
-    }
-    cudaError_t ce = cudaSuccess;
-    if (attempt > 0) ce = cudaMemsetAsync(d_ctrl, 0, sizeof(DevCtrl), st);
-    if (ce == cudaSuccess && pool_slots) ce = launch_pool_init(d_pool, pool_slots, pool_slot_words, st);
-    if (ev[0]) cudaEventRecord(ev[0], st);
-    uint32_t ksplit = 0;
-    if (ce == cudaSuccess) {
-      PairLaunch pl{in.bits, in.stride, d_frows, n1, d_C2, 0};
-      ce = launch_pair_counts(pl, db->num_sms, st, &ksplit);
-    }
-    if (ev[1]) cudaEventRecord(ev[1], st);
-    if (ce == cudaSuccess) {
-      LevelLaunch ll{d_C2, n1, in.minsup, d_frows, d_rsupp, in.d_rank_item, d_order, d_scnt, d_soff, d_eoff,
-                     d_sitems, d_entries, d_off, d_items, d_supp, cap_sets, cap_items, d_ctrl};
-      ce = launch_level2(ll, st);
-    }
-    if (ev[2]) cudaEventRecord(ev[2], st);
-    if (ce == cudaSuccess && n1 >= 3) {
-      DfsLaunch dl{};
-      dl.bits = in.bits;
-      dl.stride = in.stride;
-      dl.frows = d_frows;
-      dl.n1 = n1;
-      dl.minsup = in.minsup;
-      dl.rank_item = in.d_rank_item;
-      dl.soff = d_soff;
-      dl.scnt = d_scnt;
-      dl.sitems = d_sitems;
-      dl.entries = d_entries;
-      dl.arena = d_arena;
-      dl.arena_cta_words = arena_cta_words;
-      dl.maxd = maxd;
-      dl.pool = d_pool;
-      dl.pool_slots = pool_slots;
-      dl.pool_slot_words = pool_slot_words;
-      dl.out_off = d_off;
-      dl.out_items = d_items;
-      dl.out_supp = d_supp;
-      dl.cap_sets = cap_sets;
-      dl.cap_items = cap_items;
-      dl.ctrl = d_ctrl;
-      dl.spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
-      dl.donate = cfg.donate;
-      ce = launch_dfs(dl, grid, threads, vec, smem, psmem, L, st);
-    }
-    if (ev[3]) cudaEventRecord(ev[3], st);
-    if (ce != cudaSuccess) {
-      destroy_events();
-      return cuda_fail(ce, "mining kernels");
-    }
-    DevCtrl h{};
-    void* hstage = nullptr;
-    if ((s = stage_get(db, sizeof(DevCtrl), &hstage)) != FIM_OK) {
-      destroy_events();
-      return s;
-    }
-    ce = cudaMemcpyAsync(hstage, d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) {
-      destroy_events();
-      return cuda_fail(ce, "mining kernels (sync)");
-    }
-    std::memcpy(&h, hstage, sizeof(DevCtrl));
-    db->stage_used = 0;
-    if (h.err & DEV_ERR_TIMEOUT) {
-      destroy_events();
-      return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
-    }
-    if (h.err & DEV_ERR_DEPTH) {
-      if (maxd >= maxd_full) {
-        destroy_events();
-        return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
-      }
-      maxd = maxd_full;  // deeper than the first arena: redo with the full bound
-      continue;
-    }
-    const bool overflow = h.sets_total > cap_sets || h.items_total > cap_items;
-    if (overflow) {
-      if (cfg.fixed_capacity || attempt == 3) {
-        out->ctrl = h;
-        destroy_events();
-        set_error("output capacity exceeded");
-        return FIM_ERR_OUTPUT_OVERFLOW;
-      }
-      cap_sets = std::min<uint64_t>(kMaxCap, h.sets_total + h.sets_total / 16 + 16);
-      cap_items = std::min<uint64_t>(kMaxCap, h.items_total + h.items_total / 16 + 16);
-      if (h.sets_total > kMaxCap || h.items_total > kMaxCap) {
-        out->ctrl = h;
-        destroy_events();
-        return fail(FIM_ERR_OUTPUT_OVERFLOW, "result exceeds 2^32 sets or items");
-      }
-      continue;
-    }
-    void* hfin = nullptr;
-    FIM_TRY(stage_get(db, sizeof(uint64_t), &hfin));
-    *static_cast<uint64_t*>(hfin) = h.items_total;
-    FIM_CUDA(cudaMemcpyAsync(d_off + h.sets_total, hfin, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    out->n_sets = h.sets_total;
-    out->n_items = h.items_total;
-    out->d_off = d_off;
-    out->d_items = d_items;
-    out->d_supp = d_supp;
-    out->ctrl = h;
-    if (stats) {
-      const uint64_t rb = in.bytes_per_row_alg;
-      stats->n_frequent = h.sets_total;
-      stats->n_items_out = h.items_total;
-      stats->max_len = h.max_len;
-      stats->n_pair_intersections = npairs_max;
-      stats->n_intersections = npairs_max + h.n_intersections;
-      stats->n_classes = h.n_nodes;
-      stats->n_queue_entries = h.n_entries;
-      stats->n_donations = h.n_donations;
-      // sibling operand per intersection + one prefix read per class + materialised prefixes
-      stats->bytes_pair_kernel = npairs_max * rb + (uint64_t)(n1 - 1) * rb;
-      stats->bytes_dfs_kernel = h.n_intersections * rb + h.n_nodes * rb + h.n_frames * rb;
-      stats->bytes_algorithmic = stats->bytes_pair_kernel + stats->bytes_dfs_kernel;
-      stats->grid_ctas = n1 >= 3 ? grid : 0;
-      stats->threads_per_cta = threads;
-      stats->vec_per_lane = vec;
-      if (cfg.collect_times) {
-        cudaStreamSynchronize(st);
-        cudaEventElapsedTime(&stats->ms_pair_kernel, ev[0], ev[1]);
-        cudaEventElapsedTime(&stats->ms_dfs_kernel, ev[2], ev[3]);
-        cudaEventElapsedTime(&stats->ms_device_total, ev[0], ev[3]);
-      }
-    }
-    destroy_events();
-    return FIM_OK;
-  }
-  destroy_events();
-  return fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity exceeded");
-}
 
 // ---------------------------------------------------------------------------
 // database build
@@ -583,6 +335,75 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->collect_times = o->collect_times != 0;
 }
 
+
+fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg) {
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (minsup_abs == 0) return fail(FIM_ERR_INVALID, "minsup 0 makes every subset frequent");
+  if (minsup_abs < db->prefilter) return fail(FIM_ERR_INVALID, "minsup below the prefilter support of the database");
+  if (opts && opts->struct_size != 0 && opts->struct_size != sizeof(fim_mine_opts))
+    return fail(FIM_ERR_INVALID, "fim_mine_opts.struct_size mismatch");
+  rows_for_minsup(db, minsup_abs, in);
+  in->bits = db->d_bits;
+  in->stride = db->stride;
+  in->bytes_per_row_alg = (uint32_t)(((uint64_t)db->D + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
+  in->d_rank_item = db->d_rank_item;
+  in->minsup = minsup_abs;
+  in->max_len_bound = db->max_tx_len;
+  if (in->n1) {
+    in->d_frows = db->d_iota + (db->n_rows - in->n1);  // frequent rows are the suffix
+    in->d_row_supp = db->d_supp + (db->n_rows - in->n1);
+  }
+  const uint32_t order = opts && opts->struct_size ? opts->class_order : (uint32_t)FIM_ORDER_ESTIMATE;
+  in->row_order.clear();
+  in->row_order.reserve(in->n1);
+  if (order == FIM_ORDER_ESTIMATE && db->has_estimate && in->n1) {
+    const uint32_t r0 = db->n_rows - in->n1;
+    for (uint32_t r : db->est_order)
+      if (r >= r0) in->row_order.push_back(r - r0);
+  } else {
+    for (uint32_t k = 0; k < in->n1; ++k) in->row_order.push_back(k);
+    in->identity_order = true;
+  }
+  engine_config_from_opts(opts, cfg);
+  return FIM_OK;
+}
+
+fim_status make_result(cudaStream_t st, const EngineOutput& eo, bool on_dev, fim_result** out) {
+  fim_result* res = new (std::nothrow) fim_result();
+  if (!res) return fail(FIM_ERR_OOM, "host allocation");
+  res->n_sets = eo.n_sets;
+  res->n_items = eo.n_items;
+  res->stream = st;
+  cudaError_t e = cudaSuccess;
+  if (on_dev) {
+    res->on_device = 1;
+    e = dev_malloc_async((void**)&res->d_off, (eo.n_sets + 1) * 8, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_items, std::max<uint64_t>(1, eo.n_items) * 4, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_supp, std::max<uint64_t>(1, eo.n_sets) * 4, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res->d_off, eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && eo.n_items)
+      e = cudaMemcpyAsync(res->d_items, eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && eo.n_sets)
+      e = cudaMemcpyAsync(res->d_supp, eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToDevice, st);
+  } else {
+    res->h_off.resize(eo.n_sets + 1);
+    res->h_items.resize(eo.n_items);
+    res->h_supp.resize(eo.n_sets);
+    e = cudaMemcpyAsync(res->h_off.data(), eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && eo.n_items)
+      e = cudaMemcpyAsync(res->h_items.data(), eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && eo.n_sets)
+      e = cudaMemcpyAsync(res->h_supp.data(), eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    fim_result_free(res);
+    return cuda_fail(e, "copying the result");
+  }
+  *out = res;
+  return FIM_OK;
+}
+
 }  // namespace fim
 
 using namespace fim;
@@ -594,7 +415,7 @@ void fim_mine_opts_init(fim_mine_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->struct_size = sizeof(fim_mine_opts);
   o->class_order = FIM_ORDER_ESTIMATE;
-  o->donate = 1;
+  o->donate = 0;
 }
 
 const char* fim_status_str(fim_status s) {
@@ -684,7 +505,7 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
   in.minsup = minsup_s;
   in.max_len_bound = db->max_tx_len;
   EngineConfig cfg;
-  cfg.donate = 1;
+  cfg.donate = 0;
   EngineOutput eo;
   FIM_TRY(engine_mine(db, db->ws, in, cfg, &eo, nullptr));
   std::vector<unsigned long long> tally(R, 0ull);
@@ -727,37 +548,9 @@ fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, ui
 fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_result** out) {
   if (!out) return fail(FIM_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
-  if (minsup_abs == 0) return fail(FIM_ERR_INVALID, "minsup 0 makes every subset frequent");
-  if (minsup_abs < db->prefilter)
-    return fail(FIM_ERR_INVALID, "minsup below the prefilter support of the database");
-  if (opts && opts->struct_size != 0 && opts->struct_size != sizeof(fim_mine_opts))
-    return fail(FIM_ERR_INVALID, "fim_mine_opts.struct_size mismatch");
   EngineInput in;
-  rows_for_minsup(db, minsup_abs, &in);
-  in.bits = db->d_bits;
-  in.stride = db->stride;
-  in.bytes_per_row_alg = (uint32_t)(((uint64_t)db->D + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
-  in.d_rank_item = db->d_rank_item;
-  in.minsup = minsup_abs;
-  if (in.n1) {
-    in.d_frows = db->d_iota + (db->n_rows - in.n1);  // frequent rows are the suffix
-    in.d_row_supp = db->d_supp + (db->n_rows - in.n1);
-  }
-  in.max_len_bound = db->max_tx_len;
-  const uint32_t order = opts && opts->struct_size ? opts->class_order : (uint32_t)FIM_ORDER_ESTIMATE;
-  in.row_order.clear();
-  in.row_order.reserve(in.n1);
-  if (order == FIM_ORDER_ESTIMATE && db->has_estimate && in.n1) {
-    const uint32_t r0 = db->n_rows - in.n1;
-    for (uint32_t r : db->est_order)
-      if (r >= r0) in.row_order.push_back(r - r0);
-  } else {
-    for (uint32_t k = 0; k < in.n1; ++k) in.row_order.push_back(k);
-    in.identity_order = true;
-  }
   EngineConfig cfg;
-  engine_config_from_opts(opts, &cfg);
+  FIM_TRY(mine_input(db, minsup_abs, opts, &in, &cfg));
   fim_mine_stats local_stats{};
   fim_mine_stats* stats = opts && opts->struct_size && opts->stats ? opts->stats : &local_stats;
   std::memset(stats, 0, sizeof(*stats));
@@ -768,41 +561,7 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
     opts->out_needed_items = eo.ctrl.items_total;
   }
   if (s != FIM_OK) return s;
-  fim_result* res = new (std::nothrow) fim_result();
-  if (!res) return fail(FIM_ERR_OOM, "host allocation");
-  res->n_sets = eo.n_sets;
-  res->n_items = eo.n_items;
-  res->stream = db->stream;
-  cudaStream_t st = db->stream;
-  const bool on_dev = opts && opts->struct_size && opts->result_on_device;
-  cudaError_t e = cudaSuccess;
-  if (on_dev) {
-    res->on_device = 1;
-    e = dev_malloc_async((void**)&res->d_off, (eo.n_sets + 1) * 8, st);
-    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_items, std::max<uint64_t>(1, eo.n_items) * 4, st);
-    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_supp, std::max<uint64_t>(1, eo.n_sets) * 4, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(res->d_off, eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && eo.n_items)
-      e = cudaMemcpyAsync(res->d_items, eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && eo.n_sets)
-      e = cudaMemcpyAsync(res->d_supp, eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToDevice, st);
-  } else {
-    res->h_off.resize(eo.n_sets + 1);
-    res->h_items.resize(eo.n_items);
-    res->h_supp.resize(eo.n_sets);
-    e = cudaMemcpyAsync(res->h_off.data(), eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && eo.n_items)
-      e = cudaMemcpyAsync(res->h_items.data(), eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && eo.n_sets)
-      e = cudaMemcpyAsync(res->h_supp.data(), eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  }
-  if (e != cudaSuccess) {
-    fim_result_free(res);
-    return cuda_fail(e, "copying the result");
-  }
-  *out = res;
-  return FIM_OK;
+  return make_result(db->stream, eo, opts && opts->struct_size && opts->result_on_device, out);
 }
 
 fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,

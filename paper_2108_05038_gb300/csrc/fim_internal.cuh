@@ -62,6 +62,15 @@ struct Workspace {
   void release();
 };
 
+template <typename T>
+inline fim_status ws_get(Workspace& ws, int slot, size_t count, T** out) {
+  void* p = nullptr;
+  fim_status st = ws.get(slot, count * sizeof(T), &p);
+  if (st != FIM_OK) return st;
+  *out = static_cast<T*>(p);
+  return FIM_OK;
+}
+
 enum WsSlot {
   WS_C2 = 0,
   WS_SCNT,
@@ -207,16 +216,60 @@ struct EngineConfig {
   uint32_t threads = 256;
   uint32_t vec = 4;
   uint32_t ctas_per_sm = 0;
-  uint32_t donate = 1;
-  uint32_t dynamic_order = 0;
+  uint32_t donate = 0;
   uint64_t spin_limit = 0;
   uint64_t cap_sets = 0, cap_items = 0;  // 0 = automatic
   bool fixed_capacity = false;
   bool collect_times = false;
 };
 
+// Everything one mining call launches, with its geometry and buffers.  The
+// buffers live in a Workspace (the db's, or a plan's own for graph replays).
+struct EnginePlan {
+  uint32_t n1 = 0, minsup = 1, stride = 0, bytes_per_row_alg = 0;
+  const uint32_t* bits = nullptr;
+  const uint32_t* d_rank_item = nullptr;
+  // DFS geometry
+  uint32_t L = 3, maxd = 1, maxd_full = 1, threads = 256, vec = 4, grid = 0, pool_slots = 0;
+  bool psmem = true;
+  size_t smem = 0;
+  uint64_t per_depth = 0, pool_slot_words = 0, npairs_max = 0;
+  uint64_t cap_sets = 0, cap_items = 0;
+  bool fixed_capacity = false;
+  uint32_t donate = 0;
+  uint64_t spin_limit = 0;
+  int num_sms = 0;
+  // buffers
+  DevCtrl* d_ctrl = nullptr;
+  const uint32_t *d_frows = nullptr, *d_rsupp = nullptr, *d_order = nullptr;
+  uint32_t *d_C2 = nullptr, *d_scnt = nullptr, *d_soff = nullptr, *d_eoff = nullptr, *d_sitems = nullptr;
+  uint2* d_entries = nullptr;
+  uint32_t *d_pool = nullptr, *d_arena = nullptr;
+  uint64_t* d_off = nullptr;
+  uint32_t *d_items = nullptr, *d_supp = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // optional kernel timing
+};
+
+// geometry, row lists and the capacity-independent buffers
+fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg, EnginePlan* ep);
+// capacity- and depth-dependent buffers (outputs, DFS arena)
+fim_status engine_alloc(Workspace& ws, EnginePlan* ep);
+// all device work of one mine: no host synchronisation, no allocation (graph capturable)
+cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st);
+// wait, read the control block, check errors; *retry = true when the buffers must grow and the
+// launch be repeated (output capacity or DFS depth)
+fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutput* out, fim_mine_stats* stats,
+                         bool* retry);
+// the EngineInput / EngineConfig of a fim_mine call (validation included)
+fim_status mine_input(fim_db* db, uint32_t minsup, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg);
+// fim_result from an engine output (device copy or host copy per on_device)
+fim_status make_result(cudaStream_t st, const EngineOutput& eo, bool on_device, fim_result** out);
 fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg,
-                       EngineOutput* out, fim_mine_stats* stats);
+                       EngineOutput* out, fim_mine_stats* stats, EnginePlan* plan_out = nullptr);
+void engine_release_events(EnginePlan* ep);
+// pinned staging of a database (see fim_api.cu)
+fim_status stage_get(fim_db* db, size_t bytes, void** out);
+fim_status stream_sync(fim_db* db);
 
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)

@@ -22,7 +22,9 @@ FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
 EXPORTED = [
     "fim_mine_opts_init", "fim_build_vertical_db", "fim_build_vertical_db_device", "fim_db_info", "fim_db_rows",
     "fim_estimate_class_costs", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
-    "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc",
+    "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
+    "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
+    "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free",
 ]
 
 
@@ -100,6 +102,29 @@ def load(build_if_stale: bool = True):
         lib.fim_estimate_sample_size.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.fim_mine.restype = i32
         lib.fim_mine.argtypes = [P, u32, ctypes.POINTER(MineOpts), PP]
+        lib.fim_autotune.restype = i32
+        lib.fim_autotune.argtypes = [P, u32, ctypes.POINTER(MineOpts), ctypes.POINTER(ctypes.c_float)]
+        lib.fim_plan_create.restype = i32
+        lib.fim_plan_create.argtypes = [P, u32, ctypes.POINTER(MineOpts), PP]
+        lib.fim_plan_launch.restype = i32
+        lib.fim_plan_launch.argtypes = [P]
+        lib.fim_plan_result.restype = i32
+        lib.fim_plan_result.argtypes = [P, ctypes.POINTER(MineOpts), PP]
+        lib.fim_plan_stream.restype = i32
+        lib.fim_plan_stream.argtypes = [P, PP]
+        lib.fim_plan_free.restype = None
+        lib.fim_plan_free.argtypes = [P]
+        lib.fim_server_create.restype = i32
+        lib.fim_server_create.argtypes = [u64, u32, u32, PP]
+        lib.fim_server_submit.restype = i32
+        lib.fim_server_submit.argtypes = [P, P, P, u32, u32, u32, dbl, ctypes.POINTER(u64)]
+        lib.fim_server_wait.restype = i32
+        lib.fim_server_wait.argtypes = [P, u64, PP, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        lib.fim_server_stats.restype = i32
+        lib.fim_server_stats.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32),
+                                         ctypes.POINTER(u64)]
+        lib.fim_server_free.restype = None
+        lib.fim_server_free.argtypes = [P]
         lib.fim_mine_pairs_noalloc.restype = i32
         lib.fim_mine_pairs_noalloc.argtypes = [P, u32, P, P, u64, ctypes.POINTER(u64)]
         lib.fim_result_view.restype = i32
@@ -226,9 +251,9 @@ class Database:
                                                              ctypes.byref(ms)), "fim_estimate_sample_size")
         return nfs.value, rows.value, ms.value
 
-    def mine(self, minsup: int, class_order: str = "estimate", threads_per_cta: int = 0, vec_per_lane: int = 0,
-             ctas_per_sm: int = 0, donate: bool = True, result_on_device: bool = False, collect_times: bool = False,
-             out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True):
+    def _opts(self, class_order="estimate", threads_per_cta=0, vec_per_lane=0, ctas_per_sm=0, donate=False,
+              result_on_device=False, collect_times=False, out_capacity_sets=0, out_capacity_items=0, spin_limit=0,
+              stats=True, shape=None):
         opts = MineOpts()
         self._lib.fim_mine_opts_init(ctypes.byref(opts))
         opts.class_order = {"estimate": FIM_ORDER_ESTIMATE, "uniform": FIM_ORDER_UNIFORM}[class_order]
@@ -236,6 +261,9 @@ class Database:
         opts.vec_per_lane = vec_per_lane
         opts.ctas_per_sm = ctas_per_sm
         opts.donate = 1 if donate else 0
+        if shape:
+            opts.threads_per_cta, opts.vec_per_lane = shape["threads_per_cta"], shape["vec_per_lane"]
+            opts.ctas_per_sm, opts.donate = shape["ctas_per_sm"], shape["donate"]
         opts.result_on_device = 1 if result_on_device else 0
         opts.collect_times = 1 if collect_times else 0
         opts.out_capacity_sets = out_capacity_sets
@@ -244,6 +272,30 @@ class Database:
         st = MineStats() if stats else None
         if st is not None:
             opts.stats = ctypes.pointer(st)
+        return opts, st
+
+    def autotune(self, minsup: int, class_order: str = "estimate"):
+        """fim_autotune: fastest DFS launch shape for this database and minsup (dict, plus its time)."""
+        opts, _ = self._opts(class_order=class_order, stats=False)
+        ms = ctypes.c_float()
+        _check(self._lib, self._lib.fim_autotune(self._h, minsup, ctypes.byref(opts), ctypes.byref(ms)), "fim_autotune")
+        return {"threads_per_cta": opts.threads_per_cta, "vec_per_lane": opts.vec_per_lane,
+                "ctas_per_sm": opts.ctas_per_sm, "donate": opts.donate}, ms.value
+
+    def plan(self, minsup: int, **kw):
+        """fim_plan_create: the mine captured in a CUDA graph (see Plan)."""
+        opts, _ = self._opts(**kw)
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.fim_plan_create(self._h, minsup, ctypes.byref(opts), ctypes.byref(h)),
+               "fim_plan_create")
+        return Plan(self._lib, h.value, self)
+
+    def mine(self, minsup: int, class_order: str = "estimate", threads_per_cta: int = 0, vec_per_lane: int = 0,
+             ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
+             out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
+             shape=None):
+        opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
+                              collect_times, out_capacity_sets, out_capacity_items, spin_limit, stats, shape)
         h = ctypes.c_void_p()
         status = self._lib.fim_mine(self._h, minsup, ctypes.byref(opts), ctypes.byref(h))
         if status == FIM_ERR_OUTPUT_OVERFLOW:
@@ -268,6 +320,39 @@ class Database:
     def free(self):
         if self._h:
             self._lib.fim_db_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A captured mine (fim_plan): launch() enqueues a graph replay, result() waits and returns it."""
+
+    def __init__(self, lib, handle, db):
+        self._lib, self._h, self._db = lib, handle, db
+
+    @property
+    def stream(self) -> int:
+        s = ctypes.c_void_p()
+        _check(self._lib, self._lib.fim_plan_stream(self._h, ctypes.byref(s)), "fim_plan_stream")
+        return s.value or 0
+
+    def launch(self):
+        _check(self._lib, self._lib.fim_plan_launch(self._h), "fim_plan_launch")
+
+    def result(self, result_on_device: bool = False):
+        opts, st = self._db._opts(result_on_device=result_on_device)
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.fim_plan_result(self._h, ctypes.byref(opts), ctypes.byref(h)), "fim_plan_result")
+        return Result(self._lib, h.value, st)
+
+    def free(self):
+        if self._h:
+            self._lib.fim_plan_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -304,3 +389,49 @@ def build_vertical_db_device(d_tx_offsets, d_tx_items, D: int, N: int, word_bits
 
 def status_str(status: int) -> str:
     return load().fim_status_str(status).decode()
+
+
+class Server:
+    """fim_server: continuous-batching request loop (submit / wait)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4, ctas_per_sm: int = 1):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.fim_server_create(hbm_budget_bytes, slots, ctas_per_sm, ctypes.byref(h)),
+               "fim_server_create")
+        self._h = h.value
+
+    def submit(self, tx_offsets, tx_items, N: int, minsup: int, sample_rate: float = 0.0) -> int:
+        off = np.ascontiguousarray(tx_offsets, dtype=np.uint32)
+        it = np.ascontiguousarray(tx_items, dtype=np.uint32)
+        if it.size == 0:
+            it = np.zeros(1, dtype=np.uint32)
+        jid = ctypes.c_uint64()
+        _check(self._lib, self._lib.fim_server_submit(self._h, off.ctypes.data, it.ctypes.data, off.size - 1, N,
+                                                      minsup, sample_rate, ctypes.byref(jid)), "fim_server_submit")
+        return jid.value
+
+    def wait(self, job_id: int):
+        """Returns (Result, latency seconds, service seconds)."""
+        h = ctypes.c_void_p()
+        lat, svc = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib, self._lib.fim_server_wait(self._h, job_id, ctypes.byref(h), ctypes.byref(lat),
+                                                    ctypes.byref(svc)), "fim_server_wait")
+        return Result(self._lib, h.value, None), lat.value, svc.value
+
+    def stats(self):
+        a, b, c, d = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        _check(self._lib, self._lib.fim_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                                     ctypes.byref(d)), "fim_server_stats")
+        return {"in_use_bytes": a.value, "in_flight": b.value, "peak_in_flight": c.value, "queued": d.value}
+
+    def free(self):
+        if self._h:
+            self._lib.fim_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

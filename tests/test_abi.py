@@ -43,7 +43,7 @@ def test_opts_struct_layout_matches_header():
     o = fim.MineOpts()
     lib.fim_mine_opts_init(ctypes.byref(o))
     assert o.struct_size == ctypes.sizeof(fim.MineOpts)
-    assert o.donate == 1 and o.class_order == fim.FIM_ORDER_ESTIMATE
+    assert o.donate == 0 and o.class_order == fim.FIM_ORDER_ESTIMATE
 
 
 def test_invalid_arguments_rejected_without_gpu():

@@ -1,0 +1,81 @@
+"""Serving: jobs on different databases and minsups admitted into a
+continuous-batching loop give, in the mix, exactly the result each gives alone
+(and the oracle's)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_05038_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2108_05038_gb300 import fim  # noqa: E402
+
+
+def odict(res):
+    so, si, sp = res
+    return {tuple(int(v) for v in si[so[k]:so[k + 1]]): int(sp[k]) for k in range(len(sp))}
+
+
+def small_requests(n):
+    reqs = synth.serving_requests(n, seed=77, D_range=(2_000, 40_000), N_range=(50, 600))
+    out = []
+    for r in reqs:
+        off, items = synth.request_db(r)
+        ms = max(2, r["minsup"])
+        out.append((off, items, r["N"], ms))
+    return out
+
+
+def test_mix_equals_alone_and_oracle():
+    reqs = small_requests(12)
+    alone = []
+    for off, items, N, ms in reqs:
+        db = fim.build_vertical_db(off, items, N, prefilter_minsup=ms)
+        alone.append(db.mine(ms).as_dict())
+        db.free()
+    srv = fim.Server(slots=4, ctas_per_sm=1)
+    ids = [srv.submit(off, items, N, ms, sample_rate=0.05) for off, items, N, ms in reqs]
+    for k, jid in enumerate(ids):
+        res, lat, svc = srv.wait(jid)
+        assert lat >= svc >= 0
+        got = res.as_dict()
+        assert got == alone[k]
+        off, items, N, ms = reqs[k]
+        assert got == odict(oracle.eclat(off, items, N, ms))
+    st = srv.stats()
+    assert st["in_flight"] == 0 and st["queued"] == 0 and st["peak_in_flight"] >= 1
+    srv.free()
+
+
+def test_budget_forces_one_at_a_time_and_stays_exact():
+    reqs = small_requests(5)
+    srv = fim.Server(hbm_budget_bytes=1, slots=4)  # every job exceeds the budget: they run alone
+    ids = [srv.submit(off, items, N, ms) for off, items, N, ms in reqs]
+    for k, jid in enumerate(ids):
+        res, _, _ = srv.wait(jid)
+        off, items, N, ms = reqs[k]
+        assert res.as_dict() == odict(oracle.eclat(off, items, N, ms))
+    assert srv.stats()["peak_in_flight"] == 1
+    srv.free()
+
+
+def test_bad_job_reports_error_others_unaffected():
+    reqs = small_requests(3)
+    srv = fim.Server(slots=2)
+    off, items, N, ms = reqs[0]
+    bad_items = items.copy()
+    bad_items[0] = N + 5  # item id out of range: the job fails with FIM_ERR_INVALID
+    bad = srv.submit(off, bad_items, N, ms)
+    good = srv.submit(*reqs[1])
+    with pytest.raises(fim.FimError) as e:
+        srv.wait(bad)
+    assert e.value.status == fim.FIM_ERR_INVALID
+    res, _, _ = srv.wait(good)
+    off, items, N, ms = reqs[1]
+    assert res.as_dict() == odict(oracle.eclat(off, items, N, ms))
+    srv.free()
