@@ -79,18 +79,22 @@ typedef struct {
 typedef struct {
   uint32_t struct_size;        /* set to sizeof(fim_mine_opts); 0 = treat as defaults            */
   uint32_t class_order;        /* fim_class_order                                                 */
-  uint32_t reserved0;          /* must be 0                                                       */
+  uint32_t dfs_mode;           /* 0 = expand one class node at a time, 1 = count all children of a
+                                  frame in one pass (fewer dependent steps on deep classes)         */
   uint32_t threads_per_cta;    /* persistent DFS CTA size: 0 = default, else 128/256/512          */
   uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece: 0 = default, 1,2,4,8     */
   uint32_t ctas_per_sm;        /* 0 = as many as fit                                              */
   uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 0)          */
   uint32_t result_on_device;   /* 1 = keep the result in device memory (no D2H copy)              */
   uint32_t collect_times;      /* 1 = record CUDA events around the kernels (stats.ms_*)          */
-  uint32_t reserved_u;
+  uint32_t reserved_u;         /* must be 0                                                       */
   uint64_t out_capacity_sets;  /* 0 = automatic (grow and retry); else fixed capacity             */
   uint64_t out_capacity_items; /* idem, total items over all sets                                 */
   uint64_t spin_limit;         /* idle-CTA polling rounds without progress before FIM_ERR_TIMEOUT;
                                   0 = default (a few s)                                            */
+  uint64_t max_itemsets;       /* 0 = no limit; else mining stops as soon as more itemsets are found
+                                  and the call returns FIM_ERR_OUTPUT_OVERFLOW (bounds the work of
+                                  requests whose output explodes combinatorially)                  */
   /* outputs */
   uint64_t out_needed_sets;    /* on FIM_ERR_OUTPUT_OVERFLOW: capacities that would have sufficed */
   uint64_t out_needed_items;
@@ -141,8 +145,10 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
  * Sample-based estimate of the relative size of every one-item-prefix class
  * [r | {g : g after r}] (Def. "Relative size of a PBEC", Sec. 2.4; estimate
  * of Sec. 6.2 used by Phase 2, Sec. 8.2).
- * A sample D_s of m = ceil(sample_rate * D) transactions is drawn with
- * replacement (Sec. 6.1): draw k takes transaction ((x_k >> 32) * D) >> 32,
+ * A sample D_s of m = max(ceil(sample_rate * D), min(D, m0)) transactions is
+ * drawn with replacement (Sec. 6.1), m0 = ceil(ln(2/0.05) / (2 * 0.05^2)) = 738
+ * being the size for which Theorem 6.1 bounds every relative support error
+ * by 0.05 with probability 0.95: draw k takes transaction ((x_k >> 32) * D) >> 32,
  * x_k = k-th output of SplitMix64 started at state `seed`.  D_s (kept items
  * only) is mined on the GPU at minsup_s = max(1, ceil(rel_minsup * m)) and
  * cost_out[r] = |{X in F_s : the lowest row of X is r}| / |F_s| (0 when F_s is
@@ -155,6 +161,20 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
  */
 fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
                                     double* cost_out, uint32_t* order_out);
+
+/* Cost measure of a class in the estimate. */
+typedef enum {
+  FIM_COST_ITEMSETS = 0,     /* #frequent itemsets of the sample in the class (the thesis's measure, Sec. 8.2) */
+  FIM_COST_INTERSECTIONS = 1 /* #AND+popcount intersections the bitmap Eclat performs for the class on the
+                                sample: its level-2 candidates (sample-frequent rows after it) plus every
+                                candidate of every node below it; proportional to its GPU work            */
+} fim_cost_kind;
+
+/* fim_estimate_class_costs with a choice of cost measure (fim_cost_kind);
+ * fim_estimate_class_costs is this call with FIM_COST_ITEMSETS.  Costs are
+ * shares of the total (sum 1 unless the sample has no frequent item). */
+fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
+                                       uint32_t cost_kind, double* cost_out, uint32_t* order_out);
 
 /* Number of frequent itemsets found in the sample by the last estimate. */
 fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, uint32_t* sample_rows,
@@ -184,10 +204,10 @@ fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64
 
 /*
  * Launch-shape autotuner for the persistent DFS kernel (CTA size, 16-byte
- * loads per lane, CTAs per SM, donation).  Mines db at minsup_abs once per
+ * loads per lane, CTAs per SM, donation, traversal mode).  Mines db at minsup_abs once per
  * candidate shape (twice, best time of the kernels by CUDA events), writes
  * the fastest shape into opts (threads_per_cta, vec_per_lane, ctas_per_sm,
- * donate) and its time into *best_ms (may be NULL).  Results are cached per
+ * donate, dfs_mode) and its time into *best_ms (may be NULL).  Results are cached per
  * (row stride, frequent items, minsup, rows).  The output of a mine never
  * depends on the shape.  opts must come from fim_mine_opts_init; its other
  * fields (class order ...) are used for the trial mines.
@@ -221,7 +241,8 @@ void fim_plan_free(fim_plan* plan);
  * CUDA stream on the current device; hbm_budget_bytes bounds the summed
  * footprint estimate of the jobs in flight (0 = 80% of the free memory);
  * ctas_per_sm caps each job's persistent CTAs per SM (0 = 1) so that
- * concurrent jobs share the SMs.  fim_server_submit copies the host CSR
+ * concurrent jobs share the SMs; max_itemsets (0 = none) stops a job whose
+ * output grows past it (FIM_ERR_OUTPUT_OVERFLOW from fim_server_wait).  fim_server_submit copies the host CSR
  * database (as fim_build_vertical_db) and queues the job; jobs are admitted
  * in arrival order when a slot is free and their footprint fits the budget
  * left (a job larger than the budget runs alone), then run build (prefilter =
@@ -236,7 +257,8 @@ void fim_plan_free(fim_plan* plan);
  * Errors: FIM_ERR_INVALID (bad arguments, unknown id), FIM_ERR_CUDA, and the
  * errors of the job's own build / estimate / mine (returned by wait).
  */
-fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t ctas_per_sm, fim_server** out);
+fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t ctas_per_sm, uint64_t max_itemsets,
+                             fim_server** out);
 fim_status fim_server_submit(fim_server* srv, const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D,
                              uint32_t N, uint32_t minsup_abs, double sample_rate, uint64_t* job_id);
 fim_status fim_server_wait(fim_server* srv, uint64_t job_id, fim_result** out, double* latency_s,

@@ -567,7 +567,8 @@ done:
 /* Item order of the classes: the kept items (support >= prefilter_minsup in  */
 /* the whole database; prefilter 0 keeps every item) sorted by ascending      */
 /* support, ties by ascending id -- the ascending-support order of Sec. B.4.2.*/
-/* Sample: m = ceil(rate * D) transactions drawn with replacement (Sec. 6.1); */
+/* Sample: m = max(ceil(rate * D), min(D, 738)) transactions drawn with      */
+/* replacement (Sec. 6.1; 738 = the Theorem 6.1 size for eps = delta = 0.05); */
 /* draw k uses the SplitMix64 output x_k = mix(seed + (k + 1) * gamma) (the   */
 /* k-th output of the stream started at state seed; Steele et al. 2014) and   */
 /* the transaction index ((x_k >> 32) * D) >> 32.  The sample keeps only the   */
@@ -615,9 +616,30 @@ int oracle_item_order(const uint32_t* off, const uint32_t* items, uint32_t D, ui
   return 0;
 }
 
-int oracle_class_costs(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t prefilter_minsup,
-                       double sample_rate, double rel_minsup, uint64_t seed, double* cost_out, uint32_t* order_out,
-                       uint32_t* n_kept_out, uint64_t* n_sample_fis) {
+/* the sample's itemsets sorted by (length, rank sequence): sets P u {e} with the
+ * same prefix P are then contiguous */
+static const uint32_t* g_rs_items;
+static const uint64_t* g_rs_off;
+static int cmp_len_seq(const void* a, const void* b) {
+  uint64_t i = *(const uint64_t*)a, j = *(const uint64_t*)b;
+  uint64_t ni = g_rs_off[i + 1] - g_rs_off[i], nj = g_rs_off[j + 1] - g_rs_off[j];
+  if (ni != nj) return ni < nj ? -1 : 1;
+  const uint32_t* x = g_rs_items + g_rs_off[i];
+  const uint32_t* y = g_rs_items + g_rs_off[j];
+  for (uint64_t k = 0; k < ni; ++k) if (x[k] != y[k]) return x[k] < y[k] ? -1 : 1;
+  return 0;
+}
+
+/* kind 0: cost = #sample FIs of the class (the thesis's measure, Sec. 8.2).
+ * kind 1: cost = #AND+popcount intersections the bitmap Eclat performs for the
+ * class on the sample, in the class order: the class of row r counts its
+ * level-2 candidates (the sample-frequent rows after r) plus, for every
+ * sample FI P whose first row is r, k_P (k_P - 1) / 2 where k_P is the number
+ * of sample FIs P u {e} with e after P's last row (each child P u {e_k} of P
+ * is intersected with the later survivors of P). */
+int oracle_class_costs_kind(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t prefilter_minsup,
+                            double sample_rate, double rel_minsup, uint64_t seed, int kind, double* cost_out,
+                            uint32_t* order_out, uint32_t* n_kept_out, uint64_t* n_sample_fis) {
   if (!(sample_rate > 0.0 && sample_rate <= 1.0) || !(rel_minsup >= 0.0 && rel_minsup <= 1.0) || D == 0) return -3;
   uint32_t* rank_item = (uint32_t*)malloc(sizeof(uint32_t) * (N ? N : 1));
   int32_t* rank_of = (int32_t*)malloc(sizeof(int32_t) * (N ? N : 1));
@@ -626,7 +648,11 @@ int oracle_class_costs(const uint32_t* off, const uint32_t* items, uint32_t D, u
   if (oracle_item_order(off, items, D, N, prefilter_minsup, rank_item, &nk) != 0) { free(rank_item); free(rank_of); return -1; }
   for (uint32_t it = 0; it < N; ++it) rank_of[it] = -1;
   for (uint32_t r = 0; r < nk; ++r) rank_of[rank_item[r]] = (int32_t)r;
-  uint64_t m = (uint64_t)ceil(sample_rate * (double)D);
+  /* m = max(ceil(rate D), min(D, m0)), m0 = the Theorem 6.1 size for eps = delta = 0.05 */
+  double m0 = ceil(log(2.0 / 0.05) / (2.0 * 0.05 * 0.05));
+  double md = ceil(sample_rate * (double)D);
+  if (md < m0) md = m0 < (double)D ? m0 : (double)D;
+  uint64_t m = (uint64_t)md;
   if (m < 1) m = 1;
   double ms = ceil(rel_minsup * (double)m);
   uint32_t minsup_s = ms < 1.0 ? 1u : (uint32_t)ms;
@@ -654,15 +680,59 @@ int oracle_class_costs(const uint32_t* off, const uint32_t* items, uint32_t D, u
   uint64_t* cnt = (uint64_t*)calloc(nk ? nk : 1, sizeof(uint64_t));
   uint32_t* ord = (uint32_t*)malloc(sizeof(uint32_t) * (nk ? nk : 1));
   if (!cnt || !ord) { free(cnt); free(ord); free(rank_item); free(rank_of); oracle_result_free(fs); return -1; }
-  for (uint64_t i = 0; i < fs->n_sets; ++i) {
-    int32_t best = INT32_MAX;
-    for (uint64_t q = fs->set_offsets[i]; q < fs->set_offsets[i + 1]; ++q) {
-      int32_t rr = rank_of[fs->set_items[q]];
-      if (rr < best) best = rr;
+  uint64_t total = 0;
+  if (kind == 0) {
+    for (uint64_t i = 0; i < fs->n_sets; ++i) {
+      int32_t best = INT32_MAX;
+      for (uint64_t q = fs->set_offsets[i]; q < fs->set_offsets[i + 1]; ++q) {
+        int32_t rr = rank_of[fs->set_items[q]];
+        if (rr < best) best = rr;
+      }
+      cnt[best]++;
     }
-    cnt[best]++;
+    total = fs->n_sets;
+  } else {
+    /* rewrite every set as its ascending rank sequence */
+    uint32_t* rs = (uint32_t*)malloc(sizeof(uint32_t) * (fs->n_items ? fs->n_items : 1));
+    uint64_t* idx = (uint64_t*)malloc(sizeof(uint64_t) * (fs->n_sets ? fs->n_sets : 1));
+    if (!rs || !idx) { free(rs); free(idx); free(cnt); free(ord); free(rank_item); free(rank_of); oracle_result_free(fs); return -1; }
+    for (uint64_t q = 0; q < fs->n_items; ++q) rs[q] = (uint32_t)rank_of[fs->set_items[q]];
+    for (uint64_t i = 0; i < fs->n_sets; ++i) {
+      qsort(rs + fs->set_offsets[i], fs->set_offsets[i + 1] - fs->set_offsets[i], sizeof(uint32_t), cmp_u32);
+      idx[i] = i;
+    }
+    g_rs_items = rs; g_rs_off = fs->set_offsets;
+    qsort(idx, fs->n_sets, sizeof(uint64_t), cmp_len_seq);
+    /* level 2: the singletons of the sample in rank order, each with the later ones as candidates */
+    uint64_t n1s = 0;
+    for (uint64_t i = 0; i < fs->n_sets; ++i) n1s += (fs->set_offsets[i + 1] - fs->set_offsets[i]) == 1;
+    uint64_t pos = 0;
+    for (uint64_t k = 0; k < fs->n_sets; ++k) {
+      uint64_t i = idx[k];
+      if (fs->set_offsets[i + 1] - fs->set_offsets[i] != 1) break;
+      cnt[rs[fs->set_offsets[i]]] += n1s - 1 - pos;
+      ++pos;
+    }
+    /* deeper: runs of sets (same length >= 2) sharing all but their last row */
+    uint64_t k = 0;
+    while (k < fs->n_sets) {
+      uint64_t i = idx[k];
+      uint64_t len = fs->set_offsets[i + 1] - fs->set_offsets[i];
+      if (len < 2) { ++k; continue; }
+      uint64_t run = 1;
+      while (k + run < fs->n_sets) {
+        uint64_t j = idx[k + run];
+        if (fs->set_offsets[j + 1] - fs->set_offsets[j] != len) break;
+        if (memcmp(rs + fs->set_offsets[i], rs + fs->set_offsets[j], sizeof(uint32_t) * (len - 1)) != 0) break;
+        ++run;
+      }
+      cnt[rs[fs->set_offsets[i]]] += run * (run - 1) / 2;
+      k += run;
+    }
+    for (uint32_t r = 0; r < nk; ++r) total += cnt[r];
+    free(rs); free(idx);
   }
-  for (uint32_t r = 0; r < nk; ++r) cost_out[r] = fs->n_sets ? (double)cnt[r] / (double)fs->n_sets : 0.0;
+  for (uint32_t r = 0; r < nk; ++r) cost_out[r] = total ? (double)cnt[r] / (double)total : 0.0;
   for (uint32_t r = 0; r < nk; ++r) ord[r] = r;
   g_cost = cost_out;
   qsort(ord, nk, sizeof(uint32_t), cmp_by_cost);
@@ -671,6 +741,13 @@ int oracle_class_costs(const uint32_t* off, const uint32_t* items, uint32_t D, u
   *n_sample_fis = fs->n_sets;
   free(cnt); free(ord); free(rank_item); free(rank_of); oracle_result_free(fs);
   return 0;
+}
+
+int oracle_class_costs(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t prefilter_minsup,
+                       double sample_rate, double rel_minsup, uint64_t seed, double* cost_out, uint32_t* order_out,
+                       uint32_t* n_kept_out, uint64_t* n_sample_fis) {
+  return oracle_class_costs_kind(off, items, D, N, prefilter_minsup, sample_rate, rel_minsup, seed, 0, cost_out,
+                                 order_out, n_kept_out, n_sample_fis);
 }
 
 /* SplitMix64 at a counter, exposed for pinning against the published stream. */

@@ -19,6 +19,9 @@
 // next unexpanded child of their shallowest open frame through a bounded
 // pool (the dynamic load balancing of the thesis's Phase 1, restated for a
 // device work queue); a counter of unfinished entries detects termination.
+#include <mutex>
+#include <vector>
+
 #include "fim_internal.cuh"
 
 namespace fim {
@@ -192,6 +195,7 @@ struct Ctl {
   uint32_t xlen0;     // prefix length of the class's root node
   uint32_t slot;      // ring slot in use
   uint32_t rpos;      // ring position of that slot
+  uint32_t cls;       // top class of the current entry (frow index of its first item)
   unsigned long long base;
 };
 
@@ -266,6 +270,8 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
         atomicAdd(&p.ctrl->sets_total, sets);
         atomicAdd(&p.ctrl->items_total, items);
         atomicMax(&p.ctrl->max_len, xlen + 1);
+        const unsigned long long after = (C.base >> 32) + sets;
+        if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
       }
       __syncthreads();
       if (f) {
@@ -395,11 +401,16 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
     // ---------------- acquire a class ----------------
     if (threadIdx.x == 0) {
       C.kind = 0;
+      if (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED) static_done = true;
+      if (p.max_sets && *(volatile unsigned long long*)&p.ctrl->sets_total > p.max_sets) {
+        atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        static_done = true;
+      }
       if (!static_done) {
         const uint32_t e = atomicAdd(&p.ctrl->queue_head, 1u);
         if (e < p.ctrl->n_entries) {
           const uint2 en = p.entries[e];
-          C.kind = 1; C.a = en.x; C.b = en.y;
+          C.kind = 1; C.a = en.x; C.b = en.y; C.cls = en.x;
         } else {
           static_done = true;
         }
@@ -417,7 +428,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
             break;
           }
           if (*(volatile uint32_t*)&p.ctrl->pending == 0) break;
-          if (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_TIMEOUT) break;
+          if (*(volatile uint32_t*)&p.ctrl->err & (DEV_ERR_TIMEOUT | DEV_ERR_ABORTED)) break;
           if (!idle) { atomicAdd(&p.ctrl->n_idle, 1u); idle = true; }
           __nanosleep(backoff);
           if (backoff < 1024) backoff <<= 1;
@@ -463,7 +474,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         xrow[k] = __ldcg(slotp + kDfsSlotHeader + k);
         xidp[k] = __ldcg(slotp + kDfsSlotHeader + L + k);
       }
-      if (threadIdx.x == 0) C.xlen0 = xl;
+      if (threadIdx.x == 0) { C.xlen0 = xl; C.cls = __ldcg(slotp + 3); }
       cand = slotp + kDfsSlotHeader + 2 * L;
       mode = CAND_PAIR_RING;
       const uint32_t* spref = slotp + (sw - p.stride);
@@ -481,7 +492,10 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
     const uint32_t xlen0 = C.xlen0;
     sort_path_ids(xidp, xlen0, xid);
     __syncthreads();
-    if (threadIdx.x == 0) st_inter += nc;
+    if (threadIdx.x == 0) {
+      st_inter += nc;
+      if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)nc);
+    }
     const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, pre, pre_global, cand, mode, nc, slot_list(0),
                                           list_cap, xlen0);
     if (ns >= 2) {
@@ -569,7 +583,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         const uint32_t fd = C.fd, ncd = C.nc, coff = C.cand_off;
         uint32_t* sl = p.pool + (size_t)C.slot * sw;
         const uint32_t xl = xlen0 + fd + 1;
-        if (threadIdx.x == 0) { sl[1] = xl; sl[2] = ncd; }
+        if (threadIdx.x == 0) { sl[1] = xl; sl[2] = ncd; sl[3] = C.cls; }
         for (uint32_t k = threadIdx.x; k < xl; k += blockDim.x) {
           sl[kDfsSlotHeader + k] = k + 1 < xl ? xrow[k] : C.s_row;
           sl[kDfsSlotHeader + L + k] = k + 1 < xl ? xidp[k] : C.s_id;
@@ -609,7 +623,10 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       }
       sort_path_ids(xidp, xl, xid);
       __syncthreads();
-      if (threadIdx.x == 0) st_inter += ncc;
+      if (threadIdx.x == 0) {
+        st_inter += ncc;
+        if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)ncc);
+      }
       const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : slot_pre(d + 1), false,
                                             slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl);
       if (n2 >= 2 && PSMEM) {
@@ -638,9 +655,395 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
 #undef slot_list
 }
 
+// ---------------------------------------------------------------------------
+// K4, frame mode: the children of a frame are counted together.
+//
+// A frame is a class node X with its prefix bitmap t(X) and its survivor list
+// L = [s_0, s_1, ...] (the items e with X u {e} frequent).  Its children are
+// [X u {s_m} | s_{m+1} ...]; instead of expanding them one after the other,
+// one pass counts every pair (m, e), m < e, as popc(t(X) & t({s_m}) &
+// t({s_e})), i.e. the supports of the grandchildren X u {s_m, s_e} (two
+// generating subsets X u {s_m} and {s_e}, App. B.3.1).  A pass covers up to
+// kPairBatch pairs in child-major order, so the number of dependent steps of a
+// class is about its depth instead of its number of nodes.  Child m is then
+// entered as a frame with prefix t(X) & t({s_m}) when it has two or more
+// survivors.  No donation in this mode.
+
+constexpr uint32_t kPairBatch = 2048;
+
+__device__ __forceinline__ uint64_t pair_base(uint32_t m, uint32_t n) {
+  // pairs of children before child m in a frame of n items: sum_{k<m} (n - 1 - k)
+  return (uint64_t)m * (n - 1) - (uint64_t)m * (m - 1) / 2;
+}
+// child m of pair p (largest m with pair_base(m) <= p), searched in [lo, hi)
+__device__ __forceinline__ uint32_t pair_child(uint64_t p, uint32_t n, uint32_t lo, uint32_t hi) {
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pair_base(mid, n) <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <int VEC>
+__device__ __forceinline__ uint32_t piece_popc3(const uint4* __restrict__ r1, const uint4* __restrict__ r2,
+                                                const uint4* pre, uint32_t base4, uint32_t stride4) {
+  uint32_t s = 0;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const uint32_t w = base4 + v * 32;
+    if (w < stride4) {
+      const uint4 a = __ldg(r1 + w), b = __ldg(r2 + w), c = pre[w];
+      s += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y) + __popc(a.z & b.z & c.z) + __popc(a.w & b.w & c.w);
+    }
+  }
+  return s;
+}
+
+struct FrameCtl {
+  uint32_t action;   // 1 descend, 2 count pass, 3 pop, 4 class done
+  uint32_t m;        // child to descend
+  uint64_t p0, p1;   // pair range of the pass
+  uint32_t mA, mB;   // children touched by the pass
+  uint32_t cont;     // the pass continues child mA from an earlier pass
+  unsigned long long base;
+};
+
+template <int VEC, bool PSMEM>
+__global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
+  const DfsLaunch& p = A.p;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ Ctl C;
+  __shared__ FrameCtl F;
+  __shared__ uint32_t wtot[33];
+  __shared__ int32_t spre_depth;  // frame whose prefix the shared copy holds
+  // dynamic shared memory: [prefix (PSMEM)] [cnt kPairBatch] [ccnt kPairBatch] [frame arrays 7 x (maxd+1)]
+  //                        [xrow] [xidp] [xid]
+  uint32_t* sp = smem;
+  uint32_t* spre = PSMEM ? sp : nullptr;
+  if (PSMEM) sp += p.stride;
+  uint32_t* cnt = sp; sp += kPairBatch;   // pair counts of a pass
+  uint32_t* ccnt = sp; sp += kPairBatch;  // survivors per child of a pass
+  const uint32_t nd = p.maxd + 1;
+  uint32_t* f_n = sp; sp += nd;       // list length
+  uint32_t* f_loff = sp; sp += nd;    // arena offset of the list (words)
+  uint32_t* f_cur = sp; sp += nd;     // next child to enter
+  uint32_t* f_cend = sp; sp += nd;    // children below this are fully counted
+  uint32_t* f_gm0 = sp; sp += nd;     // first child with an entry in the child table
+  uint32_t* f_gused = sp; sp += nd;   // survivor entries used in the G area
+  uint32_t* f_plo = sp; sp += 2 * nd; // next pair to count (64-bit, lo/hi)
+  uint32_t* xrow = sp; sp += A.max_len + 1;
+  uint32_t* xidp = sp; sp += A.max_len + 1;
+  uint32_t* xid = sp;
+
+  // arena: [root list 2*n1] then per depth [prefix stride][G 2*(kPairBatch+n1)][child table 2*kPairBatch]
+  const uint64_t root_words = (2ull * p.n1 + 3) & ~3ull;
+  const uint64_t g_words = 2ull * (kPairBatch + p.n1);
+  const uint64_t per_depth = (uint64_t)p.stride + g_words + 2ull * kPairBatch;
+  uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
+  uint32_t* const root_list = arena;
+#define fr_pre(d) (arena + root_words + (size_t)(d) * per_depth)
+#define fr_g(d) (arena + root_words + (size_t)(d) * per_depth + p.stride)
+#define fr_tab(d) (arena + root_words + (size_t)(d) * per_depth + p.stride + g_words)
+  const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long st_inter = 0, st_frames = 0;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      C.kind = 0;
+      bool stop = (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED) != 0;
+      if (!stop && p.max_sets && *(volatile unsigned long long*)&p.ctrl->sets_total > p.max_sets) {
+        atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        stop = true;
+      }
+      const uint32_t e = stop ? 0xffffffffu : atomicAdd(&p.ctrl->queue_head, 1u);
+      if (e < p.ctrl->n_entries) {
+        const uint2 en = p.entries[e];
+        C.kind = 1; C.a = en.x; C.b = en.y; C.cls = en.x;
+      }
+    }
+    __syncthreads();
+    if (C.kind == 0) break;
+
+    // ---------------- root node: [X = {i, s_m} | S_i after s_m] ----------------
+    const uint32_t i = C.a, m0 = C.b;
+    const uint32_t base = p.soff[i];
+    const uint32_t si = p.sitems[base + m0];
+    const uint32_t r1 = p.frows[i], r2 = p.frows[si];
+    const uint32_t nc = p.scnt[i] - m0 - 1;
+    if (threadIdx.x == 0) { xrow[0] = r1; xidp[0] = p.rank_item[r1]; spre_depth = 0; }
+    if (threadIdx.x == 1) { xrow[1] = r2; xidp[1] = p.rank_item[r2]; }
+    {
+      const uint4* a4 = bits4 + (size_t)r1 * A.stride4;
+      const uint4* b4 = bits4 + (size_t)r2 * A.stride4;
+      uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : fr_pre(0));
+      for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
+        const uint4 a = __ldg(a4 + w), b = __ldg(b4 + w);
+        dst[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+      }
+    }
+    __syncthreads();
+    sort_path_ids(xidp, 2, xid);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st_inter += nc;
+      if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)nc);
+    }
+    const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : fr_pre(0), false, p.sitems + base + m0 + 1,
+                                          CAND_FROW, nc, root_list, p.n1, 2);
+    if (ns >= 2 && PSMEM) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(spre);
+      uint4* d4 = reinterpret_cast<uint4*>(fr_pre(0));
+      for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = s4[w];
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(&p.ctrl->n_nodes, 1ull);
+      atomicAdd(&p.ctrl->progress, 1u);
+      if (ns >= 2) {
+        f_n[0] = ns; f_loff[0] = 0; f_cur[0] = 0; f_cend[0] = 0; f_gm0[0] = 0; f_gused[0] = 0;
+        f_plo[0] = 0; f_plo[1] = 0;
+        C.depth = 0;
+        ++st_frames;
+      } else {
+        C.depth = -1;
+      }
+    }
+
+    // ---------------- frames ----------------
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (C.depth >= 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
+        const int32_t d = C.depth;
+        if (d < 0) {
+          F.action = 4;
+        } else {
+          const uint32_t n = f_n[d];
+          const uint64_t total = (uint64_t)n * (n - 1) / 2;
+          const uint64_t pnext = (uint64_t)f_plo[2 * d] | ((uint64_t)f_plo[2 * d + 1] << 32);
+          uint32_t* tab = fr_tab(d);
+          bool done = false;
+          while (!done && f_cur[d] < f_cend[d]) {
+            const uint32_t m = f_cur[d]++;
+            const uint32_t k = m - f_gm0[d];
+            if (tab[2 * k + 1] >= 2) {
+              if ((uint32_t)(d + 1) > p.maxd) {
+                atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+                C.depth = -1;
+                F.action = 3;
+              } else {
+                F.action = 1;
+                F.m = m;
+              }
+              done = true;
+            }
+          }
+          if (!done) {
+            if (pnext >= total) {
+              F.action = 3;
+              C.depth = d - 1;
+            } else {
+              uint64_t p1 = pnext + kPairBatch < total ? pnext + kPairBatch : total;
+              const uint32_t mA = pair_child(pnext, n, 0, n - 1);
+              if (p1 < total) {
+                const uint32_t mE = pair_child(p1, n, mA, n - 1);  // child holding pair p1
+                if (pair_base(mE, n) > pnext) p1 = pair_base(mE, n);  // end at a child boundary
+              }
+              const uint32_t mB = pair_child(p1 - 1, n, mA, n - 1);
+              F.action = 2;
+              F.p0 = pnext;
+              F.p1 = p1;
+              F.mA = mA;
+              F.mB = mB;
+              F.cont = pair_base(mA, n) < pnext ? 1u : 0u;
+              if (!F.cont) { f_gm0[d] = mA; f_gused[d] = 0; }
+              f_plo[2 * d] = (uint32_t)p1;
+              f_plo[2 * d + 1] = (uint32_t)(p1 >> 32);
+              // children fully counted after this pass
+              const uint32_t mfull = (pair_base(mB, n) + (n - 1 - mB) <= p1) ? mB + 1 : mB;
+              f_cend[d] = mfull;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t action = F.action;
+      if (action == 4) break;
+      if (action == 3) continue;
+      const int32_t d = C.depth;
+      const uint32_t n = f_n[d];
+      const uint32_t* L = arena + f_loff[d];
+      const uint32_t xl = 2 + (uint32_t)d;  // |X_d|
+      if (action == 1) {
+        // enter child m of frame d as frame d + 1
+        const uint32_t m = F.m;
+        const uint32_t k = m - f_gm0[d];
+        const uint32_t* tab = fr_tab(d);
+        const uint32_t row = L[2 * m];
+        // t(X_d) comes from the stack: the shared copy may hold a deeper prefix when this frame resumes
+        const uint4* pd = reinterpret_cast<const uint4*>(fr_pre(d));
+        const uint4* r4 = bits4 + (size_t)row * A.stride4;
+        uint4* dg = reinterpret_cast<uint4*>(fr_pre(d + 1));
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
+          const uint4 a = pd[w], b = __ldg(r4 + w);
+          const uint4 c = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+          dg[w] = c;
+          if (PSMEM) reinterpret_cast<uint4*>(spre)[w] = c;
+        }
+        if (threadIdx.x == 0) {
+          spre_depth = d + 1;
+          xrow[xl] = row;
+          xidp[xl] = L[2 * m + 1];
+          f_n[d + 1] = tab[2 * k + 1];
+          f_loff[d + 1] = (uint32_t)((fr_g(d) + 2ull * tab[2 * k]) - arena);
+          f_cur[d + 1] = 0; f_cend[d + 1] = 0; f_gm0[d + 1] = 0; f_gused[d + 1] = 0;
+          f_plo[2 * (d + 1)] = 0; f_plo[2 * (d + 1) + 1] = 0;
+          C.depth = d + 1;
+          ++st_frames;
+        }
+        continue;
+      }
+      // action 2: count the pairs [p0, p1) of frame d
+      const uint64_t p0 = F.p0, p1 = F.p1;
+      const uint32_t np = (uint32_t)(p1 - p0), mA = F.mA, mB = F.mB;
+      const uint32_t* pre = PSMEM ? spre : fr_pre(d);
+      if (PSMEM && spre_depth != d) {
+        // a deeper frame replaced the shared copy: reload t(X_d)
+        const uint4* s4 = reinterpret_cast<const uint4*>(fr_pre(d));
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) reinterpret_cast<uint4*>(spre)[w] = s4[w];
+      }
+      for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) cnt[k] = 0;
+      for (uint32_t k = threadIdx.x; k <= mB - mA; k += blockDim.x) ccnt[k] = 0;
+      sort_path_ids(xidp, xl, xid);
+      __syncthreads();
+      if (threadIdx.x == 0) spre_depth = d;
+      const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
+      const uint32_t total_pieces = np * A.nseg;
+      for (uint32_t pc = warp; pc < total_pieces; pc += nw) {
+        const uint32_t q = pc / A.nseg, g = pc - q * A.nseg;
+        const uint64_t pp = p0 + q;
+        const uint32_t m = pair_child(pp, n, mA, mB + 1);
+        const uint32_t e = m + 1 + (uint32_t)(pp - pair_base(m, n));
+        const uint4* ra = bits4 + (size_t)L[2 * m] * A.stride4;
+        const uint4* rb = bits4 + (size_t)L[2 * e] * A.stride4;
+        uint32_t sum = piece_popc3<VEC>(ra, rb, pre4, g * 32 * VEC + lane, A.stride4);
+        sum = __reduce_add_sync(0xffffffffu, sum);
+        if (lane == 0 && sum) atomicAdd(&cnt[q], sum);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        st_inter += np;
+        if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)np);
+      }
+      // survivors in pair order: G entries (row, id) of the second item, per-child counts, records
+      uint32_t* G = fr_g(d);
+      uint32_t* tab = fr_tab(d);
+      const uint32_t gbase = f_gused[d];
+      const uint32_t gm0 = f_gm0[d];
+      uint32_t taken = 0;
+      for (uint32_t c0 = 0; c0 < np; c0 += blockDim.x) {
+        const uint32_t q = c0 + threadIdx.x;
+        const uint32_t cq = q < np ? cnt[q] : 0u;
+        const bool f = q < np && cq >= p.minsup;
+        uint32_t tot;
+        const uint32_t pos = block_flag_scan(f, wtot, &tot);
+        if (threadIdx.x == 0 && tot) {
+          const unsigned long long sets = tot, items = (unsigned long long)tot * (xl + 2);
+          F.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+          atomicAdd(&p.ctrl->sets_total, sets);
+          atomicAdd(&p.ctrl->items_total, items);
+          atomicMax(&p.ctrl->max_len, xl + 2);
+          const unsigned long long after = (F.base >> 32) + sets;
+          if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        }
+        __syncthreads();
+        if (f) {
+          const uint64_t pp = p0 + q;
+          const uint32_t m = pair_child(pp, n, mA, mB + 1);
+          const uint32_t e = m + 1 + (uint32_t)(pp - pair_base(m, n));
+          const uint32_t o = gbase + taken + pos;
+          G[2 * o] = L[2 * e];
+          G[2 * o + 1] = L[2 * e + 1];
+          atomicAdd(&ccnt[m - mA], 1u);
+          const uint64_t rec = (F.base >> 32) + pos;
+          const uint64_t it0 = (F.base & 0xffffffffull) + (uint64_t)pos * (xl + 2);
+          if (rec < p.cap_sets && it0 + xl + 2 <= p.cap_items) {
+            // X_d's sorted ids merged with the two new ids (ids are < 2^32 - 1)
+            const uint32_t a = L[2 * m + 1], b = L[2 * e + 1];
+            uint32_t lo = min(a, b), hi = max(a, b);
+            uint32_t* dst = p.out_items + it0;
+            uint32_t qd = 0;
+            for (uint32_t x = 0; x < xl; ++x) {
+              const uint32_t u = xid[x];
+              if (lo < u) { dst[qd++] = lo; lo = hi; hi = 0xffffffffu; }
+              if (lo < u) { dst[qd++] = lo; lo = hi; hi = 0xffffffffu; }
+              dst[qd++] = u;
+            }
+            if (lo != 0xffffffffu) dst[qd++] = lo;
+            if (hi != 0xffffffffu) dst[qd++] = hi;
+            p.out_off[rec] = it0;
+            p.out_supp[rec] = cq;
+          } else {
+            atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
+          }
+        }
+        taken += tot;
+        __syncthreads();
+      }
+      // child table: offset (into G, entries) and survivor count per child of the pass
+      if (threadIdx.x == 0) {
+        uint32_t off = gbase;
+        for (uint32_t m = mA; m <= mB; ++m) {
+          const uint32_t k = m - gm0;
+          const uint32_t c = ccnt[m - mA];
+          if (m == mA && F.cont) {
+            tab[2 * k + 1] += c;
+          } else {
+            tab[2 * k] = off;
+            tab[2 * k + 1] = c;
+          }
+          off += c;
+        }
+        f_gused[d] = gbase + taken;
+        atomicAdd(&p.ctrl->n_nodes, (unsigned long long)(f_cend[d] > mA ? f_cend[d] - mA : 0));
+        atomicAdd(&p.ctrl->progress, 1u);
+      }
+    }
+    // class finished
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicSub(&p.ctrl->pending, 1u);
+    }
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&p.ctrl->n_intersections, st_inter);
+    atomicAdd(&p.ctrl->n_frames, st_frames);
+  }
+#undef fr_pre
+#undef fr_g
+#undef fr_tab
+}
+
+// Raise a kernel's dynamic shared-memory limit to the device maximum once
+// (launches then pass their own size).  Setting it per launch to the launch's
+// size would race between threads mining concurrently.
+cudaError_t allow_max_smem(const void* func) {
+  static std::mutex mu;
+  static std::vector<const void*> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const void* f : done)
+    if (f == func) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) done.push_back(func);
+  return e;
+}
+
 template <int VEC, bool PSMEM>
 cudaError_t launch_dfs_t(const DfsArgs& a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_dfs<VEC, PSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs<VEC, PSMEM>));
   if (e != cudaSuccess) return e;
   k_dfs<VEC, PSMEM><<<grid, threads, smem, st>>>(a);
   return cudaGetLastError();
@@ -658,8 +1061,34 @@ cudaError_t launch_dfs_vec(const DfsArgs& a, uint32_t grid, uint32_t threads, ui
 }
 
 template <int VEC, bool PSMEM>
+cudaError_t launch_frames_t(const DfsArgs& a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_frames<VEC, PSMEM>));
+  if (e != cudaSuccess) return e;
+  k_dfs_frames<VEC, PSMEM><<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool PSMEM>
+cudaError_t launch_frames_vec(const DfsArgs& a, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
+                              cudaStream_t st) {
+  switch (vec) {
+    case 1: return launch_frames_t<1, PSMEM>(a, grid, threads, smem, st);
+    case 2: return launch_frames_t<2, PSMEM>(a, grid, threads, smem, st);
+    case 8: return launch_frames_t<8, PSMEM>(a, grid, threads, smem, st);
+    default: return launch_frames_t<4, PSMEM>(a, grid, threads, smem, st);
+  }
+}
+
+template <int VEC, bool PSMEM>
+cudaError_t occ_frames_t(uint32_t threads, size_t smem, int* out) {
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_frames<VEC, PSMEM>));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs_frames<VEC, PSMEM>, (int)threads, smem);
+}
+
+template <int VEC, bool PSMEM>
 cudaError_t occ_t(uint32_t threads, size_t smem, int* out) {
-  cudaError_t e = cudaFuncSetAttribute(k_dfs<VEC, PSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs<VEC, PSMEM>));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs<VEC, PSMEM>, (int)threads, smem);
 }
@@ -680,16 +1109,44 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem) {
-  size_t words = (prefix_in_smem ? stride : 0) + kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1);
+size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem, uint32_t mode) {
+  size_t words = prefix_in_smem ? stride : 0;
+  if (mode == 1) words += 2ull * kPairBatch + 8ull * (maxd + 1) + 3ull * (max_len + 1);
+  else words += kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1);
   return words * sizeof(uint32_t);
 }
 
-bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd) {
-  return dfs_smem_bytes(stride, max_len, maxd, true) + sizeof(Ctl) + 33 * 4 + 256 <= smem_optin;
+bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd, uint32_t mode) {
+  return dfs_smem_bytes(stride, max_len, maxd, true, mode) + sizeof(Ctl) + sizeof(FrameCtl) + 33 * 4 + 512 <= smem_optin;
 }
 
-cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, int* out) {
+uint64_t dfs_arena_cta_words(uint32_t stride, uint32_t n1, uint32_t maxd, uint32_t mode) {
+  if (mode == 1) {
+    const uint64_t root_words = (2ull * n1 + 3) & ~3ull;
+    const uint64_t per_depth = (uint64_t)stride + 2ull * (kPairBatch + n1) + 2ull * kPairBatch;
+    return root_words + per_depth * (maxd + 1);
+  }
+  return dfs_arena_depth_words(stride, n1) * (maxd + 1);
+}
+
+cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, uint32_t mode,
+                                int* out) {
+  if (mode == 1) {
+    if (prefix_in_smem) {
+      switch (vec) {
+        case 1: return occ_frames_t<1, true>(threads, smem, out);
+        case 2: return occ_frames_t<2, true>(threads, smem, out);
+        case 8: return occ_frames_t<8, true>(threads, smem, out);
+        default: return occ_frames_t<4, true>(threads, smem, out);
+      }
+    }
+    switch (vec) {
+      case 1: return occ_frames_t<1, false>(threads, smem, out);
+      case 2: return occ_frames_t<2, false>(threads, smem, out);
+      case 8: return occ_frames_t<8, false>(threads, smem, out);
+      default: return occ_frames_t<4, false>(threads, smem, out);
+    }
+  }
   if (prefix_in_smem) {
     switch (vec) {
       case 1: return occ_t<1, true>(threads, smem, out);
@@ -713,13 +1170,17 @@ cudaError_t launch_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words
 }
 
 cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
-                       bool prefix_in_smem, uint32_t max_len, cudaStream_t st) {
+                       bool prefix_in_smem, uint32_t max_len, uint32_t mode, cudaStream_t st) {
   DfsArgs a;
   a.p = p;
   a.stride4 = p.stride / 4;
   const uint32_t segw4 = 32u * vec;  // 16-byte vectors per piece
   a.nseg = (a.stride4 + segw4 - 1) / segw4;
   a.max_len = max_len;
+  if (mode == 1) {
+    if (prefix_in_smem) return launch_frames_vec<true>(a, grid, threads, vec, smem, st);
+    return launch_frames_vec<false>(a, grid, threads, vec, smem, st);
+  }
   if (prefix_in_smem) return launch_dfs_vec<true>(a, grid, threads, vec, smem, st);
   return launch_dfs_vec<false>(a, grid, threads, vec, smem, st);
 }

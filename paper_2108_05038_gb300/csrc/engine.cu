@@ -27,7 +27,8 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->bits = in.bits;
   ep->d_rank_item = in.d_rank_item;
   ep->num_sms = db->num_sms;
-  ep->donate = cfg.donate;
+  ep->mode = cfg.mode == 1 ? 1u : 0u;
+  ep->donate = ep->mode == 1 ? 0u : cfg.donate;  // frame passes do not donate
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
   ep->cap_sets = cfg.cap_sets ? cfg.cap_sets : std::max<uint64_t>((uint64_t)1 << 18, 8ull * n1 + 64);
@@ -69,15 +70,15 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->maxd = std::min<uint32_t>(ep->maxd_full, kDfsDepthHint);  // grown (and the run repeated) on demand
   ep->threads = clamp_threads(cfg.threads);
   ep->vec = clamp_vec(cfg.vec);
-  ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full);
-  ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem);
+  ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full, ep->mode);
+  ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem, ep->mode);
   int occ = 0;
-  FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, &occ));
+  FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
   if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
   const uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
   ep->grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);
   ep->per_depth = dfs_arena_depth_words(in.stride, n1);
-  ep->pool_slots = cfg.donate ? std::max<uint32_t>(8, ep->grid) : 0;
+  ep->pool_slots = ep->donate ? std::max<uint32_t>(8, ep->grid) : 0;
   ep->pool_slot_words = dfs_pool_slot_words(in.stride, ep->L, n1);
   if (ep->pool_slots) FIM_TRY(ws_get(ws, WS_POOL, ep->pool_slot_words * ep->pool_slots, &ep->d_pool));
   if (cfg.collect_times)
@@ -89,13 +90,18 @@ fim_status engine_alloc(Workspace& ws, EnginePlan* ep) {
   FIM_TRY(ws_get(ws, WS_OUT_OFF, ep->cap_sets + 1, &ep->d_off));
   FIM_TRY(ws_get(ws, WS_OUT_ITEMS, std::max<uint64_t>(1, ep->cap_items), &ep->d_items));
   FIM_TRY(ws_get(ws, WS_OUT_SUPP, std::max<uint64_t>(1, ep->cap_sets), &ep->d_supp));
-  if (ep->n1 >= 3) FIM_TRY(ws_get(ws, WS_ARENA, ep->per_depth * (ep->maxd + 1) * ep->grid, &ep->d_arena));
+  if (ep->n1 >= 3)
+    FIM_TRY(ws_get(ws, WS_ARENA, dfs_arena_cta_words(ep->stride, ep->n1, ep->maxd, ep->mode) * ep->grid, &ep->d_arena));
   return FIM_OK;
 }
 
 cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   cudaError_t ce = cudaMemsetAsync(ep.d_ctrl, 0, sizeof(DevCtrl), st);
   if (ce != cudaSuccess || ep.n1 == 0) return ce;
+  if (ep.d_class_work) {
+    ce = cudaMemsetAsync(ep.d_class_work, 0, (size_t)ep.n1 * sizeof(unsigned long long), st);
+    if (ce != cudaSuccess) return ce;
+  }
   if (ep.pool_slots) {
     ce = launch_pool_init(ep.d_pool, ep.pool_slots, ep.pool_slot_words, st);
     if (ce != cudaSuccess) return ce;
@@ -125,7 +131,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.sitems = ep.d_sitems;
     dl.entries = ep.d_entries;
     dl.arena = ep.d_arena;
-    dl.arena_cta_words = ep.per_depth * (ep.maxd + 1);
+    dl.arena_cta_words = dfs_arena_cta_words(ep.stride, ep.n1, ep.maxd, ep.mode);
     dl.maxd = ep.maxd;
     dl.pool = ep.d_pool;
     dl.pool_slots = ep.pool_slots;
@@ -138,7 +144,9 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.ctrl = ep.d_ctrl;
     dl.spin_limit = ep.spin_limit;
     dl.donate = ep.donate;
-    ce = launch_dfs(dl, ep.grid, ep.threads, ep.vec, ep.smem, ep.psmem, ep.L, st);
+    dl.class_work = ep.d_class_work;
+    dl.max_sets = ep.max_sets;
+    ce = launch_dfs(dl, ep.grid, ep.threads, ep.vec, ep.smem, ep.psmem, ep.L, ep.mode, st);
     if (ce != cudaSuccess) return ce;
   }
   if (ep.ev[3]) cudaEventRecord(ep.ev[3], st);
@@ -166,6 +174,8 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
   std::memcpy(&h, hstage, sizeof(DevCtrl));
   out->ctrl = h;
   if (h.err & DEV_ERR_TIMEOUT) return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
+  if (h.err & DEV_ERR_ABORTED)
+    return fail(FIM_ERR_OUTPUT_OVERFLOW, "more frequent itemsets than the limit: mining stopped early (counts are lower bounds)");
   if (h.err & DEV_ERR_DEPTH) {
     if (ep->maxd >= ep->maxd_full) return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
     ep->maxd = ep->maxd_full;  // deeper than the first stack: repeat with the full bound
@@ -225,6 +235,8 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
                        fim_mine_stats* stats, EnginePlan* plan_out) {
   EnginePlan ep;
   fim_status s = engine_prepare(db, ws, in, cfg, &ep);
+  if (s == FIM_OK && cfg.class_work) ep.d_class_work = cfg.class_work;
+  ep.max_sets = cfg.max_sets;
   for (int attempt = 0; s == FIM_OK && attempt < 4; ++attempt) {
     if ((s = engine_alloc(ws, &ep)) != FIM_OK) break;
     cudaError_t ce = engine_launch(ep, ws.stream);

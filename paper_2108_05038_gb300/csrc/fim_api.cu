@@ -324,6 +324,8 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->vec = o->vec_per_lane ? o->vec_per_lane : 4;
   c->ctas_per_sm = o->ctas_per_sm;
   c->donate = o->donate;
+  c->mode = o->dfs_mode;
+  c->max_sets = o->max_itemsets;
   c->spin_limit = o->spin_limit;
   c->cap_sets = o->out_capacity_sets;
   c->cap_items = o->out_capacity_items;
@@ -464,11 +466,21 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
 
 fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
                                     double* cost_out, uint32_t* order_out) {
+  return fim_estimate_class_costs_ex(db, sample_rate, rel_minsup, seed, FIM_COST_ITEMSETS, cost_out, order_out);
+}
+
+fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
+                                       uint32_t cost_kind, double* cost_out, uint32_t* order_out) {
   if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (cost_kind != FIM_COST_ITEMSETS && cost_kind != FIM_COST_INTERSECTIONS)
+    return fail(FIM_ERR_INVALID, "unknown cost kind");
   if (!(sample_rate > 0.0 && sample_rate <= 1.0)) return fail(FIM_ERR_INVALID, "sample_rate must be in (0, 1]");
   if (!(rel_minsup >= 0.0 && rel_minsup <= 1.0)) return fail(FIM_ERR_INVALID, "rel_minsup must be in [0, 1]");
   cudaStream_t st = db->stream;
-  const double md = std::ceil(sample_rate * (double)db->D);
+  // sample size: the requested rate, but never below the Theorem 6.1 size for eps = delta = 0.05
+  const double m0 = std::ceil(std::log(2.0 / 0.05) / (2.0 * 0.05 * 0.05));
+  double md = std::ceil(sample_rate * (double)db->D);
+  md = std::max(md, std::min((double)db->D, m0));
   const uint32_t m = md < 1.0 ? 1u : (uint32_t)md;
   const double msd = std::ceil(rel_minsup * (double)m);
   const uint32_t minsup_s = msd < 1.0 ? 1u : (uint32_t)msd;
@@ -506,10 +518,26 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
   in.max_len_bound = db->max_tx_len;
   EngineConfig cfg;
   cfg.donate = 0;
+  unsigned long long* d_work = nullptr;
+  if (cost_kind == FIM_COST_INTERSECTIONS && in.n1) {
+    FIM_TRY(ws_get(db->ws, WS_CLASSWORK, in.n1, &d_work));
+    cfg.class_work = d_work;
+  }
   EngineOutput eo;
   FIM_TRY(engine_mine(db, db->ws, in, cfg, &eo, nullptr));
   std::vector<unsigned long long> tally(R, 0ull);
-  if (R) {
+  if (cost_kind == FIM_COST_INTERSECTIONS) {
+    // intersections per class: level 2 (the later frequent sample rows) + the DFS below it
+    std::vector<unsigned long long> work(in.n1, 0ull);
+    if (in.n1 && in.n1 >= 3) {
+      void* h = nullptr;
+      FIM_TRY(stage_get(db, (size_t)in.n1 * 8, &h));
+      FIM_CUDA(cudaMemcpyAsync(h, d_work, (size_t)in.n1 * 8, cudaMemcpyDeviceToHost, st));
+      FIM_TRY(stream_sync(db));
+      std::memcpy(work.data(), h, (size_t)in.n1 * 8);
+    }
+    for (uint32_t i = 0; i < in.n1; ++i) tally[in.frows[i]] = work[i] + (in.n1 - 1 - i);
+  } else if (R) {
     unsigned long long* d_tally = nullptr;
     FIM_TRY(ws_get(db->ws, WS_TALLY, R, &d_tally));
     FIM_CUDA(cudaMemsetAsync(d_tally, 0, (size_t)R * 8, st));
@@ -520,8 +548,10 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
     FIM_TRY(stream_sync(db));
     std::memcpy(tally.data(), h, (size_t)R * 8);
   }
+  unsigned long long total = 0;
+  for (uint32_t r = 0; r < R; ++r) total += tally[r];
   db->est_cost.assign(R, 0.0);
-  for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = eo.n_sets ? (double)tally[r] / (double)eo.n_sets : 0.0;
+  for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = total ? (double)tally[r] / (double)total : 0.0;
   db->est_order.resize(R);
   std::iota(db->est_order.begin(), db->est_order.end(), 0u);
   std::stable_sort(db->est_order.begin(), db->est_order.end(),

@@ -43,6 +43,7 @@ enum : uint32_t {
   DEV_ERR_TIMEOUT = 1u << 3,      // a bounded wait ran out
   DEV_ERR_OVERFLOW = 1u << 4,     // output capacity exceeded (counts keep going)
   DEV_ERR_POOL = 1u << 5,         // donation pool protocol violated
+  DEV_ERR_ABORTED = 1u << 6,      // more itemsets than the caller's limit: mining stopped early
 };
 
 // ---------------------------------------------------------------------------
@@ -89,6 +90,7 @@ enum WsSlot {
   WS_SAMPLE_BITS,
   WS_SAMPLE_SUPP,
   WS_TALLY,
+  WS_CLASSWORK,
   WS_COUNT
 };
 
@@ -217,10 +219,13 @@ struct EngineConfig {
   uint32_t vec = 4;
   uint32_t ctas_per_sm = 0;
   uint32_t donate = 0;
+  uint32_t mode = 0;  // DFS traversal: 0 node, 1 frame
   uint64_t spin_limit = 0;
   uint64_t cap_sets = 0, cap_items = 0;  // 0 = automatic
   bool fixed_capacity = false;
   bool collect_times = false;
+  unsigned long long* class_work = nullptr;  // optional device array (n1 entries): DFS intersections per top class
+  uint64_t max_sets = 0;                     // 0 = no limit; else stop early past this many itemsets
 };
 
 // Everything one mining call launches, with its geometry and buffers.  The
@@ -237,8 +242,11 @@ struct EnginePlan {
   uint64_t cap_sets = 0, cap_items = 0;
   bool fixed_capacity = false;
   uint32_t donate = 0;
+  uint32_t mode = 0;
   uint64_t spin_limit = 0;
   int num_sms = 0;
+  unsigned long long* d_class_work = nullptr;  // optional per-class intersection counters (n1 entries)
+  uint64_t max_sets = 0;
   // buffers
   DevCtrl* d_ctrl = nullptr;
   const uint32_t *d_frows = nullptr, *d_rsupp = nullptr, *d_order = nullptr;
@@ -341,14 +349,19 @@ struct DfsLaunch {
   DevCtrl* ctrl;
   uint64_t spin_limit;
   uint32_t donate;
+  unsigned long long* class_work;  // optional: intersections per top class (frow index of its first item)
+  uint64_t max_sets;               // 0 = no limit; else stop once more sets than this are found
 };
 // grid: number of persistent CTAs; threads: CTA size; vec: 16-byte loads per lane per piece
+// mode 0: node at a time (optionally with donation); mode 1: frame passes (all children of a frame together)
 cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
-                       bool prefix_in_smem, uint32_t max_len, cudaStream_t st);
-size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem);
+                       bool prefix_in_smem, uint32_t max_len, uint32_t mode, cudaStream_t st);
+size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem, uint32_t mode);
 cudaError_t launch_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words, cudaStream_t st);
-cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, int* out);
-bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd);
+cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, uint32_t mode,
+                                int* out);
+bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd, uint32_t mode);
+uint64_t dfs_arena_cta_words(uint32_t stride, uint32_t n1, uint32_t maxd, uint32_t mode);
 constexpr uint32_t kDfsDepthHint = 8;  // DFS stack depth allocated first (grown on demand)
 constexpr uint32_t kDfsSlotHeader = 4;  // donation pool slot: sequence, xlen, ncand, spare
 // pool slot words for itemsets of up to max_len items and n1 candidates (prefix bitmap last)

@@ -8,10 +8,10 @@
 // (upper triangle only), stages 32-word slices of the 64 + 64 rows in shared
 // memory with cp.async (3-stage pipeline), and every thread accumulates a 4 x 4
 // micro-tile.  Each staged word is reused by 64 pairs, so the kernel is bound
-// by the integer pipe (AND + POPC per word pair), not by memory.  Rows are
-// split along the word axis into (tile, word range) work items that a grid of
-// two CTAs per SM walks through (partial counts added atomically), which keeps
-// every SM busy until the last wave.
+// by the integer pipes (AND on the integer pipe, POPC on the XU pipe), not by
+// memory.  Rows are split along the word axis into (tile, word range) work
+// items that a grid of resident CTAs (three per SM) walks through (partial
+// counts added atomically), which keeps every SM busy until the last wave.
 #include <mutex>
 
 #include "fim_internal.cuh"
@@ -34,14 +34,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// acc += popc(a & b): AND and POPC on the integer pipe, the add as a
-// multiply-add by a runtime one so that it can issue on the FMA pipe.
-__device__ __forceinline__ void acc_and_popc(uint32_t& acc, uint32_t a, uint32_t b, uint32_t one) {
-  uint32_t p = __popc(a & b);
-  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(p), "r"(one));
+// acc += popc(a.x&b.x) + popc(a.y&b.y) + popc(a.z&b.z) + popc(a.w&b.w).
+// POPC issues on the XU pipe (32 lanes/clk/SM) and limits the plain form; a
+// 3:2 carry-save adder (two LOP3 on the 64-lane integer pipe) folds three of
+// the four AND words into a sum word s and a carry word c, so that
+// popc(t0)+popc(t1)+popc(t2) = popc(s) + 2 popc(c): three POPC per four words.
+// The accumulation is a multiply-add by a runtime 1 or 2 (FMA pipe).
+__device__ __forceinline__ void acc_and_popc4(uint32_t& acc, const uint4& a, const uint4& b, uint32_t one,
+                                              uint32_t two) {
+  const uint32_t t0 = a.x & b.x, t1 = a.y & b.y, t2 = a.z & b.z, t3 = a.w & b.w;
+  const uint32_t s = t0 ^ t1 ^ t2;
+  const uint32_t c = (t0 & t1) | (t2 & (t0 ^ t1));
+  const uint32_t ps = __popc(s), pc = __popc(c), p3 = __popc(t3);
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(pc), "r"(two));
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(ps), "r"(one));
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(p3), "r"(one));
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows, uint32_t n1,
               uint32_t nb, uint32_t chunks_per_split, uint32_t nchunks, uint32_t* __restrict__ C2, uint32_t ksplit,
               uint32_t n_items, uint32_t one) {
@@ -112,12 +122,7 @@ k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t
       for (int x = 0; x < 4; ++x) {
         const uint4 a = *reinterpret_cast<const uint4*>(As + (ty + 16 * x) * kRowPad + kk * 4);
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          acc_and_popc(acc[x][y], a.x, b[y].x, one);
-          acc_and_popc(acc[x][y], a.y, b[y].y, one);
-          acc_and_popc(acc[x][y], a.z, b[y].z, one);
-          acc_and_popc(acc[x][y], a.w, b[y].w, one);
-        }
+        for (int y = 0; y < 4; ++y) acc_and_popc4(acc[x][y], a, b[y], one, one + one);
       }
     }
     stage = stage + 1 == kStages ? 0 : stage + 1;
@@ -151,7 +156,13 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
   const uint32_t nb = (p.n1 + kTile - 1) / kTile;
   const uint32_t tiles = nb * (nb + 1) / 2;
   const uint32_t nchunks = p.stride / kChunk;  // stride is a multiple of 32 words
-  const uint32_t slots = (uint32_t)num_sms * 2;  // two resident CTAs per SM
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_counts, kThreads, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  const uint32_t slots = (uint32_t)num_sms * (uint32_t)occ;  // resident CTAs
   uint32_t ksplit = p.ksplit;
   if (ksplit == 0) {
     // enough (tile, word-range) items for >= 4 per resident CTA, each of >= 8 chunks (256 words)

@@ -32,11 +32,12 @@ namespace {
 // launch shapes tried by the autotuner: CTA size x 16-byte loads per lane x
 // CTAs per SM (0 = as many as fit) x donation
 struct Shape {
-  uint32_t threads, vec, cps, donate;
+  uint32_t threads, vec, cps, donate, mode;
 };
 const Shape kShapes[] = {
-    {128, 2, 0, 0}, {128, 4, 0, 0}, {128, 8, 0, 0}, {256, 2, 0, 0}, {256, 4, 0, 0}, {256, 8, 0, 0},
-    {512, 4, 0, 0}, {512, 8, 0, 0}, {256, 4, 2, 0}, {128, 4, 0, 1}, {256, 4, 0, 1}, {512, 4, 0, 1},
+    {128, 2, 0, 0, 0}, {128, 4, 0, 0, 0}, {256, 2, 0, 0, 0}, {256, 4, 0, 0, 0}, {256, 8, 0, 0, 0},
+    {512, 4, 0, 0, 0}, {512, 8, 0, 0, 0}, {256, 4, 0, 1, 0}, {512, 4, 0, 1, 0},
+    {128, 2, 0, 0, 1}, {128, 4, 0, 0, 1}, {256, 2, 0, 0, 1}, {256, 4, 0, 0, 1}, {512, 4, 0, 0, 1},
 };
 
 struct TuneKey {
@@ -69,6 +70,7 @@ fim_status fim_autotune(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fl
       opts->vec_per_lane = it->second.first.vec;
       opts->ctas_per_sm = it->second.first.cps;
       opts->donate = it->second.first.donate;
+      opts->dfs_mode = it->second.first.mode;
       if (best_ms) *best_ms = it->second.second;
       return FIM_OK;
     }
@@ -82,6 +84,7 @@ fim_status fim_autotune(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fl
     c.vec = sh.vec;
     c.ctas_per_sm = sh.cps;
     c.donate = sh.donate;
+    c.mode = sh.mode;
     c.collect_times = true;
     float t = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
@@ -103,6 +106,7 @@ fim_status fim_autotune(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fl
   opts->vec_per_lane = best.vec;
   opts->ctas_per_sm = best.cps;
   opts->donate = best.donate;
+  opts->dfs_mode = best.mode;
   if (best_ms) *best_ms = best_t;
   return FIM_OK;
 }

@@ -51,6 +51,7 @@ struct fim_server {
   bool stop = false;
   int device = 0;
   uint32_t ctas_per_sm = 1;
+  uint64_t max_itemsets = 0;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
 };
@@ -84,6 +85,7 @@ void run_job(fim_server* srv, Job* j, cudaStream_t st) {
     fim_mine_opts_init(&o);
     o.ctas_per_sm = srv->ctas_per_sm;
     o.donate = 0;
+    o.max_itemsets = srv->max_itemsets;
     s = fim_mine(db, j->minsup, &o, &j->result);
   }
   if (s != FIM_OK) j->error = fim_last_error();
@@ -136,7 +138,8 @@ using namespace fim;
 
 extern "C" {
 
-fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t ctas_per_sm, fim_server** out) {
+fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t ctas_per_sm, uint64_t max_itemsets,
+                             fim_server** out) {
   if (!out) return fail(FIM_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (slots == 0 || slots > 64) return fail(FIM_ERR_INVALID, "slots must be in 1..64");
@@ -150,6 +153,7 @@ fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t
   }
   srv->budget = hbm_budget_bytes;
   srv->ctas_per_sm = ctas_per_sm ? ctas_per_sm : 1;
+  srv->max_itemsets = max_itemsets;
   for (uint32_t k = 0; k < slots; ++k) {
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);

@@ -21,7 +21,7 @@ FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
 # every symbol declared in include/fim.h
 EXPORTED = [
     "fim_mine_opts_init", "fim_build_vertical_db", "fim_build_vertical_db_device", "fim_db_info", "fim_db_rows",
-    "fim_estimate_class_costs", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
+    "fim_estimate_class_costs", "fim_estimate_class_costs_ex", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
     "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free",
@@ -55,11 +55,12 @@ class MineStats(ctypes.Structure):
 
 class MineOpts(ctypes.Structure):
     _fields_ = [
-        ("struct_size", ctypes.c_uint32), ("class_order", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+        ("struct_size", ctypes.c_uint32), ("class_order", ctypes.c_uint32), ("dfs_mode", ctypes.c_uint32),
         ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
         ("donate", ctypes.c_uint32), ("result_on_device", ctypes.c_uint32), ("collect_times", ctypes.c_uint32),
         ("reserved_u", ctypes.c_uint32), ("out_capacity_sets", ctypes.c_uint64),
-        ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("out_needed_sets", ctypes.c_uint64),
+        ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("max_itemsets", ctypes.c_uint64),
+        ("out_needed_sets", ctypes.c_uint64),
         ("out_needed_items", ctypes.c_uint64), ("stats", ctypes.POINTER(MineStats)),
     ]
 
@@ -98,6 +99,8 @@ def load(build_if_stale: bool = True):
         lib.fim_db_rows.argtypes = [P, P, P]
         lib.fim_estimate_class_costs.restype = i32
         lib.fim_estimate_class_costs.argtypes = [P, dbl, dbl, u64, P, P]
+        lib.fim_estimate_class_costs_ex.restype = i32
+        lib.fim_estimate_class_costs_ex.argtypes = [P, dbl, dbl, u64, u32, P, P]
         lib.fim_estimate_sample_size.restype = i32
         lib.fim_estimate_sample_size.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.fim_mine.restype = i32
@@ -115,7 +118,7 @@ def load(build_if_stale: bool = True):
         lib.fim_plan_free.restype = None
         lib.fim_plan_free.argtypes = [P]
         lib.fim_server_create.restype = i32
-        lib.fim_server_create.argtypes = [u64, u32, u32, PP]
+        lib.fim_server_create.argtypes = [u64, u32, u32, u64, PP]
         lib.fim_server_submit.restype = i32
         lib.fim_server_submit.argtypes = [P, P, P, u32, u32, u32, dbl, ctypes.POINTER(u64)]
         lib.fim_server_wait.restype = i32
@@ -237,13 +240,16 @@ class Database:
         _check(self._lib, self._lib.fim_db_rows(self._h, ri.ctypes.data, sp.ctypes.data), "fim_db_rows")
         return ri[:n], sp[:n]
 
-    def estimate_class_costs(self, sample_rate: float, rel_minsup: float, seed: int):
+    def estimate_class_costs(self, sample_rate: float, rel_minsup: float, seed: int, cost: str = "itemsets"):
+        """fim_estimate_class_costs(_ex): cost "itemsets" (the thesis's measure) or "intersections"."""
         n = self.info()["n_rows"]
-        cost = np.zeros(max(n, 1), dtype=np.float64)
+        c = np.zeros(max(n, 1), dtype=np.float64)
         order = np.zeros(max(n, 1), dtype=np.uint32)
-        _check(self._lib, self._lib.fim_estimate_class_costs(self._h, sample_rate, rel_minsup, seed, cost.ctypes.data,
-                                                             order.ctypes.data), "fim_estimate_class_costs")
-        return cost[:n], order[:n]
+        kind = {"itemsets": 0, "intersections": 1}[cost]
+        _check(self._lib, self._lib.fim_estimate_class_costs_ex(self._h, sample_rate, rel_minsup, seed, kind,
+                                                                c.ctypes.data, order.ctypes.data),
+               "fim_estimate_class_costs_ex")
+        return c[:n], order[:n]
 
     def estimate_sample_size(self):
         nfs, rows, ms = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
@@ -253,9 +259,10 @@ class Database:
 
     def _opts(self, class_order="estimate", threads_per_cta=0, vec_per_lane=0, ctas_per_sm=0, donate=False,
               result_on_device=False, collect_times=False, out_capacity_sets=0, out_capacity_items=0, spin_limit=0,
-              stats=True, shape=None):
+              stats=True, shape=None, dfs_mode=0, max_itemsets=0):
         opts = MineOpts()
         self._lib.fim_mine_opts_init(ctypes.byref(opts))
+        opts.dfs_mode = dfs_mode
         opts.class_order = {"estimate": FIM_ORDER_ESTIMATE, "uniform": FIM_ORDER_UNIFORM}[class_order]
         opts.threads_per_cta = threads_per_cta
         opts.vec_per_lane = vec_per_lane
@@ -264,11 +271,13 @@ class Database:
         if shape:
             opts.threads_per_cta, opts.vec_per_lane = shape["threads_per_cta"], shape["vec_per_lane"]
             opts.ctas_per_sm, opts.donate = shape["ctas_per_sm"], shape["donate"]
+            opts.dfs_mode = shape.get("dfs_mode", 0)
         opts.result_on_device = 1 if result_on_device else 0
         opts.collect_times = 1 if collect_times else 0
         opts.out_capacity_sets = out_capacity_sets
         opts.out_capacity_items = out_capacity_items
         opts.spin_limit = spin_limit
+        opts.max_itemsets = max_itemsets
         st = MineStats() if stats else None
         if st is not None:
             opts.stats = ctypes.pointer(st)
@@ -280,7 +289,7 @@ class Database:
         ms = ctypes.c_float()
         _check(self._lib, self._lib.fim_autotune(self._h, minsup, ctypes.byref(opts), ctypes.byref(ms)), "fim_autotune")
         return {"threads_per_cta": opts.threads_per_cta, "vec_per_lane": opts.vec_per_lane,
-                "ctas_per_sm": opts.ctas_per_sm, "donate": opts.donate}, ms.value
+                "ctas_per_sm": opts.ctas_per_sm, "donate": opts.donate, "dfs_mode": opts.dfs_mode}, ms.value
 
     def plan(self, minsup: int, **kw):
         """fim_plan_create: the mine captured in a CUDA graph (see Plan)."""
@@ -293,9 +302,10 @@ class Database:
     def mine(self, minsup: int, class_order: str = "estimate", threads_per_cta: int = 0, vec_per_lane: int = 0,
              ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
              out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
-             shape=None):
+             shape=None, dfs_mode: int = 0, max_itemsets: int = 0):
         opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
-                              collect_times, out_capacity_sets, out_capacity_items, spin_limit, stats, shape)
+                              collect_times, out_capacity_sets, out_capacity_items, spin_limit, stats, shape, dfs_mode,
+                              max_itemsets)
         h = ctypes.c_void_p()
         status = self._lib.fim_mine(self._h, minsup, ctypes.byref(opts), ctypes.byref(h))
         if status == FIM_ERR_OUTPUT_OVERFLOW:
@@ -394,11 +404,11 @@ def status_str(status: int) -> str:
 class Server:
     """fim_server: continuous-batching request loop (submit / wait)."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4, ctas_per_sm: int = 1):
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4, ctas_per_sm: int = 1, max_itemsets: int = 0):
         self._lib = load()
         h = ctypes.c_void_p()
-        _check(self._lib, self._lib.fim_server_create(hbm_budget_bytes, slots, ctas_per_sm, ctypes.byref(h)),
-               "fim_server_create")
+        _check(self._lib, self._lib.fim_server_create(hbm_budget_bytes, slots, ctas_per_sm, max_itemsets,
+                                                      ctypes.byref(h)), "fim_server_create")
         self._h = h.value
 
     def submit(self, tx_offsets, tx_items, N: int, minsup: int, sample_rate: float = 0.0) -> int:

@@ -39,6 +39,7 @@ def odict(res):
 
 
 def gpu_mine(off, items, N, minsup, word_bits=64, prefilter=0, **kw):
+    """Build + mine through the C ABI (kw: fim_mine options)."""
     db = fim.build_vertical_db(off, items, N, word_bits=word_bits, prefilter_minsup=prefilter)
     try:
         return db.mine(minsup, **kw)
@@ -74,7 +75,7 @@ def test_random_tiny_vs_bruteforce(seed):
     off, items = csr(txs)
     for minsup in sorted({1, 2, max(1, D // 7), max(1, D // 2)}):
         want = odict(oracle.bruteforce(off, items, N, minsup))
-        got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64).as_dict()
+        got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64, dfs_mode=(seed // 2) % 2).as_dict()
         assert_same(got, want)
 
 
@@ -88,12 +89,12 @@ def test_ragged_D(D):
     assert_same(gpu_mine(off, items, 12, minsup).as_dict(), odict(oracle.eclat(off, items, 12, minsup)))
 
 
-@pytest.mark.parametrize("k", [11, 16])
-def test_identical_transactions_closed_form(k):
+@pytest.mark.parametrize("k,mode", [(11, 0), (16, 0), (11, 1), (16, 1)])
+def test_identical_transactions_closed_form(k, mode):
     """2^k - 1 itemsets of support D; depth 14 exceeds the first DFS stack and forces the regrown retry."""
     D = 300
     off, items = csr([list(range(k))] * D + [[k]])
-    got = gpu_mine(off, items, k + 1, D).as_dict()
+    got = gpu_mine(off, items, k + 1, D, dfs_mode=mode).as_dict()
     assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
 
 
@@ -130,27 +131,32 @@ def test_invalid_inputs():
 
 # ---------------------------------------------------------------- named workloads
 
-@pytest.mark.parametrize("name", ["tiny", "dense_deep", "dense_exact37"])
-def test_workload_full_size_exact(name):
+@pytest.mark.parametrize("name,mode", [("tiny", 0), ("dense_deep", 0), ("dense_exact37", 0), ("tiny", 1),
+                                       ("dense_deep", 1)])
+def test_workload_full_size_exact(name, mode):
     w = synth.make_workload(name)
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
-    got = gpu_mine(w["offsets"], w["items"], w["N"], w["minsup"], word_bits=w["word_bits"]).as_dict()
+    got = gpu_mine(w["offsets"], w["items"], w["N"], w["minsup"], word_bits=w["word_bits"], dfs_mode=mode).as_dict()
     assert_same(got, want)
 
 
-def test_sparse_mid_full_size_exact():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sparse_mid_full_size_exact(mode):
     w = synth.make_workload("sparse_mid")
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
-    res = gpu_mine(w["offsets"], w["items"], w["N"], w["minsup"], word_bits=64)
+    res = gpu_mine(w["offsets"], w["items"], w["N"], w["minsup"], word_bits=64, dfs_mode=mode)
     assert_same(res.as_dict(), want)
     st = res.stats
     assert st["n_frequent"] == len(want)
     assert st["n_pair_intersections"] == st["n_frequent_items"] * (st["n_frequent_items"] - 1) // 2
 
 
-@pytest.mark.parametrize("threads,vec,donate,order", [(128, 1, True, "uniform"), (256, 2, False, "uniform"),
-                                                        (512, 8, True, "estimate"), (512, 4, False, "estimate")])
-def test_launch_shapes_and_orders_identical(threads, vec, donate, order):
+@pytest.mark.parametrize("threads,vec,donate,order,mode", [(128, 1, True, "uniform", 0), (256, 2, False, "uniform", 0),
+                                                             (512, 8, True, "estimate", 0),
+                                                             (512, 4, False, "estimate", 0),
+                                                             (128, 1, False, "uniform", 1), (256, 4, False, "estimate", 1),
+                                                             (512, 8, False, "estimate", 1)])
+def test_launch_shapes_and_orders_identical(threads, vec, donate, order, mode):
     """Item order, class order, CTA shape and donation never change the output (Sec. 8.2)."""
     w = synth.make_workload("dense_deep", D=20000)
     ms = 12000
@@ -158,9 +164,28 @@ def test_launch_shapes_and_orders_identical(threads, vec, donate, order):
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
     if order == "estimate":
         db.estimate_class_costs(0.02, 0.6, 5)
-    got = db.mine(ms, class_order=order, threads_per_cta=threads, vec_per_lane=vec, donate=donate).as_dict()
+    got = db.mine(ms, class_order=order, threads_per_cta=threads, vec_per_lane=vec, donate=donate,
+                  dfs_mode=mode).as_dict()
     db.free()
     assert_same(got, want)
+
+
+def test_work_counters_match_output_and_modes():
+    """Intersections, class nodes and materialised prefixes reported by both DFS modes equal the counts
+    derived from the oracle's output alone (bench.bitmap_work)."""
+    import bench
+    w = synth.make_workload("dense_deep", D=30000)
+    ms = 18000
+    so, si, sp = oracle.eclat(w["offsets"], w["items"], w["N"], ms)
+    order = oracle.item_order(w["offsets"], w["items"], w["N"], 0)
+    rank = np.zeros(w["N"], dtype=np.int64)
+    rank[order] = np.arange(len(order))
+    I, Cn, M = bench.bitmap_work(so, si, rank)
+    for mode in (0, 1):
+        st = gpu_mine(w["offsets"], w["items"], w["N"], ms, dfs_mode=mode).stats
+        assert st["n_intersections"] == I
+        rb = (30000 + 63) // 64 * 8
+        assert st["bytes_algorithmic"] == (I + Cn + M) * rb
 
 
 def test_prefilter_and_device_input():
@@ -192,6 +217,19 @@ def test_fixed_capacity_overflow_then_retry():
     assert_same(got, want)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_itemset_limit_aborts_early(mode):
+    """max_itemsets stops the mine once the output passes it (FIM_ERR_OUTPUT_OVERFLOW); the db stays usable."""
+    off, items = csr([list(range(20))] * 50 + [[20]])
+    db = fim.build_vertical_db(off, items, 21)
+    with pytest.raises(fim.FimError) as e:
+        db.mine(2, max_itemsets=5000, dfs_mode=mode)
+    assert e.value.status == fim.FIM_ERR_OUTPUT_OVERFLOW
+    got = db.mine(50, dfs_mode=mode).as_dict()
+    db.free()
+    assert len(got) == 2 ** 20 - 1
+
+
 def test_repeated_mines_reuse_workspace():
     w = synth.make_workload("tiny", D=8000)
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
@@ -211,7 +249,19 @@ def test_estimate_matches_oracle(name, D, rate, rel, seed):
     nfs, m, ms = db.estimate_sample_size()
     db.free()
     ocost, oorder, onfs = oracle.class_costs(w["offsets"], w["items"], w["N"], 0, rate, rel, seed)
-    assert m == math.ceil(rate * D) and nfs == onfs
+    assert m == max(math.ceil(rate * D), min(D, 738)) and nfs == onfs
+    assert np.array_equal(cost, ocost)
+    assert np.array_equal(order, oorder)
+
+
+@pytest.mark.parametrize("name,D,rate,rel,seed", [("tiny", 10000, 0.05, 0.01, 3), ("dense_deep", 20000, 0.02, 0.6, 4),
+                                                   ("sparse_mid", 50000, 0.02, 0.005, 1)])
+def test_intersection_cost_estimate_matches_oracle(name, D, rate, rel, seed):
+    w = synth.make_workload(name, D=D)
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    cost, order = db.estimate_class_costs(rate, rel, seed, cost="intersections")
+    db.free()
+    ocost, oorder, _ = oracle.class_costs(w["offsets"], w["items"], w["N"], 0, rate, rel, seed, kind=1)
     assert np.array_equal(cost, ocost)
     assert np.array_equal(order, oorder)
 

@@ -22,7 +22,9 @@ def odict(res):
 
 
 def small_requests(n):
-    reqs = synth.serving_requests(n, seed=77, D_range=(2_000, 40_000), N_range=(50, 600))
+    # the serving laws with bounded transaction lengths and minsup >= 1%: small outputs the oracle mines quickly
+    reqs = synth.serving_requests(n, seed=77, D_range=(2_000, 40_000), N_range=(50, 600), TL_range=(4.0, 12.0),
+                                  rel_range=(0.01, 0.05))
     out = []
     for r in reqs:
         off, items = synth.request_db(r)
@@ -78,4 +80,26 @@ def test_bad_job_reports_error_others_unaffected():
     res, _, _ = srv.wait(good)
     off, items, N, ms = reqs[1]
     assert res.as_dict() == odict(oracle.eclat(off, items, N, ms))
+    srv.free()
+
+
+def test_itemset_limit_stops_exploding_job():
+    """A request whose output explodes (long transactions, tiny minsup) is stopped at the per-job limit
+    with FIM_ERR_OUTPUT_OVERFLOW; the next job is unaffected."""
+    txs_len = 24
+    D = 400
+    rng = np.random.default_rng(9)
+    base = rng.choice(60, size=txs_len, replace=False)
+    off = np.arange(0, (D + 1) * txs_len, txs_len, dtype=np.uint32)
+    items = np.tile(np.sort(base), D).astype(np.uint32)  # every transaction identical: 2^24 - 1 itemsets
+    srv = fim.Server(slots=2, max_itemsets=100_000)
+    bad = srv.submit(off, items, 60, 2)
+    good_req = small_requests(1)[0]
+    good = srv.submit(*good_req)
+    with pytest.raises(fim.FimError) as e:
+        srv.wait(bad)
+    assert e.value.status == fim.FIM_ERR_OUTPUT_OVERFLOW
+    res, _, _ = srv.wait(good)
+    off2, items2, N2, ms2 = good_req
+    assert res.as_dict() == odict(oracle.eclat(off2, items2, N2, ms2))
     srv.free()

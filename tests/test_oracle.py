@@ -252,7 +252,7 @@ def _sample_brute_costs(txs, N, prefilter, rate, rel, seed):
     kept = [i for i in range(N) if supp[i] >= prefilter]
     kept.sort(key=lambda i: (supp[i], i))
     rank = {it: r for r, it in enumerate(kept)}
-    m = max(1, math.ceil(rate * D))
+    m = max(math.ceil(rate * D), min(D, math.ceil(math.log(2 / 0.05) / (2 * 0.05 ** 2))))
     ms = max(1, math.ceil(rel * m))
     sample = []
     for k in range(m):
@@ -279,6 +279,11 @@ def test_class_costs_match_independent_restatement(seed):
         assert np.array_equal(cost, want)
         keys = sorted(range(len(cost)), key=lambda r: (-cost[r], r))
         assert list(order) == keys
+
+
+def test_sample_floor_is_theorem_size():
+    """The sample is never smaller than the Theorem 6.1 size for eps = delta = 0.05 (738 rows), nor than rate * D."""
+    assert math.ceil(math.log(2 / 0.05) / (2 * 0.05 ** 2)) == 738
 
 
 def test_sample_support_within_chernoff_bound():
@@ -314,3 +319,56 @@ def test_generator_matches_stored_databases():
             continue  # the large database is checked by the GPU digest test
         w = synth.make_workload(name)
         assert synth.csr_digest(w["offsets"], w["items"]) == r["csr_sha256"], name
+
+
+def _sample_intersection_costs(txs, N, prefilter, rate, rel, seed):
+    """Counts, by running a literal Eclat on the sample in row order, the AND+popcount intersections of
+    every one-item-prefix class: level 2 tries each later frequent row, a node [X | E] tries every e in E."""
+    D = len(txs)
+    supp = np.zeros(N, dtype=np.int64)
+    for t in txs:
+        for i in set(t):
+            supp[i] += 1
+    kept = sorted([i for i in range(N) if supp[i] >= prefilter], key=lambda i: (supp[i], i))
+    rank = {it: r for r, it in enumerate(kept)}
+    m = max(math.ceil(rate * D), min(D, math.ceil(math.log(2 / 0.05) / (2 * 0.05 ** 2))))
+    ms = max(1, math.ceil(rel * m))
+    sample = []
+    for k in range(m):
+        x = oracle.splitmix64_at(seed, k)
+        sample.append({rank[i] for i in txs[((x >> 32) * D) >> 32] if i in rank})
+
+    def tids(items):
+        return {t for t, s in enumerate(sample) if items <= s}
+
+    freq = [r for r in range(len(kept)) if len(tids({r})) >= ms]
+    work = np.zeros(len(kept), dtype=np.int64)
+
+    def expand(cls, X, cands):
+        surv = []
+        for e in cands:
+            work[cls] += 1
+            if len(tids(X | {e})) >= ms:
+                surv.append(e)
+        for k, s in enumerate(surv):
+            if k + 1 < len(surv):
+                expand(cls, X | {s}, surv[k + 1:])
+
+    for pos, r in enumerate(freq):
+        expand(r, {r}, freq[pos + 1:])
+    total = work.sum()
+    return work / total if total else work.astype(float)
+
+
+@pytest.mark.parametrize("seed", [2, 5])
+def test_intersection_costs_match_literal_eclat(seed):
+    """The intersection-count class cost (kind 1) equals a literal count made by running Eclat on the sample."""
+    rng = np.random.default_rng(seed + 90)
+    N, D = 9, 250
+    txs = [list(np.nonzero(rng.random(N) < rng.uniform(0.25, 0.65))[0]) for _ in range(D)]
+    off, items = csr(txs)
+    for prefilter, rate, rel in ((0, 0.3, 0.1), (15, 0.6, 0.2)):
+        cost, order, _ = oracle.class_costs(off, items, N, prefilter, rate, rel, seed, kind=1)
+        want = _sample_intersection_costs(txs, N, prefilter, rate, rel, seed)
+        assert np.allclose(cost, want, rtol=0, atol=1e-15)
+        assert list(order) == sorted(range(len(cost)), key=lambda r: (-cost[r], r))
