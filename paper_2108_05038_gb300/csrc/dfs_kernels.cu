@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
 // entered as a frame with prefix t(X) & t({s_m}) when it has two or more
 // survivors.  No donation in this mode.
 
-constexpr uint32_t kPairBatch = 2048;
+constexpr uint32_t kPairBatch = kDfsPairBatch;
 
 __device__ __forceinline__ uint64_t pair_base(uint32_t m, uint32_t n) {
   // pairs of children before child m in a frame of n items: sum_{k<m} (n - 1 - k)
@@ -736,9 +736,9 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
   uint32_t* xid = sp;
 
   // arena: [root list 2*n1] then per depth [prefix stride][G 2*(kPairBatch+n1)][child table 2*kPairBatch]
-  const uint64_t root_words = (2ull * p.n1 + 3) & ~3ull;
-  const uint64_t g_words = 2ull * (kPairBatch + p.n1);
-  const uint64_t per_depth = (uint64_t)p.stride + g_words + 2ull * kPairBatch;
+  const uint64_t root_words = frames_root_words(p.n1);
+  const uint64_t g_words = frames_g_words(p.n1);
+  const uint64_t per_depth = frames_depth_words(p.stride, p.n1);
   uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
   uint32_t* const root_list = arena;
 #define fr_pre(d) (arena + root_words + (size_t)(d) * per_depth)
@@ -1034,9 +1034,13 @@ cudaError_t allow_max_smem(const void* func) {
   for (const void* f : done)
     if (f == func) return cudaSuccess;
   int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  // static shared memory counts against the same per-block limit
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess) done.push_back(func);
   return e;
 }
@@ -1121,11 +1125,7 @@ bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint3
 }
 
 uint64_t dfs_arena_cta_words(uint32_t stride, uint32_t n1, uint32_t maxd, uint32_t mode) {
-  if (mode == 1) {
-    const uint64_t root_words = (2ull * n1 + 3) & ~3ull;
-    const uint64_t per_depth = (uint64_t)stride + 2ull * (kPairBatch + n1) + 2ull * kPairBatch;
-    return root_words + per_depth * (maxd + 1);
-  }
+  if (mode == 1) return frames_root_words(n1) + frames_depth_words(stride, n1) * (maxd + 1);
   return dfs_arena_depth_words(stride, n1) * (maxd + 1);
 }
 

@@ -368,6 +368,15 @@ constexpr uint32_t kDfsSlotHeader = 4;  // donation pool slot: sequence, xlen, n
 __host__ __device__ inline uint64_t dfs_pool_slot_words(uint32_t stride, uint32_t max_len, uint32_t n1) {
   return (((uint64_t)kDfsSlotHeader + 2ull * max_len + 2ull * n1 + 3) & ~3ull) + stride;
 }
+// frame mode (all children of a frame counted together): pairs per pass, and the
+// stack layout [root list][per depth: prefix | survivor area | child table], every
+// region a multiple of four words so that prefix bitmaps stay 16-byte aligned
+constexpr uint32_t kDfsPairBatch = 2048;
+__host__ __device__ inline uint64_t frames_root_words(uint32_t n1) { return (2ull * n1 + 3) & ~3ull; }
+__host__ __device__ inline uint64_t frames_g_words(uint32_t n1) { return (2ull * (kDfsPairBatch + n1) + 3) & ~3ull; }
+__host__ __device__ inline uint64_t frames_depth_words(uint32_t stride, uint32_t n1) {
+  return (uint64_t)stride + frames_g_words(n1) + 2ull * kDfsPairBatch;
+}
 // arena words per depth: one prefix bitmap + one (row, id) survivor list
 __host__ __device__ inline uint64_t dfs_arena_depth_words(uint32_t stride, uint32_t n1) { return (uint64_t)stride + ((2ull * n1 + 3) & ~3ull); }
 
