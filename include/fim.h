@@ -152,7 +152,9 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
  * x_k = k-th output of SplitMix64 started at state `seed`.  D_s (kept items
  * only) is mined on the GPU at minsup_s = max(1, ceil(rel_minsup * m)) and
  * cost_out[r] = |{X in F_s : the lowest row of X is r}| / |F_s| (0 when F_s is
- * empty).  order_out = rows by descending cost, ties by ascending row (the
+ * empty).  While D_s has more than FIM_SAMPLE_ITEMSET_LIMIT frequent itemsets
+ * at minsup_s, minsup_s doubles (the thesis does not treat a sample whose
+ * itemsets explode; this keeps the estimate's cost bounded).  order_out = rows by descending cost, ties by ascending row (the
  * LPT order, Sec. 8.2).  Both arrays have n_rows entries (host memory).
  * The estimate is kept in the db and orders the classes of later fim_mine
  * calls (FIM_ORDER_ESTIMATE); it never changes their output.
@@ -162,6 +164,9 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
 fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
                                     double* cost_out, uint32_t* order_out);
 
+/* Default bound on the sample's frequent itemsets (see above). */
+#define FIM_SAMPLE_ITEMSET_LIMIT (1ull << 20)
+
 /* Cost measure of a class in the estimate. */
 typedef enum {
   FIM_COST_ITEMSETS = 0,     /* #frequent itemsets of the sample in the class (the thesis's measure, Sec. 8.2) */
@@ -170,13 +175,17 @@ typedef enum {
                                 candidate of every node below it; proportional to its GPU work            */
 } fim_cost_kind;
 
-/* fim_estimate_class_costs with a choice of cost measure (fim_cost_kind);
- * fim_estimate_class_costs is this call with FIM_COST_ITEMSETS.  Costs are
- * shares of the total (sum 1 unless the sample has no frequent item). */
+/* fim_estimate_class_costs with a choice of cost measure (fim_cost_kind) and
+ * of the bound on the sample's itemsets (0 = no bound: the sample is mined at
+ * minsup_s whatever its output); fim_estimate_class_costs is this call with
+ * FIM_COST_ITEMSETS and FIM_SAMPLE_ITEMSET_LIMIT.  Costs are shares of the
+ * total (sum 1 unless the sample has no frequent item). */
 fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
-                                       uint32_t cost_kind, double* cost_out, uint32_t* order_out);
+                                       uint32_t cost_kind, uint64_t max_sample_itemsets, double* cost_out,
+                                       uint32_t* order_out);
 
-/* Number of frequent itemsets found in the sample by the last estimate. */
+/* Number of frequent itemsets found in the sample by the last estimate, the
+ * sample's size and the sample minsup it was mined at (after any doubling). */
 fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, uint32_t* sample_rows,
                                     uint32_t* sample_minsup);
 

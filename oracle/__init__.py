@@ -66,6 +66,9 @@ def _load():
             lib.oracle_class_costs_kind.restype = ctypes.c_int
             lib.oracle_class_costs_kind.argtypes = [P, P, u32, u32, u32, dbl, dbl, u64, ctypes.c_int, P, P,
                                                     ctypes.POINTER(u32), ctypes.POINTER(u64)]
+            lib.oracle_class_costs_limit.restype = ctypes.c_int
+            lib.oracle_class_costs_limit.argtypes = [P, P, u32, u32, u32, dbl, dbl, u64, ctypes.c_int, u64, P, P,
+                                                     ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)]
             lib.oracle_splitmix64_at.restype = u64
             lib.oracle_splitmix64_at.argtypes = [u64, u64]
             _lib = lib
@@ -155,22 +158,30 @@ def item_order(offsets, items, N: int, prefilter_minsup: int = 0):
     return out[: nk.value]
 
 
-def class_costs(offsets, items, N: int, prefilter_minsup: int, sample_rate: float, rel_minsup: float, seed: int,
-                kind: int = 0):
-    """Sample-based relative class sizes and their LPT order; returns (cost f64[N_f], order u32[N_f], |F_s|).
+SAMPLE_ITEMSET_LIMIT = 1 << 20
 
-    kind 0: share of the sample's frequent itemsets; kind 1: share of the bitmap intersections."""
+
+def class_costs(offsets, items, N: int, prefilter_minsup: int, sample_rate: float, rel_minsup: float, seed: int,
+                kind: int = 0, limit: int = SAMPLE_ITEMSET_LIMIT, return_minsup: bool = False):
+    """Sample-based relative class sizes and their LPT order; returns (cost f64[N_f], order u32[N_f], |F_s|)
+    (plus the sample minsup used when ``return_minsup``).
+
+    kind 0: share of the sample's frequent itemsets; kind 1: share of the bitmap intersections.
+    While the sample has more than ``limit`` frequent itemsets (0: no limit) its minsup doubles."""
     lib = _load()
     offsets, items = _csr(offsets, items)
     cost = np.zeros(max(N, 1), dtype=np.float64)
     order = np.zeros(max(N, 1), dtype=np.uint32)
     nk = ctypes.c_uint32(0)
     nfs = ctypes.c_uint64(0)
-    rc = lib.oracle_class_costs_kind(offsets.ctypes.data, items.ctypes.data, offsets.size - 1, N, prefilter_minsup,
-                                     sample_rate, rel_minsup, seed, kind, cost.ctypes.data, order.ctypes.data,
-                                     ctypes.byref(nk), ctypes.byref(nfs))
+    ms = ctypes.c_uint32(0)
+    rc = lib.oracle_class_costs_limit(offsets.ctypes.data, items.ctypes.data, offsets.size - 1, N, prefilter_minsup,
+                                      sample_rate, rel_minsup, seed, kind, limit, cost.ctypes.data, order.ctypes.data,
+                                      ctypes.byref(nk), ctypes.byref(nfs), ctypes.byref(ms))
     if rc != 0:
         raise ValueError(f"class_costs failed {rc}")
+    if return_minsup:
+        return cost[: nk.value], order[: nk.value], nfs.value, ms.value
     return cost[: nk.value], order[: nk.value], nfs.value
 
 

@@ -179,6 +179,7 @@ static void tl_free(tidlists* t) { free(t->off); free(t->tids); }
 
 static int tl_build(tidlists* t, const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N) {
   t->N = N;
+  t->tids = NULL;
   t->off = (uint64_t*)calloc((size_t)N + 1, sizeof(uint64_t));
   uint32_t* last = (uint32_t*)malloc(sizeof(uint32_t) * (N ? N : 1));
   if (!t->off || !last) { free(last); return -1; }
@@ -227,7 +228,8 @@ typedef struct {
   uint32_t minsup;
   uint32_t* prefix; /* current P, up to depth */
   or_result* out;
-  int err;
+  int err;          /* -1 allocation failure, 1 more than `limit` itemsets */
+  uint64_t limit;   /* 0 = none */
 } eclat_ctx;
 
 /* Eclat-DFS-Computation(A, P): A holds atoms a with t(P u {a}); every atom is
@@ -247,6 +249,7 @@ static void eclat_rec(eclat_ctx* c, atom* A, uint32_t nA, uint32_t depth) {
         Ai[nAi].item = A[j].item; Ai[nAi].n = n; Ai[nAi].tids = buf; ++nAi;
         c->prefix[depth + 1] = A[j].item;
         if (res_add(c->out, c->prefix, depth + 2, n) != 0) { c->err = -1; break; }
+        if (c->limit && c->out->n_sets > c->limit) { c->err = 1; break; }
       } else {
         free(buf);
       }
@@ -257,10 +260,12 @@ static void eclat_rec(eclat_ctx* c, atom* A, uint32_t nA, uint32_t depth) {
   }
 }
 
-/* Eclat-DFS(D, minsupp, F): returns 0 on success, -2 on an item id >= N,
- * -3 on minsup == 0, -1 on allocation failure. Items are visited in id order. */
-int oracle_eclat(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t minsup,
-                 or_result** out) {
+/* Eclat-DFS(D, minsupp, F) that gives up once F holds more than `limit`
+ * itemsets (limit 0: never): returns 0 on success, 1 when |F| > limit, -2 on an
+ * item id >= N, -3 on minsup == 0, -1 on allocation failure. Items are visited
+ * in id order. */
+static int eclat_limited(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t minsup,
+                         uint64_t limit, or_result** out) {
   *out = NULL;
   if (minsup == 0) return -3;
   tidlists t;
@@ -276,9 +281,10 @@ int oracle_eclat(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_
     if (n >= minsup) {
       A[nA].item = it; A[nA].n = n; A[nA].tids = t.tids + t.off[it]; ++nA;
       if (res_add(r, &it, 1, n) != 0) { rc = -1; break; }
+      if (limit && r->n_sets > limit) { rc = 1; break; }
     }
   }
-  eclat_ctx c = {minsup, prefix, r, 0};
+  eclat_ctx c = {minsup, prefix, r, 0, limit};
   if (rc == 0) {
     /* top-level atoms point into the tidlist table, which eclat_rec never frees */
     eclat_rec(&c, A, nA, 0);
@@ -288,6 +294,11 @@ int oracle_eclat(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_
   if (rc != 0) { oracle_result_free(r); return rc; }
   *out = r;
   return 0;
+}
+
+int oracle_eclat(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t minsup,
+                 or_result** out) {
+  return eclat_limited(off, items, D, N, minsup, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -572,7 +583,10 @@ done:
 /* draw k uses the SplitMix64 output x_k = mix(seed + (k + 1) * gamma) (the   */
 /* k-th output of the stream started at state seed; Steele et al. 2014) and   */
 /* the transaction index ((x_k >> 32) * D) >> 32.  The sample keeps only the   */
-/* kept items and is mined at minsup_s = max(1, ceil(rel_minsup * m)).        */
+/* kept items and is mined at minsup_s = max(1, ceil(rel_minsup * m)); while   */
+/* the sample then has more than `limit` frequent itemsets (limit 0: never),  */
+/* minsup_s doubles (a reading: the thesis does not treat a sample whose      */
+/* itemsets explode; a coarser threshold keeps the estimate's cost bounded).  */
 /* cost[r] = #{X in F_s : the first item of X in the class order is rank r}   */
 /*           / |F_s|  (0 when F_s is empty);  order = ranks by cost desc,     */
 /* ties by rank asc (LPT order, Sec. 8.2).                                    */
@@ -637,9 +651,10 @@ static int cmp_len_seq(const void* a, const void* b) {
  * sample FI P whose first row is r, k_P (k_P - 1) / 2 where k_P is the number
  * of sample FIs P u {e} with e after P's last row (each child P u {e_k} of P
  * is intersected with the later survivors of P). */
-int oracle_class_costs_kind(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t prefilter_minsup,
-                            double sample_rate, double rel_minsup, uint64_t seed, int kind, double* cost_out,
-                            uint32_t* order_out, uint32_t* n_kept_out, uint64_t* n_sample_fis) {
+int oracle_class_costs_limit(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N,
+                             uint32_t prefilter_minsup, double sample_rate, double rel_minsup, uint64_t seed, int kind,
+                             uint64_t limit, double* cost_out, uint32_t* order_out, uint32_t* n_kept_out,
+                             uint64_t* n_sample_fis, uint32_t* minsup_used) {
   if (!(sample_rate > 0.0 && sample_rate <= 1.0) || !(rel_minsup >= 0.0 && rel_minsup <= 1.0) || D == 0) return -3;
   uint32_t* rank_item = (uint32_t*)malloc(sizeof(uint32_t) * (N ? N : 1));
   int32_t* rank_of = (int32_t*)malloc(sizeof(int32_t) * (N ? N : 1));
@@ -674,8 +689,14 @@ int oracle_class_costs_kind(const uint32_t* off, const uint32_t* items, uint32_t
     soff[k + 1] = (uint32_t)nnz;
   }
   or_result* fs = NULL;
-  int rc = oracle_eclat(soff, sit, (uint32_t)m, N, minsup_s, &fs);
+  int rc;
+  for (;;) {
+    rc = eclat_limited(soff, sit, (uint32_t)m, N, minsup_s, limit, &fs);
+    if (rc != 1) break;
+    minsup_s = minsup_s > UINT32_MAX / 2 ? UINT32_MAX : 2 * minsup_s;
+  }
   free(soff); free(sit);
+  if (minsup_used) *minsup_used = minsup_s;
   if (rc != 0) { free(rank_item); free(rank_of); return rc; }
   uint64_t* cnt = (uint64_t*)calloc(nk ? nk : 1, sizeof(uint64_t));
   uint32_t* ord = (uint32_t*)malloc(sizeof(uint32_t) * (nk ? nk : 1));
@@ -741,6 +762,13 @@ int oracle_class_costs_kind(const uint32_t* off, const uint32_t* items, uint32_t
   *n_sample_fis = fs->n_sets;
   free(cnt); free(ord); free(rank_item); free(rank_of); oracle_result_free(fs);
   return 0;
+}
+
+int oracle_class_costs_kind(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t prefilter_minsup,
+                            double sample_rate, double rel_minsup, uint64_t seed, int kind, double* cost_out,
+                            uint32_t* order_out, uint32_t* n_kept_out, uint64_t* n_sample_fis) {
+  return oracle_class_costs_limit(off, items, D, N, prefilter_minsup, sample_rate, rel_minsup, seed, kind,
+                                  (uint64_t)1 << 20, cost_out, order_out, n_kept_out, n_sample_fis, NULL);
 }
 
 int oracle_class_costs(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t prefilter_minsup,

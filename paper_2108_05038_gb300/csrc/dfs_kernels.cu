@@ -519,10 +519,12 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
     }
 
     // ---------------- depth-first expansion ----------------
-    uint32_t cool = 0;
+    uint32_t cool = 0, poll = 0;
     for (;;) {
       __syncthreads();  // every thread has read the previous decision
       if (threadIdx.x == 0) {
+        // a run past the itemset limit unwinds at once (every 8th node looks at the flag)
+        if (C.depth >= 0 && (++poll & 7) == 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
         const int32_t d = C.depth;
         C.action = 0;
         if (d < 0) {

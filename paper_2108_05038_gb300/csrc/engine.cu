@@ -174,7 +174,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
   std::memcpy(&h, hstage, sizeof(DevCtrl));
   out->ctrl = h;
   if (h.err & DEV_ERR_TIMEOUT) return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
-  if (h.err & DEV_ERR_ABORTED)
+  if ((h.err & DEV_ERR_ABORTED) || (ep->max_sets && h.sets_total > ep->max_sets))
     return fail(FIM_ERR_OUTPUT_OVERFLOW, "more frequent itemsets than the limit: mining stopped early (counts are lower bounds)");
   if (h.err & DEV_ERR_DEPTH) {
     if (ep->maxd >= ep->maxd_full) return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");

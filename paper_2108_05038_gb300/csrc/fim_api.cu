@@ -466,11 +466,13 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
 
 fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
                                     double* cost_out, uint32_t* order_out) {
-  return fim_estimate_class_costs_ex(db, sample_rate, rel_minsup, seed, FIM_COST_ITEMSETS, cost_out, order_out);
+  return fim_estimate_class_costs_ex(db, sample_rate, rel_minsup, seed, FIM_COST_ITEMSETS, FIM_SAMPLE_ITEMSET_LIMIT,
+                                     cost_out, order_out);
 }
 
 fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
-                                       uint32_t cost_kind, double* cost_out, uint32_t* order_out) {
+                                       uint32_t cost_kind, uint64_t max_sample_itemsets, double* cost_out,
+                                       uint32_t* order_out) {
   if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
   if (cost_kind != FIM_COST_ITEMSETS && cost_kind != FIM_COST_INTERSECTIONS)
     return fail(FIM_ERR_INVALID, "unknown cost kind");
@@ -483,7 +485,7 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   md = std::max(md, std::min((double)db->D, m0));
   const uint32_t m = md < 1.0 ? 1u : (uint32_t)md;
   const double msd = std::ceil(rel_minsup * (double)m);
-  const uint32_t minsup_s = msd < 1.0 ? 1u : (uint32_t)msd;
+  uint32_t minsup_s = msd < 1.0 ? 1u : (uint32_t)msd;
   const uint32_t sw = (m + 31) / 32, sstride = ((sw + 31) / 32) * 32;
   const uint32_t R = db->n_rows;
   uint32_t *d_sbits = nullptr, *d_ssupp = nullptr;
@@ -501,30 +503,40 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
     std::memcpy(ssupp.data(), h, (size_t)R * 4);
   }
   EngineInput in;
-  in.bits = d_sbits;
-  in.stride = sstride;
-  in.bytes_per_row_alg = (uint32_t)(((uint64_t)m + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
-  for (uint32_t r = 0; r < R; ++r)
-    if (ssupp[r] >= minsup_s) {
-      in.frows.push_back(r);
-      in.row_supp.push_back(ssupp[r]);
-    }
-  in.n1 = (uint32_t)in.frows.size();
-  in.row_order.resize(in.n1);
-  std::iota(in.row_order.begin(), in.row_order.end(), 0u);
-  in.identity_order = true;
-  in.d_rank_item = db->d_rank_item;
-  in.minsup = minsup_s;
-  in.max_len_bound = db->max_tx_len;
-  EngineConfig cfg;
-  cfg.donate = 0;
-  unsigned long long* d_work = nullptr;
-  if (cost_kind == FIM_COST_INTERSECTIONS && in.n1) {
-    FIM_TRY(ws_get(db->ws, WS_CLASSWORK, in.n1, &d_work));
-    cfg.class_work = d_work;
-  }
   EngineOutput eo;
-  FIM_TRY(engine_mine(db, db->ws, in, cfg, &eo, nullptr));
+  unsigned long long* d_work = nullptr;
+  for (;;) {  // minsup_s doubles while the sample has more than max_sample_itemsets frequent itemsets
+    in = EngineInput{};
+    in.bits = d_sbits;
+    in.stride = sstride;
+    in.bytes_per_row_alg = (uint32_t)(((uint64_t)m + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
+    for (uint32_t r = 0; r < R; ++r)
+      if (ssupp[r] >= minsup_s) {
+        in.frows.push_back(r);
+        in.row_supp.push_back(ssupp[r]);
+      }
+    in.n1 = (uint32_t)in.frows.size();
+    in.row_order.resize(in.n1);
+    std::iota(in.row_order.begin(), in.row_order.end(), 0u);
+    in.identity_order = true;
+    in.d_rank_item = db->d_rank_item;
+    in.minsup = minsup_s;
+    in.max_len_bound = db->max_tx_len;
+    EngineConfig cfg;
+    cfg.donate = 0;
+    cfg.max_sets = max_sample_itemsets;
+    if (cost_kind == FIM_COST_INTERSECTIONS && in.n1) {
+      FIM_TRY(ws_get(db->ws, WS_CLASSWORK, in.n1, &d_work));
+      cfg.class_work = d_work;
+    }
+    eo = EngineOutput{};
+    const fim_status s = engine_mine(db, db->ws, in, cfg, &eo, nullptr);
+    if (s == FIM_OK) break;
+    const bool over = max_sample_itemsets &&
+                      ((eo.ctrl.err & DEV_ERR_ABORTED) || eo.ctrl.sets_total > max_sample_itemsets);
+    if (!over || minsup_s == UINT32_MAX) return s;
+    minsup_s = minsup_s > UINT32_MAX / 2 ? UINT32_MAX : 2 * minsup_s;
+  }
   std::vector<unsigned long long> tally(R, 0ull);
   if (cost_kind == FIM_COST_INTERSECTIONS) {
     // intersections per class: level 2 (the later frequent sample rows) + the DFS below it

@@ -17,6 +17,7 @@ from . import _build
 
 FIM_OK, FIM_ERR_INVALID, FIM_ERR_OOM, FIM_ERR_OUTPUT_OVERFLOW, FIM_ERR_CUDA, FIM_ERR_TIMEOUT = range(6)
 FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
+SAMPLE_ITEMSET_LIMIT = 1 << 20  # FIM_SAMPLE_ITEMSET_LIMIT
 
 # every symbol declared in include/fim.h
 EXPORTED = [
@@ -100,7 +101,7 @@ def load(build_if_stale: bool = True):
         lib.fim_estimate_class_costs.restype = i32
         lib.fim_estimate_class_costs.argtypes = [P, dbl, dbl, u64, P, P]
         lib.fim_estimate_class_costs_ex.restype = i32
-        lib.fim_estimate_class_costs_ex.argtypes = [P, dbl, dbl, u64, u32, P, P]
+        lib.fim_estimate_class_costs_ex.argtypes = [P, dbl, dbl, u64, u32, u64, P, P]
         lib.fim_estimate_sample_size.restype = i32
         lib.fim_estimate_sample_size.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.fim_mine.restype = i32
@@ -240,14 +241,17 @@ class Database:
         _check(self._lib, self._lib.fim_db_rows(self._h, ri.ctypes.data, sp.ctypes.data), "fim_db_rows")
         return ri[:n], sp[:n]
 
-    def estimate_class_costs(self, sample_rate: float, rel_minsup: float, seed: int, cost: str = "itemsets"):
-        """fim_estimate_class_costs(_ex): cost "itemsets" (the thesis's measure) or "intersections"."""
+    def estimate_class_costs(self, sample_rate: float, rel_minsup: float, seed: int, cost: str = "itemsets",
+                             max_sample_itemsets: int = SAMPLE_ITEMSET_LIMIT):
+        """fim_estimate_class_costs_ex: cost "itemsets" (the thesis's measure) or "intersections"; the sample
+        minsup doubles while the sample has more than ``max_sample_itemsets`` frequent itemsets (0: never)."""
         n = self.info()["n_rows"]
         c = np.zeros(max(n, 1), dtype=np.float64)
         order = np.zeros(max(n, 1), dtype=np.uint32)
         kind = {"itemsets": 0, "intersections": 1}[cost]
         _check(self._lib, self._lib.fim_estimate_class_costs_ex(self._h, sample_rate, rel_minsup, seed, kind,
-                                                                c.ctypes.data, order.ctypes.data),
+                                                                max_sample_itemsets, c.ctypes.data,
+                                                                order.ctypes.data),
                "fim_estimate_class_costs_ex")
         return c[:n], order[:n]
 

@@ -6,6 +6,7 @@ as canonical dictionaries (items ascending inside a set).
 """
 import json
 import math
+import time
 import os
 
 import numpy as np
@@ -264,6 +265,50 @@ def test_intersection_cost_estimate_matches_oracle(name, D, rate, rel, seed):
     ocost, oorder, _ = oracle.class_costs(w["offsets"], w["items"], w["N"], 0, rate, rel, seed, kind=1)
     assert np.array_equal(cost, ocost)
     assert np.array_equal(order, oorder)
+
+
+@pytest.mark.parametrize("rel,limit,kind", [(0.2, 20000, "itemsets"), (0.3, 20000, "intersections"),
+                                            (0.45, 300, "itemsets"), (0.6, 0, "intersections")])
+def test_estimate_sample_limit_matches_oracle(rel, limit, kind):
+    """The sample minsup doubles while the sample has more than `limit` frequent itemsets, as in the oracle
+    (dense_deep, 8,000 rows: 148 -> 592, 222 -> 444, 333 -> 666, and no limit at 443)."""
+    w = synth.make_workload("dense_deep", D=8000)
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    cost, order = db.estimate_class_costs(0.05, rel, 11, cost=kind, max_sample_itemsets=limit)
+    nfs, m, ms = db.estimate_sample_size()
+    db.free()
+    k = {"itemsets": 0, "intersections": 1}[kind]
+    ocost, oorder, onfs, oms = oracle.class_costs(w["offsets"], w["items"], w["N"], 0, 0.05, rel, 11, kind=k,
+                                                  limit=limit, return_minsup=True)
+    assert (nfs, ms) == (onfs, oms)
+    assert np.array_equal(cost, ocost)
+    assert np.array_equal(order, oorder)
+
+
+def test_estimate_of_exploding_sample_is_bounded():
+    """minsup 0.1% on 30-of-100-item transactions, 30% of them holding an 18-item core: at the start
+    minsup (1) the sample's itemsets explode; the limit doubles the sample minsup until the sample mines
+    within it.  Limit 2^16: parity with the oracle (1 -> 256, 128 itemsets); default limit: bounded time."""
+    rng = np.random.default_rng(3)
+    N, D = 100, 20000
+    txs = [list(rng.choice(N, size=30, replace=False)) for _ in range(D)]
+    for t in txs[: int(D * 0.3)]:
+        t[:] = sorted(set(t) | set(range(18)))
+    off, items = csr(txs)
+    db = fim.build_vertical_db(off, items, N)
+    cost, order = db.estimate_class_costs(0.01, 0.001, 2, max_sample_itemsets=1 << 16)
+    nfs, m, ms = db.estimate_sample_size()
+    ocost, oorder, onfs, oms = oracle.class_costs(off, items, N, 0, 0.01, 0.001, 2, limit=1 << 16,
+                                                  return_minsup=True)
+    assert (nfs, ms) == (onfs, oms) and ms > 1
+    assert np.array_equal(cost, ocost) and np.array_equal(order, oorder)
+    t0 = time.perf_counter()
+    db.estimate_class_costs(0.01, 0.001, 2)
+    dt = time.perf_counter() - t0
+    nfs, m, ms = db.estimate_sample_size()
+    db.free()
+    assert nfs <= fim.SAMPLE_ITEMSET_LIMIT and ms > 1
+    assert dt < 20.0
 
 
 def test_row_order_matches_oracle():

@@ -242,8 +242,9 @@ def test_splitmix64_published_stream():
 
 # ---------------------------------------------------------------- class-cost estimate
 
-def _sample_brute_costs(txs, N, prefilter, rate, rel, seed):
-    """Estimate written out independently: sample by SplitMix64, brute-force mine, tally by first rank."""
+def _sample_brute_costs(txs, N, prefilter, rate, rel, seed, limit=0, return_minsup=False):
+    """Estimate written out independently: sample by SplitMix64, brute-force mine, tally by first rank;
+    the sample minsup doubles while the sample has more than ``limit`` frequent itemsets."""
     D = len(txs)
     supp = np.zeros(N, dtype=np.int64)
     for t in txs:
@@ -259,10 +260,15 @@ def _sample_brute_costs(txs, N, prefilter, rate, rel, seed):
         x = oracle.splitmix64_at(seed, k)
         sample.append([i for i in txs[((x >> 32) * D) >> 32] if i in rank])
     fs = brute_dict(sample, N, ms)
+    while limit and len(fs) > limit:
+        ms *= 2
+        fs = brute_dict(sample, N, ms)
     cnt = np.zeros(len(kept), dtype=np.int64)
     for s in fs:
         cnt[min(rank[i] for i in s)] += 1
     cost = cnt / len(fs) if fs else cnt.astype(float)
+    if return_minsup:
+        return cost, len(fs), ms
     return cost, len(fs)
 
 
@@ -279,6 +285,25 @@ def test_class_costs_match_independent_restatement(seed):
         assert np.array_equal(cost, want)
         keys = sorted(range(len(cost)), key=lambda r: (-cost[r], r))
         assert list(order) == keys
+
+
+@pytest.mark.parametrize("limit", [1, 40, 150, 1023])
+def test_class_costs_sample_limit_doubles_minsup(limit):
+    """A sample with more than `limit` frequent itemsets is mined again at twice the minsup until it has no more."""
+    rng = np.random.default_rng(7)
+    N, D = 10, 400
+    txs = [list(np.nonzero(rng.random(N) < 0.55)[0]) for _ in range(D)]
+    off, items = csr(txs)
+    cost, order, nfs, ms = oracle.class_costs(off, items, N, 0, 1.0, 0.01, 5, limit=limit, return_minsup=True)
+    want, nfs2, ms2 = _sample_brute_costs(txs, N, 0, 1.0, 0.01, 5, limit=limit, return_minsup=True)
+    assert (nfs, ms) == (nfs2, ms2)
+    assert nfs <= limit
+    assert np.array_equal(cost, want)
+    if limit < 1023:  # minsup 4 (= ceil(0.01 * 400)) keeps almost every subset of 10 dense items
+        assert ms > 4
+    # limit 0: no doubling
+    _, _, nfs0, ms0 = oracle.class_costs(off, items, N, 0, 1.0, 0.01, 5, limit=0, return_minsup=True)
+    assert ms0 == 4 and nfs0 == _sample_brute_costs(txs, N, 0, 1.0, 0.01, 5)[1]
 
 
 def test_sample_floor_is_theorem_size():
