@@ -313,6 +313,12 @@ const char* fim_status_str(fim_status s);
 /* Description of the last error on the calling thread ("" if none). */
 const char* fim_last_error(void);
 
+/* Kernels this library has put on a stream since it was loaded, all threads
+ * together: every kernel launch, and for a plan every kernel of its graph at
+ * each fim_plan_launch (the launches recorded while capturing it do not
+ * count).  Kernels run by other libraries (memsets, copies) are not counted. */
+uint64_t fim_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

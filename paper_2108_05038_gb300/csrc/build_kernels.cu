@@ -137,6 +137,7 @@ cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32
   // with a shared histogram every CTA flushes N counters: keep the grid modest
   uint32_t grid = grid_for(D, threads, N <= kSmemHistMax ? 152 * 4 : 152 * 32);
   k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, err, max_len);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -144,6 +145,7 @@ cudaError_t launch_bitmap_build(const uint32_t* off, const uint32_t* items, uint
                                 uint32_t* bits, uint32_t stride, cudaStream_t st) {
   const uint32_t threads = 256;
   k_bitmap_build<<<grid_for(D, threads), threads, 0, st>>>(off, items, D, item_rank, bits, stride);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -151,12 +153,14 @@ cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint
                                 uint64_t seed, uint32_t m, uint32_t* sbits, uint32_t sstride, cudaStream_t st) {
   const uint32_t threads = 256;
   k_sample_build<<<grid_for(m, threads), threads, 0, st>>>(off, items, D, item_rank, seed, m, sbits, sstride);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_iota<<<grid_for(n, 256), 256, 0, st>>>(out, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -164,6 +168,7 @@ cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t 
                                 cudaStream_t st) {
   if (n_rows == 0) return cudaSuccess;
   k_row_popcount<<<n_rows, 256, 0, st>>>(bits, stride, supp);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -172,6 +177,7 @@ cudaError_t launch_tally_min_rank(const uint64_t* set_off, const uint32_t* set_i
   if (n_sets == 0) return cudaSuccess;
   const uint32_t threads = 256;
   k_tally_min_rank<<<grid_for(n_sets, threads), threads, 0, st>>>(set_off, set_items, n_sets, item_rank, tally);
+  note_launch();
   return cudaGetLastError();
 }
 

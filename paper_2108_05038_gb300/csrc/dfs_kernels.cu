@@ -1052,6 +1052,7 @@ cudaError_t launch_dfs_t(const DfsArgs& a, uint32_t grid, uint32_t threads, size
   cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs<VEC, PSMEM>));
   if (e != cudaSuccess) return e;
   k_dfs<VEC, PSMEM><<<grid, threads, smem, st>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1071,6 +1072,7 @@ cudaError_t launch_frames_t(const DfsArgs& a, uint32_t grid, uint32_t threads, s
   cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_frames<VEC, PSMEM>));
   if (e != cudaSuccess) return e;
   k_dfs_frames<VEC, PSMEM><<<grid, threads, smem, st>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1104,14 +1106,17 @@ cudaError_t occ_t(uint32_t threads, size_t smem, int* out) {
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   if (p.n1 == 0) return cudaSuccess;
   k_surv_count<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.scnt);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_level2_scan<<<1, 1024, 0, st>>>(p.scnt, p.row_order, p.n1, p.soff, p.eoff, p.cap_sets, p.cap_items, p.ctrl);
+  note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_level2_fill<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.frows, p.row_supp, p.rank_item, p.row_order, p.scnt,
                                       p.soff, p.eoff, p.sitems, p.entries, p.out_off, p.out_items, p.out_supp,
                                       p.cap_sets, p.cap_items);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1168,6 +1173,7 @@ cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, boo
 cudaError_t launch_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words, cudaStream_t st) {
   if (slots == 0) return cudaSuccess;
   k_pool_init<<<(slots + 255) / 256, 256, 0, st>>>(pool, slots, slot_words);
+  note_launch();
   return cudaGetLastError();
 }
 

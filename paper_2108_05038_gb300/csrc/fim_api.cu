@@ -1,6 +1,7 @@
 // C ABI of the miner (include/fim.h): database build, sample-based class-cost
 // estimate, mining engine orchestration and result handling.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -13,6 +14,10 @@
 namespace fim {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 fim_status fail(fim_status s, const std::string& msg) {
@@ -433,6 +438,8 @@ const char* fim_status_str(fim_status s) {
 }
 
 const char* fim_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t fim_kernel_launches(void) { return launches_so_far(); }
 
 fim_status fim_build_vertical_db(const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D, uint32_t N,
                                  uint32_t word_bits, uint32_t prefilter_minsup, void* cuda_stream, fim_db** out) {

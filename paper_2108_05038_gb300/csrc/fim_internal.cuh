@@ -12,6 +12,10 @@
 
 namespace fim {
 
+// kernels put on a stream by this library (fim_kernel_launches)
+void note_launch(uint64_t n = 1);
+uint64_t launches_so_far();
+
 // ---------------------------------------------------------------------------
 // error reporting
 

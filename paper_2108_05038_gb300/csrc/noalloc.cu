@@ -98,11 +98,13 @@ extern "C" fim_status fim_mine_pairs_noalloc(const fim_db* db, uint32_t minsup_a
   // the previous call's counter is still in the array: clear it
   FIM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   k_rows_iota<<<(n1 + 255) / 256, 256, 0, st>>>(frows, r0, n1);
+  note_launch();
   FIM_CUDA(cudaGetLastError());
   uint32_t ksplit = 0;
   PairLaunch pl{db->d_bits, db->stride, frows, n1, C2, 0};
   FIM_CUDA(launch_pair_counts(pl, db->num_sms, st, &ksplit));  // clears C2 itself when it splits rows
   k_pairs_emit<<<n1, 256, 0, st>>>(C2, n1, minsup_abs, r0, db->d_rank_item, d_pairs, d_supports, capacity, counter);
+  note_launch();
   FIM_CUDA(cudaGetLastError());
   unsigned long long found = 0;
   FIM_CUDA(cudaMemcpyAsync(&found, counter, sizeof(found), cudaMemcpyDeviceToHost, st));

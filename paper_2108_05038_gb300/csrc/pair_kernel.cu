@@ -183,6 +183,7 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
   const uint32_t grid = n_items < slots ? n_items : slots;
   k_pair_counts<<<grid, kThreads, kSmemBytes, st>>>(p.bits, p.stride, p.frows, p.n1, nb, cps, nchunks, p.C2, ksplit,
                                                      n_items, 1u);
+  note_launch();
   return cudaGetLastError();
 }
 

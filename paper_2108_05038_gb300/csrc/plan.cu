@@ -24,6 +24,7 @@ struct fim_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t launches = 0;
+  uint64_t kernels = 0;  // kernels in the graph
 };
 
 namespace fim {
@@ -142,7 +143,11 @@ fim_status fim_plan_create(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts,
   plan->ep.fixed_capacity = true;
   cudaError_t e = cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamBeginCapture"));
+  const uint64_t before = launches_so_far();
   cudaError_t le = engine_launch(plan->ep, plan->stream);
+  // launches recorded into the graph run only when it is launched
+  plan->kernels = launches_so_far() - before;
+  note_launch(0 - plan->kernels);
   e = cudaStreamEndCapture(plan->stream, &plan->graph);
   if (le != cudaSuccess) return bail(cuda_fail(le, "capturing the mining kernels"));
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
@@ -156,6 +161,7 @@ fim_status fim_plan_launch(fim_plan* plan) {
   if (!plan || !plan->exec) return fail(FIM_ERR_INVALID, "plan is NULL");
   FIM_CUDA(cudaGraphLaunch(plan->exec, plan->stream));
   ++plan->launches;
+  note_launch(plan->kernels);
   return FIM_OK;
 }
 

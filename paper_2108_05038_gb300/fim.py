@@ -25,7 +25,7 @@ EXPORTED = [
     "fim_estimate_class_costs", "fim_estimate_class_costs_ex", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
-    "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free",
+    "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free", "fim_kernel_launches",
 ]
 
 
@@ -141,6 +141,8 @@ def load(build_if_stale: bool = True):
         lib.fim_status_str.argtypes = [i32]
         lib.fim_last_error.restype = ctypes.c_char_p
         lib.fim_last_error.argtypes = []
+        lib.fim_kernel_launches.restype = u64
+        lib.fim_kernel_launches.argtypes = []
         _lib = lib
         return lib
 
@@ -399,6 +401,11 @@ def build_vertical_db_device(d_tx_offsets, d_tx_items, D: int, N: int, word_bits
                                                  prefilter_minsup, _stream_handle(stream), ctypes.byref(h)),
            "fim_build_vertical_db_device")
     return Database(lib, h.value)
+
+
+def kernel_launches() -> int:
+    """fim_kernel_launches: kernels this library has put on a stream so far (graph replays included)."""
+    return int(load().fim_kernel_launches())
 
 
 def status_str(status: int) -> str:

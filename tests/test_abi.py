@@ -38,6 +38,13 @@ def test_status_strings_without_gpu():
     assert lib.fim_last_error() == b""
 
 
+def test_launch_counter_starts_at_zero_without_gpu():
+    """No kernel has been launched by a CPU-only process (failed calls launch nothing)."""
+    lib = fim.load()
+    lib.fim_build_vertical_db(None, None, 0, 1, 64, 0, None, None)
+    assert fim.kernel_launches() == 0
+
+
 def test_opts_struct_layout_matches_header():
     lib = fim.load()
     o = fim.MineOpts()

@@ -70,3 +70,25 @@ def test_autotune_shape_is_valid_and_output_unchanged():
     assert plan.result().as_dict() == want
     plan.free()
     db.free()
+
+
+def test_launch_counter_counts_graph_kernels_per_replay():
+    """fim_kernel_launches: a mine adds its kernels; each plan replay adds the kernels of its graph."""
+    w = synth.make_workload("dense_deep", D=20_000)
+    ms = 12_000
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    c0 = fim.kernel_launches()
+    db.mine(ms).free()
+    c1 = fim.kernel_launches()
+    assert c1 - c0 >= 5  # pair counts, survivor count, level-2 scan and fill, DFS
+    plan = db.plan(ms)
+    c2 = fim.kernel_launches()
+    plan.launch()
+    c3 = fim.kernel_launches()
+    plan.launch()
+    plan.launch()
+    c4 = fim.kernel_launches()
+    assert c3 - c2 >= 5 and c4 - c3 == 2 * (c3 - c2)
+    plan.result().free()
+    plan.free()
+    db.free()
