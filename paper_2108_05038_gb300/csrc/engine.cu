@@ -107,10 +107,12 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     if (ce != cudaSuccess) return ce;
   }
   if (ep.ev[0]) cudaEventRecord(ep.ev[0], st);
-  uint32_t ksplit = 0;
-  PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
-  ce = launch_pair_counts(pl, ep.num_sms, st, &ksplit);
-  if (ce != cudaSuccess) return ce;
+  if (!ep.skip_pairs) {
+    uint32_t ksplit = 0;
+    PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
+    ce = launch_pair_counts(pl, ep.num_sms, st, &ksplit);
+    if (ce != cudaSuccess) return ce;
+  }
   if (ep.ev[1]) cudaEventRecord(ep.ev[1], st);
   LevelLaunch ll{ep.d_C2, ep.n1, ep.minsup, ep.d_frows, ep.d_rsupp, ep.d_rank_item, ep.d_order, ep.d_scnt,
                  ep.d_soff, ep.d_eoff, ep.d_sitems, ep.d_entries, ep.d_off, ep.d_items, ep.d_supp,
@@ -173,6 +175,11 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
   DevCtrl h;
   std::memcpy(&h, hstage, sizeof(DevCtrl));
   out->ctrl = h;
+  if (ep->ev[0] && ep->n1 > 0) {
+    float t = 0.f;
+    if (!ep->skip_pairs && cudaEventElapsedTime(&t, ep->ev[0], ep->ev[1]) == cudaSuccess) ep->ms_pair = t;
+    if (cudaEventElapsedTime(&t, ep->ev[0], ep->ev[3]) == cudaSuccess) ep->ms_total += t;
+  }
   if (h.err & DEV_ERR_TIMEOUT) return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
   if ((h.err & DEV_ERR_ABORTED) || (ep->max_sets && h.sets_total > ep->max_sets))
     return fail(FIM_ERR_OUTPUT_OVERFLOW, "more frequent itemsets than the limit: mining stopped early (counts are lower bounds)");
@@ -223,9 +230,9 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     stats->threads_per_cta = ep->threads;
     stats->vec_per_lane = ep->vec;
     if (ep->ev[0] && n1 > 0) {
-      cudaEventElapsedTime(&stats->ms_pair_kernel, ep->ev[0], ep->ev[1]);
-      cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);
-      cudaEventElapsedTime(&stats->ms_device_total, ep->ev[0], ep->ev[3]);
+      stats->ms_pair_kernel = ep->ms_pair;  // the one pair-kernel launch of this mine
+      cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);  // the last DFS run
+      stats->ms_device_total = ep->ms_total;  // every launch, repeated runs included
     }
   }
   return FIM_OK;
@@ -248,7 +255,9 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
     s = engine_finish(db, ws.stream, &ep, out, stats, &retry);
     if (s != FIM_OK || !retry) break;
     if (attempt == 3) s = fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity still exceeded after regrowth");
+    ep.skip_pairs = true;  // the pair counts in the workspace stay valid: only the later stages repeat
   }
+  ep.skip_pairs = false;
   if (plan_out && s == FIM_OK) {
     *plan_out = ep;
     for (auto& e : ep.ev) e = nullptr;  // events belong to the caller's copy now

@@ -167,6 +167,8 @@ struct fim_db {
   std::vector<uint32_t> est_order;
   uint64_t est_nfs = 0;
   uint32_t est_m = 0, est_minsup = 0;
+  double est_rel = 0.0;      // relative minsup the estimate was asked for
+  bool est_doubled = false;  // the sample minsup was raised by the itemset limit
 
   fim::Workspace ws;
 
@@ -251,6 +253,8 @@ struct EnginePlan {
   int num_sms = 0;
   unsigned long long* d_class_work = nullptr;  // optional per-class intersection counters (n1 entries)
   uint64_t max_sets = 0;
+  bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
+  float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
   // buffers
   DevCtrl* d_ctrl = nullptr;
   const uint32_t *d_frows = nullptr, *d_rsupp = nullptr, *d_order = nullptr;

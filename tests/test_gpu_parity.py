@@ -231,6 +231,20 @@ def test_itemset_limit_aborts_early(mode):
     assert len(got) == 2 ** 20 - 1
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_output_regrowth_reuses_pair_counts(mode):
+    """2^20 - 1 itemsets overflow the first output buffer: the repeated run skips the pair kernel
+    (its counts stay in the workspace) and still gives the exact closed-form answer."""
+    off, items = csr([list(range(20))] * 50 + [[20]])
+    db = fim.build_vertical_db(off, items, 21)
+    res = db.mine(50, dfs_mode=mode, collect_times=True)
+    st = res.stats
+    got = res.as_dict()
+    db.free()
+    assert len(got) == 2 ** 20 - 1 and all(v == 50 for v in got.values())
+    assert st["ms_pair_kernel"] > 0 and st["ms_device_total"] >= st["ms_dfs_kernel"] > 0
+
+
 def test_repeated_mines_reuse_workspace():
     w = synth.make_workload("tiny", D=8000)
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
