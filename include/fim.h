@@ -73,6 +73,8 @@ typedef struct {
   float ms_pair_kernel;          /* CUDA-event time of the pair kernel (collect_times = 1)         */
   float ms_dfs_kernel;           /* CUDA-event time of the persistent DFS kernel                   */
   float ms_device_total;         /* CUDA-event time from the first to the last mining kernel       */
+  float dfs_cta_busy_max_ms;     /* longest time a persistent DFS CTA was resident (collect_times)  */
+  float dfs_cta_busy_mean_ms;    /* mean over the CTAs; max / mean is the load imbalance           */
   float reserved_f;
 } fim_mine_stats;
 

@@ -206,6 +206,12 @@ struct DfsArgs {
   uint32_t max_len;    // itemset length bound (entries of the path arrays)
 };
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // candidate list encodings
 enum : uint32_t { CAND_FROW = 0, CAND_PAIR = 1, CAND_PAIR_RING = 2 };
 
@@ -370,6 +376,7 @@ __global__ void k_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words)
 template <int VEC, bool PSMEM>
 __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
   const DfsLaunch& p = A.p;
+  if (p.cta_time && threadIdx.x == 0) p.cta_time[2 * blockIdx.x] = global_ns();
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ Ctl C;
   __shared__ uint32_t wtot[33];
@@ -652,6 +659,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
     atomicAdd(&p.ctrl->n_intersections, st_inter);
     atomicAdd(&p.ctrl->n_frames, st_frames);
     atomicAdd(&p.ctrl->n_donations, st_don);
+    if (p.cta_time) p.cta_time[2 * blockIdx.x + 1] = global_ns();
   }
 #undef slot_pre
 #undef slot_list
@@ -713,6 +721,7 @@ struct FrameCtl {
 template <int VEC, bool PSMEM>
 __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
   const DfsLaunch& p = A.p;
+  if (p.cta_time && threadIdx.x == 0) p.cta_time[2 * blockIdx.x] = global_ns();
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ Ctl C;
   __shared__ FrameCtl F;
@@ -1020,6 +1029,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
   if (threadIdx.x == 0) {
     atomicAdd(&p.ctrl->n_intersections, st_inter);
     atomicAdd(&p.ctrl->n_frames, st_frames);
+    if (p.cta_time) p.cta_time[2 * blockIdx.x + 1] = global_ns();
   }
 #undef fr_pre
 #undef fr_g

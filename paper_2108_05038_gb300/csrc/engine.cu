@@ -7,6 +7,7 @@
 // finish   - read the control block, check the device-side error bits
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "fim_internal.cuh"
 
@@ -92,6 +93,7 @@ fim_status engine_alloc(Workspace& ws, EnginePlan* ep) {
   FIM_TRY(ws_get(ws, WS_OUT_SUPP, std::max<uint64_t>(1, ep->cap_sets), &ep->d_supp));
   if (ep->n1 >= 3)
     FIM_TRY(ws_get(ws, WS_ARENA, dfs_arena_cta_words(ep->stride, ep->n1, ep->maxd, ep->mode) * ep->grid, &ep->d_arena));
+  if (ep->n1 >= 3 && ep->ev[0]) FIM_TRY(ws_get(ws, WS_CTATIME, 2ull * ep->grid, &ep->d_cta_time));
   return FIM_OK;
 }
 
@@ -148,6 +150,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.donate = ep.donate;
     dl.class_work = ep.d_class_work;
     dl.max_sets = ep.max_sets;
+    dl.cta_time = ep.d_cta_time;
     ce = launch_dfs(dl, ep.grid, ep.threads, ep.vec, ep.smem, ep.psmem, ep.L, ep.mode, st);
     if (ce != cudaSuccess) return ce;
   }
@@ -233,6 +236,19 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
       stats->ms_pair_kernel = ep->ms_pair;  // the one pair-kernel launch of this mine
       cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);  // the last DFS run
       stats->ms_device_total = ep->ms_total;  // every launch, repeated runs included
+    }
+    if (ep->d_cta_time && ep->grid) {  // load balance of the persistent DFS: busy time per CTA
+      std::vector<unsigned long long> t(2ull * ep->grid);
+      FIM_CUDA(cudaMemcpyAsync(t.data(), ep->d_cta_time, t.size() * 8, cudaMemcpyDeviceToHost, st));
+      FIM_CUDA(cudaStreamSynchronize(st));
+      double sum = 0.0, mx = 0.0;
+      for (uint32_t c = 0; c < ep->grid; ++c) {
+        const double b = t[2 * c + 1] > t[2 * c] ? (double)(t[2 * c + 1] - t[2 * c]) * 1e-6 : 0.0;
+        sum += b;
+        mx = std::max(mx, b);
+      }
+      stats->dfs_cta_busy_max_ms = (float)mx;
+      stats->dfs_cta_busy_mean_ms = (float)(sum / ep->grid);
     }
   }
   return FIM_OK;

@@ -95,6 +95,7 @@ enum WsSlot {
   WS_SAMPLE_SUPP,
   WS_TALLY,
   WS_CLASSWORK,
+  WS_CTATIME,
   WS_COUNT
 };
 
@@ -255,6 +256,7 @@ struct EnginePlan {
   uint64_t max_sets = 0;
   bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
   float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
+  unsigned long long* d_cta_time = nullptr;  // per-CTA [start, end] of the DFS (with timing only)
   // buffers
   DevCtrl* d_ctrl = nullptr;
   const uint32_t *d_frows = nullptr, *d_rsupp = nullptr, *d_order = nullptr;
@@ -359,6 +361,7 @@ struct DfsLaunch {
   uint32_t donate;
   unsigned long long* class_work;  // optional: intersections per top class (frow index of its first item)
   uint64_t max_sets;               // 0 = no limit; else stop once more sets than this are found
+  unsigned long long* cta_time;    // optional: [start, end] global time (ns) of every CTA
 };
 // grid: number of persistent CTAs; threads: CTA size; vec: 16-byte loads per lane per piece
 // mode 0: node at a time (optionally with donation); mode 1: frame passes (all children of a frame together)

@@ -47,7 +47,8 @@ class MineStats(ctypes.Structure):
         ("bytes_algorithmic", ctypes.c_uint64), ("bytes_pair_kernel", ctypes.c_uint64),
         ("bytes_dfs_kernel", ctypes.c_uint64), ("words_per_row", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
         ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ms_pair_kernel", ctypes.c_float),
-        ("ms_dfs_kernel", ctypes.c_float), ("ms_device_total", ctypes.c_float), ("reserved_f", ctypes.c_float),
+        ("ms_dfs_kernel", ctypes.c_float), ("ms_device_total", ctypes.c_float),
+        ("dfs_cta_busy_max_ms", ctypes.c_float), ("dfs_cta_busy_mean_ms", ctypes.c_float), ("reserved_f", ctypes.c_float),
     ]
 
     def as_dict(self):

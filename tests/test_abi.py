@@ -3,6 +3,8 @@ function that include/fim.h declares.  No compute call is made here."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -51,6 +53,27 @@ def test_opts_struct_layout_matches_header():
     lib.fim_mine_opts_init(ctypes.byref(o))
     assert o.struct_size == ctypes.sizeof(fim.MineOpts)
     assert o.donate == 0 and o.class_order == fim.FIM_ORDER_ESTIMATE
+
+
+@pytest.mark.parametrize("cname,pycls", [("fim_mine_stats", "MineStats"), ("fim_mine_opts", "MineOpts")])
+def test_struct_offsets_match_header(cname, pycls, tmp_path):
+    """Field offsets and sizes of the ctypes mirrors equal what a C compiler makes of include/fim.h."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    cls = getattr(fim, pycls)
+    fields = [f for f, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{os.path.join(ROOT, "include", "fim.h")}"',
+             "int main(void) {", f'  printf("size %zu\\n", sizeof({cname}));']
+    lines += [f'  printf("{f} %zu\\n", offsetof({cname}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(got["size"]) == ctypes.sizeof(cls)
+    for f in fields:
+        assert int(got[f]) == getattr(cls, f).offset, f
 
 
 def test_invalid_arguments_rejected_without_gpu():

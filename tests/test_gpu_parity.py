@@ -245,6 +245,16 @@ def test_output_regrowth_reuses_pair_counts(mode):
     assert st["ms_pair_kernel"] > 0 and st["ms_device_total"] >= st["ms_dfs_kernel"] > 0
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cta_busy_times_are_consistent(mode):
+    """collect_times records every persistent CTA's resident time: 0 < mean <= max <= the kernel's time."""
+    w = synth.make_workload("dense_deep", D=20_000)
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    st = db.mine(12_000, dfs_mode=mode, collect_times=True).stats
+    db.free()
+    assert 0 < st["dfs_cta_busy_mean_ms"] <= st["dfs_cta_busy_max_ms"] <= st["ms_dfs_kernel"] * 1.05 + 0.01
+
+
 def test_repeated_mines_reuse_workspace():
     w = synth.make_workload("tiny", D=8000)
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
