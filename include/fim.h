@@ -101,6 +101,10 @@ typedef struct {
   uint64_t out_needed_sets;    /* on FIM_ERR_OUTPUT_OVERFLOW: capacities that would have sufficed */
   uint64_t out_needed_items;
   fim_mine_stats* stats;       /* optional                                                        */
+  uint64_t* class_work_out;    /* optional host array of n_rows entries (fim_db_info): entry r gets
+                                  the AND+popcount intersections of the class [r | rows after r],
+                                  level 2 and below (the actual cost that the sample estimate
+                                  predicts); 0 for rows that are not frequent                      */
 } fim_mine_opts;
 
 /* Fill *opts with the defaults (struct_size set, all options default). */

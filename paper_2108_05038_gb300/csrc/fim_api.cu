@@ -612,6 +612,12 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
   fim_mine_stats local_stats{};
   fim_mine_stats* stats = opts && opts->struct_size && opts->stats ? opts->stats : &local_stats;
   std::memset(stats, 0, sizeof(*stats));
+  uint64_t* work_out = opts && opts->struct_size ? opts->class_work_out : nullptr;
+  unsigned long long* d_work = nullptr;
+  if (work_out && in.n1) {
+    FIM_TRY(ws_get(db->ws, WS_CLASSWORK, in.n1, &d_work));
+    cfg.class_work = d_work;
+  }
   EngineOutput eo;
   fim_status s = engine_mine(db, db->ws, in, cfg, &eo, stats);
   if (s == FIM_ERR_OUTPUT_OVERFLOW && opts && opts->struct_size) {
@@ -619,6 +625,21 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
     opts->out_needed_items = eo.ctrl.items_total;
   }
   if (s != FIM_OK) return s;
+  if (work_out) {  // per row: level-2 candidates (the later frequent rows) + the DFS below the class
+    std::fill(work_out, work_out + db->n_rows, 0ull);
+    if (in.n1) {
+      std::vector<unsigned long long> w(in.n1, 0ull);
+      if (in.n1 >= 3) {
+        void* h = nullptr;
+        FIM_TRY(stage_get(db, (size_t)in.n1 * 8, &h));
+        FIM_CUDA(cudaMemcpyAsync(h, d_work, (size_t)in.n1 * 8, cudaMemcpyDeviceToHost, db->stream));
+        FIM_TRY(stream_sync(db));
+        std::memcpy(w.data(), h, (size_t)in.n1 * 8);
+      }
+      const uint32_t r0 = db->n_rows - in.n1;
+      for (uint32_t i = 0; i < in.n1; ++i) work_out[r0 + i] = w[i] + (in.n1 - 1 - i);
+    }
+  }
   return make_result(db->stream, eo, opts && opts->struct_size && opts->result_on_device, out);
 }
 

@@ -64,6 +64,7 @@ class MineOpts(ctypes.Structure):
         ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("max_itemsets", ctypes.c_uint64),
         ("out_needed_sets", ctypes.c_uint64),
         ("out_needed_items", ctypes.c_uint64), ("stats", ctypes.POINTER(MineStats)),
+        ("class_work_out", ctypes.c_void_p),
     ]
 
 
@@ -309,10 +310,16 @@ class Database:
     def mine(self, minsup: int, class_order: str = "estimate", threads_per_cta: int = 0, vec_per_lane: int = 0,
              ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
              out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
-             shape=None, dfs_mode: int = 0, max_itemsets: int = 0):
+             shape=None, dfs_mode: int = 0, max_itemsets: int = 0, class_work: bool = False):
+        """fim_mine; with ``class_work`` the result carries ``class_work`` (u64[n_rows]): the intersections
+        of every one-row class, level 2 and below."""
         opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
                               collect_times, out_capacity_sets, out_capacity_items, spin_limit, stats, shape, dfs_mode,
                               max_itemsets)
+        cw = None
+        if class_work:
+            cw = np.zeros(max(1, self.info()["n_rows"]), dtype=np.uint64)
+            opts.class_work_out = cw.ctypes.data
         h = ctypes.c_void_p()
         status = self._lib.fim_mine(self._h, minsup, ctypes.byref(opts), ctypes.byref(h))
         if status == FIM_ERR_OUTPUT_OVERFLOW:
@@ -320,7 +327,10 @@ class Database:
             err.needed = (opts.out_needed_sets, opts.out_needed_items)
             raise err
         _check(self._lib, status, "fim_mine")
-        return Result(self._lib, h.value, st)
+        res = Result(self._lib, h.value, st)
+        if cw is not None:
+            res.class_work = cw[: self.info()["n_rows"]]
+        return res
 
     def mine_pairs_noalloc(self, minsup: int, d_pairs, d_supports, capacity: int) -> int:
         """fim_mine_pairs_noalloc into caller-owned device buffers; returns the number of frequent pairs."""

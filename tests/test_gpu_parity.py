@@ -255,6 +255,55 @@ def test_cta_busy_times_are_consistent(mode):
     assert 0 < st["dfs_cta_busy_mean_ms"] <= st["dfs_cta_busy_max_ms"] <= st["ms_dfs_kernel"] * 1.05 + 0.01
 
 
+def _literal_class_work(txs, N, minsup):
+    """Intersections per one-row class of a literal Eclat in the row order (ascending support, ties by id):
+    level 2 tries every later frequent row, a node [X | E] tries every e in E, and a child is expanded
+    when it has a later survivor."""
+    supp = np.zeros(N, dtype=np.int64)
+    sets = [set(t) for t in txs]
+    for t in sets:
+        for i in t:
+            supp[i] += 1
+    rows = sorted(range(N), key=lambda i: (supp[i], i))
+    sets = [{rows.index(i) for i in t} for t in sets]
+
+    def sup(X):
+        return sum(1 for t in sets if X <= t)
+
+    freq = [r for r in range(N) if sup({r}) >= minsup]
+    work = np.zeros(N, dtype=np.uint64)
+
+    def expand(cls, X, cands):
+        surv = []
+        for e in cands:
+            work[cls] += 1
+            if sup(X | {e}) >= minsup:
+                surv.append(e)
+        for k, e in enumerate(surv):
+            if k + 1 < len(surv):
+                expand(cls, X | {e}, surv[k + 1:])
+
+    for pos, r in enumerate(freq):
+        expand(r, {r}, freq[pos + 1:])
+    return work
+
+
+@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1)])
+def test_class_work_matches_literal_eclat(seed, mode):
+    """class_work_out: intersections per one-row class equal a literal Eclat's count, and sum to the total."""
+    rng = np.random.default_rng(700 + seed)
+    N, D = 12, 400
+    txs = [list(np.nonzero(rng.random(N) < rng.uniform(0.2, 0.7))[0]) for _ in range(D)]
+    off, items = csr(txs)
+    minsup = int(rng.integers(15, 60))
+    db = fim.build_vertical_db(off, items, N, word_bits=32 if seed % 2 else 64)
+    res = db.mine(minsup, dfs_mode=mode, class_work=True)
+    db.free()
+    want = _literal_class_work(txs, N, minsup)
+    assert np.array_equal(res.class_work, want)
+    assert int(res.class_work.sum()) == res.stats["n_intersections"]
+
+
 def test_repeated_mines_reuse_workspace():
     w = synth.make_workload("tiny", D=8000)
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
