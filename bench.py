@@ -296,6 +296,67 @@ def run_plan(args):
             "n_classes": st["n_classes"], "n_queue_entries": st["n_queue_entries"], "gpu_launches": int(launches)}
 
 
+def run_balance(args):
+    """Estimator fidelity (the thesis's Exp. 1/2 on one GPU): estimated vs actual class costs, and the
+    persistent DFS's time and per-CTA load imbalance under each class order."""
+    import torch
+
+    from paper_2108_05038_gb300 import fim
+
+    torch.cuda.set_device(0)
+    w = synth.make_workload(args.workload)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], w["word_bits"], 0)
+    ms = w["minsup"]
+
+    def run(order, reps):
+        best = None
+        for _ in range(reps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            res = db.mine(ms, class_order=order, collect_times=True, result_on_device=True, class_work=True)
+            st = res.stats
+            cw = res.class_work.astype(np.float64)
+            res.free()
+            if best is None or st["ms_dfs_kernel"] < best[0]["ms_dfs_kernel"]:
+                best = (st, cw)
+        st, cw = best
+        return {"dfs_ms": round(st["ms_dfs_kernel"], 4),
+                "cta_busy_max_ms": round(st["dfs_cta_busy_max_ms"], 4),
+                "cta_busy_mean_ms": round(st["dfs_cta_busy_mean_ms"], 4),
+                "imbalance_max_over_mean": round(st["dfs_cta_busy_max_ms"] / max(st["dfs_cta_busy_mean_ms"], 1e-9), 3)}, cw
+
+    def ranks(v):
+        r = np.empty(len(v))
+        r[np.argsort(v, kind="stable")] = np.arange(len(v))
+        return r
+
+    def fidelity(est, actual):
+        m = actual > 0
+        e, a = est[m], actual[m] / actual[m].sum()
+        pear = float(np.corrcoef(e, a)[0, 1]) if m.sum() > 1 else float("nan")
+        spear = float(np.corrcoef(ranks(e), ranks(a))[0, 1]) if m.sum() > 1 else float("nan")
+        k = max(1, int(0.05 * m.sum()))
+        top = len(set(np.argsort(-e)[:k]) & set(np.argsort(-a)[:k])) / k
+        return {"pearson": round(pear, 4), "spearman": round(spear, 4), "top5pct_overlap": round(top, 3),
+                "abs_share_error_sum": round(float(np.abs(e - a).sum()), 4)}
+
+    reps = max(3, args.steps)
+    out = {"metric": "estimator fidelity and DFS load balance", "mode": "balance", "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": workload_desc(w), "sample_rate": SAMPLE_RATE, "reps": reps}}
+    uni, actual = run("uniform", reps)
+    out["uniform_order"] = uni
+    out["actual_classes"] = int((actual > 0).sum())
+    out["actual_top_class_share"] = round(float(actual.max() / actual.sum()), 4)
+    for kind in ("itemsets", "intersections"):
+        cost, _ = db.estimate_class_costs(SAMPLE_RATE, w["rel_minsup"], EST_SEED, cost=kind)
+        r, _ = run("estimate", reps)
+        r["fidelity"] = fidelity(np.asarray(cost, dtype=np.float64), actual)
+        out[f"estimate_{kind}"] = r
+    db.free()
+    return out
+
+
 def _gen_request(r):
     off, items = synth.request_db(r)
     return off, items
@@ -482,9 +543,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--mode", default="step", choices=["step", "plan", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "plan", "serve", "balance"],
                     help="step: build+estimate+mine per step (default); plan: graph replays of one captured "
-                         "mine; serve: the request loop against the plain one-job-at-a-time loop")
+                         "mine; serve: the request loop against the plain one-job-at-a-time loop; balance: "
+                         "estimated vs actual class costs and the DFS load balance per class order")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--slots", type=int, default=4)
@@ -497,6 +559,8 @@ def main():
         out = run_plan(args)
     elif args.mode == "serve":
         out = run_serve(args)
+    elif args.mode == "balance":
+        out = run_balance(args)
     else:
         out = run_ours(args)
     if out is not None:
