@@ -89,7 +89,9 @@ typedef struct {
   uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 0)          */
   uint32_t result_on_device;   /* 1 = keep the result in device memory (no D2H copy)              */
   uint32_t collect_times;      /* 1 = record CUDA events around the kernels (stats.ms_*)          */
-  uint32_t reserved_u;         /* must be 0                                                       */
+  uint32_t dfs_depth_first;    /* 0 = automatic (the full depth bound when its stack fits in 1/32 of
+                                  device memory); else the first DFS stack depth, grown and the run
+                                  repeated when an itemset is deeper                                */
   uint64_t out_capacity_sets;  /* 0 = automatic (grow and retry); else fixed capacity             */
   uint64_t out_capacity_items; /* idem, total items over all sets                                 */
   uint64_t spin_limit;         /* idle-CTA polling rounds without progress before FIM_ERR_TIMEOUT;

@@ -68,7 +68,6 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // persistent DFS geometry: itemsets are no longer than the longest transaction
   ep->L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
   ep->maxd_full = std::max<uint32_t>(1, ep->L - 2);
-  ep->maxd = std::min<uint32_t>(ep->maxd_full, kDfsDepthHint);  // grown (and the run repeated) on demand
   ep->threads = clamp_threads(cfg.threads);
   ep->vec = clamp_vec(cfg.vec);
   ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full, ep->mode);
@@ -78,6 +77,11 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
   const uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
   ep->grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);
+  // DFS stack depth: the full bound when its arena fits in 1/32 of the device memory (no run can
+  // then fail for depth); otherwise a shallow first stack, grown and the run repeated on demand
+  const uint64_t full_bytes = 4ull * dfs_arena_cta_words(in.stride, n1, ep->maxd_full, ep->mode) * ep->grid;
+  ep->maxd = full_bytes <= db->total_mem / 32 ? ep->maxd_full : std::min<uint32_t>(ep->maxd_full, kDfsDepthHint);
+  if (cfg.depth_first) ep->maxd = std::min<uint32_t>(ep->maxd_full, cfg.depth_first);
   ep->per_depth = dfs_arena_depth_words(in.stride, n1);
   ep->pool_slots = ep->donate ? std::max<uint32_t>(8, ep->grid) : 0;
   ep->pool_slot_words = dfs_pool_slot_words(in.stride, ep->L, n1);

@@ -171,6 +171,20 @@ void Workspace::release() {
 // ---------------------------------------------------------------------------
 // database build
 
+// total device memory, asked once per device
+static uint64_t device_total_mem(int dev) {
+  static std::mutex mu;
+  static uint64_t total[64] = {};
+  if (dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!total[dev]) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) total[dev] = total_b;
+    else cudaGetLastError();
+  }
+  return total[dev];
+}
+
 static fim_status db_init(fim_db* db, uint32_t D, uint32_t N, uint32_t word_bits, uint32_t prefilter,
                           void* stream) {
   db->D = D;
@@ -184,6 +198,7 @@ static fim_status db_init(fim_db* db, uint32_t D, uint32_t N, uint32_t word_bits
   int optin = 0;
   FIM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, db->device));
   db->smem_optin = (size_t)optin;
+  db->total_mem = device_total_mem(db->device);
   db->W32 = (D + 31) / 32;
   db->stride = ((db->W32 + 31) / 32) * 32;
   return FIM_OK;
@@ -330,6 +345,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->ctas_per_sm = o->ctas_per_sm;
   c->donate = o->donate;
   c->mode = o->dfs_mode;
+  c->depth_first = o->dfs_depth_first;
   c->max_sets = o->max_itemsets;
   c->spin_limit = o->spin_limit;
   c->cap_sets = o->out_capacity_sets;

@@ -149,6 +149,7 @@ struct fim_db {
   cudaStream_t stream = nullptr;
   int device = 0;
   int num_sms = 0;
+  uint64_t total_mem = 0;  // device memory (bytes)
   size_t smem_optin = 0;
 
   uint32_t* d_bits = nullptr;       // n_rows * stride
@@ -222,6 +223,7 @@ struct EngineOutput {
 };
 
 struct EngineConfig {
+  uint32_t depth_first = 0;  // 0 = automatic
   uint32_t threads = 256;
   uint32_t vec = 4;
   uint32_t ctas_per_sm = 0;

@@ -52,6 +52,7 @@ struct fim_server {
   int device = 0;
   uint32_t ctas_per_sm = 1;
   uint64_t max_itemsets = 0;
+  uint64_t total_mem = 0;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
 };
@@ -61,13 +62,18 @@ namespace {
 // Upper bound of the device bytes of one job: CSR copy, bitmaps of the items that
 // can reach minsup (at most nnz / minsup of them), pair block, queue, DFS stack,
 // output, with the sample of the estimate on top.
-uint64_t job_footprint(uint32_t D, uint32_t N, uint64_t nnz, uint32_t minsup, uint32_t grid) {
+uint64_t job_footprint(uint32_t D, uint32_t N, uint64_t nnz, uint32_t max_len, uint32_t minsup, uint32_t grid,
+                       uint64_t total_mem) {
   const uint64_t stride = ((uint64_t)(D + 31) / 32 + 31) / 32 * 32;
   const uint64_t rows = std::min<uint64_t>(N, nnz / std::max<uint32_t>(1, minsup) + 1);
   uint64_t b = 4ull * ((uint64_t)D + 1 + nnz);           // CSR
   b += 4ull * rows * stride;                              // bitmaps
   b += 4ull * rows * rows + 12ull * rows * rows / 2;      // pair counts, survivors, queue
-  b += 4ull * (stride + 2 * rows) * (fim::kDfsDepthHint + 1) * grid;  // DFS stack
+  // DFS stack: the full depth (itemsets are no longer than the longest transaction) when it fits
+  // in 1/32 of the device memory, as the engine decides
+  const uint64_t depth = std::max<uint32_t>(3, std::min<uint64_t>(max_len, rows)) - 1;
+  const uint64_t full = 4ull * (stride + 2 * rows + 8) * depth * grid;
+  b += full <= total_mem / 32 ? full : 4ull * (stride + 2 * rows + 8) * (fim::kDfsDepthHint + 1) * grid;
   b += 64ull << 20;                                       // output, sample, small buffers
   return b;
 }
@@ -145,11 +151,16 @@ fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t
   if (slots == 0 || slots > 64) return fail(FIM_ERR_INVALID, "slots must be in 1..64");
   fim_server* srv = new (std::nothrow) fim_server();
   if (!srv) return fail(FIM_ERR_OOM, "host allocation");
-  FIM_CUDA(cudaGetDevice(&srv->device));
-  if (hbm_budget_bytes == 0) {
+  {
     size_t free_b = 0, total_b = 0;
-    FIM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    hbm_budget_bytes = (uint64_t)(free_b * 0.8);
+    cudaError_t e = cudaGetDevice(&srv->device);
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+      delete srv;
+      return cuda_fail(e, "server device");
+    }
+    srv->total_mem = total_b;
+    if (hbm_budget_bytes == 0) hbm_budget_bytes = (uint64_t)(free_b * 0.8);
   }
   srv->budget = hbm_budget_bytes;
   srv->ctas_per_sm = ctas_per_sm ? ctas_per_sm : 1;
@@ -185,7 +196,10 @@ fim_status fim_server_submit(fim_server* srv, const uint32_t* tx_offsets, const 
   j->sample_rate = sample_rate;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, srv->device);
-  j->footprint = job_footprint(D, N, nnz, minsup_abs, (uint32_t)nsm * srv->ctas_per_sm);
+  uint32_t max_len = 0;
+  for (uint32_t t = 0; t < D; ++t)
+    if (tx_offsets[t + 1] > tx_offsets[t]) max_len = std::max(max_len, tx_offsets[t + 1] - tx_offsets[t]);
+  j->footprint = job_footprint(D, N, nnz, max_len, minsup_abs, (uint32_t)nsm * srv->ctas_per_sm, srv->total_mem);
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     j->id = srv->next_id++;

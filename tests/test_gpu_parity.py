@@ -90,12 +90,13 @@ def test_ragged_D(D):
     assert_same(gpu_mine(off, items, 12, minsup).as_dict(), odict(oracle.eclat(off, items, 12, minsup)))
 
 
-@pytest.mark.parametrize("k,mode", [(11, 0), (16, 0), (11, 1), (16, 1)])
-def test_identical_transactions_closed_form(k, mode):
-    """2^k - 1 itemsets of support D; depth 14 exceeds the first DFS stack and forces the regrown retry."""
+@pytest.mark.parametrize("k,mode,depth", [(11, 0, 0), (16, 0, 8), (11, 1, 4), (16, 1, 0)])
+def test_identical_transactions_closed_form(k, mode, depth):
+    """2^k - 1 itemsets of support D; with a first DFS stack of 4 or 8 the depth of 9 or 14 forces the
+    regrown retry, with 0 the stack has the full depth at once."""
     D = 300
     off, items = csr([list(range(k))] * D + [[k]])
-    got = gpu_mine(off, items, k + 1, D, dfs_mode=mode).as_dict()
+    got = gpu_mine(off, items, k + 1, D, dfs_mode=mode, dfs_depth_first=depth).as_dict()
     assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
 
 
@@ -233,11 +234,12 @@ def test_itemset_limit_aborts_early(mode):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_output_regrowth_reuses_pair_counts(mode):
-    """2^20 - 1 itemsets overflow the first output buffer: the repeated run skips the pair kernel
-    (its counts stay in the workspace) and still gives the exact closed-form answer."""
+    """2^20 - 1 itemsets of length up to 20 overflow the first output buffer and a 3-deep first DFS
+    stack: the repeated runs skip the pair kernel (its counts stay in the workspace) and still give
+    the exact closed-form answer."""
     off, items = csr([list(range(20))] * 50 + [[20]])
     db = fim.build_vertical_db(off, items, 21)
-    res = db.mine(50, dfs_mode=mode, collect_times=True)
+    res = db.mine(50, dfs_mode=mode, collect_times=True, dfs_depth_first=3)  # depth 20 > 3: stack grows too
     st = res.stats
     got = res.as_dict()
     db.free()
