@@ -106,17 +106,6 @@ __global__ void k_row_popcount(const uint32_t* __restrict__ bits, uint32_t strid
   }
 }
 
-// tally[r] += 1 for every itemset whose lowest row (rank) is r.
-__global__ void k_tally_min_rank(const uint64_t* __restrict__ set_off, const uint32_t* __restrict__ set_items,
-                                 uint64_t n_sets, const int32_t* __restrict__ item_rank,
-                                 unsigned long long* __restrict__ tally) {
-  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_sets; s += (uint64_t)gridDim.x * blockDim.x) {
-    int32_t best = 0x7fffffff;
-    for (uint64_t q = set_off[s]; q < set_off[s + 1]; ++q) best = min(best, item_rank[set_items[q]]);
-    if (best >= 0 && best != 0x7fffffff) atomicAdd(&tally[best], 1ull);
-  }
-}
-
 __global__ void k_iota(uint32_t* out, uint32_t n) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
 }
@@ -168,15 +157,6 @@ cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t 
                                 cudaStream_t st) {
   if (n_rows == 0) return cudaSuccess;
   k_row_popcount<<<n_rows, 256, 0, st>>>(bits, stride, supp);
-  note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tally_min_rank(const uint64_t* set_off, const uint32_t* set_items, uint64_t n_sets,
-                                  const int32_t* item_rank, unsigned long long* tally, cudaStream_t st) {
-  if (n_sets == 0) return cudaSuccess;
-  const uint32_t threads = 256;
-  k_tally_min_rank<<<grid_for(n_sets, threads), threads, 0, st>>>(set_off, set_items, n_sets, item_rank, tally);
   note_launch();
   return cudaGetLastError();
 }

@@ -130,7 +130,7 @@ __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t*
     ctrl->pending = carry_e;
     ctrl->queue_head = 0;
     ctrl->max_len = n1 > 0 ? (P > 0 ? 2u : 1u) : 0u;
-    if (sets > cap_sets || items > cap_items) ctrl->err |= DEV_ERR_OVERFLOW;
+    if (cap_sets && (sets > cap_sets || items > cap_items)) ctrl->err |= DEV_ERR_OVERFLOW;  // 0: count only
   }
 }
 
@@ -144,12 +144,14 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
                               const uint32_t* __restrict__ eoff, uint32_t* __restrict__ sitems,
                               uint2* __restrict__ entries, uint64_t* __restrict__ out_off,
                               uint32_t* __restrict__ out_items, uint32_t* __restrict__ out_supp, uint64_t cap_sets,
-                              uint64_t cap_items) {
+                              uint64_t cap_items, unsigned long long* __restrict__ class_sets) {
   __shared__ uint32_t wtot[33];
   const uint32_t q = blockIdx.x;
   const uint32_t i = row_order[q];
   const uint32_t id_i = rank_item[frows[i]];
-  if (threadIdx.x == 0 && i < cap_sets && i < cap_items) {
+  // sets of class i found at levels 1 and 2: {i} and its frequent pairs (the DFS adds the rest)
+  if (class_sets && threadIdx.x == 0) class_sets[i] = 1ull + scnt[i];
+  if (threadIdx.x == 0 && out_off && i < cap_sets && i < cap_items) {
     out_off[i] = i;
     out_items[i] = id_i;
     out_supp[i] = row_supp[i];
@@ -167,7 +169,7 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
       uint32_t k = soff[i] + pos0 + pos;
       sitems[k] = j;
       uint64_t rec = (uint64_t)n1 + k, it = (uint64_t)n1 + 2ull * k;
-      if (rec < cap_sets && it + 2 <= cap_items) {
+      if (out_off && rec < cap_sets && it + 2 <= cap_items) {
         uint32_t id_j = rank_item[frows[j]];
         out_off[rec] = it;
         out_items[it] = min(id_i, id_j);
@@ -278,6 +280,7 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
         atomicMax(&p.ctrl->max_len, xlen + 1);
         const unsigned long long after = (C.base >> 32) + sets;
         if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        if (p.class_sets) atomicAdd(&p.class_sets[C.cls], sets);
       }
       __syncthreads();
       if (f) {
@@ -293,7 +296,9 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
         }
         const uint64_t rec = (C.base >> 32) + pos;
         const uint64_t it0 = (C.base & 0xffffffffull) + (uint64_t)pos * (xlen + 1);
-        if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
+        if (!p.out_off) {
+          // count only: no records
+        } else if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
           uint32_t* dst = p.out_items + it0;
           uint32_t q = 0;
           bool placed = false;
@@ -966,6 +971,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
           atomicMax(&p.ctrl->max_len, xl + 2);
           const unsigned long long after = (F.base >> 32) + sets;
           if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+          if (p.class_sets) atomicAdd(&p.class_sets[C.cls], sets);
         }
         __syncthreads();
         if (f) {
@@ -978,7 +984,9 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
           atomicAdd(&ccnt[m - mA], 1u);
           const uint64_t rec = (F.base >> 32) + pos;
           const uint64_t it0 = (F.base & 0xffffffffull) + (uint64_t)pos * (xl + 2);
-          if (rec < p.cap_sets && it0 + xl + 2 <= p.cap_items) {
+          if (!p.out_off) {
+            // count only: no records
+          } else if (rec < p.cap_sets && it0 + xl + 2 <= p.cap_items) {
             // X_d's sorted ids merged with the two new ids (ids are < 2^32 - 1)
             const uint32_t a = L[2 * m + 1], b = L[2 * e + 1];
             uint32_t lo = min(a, b), hi = max(a, b);
@@ -1125,7 +1133,7 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_level2_fill<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.frows, p.row_supp, p.rank_item, p.row_order, p.scnt,
                                       p.soff, p.eoff, p.sitems, p.entries, p.out_off, p.out_items, p.out_supp,
-                                      p.cap_sets, p.cap_items);
+                                      p.cap_sets, p.cap_items, p.class_sets);
   note_launch();
   return cudaGetLastError();
 }

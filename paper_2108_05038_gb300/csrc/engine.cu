@@ -92,9 +92,11 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
 }
 
 fim_status engine_alloc(Workspace& ws, EnginePlan* ep) {
-  FIM_TRY(ws_get(ws, WS_OUT_OFF, ep->cap_sets + 1, &ep->d_off));
-  FIM_TRY(ws_get(ws, WS_OUT_ITEMS, std::max<uint64_t>(1, ep->cap_items), &ep->d_items));
-  FIM_TRY(ws_get(ws, WS_OUT_SUPP, std::max<uint64_t>(1, ep->cap_sets), &ep->d_supp));
+  if (!ep->count_only) {
+    FIM_TRY(ws_get(ws, WS_OUT_OFF, ep->cap_sets + 1, &ep->d_off));
+    FIM_TRY(ws_get(ws, WS_OUT_ITEMS, std::max<uint64_t>(1, ep->cap_items), &ep->d_items));
+    FIM_TRY(ws_get(ws, WS_OUT_SUPP, std::max<uint64_t>(1, ep->cap_sets), &ep->d_supp));
+  }
   if (ep->n1 >= 3)
     FIM_TRY(ws_get(ws, WS_ARENA, dfs_arena_cta_words(ep->stride, ep->n1, ep->maxd, ep->mode) * ep->grid, &ep->d_arena));
   if (ep->n1 >= 3 && ep->ev[0]) FIM_TRY(ws_get(ws, WS_CTATIME, 2ull * ep->grid, &ep->d_cta_time));
@@ -122,7 +124,8 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   if (ep.ev[1]) cudaEventRecord(ep.ev[1], st);
   LevelLaunch ll{ep.d_C2, ep.n1, ep.minsup, ep.d_frows, ep.d_rsupp, ep.d_rank_item, ep.d_order, ep.d_scnt,
                  ep.d_soff, ep.d_eoff, ep.d_sitems, ep.d_entries, ep.d_off, ep.d_items, ep.d_supp,
-                 ep.cap_sets, ep.cap_items, ep.d_ctrl};
+                 ep.count_only ? 0ull : ep.cap_sets, ep.count_only ? 0ull : ep.cap_items, ep.d_ctrl,
+                 ep.d_class_sets};
   ce = launch_level2(ll, st);
   if (ce != cudaSuccess) return ce;
   if (ep.ev[2]) cudaEventRecord(ep.ev[2], st);
@@ -147,8 +150,9 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.out_off = ep.d_off;
     dl.out_items = ep.d_items;
     dl.out_supp = ep.d_supp;
-    dl.cap_sets = ep.cap_sets;
-    dl.cap_items = ep.cap_items;
+    dl.cap_sets = ep.count_only ? 0ull : ep.cap_sets;
+    dl.cap_items = ep.count_only ? 0ull : ep.cap_items;
+    dl.class_sets = ep.d_class_sets;
     dl.ctrl = ep.d_ctrl;
     dl.spin_limit = ep.spin_limit;
     dl.donate = ep.donate;
@@ -196,7 +200,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     *retry = true;
     return FIM_OK;
   }
-  if (h.sets_total > ep->cap_sets || h.items_total > ep->cap_items) {
+  if (!ep->count_only && (h.sets_total > ep->cap_sets || h.items_total > ep->cap_items)) {
     if (h.sets_total > kMaxCap || h.items_total > kMaxCap)
       return fail(FIM_ERR_OUTPUT_OVERFLOW, "result exceeds 2^32 sets or items");
     if (ep->fixed_capacity) return fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity exceeded");
@@ -263,6 +267,8 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
   EnginePlan ep;
   fim_status s = engine_prepare(db, ws, in, cfg, &ep);
   if (s == FIM_OK && cfg.class_work) ep.d_class_work = cfg.class_work;
+  if (s == FIM_OK && cfg.class_sets) ep.d_class_sets = cfg.class_sets;
+  ep.count_only = cfg.count_only;
   ep.max_sets = cfg.max_sets;
   for (int attempt = 0; s == FIM_OK && attempt < 4; ++attempt) {
     if ((s = engine_alloc(ws, &ep)) != FIM_OK) break;

@@ -555,9 +555,11 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
     EngineConfig cfg;
     cfg.donate = 0;
     cfg.max_sets = max_sample_itemsets;
-    if (cost_kind == FIM_COST_INTERSECTIONS && in.n1) {
+    cfg.count_only = true;  // the estimate needs per-class counts, not the itemsets themselves
+    if (in.n1) {
       FIM_TRY(ws_get(db->ws, WS_CLASSWORK, in.n1, &d_work));
-      cfg.class_work = d_work;
+      if (cost_kind == FIM_COST_INTERSECTIONS) cfg.class_work = d_work;
+      else cfg.class_sets = d_work;
     }
     eo = EngineOutput{};
     const fim_status s = engine_mine(db, db->ws, in, cfg, &eo, nullptr);
@@ -567,29 +569,20 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
     if (!over || minsup_s == UINT32_MAX) return s;
     minsup_s = minsup_s > UINT32_MAX / 2 ? UINT32_MAX : 2 * minsup_s;
   }
+  // per class (the lowest row of its itemsets): intersections = level-2 candidates (the later
+  // frequent sample rows) + the DFS below; itemsets = {r}, its frequent pairs and the DFS sets
   std::vector<unsigned long long> tally(R, 0ull);
-  if (cost_kind == FIM_COST_INTERSECTIONS) {
-    // intersections per class: level 2 (the later frequent sample rows) + the DFS below it
-    std::vector<unsigned long long> work(in.n1, 0ull);
-    if (in.n1 && in.n1 >= 3) {
-      void* h = nullptr;
-      FIM_TRY(stage_get(db, (size_t)in.n1 * 8, &h));
-      FIM_CUDA(cudaMemcpyAsync(h, d_work, (size_t)in.n1 * 8, cudaMemcpyDeviceToHost, st));
-      FIM_TRY(stream_sync(db));
-      std::memcpy(work.data(), h, (size_t)in.n1 * 8);
-    }
-    for (uint32_t i = 0; i < in.n1; ++i) tally[in.frows[i]] = work[i] + (in.n1 - 1 - i);
-  } else if (R) {
-    unsigned long long* d_tally = nullptr;
-    FIM_TRY(ws_get(db->ws, WS_TALLY, R, &d_tally));
-    FIM_CUDA(cudaMemsetAsync(d_tally, 0, (size_t)R * 8, st));
-    FIM_CUDA(launch_tally_min_rank(eo.d_off, eo.d_items, eo.n_sets, db->d_item_rank, d_tally, st));
+  std::vector<unsigned long long> per(in.n1, 0ull);
+  const bool dfs_ran = cost_kind == FIM_COST_INTERSECTIONS ? in.n1 >= 3 : in.n1 >= 1;
+  if (dfs_ran) {
     void* h = nullptr;
-    FIM_TRY(stage_get(db, (size_t)R * 8, &h));
-    FIM_CUDA(cudaMemcpyAsync(h, d_tally, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+    FIM_TRY(stage_get(db, (size_t)in.n1 * 8, &h));
+    FIM_CUDA(cudaMemcpyAsync(h, d_work, (size_t)in.n1 * 8, cudaMemcpyDeviceToHost, st));
     FIM_TRY(stream_sync(db));
-    std::memcpy(tally.data(), h, (size_t)R * 8);
+    std::memcpy(per.data(), h, (size_t)in.n1 * 8);
   }
+  for (uint32_t i = 0; i < in.n1; ++i)
+    tally[in.frows[i]] = per[i] + (cost_kind == FIM_COST_INTERSECTIONS ? (in.n1 - 1 - i) : 0ull);
   unsigned long long total = 0;
   for (uint32_t r = 0; r < R; ++r) total += tally[r];
   db->est_cost.assign(R, 0.0);

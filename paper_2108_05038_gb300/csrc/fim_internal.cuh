@@ -234,6 +234,8 @@ struct EngineConfig {
   bool fixed_capacity = false;
   bool collect_times = false;
   unsigned long long* class_work = nullptr;  // optional device array (n1 entries): DFS intersections per top class
+  unsigned long long* class_sets = nullptr;  // optional device array (n1 entries): itemsets per top class
+  bool count_only = false;                   // count itemsets, write no records (no output buffers)
   uint64_t max_sets = 0;                     // 0 = no limit; else stop early past this many itemsets
 };
 
@@ -255,6 +257,8 @@ struct EnginePlan {
   uint64_t spin_limit = 0;
   int num_sms = 0;
   unsigned long long* d_class_work = nullptr;  // optional per-class intersection counters (n1 entries)
+  unsigned long long* d_class_sets = nullptr;  // optional per-class itemset counters (n1 entries)
+  bool count_only = false;
   uint64_t max_sets = 0;
   bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
   float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
@@ -303,8 +307,6 @@ cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint
 cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t n_rows, uint32_t* supp,
                                 cudaStream_t st);
-cudaError_t launch_tally_min_rank(const uint64_t* set_off, const uint32_t* set_items, uint64_t n_sets,
-                                  const int32_t* item_rank, unsigned long long* tally, cudaStream_t st);
 
 struct PairLaunch {
   const uint32_t* bits;
@@ -329,11 +331,12 @@ struct LevelLaunch {
   uint32_t* eoff;               // n1 + 1 entry offsets (queue order)
   uint32_t* sitems;             // survivors (frow indices)
   uint2* entries;               // (row, m)
-  uint64_t* out_off;
+  uint64_t* out_off;            // NULL: count only (no records)
   uint32_t* out_items;
   uint32_t* out_supp;
   uint64_t cap_sets, cap_items;
   DevCtrl* ctrl;
+  unsigned long long* class_sets;  // optional: frequent itemsets per top class
 };
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st);
 
@@ -364,6 +367,7 @@ struct DfsLaunch {
   unsigned long long* class_work;  // optional: intersections per top class (frow index of its first item)
   uint64_t max_sets;               // 0 = no limit; else stop once more sets than this are found
   unsigned long long* cta_time;    // optional: [start, end] global time (ns) of every CTA
+  unsigned long long* class_sets;  // optional: frequent itemsets per top class
 };
 // grid: number of persistent CTAs; threads: CTA size; vec: 16-byte loads per lane per piece
 // mode 0: node at a time (optionally with donation); mode 1: frame passes (all children of a frame together)
