@@ -4,14 +4,15 @@
 // for every pair of frequent rows i < j, i.e. the first DFS step of Eclat
 // (App. B.3.2) for all one-item prefix classes [i | {j > i}] at once.  The
 // n1 x n1 block of pair counts is a dense contraction over the transaction
-// bits, so it is tiled like a GEMM: a CTA owns a 64 x 64 tile of (i, j) pairs
-// (upper triangle only), stages 32-word slices of the 64 + 64 rows in shared
-// memory with cp.async (3-stage pipeline), and every thread accumulates a 4 x 4
-// micro-tile.  Each staged word is reused by 64 pairs, so the kernel is bound
-// by the integer pipes (AND on the integer pipe, POPC on the XU pipe), not by
-// memory.  Rows are split along the word axis into (tile, word range) work
-// items that a grid of resident CTAs (three per SM) walks through (partial
-// counts added atomically), which keeps every SM busy until the last wave.
+// bits, so it is tiled like a GEMM: a CTA of 128 threads owns a 64 x 64 tile
+// of (i, j) pairs (upper triangle only), stages 32-word slices of the 64 + 64
+// rows in shared memory with cp.async (3-stage pipeline), and every thread
+// accumulates an 8 x 4 micro-tile.  Each staged word is reused by 64 pairs, so
+// the kernel is bound by the integer pipes (AND and the adders on the integer
+// pipe, POPC on the XU pipe), not by memory.  Rows are split along the word
+// axis into (tile, word range) work items that a grid of resident CTAs walks
+// through (partial counts added atomically), which keeps every SM busy until
+// the last wave.
 #include <mutex>
 
 #include "fim_internal.cuh"
@@ -23,8 +24,13 @@ constexpr int kTile = 64;      // rows per tile side
 constexpr int kChunk = 32;     // words staged per row per pipeline stage
 constexpr int kRowPad = 36;    // padded shared-memory row (words): conflict-free 16-byte loads
 constexpr int kStages = 3;
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
+constexpr int kMX = 8, kMY = 4;                      // micro-tile: A rows x B rows per thread
+constexpr int kTY = kTile / kMX, kTX = kTile / kMY;  // 8 x 16 threads
+constexpr int kCopyRows = kThreads / 8;              // tile rows per copy pass (8 x 16 B per row slice)
+constexpr int kPasses = kTile / kCopyRows;           // copy passes per operand
 constexpr size_t kSmemBytes = (size_t)kStages * 2 * kTile * kRowPad * sizeof(uint32_t);
+static_assert(kTY * kTX == kThreads && kPasses * kCopyRows == kTile, "thread layout");
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, uint32_t src_bytes) {
   uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -34,21 +40,30 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// acc += popc(a.x&b.x) + popc(a.y&b.y) + popc(a.z&b.z) + popc(a.w&b.w).
-// POPC issues on the XU pipe (32 lanes/clk/SM) and limits the plain form; a
-// 3:2 carry-save adder (two LOP3 on the 64-lane integer pipe) folds three of
-// the four AND words into a sum word s and a carry word c, so that
-// popc(t0)+popc(t1)+popc(t2) = popc(s) + 2 popc(c): three POPC per four words.
-// The accumulation is a multiply-add by a runtime 1 or 2 (FMA pipe).
-__device__ __forceinline__ void acc_and_popc4(uint32_t& acc, const uint4& a, const uint4& b, uint32_t one,
-                                              uint32_t two) {
-  const uint32_t t0 = a.x & b.x, t1 = a.y & b.y, t2 = a.z & b.z, t3 = a.w & b.w;
-  const uint32_t s = t0 ^ t1 ^ t2;
-  const uint32_t c = (t0 & t1) | (t2 & (t0 ^ t1));
-  const uint32_t ps = __popc(s), pc = __popc(c), p3 = __popc(t3);
-  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(pc), "r"(two));
-  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(ps), "r"(one));
-  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(p3), "r"(one));
+__device__ __forceinline__ void madd(uint32_t& acc, uint32_t p, uint32_t w) {
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(p), "r"(w));
+}
+
+// acc += sum over 8 words of popc(a_k & b_k).  POPC issues on the XU pipe (32
+// lanes/clk/SM, half the integer pipe) and limits the plain form.  A tree of
+// 3:2 carry-save adders (two LOP3 each, integer pipe) compresses seven of the
+// eight AND words into bit-planes of weight 1, 2 and 4:
+//   (t0,t1,t2) -> s1 + 2 c1,  (t3,t4,t5) -> s2 + 2 c2,  (s1,s2,t6) -> s + 2 c3,
+//   (c1,c2,c3) -> tw + 2 f,   so  t0 + .. + t6 = s + 2 tw + 4 f  (bitwise counts),
+// and popc(s) + 2 popc(tw) + 4 popc(f) + popc(t7) is the sum: four POPC per
+// eight words.  The weighted adds are multiply-adds by runtime constants (FMA pipe).
+__device__ __forceinline__ void acc_and_popc8(uint32_t& acc, const uint4& a0, const uint4& a1, const uint4& b0,
+                                              const uint4& b1, uint32_t one, uint32_t two, uint32_t four) {
+  const uint32_t t0 = a0.x & b0.x, t1 = a0.y & b0.y, t2 = a0.z & b0.z, t3 = a0.w & b0.w;
+  const uint32_t t4 = a1.x & b1.x, t5 = a1.y & b1.y, t6 = a1.z & b1.z, t7 = a1.w & b1.w;
+  const uint32_t s1 = t0 ^ t1 ^ t2, c1 = (t0 & t1) | (t2 & (t0 ^ t1));
+  const uint32_t s2 = t3 ^ t4 ^ t5, c2 = (t3 & t4) | (t5 & (t3 ^ t4));
+  const uint32_t s = s1 ^ s2 ^ t6, c3 = (s1 & s2) | (t6 & (s1 ^ s2));
+  const uint32_t tw = c1 ^ c2 ^ c3, f = (c1 & c2) | (c3 & (c1 ^ c2));
+  madd(acc, __popc(f), four);
+  madd(acc, __popc(tw), two);
+  madd(acc, __popc(s), one);
+  madd(acc, __popc(t7), one);
 }
 
 __global__ void __launch_bounds__(kThreads, 3)
@@ -56,90 +71,96 @@ k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t
               uint32_t nb, uint32_t chunks_per_split, uint32_t nchunks, uint32_t* __restrict__ C2, uint32_t ksplit,
               uint32_t n_items, uint32_t one) {
   extern __shared__ __align__(16) uint32_t sm[];
-  const uint32_t tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const uint32_t tid = threadIdx.x, ty = tid / kTX, tx = tid % kTX;
+  const uint32_t two = one + one, four = two + two;
   // persistent loop over work items (tile, word range); consecutive items share a tile
   for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-  uint32_t t = item / ksplit, bi = 0;
-  const uint32_t split = item - t * ksplit;
-  while (t >= nb - bi) { t -= nb - bi; ++bi; }
-  const uint32_t bj = bi + t;
-  const uint32_t i0 = bi * kTile, j0 = bj * kTile;
-  const uint32_t c_begin = split * chunks_per_split;
-  const uint32_t c_end = min(nchunks, c_begin + chunks_per_split);
-  if (c_begin >= c_end) continue;
+    uint32_t t = item / ksplit, bi = 0;
+    const uint32_t split = item - t * ksplit;
+    while (t >= nb - bi) { t -= nb - bi; ++bi; }
+    const uint32_t bj = bi + t;
+    const uint32_t i0 = bi * kTile, j0 = bj * kTile;
+    const uint32_t c_begin = split * chunks_per_split;
+    const uint32_t c_end = min(nchunks, c_begin + chunks_per_split);
+    if (c_begin >= c_end) continue;
 
-  // four 16-byte copies per thread and stage: 64 A rows + 64 B rows x 8 vectors.
-  // Copy q moves vector (tid & 7) of tile row (tid >> 3) + 32 * (q & 1) of A (q < 2) or B.
-  const uint32_t lr = tid >> 3, lc = tid & 7;
-  const uint32_t* src[4];
-  uint32_t okmask = 0;
+    // 2 x kPasses 16-byte copies per thread and stage: copy q moves vector (tid & 7) of tile row
+    // (tid >> 3) + kCopyRows * (q % kPasses) of A (q < kPasses) or B; rows past n1 are zero-filled
+    const uint32_t lr = tid >> 3, lc = tid & 7;
+    uint32_t rowid[2 * kPasses];
+    uint32_t okmask = 0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint32_t g = (q < 2 ? i0 : j0) + lr + 32 * (q & 1);
-    bool ok = g < n1;
-    okmask |= (ok ? 1u : 0u) << q;
-    src[q] = bits + (size_t)frows[ok ? g : 0] * stride + lc * 4;
-  }
-  auto load_stage = [&](uint32_t stage, uint32_t chunk) {
-    uint32_t* base = sm + stage * (2 * kTile * kRowPad);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t dst = ((q >> 1) * kTile + lr + 32 * (q & 1)) * kRowPad + lc * 4;
-      cp_async16(base + dst, src[q] + (size_t)chunk * kChunk, (okmask >> q) & 1u ? 16u : 0u);
+    for (int q = 0; q < 2 * kPasses; ++q) {
+      const uint32_t g = (q < kPasses ? i0 : j0) + lr + kCopyRows * (q % kPasses);
+      const bool ok = g < n1;
+      okmask |= (ok ? 1u : 0u) << q;
+      rowid[q] = frows[ok ? g : 0];
     }
-  };
+    auto load_stage = [&](uint32_t stage, uint32_t chunk) {
+      uint32_t* base = sm + stage * (2 * kTile * kRowPad);
+#pragma unroll
+      for (int q = 0; q < 2 * kPasses; ++q) {
+        const uint32_t dst = ((q / kPasses) * kTile + lr + kCopyRows * (q % kPasses)) * kRowPad + lc * 4;
+        const uint32_t* src = bits + (size_t)rowid[q] * stride + (size_t)chunk * kChunk + lc * 4;
+        cp_async16(base + dst, src, (okmask >> q) & 1u ? 16u : 0u);
+      }
+    };
 
-  uint32_t acc[4][4];
+    uint32_t acc[kMX][kMY];
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+    for (int x = 0; x < kMX; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) acc[x][y] = 0;
+      for (int y = 0; y < kMY; ++y) acc[x][y] = 0;
 
 #pragma unroll
-  for (int s = 0; s < kStages - 1; ++s) {
-    if (c_begin + s < c_end) load_stage(s, c_begin + s);
-    cp_async_commit();
-  }
-  uint32_t stage = 0;
-  for (uint32_t c = c_begin; c < c_end; ++c) {
-    cp_async_wait<kStages - 2>();
-    __syncthreads();
-    {
-      uint32_t nc = c + kStages - 1;
-      uint32_t ns = stage + kStages - 1;
-      if (ns >= kStages) ns -= kStages;
-      if (nc < c_end) load_stage(ns, nc);
+    for (int s = 0; s < kStages - 1; ++s) {
+      if (c_begin + s < c_end) load_stage(s, c_begin + s);
       cp_async_commit();
     }
-    const uint32_t* As = sm + stage * (2 * kTile * kRowPad);
-    const uint32_t* Bs = As + kTile * kRowPad;
-#pragma unroll 2
-    for (int kk = 0; kk < kChunk / 4; ++kk) {
-      uint4 b[4];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) b[y] = *reinterpret_cast<const uint4*>(Bs + (tx + 16 * y) * kRowPad + kk * 4);
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const uint4 a = *reinterpret_cast<const uint4*>(As + (ty + 16 * x) * kRowPad + kk * 4);
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc_and_popc4(acc[x][y], a, b[y], one, one + one);
+    uint32_t stage = 0;
+    for (uint32_t c = c_begin; c < c_end; ++c) {
+      cp_async_wait<kStages - 2>();
+      __syncthreads();
+      {
+        const uint32_t nc = c + kStages - 1;
+        uint32_t ns = stage + kStages - 1;
+        if (ns >= kStages) ns -= kStages;
+        if (nc < c_end) load_stage(ns, nc);
+        cp_async_commit();
       }
+      const uint32_t* As = sm + stage * (2 * kTile * kRowPad);
+      const uint32_t* Bs = As + kTile * kRowPad;
+#pragma unroll 1
+      for (int kk = 0; kk < kChunk / 8; ++kk) {
+        uint4 b0[kMY], b1[kMY];
+#pragma unroll
+        for (int y = 0; y < kMY; ++y) {
+          b0[y] = *reinterpret_cast<const uint4*>(Bs + (tx + kTX * y) * kRowPad + kk * 8);
+          b1[y] = *reinterpret_cast<const uint4*>(Bs + (tx + kTX * y) * kRowPad + kk * 8 + 4);
+        }
+#pragma unroll
+        for (int x = 0; x < kMX; ++x) {
+          const uint4 a0 = *reinterpret_cast<const uint4*>(As + (ty + kTY * x) * kRowPad + kk * 8);
+          const uint4 a1 = *reinterpret_cast<const uint4*>(As + (ty + kTY * x) * kRowPad + kk * 8 + 4);
+#pragma unroll
+          for (int y = 0; y < kMY; ++y) acc_and_popc8(acc[x][y], a0, a1, b0[y], b1[y], one, two, four);
+        }
+      }
+      stage = stage + 1 == kStages ? 0 : stage + 1;
     }
-    stage = stage + 1 == kStages ? 0 : stage + 1;
-  }
-  cp_async_wait<0>();
-  __syncthreads();  // the next item refills the stages
+    cp_async_wait<0>();
+    __syncthreads();  // the next item refills the stages
 
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+    for (int x = 0; x < kMX; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      uint32_t i = i0 + ty + 16 * x, j = j0 + tx + 16 * y;
-      if (i < j && j < n1) {
-        if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], acc[x][y]);
-        else C2[(size_t)i * n1 + j] = acc[x][y];
+      for (int y = 0; y < kMY; ++y) {
+        const uint32_t i = i0 + ty + kTY * x, j = j0 + tx + kTX * y;
+        if (i < j && j < n1) {
+          if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], acc[x][y]);
+          else C2[(size_t)i * n1 + j] = acc[x][y];
+        }
       }
-    }
   }
 }
 
@@ -149,19 +170,17 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
   if (p.n1 < 2) { *ksplit_used = 0; return cudaSuccess; }
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
+  static int occ = 0;
   std::call_once(once, [] {
     attr_err = cudaFuncSetAttribute(k_pair_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_counts, kThreads, kSmemBytes);
+    if (occ < 1) occ = 1;
   });
   if (attr_err != cudaSuccess) return attr_err;
   const uint32_t nb = (p.n1 + kTile - 1) / kTile;
   const uint32_t tiles = nb * (nb + 1) / 2;
   const uint32_t nchunks = p.stride / kChunk;  // stride is a multiple of 32 words
-  static int occ = 0;
-  if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_counts, kThreads, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-  }
   const uint32_t slots = (uint32_t)num_sms * (uint32_t)occ;  // resident CTAs
   uint32_t ksplit = p.ksplit;
   if (ksplit == 0) {
