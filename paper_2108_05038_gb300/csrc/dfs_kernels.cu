@@ -217,6 +217,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // candidate list encodings
 enum : uint32_t { CAND_FROW = 0, CAND_PAIR = 1, CAND_PAIR_RING = 2 };
 
+__device__ __forceinline__ bool any4(const uint4& v) { return (v.x | v.y | v.z | v.w) != 0u; }
+
+// Sparse skipping: a prefix bitmap of support s over D transactions has at most
+// s nonzero words, so wherever its 16 bytes are zero the candidate row is not
+// read at all (its AND is zero there).  Prefixes deep in the DFS are much
+// sparser than the rows, so this cuts the bytes read per intersection.
 template <int VEC>
 __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, const uint4* pre, uint32_t base4,
                                                uint32_t stride4, bool pre_global) {
@@ -225,12 +231,21 @@ __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, co
   for (int v = 0; v < VEC; ++v) {
     uint32_t w = base4 + v * 32;
     if (w < stride4) {
-      uint4 a = __ldg(row + w);
-      uint4 b = pre_global ? __ldcg(pre + w) : pre[w];
-      s += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+      const uint4 b = pre_global ? __ldcg(pre + w) : pre[w];
+      if (any4(b)) {
+        const uint4 a = __ldg(row + w);
+        s += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+      }
     }
   }
   return s;
+}
+
+// dst[w] = a[w] & row[w], reading row[w] only where a[w] is nonzero
+__device__ __forceinline__ uint4 and_skip(const uint4& a, const uint4* __restrict__ row, uint32_t w) {
+  if (!any4(a)) return a;
+  const uint4 b = __ldg(row + w);
+  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
 }
 
 __device__ __forceinline__ uint32_t cand_row(const DfsLaunch& p, const uint32_t* cand, uint32_t mode, uint32_t k) {
@@ -474,8 +489,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       const uint4* b4 = bits4 + (size_t)r2 * A.stride4;
       uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(0));
       for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-        const uint4 a = __ldg(a4 + w), b = __ldg(b4 + w);
-        dst[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+        dst[w] = and_skip(__ldg(a4 + w), b4, w);
       }
       pre = PSMEM ? spre : slot_pre(0);
     } else {
@@ -608,8 +622,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
         uint4* d4 = reinterpret_cast<uint4*>(sl + (sw - p.stride));
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          const uint4 a = a4[w], b = __ldg(r4 + w);
-          d4[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+          d4[w] = and_skip(a4[w], r4, w);
         }
         __threadfence();
         __syncthreads();
@@ -631,8 +644,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
         uint4* d4 = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(d + 1));
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          const uint4 a = a4[w], b = __ldg(r4 + w);
-          d4[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+          d4[w] = and_skip(a4[w], r4, w);
         }
       }
       sort_path_ids(xidp, xl, xid);
@@ -707,8 +719,15 @@ __device__ __forceinline__ uint32_t piece_popc3(const uint4* __restrict__ r1, co
   for (int v = 0; v < VEC; ++v) {
     const uint32_t w = base4 + v * 32;
     if (w < stride4) {
-      const uint4 a = __ldg(r1 + w), b = __ldg(r2 + w), c = pre[w];
-      s += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y) + __popc(a.z & b.z & c.z) + __popc(a.w & b.w & c.w);
+      const uint4 c = pre[w];
+      if (any4(c)) {
+        const uint4 a = __ldg(r1 + w);
+        const uint4 ac = make_uint4(a.x & c.x, a.y & c.y, a.z & c.z, a.w & c.w);
+        if (any4(ac)) {
+          const uint4 b = __ldg(r2 + w);
+          s += __popc(ac.x & b.x) + __popc(ac.y & b.y) + __popc(ac.z & b.z) + __popc(ac.w & b.w);
+        }
+      }
     }
   }
   return s;
@@ -794,8 +813,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
       const uint4* b4 = bits4 + (size_t)r2 * A.stride4;
       uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : fr_pre(0));
       for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-        const uint4 a = __ldg(a4 + w), b = __ldg(b4 + w);
-        dst[w] = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+        dst[w] = and_skip(__ldg(a4 + w), b4, w);
       }
     }
     __syncthreads();
@@ -901,8 +919,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
         const uint4* r4 = bits4 + (size_t)row * A.stride4;
         uint4* dg = reinterpret_cast<uint4*>(fr_pre(d + 1));
         for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          const uint4 a = pd[w], b = __ldg(r4 + w);
-          const uint4 c = make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+          const uint4 c = and_skip(pd[w], r4, w);
           dg[w] = c;
           if (PSMEM) reinterpret_cast<uint4*>(spre)[w] = c;
         }
