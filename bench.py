@@ -305,6 +305,7 @@ def run_balance(args):
 
     torch.cuda.set_device(0)
     w = synth.make_workload(args.workload)
+    w["name"] = args.workload
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], w["word_bits"], 0)
     ms = w["minsup"]

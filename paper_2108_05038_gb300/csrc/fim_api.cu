@@ -390,10 +390,12 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
   engine_config_from_opts(opts, cfg);
   // first output capacity: |F| of the whole database at about the same relative minsup is of
   // the order of the sample's |F_s|, so a few times |F_s| usually avoids a second DFS run
-  if (!cfg->cap_sets && db->has_estimate && !db->est_doubled && db->est_nfs && db->est_rel > 0.0) {
+  // (when the sample's minsup had to be raised, its count at the requested minsup passed the
+  // limit, so the limit is the better lower bound)
+  if (!cfg->cap_sets && db->has_estimate && db->est_nfs && db->est_rel > 0.0) {
     const double rel = (double)minsup_abs / (double)db->D;
-    if (std::fabs(rel - db->est_rel) <= 0.1 * db->est_rel)
-      cfg->cap_sets = std::min<uint64_t>(4ull * db->est_nfs, 1ull << 28);
+    const uint64_t f = db->est_doubled ? std::max<uint64_t>(db->est_nfs, db->est_limit) : db->est_nfs;
+    if (std::fabs(rel - db->est_rel) <= 0.1 * db->est_rel) cfg->cap_sets = std::min<uint64_t>(4ull * f, 1ull << 28);
   }
   return FIM_OK;
 }
@@ -596,6 +598,7 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   db->est_m = m;
   db->est_minsup = minsup_s;
   db->est_rel = rel_minsup;
+  db->est_limit = max_sample_itemsets;
   db->est_doubled = minsup_s != (msd < 1.0 ? 1u : (uint32_t)msd);
   if (cost_out && R) std::memcpy(cost_out, db->est_cost.data(), R * sizeof(double));
   if (order_out && R) std::memcpy(order_out, db->est_order.data(), R * sizeof(uint32_t));

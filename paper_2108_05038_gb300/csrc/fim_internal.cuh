@@ -171,6 +171,7 @@ struct fim_db {
   uint32_t est_m = 0, est_minsup = 0;
   double est_rel = 0.0;      // relative minsup the estimate was asked for
   bool est_doubled = false;  // the sample minsup was raised by the itemset limit
+  uint64_t est_limit = 0;    // that limit
 
   fim::Workspace ws;
 
