@@ -134,8 +134,11 @@ void fim_mine_opts_init(fim_mine_opts* opts);
 fim_status fim_build_vertical_db(const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D, uint32_t N,
                                  uint32_t word_bits, uint32_t prefilter_minsup, void* cuda_stream, fim_db** out);
 
-/* Same as fim_build_vertical_db with tx_offsets / tx_items in DEVICE memory
- * (read on cuda_stream; the library copies what it keeps). */
+/* Same as fim_build_vertical_db with tx_offsets / tx_items in DEVICE memory,
+ * read on cuda_stream: both must stay valid until the work queued on that
+ * stream by this call has run (as for cudaMemcpyAsync); the library copies
+ * what it keeps.  d_tx_items must not be NULL.  The offsets are validated on
+ * the device before any item is read past tx_offsets[D]. */
 fim_status fim_build_vertical_db_device(const uint32_t* d_tx_offsets, const uint32_t* d_tx_items, uint32_t D,
                                         uint32_t N, uint32_t word_bits, uint32_t prefilter_minsup,
                                         void* cuda_stream, fim_db** out);

@@ -1,6 +1,5 @@
 // Vertical-database kernels: item counting (K1), bitmap build (K2), the
-// database sample of the class-cost estimate, row popcounts and the tally of
-// sample itemsets per one-item-prefix class.
+// database sample of the class-cost estimate and row popcounts.
 //
 // Vertical representation (Ch. 2, Def. "Transaction id list"): row r holds the
 // tidlist of item rank_item[r] as a bitmap, bit t of the row set iff
@@ -15,19 +14,27 @@ constexpr uint32_t kSmemHistMax = 12288;  // items counted in shared memory (48 
 // K1: item supports with set semantics.  One thread per transaction; an item
 // counts once per transaction (a repeat is detected by scanning the earlier
 // positions of the same transaction).  Also validates ids and offsets and
-// records the longest transaction (distinct items).
+// records the longest transaction (distinct items).  Only items[0, off[D]) is
+// ever read, whatever the offsets: a transaction whose range is reversed or
+// leaves [0, off[D]] is reported and skipped, and so is every transaction when
+// off[0] != 0.  flags = [error bits, longest transaction, off[0], off[D]].
 __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
-                             uint32_t N, uint32_t* __restrict__ cnt, uint32_t* err, uint32_t* max_len) {
+                             uint32_t N, uint32_t* __restrict__ cnt, uint32_t* flags) {
   extern __shared__ uint32_t hist[];
   const bool use_smem = N <= kSmemHistMax;
   if (use_smem) {
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) hist[i] = 0;
     __syncthreads();
   }
-  uint32_t local_max = 0, local_err = 0;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D; t += gridDim.x * blockDim.x) {
+  const uint32_t first = off[0], nnz = off[D];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    flags[2] = first;
+    flags[3] = nnz;
+  }
+  uint32_t local_max = 0, local_err = first != 0 ? DEV_ERR_OFFSETS : 0u;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D && first == 0; t += gridDim.x * blockDim.x) {
     uint32_t b = off[t], e = off[t + 1];
-    if (e < b) { local_err |= DEV_ERR_OFFSETS; continue; }
+    if (e < b || e > nnz) { local_err |= DEV_ERR_OFFSETS; continue; }
     uint32_t distinct = 0;
     for (uint32_t k = b; k < e; ++k) {
       uint32_t it = items[k];
@@ -41,8 +48,8 @@ __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* _
     }
     local_max = max(local_max, distinct);
   }
-  if (local_err) atomicOr(err, local_err);
-  if (local_max) atomicMax(max_len, local_max);
+  if (local_err) atomicOr(&flags[0], local_err);
+  if (local_max) atomicMax(&flags[1], local_max);
   if (use_smem) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
@@ -120,12 +127,12 @@ uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t cap = 152 * 32) {
 }  // namespace
 
 cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t* cnt,
-                              uint32_t* err, uint32_t* max_len, cudaStream_t st) {
+                              uint32_t* flags, cudaStream_t st) {
   const uint32_t threads = 256;
   size_t smem = N <= kSmemHistMax ? (size_t)N * 4 : 0;
   // with a shared histogram every CTA flushes N counters: keep the grid modest
   uint32_t grid = grid_for(D, threads, N <= kSmemHistMax ? 152 * 4 : 152 * 32);
-  k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, err, max_len);
+  k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, flags);
   note_launch();
   return cudaGetLastError();
 }

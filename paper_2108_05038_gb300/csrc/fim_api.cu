@@ -217,24 +217,35 @@ static fim_status dev_alloc(fim_db* db, T** p, size_t count) {
   return FIM_OK;
 }
 
-// Items counted (K1), rows relabelled on the host, bitmaps built (K2).
-static fim_status db_build_rows(fim_db* db) {
+// Items counted (K1) on the input CSR (the caller's device arrays or the db's
+// copy of host arrays), the offsets validated on the device, rows relabelled on
+// the host, the CSR copied into the db (device input), bitmaps built (K2).
+static fim_status db_build_rows(fim_db* db, const uint32_t* src_off, const uint32_t* src_items, bool device_input) {
   cudaStream_t st = db->stream;
   const uint32_t N = db->N, D = db->D;
   uint32_t *d_cnt = nullptr, *d_flags = nullptr;
-  FIM_TRY(ws_get(db->ws, WS_TALLY, (size_t)N + 2, &d_cnt));
-  d_flags = d_cnt + N;  // [err, max_len]
-  FIM_CUDA(cudaMemsetAsync(d_cnt, 0, ((size_t)N + 2) * 4, st));
-  FIM_CUDA(launch_item_count(db->d_tx_off, db->d_tx_items, D, N, d_cnt, d_flags, d_flags + 1, st));
+  FIM_TRY(ws_get(db->ws, WS_TALLY, (size_t)N + 4, &d_cnt));
+  d_flags = d_cnt + N;  // [err, max_len, off[0], off[D]]
+  FIM_CUDA(cudaMemsetAsync(d_cnt, 0, ((size_t)N + 4) * 4, st));
+  FIM_CUDA(launch_item_count(src_off, src_items, D, N, d_cnt, d_flags, st));
   void* hcnt = nullptr;
-  FIM_TRY(stage_get(db, ((size_t)N + 2) * 4, &hcnt));
-  FIM_CUDA(cudaMemcpyAsync(hcnt, d_cnt, ((size_t)N + 2) * 4, cudaMemcpyDeviceToHost, st));
+  FIM_TRY(stage_get(db, ((size_t)N + 4) * 4, &hcnt));
+  FIM_CUDA(cudaMemcpyAsync(hcnt, d_cnt, ((size_t)N + 4) * 4, cudaMemcpyDeviceToHost, st));
   FIM_TRY(stream_sync(db));
-  std::vector<uint32_t> cnt(static_cast<uint32_t*>(hcnt), static_cast<uint32_t*>(hcnt) + N + 2);
+  std::vector<uint32_t> cnt(static_cast<uint32_t*>(hcnt), static_cast<uint32_t*>(hcnt) + N + 4);
   const uint32_t err = cnt[N];
-  if (err & DEV_ERR_ITEM_RANGE) return fail(FIM_ERR_INVALID, "an item id is >= N");
+  if (cnt[N + 2] != 0) return fail(FIM_ERR_INVALID, "tx_offsets[0] must be 0");
   if (err & DEV_ERR_OFFSETS) return fail(FIM_ERR_INVALID, "tx_offsets is not non-decreasing");
+  if (err & DEV_ERR_ITEM_RANGE) return fail(FIM_ERR_INVALID, "an item id is >= N");
   db->max_tx_len = cnt[N + 1];
+  if (device_input) {  // the offsets are valid: keep a copy of the CSR (the sample draw reads it)
+    db->nnz = cnt[N + 3];
+    FIM_TRY(dev_alloc(db, &db->d_tx_off, (size_t)D + 1));
+    FIM_TRY(dev_alloc(db, &db->d_tx_items, std::max<uint64_t>(1, db->nnz)));
+    FIM_CUDA(cudaMemcpyAsync(db->d_tx_off, src_off, ((size_t)D + 1) * 4, cudaMemcpyDeviceToDevice, st));
+    if (db->nnz)
+      FIM_CUDA(cudaMemcpyAsync(db->d_tx_items, src_items, db->nnz * 4ull, cudaMemcpyDeviceToDevice, st));
+  }
   std::vector<uint32_t> kept;
   kept.reserve(N);
   for (uint32_t i = 0; i < N; ++i)
@@ -292,34 +303,23 @@ static fim_status build_common(const uint32_t* off, const uint32_t* items, uint3
   };
   if (s != FIM_OK) return bail(s);
   cudaStream_t st = db->stream;
-  uint32_t first = 0, last = 0;
   if (device_input) {
-    void* h = nullptr;
-    if ((s = stage_get(db, 8, &h)) != FIM_OK) return bail(s);
-    uint32_t* hu = static_cast<uint32_t*>(h);
-    cudaError_t e = cudaMemcpyAsync(hu, off, 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hu + 1, off + D, 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "reading tx_offsets"));
-    db->stage_used = 0;
-    first = hu[0];
-    last = hu[1];
+    // counted and validated on the caller's arrays; copied once the offsets are known to be valid
+    if (!items) return bail(fail(FIM_ERR_INVALID, "tx_items is NULL"));
+    if ((s = db_build_rows(db, off, items, true)) != FIM_OK) return bail(s);
   } else {
-    first = off[0];
+    if (off[0] != 0) return bail(fail(FIM_ERR_INVALID, "tx_offsets[0] must be 0"));
     for (uint32_t t = 0; t < D; ++t)
       if (off[t + 1] < off[t]) return bail(fail(FIM_ERR_INVALID, "tx_offsets is not non-decreasing"));
-    last = off[D];
+    db->nnz = off[D];
+    if (db->nnz > 0 && !items) return bail(fail(FIM_ERR_INVALID, "tx_items is NULL"));
+    if ((s = dev_alloc(db, &db->d_tx_off, (size_t)D + 1)) != FIM_OK) return bail(s);
+    if ((s = dev_alloc(db, &db->d_tx_items, std::max<uint64_t>(1, db->nnz))) != FIM_OK) return bail(s);
+    cudaError_t e = cudaMemcpyAsync(db->d_tx_off, off, ((size_t)D + 1) * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && db->nnz) e = cudaMemcpyAsync(db->d_tx_items, items, db->nnz * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "copying the CSR database"));
+    if ((s = db_build_rows(db, db->d_tx_off, db->d_tx_items, false)) != FIM_OK) return bail(s);
   }
-  if (first != 0) return bail(fail(FIM_ERR_INVALID, "tx_offsets[0] must be 0"));
-  if (last > 0 && !items) return bail(fail(FIM_ERR_INVALID, "tx_items is NULL"));
-  db->nnz = last;
-  if ((s = dev_alloc(db, &db->d_tx_off, (size_t)D + 1)) != FIM_OK) return bail(s);
-  if ((s = dev_alloc(db, &db->d_tx_items, std::max<uint64_t>(1, db->nnz))) != FIM_OK) return bail(s);
-  const cudaMemcpyKind kind = device_input ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaError_t e = cudaMemcpyAsync(db->d_tx_off, off, ((size_t)D + 1) * 4, kind, st);
-  if (e == cudaSuccess && db->nnz) e = cudaMemcpyAsync(db->d_tx_items, items, db->nnz * 4, kind, st);
-  if (e != cudaSuccess) return bail(cuda_fail(e, "copying the CSR database"));
-  if ((s = db_build_rows(db)) != FIM_OK) return bail(s);
   *out = db;
   return FIM_OK;
 }

@@ -299,8 +299,9 @@ fim_status stream_sync(fim_db* db);
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)
 
+// flags (4 words, zeroed by the caller): error bits, longest transaction, off[0], off[D]
 cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t* cnt,
-                              uint32_t* err, uint32_t* max_len, cudaStream_t st);
+                              uint32_t* flags, cudaStream_t st);
 cudaError_t launch_bitmap_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
                                 uint32_t* bits, uint32_t stride, cudaStream_t st);
 cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,

@@ -225,6 +225,7 @@ class Database:
 
     def __init__(self, lib, handle):
         self._lib, self._h = lib, handle
+        self._inputs = None
 
     @property
     def handle(self):
@@ -413,7 +414,9 @@ def build_vertical_db_device(d_tx_offsets, d_tx_items, D: int, N: int, word_bits
     _check(lib, lib.fim_build_vertical_db_device(_ptr(d_tx_offsets), _ptr(d_tx_items), D, N, word_bits,
                                                  prefilter_minsup, _stream_handle(stream), ctypes.byref(h)),
            "fim_build_vertical_db_device")
-    return Database(lib, h.value)
+    db = Database(lib, h.value)
+    db._inputs = (d_tx_offsets, d_tx_items)  # read on the stream after the call returns: keep them alive
+    return db
 
 
 def kernel_launches() -> int:

@@ -131,6 +131,21 @@ def test_invalid_inputs():
     db.free()
 
 
+@pytest.mark.parametrize("offsets,why", [([0, 100, 5], "non-decreasing"), ([3, 4, 5], "[0] must be 0"),
+                                         ([0, 6, 5], "non-decreasing")])
+def test_invalid_device_offsets_rejected_before_reading_items(offsets, why):
+    """Device input: a range past tx_offsets[D] or a nonzero first offset is reported, and the count kernel
+    reads no item past tx_offsets[D] (the items buffer holds exactly 5 ids here)."""
+    d_off = torch.tensor(offsets, dtype=torch.int32, device="cuda")
+    d_it = torch.tensor([0, 1, 2, 1, 0], dtype=torch.int32, device="cuda")
+    with pytest.raises(fim.FimError) as e:
+        fim.build_vertical_db_device(d_off, d_it, len(offsets) - 1, 3)
+    assert e.value.status == fim.FIM_ERR_INVALID and why in str(e.value)
+    ok = fim.build_vertical_db_device(torch.tensor([0, 2, 5], dtype=torch.int32, device="cuda"), d_it, 2, 3)
+    assert ok.mine(1).as_dict() == {(0,): 2, (1,): 2, (2,): 1, (0, 1): 2, (0, 2): 1, (1, 2): 1, (0, 1, 2): 1}
+    ok.free()
+
+
 # ---------------------------------------------------------------- named workloads
 
 @pytest.mark.parametrize("name,mode", [("tiny", 0), ("dense_deep", 0), ("dense_exact37", 0), ("tiny", 1),
