@@ -327,9 +327,17 @@ def run_balance(args):
                 "cta_busy_mean_ms": round(st["dfs_cta_busy_mean_ms"], 4),
                 "imbalance_max_over_mean": round(st["dfs_cta_busy_max_ms"] / max(st["dfs_cta_busy_mean_ms"], 1e-9), 3)}, cw
 
-    def ranks(v):
+    def ranks(v):  # average ranks for ties
+        order = np.argsort(v, kind="stable")
         r = np.empty(len(v))
-        r[np.argsort(v, kind="stable")] = np.arange(len(v))
+        sv = v[order]
+        i = 0
+        while i < len(v):
+            j = i
+            while j + 1 < len(v) and sv[j + 1] == sv[i]:
+                j += 1
+            r[order[i:j + 1]] = (i + j) / 2.0
+            i = j + 1
         return r
 
     def fidelity(est, actual):

@@ -222,30 +222,57 @@ __device__ __forceinline__ bool any4(const uint4& v) { return (v.x | v.y | v.z |
 // Sparse skipping: a prefix bitmap of support s over D transactions has at most
 // s nonzero words, so wherever its 16 bytes are zero the candidate row is not
 // read at all (its AND is zero there).  Prefixes deep in the DFS are much
-// sparser than the rows, so this cuts the bytes read per intersection.
+// sparser than the rows, so this cuts the bytes read per intersection.  The
+// prefix words of a piece are read first, all together, then the row words
+// they need, all together: two round trips per piece, each with VEC loads in
+// flight per lane.
 template <int VEC>
 __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, const uint4* pre, uint32_t base4,
                                                uint32_t stride4, bool pre_global) {
-  uint32_t s = 0;
+  uint4 b[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) {
-    uint32_t w = base4 + v * 32;
-    if (w < stride4) {
-      const uint4 b = pre_global ? __ldcg(pre + w) : pre[w];
-      if (any4(b)) {
-        const uint4 a = __ldg(row + w);
-        s += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
-      }
-    }
+    const uint32_t w = base4 + v * 32;
+    b[v] = w < stride4 ? (pre_global ? __ldcg(pre + w) : pre[w]) : make_uint4(0u, 0u, 0u, 0u);
   }
+  uint4 a[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) a[v] = any4(b[v]) ? __ldg(row + base4 + v * 32) : make_uint4(0u, 0u, 0u, 0u);
+  uint32_t s = 0;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+    s += __popc(a[v].x & b[v].x) + __popc(a[v].y & b[v].y) + __popc(a[v].z & b[v].z) + __popc(a[v].w & b[v].w);
   return s;
 }
 
-// dst[w] = a[w] & row[w], reading row[w] only where a[w] is nonzero
-__device__ __forceinline__ uint4 and_skip(const uint4& a, const uint4* __restrict__ row, uint32_t w) {
-  if (!any4(a)) return a;
-  const uint4 b = __ldg(row + w);
-  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+// Block-wide dst[w] = a[w] & row[w] (and the same into dst2 when given), reading
+// row[w] only where a[w] is nonzero; four words per thread in flight per round
+// trip.  A_RO: `a` is read-only for the kernel's lifetime (a bitmap row), so it
+// may go through the non-coherent cache; otherwise (a prefix this CTA wrote) it
+// is read with plain loads.
+template <bool A_RO>
+__device__ __forceinline__ void and_rows(uint4* dst, uint4* dst2, const uint4* a4, const uint4* __restrict__ r4,
+                                         uint32_t stride4) {
+  constexpr uint32_t U = 4;
+  for (uint32_t w0 = threadIdx.x; w0 < stride4; w0 += U * blockDim.x) {
+    uint4 a[U], b[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t w = w0 + u * blockDim.x;
+      a[u] = w < stride4 ? (A_RO ? __ldg(a4 + w) : a4[w]) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) b[u] = any4(a[u]) ? __ldg(r4 + w0 + u * blockDim.x) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t w = w0 + u * blockDim.x;
+      if (w < stride4) {
+        const uint4 c = make_uint4(a[u].x & b[u].x, a[u].y & b[u].y, a[u].z & b[u].z, a[u].w & b[u].w);
+        dst[w] = c;
+        if (dst2) dst2[w] = c;
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ uint32_t cand_row(const DfsLaunch& p, const uint32_t* cand, uint32_t mode, uint32_t k) {
@@ -488,9 +515,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       const uint4* a4 = bits4 + (size_t)r1 * A.stride4;
       const uint4* b4 = bits4 + (size_t)r2 * A.stride4;
       uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(0));
-      for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-        dst[w] = and_skip(__ldg(a4 + w), b4, w);
-      }
+      and_rows<true>(dst, nullptr, a4, b4, A.stride4);
       pre = PSMEM ? spre : slot_pre(0);
     } else {
       slotp = p.pool + (size_t)C.slot * sw;
@@ -621,9 +646,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(fd));
         const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
         uint4* d4 = reinterpret_cast<uint4*>(sl + (sw - p.stride));
-        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          d4[w] = and_skip(a4[w], r4, w);
-        }
+        and_rows<false>(d4, nullptr, a4, r4, A.stride4);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -643,9 +666,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(d));
         const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
         uint4* d4 = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(d + 1));
-        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          d4[w] = and_skip(a4[w], r4, w);
-        }
+        and_rows<false>(d4, nullptr, a4, r4, A.stride4);
       }
       sort_path_ids(xidp, xl, xid);
       __syncthreads();
@@ -714,22 +735,24 @@ __device__ __forceinline__ uint32_t pair_child(uint64_t p, uint32_t n, uint32_t 
 template <int VEC>
 __device__ __forceinline__ uint32_t piece_popc3(const uint4* __restrict__ r1, const uint4* __restrict__ r2,
                                                 const uint4* pre, uint32_t base4, uint32_t stride4) {
-  uint32_t s = 0;
+  // popc(pre & r1 & r2), reading r1 only where pre is nonzero and r2 only where pre & r1 is
+  uint4 c[VEC], a[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) {
     const uint32_t w = base4 + v * 32;
-    if (w < stride4) {
-      const uint4 c = pre[w];
-      if (any4(c)) {
-        const uint4 a = __ldg(r1 + w);
-        const uint4 ac = make_uint4(a.x & c.x, a.y & c.y, a.z & c.z, a.w & c.w);
-        if (any4(ac)) {
-          const uint4 b = __ldg(r2 + w);
-          s += __popc(ac.x & b.x) + __popc(ac.y & b.y) + __popc(ac.z & b.z) + __popc(ac.w & b.w);
-        }
-      }
-    }
+    c[v] = w < stride4 ? pre[w] : make_uint4(0u, 0u, 0u, 0u);
   }
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const uint4 x = any4(c[v]) ? __ldg(r1 + base4 + v * 32) : make_uint4(0u, 0u, 0u, 0u);
+    c[v] = make_uint4(x.x & c[v].x, x.y & c[v].y, x.z & c[v].z, x.w & c[v].w);
+  }
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) a[v] = any4(c[v]) ? __ldg(r2 + base4 + v * 32) : make_uint4(0u, 0u, 0u, 0u);
+  uint32_t s = 0;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+    s += __popc(a[v].x & c[v].x) + __popc(a[v].y & c[v].y) + __popc(a[v].z & c[v].z) + __popc(a[v].w & c[v].w);
   return s;
 }
 
@@ -812,9 +835,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
       const uint4* a4 = bits4 + (size_t)r1 * A.stride4;
       const uint4* b4 = bits4 + (size_t)r2 * A.stride4;
       uint4* dst = reinterpret_cast<uint4*>(PSMEM ? spre : fr_pre(0));
-      for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-        dst[w] = and_skip(__ldg(a4 + w), b4, w);
-      }
+      and_rows<true>(dst, nullptr, a4, b4, A.stride4);
     }
     __syncthreads();
     sort_path_ids(xidp, 2, xid);
@@ -918,11 +939,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
         const uint4* pd = reinterpret_cast<const uint4*>(fr_pre(d));
         const uint4* r4 = bits4 + (size_t)row * A.stride4;
         uint4* dg = reinterpret_cast<uint4*>(fr_pre(d + 1));
-        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) {
-          const uint4 c = and_skip(pd[w], r4, w);
-          dg[w] = c;
-          if (PSMEM) reinterpret_cast<uint4*>(spre)[w] = c;
-        }
+        and_rows<false>(dg, PSMEM ? reinterpret_cast<uint4*>(spre) : nullptr, pd, r4, A.stride4);
         if (threadIdx.x == 0) {
           spre_depth = d + 1;
           xrow[xl] = row;

@@ -179,12 +179,24 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
   *retry = false;
   *out = EngineOutput{};
   void* hstage = nullptr;
-  FIM_TRY(stage_get(db, sizeof(DevCtrl), &hstage));
+  void* hcls = nullptr;
+  const unsigned long long* d_cls = ep->d_class_sets ? ep->d_class_sets : ep->d_class_work;
+  const bool want_cls = ep->class_out && d_cls && ep->n1;
+  const size_t ctrl_bytes = (sizeof(DevCtrl) + 63) & ~(size_t)63;
+  FIM_TRY(stage_get(db, ctrl_bytes + (want_cls ? ep->n1 * 8ull : 0ull), &hstage));
   FIM_CUDA(cudaMemcpyAsync(hstage, ep->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+  if (want_cls) {  // the per-class counters travel with the control block (one round trip)
+    hcls = static_cast<uint8_t*>(hstage) + ctrl_bytes;
+    FIM_CUDA(cudaMemcpyAsync(hcls, d_cls, ep->n1 * 8ull, cudaMemcpyDeviceToHost, st));
+  }
   FIM_CUDA(cudaStreamSynchronize(st));
   db->stage_used = 0;
   DevCtrl h;
   std::memcpy(&h, hstage, sizeof(DevCtrl));
+  if (want_cls) {
+    ep->class_out->resize(ep->n1);
+    std::memcpy(ep->class_out->data(), hcls, ep->n1 * 8ull);
+  }
   out->ctrl = h;
   if (ep->ev[0] && ep->n1 > 0) {
     float t = 0.f;
@@ -269,6 +281,7 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
   if (s == FIM_OK && cfg.class_work) ep.d_class_work = cfg.class_work;
   if (s == FIM_OK && cfg.class_sets) ep.d_class_sets = cfg.class_sets;
   ep.count_only = cfg.count_only;
+  ep.class_out = cfg.class_out;
   ep.max_sets = cfg.max_sets;
   for (int attempt = 0; s == FIM_OK && attempt < 4; ++attempt) {
     if ((s = engine_alloc(ws, &ep)) != FIM_OK) break;

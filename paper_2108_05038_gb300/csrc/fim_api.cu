@@ -537,6 +537,7 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   EngineInput in;
   EngineOutput eo;
   unsigned long long* d_work = nullptr;
+  std::vector<unsigned long long> per;  // per-class counters, read back with the control block
   for (;;) {  // minsup_s doubles while the sample has more than max_sample_itemsets frequent itemsets
     in = EngineInput{};
     in.bits = d_sbits;
@@ -562,6 +563,7 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
       FIM_TRY(ws_get(db->ws, WS_CLASSWORK, in.n1, &d_work));
       if (cost_kind == FIM_COST_INTERSECTIONS) cfg.class_work = d_work;
       else cfg.class_sets = d_work;
+      cfg.class_out = &per;
     }
     eo = EngineOutput{};
     const fim_status s = engine_mine(db, db->ws, in, cfg, &eo, nullptr);
@@ -574,15 +576,7 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   // per class (the lowest row of its itemsets): intersections = level-2 candidates (the later
   // frequent sample rows) + the DFS below; itemsets = {r}, its frequent pairs and the DFS sets
   std::vector<unsigned long long> tally(R, 0ull);
-  std::vector<unsigned long long> per(in.n1, 0ull);
-  const bool dfs_ran = cost_kind == FIM_COST_INTERSECTIONS ? in.n1 >= 3 : in.n1 >= 1;
-  if (dfs_ran) {
-    void* h = nullptr;
-    FIM_TRY(stage_get(db, (size_t)in.n1 * 8, &h));
-    FIM_CUDA(cudaMemcpyAsync(h, d_work, (size_t)in.n1 * 8, cudaMemcpyDeviceToHost, st));
-    FIM_TRY(stream_sync(db));
-    std::memcpy(per.data(), h, (size_t)in.n1 * 8);
-  }
+  per.resize(in.n1, 0ull);
   for (uint32_t i = 0; i < in.n1; ++i)
     tally[in.frows[i]] = per[i] + (cost_kind == FIM_COST_INTERSECTIONS ? (in.n1 - 1 - i) : 0ull);
   unsigned long long total = 0;

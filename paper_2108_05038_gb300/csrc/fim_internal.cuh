@@ -237,6 +237,7 @@ struct EngineConfig {
   unsigned long long* class_work = nullptr;  // optional device array (n1 entries): DFS intersections per top class
   unsigned long long* class_sets = nullptr;  // optional device array (n1 entries): itemsets per top class
   bool count_only = false;                   // count itemsets, write no records (no output buffers)
+  std::vector<unsigned long long>* class_out = nullptr;  // host copy of class_sets / class_work (n1 entries)
   uint64_t max_sets = 0;                     // 0 = no limit; else stop early past this many itemsets
 };
 
@@ -260,6 +261,7 @@ struct EnginePlan {
   unsigned long long* d_class_work = nullptr;  // optional per-class intersection counters (n1 entries)
   unsigned long long* d_class_sets = nullptr;  // optional per-class itemset counters (n1 entries)
   bool count_only = false;
+  std::vector<unsigned long long>* class_out = nullptr;  // read back with the control block
   uint64_t max_sets = 0;
   bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
   float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
