@@ -245,6 +245,70 @@ __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, co
   return s;
 }
 
+// As piece_popc over the nonzero 16-byte words of a shared-memory prefix only,
+// listed in nzl[0, nnz): a piece covers 32 * VEC list entries, so a prefix with
+// a fraction f of nonzero words costs f of the dense pieces, one round trip each.
+template <int VEC>
+__device__ __forceinline__ uint32_t piece_popc_list(const uint4* __restrict__ row, const uint4* pre,
+                                                    const uint16_t* nzl, uint32_t nnz, uint32_t base) {
+  uint32_t w[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const uint32_t e = base + v * 32;
+    w[v] = e < nnz ? (uint32_t)nzl[e] : 0xffffffffu;
+  }
+  uint4 a[VEC], b[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const bool ok = w[v] != 0xffffffffu;
+    b[v] = ok ? pre[w[v]] : make_uint4(0u, 0u, 0u, 0u);
+    a[v] = ok ? __ldg(row + w[v]) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v)
+    s += __popc(a[v].x & b[v].x) + __popc(a[v].y & b[v].y) + __popc(a[v].z & b[v].z) + __popc(a[v].w & b[v].w);
+  return s;
+}
+
+// nzl[0, n) = ascending indices of the nonzero 16-byte words of pre4[0, stride4)
+// (shared memory); every warp compacts one contiguous segment, ballots give the
+// positions.  All threads call it; returns n in every thread.  wcnt: one word
+// per warp of scratch.
+__device__ __forceinline__ uint32_t build_nz_list(const uint4* pre4, uint32_t stride4, uint16_t* nzl, uint32_t* wcnt,
+                                                  uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t seg = ((stride4 + nw - 1) / nw + 31) & ~31u;
+  const uint32_t beg = min(stride4, warp * seg), end = min(stride4, beg + seg);
+  uint32_t c = 0;
+  for (uint32_t w0 = beg; w0 < end; w0 += 32) {
+    const uint32_t w = w0 + lane;
+    c += __popc(__ballot_sync(0xffffffffu, w < end && any4(pre4[w])));
+  }
+  if (lane == 0) wcnt[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (uint32_t k = 0; k < nw; ++k) {
+      const uint32_t t = wcnt[k];
+      wcnt[k] = acc;
+      acc += t;
+    }
+    *total = acc;
+  }
+  __syncthreads();
+  uint32_t pos = wcnt[warp];
+  for (uint32_t w0 = beg; w0 < end; w0 += 32) {
+    const uint32_t w = w0 + lane;
+    const bool nz = w < end && any4(pre4[w]);
+    const uint32_t m = __ballot_sync(0xffffffffu, nz);
+    if (nz) nzl[pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
+    pos += __popc(m);
+  }
+  __syncthreads();
+  return *total;
+}
+
 // Block-wide dst[w] = a[w] & row[w] (and the same into dst2 when given), reading
 // row[w] only where a[w] is nonzero; four words per thread in flight per round
 // trip.  A_RO: `a` is read-only for the kernel's lifetime (a bitmap row), so it
@@ -289,21 +353,25 @@ template <int VEC>
 __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint32_t* cnt, uint32_t* wtot,
                                                  const uint32_t* xid, const uint32_t* pre, bool pre_global,
                                                  const uint32_t* cand, uint32_t mode, uint32_t nc, uint32_t* out_list,
-                                                 uint32_t out_cap, uint32_t xlen) {
+                                                 uint32_t out_cap, uint32_t xlen, const uint16_t* nzl = nullptr,
+                                                 uint32_t nnz = 0) {
   const DfsLaunch& p = A.p;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
+  // pieces per candidate: over the nonzero-word list of the prefix when given, else over the row
+  const uint32_t nseg = nzl ? (nnz + 32 * VEC - 1) / (32 * VEC) : A.nseg;
   uint32_t nsurv = 0;
   for (uint32_t b0 = 0; b0 < nc; b0 += kCandBatch) {
     const uint32_t nb = min(kCandBatch, nc - b0);
     for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) cnt[k] = 0;
     __syncthreads();
-    const uint32_t total = nb * A.nseg;
+    const uint32_t total = nb * nseg;
     for (uint32_t pc = warp; pc < total; pc += nw) {
-      const uint32_t k = pc / A.nseg, g = pc - k * A.nseg;
+      const uint32_t k = pc / nseg, g = pc - k * nseg;
       const uint32_t row = cand_row(p, cand, mode, b0 + k);
       const uint4* rp = reinterpret_cast<const uint4*>(p.bits + (size_t)row * p.stride);
-      uint32_t s = piece_popc<VEC>(rp, pre4, g * 32 * VEC + lane, A.stride4, pre_global);
+      uint32_t s = nzl ? piece_popc_list<VEC>(rp, pre4, nzl, nnz, g * 32 * VEC + lane)
+                       : piece_popc<VEC>(rp, pre4, g * 32 * VEC + lane, A.stride4, pre_global);
       s = __reduce_add_sync(0xffffffffu, s);
       if (lane == 0 && s) atomicAdd(&cnt[k], s);
     }
@@ -436,7 +504,16 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
   uint32_t* f_cur = sp; sp += p.maxd + 1;
   uint32_t* xrow = sp; sp += A.max_len + 1;
   uint32_t* xidp = sp; sp += A.max_len + 1;
-  uint32_t* xid = sp;
+  uint32_t* xid = sp; sp += A.max_len + 1;
+  uint16_t* nzl = reinterpret_cast<uint16_t*>(sp);  // nonzero-word list of the shared prefix (PSMEM)
+  __shared__ uint32_t nz_total;
+  // sparse pieces pay off when at most half of the prefix's 16-byte words are nonzero
+  auto node_list = [&](uint32_t* nn) -> const uint16_t* {
+    if (!PSMEM) return nullptr;
+    const uint32_t n = build_nz_list(reinterpret_cast<const uint4*>(spre), A.stride4, nzl, wtot, &nz_total);
+    *nn = n;
+    return 2 * n <= A.stride4 ? nzl : nullptr;
+  };
 
   const uint64_t per_depth = dfs_arena_depth_words(p.stride, p.n1);
   uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
@@ -547,8 +624,10 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       st_inter += nc;
       if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)nc);
     }
+    uint32_t nnz = 0;
+    const uint16_t* nl = nc ? node_list(&nnz) : nullptr;
     const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, pre, pre_global, cand, mode, nc, slot_list(0),
-                                          list_cap, xlen0);
+                                          list_cap, xlen0, nl, nnz);
     if (ns >= 2) {
       // the root prefix goes to depth slot 0 (it is in shared memory or in the ring slot)
       if (PSMEM || C.kind == 2) {
@@ -674,8 +753,11 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         st_inter += ncc;
         if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)ncc);
       }
+      uint32_t nnz2 = 0;
+      const uint16_t* nl2 = ncc ? node_list(&nnz2) : nullptr;
       const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : slot_pre(d + 1), false,
-                                            slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl);
+                                            slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl,
+                                            nl2, nnz2);
       if (n2 >= 2 && PSMEM) {
         const uint4* s4 = reinterpret_cast<const uint4*>(spre);
         uint4* d4 = reinterpret_cast<uint4*>(slot_pre(d + 1));
@@ -1175,7 +1257,7 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
 size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem, uint32_t mode) {
   size_t words = prefix_in_smem ? stride : 0;
   if (mode == 1) words += 2ull * kPairBatch + 8ull * (maxd + 1) + 3ull * (max_len + 1);
-  else words += kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1);
+  else words += kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1) + (prefix_in_smem ? stride / 8 + 1 : 0);
   return words * sizeof(uint32_t);
 }
 
