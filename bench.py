@@ -36,6 +36,9 @@ WORKLOAD = "sparse_mid"  # the configuration the headline metric is quoted on; -
 SAMPLE_RATE = 0.01
 EST_SEED = 1
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one launch of the current k_pair_counts, from one ncu capture of the
+# mine's launch per workload (profiles/k_pair_counts_sparse_mid.md); None where none was taken
+PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_693_850_000}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 
 
@@ -234,7 +237,7 @@ def run_ours(args):
                              "step": round(max_ms / args.steps, 4)},
             "roofline": {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                          "peak": round(alu_peak_gword, 1), "unit": "Gword/s", "frac": round(achieved_gword / alu_peak_gword, 4),
-                         "traffic": None,
+                         "traffic": PAIR_KERNEL_TRAFFIC.get(args.workload),
                          "peak_source": "derived: (64 LOP3 + 32 POPC lanes/clk/SM) -> 42.67 word pairs/clk/SM x SMs "
                                         "x max SM clock"},
             "e2e": {"value": round(tot_bytes / max_e2e / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
@@ -364,6 +367,32 @@ def run_balance(args):
         out[f"estimate_{kind}"] = r
     db.free()
     return out
+
+
+def run_once(args):
+    """One build + one mine of a workload, nothing else (for profiler captures): with --no-estimate the
+    mine's kernels are the first of their kind in the process."""
+    import torch
+
+    from paper_2108_05038_gb300 import fim
+
+    torch.cuda.set_device(0)
+    w = synth.make_workload(args.workload)
+    w["name"] = args.workload
+    d_off = torch.from_numpy(w["offsets"].astype(np.int32)).cuda()
+    d_items = torch.from_numpy(w["items"].astype(np.int32)).cuda()
+    db = fim.build_vertical_db_device(d_off, d_items, w["D"], w["N"], w["word_bits"], 0)
+    if not args.no_estimate:
+        db.estimate_class_costs(SAMPLE_RATE, w["rel_minsup"], EST_SEED)
+    res = db.mine(w["minsup"], result_on_device=True, collect_times=True)
+    st = res.stats
+    res.free()
+    db.free()
+    return {"mode": "once", "config": {"workload": workload_desc(w), "estimate": not args.no_estimate},
+            "n_frequent": st["n_frequent"], "n_intersections": st["n_intersections"],
+            "ms_pair_kernel": round(st["ms_pair_kernel"], 4), "ms_dfs_kernel": round(st["ms_dfs_kernel"], 4),
+            "bytes_pair_kernel": st["bytes_pair_kernel"], "bytes_dfs_kernel": st["bytes_dfs_kernel"],
+            "gpu_launches": fim.kernel_launches()}
 
 
 def _gen_request(r):
@@ -552,10 +581,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--mode", default="step", choices=["step", "plan", "serve", "balance"],
+    ap.add_argument("--no-estimate", action="store_true", help="--mode once: mine without a sample estimate")
+    ap.add_argument("--mode", default="step", choices=["step", "plan", "serve", "balance", "once"],
                     help="step: build+estimate+mine per step (default); plan: graph replays of one captured "
                          "mine; serve: the request loop against the plain one-job-at-a-time loop; balance: "
-                         "estimated vs actual class costs and the DFS load balance per class order")
+                         "estimated vs actual class costs and the DFS load balance per class order; once: one "
+                         "build + mine (profiler captures)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--slots", type=int, default=4)
@@ -570,6 +601,8 @@ def main():
         out = run_serve(args)
     elif args.mode == "balance":
         out = run_balance(args)
+    elif args.mode == "once":
+        out = run_once(args)
     else:
         out = run_ours(args)
     if out is not None:
