@@ -152,13 +152,15 @@ def run_ours(args):
     stats = None
     wall0 = time.perf_counter()
     launches0 = fim.kernel_launches()
+    step_ms = []
     for _ in range(args.steps):
         flush.fill_(1)  # write 512 MB: the 129 MB L2 holds nothing of the previous step
         e0.record(stream)
         stats = step()
         e1.record(stream)
         e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
+        step_ms.append(e0.elapsed_time(e1))
+        total_ms += step_ms[-1]
         bytes_alg += stats["bytes_algorithmic"]
         n_sets += stats["n_frequent"]
     torch.cuda.synchronize()
@@ -234,7 +236,9 @@ def run_ours(args):
             "itemsets_per_s": round(tot_sets / (max_ms * 1e-3), 1),
             "n_frequent": int(stats["n_frequent"]),
             "breakdown_ms": {"pair_kernel": round(pair_avg, 4), "dfs_kernel": round(dfs_avg, 4),
-                             "step": round(max_ms / args.steps, 4)},
+                             "step": round(max_ms / args.steps, 4),
+                             "step_min": round(min(step_ms), 4), "step_median": round(statistics.median(step_ms), 4),
+                             "step_max": round(max(step_ms), 4)},
             "roofline": {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                          "peak": round(alu_peak_gword, 1), "unit": "Gword/s", "frac": round(achieved_gword / alu_peak_gword, 4),
                          "traffic": PAIR_KERNEL_TRAFFIC.get(args.workload),
@@ -377,7 +381,7 @@ def run_once(args):
     from paper_2108_05038_gb300 import fim
 
     torch.cuda.set_device(0)
-    w = synth.make_workload(args.workload)
+    w = synth.make_workload(args.workload, D=args.D)
     w["name"] = args.workload
     d_off = torch.from_numpy(w["offsets"].astype(np.int32)).cuda()
     d_items = torch.from_numpy(w["items"].astype(np.int32)).cuda()
@@ -582,6 +586,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-estimate", action="store_true", help="--mode once: mine without a sample estimate")
+    ap.add_argument("--D", type=int, default=None, help="--mode once: the workload's laws at another D")
     ap.add_argument("--mode", default="step", choices=["step", "plan", "serve", "balance", "once"],
                     help="step: build+estimate+mine per step (default); plan: graph replays of one captured "
                          "mine; serve: the request loop against the plain one-job-at-a-time loop; balance: "

@@ -507,9 +507,10 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
   uint32_t* xid = sp; sp += A.max_len + 1;
   uint16_t* nzl = reinterpret_cast<uint16_t*>(sp);  // nonzero-word list of the shared prefix (PSMEM)
   __shared__ uint32_t nz_total;
-  // sparse pieces pay off when at most half of the prefix's 16-byte words are nonzero
-  auto node_list = [&](uint32_t* nn) -> const uint16_t* {
-    if (!PSMEM) return nullptr;
+  // sparse pieces pay off when at most half of the prefix's 16-byte words are nonzero and the
+  // node has enough dense pieces (>= 4 per warp) to repay the two passes that build the list
+  auto node_list = [&](uint32_t nc, uint32_t* nn) -> const uint16_t* {
+    if (!PSMEM || nc * A.nseg < 4u * (blockDim.x >> 5)) return nullptr;
     const uint32_t n = build_nz_list(reinterpret_cast<const uint4*>(spre), A.stride4, nzl, wtot, &nz_total);
     *nn = n;
     return 2 * n <= A.stride4 ? nzl : nullptr;
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)nc);
     }
     uint32_t nnz = 0;
-    const uint16_t* nl = nc ? node_list(&nnz) : nullptr;
+    const uint16_t* nl = node_list(nc, &nnz);
     const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, pre, pre_global, cand, mode, nc, slot_list(0),
                                           list_cap, xlen0, nl, nnz);
     if (ns >= 2) {
@@ -754,7 +755,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)ncc);
       }
       uint32_t nnz2 = 0;
-      const uint16_t* nl2 = ncc ? node_list(&nnz2) : nullptr;
+      const uint16_t* nl2 = node_list(ncc, &nnz2);
       const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, PSMEM ? spre : slot_pre(d + 1), false,
                                             slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl,
                                             nl2, nnz2);
