@@ -27,6 +27,7 @@
 namespace fim {
 namespace {
 
+constexpr uint32_t kDensePrefix = 0xffffffffu;  // stack slot header: the prefix is stored dense
 constexpr uint32_t kCandBatch = 1024;  // candidates counted per pass (shared-memory counters)
 
 // Exclusive block-wide scan of a 0/1 flag.  wtot: 33 shared words.  Returns
@@ -507,19 +508,72 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
   uint32_t* xid = sp; sp += A.max_len + 1;
   uint16_t* nzl = reinterpret_cast<uint16_t*>(sp);  // nonzero-word list of the shared prefix (PSMEM)
   __shared__ uint32_t nz_total;
-  // sparse pieces pay off when at most half of the prefix's 16-byte words are nonzero and the
-  // node has enough dense pieces (>= 4 per warp) to repay the two passes that build the list
+  const uint64_t per_depth = dfs_arena_depth_words(p.stride, p.n1);
+  const uint64_t lw = dfs_list_words(p.stride);
+  uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
+#define slot_pre(d) (arena + (size_t)(d) * per_depth)
+#define slot_hdr(d) (arena + (size_t)(d) * per_depth + p.stride)
+#define slot_list(d) (arena + (size_t)(d) * per_depth + p.stride + lw)
+  // Wide prefixes (more than four 16-byte words per thread) held in shared memory get the list of
+  // their nonzero words: counting runs over it when at most half of the words are nonzero, and such
+  // a prefix is saved on the stack as (list, values) so that its children read only those words.
+  const bool use_lists = PSMEM && A.stride4 > 4u * blockDim.x;
   auto node_list = [&](uint32_t nc, uint32_t* nn) -> const uint16_t* {
-    if (!PSMEM || nc * A.nseg < 4u * (blockDim.x >> 5)) return nullptr;
+    if (!use_lists || nc == 0) return nullptr;
     const uint32_t n = build_nz_list(reinterpret_cast<const uint4*>(spre), A.stride4, nzl, wtot, &nz_total);
     *nn = n;
     return 2 * n <= A.stride4 ? nzl : nullptr;
   };
+  // stack slot d <- the shared prefix (after process_node of that node; the list is still valid)
+  auto save_prefix = [&](uint32_t d) {
+    uint32_t* hdr = slot_hdr(d);
+    const uint32_t n = nz_total;
+    uint4* gv = reinterpret_cast<uint4*>(slot_pre(d));
+    const uint4* s4 = reinterpret_cast<const uint4*>(spre);
+    if (use_lists && 2 * n <= A.stride4) {
+      uint16_t* gl = reinterpret_cast<uint16_t*>(hdr + 4);
+      if (threadIdx.x == 0) hdr[0] = n;
+      for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const uint32_t w = nzl[e];
+        gl[e] = (uint16_t)w;
+        gv[e] = s4[w];
+      }
+    } else {
+      if (threadIdx.x == 0) hdr[0] = kDensePrefix;
+      for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) gv[w] = s4[w];
+    }
+  };
+  // dst <- (prefix of slot d) & row r4, dense image; dst is shared memory or a ring slot
+  auto child_prefix = [&](uint4* dst, uint32_t d, const uint4* r4) {
+    const uint32_t* hdr = slot_hdr(d);
+    const uint32_t n = PSMEM ? *(volatile const uint32_t*)hdr : kDensePrefix;
+    const uint4* gv = reinterpret_cast<const uint4*>(slot_pre(d));
+    if (n == kDensePrefix) {
+      and_rows<false>(dst, nullptr, gv, r4, A.stride4);
+      return;
+    }
+    const uint16_t* gl = reinterpret_cast<const uint16_t*>(hdr + 4);
+    for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) dst[w] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    constexpr uint32_t U = 4;
+    for (uint32_t e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+      uint32_t w[U];
+      uint4 v[U], b[U];
+#pragma unroll
+      for (uint32_t u = 0; u < U; ++u) {
+        const uint32_t e = e0 + u * blockDim.x;
+        w[u] = e < n ? (uint32_t)gl[e] : 0xffffffffu;
+        v[u] = e < n ? gv[e] : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < U; ++u) b[u] = w[u] != 0xffffffffu ? __ldg(r4 + w[u]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (uint32_t u = 0; u < U; ++u)
+        if (w[u] != 0xffffffffu)
+          dst[w[u]] = make_uint4(v[u].x & b[u].x, v[u].y & b[u].y, v[u].z & b[u].z, v[u].w & b[u].w);
+    }
+  };
 
-  const uint64_t per_depth = dfs_arena_depth_words(p.stride, p.n1);
-  uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
-#define slot_pre(d) (arena + (size_t)(d) * per_depth)
-#define slot_list(d) (arena + (size_t)(d) * per_depth + p.stride)
   const uint32_t list_cap = p.n1;
   const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
   const uint32_t L = A.max_len;
@@ -631,10 +685,13 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
                                           list_cap, xlen0, nl, nnz);
     if (ns >= 2) {
       // the root prefix goes to depth slot 0 (it is in shared memory or in the ring slot)
-      if (PSMEM || C.kind == 2) {
+      if (PSMEM) {
+        if (!use_lists) nz_total = 0;  // (no list: saved dense)
+        save_prefix(0);
+      } else if (C.kind == 2) {
         const uint4* s4 = reinterpret_cast<const uint4*>(pre);
         uint4* d4 = reinterpret_cast<uint4*>(slot_pre(0));
-        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = pre_global ? __ldcg(s4 + w) : s4[w];
+        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = __ldcg(s4 + w);
       }
     }
     if (threadIdx.x == 0) {
@@ -723,10 +780,8 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
         }
         const uint32_t* src_list = slot_list(fd) + 2 * coff;
         for (uint32_t k = threadIdx.x; k < 2 * ncd; k += blockDim.x) sl[kDfsSlotHeader + 2 * L + k] = src_list[k];
-        const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(fd));
         const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
-        uint4* d4 = reinterpret_cast<uint4*>(sl + (sw - p.stride));
-        and_rows<false>(d4, nullptr, a4, r4, A.stride4);
+        child_prefix(reinterpret_cast<uint4*>(sl + (sw - p.stride)), fd, r4);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -742,12 +797,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       const int32_t d = C.depth;
       const uint32_t ncc = C.nc, coff = C.cand_off;
       const uint32_t xl = xlen0 + d + 1;  // prefix length of the child
-      {
-        const uint4* a4 = reinterpret_cast<const uint4*>(slot_pre(d));
-        const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
-        uint4* d4 = reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(d + 1));
-        and_rows<false>(d4, nullptr, a4, r4, A.stride4);
-      }
+      child_prefix(reinterpret_cast<uint4*>(PSMEM ? spre : slot_pre(d + 1)), d, bits4 + (size_t)C.s_row * A.stride4);
       sort_path_ids(xidp, xl, xid);
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -760,9 +810,8 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
                                             slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl,
                                             nl2, nnz2);
       if (n2 >= 2 && PSMEM) {
-        const uint4* s4 = reinterpret_cast<const uint4*>(spre);
-        uint4* d4 = reinterpret_cast<uint4*>(slot_pre(d + 1));
-        for (uint32_t w = threadIdx.x; w < A.stride4; w += blockDim.x) d4[w] = s4[w];
+        if (!use_lists) nz_total = 0;
+        save_prefix(d + 1);
       }
       if (threadIdx.x == 0) {
         atomicAdd(&p.ctrl->n_nodes, 1ull);
@@ -783,6 +832,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
     if (p.cta_time) p.cta_time[2 * blockIdx.x + 1] = global_ns();
   }
 #undef slot_pre
+#undef slot_hdr
 #undef slot_list
 }
 

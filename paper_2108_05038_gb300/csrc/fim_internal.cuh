@@ -398,7 +398,12 @@ __host__ __device__ inline uint64_t frames_g_words(uint32_t n1) { return (2ull *
 __host__ __device__ inline uint64_t frames_depth_words(uint32_t stride, uint32_t n1) {
   return (uint64_t)stride + frames_g_words(n1) + 2ull * kDfsPairBatch;
 }
-// arena words per depth: one prefix bitmap + one (row, id) survivor list
-__host__ __device__ inline uint64_t dfs_arena_depth_words(uint32_t stride, uint32_t n1) { return (uint64_t)stride + ((2ull * n1 + 3) & ~3ull); }
+// node-mode arena words per depth: the prefix (stride words: dense, or the values of its nonzero
+// 16-byte words), its index list (4-word header + stride/8 words of 16-bit indices), one (row, id)
+// survivor list; every region a multiple of four words
+__host__ __device__ inline uint64_t dfs_list_words(uint32_t stride) { return (uint64_t)stride / 8 + 4; }
+__host__ __device__ inline uint64_t dfs_arena_depth_words(uint32_t stride, uint32_t n1) {
+  return (uint64_t)stride + dfs_list_words(stride) + ((2ull * n1 + 3) & ~3ull);
+}
 
 }  // namespace fim
