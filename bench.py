@@ -107,6 +107,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gather_ranks(values, dist, world: int, device: str):
+    """Every rank's per-rank figures (world x k array; one row when not distributed)."""
+    import torch
+
+    per_rank = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is None or world == 1:
+        return per_rank.cpu().numpy()[None, :]
+    gathered = [torch.zeros_like(per_rank) for _ in range(world)]
+    dist.all_gather(gathered, per_rank)
+    return torch.stack(gathered).cpu().numpy()
+
+
+def combine_ranks(allv):
+    """Replicas (weak scaling): the job takes as long as its slowest rank; bytes and itemsets add up.
+    Columns: device ms, algorithmic bytes, itemsets, end-to-end seconds."""
+    return float(allv[:, 0].max()), float(allv[:, 1].sum()), float(allv[:, 2].sum()), float(allv[:, 3].max())
+
+
 def run_ours(args):
     import torch
 
@@ -207,17 +225,8 @@ def run_ours(args):
     h2d = int(w["offsets"].nbytes + w["items"].nbytes)
 
     # max over ranks
-    per_rank = torch.tensor([total_ms, bytes_alg, n_sets, e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        gathered = [torch.zeros_like(per_rank) for _ in range(world)]
-        dist.all_gather(gathered, per_rank)
-        allv = torch.stack(gathered).cpu().numpy()
-    else:
-        allv = per_rank.cpu().numpy()[None, :]
-    max_ms = float(allv[:, 0].max())
-    tot_bytes = float(allv[:, 1].sum())
-    tot_sets = float(allv[:, 2].sum())
-    max_e2e = float(allv[:, 3].max())
+    allv = gather_ranks([total_ms, bytes_alg, n_sets, e2e_s], dist, world, "cuda")
+    max_ms, tot_bytes, tot_sets, max_e2e = combine_ranks(allv)
 
     out = None
     if rank == 0:
