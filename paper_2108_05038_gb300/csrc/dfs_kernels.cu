@@ -19,7 +19,9 @@
 // next unexpanded child of their shallowest open frame through a bounded
 // pool (the dynamic load balancing of the thesis's Phase 1, restated for a
 // device work queue); a counter of unfinished entries detects termination.
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "fim_internal.cuh"
@@ -1321,8 +1323,37 @@ uint64_t dfs_arena_cta_words(uint32_t stride, uint32_t n1, uint32_t maxd, uint32
   return dfs_arena_depth_words(stride, n1) * (maxd + 1);
 }
 
+static cudaError_t dfs_max_ctas_per_sm_query(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem,
+                                             uint32_t mode, int* out);
+
+// occupancy of a launch shape, asked once per shape and device (the query costs microseconds of host
+// time on every mine otherwise)
 cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, uint32_t mode,
                                 int* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, uint32_t, uint32_t, size_t, bool, uint32_t>, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(dev, threads, vec, smem, prefix_in_smem, mode);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+  }
+  e = dfs_max_ctas_per_sm_query(threads, vec, smem, prefix_in_smem, mode, out);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = *out;
+  }
+  return e;
+}
+
+static cudaError_t dfs_max_ctas_per_sm_query(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem,
+                                             uint32_t mode, int* out) {
   if (mode == 1) {
     if (prefix_in_smem) {
       switch (vec) {

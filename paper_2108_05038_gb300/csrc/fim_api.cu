@@ -163,6 +163,43 @@ void Workspace::release() {
   bytes = 0;
 }
 
+// Workspaces of freed databases, per device, handed to the next database built on that device:
+// a repeated build / estimate / mine then allocates nothing.  At most kWsCached workspaces and
+// 1/16 of the device memory are kept; the memory is idle (its stream was synchronised).
+static constexpr size_t kWsCached = 4;
+static std::mutex g_ws_mu;
+static std::vector<Workspace> g_ws_cache[64];
+
+static void ws_take_cached(int dev, Workspace* ws) {
+  if (dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto& c = g_ws_cache[dev];
+  if (c.empty()) return;
+  ws->bufs = std::move(c.back().bufs);
+  ws->bytes = c.back().bytes;
+  c.pop_back();
+}
+
+// called with the workspace's stream synchronised
+static void ws_give_back(int dev, uint64_t total_mem, Workspace* ws) {
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    auto& c = g_ws_cache[dev];
+    uint64_t held = ws->bytes;
+    for (const auto& w : c) held += w.bytes;
+    if (c.size() < kWsCached && held <= total_mem / 16) {
+      Workspace keep;
+      keep.bufs = std::move(ws->bufs);
+      keep.bytes = ws->bytes;
+      c.push_back(std::move(keep));
+      ws->bufs.clear();
+      ws->bytes = 0;
+      return;
+    }
+  }
+  ws->release();
+}
+
 
 // ---------------------------------------------------------------------------
 // mining engine
@@ -199,23 +236,12 @@ static fim_status db_init(fim_db* db, uint32_t D, uint32_t N, uint32_t word_bits
   FIM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, db->device));
   db->smem_optin = (size_t)optin;
   db->total_mem = device_total_mem(db->device);
+  ws_take_cached(db->device, &db->ws);
   db->W32 = (D + 31) / 32;
   db->stride = ((db->W32 + 31) / 32) * 32;
   return FIM_OK;
 }
 
-template <typename T>
-static fim_status dev_alloc(fim_db* db, T** p, size_t count) {
-  size_t bytes = std::max<size_t>(16, count * sizeof(T));
-  cudaError_t e = dev_malloc_async((void**)p, bytes, db->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return cuda_fail(e, "device allocation");
-  }
-  db->device_bytes += bytes;
-  return FIM_OK;
-}
 
 // Items counted (K1) on the input CSR (the caller's device arrays or the db's
 // copy of host arrays), the offsets validated on the device, rows relabelled on
@@ -240,8 +266,8 @@ static fim_status db_build_rows(fim_db* db, const uint32_t* src_off, const uint3
   db->max_tx_len = cnt[N + 1];
   if (device_input) {  // the offsets are valid: keep a copy of the CSR (the sample draw reads it)
     db->nnz = cnt[N + 3];
-    FIM_TRY(dev_alloc(db, &db->d_tx_off, (size_t)D + 1));
-    FIM_TRY(dev_alloc(db, &db->d_tx_items, std::max<uint64_t>(1, db->nnz)));
+    FIM_TRY(ws_get(db->ws, WS_DB_TXOFF, (size_t)D + 1, &db->d_tx_off));
+    FIM_TRY(ws_get(db->ws, WS_DB_TXITEMS, std::max<uint64_t>(1, db->nnz), &db->d_tx_items));
     FIM_CUDA(cudaMemcpyAsync(db->d_tx_off, src_off, ((size_t)D + 1) * 4, cudaMemcpyDeviceToDevice, st));
     if (db->nnz)
       FIM_CUDA(cudaMemcpyAsync(db->d_tx_items, src_items, db->nnz * 4ull, cudaMemcpyDeviceToDevice, st));
@@ -259,25 +285,25 @@ static fim_status db_build_rows(fim_db* db, const uint32_t* src_off, const uint3
     db->supp[r] = cnt[kept[r]];
     db->item_rank[kept[r]] = (int32_t)r;
   }
-  FIM_TRY(dev_alloc(db, &db->d_item_rank, N));
-  FIM_TRY(dev_alloc(db, &db->d_rank_item, db->n_rows));
-  FIM_TRY(dev_alloc(db, &db->d_supp, db->n_rows));
-  FIM_TRY(dev_alloc(db, &db->d_bits, (size_t)db->n_rows * db->stride));
-  FIM_TRY(dev_alloc(db, &db->d_iota, db->n_rows));
+  // item_rank | rank_item | supp | iota in one block (each part 16-byte aligned), filled by one copy
+  const size_t a4 = ((size_t)N + 3) & ~(size_t)3, r4 = ((size_t)db->n_rows + 3) & ~(size_t)3;
+  uint32_t* small = nullptr;
+  FIM_TRY(ws_get(db->ws, WS_DB_SMALL, a4 + 3 * r4 + 4, &small));
+  db->d_item_rank = reinterpret_cast<int32_t*>(small);
+  db->d_rank_item = small + a4;
+  db->d_supp = small + a4 + r4;
+  db->d_iota = small + a4 + 2 * r4;
+  FIM_TRY(ws_get(db->ws, WS_DB_BITS, std::max<size_t>(1, (size_t)db->n_rows * db->stride), &db->d_bits));
   {
     void* h = nullptr;
-    FIM_TRY(stage_get(db, ((size_t)N + 2ull * db->n_rows) * 4, &h));
+    FIM_TRY(stage_get(db, (a4 + 2 * r4) * 4, &h));
     uint32_t* hu = static_cast<uint32_t*>(h);
     std::memcpy(hu, db->item_rank.data(), (size_t)N * 4);
     if (db->n_rows) {
-      std::memcpy(hu + N, db->rank_item.data(), (size_t)db->n_rows * 4);
-      std::memcpy(hu + N + db->n_rows, db->supp.data(), (size_t)db->n_rows * 4);
+      std::memcpy(hu + a4, db->rank_item.data(), (size_t)db->n_rows * 4);
+      std::memcpy(hu + a4 + r4, db->supp.data(), (size_t)db->n_rows * 4);
     }
-    FIM_CUDA(cudaMemcpyAsync(db->d_item_rank, hu, (size_t)N * 4, cudaMemcpyHostToDevice, st));
-    if (db->n_rows) {
-      FIM_CUDA(cudaMemcpyAsync(db->d_rank_item, hu + N, (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
-      FIM_CUDA(cudaMemcpyAsync(db->d_supp, hu + N + db->n_rows, (size_t)db->n_rows * 4, cudaMemcpyHostToDevice, st));
-    }
+    FIM_CUDA(cudaMemcpyAsync(small, hu, (a4 + 2 * r4) * 4, cudaMemcpyHostToDevice, st));
   }
   FIM_CUDA(launch_iota(db->d_iota, db->n_rows, st));
   if (db->n_rows) {
@@ -313,8 +339,9 @@ static fim_status build_common(const uint32_t* off, const uint32_t* items, uint3
       if (off[t + 1] < off[t]) return bail(fail(FIM_ERR_INVALID, "tx_offsets is not non-decreasing"));
     db->nnz = off[D];
     if (db->nnz > 0 && !items) return bail(fail(FIM_ERR_INVALID, "tx_items is NULL"));
-    if ((s = dev_alloc(db, &db->d_tx_off, (size_t)D + 1)) != FIM_OK) return bail(s);
-    if ((s = dev_alloc(db, &db->d_tx_items, std::max<uint64_t>(1, db->nnz))) != FIM_OK) return bail(s);
+    if ((s = ws_get(db->ws, WS_DB_TXOFF, (size_t)D + 1, &db->d_tx_off)) != FIM_OK) return bail(s);
+    if ((s = ws_get(db->ws, WS_DB_TXITEMS, std::max<uint64_t>(1, db->nnz), &db->d_tx_items)) != FIM_OK)
+      return bail(s);
     cudaError_t e = cudaMemcpyAsync(db->d_tx_off, off, ((size_t)D + 1) * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && db->nnz) e = cudaMemcpyAsync(db->d_tx_items, items, db->nnz * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "copying the CSR database"));
@@ -676,12 +703,12 @@ void fim_result_free(fim_result* res) {
 
 void fim_db_free(fim_db* db) {
   if (!db) return;
-  cudaStream_t st = db->stream;
-  db->ws.release();
-  void* ptrs[] = {db->d_bits, db->d_rank_item, db->d_item_rank, db->d_supp, db->d_tx_off, db->d_tx_items, db->d_iota};
-  for (void* p : ptrs)
-    if (p) cudaFreeAsync(p, st);
-  cudaStreamSynchronize(st);
+  if (cudaStreamSynchronize(db->stream) == cudaSuccess) {
+    ws_give_back(db->device, db->total_mem, &db->ws);  // idle now: the next database may reuse it
+  } else {
+    cudaGetLastError();
+    db->ws.release();
+  }
   fim::pinned_release(db->stage, db->stage_cap);
   delete db;
 }

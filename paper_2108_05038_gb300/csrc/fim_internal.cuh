@@ -96,6 +96,11 @@ enum WsSlot {
   WS_TALLY,
   WS_CLASSWORK,
   WS_CTATIME,
+  // the database's own arrays (kept in the workspace so that a freed database's memory serves the next)
+  WS_DB_TXOFF,
+  WS_DB_TXITEMS,
+  WS_DB_BITS,
+  WS_DB_SMALL,  // item_rank (N) | rank_item (rows) | supp (rows) | iota (rows), each 16-byte aligned
   WS_COUNT
 };
 
