@@ -321,6 +321,20 @@ def test_class_work_matches_literal_eclat(seed, mode):
     assert int(res.class_work.sum()) == res.stats["n_intersections"]
 
 
+def test_workspaces_pass_between_databases():
+    """A freed database's device workspace serves the next build (larger, smaller, other data): every
+    result stays exact."""
+    for name, D, ms in (("sparse_mid", 30_000, 75), ("tiny", 4000, 40), ("dense_deep", 20_000, 12_000),
+                        ("sparse_mid", 60_000, 150), ("tiny", 2000, 20)):
+        w = synth.make_workload(name, D=D)
+        want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+        db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+        db.estimate_class_costs(0.05, ms / D, 3)
+        got = db.mine(ms).as_dict()
+        db.free()
+        assert_same(got, want)
+
+
 def test_repeated_mines_reuse_workspace():
     w = synth.make_workload("tiny", D=8000)
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
