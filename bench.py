@@ -56,21 +56,26 @@ def workload_desc(w):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, one sample every 50 ms, each stamped with its arrival time.
+
+    Started before the clock ramp so that it is streaming when the timed region begins; `summary`
+    reports the samples that arrived during the timed region, or, when the region is shorter than
+    the sampling interval, those since the ramp began (the GPU is under load throughout)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_S = 0.05
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.samples = []  # (arrival time, line)
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(int(self.INTERVAL_S * 1000))],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -79,19 +84,27 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.samples.append((time.perf_counter(), line.strip()))
 
     def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t_load: float, t0: float, t1: float):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        inside = [ln for t, ln in self.samples if t0 <= t <= t1 + self.INTERVAL_S]
+        window = "timed region"
+        if not inside:
+            inside = [ln for t, ln in self.samples if t_load <= t <= t1 + self.INTERVAL_S]
+            window = "clock ramp + warm-up + timed region (timed region shorter than the 50 ms sampling interval)"
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -104,7 +117,7 @@ class ClockSampler:
                 if flag.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def gather_ranks(values, dist, world: int, device: str):
@@ -158,6 +171,8 @@ def run_ours(args):
         db.free()
         return st
 
+    clocks = ClockSampler(local)
+    clocks.start()
     # bring the SM clocks up from idle (a few hundred ms of device work) before the warm-up steps:
     # sub-millisecond steps would otherwise be timed while the clocks still ramp
     t_ramp = time.perf_counter()
@@ -168,8 +183,6 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
-    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -193,8 +206,10 @@ def run_ours(args):
     launches = fim.kernel_launches() - launches0  # the library's own kernels in the timed region
     if dist:
         dist.barrier()
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
+    t_end = time.perf_counter()
+    wall = t_end - wall0
+    clocks.stop()
+    clk = clocks.summary(t_ramp, wall0, t_end)
 
     # dominant kernel: live CUDA-event timing of each launch inside the library
     pair_ms, dfs_ms, reps = [], [], max(3, args.steps)

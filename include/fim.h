@@ -78,12 +78,19 @@ typedef struct {
   float reserved_f;
 } fim_mine_stats;
 
+/* Traversal of the persistent DFS (fim_mine_opts.dfs_mode). */
+enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2 };
+
 typedef struct {
   uint32_t struct_size;        /* set to sizeof(fim_mine_opts); 0 = treat as defaults            */
   uint32_t class_order;        /* fim_class_order                                                 */
-  uint32_t dfs_mode;           /* 0 = expand one class node at a time, 1 = count all children of a
-                                  frame in one pass (fewer dependent steps on deep classes)         */
-  uint32_t threads_per_cta;    /* persistent DFS CTA size: 0 = default, else 128/256/512          */
+  uint32_t dfs_mode;           /* FIM_DFS_NODES (0): expand one class node at a time;
+                                  FIM_DFS_FRAMES (1): count all children of a frame in one pass
+                                  (fewer dependent steps on short rows); FIM_DFS_AUTO (2, the
+                                  default): frames when rows are at most 2,048 words (8 KB), else
+                                  nodes                                                            */
+  uint32_t threads_per_cta;    /* persistent DFS CTA size: 0 = the one of 256 / 512 that keeps more
+                                  warps resident per SM, else 128/256/512                         */
   uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece: 0 = default, 1,2,4,8     */
   uint32_t ctas_per_sm;        /* 0 = as many as fit                                              */
   uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 0)          */

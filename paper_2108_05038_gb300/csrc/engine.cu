@@ -28,7 +28,9 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->bits = in.bits;
   ep->d_rank_item = in.d_rank_item;
   ep->num_sms = db->num_sms;
-  ep->mode = cfg.mode == 1 ? 1u : 0u;
+  // traversal: frame passes pay off on short rows (fewer dependent steps per intersection), node
+  // expansion with sparse prefixes on long ones
+  ep->mode = cfg.mode == 2 ? (in.stride <= 2048 ? 1u : 0u) : (cfg.mode == 1 ? 1u : 0u);
   ep->donate = ep->mode == 1 ? 0u : cfg.donate;  // frame passes do not donate
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
@@ -68,12 +70,21 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // persistent DFS geometry: itemsets are no longer than the longest transaction
   ep->L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
   ep->maxd_full = std::max<uint32_t>(1, ep->L - 2);
-  ep->threads = clamp_threads(cfg.threads);
   ep->vec = clamp_vec(cfg.vec);
   ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full, ep->mode);
   ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem, ep->mode);
   int occ = 0;
-  FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
+  if (cfg.threads == 0) {
+    // the DFS is latency bound: of 256 and 512 threads per CTA take the one with more resident warps
+    int o256 = 0, o512 = 0;
+    FIM_CUDA(dfs_max_ctas_per_sm(256, ep->vec, ep->smem, ep->psmem, ep->mode, &o256));
+    FIM_CUDA(dfs_max_ctas_per_sm(512, ep->vec, ep->smem, ep->psmem, ep->mode, &o512));
+    ep->threads = 2 * o512 > o256 ? 512u : 256u;
+    occ = ep->threads == 512 ? o512 : o256;
+  } else {
+    ep->threads = clamp_threads(cfg.threads);
+    FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
+  }
   if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
   const uint32_t cps = cfg.ctas_per_sm ? std::min<uint32_t>(cfg.ctas_per_sm, occ) : (uint32_t)occ;
   ep->grid = std::max<uint32_t>(1, (uint32_t)db->num_sms * cps);

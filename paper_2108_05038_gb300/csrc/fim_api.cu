@@ -367,7 +367,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   fim_mine_opts d;
   fim_mine_opts_init(&d);
   if (!o || o->struct_size == 0) o = &d;
-  c->threads = o->threads_per_cta ? o->threads_per_cta : 256;
+  c->threads = o->threads_per_cta;  // 0: chosen by the engine
   c->vec = o->vec_per_lane ? o->vec_per_lane : 4;
   c->ctas_per_sm = o->ctas_per_sm;
   c->donate = o->donate;
@@ -474,6 +474,7 @@ void fim_mine_opts_init(fim_mine_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->struct_size = sizeof(fim_mine_opts);
   o->class_order = FIM_ORDER_ESTIMATE;
+  o->dfs_mode = FIM_DFS_AUTO;
   o->donate = 0;
 }
 

@@ -17,6 +17,7 @@ from . import _build
 
 FIM_OK, FIM_ERR_INVALID, FIM_ERR_OOM, FIM_ERR_OUTPUT_OVERFLOW, FIM_ERR_CUDA, FIM_ERR_TIMEOUT = range(6)
 FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
+FIM_DFS_NODES, FIM_DFS_FRAMES, FIM_DFS_AUTO = 0, 1, 2
 SAMPLE_ITEMSET_LIMIT = 1 << 20  # FIM_SAMPLE_ITEMSET_LIMIT
 
 # every symbol declared in include/fim.h
@@ -268,10 +269,11 @@ class Database:
 
     def _opts(self, class_order="estimate", threads_per_cta=0, vec_per_lane=0, ctas_per_sm=0, donate=False,
               result_on_device=False, collect_times=False, out_capacity_sets=0, out_capacity_items=0, spin_limit=0,
-              stats=True, shape=None, dfs_mode=0, max_itemsets=0):
+              stats=True, shape=None, dfs_mode=None, max_itemsets=0):
         opts = MineOpts()
         self._lib.fim_mine_opts_init(ctypes.byref(opts))
-        opts.dfs_mode = dfs_mode
+        if dfs_mode is not None:
+            opts.dfs_mode = dfs_mode
         opts.class_order = {"estimate": FIM_ORDER_ESTIMATE, "uniform": FIM_ORDER_UNIFORM}[class_order]
         opts.threads_per_cta = threads_per_cta
         opts.vec_per_lane = vec_per_lane
@@ -311,7 +313,7 @@ class Database:
     def mine(self, minsup: int, class_order: str = "estimate", threads_per_cta: int = 0, vec_per_lane: int = 0,
              ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
              out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
-             shape=None, dfs_mode: int = 0, max_itemsets: int = 0, class_work: bool = False,
+             shape=None, dfs_mode: int | None = None, max_itemsets: int = 0, class_work: bool = False,
              dfs_depth_first: int = 0):
         """fim_mine; with ``class_work`` the result carries ``class_work`` (u64[n_rows]): the intersections
         of every one-row class, level 2 and below."""

@@ -52,7 +52,8 @@ def test_opts_struct_layout_matches_header():
     o = fim.MineOpts()
     lib.fim_mine_opts_init(ctypes.byref(o))
     assert o.struct_size == ctypes.sizeof(fim.MineOpts)
-    assert o.donate == 0 and o.class_order == fim.FIM_ORDER_ESTIMATE
+    assert o.donate == 0 and o.class_order == fim.FIM_ORDER_ESTIMATE and o.dfs_mode == fim.FIM_DFS_AUTO
+    assert o.threads_per_cta == 0 and o.vec_per_lane == 0
 
 
 @pytest.mark.parametrize("cname,pycls", [("fim_mine_stats", "MineStats"), ("fim_mine_opts", "MineOpts")])
