@@ -79,18 +79,23 @@ typedef struct {
 } fim_mine_stats;
 
 /* Traversal of the persistent DFS (fim_mine_opts.dfs_mode). */
-enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2 };
+enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3 };
 
 typedef struct {
   uint32_t struct_size;        /* set to sizeof(fim_mine_opts); 0 = treat as defaults            */
   uint32_t class_order;        /* fim_class_order                                                 */
-  uint32_t dfs_mode;           /* FIM_DFS_NODES (0): expand one class node at a time;
+  uint32_t dfs_mode;           /* FIM_DFS_NODES (0): expand one class node at a time, the prefix
+                                  dense in shared memory (or in its stack slot when too wide);
                                   FIM_DFS_FRAMES (1): count all children of a frame in one pass
-                                  (fewer dependent steps on short rows); FIM_DFS_AUTO (2, the
+                                  (fewer dependent steps on short rows); FIM_DFS_SPARSE (3): node
+                                  expansion with each prefix held as the list of its nonzero 16-byte
+                                  words when it has at most 2,048 of them (small CTAs, several per
+                                  SM), dense in its stack slot otherwise; rows of at most 65,535
+                                  16-byte words, no donation (else as NODES); FIM_DFS_AUTO (2, the
                                   default): frames when rows are at most 2,048 words (8 KB), else
-                                  nodes                                                            */
-  uint32_t threads_per_cta;    /* persistent DFS CTA size: 0 = the one of 256 / 512 that keeps more
-                                  warps resident per SM, else 128/256/512                         */
+                                  sparse nodes                                                     */
+  uint32_t threads_per_cta;    /* persistent DFS CTA size, 128/256/512; 0 = node modes: the one with
+                                  the most CTAs per SM (then warps), frames: the most warps        */
   uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece: 0 = default, 1,2,4,8     */
   uint32_t ctas_per_sm;        /* 0 = as many as fit                                              */
   uint32_t donate;             /* 1 = busy CTAs hand subclasses to idle CTAs (default 0)          */

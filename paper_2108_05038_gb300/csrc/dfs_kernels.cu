@@ -30,6 +30,7 @@ namespace fim {
 namespace {
 
 constexpr uint32_t kDensePrefix = 0xffffffffu;  // stack slot header: the prefix is stored dense
+constexpr uint32_t kSparseCap = 2048;  // sparse node mode: listed words of a shared-memory prefix (36 KB)
 constexpr uint32_t kCandBatch = 1024;  // candidates counted per pass (shared-memory counters)
 
 // Exclusive block-wide scan of a 0/1 flag.  wtot: 33 shared words.  Returns
@@ -209,6 +210,7 @@ struct DfsArgs {
   uint32_t stride4;
   uint32_t nseg;       // pieces per candidate row
   uint32_t max_len;    // itemset length bound (entries of the path arrays)
+  uint32_t cap;        // sparse node mode: nonzero 16-byte words a shared-memory prefix list holds
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -251,9 +253,12 @@ __device__ __forceinline__ uint32_t piece_popc(const uint4* __restrict__ row, co
 // As piece_popc over the nonzero 16-byte words of a shared-memory prefix only,
 // listed in nzl[0, nnz): a piece covers 32 * VEC list entries, so a prefix with
 // a fraction f of nonzero words costs f of the dense pieces, one round trip each.
+// The word values come from the dense prefix pre[nzl[e]], or from vals[e] when the
+// prefix is held as a list of (index, value) pairs only.
 template <int VEC>
 __device__ __forceinline__ uint32_t piece_popc_list(const uint4* __restrict__ row, const uint4* pre,
-                                                    const uint16_t* nzl, uint32_t nnz, uint32_t base) {
+                                                    const uint16_t* nzl, uint32_t nnz, uint32_t base,
+                                                    const uint4* vals) {
   uint32_t w[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) {
@@ -264,7 +269,7 @@ __device__ __forceinline__ uint32_t piece_popc_list(const uint4* __restrict__ ro
 #pragma unroll
   for (int v = 0; v < VEC; ++v) {
     const bool ok = w[v] != 0xffffffffu;
-    b[v] = ok ? pre[w[v]] : make_uint4(0u, 0u, 0u, 0u);
+    b[v] = ok ? (vals ? vals[base + v * 32] : pre[w[v]]) : make_uint4(0u, 0u, 0u, 0u);
     a[v] = ok ? __ldg(row + w[v]) : make_uint4(0u, 0u, 0u, 0u);
   }
   uint32_t s = 0;
@@ -357,7 +362,7 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
                                                  const uint32_t* xid, const uint32_t* pre, bool pre_global,
                                                  const uint32_t* cand, uint32_t mode, uint32_t nc, uint32_t* out_list,
                                                  uint32_t out_cap, uint32_t xlen, const uint16_t* nzl = nullptr,
-                                                 uint32_t nnz = 0) {
+                                                 uint32_t nnz = 0, const uint4* vals = nullptr) {
   const DfsLaunch& p = A.p;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
@@ -373,7 +378,7 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
       const uint32_t k = pc / nseg, g = pc - k * nseg;
       const uint32_t row = cand_row(p, cand, mode, b0 + k);
       const uint4* rp = reinterpret_cast<const uint4*>(p.bits + (size_t)row * p.stride);
-      uint32_t s = nzl ? piece_popc_list<VEC>(rp, pre4, nzl, nnz, g * 32 * VEC + lane)
+      uint32_t s = nzl ? piece_popc_list<VEC>(rp, pre4, nzl, nnz, g * 32 * VEC + lane, vals)
                        : piece_popc<VEC>(rp, pre4, g * 32 * VEC + lane, A.stride4, pre_global);
       s = __reduce_add_sync(0xffffffffu, s);
       if (lane == 0 && s) atomicAdd(&cnt[k], s);
@@ -867,6 +872,296 @@ __device__ __forceinline__ uint32_t pair_child(uint64_t p, uint32_t n, uint32_t 
   return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Node expansion with sparse prefixes (FIM_DFS_SPARSE).  A prefix whose
+// nonzero 16-byte words number at most A.cap lives in shared memory as a list
+// of (index, value) pairs only (18 bytes per nonzero word instead of the whole
+// row), so several small CTAs fit on an SM and their per-node barriers overlap;
+// a denser prefix stays dense in its stack slot and is counted from there with
+// sparse skipping.  Children of a listed prefix are built from its list alone:
+// value & candidate row at the listed indices, zero results dropped.
+
+// block-wide sum of one value per thread (wtot: 33 words of scratch); every thread gets the sum
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* wtot) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  if (lane == 0) wtot[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t k = 0; k < nw; ++k) t += wtot[k];
+    wtot[32] = t;
+  }
+  __syncthreads();
+  const uint32_t t = wtot[32];
+  __syncthreads();
+  return t;
+}
+
+// dst[w] = a[w] & row[w] over the whole row (row read only under nonzero a); returns the number of
+// nonzero results (block-wide).  A_RO as in and_rows.
+template <bool A_RO>
+__device__ __forceinline__ uint32_t and_rows_count(uint4* dst, const uint4* a4, const uint4* __restrict__ r4,
+                                                   uint32_t stride4, uint32_t* wtot) {
+  constexpr uint32_t U = 4;
+  uint32_t c = 0;
+  for (uint32_t w0 = threadIdx.x; w0 < stride4; w0 += U * blockDim.x) {
+    uint4 a[U], b[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t w = w0 + u * blockDim.x;
+      a[u] = w < stride4 ? (A_RO ? __ldg(a4 + w) : a4[w]) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) b[u] = any4(a[u]) ? __ldg(r4 + w0 + u * blockDim.x) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t w = w0 + u * blockDim.x;
+      if (w < stride4) {
+        const uint4 v = make_uint4(a[u].x & b[u].x, a[u].y & b[u].y, a[u].z & b[u].z, a[u].w & b[u].w);
+        dst[w] = v;
+        c += any4(v) ? 1u : 0u;
+      }
+    }
+  }
+  return block_sum(c, wtot);
+}
+
+// append (w, v) to the shared list when v is nonzero: one shared atomic per warp and call
+__device__ __forceinline__ void list_push(bool nz, uint32_t w, const uint4& v, uint16_t* sidx, uint4* sval,
+                                          uint32_t* count) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t m = __ballot_sync(0xffffffffu, nz);
+  uint32_t base = 0;
+  if (lane == 0 && m) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (nz) {
+    const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+    sidx[pos] = (uint16_t)w;
+    sval[pos] = v;
+  }
+}
+
+// shared list <- the nonzero words of a dense prefix in global memory (written by this CTA)
+__device__ __forceinline__ uint32_t list_from_dense(const uint4* src, uint32_t stride4, uint16_t* sidx, uint4* sval,
+                                                    uint32_t* count) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) *count = 0;
+  __syncthreads();
+  for (uint32_t w0 = warp * 32; w0 < stride4; w0 += nw * 32) {
+    const uint32_t w = w0 + lane;
+    const uint4 v = w < stride4 ? __ldcg(src + w) : make_uint4(0u, 0u, 0u, 0u);
+    list_push(any4(v), w, v, sidx, sval, count);
+  }
+  __syncthreads();
+  return *count;
+}
+
+// shared list <- (listed prefix of a stack slot) & row, zero results dropped
+__device__ __forceinline__ uint32_t list_from_list(const uint16_t* gl, const uint4* gv, uint32_t n,
+                                                   const uint4* __restrict__ r4, uint16_t* sidx, uint4* sval,
+                                                   uint32_t* count) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) *count = 0;
+  __syncthreads();
+  constexpr uint32_t U = 2;
+  for (uint32_t e0 = warp * 32 * U; e0 < n; e0 += nw * 32 * U) {
+    uint32_t w[U];
+    uint4 v[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t e = e0 + u * 32 + lane;
+      w[u] = e < n ? (uint32_t)gl[e] : 0xffffffffu;
+      v[u] = e < n ? gv[e] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint4 b = w[u] != 0xffffffffu ? __ldg(r4 + w[u]) : make_uint4(0u, 0u, 0u, 0u);
+      v[u] = make_uint4(v[u].x & b.x, v[u].y & b.y, v[u].z & b.z, v[u].w & b.w);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) list_push(w[u] != 0xffffffffu && any4(v[u]), w[u], v[u], sidx, sval, count);
+  }
+  __syncthreads();
+  return *count;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
+  const DfsLaunch& p = A.p;
+  if (p.cta_time && threadIdx.x == 0) p.cta_time[2 * blockIdx.x] = global_ns();
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ Ctl C;
+  __shared__ uint32_t wtot[33];
+  __shared__ uint32_t list_count;
+  // dynamic shared memory: [values: cap x 16 B] [cnt] [f_n] [f_cur] [xrow] [xidp] [xid] [indices: cap x 2 B]
+  uint4* sval = reinterpret_cast<uint4*>(smem);
+  uint32_t* sp = smem + 4ull * A.cap;
+  uint32_t* cnt = sp; sp += kCandBatch;
+  uint32_t* f_n = sp; sp += p.maxd + 1;
+  uint32_t* f_cur = sp; sp += p.maxd + 1;
+  uint32_t* xrow = sp; sp += A.max_len + 1;
+  uint32_t* xidp = sp; sp += A.max_len + 1;
+  uint32_t* xid = sp; sp += A.max_len + 1;
+  uint16_t* sidx = reinterpret_cast<uint16_t*>(sp);
+
+  const uint64_t per_depth = dfs_arena_depth_words(p.stride, p.n1);
+  const uint64_t lw = dfs_list_words(p.stride);
+  uint32_t* const arena = p.arena + (size_t)blockIdx.x * p.arena_cta_words;
+#define slot_pre(d) (arena + (size_t)(d) * per_depth)
+#define slot_hdr(d) (arena + (size_t)(d) * per_depth + p.stride)
+#define slot_list(d) (arena + (size_t)(d) * per_depth + p.stride + lw)
+  const uint32_t list_cap = p.n1;
+  const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
+  unsigned long long st_inter = 0, st_frames = 0;
+
+  // the current node's prefix: listed in shared memory (n <= cap) or dense in stack slot d
+  // stack slot d <- that prefix (the node has become a frame)
+  auto save = [&](uint32_t d, bool listed, uint32_t n) {
+    uint32_t* hdr = slot_hdr(d);
+    if (!listed) {  // its dense image is in the slot already
+      if (threadIdx.x == 0) hdr[0] = kDensePrefix;
+      return;
+    }
+    uint16_t* gl = reinterpret_cast<uint16_t*>(hdr + 4);
+    uint4* gv = reinterpret_cast<uint4*>(slot_pre(d));
+    if (threadIdx.x == 0) hdr[0] = n;
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+      gl[e] = sidx[e];
+      gv[e] = sval[e];
+    }
+  };
+
+  for (;;) {
+    // ---------------- acquire a class ----------------
+    if (threadIdx.x == 0) {
+      C.kind = 0;
+      bool stop = (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED) != 0;
+      if (!stop && p.max_sets && *(volatile unsigned long long*)&p.ctrl->sets_total > p.max_sets) {
+        atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        stop = true;
+      }
+      const uint32_t e = stop ? 0xffffffffu : atomicAdd(&p.ctrl->queue_head, 1u);
+      if (e < p.ctrl->n_entries) {
+        const uint2 en = p.entries[e];
+        C.kind = 1; C.a = en.x; C.b = en.y; C.cls = en.x;
+      }
+    }
+    __syncthreads();
+    if (C.kind == 0) break;
+
+    // ---------------- root node: X = {i, s_m}, candidates = survivors of i after s_m ----------------
+    const uint32_t i = C.a, m = C.b;
+    const uint32_t base = p.soff[i];
+    const uint32_t si = p.sitems[base + m];
+    const uint32_t r1 = p.frows[i], r2 = p.frows[si];
+    const uint32_t nc = p.scnt[i] - m - 1;
+    if (threadIdx.x == 0) { xrow[0] = r1; xidp[0] = p.rank_item[r1]; C.xlen0 = 2; }
+    if (threadIdx.x == 1) { xrow[1] = r2; xidp[1] = p.rank_item[r2]; }
+    uint32_t nz = and_rows_count<true>(reinterpret_cast<uint4*>(slot_pre(0)), bits4 + (size_t)r1 * A.stride4,
+                                       bits4 + (size_t)r2 * A.stride4, A.stride4, wtot);
+    bool listed = nz <= A.cap;
+    if (listed) nz = list_from_dense(reinterpret_cast<const uint4*>(slot_pre(0)), A.stride4, sidx, sval, &list_count);
+    sort_path_ids(xidp, 2, xid);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st_inter += nc;
+      if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)nc);
+    }
+    const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, slot_pre(0), !listed, p.sitems + base + m + 1,
+                                          CAND_FROW, nc, slot_list(0), list_cap, 2, listed ? sidx : nullptr, nz,
+                                          listed ? sval : nullptr);
+    if (ns >= 2) save(0, listed, nz);
+    if (threadIdx.x == 0) {
+      atomicAdd(&p.ctrl->n_nodes, 1ull);
+      atomicAdd(&p.ctrl->progress, 1u);
+      if (ns >= 2) { f_n[0] = ns; f_cur[0] = 0; C.depth = 0; ++st_frames; }
+      else C.depth = -1;
+    }
+
+    // ---------------- depth-first expansion ----------------
+    uint32_t poll = 0;
+    for (;;) {
+      __syncthreads();  // every thread has read the previous decision
+      if (threadIdx.x == 0) {
+        if (C.depth >= 0 && (++poll & 7) == 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
+        const int32_t d = C.depth;
+        if (d < 0) {
+          C.action = 4;
+        } else if (f_cur[d] + 1 >= f_n[d]) {
+          C.depth = d - 1;
+          C.action = 3;
+        } else if ((uint32_t)(d + 1) > p.maxd) {
+          atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+          C.depth = -1;
+          C.action = 3;
+        } else {
+          const uint32_t k = f_cur[d];
+          C.action = 1;
+          C.s_row = slot_list(d)[2 * k];
+          C.s_id = slot_list(d)[2 * k + 1];
+          C.cand_off = k + 1;
+          C.nc = f_n[d] - k - 1;
+          f_cur[d] = k + 1;
+          xrow[C.xlen0 + d] = C.s_row;
+          xidp[C.xlen0 + d] = C.s_id;
+        }
+      }
+      __syncthreads();
+      const uint32_t action = C.action;
+      if (action == 4) break;
+      if (action == 3) continue;
+      // expand the child [X_d u {s} | rest of frame d]
+      const int32_t d = C.depth;
+      const uint32_t ncc = C.nc, coff = C.cand_off;
+      const uint32_t xl = C.xlen0 + d + 1;  // prefix length of the child
+      const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
+      const uint32_t hdr = *(volatile const uint32_t*)slot_hdr(d);
+      uint32_t nz2;
+      bool listed2;
+      if (hdr != kDensePrefix) {  // listed parent: the child is listed too (no more nonzero words)
+        nz2 = list_from_list(reinterpret_cast<const uint16_t*>(slot_hdr(d) + 4),
+                             reinterpret_cast<const uint4*>(slot_pre(d)), hdr, r4, sidx, sval, &list_count);
+        listed2 = true;
+      } else {
+        nz2 = and_rows_count<false>(reinterpret_cast<uint4*>(slot_pre(d + 1)),
+                                    reinterpret_cast<const uint4*>(slot_pre(d)), r4, A.stride4, wtot);
+        listed2 = nz2 <= A.cap;
+        if (listed2)
+          nz2 = list_from_dense(reinterpret_cast<const uint4*>(slot_pre(d + 1)), A.stride4, sidx, sval, &list_count);
+      }
+      sort_path_ids(xidp, xl, xid);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        st_inter += ncc;
+        if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)ncc);
+      }
+      const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, slot_pre(d + 1), !listed2,
+                                            slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl,
+                                            listed2 ? sidx : nullptr, nz2, listed2 ? sval : nullptr);
+      if (n2 >= 2) save(d + 1, listed2, nz2);
+      if (threadIdx.x == 0) {
+        atomicAdd(&p.ctrl->n_nodes, 1ull);
+        atomicAdd(&p.ctrl->progress, 1u);
+        if (n2 >= 2) { f_n[d + 1] = n2; f_cur[d + 1] = 0; C.depth = d + 1; ++st_frames; }
+      }
+    }
+    // class finished
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicSub(&p.ctrl->pending, 1u);
+    }
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&p.ctrl->n_intersections, st_inter);
+    atomicAdd(&p.ctrl->n_frames, st_frames);
+    if (p.cta_time) p.cta_time[2 * blockIdx.x + 1] = global_ns();
+  }
+#undef slot_pre
+#undef slot_hdr
+#undef slot_list
+}
+
 template <int VEC>
 __device__ __forceinline__ uint32_t piece_popc3(const uint4* __restrict__ r1, const uint4* __restrict__ r2,
                                                 const uint4* pre, uint32_t base4, uint32_t stride4) {
@@ -1288,6 +1583,32 @@ cudaError_t occ_t(uint32_t threads, size_t smem, int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs<VEC, PSMEM>, (int)threads, smem);
 }
 
+template <int VEC>
+cudaError_t launch_sparse_t(const DfsArgs& a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_sparse<VEC>));
+  if (e != cudaSuccess) return e;
+  k_dfs_sparse<VEC><<<grid, threads, smem, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_vec(const DfsArgs& a, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
+                              cudaStream_t st) {
+  switch (vec) {
+    case 1: return launch_sparse_t<1>(a, grid, threads, smem, st);
+    case 2: return launch_sparse_t<2>(a, grid, threads, smem, st);
+    case 8: return launch_sparse_t<8>(a, grid, threads, smem, st);
+    default: return launch_sparse_t<4>(a, grid, threads, smem, st);
+  }
+}
+
+template <int VEC>
+cudaError_t occ_sparse_t(uint32_t threads, size_t smem, int* out) {
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_sparse<VEC>));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs_sparse<VEC>, (int)threads, smem);
+}
+
 }  // namespace
 
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
@@ -1307,7 +1628,13 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+uint32_t dfs_sparse_cap(uint32_t stride) { return std::min<uint32_t>(kSparseCap, std::max<uint32_t>(32, stride / 4)); }
+
 size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem, uint32_t mode) {
+  if (mode == 3) {  // listed prefix: values (16 B) + indices (2 B) per entry
+    const size_t cap = dfs_sparse_cap(stride);
+    return (4ull * cap + kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1) + cap / 2 + 1) * sizeof(uint32_t);
+  }
   size_t words = prefix_in_smem ? stride : 0;
   if (mode == 1) words += 2ull * kPairBatch + 8ull * (maxd + 1) + 3ull * (max_len + 1);
   else words += kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1) + (prefix_in_smem ? stride / 8 + 1 : 0);
@@ -1315,6 +1642,7 @@ size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool pre
 }
 
 bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd, uint32_t mode) {
+  if (mode == 3) return false;  // the sparse node mode never holds a dense prefix in shared memory
   return dfs_smem_bytes(stride, max_len, maxd, true, mode) + sizeof(Ctl) + sizeof(FrameCtl) + 33 * 4 + 512 <= smem_optin;
 }
 
@@ -1354,6 +1682,14 @@ cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, boo
 
 static cudaError_t dfs_max_ctas_per_sm_query(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem,
                                              uint32_t mode, int* out) {
+  if (mode == 3) {
+    switch (vec) {
+      case 1: return occ_sparse_t<1>(threads, smem, out);
+      case 2: return occ_sparse_t<2>(threads, smem, out);
+      case 8: return occ_sparse_t<8>(threads, smem, out);
+      default: return occ_sparse_t<4>(threads, smem, out);
+    }
+  }
   if (mode == 1) {
     if (prefix_in_smem) {
       switch (vec) {
@@ -1401,6 +1737,8 @@ cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint
   const uint32_t segw4 = 32u * vec;  // 16-byte vectors per piece
   a.nseg = (a.stride4 + segw4 - 1) / segw4;
   a.max_len = max_len;
+  a.cap = dfs_sparse_cap(p.stride);
+  if (mode == 3) return launch_sparse_vec(a, grid, threads, vec, smem, st);
   if (mode == 1) {
     if (prefix_in_smem) return launch_frames_vec<true>(a, grid, threads, vec, smem, st);
     return launch_frames_vec<false>(a, grid, threads, vec, smem, st);

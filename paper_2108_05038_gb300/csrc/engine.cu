@@ -30,8 +30,12 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->num_sms = db->num_sms;
   // traversal: frame passes pay off on short rows (fewer dependent steps per intersection), node
   // expansion with sparse prefixes on long ones
-  ep->mode = cfg.mode == 2 ? (in.stride <= 2048 ? 1u : 0u) : (cfg.mode == 1 ? 1u : 0u);
-  ep->donate = ep->mode == 1 ? 0u : cfg.donate;  // frame passes do not donate
+  // (16-bit word indices: listed prefixes need rows of at most 65,535 16-byte words)
+  const bool list_ok = in.stride / 4 <= 65535;
+  if (cfg.mode == 2) ep->mode = in.stride <= 2048 ? 1u : (list_ok && !cfg.donate ? 3u : 0u);
+  else if (cfg.mode == 3) ep->mode = list_ok && !cfg.donate ? 3u : 0u;
+  else ep->mode = cfg.mode == 1 ? 1u : 0u;
+  ep->donate = ep->mode == 0 ? cfg.donate : 0u;  // only dense node expansion donates
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
   ep->cap_sets = cfg.cap_sets ? cfg.cap_sets : std::max<uint64_t>((uint64_t)1 << 18, 8ull * n1 + 64);
@@ -75,12 +79,27 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem, ep->mode);
   int occ = 0;
   if (cfg.threads == 0) {
-    // the DFS is latency bound: of 256 and 512 threads per CTA take the one with more resident warps
-    int o256 = 0, o512 = 0;
-    FIM_CUDA(dfs_max_ctas_per_sm(256, ep->vec, ep->smem, ep->psmem, ep->mode, &o256));
-    FIM_CUDA(dfs_max_ctas_per_sm(512, ep->vec, ep->smem, ep->psmem, ep->mode, &o512));
-    ep->threads = 2 * o512 > o256 ? 512u : 256u;
-    occ = ep->threads == 512 ? o512 : o256;
+    // The DFS is latency bound.  Node expansion runs one class node per CTA with CTA-wide barriers
+    // between its steps, so more CTAs per SM (independent nodes in flight) beat bigger CTAs: the
+    // most CTAs per SM, then the most warps.  Frame passes spread one pass over the whole CTA: the
+    // most warps (256 on a tie).
+    const uint32_t cand[3] = {128, 256, 512};
+    int best_occ = 0;
+    uint32_t best_t = 256;
+    for (uint32_t t : cand) {
+      if (ep->mode == 1 && t == 128) continue;
+      int o = 0;
+      FIM_CUDA(dfs_max_ctas_per_sm(t, ep->vec, ep->smem, ep->psmem, ep->mode, &o));
+      if (o < 1) continue;
+      const bool better = ep->mode == 1 ? (uint64_t)o * t > (uint64_t)best_occ * best_t
+                                        : (o > best_occ || (o == best_occ && t > best_t));
+      if (best_occ == 0 || better) {
+        best_occ = o;
+        best_t = t;
+      }
+    }
+    ep->threads = best_t;
+    occ = best_occ;
   } else {
     ep->threads = clamp_threads(cfg.threads);
     FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));

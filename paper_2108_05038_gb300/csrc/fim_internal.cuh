@@ -382,7 +382,9 @@ struct DfsLaunch {
 // mode 0: node at a time (optionally with donation); mode 1: frame passes (all children of a frame together)
 cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
                        bool prefix_in_smem, uint32_t max_len, uint32_t mode, cudaStream_t st);
+// mode 0 node expansion (dense prefix), 1 frame passes, 3 node expansion with listed (sparse) prefixes
 size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem, uint32_t mode);
+uint32_t dfs_sparse_cap(uint32_t stride);
 cudaError_t launch_pool_init(uint32_t* pool, uint32_t slots, uint64_t slot_words, cudaStream_t st);
 cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem, uint32_t mode,
                                 int* out);

@@ -76,7 +76,8 @@ def test_random_tiny_vs_bruteforce(seed):
     off, items = csr(txs)
     for minsup in sorted({1, 2, max(1, D // 7), max(1, D // 2)}):
         want = odict(oracle.bruteforce(off, items, N, minsup))
-        got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64, dfs_mode=(seed // 2) % 2).as_dict()
+        got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64,
+                       dfs_mode=(0, 1, 3)[(seed // 2) % 3]).as_dict()
         assert_same(got, want)
 
 
@@ -90,7 +91,7 @@ def test_ragged_D(D):
     assert_same(gpu_mine(off, items, 12, minsup).as_dict(), odict(oracle.eclat(off, items, 12, minsup)))
 
 
-@pytest.mark.parametrize("k,mode,depth", [(11, 0, 0), (16, 0, 8), (11, 1, 4), (16, 1, 0)])
+@pytest.mark.parametrize("k,mode,depth", [(11, 0, 0), (16, 0, 8), (11, 1, 4), (16, 1, 0), (11, 3, 0), (16, 3, 4)])
 def test_identical_transactions_closed_form(k, mode, depth):
     """2^k - 1 itemsets of support D; with a first DFS stack of 4 or 8 the depth of 9 or 14 forces the
     regrown retry, with 0 the stack has the full depth at once."""
@@ -149,7 +150,7 @@ def test_invalid_device_offsets_rejected_before_reading_items(offsets, why):
 # ---------------------------------------------------------------- named workloads
 
 @pytest.mark.parametrize("name,mode", [("tiny", 0), ("dense_deep", 0), ("dense_exact37", 0), ("tiny", 1),
-                                       ("dense_deep", 1)])
+                                       ("dense_deep", 1), ("tiny", 3), ("dense_deep", 3)])
 def test_workload_full_size_exact(name, mode):
     w = synth.make_workload(name)
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
@@ -157,7 +158,7 @@ def test_workload_full_size_exact(name, mode):
     assert_same(got, want)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_sparse_mid_full_size_exact(mode):
     w = synth.make_workload("sparse_mid")
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
@@ -172,7 +173,8 @@ def test_sparse_mid_full_size_exact(mode):
                                                              (512, 8, True, "estimate", 0),
                                                              (512, 4, False, "estimate", 0),
                                                              (128, 1, False, "uniform", 1), (256, 4, False, "estimate", 1),
-                                                             (512, 8, False, "estimate", 1)])
+                                                             (512, 8, False, "estimate", 1), (128, 4, False, "estimate", 3),
+                                                             (256, 8, False, "uniform", 3), (512, 2, False, "estimate", 3)])
 def test_launch_shapes_and_orders_identical(threads, vec, donate, order, mode):
     """Item order, class order, CTA shape and donation never change the output (Sec. 8.2)."""
     w = synth.make_workload("dense_deep", D=20000)
@@ -187,6 +189,22 @@ def test_launch_shapes_and_orders_identical(threads, vec, donate, order, mode):
     assert_same(got, want)
 
 
+def test_sparse_mode_mixes_listed_and_dense_prefixes():
+    """300,000 transactions: five items in ~90% of them give prefixes with more nonzero words than a
+    shared-memory list holds (dense, counted from the stack), 25 items in ~0.5% give listed ones;
+    every DFS mode gives the oracle's answer."""
+    rng = np.random.default_rng(17)
+    D = 300_000
+    dense = rng.random((D, 5)) < 0.9
+    sparse = rng.random((D, 25)) < 0.005
+    txs = [list(np.nonzero(dense[t])[0]) + list(5 + np.nonzero(sparse[t])[0]) for t in range(D)]
+    off, items = csr(txs)
+    ms = 300
+    want = odict(oracle.eclat(off, items, 30, ms))
+    for mode in (3, 0, 1):
+        assert_same(gpu_mine(off, items, 30, ms, dfs_mode=mode).as_dict(), want)
+
+
 def test_work_counters_match_output_and_modes():
     """Intersections, class nodes and materialised prefixes reported by both DFS modes equal the counts
     derived from the oracle's output alone (bench.bitmap_work)."""
@@ -198,7 +216,7 @@ def test_work_counters_match_output_and_modes():
     rank = np.zeros(w["N"], dtype=np.int64)
     rank[order] = np.arange(len(order))
     I, Cn, M = bench.bitmap_work(so, si, rank)
-    for mode in (0, 1):
+    for mode in (0, 1, 3):
         st = gpu_mine(w["offsets"], w["items"], w["N"], ms, dfs_mode=mode).stats
         assert st["n_intersections"] == I
         rb = (30000 + 63) // 64 * 8
@@ -234,7 +252,7 @@ def test_fixed_capacity_overflow_then_retry():
     assert_same(got, want)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_itemset_limit_aborts_early(mode):
     """max_itemsets stops the mine once the output passes it (FIM_ERR_OUTPUT_OVERFLOW); the db stays usable."""
     off, items = csr([list(range(20))] * 50 + [[20]])
@@ -247,7 +265,7 @@ def test_itemset_limit_aborts_early(mode):
     assert len(got) == 2 ** 20 - 1
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_output_regrowth_reuses_pair_counts(mode):
     """2^20 - 1 itemsets of length up to 20 overflow the first output buffer and a 3-deep first DFS
     stack: the repeated runs skip the pair kernel (its counts stay in the workspace) and still give
@@ -262,7 +280,7 @@ def test_output_regrowth_reuses_pair_counts(mode):
     assert st["ms_pair_kernel"] > 0 and st["ms_device_total"] >= st["ms_dfs_kernel"] > 0
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_cta_busy_times_are_consistent(mode):
     """collect_times records every persistent CTA's resident time: 0 < mean <= max <= the kernel's time."""
     w = synth.make_workload("dense_deep", D=20_000)
@@ -305,7 +323,7 @@ def _literal_class_work(txs, N, minsup):
     return work
 
 
-@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1)])
+@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1), (4, 3), (5, 3)])
 def test_class_work_matches_literal_eclat(seed, mode):
     """class_work_out: intersections per one-row class equal a literal Eclat's count, and sum to the total."""
     rng = np.random.default_rng(700 + seed)
