@@ -368,7 +368,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   fim_mine_opts_init(&d);
   if (!o || o->struct_size == 0) o = &d;
   c->threads = o->threads_per_cta;  // 0: chosen by the engine
-  c->vec = o->vec_per_lane ? o->vec_per_lane : 4;
+  c->vec = o->vec_per_lane;  // 0: chosen by the engine
   c->ctas_per_sm = o->ctas_per_sm;
   c->donate = o->donate;
   c->mode = o->dfs_mode;

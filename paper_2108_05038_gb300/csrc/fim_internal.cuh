@@ -231,7 +231,7 @@ struct EngineOutput {
 struct EngineConfig {
   uint32_t depth_first = 0;  // 0 = automatic
   uint32_t threads = 0;      // 0 = automatic
-  uint32_t vec = 4;
+  uint32_t vec = 0;          // 0 = automatic
   uint32_t ctas_per_sm = 0;
   uint32_t donate = 0;
   uint32_t mode = 2;  // DFS traversal: 0 node, 1 frame, 2 automatic (frames for rows of at most 2,048 words)

@@ -39,7 +39,8 @@ const Shape kShapes[] = {
     {128, 2, 0, 0, 0}, {128, 4, 0, 0, 0}, {256, 2, 0, 0, 0}, {256, 4, 0, 0, 0}, {256, 8, 0, 0, 0},
     {512, 4, 0, 0, 0}, {512, 8, 0, 0, 0}, {256, 4, 0, 1, 0}, {512, 4, 0, 1, 0},
     {512, 2, 0, 0, 0}, {128, 2, 0, 0, 1}, {128, 4, 0, 0, 1}, {256, 2, 0, 0, 1}, {256, 4, 0, 0, 1},
-    {256, 8, 0, 0, 1}, {512, 4, 0, 0, 1}, {512, 8, 0, 0, 1},
+    {256, 8, 0, 0, 1}, {512, 4, 0, 0, 1}, {512, 8, 0, 0, 1}, {128, 4, 0, 0, 3}, {128, 8, 0, 0, 3},
+    {256, 4, 0, 0, 3}, {256, 8, 0, 0, 3},
 };
 
 struct TuneKey {
