@@ -193,7 +193,7 @@ struct Ctl {
   uint32_t kind;      // 0 exit, 1 static entry, 2 donated class from the ring
   uint32_t a, b;      // static entry (row index, m)
   uint32_t action;    // 1 expand child, 2 donate child, 3 frame exhausted, 4 class done
-  uint32_t s_row, s_id;
+  uint32_t s_row, s_id, s_supp;
   uint32_t nc;        // candidates of the child
   uint32_t cand_off;  // their offset (entries) in the frame's list
   uint32_t fd;        // frame the donated child comes from
@@ -362,7 +362,8 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
                                                  const uint32_t* xid, const uint32_t* pre, bool pre_global,
                                                  const uint32_t* cand, uint32_t mode, uint32_t nc, uint32_t* out_list,
                                                  uint32_t out_cap, uint32_t xlen, const uint16_t* nzl = nullptr,
-                                                 uint32_t nnz = 0, const uint4* vals = nullptr) {
+                                                 uint32_t nnz = 0, const uint4* vals = nullptr,
+                                                 uint32_t* out_supp = nullptr) {
   const DfsLaunch& p = A.p;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
@@ -409,6 +410,7 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
         if (o < out_cap) {
           out_list[2 * o] = row;
           out_list[2 * o + 1] = v;
+          if (out_supp) out_supp[o] = ck;
         } else {
           atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
         }
@@ -942,16 +944,46 @@ __device__ __forceinline__ void list_push(bool nz, uint32_t w, const uint4& v, u
   }
 }
 
-// shared list <- the nonzero words of a dense prefix in global memory (written by this CTA)
-__device__ __forceinline__ uint32_t list_from_dense(const uint4* src, uint32_t stride4, uint16_t* sidx, uint4* sval,
-                                                    uint32_t* count) {
+// as list_push, but entries past `cap` are only counted (the caller then falls back to a dense prefix)
+__device__ __forceinline__ void list_push_capped(bool nz, uint32_t w, const uint4& v, uint16_t* sidx, uint4* sval,
+                                                 uint32_t* count, uint32_t cap) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t m = __ballot_sync(0xffffffffu, nz);
+  uint32_t base = 0;
+  if (lane == 0 && m) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (nz) {
+    const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < cap) {
+      sidx[pos] = (uint16_t)w;
+      sval[pos] = v;
+    }
+  }
+}
+
+// shared list <- the nonzero words of a[w] & row[w] (row read only under nonzero a); returns how many
+// there are, which may exceed cap (then the list is incomplete)
+template <bool A_RO>
+__device__ __forceinline__ uint32_t and_rows_to_list(const uint4* a4, const uint4* __restrict__ r4, uint32_t stride4,
+                                                     uint16_t* sidx, uint4* sval, uint32_t* count, uint32_t cap) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) *count = 0;
   __syncthreads();
-  for (uint32_t w0 = warp * 32; w0 < stride4; w0 += nw * 32) {
-    const uint32_t w = w0 + lane;
-    const uint4 v = w < stride4 ? __ldcg(src + w) : make_uint4(0u, 0u, 0u, 0u);
-    list_push(any4(v), w, v, sidx, sval, count);
+  constexpr uint32_t U = 4;
+  for (uint32_t w0 = warp * 32 * U; w0 < stride4; w0 += nw * 32 * U) {
+    uint4 a[U], b[U];
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t w = w0 + u * 32 + lane;
+      a[u] = w < stride4 ? (A_RO ? __ldg(a4 + w) : a4[w]) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) b[u] = any4(a[u]) ? __ldg(r4 + w0 + u * 32 + lane) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint4 v = make_uint4(a[u].x & b[u].x, a[u].y & b[u].y, a[u].z & b[u].z, a[u].w & b[u].w);
+      list_push_capped(any4(v), w0 + u * 32 + lane, v, sidx, sval, count, cap);
+    }
   }
   __syncthreads();
   return *count;
@@ -1011,6 +1043,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
 #define slot_pre(d) (arena + (size_t)(d) * per_depth)
 #define slot_hdr(d) (arena + (size_t)(d) * per_depth + p.stride)
 #define slot_list(d) (arena + (size_t)(d) * per_depth + p.stride + lw)
+#define slot_supp(d) (arena + (size_t)(d) * per_depth + p.stride + lw + ((2ull * p.n1 + 3) & ~3ull))
   const uint32_t list_cap = p.n1;
   const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
   unsigned long long st_inter = 0, st_frames = 0;
@@ -1058,10 +1091,15 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
     const uint32_t nc = p.scnt[i] - m - 1;
     if (threadIdx.x == 0) { xrow[0] = r1; xidp[0] = p.rank_item[r1]; C.xlen0 = 2; }
     if (threadIdx.x == 1) { xrow[1] = r2; xidp[1] = p.rank_item[r2]; }
-    uint32_t nz = and_rows_count<true>(reinterpret_cast<uint4*>(slot_pre(0)), bits4 + (size_t)r1 * A.stride4,
-                                       bits4 + (size_t)r2 * A.stride4, A.stride4, wtot);
-    bool listed = nz <= A.cap;
-    if (listed) nz = list_from_dense(reinterpret_cast<const uint4*>(slot_pre(0)), A.stride4, sidx, sval, &list_count);
+    // a prefix of support s has at most s nonzero words: s <= cap lists it in one pass; up to 4 cap
+    // the list is tried first; above, or when the try overflows, the prefix is built dense
+    const uint4* ra4 = bits4 + (size_t)r1 * A.stride4;
+    const uint4* rb4 = bits4 + (size_t)r2 * A.stride4;
+    const uint32_t supp0 = __ldg(p.C2 + (size_t)i * p.n1 + si);
+    uint32_t nz = 0xffffffffu;
+    if (supp0 <= 4u * A.cap) nz = and_rows_to_list<true>(ra4, rb4, A.stride4, sidx, sval, &list_count, A.cap);
+    const bool listed = nz <= A.cap;
+    if (!listed) nz = and_rows_count<true>(reinterpret_cast<uint4*>(slot_pre(0)), ra4, rb4, A.stride4, wtot);
     sort_path_ids(xidp, 2, xid);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1070,7 +1108,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
     }
     const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, slot_pre(0), !listed, p.sitems + base + m + 1,
                                           CAND_FROW, nc, slot_list(0), list_cap, 2, listed ? sidx : nullptr, nz,
-                                          listed ? sval : nullptr);
+                                          listed ? sval : nullptr, slot_supp(0));
     if (ns >= 2) save(0, listed, nz);
     if (threadIdx.x == 0) {
       atomicAdd(&p.ctrl->n_nodes, 1ull);
@@ -1100,6 +1138,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
           C.action = 1;
           C.s_row = slot_list(d)[2 * k];
           C.s_id = slot_list(d)[2 * k + 1];
+          C.s_supp = slot_supp(d)[k];
           C.cand_off = k + 1;
           C.nc = f_n[d] - k - 1;
           f_cur[d] = k + 1;
@@ -1123,12 +1162,15 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
         nz2 = list_from_list(reinterpret_cast<const uint16_t*>(slot_hdr(d) + 4),
                              reinterpret_cast<const uint4*>(slot_pre(d)), hdr, r4, sidx, sval, &list_count);
         listed2 = true;
-      } else {
-        nz2 = and_rows_count<false>(reinterpret_cast<uint4*>(slot_pre(d + 1)),
-                                    reinterpret_cast<const uint4*>(slot_pre(d)), r4, A.stride4, wtot);
+      } else {  // dense parent: as for the root, by the child's support
+        nz2 = 0xffffffffu;
+        if (C.s_supp <= 4u * A.cap)
+          nz2 = and_rows_to_list<false>(reinterpret_cast<const uint4*>(slot_pre(d)), r4, A.stride4, sidx, sval,
+                                        &list_count, A.cap);
         listed2 = nz2 <= A.cap;
-        if (listed2)
-          nz2 = list_from_dense(reinterpret_cast<const uint4*>(slot_pre(d + 1)), A.stride4, sidx, sval, &list_count);
+        if (!listed2)
+          nz2 = and_rows_count<false>(reinterpret_cast<uint4*>(slot_pre(d + 1)),
+                                      reinterpret_cast<const uint4*>(slot_pre(d)), r4, A.stride4, wtot);
       }
       sort_path_ids(xidp, xl, xid);
       __syncthreads();
@@ -1138,7 +1180,8 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
       }
       const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, slot_pre(d + 1), !listed2,
                                             slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl,
-                                            listed2 ? sidx : nullptr, nz2, listed2 ? sval : nullptr);
+                                            listed2 ? sidx : nullptr, nz2, listed2 ? sval : nullptr,
+                                            slot_supp(d + 1));
       if (n2 >= 2) save(d + 1, listed2, nz2);
       if (threadIdx.x == 0) {
         atomicAdd(&p.ctrl->n_nodes, 1ull);
@@ -1159,6 +1202,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
   }
 #undef slot_pre
 #undef slot_hdr
+#undef slot_supp
 #undef slot_list
 }
 

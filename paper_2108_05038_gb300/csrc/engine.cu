@@ -185,6 +185,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.cap_sets = ep.count_only ? 0ull : ep.cap_sets;
     dl.cap_items = ep.count_only ? 0ull : ep.cap_items;
     dl.class_sets = ep.d_class_sets;
+    dl.C2 = ep.d_C2;
     dl.ctrl = ep.d_ctrl;
     dl.spin_limit = ep.spin_limit;
     dl.donate = ep.donate;

@@ -377,6 +377,7 @@ struct DfsLaunch {
   uint64_t max_sets;               // 0 = no limit; else stop once more sets than this are found
   unsigned long long* cta_time;    // optional: [start, end] global time (ns) of every CTA
   unsigned long long* class_sets;  // optional: frequent itemsets per top class
+  const uint32_t* C2;              // level-2 pair counts (n1 x n1): supports of the root prefixes
 };
 // grid: number of persistent CTAs; threads: CTA size; vec: 16-byte loads per lane per piece
 // mode 0: node at a time (optionally with donation); mode 1: frame passes (all children of a frame together)
@@ -407,10 +408,10 @@ __host__ __device__ inline uint64_t frames_depth_words(uint32_t stride, uint32_t
 }
 // node-mode arena words per depth: the prefix (stride words: dense, or the values of its nonzero
 // 16-byte words), its index list (4-word header + stride/8 words of 16-bit indices), one (row, id)
-// survivor list; every region a multiple of four words
+// survivor list, the survivors' supports; every region a multiple of four words
 __host__ __device__ inline uint64_t dfs_list_words(uint32_t stride) { return (uint64_t)stride / 8 + 4; }
 __host__ __device__ inline uint64_t dfs_arena_depth_words(uint32_t stride, uint32_t n1) {
-  return (uint64_t)stride + dfs_list_words(stride) + ((2ull * n1 + 3) & ~3ull);
+  return (uint64_t)stride + dfs_list_words(stride) + ((2ull * n1 + 3) & ~3ull) + ((uint64_t)n1 + 3 & ~3ull);
 }
 
 }  // namespace fim
