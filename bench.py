@@ -266,8 +266,11 @@ def run_ours(args):
                         "traffic": DFS_KERNEL_TRAFFIC.get(args.workload),
                         "peak_source": "measured copy rate (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
                         else "fallback 6.8 TB/s",
-                        "note": "algorithmic bytes count every candidate row in full; the kernel reads row words "
-                                "only under nonzero prefix words, so traffic is far below them"}
+                        "note": ("algorithmic bytes count every candidate row in full; the kernel reads row words "
+                                 "only under nonzero prefix words, so traffic is far below them"
+                                 if stats["n_frequent_items"] * ((D + 31) // 32) * 4 > 129e6 else
+                                 "the rows fit in L2 (129 MB): the DFS is bound by the latency of its dependent "
+                                 "per-node steps, not by HBM; the fraction is of the HBM copy rate")}
         else:
             roofline = {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                         "peak": round(alu_peak_gword, 1), "unit": "Gword/s",
