@@ -205,6 +205,28 @@ def test_sparse_mode_mixes_listed_and_dense_prefixes():
         assert_same(gpu_mine(off, items, 30, ms, dfs_mode=mode).as_dict(), want)
 
 
+def test_pair_lists_for_sparse_leading_rows():
+    """150,000 transactions, 150 rare items co-occurring in fixed pairs (supports ~200, below a quarter
+    of the 1,176 16-byte words of a row: their pairs are counted from nonzero-word lists) and 50 common
+    ones (tiles); the counts, and so the itemsets, equal the oracle's."""
+    rng = np.random.default_rng(29)
+    D = 150_000
+    common = rng.random((D, 50)) < rng.uniform(0.02, 0.1, 50)
+    pat = np.where(rng.random(D) < 0.1, rng.integers(0, 75, D), -1)
+    txs = []
+    for t in range(D):
+        tx = list(150 + np.nonzero(common[t])[0])
+        if pat[t] >= 0:
+            tx += [2 * int(pat[t]), 2 * int(pat[t]) + 1]
+        txs.append(tx)
+    off, items = csr(txs)
+    ms = 50
+    want = odict(oracle.eclat(off, items, 200, ms))
+    assert any(k == (0, 1) for k in want)  # rare pairs are frequent
+    for mode in (2, 0):
+        assert_same(gpu_mine(off, items, 200, ms, dfs_mode=mode).as_dict(), want)
+
+
 def test_work_counters_match_output_and_modes():
     """Intersections, class nodes and materialised prefixes reported by both DFS modes equal the counts
     derived from the oracle's output alone (bench.bitmap_work)."""
