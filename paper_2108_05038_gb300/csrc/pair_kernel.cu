@@ -294,9 +294,14 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
     static cudaError_t lerr = cudaSuccess;
     std::call_once(lonce, [] {
       int dev = 0, optin = 0;
+      cudaFuncAttributes fa{};
       lerr = cudaGetDevice(&dev);
       if (lerr == cudaSuccess) lerr = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (lerr == cudaSuccess) lerr = cudaFuncSetAttribute(k_pair_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (lerr == cudaSuccess) lerr = cudaFuncGetAttributes(&fa, k_pair_lists);
+      // (the static shared memory counts against the same per-block limit)
+      if (lerr == cudaSuccess)
+        lerr = cudaFuncSetAttribute(k_pair_lists, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes);
     });
     if (lerr != cudaSuccess) return lerr;
     const size_t lsmem = (size_t)p.sparse_cap * 16 + ((size_t)p.sparse_cap * 2 + 15) / 16 * 16;
