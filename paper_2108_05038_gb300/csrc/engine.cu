@@ -64,7 +64,6 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   if (!ep->d_order) FIM_TRY(upload(WS_ROWORDER, in.row_order, &ep->d_order));
 
   ep->npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
-  if (in.row_supp.size() == n1) pair_sparse_split(in.row_supp.data(), n1, in.stride, &ep->pair_nsparse, &ep->pair_cap);
   FIM_TRY(ws_get(ws, WS_C2, (size_t)n1 * n1, &ep->d_C2));
   FIM_TRY(ws_get(ws, WS_SCNT, n1, &ep->d_scnt));
   FIM_TRY(ws_get(ws, WS_SOFF, 2ull * (n1 + 1), &ep->d_soff));
@@ -150,7 +149,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   if (ep.ev[0]) cudaEventRecord(ep.ev[0], st);
   if (!ep.skip_pairs) {
     uint32_t ksplit = 0;
-    PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0, ep.pair_nsparse, ep.pair_cap};
+    PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
     ce = launch_pair_counts(pl, ep.num_sms, st, &ksplit);
     if (ce != cudaSuccess) return ce;
   }

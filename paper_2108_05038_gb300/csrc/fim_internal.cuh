@@ -269,7 +269,6 @@ struct EnginePlan {
   std::vector<unsigned long long>* class_out = nullptr;  // read back with the control block
   uint64_t max_sets = 0;
   bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
-  uint32_t pair_nsparse = 0, pair_cap = 0;  // leading rows counted from their nonzero-word lists
   float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
   unsigned long long* d_cta_time = nullptr;  // per-CTA [start, end] of the DFS (with timing only)
   // buffers
@@ -325,12 +324,7 @@ struct PairLaunch {
   uint32_t n1;
   uint32_t* C2;  // n1 * n1
   uint32_t ksplit;
-  uint32_t n_sparse;    // leading rows (a multiple of 64) counted from their nonzero-word lists; 0 = none
-  uint32_t sparse_cap;  // nonzero 16-byte words such a row has at most (its support bounds them)
 };
-// leading rows of an ascending-support row list whose pairs the list kernel counts (0 = none), and
-// the list capacity; rows whose support is at most a quarter of their 16-byte words qualify
-void pair_sparse_split(const uint32_t* row_supp, uint32_t n1, uint32_t stride, uint32_t* n_sparse, uint32_t* cap);
 cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used);
 
 struct LevelLaunch {

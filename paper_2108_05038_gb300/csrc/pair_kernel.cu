@@ -70,13 +70,13 @@ __device__ __forceinline__ void acc_and_popc8(uint32_t& acc, const uint4& a0, co
 __global__ void __launch_bounds__(kThreads, 3)
 k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows, uint32_t n1,
               uint32_t nb, uint32_t chunks_per_split, uint32_t nchunks, uint32_t* __restrict__ C2, uint32_t ksplit,
-              uint32_t n_items, uint32_t one, uint32_t tb0) {
+              uint32_t n_items, uint32_t one) {
   extern __shared__ __align__(16) uint32_t sm[];
   const uint32_t tid = threadIdx.x, ty = tid / kTX, tx = tid % kTX;
   const uint32_t two = one + one, four = two + two;
   // persistent loop over work items (tile, word range); consecutive items share a tile
   for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-    uint32_t t = item / ksplit, bi = tb0;  // tiles of row blocks tb0.. only (earlier rows: k_pair_lists)
+    uint32_t t = item / ksplit, bi = 0;
     const uint32_t split = item - t * ksplit;
     while (t >= nb - bi) { t -= nb - bi; ++bi; }
     const uint32_t bj = bi + t;
@@ -165,84 +165,7 @@ k_pair_counts(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t
   }
 }
 
-// Pairs (i, j > i) of the leading sparse rows, counted from the nonzero 16-byte words of row i: a
-// row of support s has at most s of them, so a pair reads them and the words of row j at the same
-// indices instead of two whole rows (the AND is zero elsewhere).  One CTA per row i (rows in
-// ascending support: the first rows have the most partners), one warp per partner j; every pair is
-// counted by one warp, so C2 is written without atomics.
-__global__ void __launch_bounds__(256) k_pair_lists(const uint32_t* __restrict__ bits, uint32_t stride,
-                                                    const uint32_t* __restrict__ frows, uint32_t n1, uint32_t n_sparse,
-                                                    uint32_t cap, uint32_t* __restrict__ C2) {
-  extern __shared__ __align__(16) uint4 lsm[];
-  uint4* sval = lsm;
-  uint16_t* sidx = reinterpret_cast<uint16_t*>(lsm + cap);
-  __shared__ uint32_t count;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t stride4 = stride / 4;
-  const uint4* bits4 = reinterpret_cast<const uint4*>(bits);
-  for (uint32_t i = blockIdx.x; i < n_sparse; i += gridDim.x) {
-    const uint4* ri = bits4 + (size_t)frows[i] * stride4;
-    if (threadIdx.x == 0) count = 0;
-    __syncthreads();
-    for (uint32_t w0 = warp * 32; w0 < stride4; w0 += nw * 32) {
-      const uint32_t w = w0 + lane;
-      const uint4 v = w < stride4 ? __ldg(ri + w) : make_uint4(0u, 0u, 0u, 0u);
-      const bool nz = (v.x | v.y | v.z | v.w) != 0u;
-      const uint32_t m = __ballot_sync(0xffffffffu, nz);
-      uint32_t base = 0;
-      if (lane == 0 && m) base = atomicAdd(&count, (uint32_t)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (nz) {
-        const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
-        if (pos < cap) {  // (the row's support bounds its nonzero words by cap)
-          sidx[pos] = (uint16_t)w;
-          sval[pos] = v;
-        }
-      }
-    }
-    __syncthreads();
-    const uint32_t n = min(count, cap);
-    for (uint32_t j = i + 1 + warp; j < n1; j += nw) {
-      const uint4* rj = bits4 + (size_t)frows[j] * stride4;
-      uint32_t acc = 0;
-      constexpr uint32_t U = 8;
-      for (uint32_t e0 = lane; e0 < n; e0 += 32 * U) {
-        uint32_t w[U];
-#pragma unroll
-        for (uint32_t u = 0; u < U; ++u) w[u] = e0 + u * 32 < n ? (uint32_t)sidx[e0 + u * 32] : 0xffffffffu;
-        uint4 b[U];  // the U gathers of row j go out together
-#pragma unroll
-        for (uint32_t u = 0; u < U; ++u) b[u] = w[u] != 0xffffffffu ? __ldg(rj + w[u]) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-        for (uint32_t u = 0; u < U; ++u) {
-          const uint4 a = w[u] != 0xffffffffu ? sval[e0 + u * 32] : make_uint4(0u, 0u, 0u, 0u);
-          acc += __popc(a.x & b[u].x) + __popc(a.y & b[u].y) + __popc(a.z & b[u].z) + __popc(a.w & b[u].w);
-        }
-      }
-      acc = __reduce_add_sync(0xffffffffu, acc);
-      if (lane == 0) C2[(size_t)i * n1 + j] = acc;
-    }
-    __syncthreads();  // the next row reuses the list
-  }
-}
-
 }  // namespace
-
-void pair_sparse_split(const uint32_t* row_supp, uint32_t n1, uint32_t stride, uint32_t* n_sparse, uint32_t* cap) {
-  *n_sparse = 0;
-  *cap = 0;
-  const uint32_t stride4 = stride / 4;
-  if (stride4 < 1024 || stride4 > 65535 || n1 < 128) return;  // narrow rows: the tiles are faster throughout
-  const uint32_t limit = stride4 / 4;
-  uint32_t k = 0;
-  while (k < n1 && row_supp[k] <= limit) ++k;
-  k &= ~63u;  // whole 64-row tile blocks
-  if (k < 64) return;
-  uint32_t mx = 32;
-  for (uint32_t r = 0; r < k; ++r) mx = std::max(mx, row_supp[r]);
-  *n_sparse = k;
-  *cap = mx;
-}
 
 cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used) {
   if (p.n1 < 2) { *ksplit_used = 0; return cudaSuccess; }
@@ -257,8 +180,7 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
   });
   if (attr_err != cudaSuccess) return attr_err;
   const uint32_t nb = (p.n1 + kTile - 1) / kTile;
-  const uint32_t tb0 = p.n_sparse / kTile;  // row blocks before tb0 belong to the list kernel
-  const uint32_t tiles = (nb - tb0) * (nb - tb0 + 1) / 2;
+  const uint32_t tiles = nb * (nb + 1) / 2;
   const uint32_t nchunks = p.stride / kChunk;  // stride is a multiple of 32 words
   const uint32_t slots = (uint32_t)num_sms * (uint32_t)occ;  // resident CTAs
   uint32_t ksplit = p.ksplit;
@@ -289,36 +211,10 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
     cudaError_t e = cudaMemsetAsync(p.C2, 0, (size_t)p.n1 * p.n1 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
   }
-  if (p.n_sparse) {
-    static std::once_flag lonce;
-    static cudaError_t lerr = cudaSuccess;
-    std::call_once(lonce, [] {
-      int dev = 0, optin = 0;
-      cudaFuncAttributes fa{};
-      lerr = cudaGetDevice(&dev);
-      if (lerr == cudaSuccess) lerr = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (lerr == cudaSuccess) lerr = cudaFuncGetAttributes(&fa, k_pair_lists);
-      // (the static shared memory counts against the same per-block limit)
-      if (lerr == cudaSuccess)
-        lerr = cudaFuncSetAttribute(k_pair_lists, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin - (int)fa.sharedSizeBytes);
-    });
-    if (lerr != cudaSuccess) return lerr;
-    const size_t lsmem = (size_t)p.sparse_cap * 16 + ((size_t)p.sparse_cap * 2 + 15) / 16 * 16;
-    int locc = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&locc, k_pair_lists, 256, lsmem);
-    if (e != cudaSuccess) return e;
-    const uint32_t lgrid = std::min<uint32_t>(p.n_sparse, (uint32_t)num_sms * (uint32_t)std::max(1, locc));
-    k_pair_lists<<<lgrid, 256, lsmem, st>>>(p.bits, p.stride, p.frows, p.n1, p.n_sparse, p.sparse_cap, p.C2);
-    note_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (tiles == 0) return cudaSuccess;
   const uint32_t n_items = tiles * ksplit;
   const uint32_t grid = n_items < slots ? n_items : slots;
   k_pair_counts<<<grid, kThreads, kSmemBytes, st>>>(p.bits, p.stride, p.frows, p.n1, nb, cps, nchunks, p.C2, ksplit,
-                                                     n_items, 1u, tb0);
+                                                     n_items, 1u);
   note_launch();
   return cudaGetLastError();
 }
