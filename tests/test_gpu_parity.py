@@ -101,6 +101,30 @@ def test_identical_transactions_closed_form(k, mode, depth):
     assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
 
 
+@pytest.mark.parametrize("mode", [0, 1, 3])
+def test_single_and_empty_transactions(mode):
+    """One transaction of 5 items: every non-empty subset (31) with support 1; only empty transactions:
+    nothing is frequent (no item has support); one item in every transaction: only that singleton."""
+    off, items = csr([[4, 0, 2, 3, 1]])
+    got = gpu_mine(off, items, 5, 1, dfs_mode=mode).as_dict()
+    assert len(got) == 31 and set(got.values()) == {1}
+    off, items = csr([[] for _ in range(100)])
+    assert gpu_mine(off, items, 7, 1, dfs_mode=mode).n_sets == 0
+    off, items = csr([[3]] * 40)
+    assert gpu_mine(off, items, 8, 40, dfs_mode=mode).as_dict() == {(3,): 40}
+
+
+def test_many_items_global_histogram():
+    """N = 20,000 items (above the 12,288 counted in shared memory per CTA): counts from global atomics."""
+    rng = np.random.default_rng(31)
+    D, N = 3000, 20000
+    hot = rng.choice(N, 30, replace=False)
+    txs = [list(set(rng.choice(N, 5).tolist()) | set(hot[rng.random(30) < 0.3].tolist())) for _ in range(D)]
+    off, items = csr(txs)
+    want = odict(oracle.eclat(off, items, N, 40))
+    assert_same(gpu_mine(off, items, N, 40).as_dict(), want)
+
+
 def test_degenerate_cases():
     off, items = csr([[0], [1], [2], [0, 1]])
     assert gpu_mine(off, items, 3, 5).n_sets == 0             # minsup > D: empty
