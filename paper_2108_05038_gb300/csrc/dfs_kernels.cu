@@ -1096,12 +1096,12 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
     const uint4* ra4 = bits4 + (size_t)r1 * A.stride4;
     const uint4* rb4 = bits4 + (size_t)r2 * A.stride4;
     const uint32_t supp0 = __ldg(p.C2 + (size_t)i * p.n1 + si);
+    __syncthreads();  // the path (threads 0 and 1) is written
+    sort_path_ids(xidp, 2, xid);  // made visible by the barriers of the prefix build below
     uint32_t nz = 0xffffffffu;
     if (supp0 <= 4u * A.cap) nz = and_rows_to_list<true>(ra4, rb4, A.stride4, sidx, sval, &list_count, A.cap);
     const bool listed = nz <= A.cap;
     if (!listed) nz = and_rows_count<true>(reinterpret_cast<uint4*>(slot_pre(0)), ra4, rb4, A.stride4, wtot);
-    sort_path_ids(xidp, 2, xid);
-    __syncthreads();
     if (threadIdx.x == 0) {
       st_inter += nc;
       if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)nc);
@@ -1110,52 +1110,59 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
                                           CAND_FROW, nc, slot_list(0), list_cap, 2, listed ? sidx : nullptr, nz,
                                           listed ? sval : nullptr, slot_supp(0));
     if (ns >= 2) save(0, listed, nz);
+    // the next step of the DFS (thread 0): expand the next child of the top frame, pop the frame, or
+    // finish the class; every thread has read the previous step when thread 0 runs this
+    uint32_t poll = 0;
+    auto decide = [&]() {
+      if (C.depth >= 0 && (++poll & 7) == 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
+      const int32_t d = C.depth;
+      if (d < 0) {
+        C.action = 4;
+      } else if (f_cur[d] + 1 >= f_n[d]) {
+        C.depth = d - 1;
+        C.action = 3;
+      } else if ((uint32_t)(d + 1) > p.maxd) {
+        atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+        C.depth = -1;
+        C.action = 3;
+      } else {
+        const uint32_t k = f_cur[d];
+        C.action = 1;
+        C.s_row = slot_list(d)[2 * k];
+        C.s_id = slot_list(d)[2 * k + 1];
+        C.s_supp = slot_supp(d)[k];
+        C.cand_off = k + 1;
+        C.nc = f_n[d] - k - 1;
+        f_cur[d] = k + 1;
+        xrow[C.xlen0 + d] = C.s_row;
+        xidp[C.xlen0 + d] = C.s_id;
+      }
+    };
     if (threadIdx.x == 0) {
       atomicAdd(&p.ctrl->n_nodes, 1ull);
       atomicAdd(&p.ctrl->progress, 1u);
       if (ns >= 2) { f_n[0] = ns; f_cur[0] = 0; C.depth = 0; ++st_frames; }
       else C.depth = -1;
+      decide();  // (process_node ended with a barrier: nobody reads the root's step any more)
     }
 
     // ---------------- depth-first expansion ----------------
-    uint32_t poll = 0;
     for (;;) {
-      __syncthreads();  // every thread has read the previous decision
-      if (threadIdx.x == 0) {
-        if (C.depth >= 0 && (++poll & 7) == 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
-        const int32_t d = C.depth;
-        if (d < 0) {
-          C.action = 4;
-        } else if (f_cur[d] + 1 >= f_n[d]) {
-          C.depth = d - 1;
-          C.action = 3;
-        } else if ((uint32_t)(d + 1) > p.maxd) {
-          atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
-          C.depth = -1;
-          C.action = 3;
-        } else {
-          const uint32_t k = f_cur[d];
-          C.action = 1;
-          C.s_row = slot_list(d)[2 * k];
-          C.s_id = slot_list(d)[2 * k + 1];
-          C.s_supp = slot_supp(d)[k];
-          C.cand_off = k + 1;
-          C.nc = f_n[d] - k - 1;
-          f_cur[d] = k + 1;
-          xrow[C.xlen0 + d] = C.s_row;
-          xidp[C.xlen0 + d] = C.s_id;
-        }
-      }
-      __syncthreads();
+      __syncthreads();  // the step is visible
       const uint32_t action = C.action;
       if (action == 4) break;
-      if (action == 3) continue;
+      if (action == 3) {
+        __syncthreads();  // every thread has read the pop before thread 0 decides again
+        if (threadIdx.x == 0) decide();
+        continue;
+      }
       // expand the child [X_d u {s} | rest of frame d]
       const int32_t d = C.depth;
       const uint32_t ncc = C.nc, coff = C.cand_off;
       const uint32_t xl = C.xlen0 + d + 1;  // prefix length of the child
       const uint4* r4 = bits4 + (size_t)C.s_row * A.stride4;
       const uint32_t hdr = *(volatile const uint32_t*)slot_hdr(d);
+      sort_path_ids(xidp, xl, xid);  // made visible by the barriers of the prefix build below
       uint32_t nz2;
       bool listed2;
       if (hdr != kDensePrefix) {  // listed parent: the child is listed too (no more nonzero words)
@@ -1172,8 +1179,6 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
           nz2 = and_rows_count<false>(reinterpret_cast<uint4*>(slot_pre(d + 1)),
                                       reinterpret_cast<const uint4*>(slot_pre(d)), r4, A.stride4, wtot);
       }
-      sort_path_ids(xidp, xl, xid);
-      __syncthreads();
       if (threadIdx.x == 0) {
         st_inter += ncc;
         if (p.class_work) atomicAdd(&p.class_work[C.cls], (unsigned long long)ncc);
@@ -1187,6 +1192,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
         atomicAdd(&p.ctrl->n_nodes, 1ull);
         atomicAdd(&p.ctrl->progress, 1u);
         if (n2 >= 2) { f_n[d + 1] = n2; f_cur[d + 1] = 0; C.depth = d + 1; ++st_frames; }
+        decide();  // (the step's fields were read before process_node's barriers)
       }
     }
     // class finished
