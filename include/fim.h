@@ -331,6 +331,29 @@ void fim_server_free(fim_server* srv);
 fim_status fim_mine_pairs_noalloc(const fim_db* db, uint32_t minsup_abs, uint32_t* d_pairs, uint32_t* d_supports,
                                   uint64_t capacity, uint64_t* n_pairs);
 
+/*
+ * Supports of the one-item extensions of an itemset P: supports_out[k] =
+ * supp(P u {cand_items[k]}) = |t(P) n t({cand_items[k]})|, the counting step of
+ * a class node of Eclat-DFS-Computation (App. B.3.2; support of a union as the
+ * size of the intersection of its generating subsets' tidlists, App. B.3.1),
+ * on db's bitmaps.  t(P) is the AND of the rows of P's items (a one-item P
+ * uses its row in place); each candidate row is then read once, only under
+ * the nonzero 16-byte words of t(P).  With a dense t(P) the call streams
+ * n_cand rows from HBM: it is the bandwidth-bound form of the DFS's count.
+ *
+ * prefix_items (n_prefix >= 1 original ids, any order, repeats allowed) and
+ * cand_items (n_cand original ids, any order; a candidate inside P gives
+ * supp(P)) are HOST arrays read during the call; supports_out is a HOST array
+ * of n_cand counts written by it.  Every id must be < N and must have a row
+ * (not dropped by the build's prefilter).  n_cand = 0 returns FIM_OK without
+ * device work.  The call synchronises db's stream; scratch comes from db's
+ * workspace.
+ * Errors: FIM_ERR_INVALID (NULL db, empty or NULL prefix, NULL candidates or
+ * output with n_cand > 0, an id >= N or without a row), FIM_ERR_CUDA.
+ */
+fim_status fim_extension_supports(fim_db* db, const uint32_t* prefix_items, uint32_t n_prefix,
+                                  const uint32_t* cand_items, uint32_t n_cand, uint32_t* supports_out);
+
 void fim_result_free(fim_result* res);
 void fim_db_free(fim_db* db);
 const char* fim_status_str(fim_status s);

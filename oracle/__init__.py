@@ -188,3 +188,25 @@ def class_costs(offsets, items, N: int, prefilter_minsup: int, sample_rate: floa
 def splitmix64_at(seed: int, k: int) -> int:
     """k-th output (0-based) of SplitMix64 started at state ``seed``."""
     return _load().oracle_splitmix64_at(seed, k)
+
+
+def extension_supports(offsets, items, N: int, prefix, candidates):
+    """supp(P u {c}) for every candidate c (Def. "Itemset cover and support", Ch. 2: the number of
+    transactions that contain every item of the set), counted by one scan of the transactions: a
+    transaction covers P u {c} iff it holds all distinct items of P and also c.  Repeated items in a
+    transaction or in P count once; a candidate inside P gives supp(P).  Returns u64[len(candidates)]."""
+    offsets, items = _csr(offsets, items)
+    D = offsets.size - 1
+    prefix = np.unique(np.asarray(prefix, dtype=np.int64))
+    cand = np.asarray(candidates, dtype=np.int64)
+    if prefix.size == 0 or (prefix.size and (prefix.min() < 0 or prefix.max() >= N)) or \
+            (cand.size and (cand.min() < 0 or cand.max() >= N)):
+        raise ValueError("prefix must be non-empty and every id < N")
+    tx = np.repeat(np.arange(D, dtype=np.int64), np.diff(offsets.astype(np.int64)))
+    body = items[int(offsets[0]): int(offsets[-1])].astype(np.int64)
+    pairs = np.unique(tx * N + body)  # distinct (transaction, item)
+    ptx, pit = pairs // N, pairs % N
+    in_p = np.isin(pit, prefix)
+    covers_p = np.bincount(ptx[in_p], minlength=D) == prefix.size
+    per_item = np.bincount(pit[covers_p[ptx]], minlength=N)
+    return per_item[cand].astype(np.uint64)

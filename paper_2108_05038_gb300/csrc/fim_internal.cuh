@@ -96,6 +96,9 @@ enum WsSlot {
   WS_TALLY,
   WS_CLASSWORK,
   WS_CTATIME,
+  WS_QUERY_ROWS,    // fim_extension_supports: prefix rows | candidate rows
+  WS_QUERY_OUT,     // fim_extension_supports: one count per candidate
+  WS_QUERY_PREFIX,  // fim_extension_supports: t(P) of a prefix of two or more items
   // the database's own arrays (kept in the workspace so that a freed database's memory serves the next)
   WS_DB_TXOFF,
   WS_DB_TXITEMS,

@@ -27,6 +27,7 @@ EXPORTED = [
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
     "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free", "fim_kernel_launches",
+    "fim_extension_supports",
 ]
 
 
@@ -134,6 +135,8 @@ def load(build_if_stale: bool = True):
         lib.fim_server_free.argtypes = [P]
         lib.fim_mine_pairs_noalloc.restype = i32
         lib.fim_mine_pairs_noalloc.argtypes = [P, u32, P, P, u64, ctypes.POINTER(u64)]
+        lib.fim_extension_supports.restype = i32
+        lib.fim_extension_supports.argtypes = [P, P, u32, P, u32, P]
         lib.fim_result_view.restype = i32
         lib.fim_result_view.argtypes = [P, ctypes.POINTER(u64), PP, PP, PP, ctypes.POINTER(i32)]
         lib.fim_result_free.restype = None
@@ -348,6 +351,16 @@ class Database:
             raise err
         _check(self._lib, status, "fim_mine_pairs_noalloc")
         return n.value
+
+    def extension_supports(self, prefix, candidates) -> np.ndarray:
+        """fim_extension_supports: supp(P u {c}) for every candidate item c of ``candidates``
+        (original ids), P = ``prefix``; returns u32[len(candidates)]."""
+        pre = np.ascontiguousarray(prefix, dtype=np.uint32)
+        cand = np.ascontiguousarray(candidates, dtype=np.uint32)
+        out = np.zeros(len(cand), dtype=np.uint32)
+        _check(self._lib, self._lib.fim_extension_supports(self._h, pre.ctypes.data, len(pre), cand.ctypes.data,
+                                                            len(cand), out.ctypes.data), "fim_extension_supports")
+        return out
 
     def free(self):
         if self._h:

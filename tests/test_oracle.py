@@ -397,3 +397,53 @@ def test_intersection_costs_match_literal_eclat(seed):
         want = _sample_intersection_costs(txs, N, prefilter, rate, rel, seed)
         assert np.allclose(cost, want, rtol=0, atol=1e-15)
         assert list(order) == sorted(range(len(cost)), key=lambda r: (-cost[r], r))
+
+
+# ---------------------------------------------------------------- extension supports
+
+def test_extension_supports_worked_example(golden):
+    """Every printed support of the App. B.3.2 example (frequent and infrequent rows) is reached as
+    supp(P u {c}) for P = the set minus its last item (minus nothing for a singleton: P = {c})."""
+    minsup, txs, rows = golden("eclat_example.txt")
+    off, items = csr(txs)
+    for _f, s, v in rows:
+        prefix = s[:-1] if len(s) > 1 else s
+        got = oracle.extension_supports(off, items, 6, prefix, [s[-1]])
+        assert int(got[0]) == v, (s, v)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_extension_supports_equal_eclat_outputs(seed):
+    """At minsup 1 Eclat outputs every itemset with nonzero support: each extension of an output set
+    by any item is either output with that support or absent with support 0."""
+    rng = np.random.default_rng(seed)
+    N = 12
+    txs = [list(rng.choice(N, size=rng.integers(0, 6), replace=False)) for _ in range(300)]
+    off, items = csr(txs)
+    d = as_dict(oracle.eclat(off, items, N, 1))
+    for s in list(d)[:: 7]:
+        got = oracle.extension_supports(off, items, N, list(s), np.arange(N))
+        for c in range(N):
+            want = d.get(tuple(sorted(set(s) | {c})), 0)
+            assert int(got[c]) == want, (s, c)
+
+
+def test_extension_supports_closed_forms():
+    """An item in every transaction: supp({0, c}) = supp(c); a candidate inside P gives supp(P);
+    disjoint halves give 0; repeats inside a transaction or P count once."""
+    D, N = 500, 9
+    rng = np.random.default_rng(11)
+    txs = [[0] + list(rng.choice(np.arange(1, N), size=rng.integers(0, 4), replace=False)) for _ in range(D)]
+    off, items = csr(txs)
+    hist = np.bincount(items, minlength=N)
+    assert list(oracle.extension_supports(off, items, N, [0], np.arange(N))) == list(hist)
+    assert list(oracle.extension_supports(off, items, N, [0, 0], [0, 0])) == [D, D]
+    lo = [[1, 2]] * 5 + [[3, 4, 4]] * 7 + [[]] * 2  # raw CSR: the repeated 4 stays in
+    off2 = np.cumsum([0] + [len(t) for t in lo]).astype(np.uint32)
+    items2 = np.array([i for t in lo for i in t], dtype=np.uint32)
+    assert list(oracle.extension_supports(off2, items2, 5, [1], [2, 3, 4])) == [5, 0, 0]
+    assert list(oracle.extension_supports(off2, items2, 5, [4, 4], [3, 4, 1])) == [7, 7, 0]
+    with pytest.raises(ValueError):
+        oracle.extension_supports(off2, items2, 5, [], [1])
+    with pytest.raises(ValueError):
+        oracle.extension_supports(off2, items2, 5, [1], [5])
