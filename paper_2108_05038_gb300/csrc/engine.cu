@@ -65,6 +65,17 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
 
   ep->npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
   FIM_TRY(ws_get(ws, WS_C2, (size_t)n1 * n1, &ep->d_C2));
+  // level 2 on the tensor cores when asked, or when its modelled time is lower and the widened rows
+  // (one byte per transaction) take at most 1/16 of the device memory; TMA coordinates are signed
+  // 32-bit, so widened rows of less than 2^31 bytes
+  if (n1 >= 2) {
+    const uint64_t xb = pair_mma_buffer_bytes(n1, in.stride);
+    const bool fits = (uint64_t)in.stride * 32 < (1ull << 31) && xb <= db->total_mem / 16;
+    if (cfg.pair_kernel == 2) ep->pair_mma = (uint64_t)in.stride * 32 < (1ull << 31);
+    else if (cfg.pair_kernel == 0)
+      ep->pair_mma = fits && pair_mma_cost_us(n1, in.stride, db->num_sms) < pair_cores_cost_us(n1, in.stride, db->num_sms);
+    if (ep->pair_mma) FIM_TRY(ws_get(ws, WS_PAIR_X, xb, &ep->d_X));
+  }
   FIM_TRY(ws_get(ws, WS_SCNT, n1, &ep->d_scnt));
   FIM_TRY(ws_get(ws, WS_SOFF, 2ull * (n1 + 1), &ep->d_soff));
   FIM_TRY(ws_get(ws, WS_SITEMS, ep->npairs_max + 1, &ep->d_sitems));
@@ -150,7 +161,8 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   if (!ep.skip_pairs) {
     uint32_t ksplit = 0;
     PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
-    ce = launch_pair_counts(pl, ep.num_sms, st, &ksplit);
+    ce = ep.pair_mma ? launch_pair_mma(pl, ep.d_X, &ep.d_ctrl->err, ep.num_sms, st, &ksplit)
+                     : launch_pair_counts(pl, ep.num_sms, st, &ksplit);
     if (ce != cudaSuccess) return ce;
   }
   if (ep.ev[1]) cudaEventRecord(ep.ev[1], st);
@@ -285,6 +297,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     stats->grid_ctas = n1 >= 3 ? ep->grid : 0;
     stats->threads_per_cta = ep->threads;
     stats->vec_per_lane = ep->vec;
+    stats->pair_kernel = ep->pair_mma ? FIM_PAIR_TENSOR : FIM_PAIR_CORES;
     if (ep->ev[0] && n1 > 0) {
       stats->ms_pair_kernel = ep->ms_pair;  // the one pair-kernel launch of this mine
       cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);  // the last DFS run

@@ -1,0 +1,400 @@
+// K5 on the tensor cores: level-2 supports of all pairs of frequent rows as an
+// exact integer GEMM.
+//
+// supp({a,b}) = |t({a}) n t({b})| (App. B.3.1) is the sum over transactions t of
+// x_a(t) x_b(t) with x in {0,1}, so the n1 x n1 block of pair counts is C = X X^T
+// for the 0/1 matrix X of the frequent rows (the first DFS step of Eclat,
+// App. B.3.2, for all one-item classes at once).  tcgen05 has no 1-bit kind, so
+// each row is widened once to bytes (bit set -> 1.0 in e4m3, else 0) and the
+// product runs as kind::f8f6f4 MMAs with fp32 accumulators in tensor memory.
+// Every product is 0 or 1, so a partial sum is an integer no larger than the
+// bytes it covers; a work item covers at most 2^24 bytes of K, where fp32 holds
+// every integer exactly, and items of one tile are added as u32 atomics.
+//
+// Tiles: 128 rows (i) x 256 rows (j) of X, only those that hold pairs i < j.
+// A CTA (one per SM, persistent) walks (tile, K range) items; per item one
+// thread issues TMA loads of 128-byte K slices (128B swizzle) into a 4-stage
+// ring, one thread issues four 128x256x32 MMAs per slice into a 256-column TMEM
+// accumulator, and the four warps read the accumulator back (tcgen05.ld, one
+// TMEM lane quarter per warp) and write or add the counts of pairs i < j.
+// Every mbarrier wait is bounded by time; on expiry the kernel sets
+// DEV_ERR_TIMEOUT, lets its copies and MMAs in flight finish, frees its TMEM and
+// returns.
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder comes from the driver at run time)
+
+#include <algorithm>
+#include <mutex>
+
+#include "fim_internal.cuh"
+
+namespace fim {
+namespace {
+
+constexpr uint32_t kBM = 128;       // tile rows on the i side (MMA M)
+constexpr uint32_t kBN = 256;       // tile rows on the j side (MMA N)
+constexpr uint32_t kBK = 128;       // K bytes per pipeline stage (one 128-byte swizzle row)
+constexpr uint32_t kMmaK = 32;      // K bytes per kind::f8f6f4 MMA
+constexpr uint32_t kStages = 4;
+constexpr uint32_t kThreads = 128;  // four warps: TMA issue (warp 0), MMA issue (warp 1), all four read back
+constexpr uint32_t kABytes = kBM * kBK;
+constexpr uint32_t kBBytes = kBN * kBK;
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr uint32_t kBarBytes = 8 * (2 * kStages + 1) + 8;  // full[], empty[], acc, TMEM address
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kBarBytes;  // + slack for 1024-byte alignment
+constexpr uint32_t kTmemCols = kBN;                          // fp32 accumulator: 128 lanes x 256 columns
+constexpr uint32_t kMaxStepsPerItem = (1u << 24) / kBK;      // fp32 exact: at most 2^24 bytes of K per item
+constexpr uint64_t kWaitNs = 1000000000ull;                  // bound of every mbarrier wait (1 s)
+// instruction descriptor of kind::f8f6f4: D f32 (bits 4-5 = 1), A and B e4m3 (bits 7-9, 10-12 = 0), both
+// K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | ((kBN >> 3) << 17) | ((kBM >> 4) << 24);
+constexpr uint32_t kOneE4M3 = 0x38u;
+static_assert(kBN % 16 == 0 && kBN <= 256 && kBM == 128, "MMA shape of cta_group::1");
+static_assert(kBK % kMmaK == 0, "whole MMAs per stage");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// waits for the completion of the phase of parity `parity`; false when kWaitNs pass first
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (!mbar_try(bar, parity))
+    if (now_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load of one box into shared memory; completion counted on `bar` in bytes
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle layout: rows of 128
+// bytes, 8-row groups 1024 bytes apart (stride byte offset), start address in 16-byte units, the
+// Blackwell descriptor version 1 in bits 46-47, swizzle mode 2 (128 B) in bits 61-63
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrives on `bar` once every MMA this thread issued before has completed
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive fp32 columns of this thread's TMEM lane (warp-wide; the load and its wait in one statement)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// X[f][32w .. 32w+31] (bytes) = the 32 bits of word w of row frows[f], each as 1.0 (e4m3) or 0
+__global__ void k_expand_e4m3(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows,
+                              uint32_t n1, uint4* __restrict__ X) {
+  const uint64_t total = (uint64_t)n1 * stride;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t f = (uint32_t)(idx / stride), w = (uint32_t)(idx % stride);
+    const uint32_t word = __ldg(bits + (size_t)frows[f] * stride + w);
+    uint32_t o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      // bits 4q..4q+3 to the lowest bit of bytes 0..3: the four shifted copies (0, 7, 14, 21) do not
+      // overlap, and bit b of copy b lands on bit 8b
+      const uint32_t nib = (word >> (4 * q)) & 0xFu;
+      o[q] = ((nib * 0x00204081u) & 0x01010101u) * kOneE4M3;
+    }
+    X[2 * idx] = make_uint4(o[0], o[1], o[2], o[3]);
+    X[2 * idx + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_pair_mma(const __grid_constant__ CUtensorMap xmap, uint32_t n1, uint32_t nbj, uint32_t n_tiles, uint32_t nsteps,
+               uint32_t steps_per_item, uint32_t ksplit, uint32_t* __restrict__ C2, uint32_t* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint32_t s_abort;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // the 128-byte swizzle repeats every 1024 bytes
+  const uint32_t a_st = base, b_st = base + kStages * kABytes;
+  const uint32_t bars = base + kStages * kStageBytes;
+  const uint32_t acc_bar = bars + 8 * 2 * kStages;
+  const uint32_t tslot = acc_bar + 8;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < kStages; ++s) {
+      mbar_init(bars + 8 * s, 1);              // full[s]: the producer's arrive + the TMA bytes
+      mbar_init(bars + 8 * (kStages + s), 1);  // empty[s]: the MMA commit that consumed stage s
+    }
+    mbar_init(acc_bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + (tslot - raw));
+
+  uint32_t issued = 0, consumed = 0;  // ring position of the producer and of the MMA thread
+  uint32_t acc_parity = 0;
+  const uint32_t n_items = n_tiles * ksplit;
+  for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    // items of one K range are consecutive, so the CTAs of a wave read the same K slices (L2 reuse)
+    const uint32_t split = item / n_tiles;
+    uint32_t t = item % n_tiles, bi = 0;
+    while (t >= nbj - bi / 2) {  // row block bi pairs with the column blocks bj >= bi / 2
+      t -= nbj - bi / 2;
+      ++bi;
+    }
+    const uint32_t bj = bi / 2 + t;
+    const uint32_t k0 = split * steps_per_item;
+    const uint32_t ns = min(nsteps, k0 + steps_per_item) - k0;
+
+    if (warp == 0) {
+      if (lane == 0) {
+        for (uint32_t s = 0; s < ns; ++s, ++issued) {
+          const uint32_t st = issued % kStages;
+          if (issued >= kStages && !mbar_wait(bars + 8 * (kStages + st), ((issued / kStages) - 1) & 1)) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          const uint32_t full = bars + 8 * st;
+          mbar_expect_tx(full, kStageBytes);
+          const int32_t x = (int32_t)((k0 + s) * kBK);
+          tma_load(a_st + st * kABytes, &xmap, x, (int32_t)(bi * kBM), full);
+          tma_load(b_st + st * kBBytes, &xmap, x, (int32_t)(bj * kBN), full);
+          tma_load(b_st + st * kBBytes + kABytes, &xmap, x, (int32_t)(bj * kBN + kBM), full);
+        }
+      }
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        for (uint32_t s = 0; s < ns; ++s) {
+          const uint32_t st = consumed % kStages;
+          if (!mbar_wait(bars + 8 * st, (consumed / kStages) & 1)) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          ++consumed;
+          tc_fence_after();
+          const uint64_t ad = sw128_desc(a_st + st * kABytes), bd = sw128_desc(b_st + st * kBBytes);
+#pragma unroll
+          for (uint32_t kk = 0; kk < kBK / kMmaK; ++kk)  // +32 bytes of K inside the swizzled rows: +2 in 16-byte units
+            mma_f8(tmem, ad + 2 * kk, bd + 2 * kk, (s | kk) != 0u);
+          mma_commit(bars + 8 * (kStages + st));  // stage st free once these MMAs are done
+        }
+        mma_commit(acc_bar);  // accumulator complete (also after an abort: the MMAs issued finish first)
+      }
+      __syncwarp();
+    }
+
+    const bool ok = mbar_wait(acc_bar, acc_parity);
+    acc_parity ^= 1u;
+    tc_fence_after();
+    if (!ok) {
+      atomicOr(err, DEV_ERR_TIMEOUT);
+      s_abort = 1;
+    } else {
+      const uint32_t i = bi * kBM + warp * 32 + lane;  // TMEM lane = row of the accumulator
+      const uint32_t lane_base = tmem + ((warp * 32u) << 16);
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < kBN; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(lane_base + c0, r);
+        const uint32_t j0 = bj * kBN + c0;
+        if (i < n1) {
+#pragma unroll
+          for (uint32_t c = 0; c < 16; ++c) {
+            const uint32_t j = j0 + c;
+            if (i < j && j < n1) {
+              const uint32_t v = __float2uint_rn(__uint_as_float(r[c]));
+              if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
+              else C2[(size_t)i * n1 + j] = v;
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort) break;
+  }
+
+  // copies still in flight after an abort: wait (bounded) for every issued stage not consumed
+  if (threadIdx.x == 0 && s_abort) {
+    for (uint32_t q = consumed; q < issued; ++q) (void)mbar_wait(bars + 8 * (q % kStages), (q / kStages) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                              : "memory");
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encoder(EncodeTiled* out) {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && (q != cudaDriverEntryPointSuccess || !p)) e = cudaErrorNotSupported;
+    fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  *out = fn;
+  return e;
+}
+
+uint32_t pair_tiles(uint32_t n1) {
+  const uint32_t nbi = (n1 + kBM - 1) / kBM, nbj = (n1 + kBN - 1) / kBN;
+  uint32_t tiles = 0;
+  for (uint32_t bi = 0; bi < nbi; ++bi) tiles += nbj - bi / 2;
+  return tiles;
+}
+
+}  // namespace
+
+uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride) { return (uint64_t)n1 * stride * 32ull; }
+
+double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms) {
+  // widening (bytes written at ~5 TB/s) + tile rounds at ~0.9 PFLOP/s of kind::f8f6f4 per 152 SMs
+  const double x_bytes = (double)pair_mma_buffer_bytes(n1, stride);
+  const uint32_t tiles = pair_tiles(n1);
+  const uint32_t nsteps = stride / 4;
+  const double step_us = 2.0 * kBM * kBN * kBK / (0.9e15 / 152.0) * 1e6;  // one 128-byte K slice of a tile
+  double best = 1e300;
+  for (uint32_t ks = 1; ks <= 256; ++ks) {
+    const uint32_t spi = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
+    const uint32_t k2 = (nsteps + spi - 1) / spi;
+    const uint64_t items = (uint64_t)tiles * k2;
+    const uint64_t rounds = (items + num_sms - 1) / num_sms;
+    best = std::min(best, (double)rounds * (spi * step_us + 1.5));
+  }
+  return x_bytes / 5e12 * 1e6 + best + 4.0;
+}
+
+cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, uint32_t* err, int num_sms, cudaStream_t st,
+                            uint32_t* ksplit_used) {
+  if (p.n1 < 2) {
+    *ksplit_used = 0;
+    return cudaSuccess;
+  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_pair_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  EncodeTiled encode = nullptr;
+  cudaError_t e = encoder(&encode);
+  if (e != cudaSuccess) return e;
+
+  // widen the frequent rows
+  const uint64_t words = (uint64_t)p.n1 * p.stride;
+  const uint32_t eg = (uint32_t)std::min<uint64_t>((words + 255) / 256, (uint64_t)num_sms * 16);
+  k_expand_e4m3<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  // X as a 2-D tensor of bytes: K (stride * 32 bytes) x n1 rows; boxes of 128 bytes x 128 rows, 128B swizzle;
+  // rows past n1 read as zeros
+  const uint64_t kb = (uint64_t)p.stride * 32;
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[2] = {kb, p.n1};
+  const cuuint64_t strides[1] = {kb};
+  const cuuint32_t box[2] = {kBK, kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, X, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+
+  const uint32_t nbj = (p.n1 + kBN - 1) / kBN;
+  const uint32_t tiles = pair_tiles(p.n1);
+  const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-byte slices
+  // split the K range so that the items fill whole rounds of the SMs; at most 2^24 bytes per item
+  uint32_t spi = std::min(kMaxStepsPerItem, nsteps);
+  double best = 1e300;
+  for (uint32_t ks = 1; ks <= 256; ++ks) {
+    const uint32_t c = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
+    if (c < 8 && ks > 1) break;  // at least 8 slices per item to repay its read-back
+    const uint32_t k2 = (nsteps + c - 1) / c;
+    const uint64_t items = (uint64_t)tiles * k2;
+    const uint64_t rounds = (items + num_sms - 1) / num_sms;
+    const double cost = (double)rounds * (c + 12.0);  // read-back of 256 columns ~ 12 slices
+    if (cost < best - 1e-9) {
+      best = cost;
+      spi = c;
+    }
+  }
+  const uint32_t ksplit = (nsteps + spi - 1) / spi;
+  *ksplit_used = ksplit;
+  if (ksplit > 1 && (e = cudaMemsetAsync(p.C2, 0, (size_t)p.n1 * p.n1 * sizeof(uint32_t), st)) != cudaSuccess)
+    return e;
+  const uint64_t items = (uint64_t)tiles * ksplit;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(items, (uint64_t)num_sms);
+  k_pair_mma<<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace fim

@@ -63,12 +63,18 @@ namespace {
 // can reach minsup (at most nnz / minsup of them), pair block, queue, DFS stack,
 // output, with the sample of the estimate on top.
 uint64_t job_footprint(uint32_t D, uint32_t N, uint64_t nnz, uint32_t max_len, uint32_t minsup, uint32_t grid,
-                       uint64_t total_mem) {
+                       uint64_t total_mem, int num_sms) {
   const uint64_t stride = ((uint64_t)(D + 31) / 32 + 31) / 32 * 32;
   const uint64_t rows = std::min<uint64_t>(N, nnz / std::max<uint32_t>(1, minsup) + 1);
   uint64_t b = 4ull * ((uint64_t)D + 1 + nnz);           // CSR
   b += 4ull * rows * stride;                              // bitmaps
   b += 4ull * rows * rows + 12ull * rows * rows / 2;      // pair counts, survivors, queue
+  // rows widened to bytes when the engine would take the tensor-core pair kernel
+  const uint64_t xb = fim::pair_mma_buffer_bytes((uint32_t)rows, (uint32_t)stride);
+  if (rows >= 2 && xb <= total_mem / 16 &&
+      fim::pair_mma_cost_us((uint32_t)rows, (uint32_t)stride, num_sms) <
+          fim::pair_cores_cost_us((uint32_t)rows, (uint32_t)stride, num_sms))
+    b += xb;
   // DFS stack: the full depth (itemsets are no longer than the longest transaction) when it fits
   // in 1/32 of the device memory, as the engine decides
   const uint64_t depth = std::max<uint32_t>(3, std::min<uint64_t>(max_len, rows)) - 1;
@@ -199,7 +205,7 @@ fim_status fim_server_submit(fim_server* srv, const uint32_t* tx_offsets, const 
   uint32_t max_len = 0;
   for (uint32_t t = 0; t < D; ++t)
     if (tx_offsets[t + 1] > tx_offsets[t]) max_len = std::max(max_len, tx_offsets[t + 1] - tx_offsets[t]);
-  j->footprint = job_footprint(D, N, nnz, max_len, minsup_abs, (uint32_t)nsm * srv->ctas_per_sm, srv->total_mem);
+  j->footprint = job_footprint(D, N, nnz, max_len, minsup_abs, (uint32_t)nsm * srv->ctas_per_sm, srv->total_mem, nsm);
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     j->id = srv->next_id++;

@@ -18,6 +18,7 @@ from . import _build
 FIM_OK, FIM_ERR_INVALID, FIM_ERR_OOM, FIM_ERR_OUTPUT_OVERFLOW, FIM_ERR_CUDA, FIM_ERR_TIMEOUT = range(6)
 FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
 FIM_DFS_NODES, FIM_DFS_FRAMES, FIM_DFS_AUTO, FIM_DFS_SPARSE = 0, 1, 2, 3
+FIM_PAIR_AUTO, FIM_PAIR_CORES, FIM_PAIR_TENSOR = 0, 1, 2
 SAMPLE_ITEMSET_LIMIT = 1 << 20  # FIM_SAMPLE_ITEMSET_LIMIT
 
 # every symbol declared in include/fim.h
@@ -50,11 +51,11 @@ class MineStats(ctypes.Structure):
         ("bytes_dfs_kernel", ctypes.c_uint64), ("words_per_row", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
         ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ms_pair_kernel", ctypes.c_float),
         ("ms_dfs_kernel", ctypes.c_float), ("ms_device_total", ctypes.c_float),
-        ("dfs_cta_busy_max_ms", ctypes.c_float), ("dfs_cta_busy_mean_ms", ctypes.c_float), ("reserved_f", ctypes.c_float),
+        ("dfs_cta_busy_max_ms", ctypes.c_float), ("dfs_cta_busy_mean_ms", ctypes.c_float), ("pair_kernel", ctypes.c_uint32),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class MineOpts(ctypes.Structure):
@@ -62,7 +63,8 @@ class MineOpts(ctypes.Structure):
         ("struct_size", ctypes.c_uint32), ("class_order", ctypes.c_uint32), ("dfs_mode", ctypes.c_uint32),
         ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
         ("donate", ctypes.c_uint32), ("result_on_device", ctypes.c_uint32), ("collect_times", ctypes.c_uint32),
-        ("dfs_depth_first", ctypes.c_uint32), ("out_capacity_sets", ctypes.c_uint64),
+        ("dfs_depth_first", ctypes.c_uint32), ("pair_kernel", ctypes.c_uint32), ("reserved_u", ctypes.c_uint32),
+        ("out_capacity_sets", ctypes.c_uint64),
         ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("max_itemsets", ctypes.c_uint64),
         ("out_needed_sets", ctypes.c_uint64),
         ("out_needed_items", ctypes.c_uint64), ("stats", ctypes.POINTER(MineStats)),
@@ -272,9 +274,10 @@ class Database:
 
     def _opts(self, class_order="estimate", threads_per_cta=0, vec_per_lane=0, ctas_per_sm=0, donate=False,
               result_on_device=False, collect_times=False, out_capacity_sets=0, out_capacity_items=0, spin_limit=0,
-              stats=True, shape=None, dfs_mode=None, max_itemsets=0):
+              stats=True, shape=None, dfs_mode=None, max_itemsets=0, pair_kernel=FIM_PAIR_AUTO):
         opts = MineOpts()
         self._lib.fim_mine_opts_init(ctypes.byref(opts))
+        opts.pair_kernel = pair_kernel
         if dfs_mode is not None:
             opts.dfs_mode = dfs_mode
         opts.class_order = {"estimate": FIM_ORDER_ESTIMATE, "uniform": FIM_ORDER_UNIFORM}[class_order]
@@ -317,12 +320,12 @@ class Database:
              ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
              out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
              shape=None, dfs_mode: int | None = None, max_itemsets: int = 0, class_work: bool = False,
-             dfs_depth_first: int = 0):
+             dfs_depth_first: int = 0, pair_kernel: int = FIM_PAIR_AUTO):
         """fim_mine; with ``class_work`` the result carries ``class_work`` (u64[n_rows]): the intersections
         of every one-row class, level 2 and below."""
         opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
                               collect_times, out_capacity_sets, out_capacity_items, spin_limit, stats, shape, dfs_mode,
-                              max_itemsets)
+                              max_itemsets, pair_kernel)
         opts.dfs_depth_first = dfs_depth_first
         cw = None
         if class_work:
