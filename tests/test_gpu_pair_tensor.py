@@ -49,7 +49,7 @@ def test_ragged_frequent_rows(n1, D):
     """Every item frequent (minsup 1), transactions of at most 4 items: all pairs that occur, and
     the deeper itemsets, equal the oracle; tile edges at 128 (i) and 256 (j) rows."""
     rng = np.random.default_rng(n1 * 7 + D)
-    txs = [list(rng.choice(n1, size=rng.integers(1, 5), replace=False)) for _ in range(D)]
+    txs = [list(rng.choice(n1, size=rng.integers(1, min(5, n1 + 1)), replace=False)) for _ in range(D)]
     txs += [[k, (k + 1) % n1] for k in range(n1)]  # every item occurs
     off, items = csr(txs)
     want = odict(oracle.eclat(off, items, n1, 1))
