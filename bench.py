@@ -36,9 +36,11 @@ WORKLOAD = "sparse_mid"  # the configuration the headline metric is quoted on; -
 SAMPLE_RATE = 0.01
 EST_SEED = 1
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one launch of the current k_pair_counts, from one ncu capture of the
-# mine's launch per workload (profiles/k_pair_counts_sparse_mid.md); None where none was taken
+# DRAM bytes (read + write) of one launch of the level-2 pair kernel, from one ncu capture of the mine's
+# launch per workload: the integer-pipe k_pair_counts (profiles/k_pair_counts_sparse_mid.md) and the
+# tensor-core k_expand_e4m3 + k_pair_mma (profiles/k_pair_mma.md); None where none was taken
 PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_683_390_000}
+PAIR_MMA_TRAFFIC = {}
 # the same for the persistent DFS kernel (profiles/k_dfs_large_sparse.md)
 DFS_KERNEL_TRAFFIC = {"large_sparse": 749_740_000}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
@@ -271,6 +273,18 @@ def run_ours(args):
                                  if stats["n_frequent_items"] * ((D + 31) // 32) * 4 > 129e6 else
                                  "the rows fit in L2 (129 MB): the DFS is bound by the latency of its dependent "
                                  "per-node steps, not by HBM; the fraction is of the HBM copy rate")}
+        elif stats.get("pair_kernel") == 2:  # level 2 on the tensor cores: the 0/1 contraction in e4m3
+            flops = 2.0 * stats["n_pair_intersections"] * D  # one multiply-add per pair and transaction
+            tf = flops / (pair_avg * 1e-3) / 1e12
+            peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0))
+            roofline = {"kernel": "k_expand_e4m3 + k_pair_mma", "bound": "tensor", "achieved": round(tf, 1),
+                        "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(tf / peak, 4),
+                        "traffic": PAIR_MMA_TRAFFIC.get(args.workload),
+                        "peak_source": ("e4m3 dense = 2 x the measured bf16 burst (MEASURED_PEAKS.json bf16_tflops; "
+                                        "nominal fp8:bf16 = 4.5:2.25)" if "bf16_tflops" in peaks
+                                        else "fallback 1.9 PFLOP/s bf16 x 2"),
+                        "note": "algorithmic flops: 2 x pairs i<j x transactions; the time includes widening "
+                                "the rows to bytes"}
         else:
             roofline = {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                         "peak": round(alu_peak_gword, 1), "unit": "Gword/s",

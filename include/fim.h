@@ -75,19 +75,21 @@ typedef struct {
   float ms_device_total;         /* CUDA-event time from the first to the last mining kernel       */
   float dfs_cta_busy_max_ms;     /* longest time a persistent DFS CTA was resident (collect_times)  */
   float dfs_cta_busy_mean_ms;    /* mean over the CTAs; max / mean is the load imbalance           */
-  uint32_t pair_kernel;          /* level-2 kernel that ran: FIM_PAIR_CORES or FIM_PAIR_TENSOR     */
+  uint32_t pair_kernel;          /* level-2 kernel that ran: FIM_PAIR_CORES / _TENSOR / _TENSOR_E4M3 */
 } fim_mine_stats;
 
 /* Traversal of the persistent DFS (fim_mine_opts.dfs_mode). */
 enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3 };
 
 /* Level-2 pair counts (fim_mine_opts.pair_kernel): FIM_PAIR_CORES: AND + popcount on the integer
- * pipes (8-word carry-save adder tree); FIM_PAIR_TENSOR: the 0/1 rows widened to one byte per
- * transaction (1.0 in e4m3) and multiplied on the tensor cores (tcgen05 kind::f8f6f4, fp32
- * accumulators, at most 2^24 transactions per partial sum, so exact), which needs a scratch of
- * frequent rows x padded row bytes x 8 in the database's workspace; FIM_PAIR_AUTO: the one with
- * the smaller modelled time, tensor only while that scratch is at most 1/16 of device memory. */
-enum { FIM_PAIR_AUTO = 0, FIM_PAIR_CORES = 1, FIM_PAIR_TENSOR = 2 };
+ * pipes (8-word carry-save adder tree); FIM_PAIR_TENSOR: the 0/1 rows widened to 4-bit values
+ * (1.0 in e2m1, two transactions per byte) and multiplied on the tensor cores (tcgen05
+ * kind::f8f6f4, fp32 accumulators, at most 2^24 transactions per partial sum, so exact), which
+ * needs a scratch of frequent rows x padded row bytes x 4 in the database's workspace;
+ * FIM_PAIR_TENSOR_E4M3: the same with one byte per transaction (1.0 in e4m3, twice the scratch);
+ * FIM_PAIR_AUTO: integer pipes or FIM_PAIR_TENSOR, whichever has the smaller modelled time, the
+ * tensor cores only while their scratch is at most 1/16 of device memory. */
+enum { FIM_PAIR_AUTO = 0, FIM_PAIR_CORES = 1, FIM_PAIR_TENSOR = 2, FIM_PAIR_TENSOR_E4M3 = 3 };
 
 typedef struct {
   uint32_t struct_size;        /* set to sizeof(fim_mine_opts); 0 = treat as defaults            */
@@ -113,7 +115,8 @@ typedef struct {
   uint32_t dfs_depth_first;    /* 0 = automatic (the full depth bound when its stack fits in 1/32 of
                                   device memory); else the first DFS stack depth, grown and the run
                                   repeated when an itemset is deeper                                */
-  uint32_t pair_kernel;        /* FIM_PAIR_AUTO (0, default), FIM_PAIR_CORES or FIM_PAIR_TENSOR      */
+  uint32_t pair_kernel;        /* FIM_PAIR_AUTO (0, default), FIM_PAIR_CORES, FIM_PAIR_TENSOR or
+                                  FIM_PAIR_TENSOR_E4M3                                              */
   uint32_t reserved_u;         /* 0                                                               */
   uint64_t out_capacity_sets;  /* 0 = automatic (grow and retry); else fixed capacity             */
   uint64_t out_capacity_items; /* idem, total items over all sets                                 */

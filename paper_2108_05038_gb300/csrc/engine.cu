@@ -69,11 +69,14 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // (one byte per transaction) take at most 1/16 of the device memory; TMA coordinates are signed
   // 32-bit, so widened rows of less than 2^31 bytes
   if (n1 >= 2) {
-    const uint64_t xb = pair_mma_buffer_bytes(n1, in.stride);
-    const bool fits = (uint64_t)in.stride * 32 < (1ull << 31) && xb <= db->total_mem / 16;
-    if (cfg.pair_kernel == 2) ep->pair_mma = (uint64_t)in.stride * 32 < (1ull << 31);
+    ep->pair_e2m1 = cfg.pair_kernel != 3;
+    const uint64_t xb = pair_mma_buffer_bytes(n1, in.stride, ep->pair_e2m1);
+    const bool coords_ok = (uint64_t)in.stride * 32 < (1ull << 31);
+    if (cfg.pair_kernel >= 2) ep->pair_mma = coords_ok;
     else if (cfg.pair_kernel == 0)
-      ep->pair_mma = fits && pair_mma_cost_us(n1, in.stride, db->num_sms) < pair_cores_cost_us(n1, in.stride, db->num_sms);
+      ep->pair_mma = coords_ok && xb <= db->total_mem / 16 &&
+                     pair_mma_cost_us(n1, in.stride, db->num_sms, ep->pair_e2m1) <
+                         pair_cores_cost_us(n1, in.stride, db->num_sms);
     if (ep->pair_mma) FIM_TRY(ws_get(ws, WS_PAIR_X, xb, &ep->d_X));
   }
   FIM_TRY(ws_get(ws, WS_SCNT, n1, &ep->d_scnt));
@@ -161,7 +164,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   if (!ep.skip_pairs) {
     uint32_t ksplit = 0;
     PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
-    ce = ep.pair_mma ? launch_pair_mma(pl, ep.d_X, &ep.d_ctrl->err, ep.num_sms, st, &ksplit)
+    ce = ep.pair_mma ? launch_pair_mma(pl, ep.d_X, ep.pair_e2m1, &ep.d_ctrl->err, ep.num_sms, st, &ksplit)
                      : launch_pair_counts(pl, ep.num_sms, st, &ksplit);
     if (ce != cudaSuccess) return ce;
   }
@@ -297,7 +300,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     stats->grid_ctas = n1 >= 3 ? ep->grid : 0;
     stats->threads_per_cta = ep->threads;
     stats->vec_per_lane = ep->vec;
-    stats->pair_kernel = ep->pair_mma ? FIM_PAIR_TENSOR : FIM_PAIR_CORES;
+    stats->pair_kernel = !ep->pair_mma ? FIM_PAIR_CORES : ep->pair_e2m1 ? FIM_PAIR_TENSOR : FIM_PAIR_TENSOR_E4M3;
     if (ep->ev[0] && n1 > 0) {
       stats->ms_pair_kernel = ep->ms_pair;  // the one pair-kernel launch of this mine
       cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);  // the last DFS run

@@ -7,6 +7,10 @@
 // App. B.3.2, for all one-item classes at once).  tcgen05 has no 1-bit kind, so
 // each row is widened once to bytes (bit set -> 1.0 in e4m3, else 0) and the
 // product runs as kind::f8f6f4 MMAs with fp32 accumulators in tensor memory.
+// Two operand forms: e4m3 (1.0 = 0x38, one byte per transaction in memory) and
+// e2m1 (1.0 = 0x2, two transactions per byte in memory; the TMA spreads each 8
+// packed bytes to the 16-byte unpacked form the MMA reads, so shared memory and
+// MMA rate are those of e4m3 while the widened rows and their reads halve).
 // Every product is 0 or 1, so a partial sum is an integer no larger than the
 // bytes it covers; a work item covers at most 2^24 bytes of K, where fp32 holds
 // every integer exactly, and items of one tile are added as u32 atomics.
@@ -16,7 +20,9 @@
 // thread issues TMA loads of 128-byte K slices (128B swizzle) into a 4-stage
 // ring, one thread issues four 128x256x32 MMAs per slice into a 256-column TMEM
 // accumulator, and the four warps read the accumulator back (tcgen05.ld, one
-// TMEM lane quarter per warp) and write or add the counts of pairs i < j.
+// TMEM lane quarter per warp) into shared memory (the ring is idle then), from
+// where whole 128-byte row segments are written or added (coalesced) for the
+// pairs i < j.
 // Every mbarrier wait is bounded by time; on expiry the kernel sets
 // DEV_ERR_TIMEOUT, lets its copies and MMAs in flight finish, frees its TMEM and
 // returns.
@@ -44,10 +50,16 @@ constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kBarBytes; 
 constexpr uint32_t kTmemCols = kBN;                          // fp32 accumulator: 128 lanes x 256 columns
 constexpr uint32_t kMaxStepsPerItem = (1u << 24) / kBK;      // fp32 exact: at most 2^24 bytes of K per item
 constexpr uint64_t kWaitNs = 1000000000ull;                  // bound of every mbarrier wait (1 s)
-// instruction descriptor of kind::f8f6f4: D f32 (bits 4-5 = 1), A and B e4m3 (bits 7-9, 10-12 = 0), both
-// K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | ((kBN >> 3) << 17) | ((kBM >> 4) << 24);
-constexpr uint32_t kOneE4M3 = 0x38u;
+// instruction descriptor of kind::f8f6f4: D f32 (bits 4-5 = 1), A and B format in bits 7-9 and 10-12
+// (e4m3 = 0, e2m1 = 5), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
+template <bool kE2M1>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | ((kE2M1 ? 5u : 0u) << 7) | ((kE2M1 ? 5u : 0u) << 10) | ((kBN >> 3) << 17) | ((kBM >> 4) << 24);
+}
+constexpr uint32_t kOneE4M3 = 0x38u;  // 1.0: exponent 7 (the bias), mantissa 0
+constexpr uint32_t kOneE2M1 = 0x2u;   // 1.0: exponent 1 (the bias), mantissa 0
+constexpr uint32_t kTPitch = kBN + 1;  // read-back tile in shared memory: u32, padded rows (conflict-free)
+static_assert((size_t)kBM * kTPitch * 4 <= (size_t)kStages * kStageBytes, "read-back tile fits in the ring");
 static_assert(kBN % 16 == 0 && kBN <= 256 && kBM == 128, "MMA shape of cta_group::1");
 static_assert(kBK % kMmaK == 0, "whole MMAs per stage");
 
@@ -105,12 +117,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
          (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_f8f6f4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -155,6 +168,30 @@ __global__ void k_expand_e4m3(const uint32_t* __restrict__ bits, uint32_t stride
   }
 }
 
+// X[f][16w .. 16w+15] (bytes) = the 32 bits of word w of row frows[f] as 32 e2m1 values (1.0 or 0),
+// transaction 2k in the low nibble of byte k
+__global__ void k_expand_e2m1(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows,
+                              uint32_t n1, uint4* __restrict__ X) {
+  const uint64_t total = (uint64_t)n1 * stride;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t f = (uint32_t)(idx / stride), w = (uint32_t)(idx % stride);
+    const uint32_t word = __ldg(bits + (size_t)frows[f] * stride + w);
+    uint32_t o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // the 8 bits of byte q to bit 0 of nibbles 0..7 (interleave with three zero bits), then x 2
+      uint32_t t = (word >> (8 * q)) & 0xFFu;
+      t = (t | (t << 12)) & 0x000F000Fu;
+      t = (t | (t << 6)) & 0x03030303u;
+      t = (t | (t << 3)) & 0x11111111u;
+      o[q] = t * kOneE2M1;
+    }
+    X[idx] = make_uint4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+template <bool kE2M1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pair_mma(const __grid_constant__ CUtensorMap xmap, uint32_t n1, uint32_t nbj, uint32_t n_tiles, uint32_t nsteps,
                uint32_t steps_per_item, uint32_t ksplit, uint32_t* __restrict__ C2, uint32_t* __restrict__ err) {
@@ -212,7 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           const uint32_t full = bars + 8 * st;
-          mbar_expect_tx(full, kStageBytes);
+          // transaction bytes = bytes the TMA moves: e2m1 boxes carry 64 packed bytes per row (the gaps of
+          // the unpacked shared-memory form are not written)
+          mbar_expect_tx(full, kE2M1 ? kStageBytes / 2 : kStageBytes);
           const int32_t x = (int32_t)((k0 + s) * kBK);
           tma_load(a_st + st * kABytes, &xmap, x, (int32_t)(bi * kBM), full);
           tma_load(b_st + st * kBBytes, &xmap, x, (int32_t)(bj * kBN), full);
@@ -234,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t ad = sw128_desc(a_st + st * kABytes), bd = sw128_desc(b_st + st * kBBytes);
 #pragma unroll
           for (uint32_t kk = 0; kk < kBK / kMmaK; ++kk)  // +32 bytes of K inside the swizzled rows: +2 in 16-byte units
-            mma_f8(tmem, ad + 2 * kk, bd + 2 * kk, (s | kk) != 0u);
+            mma_f8f6f4(tmem, ad + 2 * kk, bd + 2 * kk, idesc<kE2M1>(), (s | kk) != 0u);
           mma_commit(bars + 8 * (kStages + st));  // stage st free once these MMAs are done
         }
         mma_commit(acc_bar);  // accumulator complete (also after an abort: the MMAs issued finish first)
@@ -242,32 +281,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
     }
 
-    const bool ok = mbar_wait(acc_bar, acc_parity);
+    // every thread takes the same branch below (it holds barriers): all waited successfully, or none goes on
+    const bool ok = __syncthreads_and(mbar_wait(acc_bar, acc_parity)) != 0;
     acc_parity ^= 1u;
     tc_fence_after();
     if (!ok) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       s_abort = 1;
     } else {
-      const uint32_t i = bi * kBM + warp * 32 + lane;  // TMEM lane = row of the accumulator
+      // TMEM lane = row of the accumulator; the ring is idle (every stage consumed), so it holds the
+      // counts as a padded u32 tile: lane l of warp w writes row 32w + l (banks (l + c) mod 32)
+      uint32_t* T = reinterpret_cast<uint32_t*>(smem_raw + (base - raw));
+      const uint32_t row = warp * 32 + lane;
       const uint32_t lane_base = tmem + ((warp * 32u) << 16);
 #pragma unroll 1
       for (uint32_t c0 = 0; c0 < kBN; c0 += 16) {
         uint32_t r[16];
         tmem_ld16(lane_base + c0, r);
-        const uint32_t j0 = bj * kBN + c0;
-        if (i < n1) {
 #pragma unroll
-          for (uint32_t c = 0; c < 16; ++c) {
-            const uint32_t j = j0 + c;
-            if (i < j && j < n1) {
-              const uint32_t v = __float2uint_rn(__uint_as_float(r[c]));
-              if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
-              else C2[(size_t)i * n1 + j] = v;
-            }
+        for (uint32_t c = 0; c < 16; ++c) T[row * kTPitch + c0 + c] = __float2uint_rn(__uint_as_float(r[c]));
+      }
+      __syncthreads();
+      // row segments of 128 consecutive j per instruction group: thread t takes columns t and t + 128
+      const uint32_t i_end = min(kBM, n1 - bi * kBM);
+#pragma unroll 1
+      for (uint32_t rr = 0; rr < i_end; ++rr) {
+        const uint32_t i = bi * kBM + rr;
+#pragma unroll
+        for (uint32_t h = 0; h < kBN / kThreads; ++h) {
+          const uint32_t cc = threadIdx.x + h * kThreads, j = bj * kBN + cc;
+          if (i < j && j < n1) {
+            const uint32_t v = T[rr * kTPitch + cc];
+            if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
+            else C2[(size_t)i * n1 + j] = v;
           }
         }
       }
+      // the ring's next writes come from the async proxy (TMA): order these generic accesses first
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
@@ -313,26 +364,28 @@ uint32_t pair_tiles(uint32_t n1) {
 
 }  // namespace
 
-uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride) { return (uint64_t)n1 * stride * 32ull; }
+uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride, bool e2m1) {
+  return (uint64_t)n1 * stride * (e2m1 ? 16ull : 32ull);
+}
 
-double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms) {
-  // widening (bytes written at ~5 TB/s) + tile rounds at ~0.9 PFLOP/s of kind::f8f6f4 per 152 SMs
-  const double x_bytes = (double)pair_mma_buffer_bytes(n1, stride);
+double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1) {
+  // widening (bytes written at ~5 TB/s) + tile rounds at ~1.5 PFLOP/s of kind::f8f6f4 per 152 SMs
+  const double x_bytes = (double)pair_mma_buffer_bytes(n1, stride, e2m1);
   const uint32_t tiles = pair_tiles(n1);
   const uint32_t nsteps = stride / 4;
-  const double step_us = 2.0 * kBM * kBN * kBK / (0.9e15 / 152.0) * 1e6;  // one 128-byte K slice of a tile
+  const double step_us = 2.0 * kBM * kBN * kBK / (1.5e15 / 152.0) * 1e6;  // one 128-element K slice of a tile
   double best = 1e300;
   for (uint32_t ks = 1; ks <= 256; ++ks) {
     const uint32_t spi = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
     const uint32_t k2 = (nsteps + spi - 1) / spi;
     const uint64_t items = (uint64_t)tiles * k2;
     const uint64_t rounds = (items + num_sms - 1) / num_sms;
-    best = std::min(best, (double)rounds * (spi * step_us + 1.5));
+    best = std::min(best, (double)rounds * (spi * step_us + 1.0));
   }
   return x_bytes / 5e12 * 1e6 + best + 4.0;
 }
 
-cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, uint32_t* err, int num_sms, cudaStream_t st,
+cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t* err, int num_sms, cudaStream_t st,
                             uint32_t* ksplit_used) {
   if (p.n1 < 2) {
     *ksplit_used = 0;
@@ -341,7 +394,9 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, uint32_t* err, int 
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_pair_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    attr_err = cudaFuncSetAttribute(k_pair_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k_pair_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   });
   if (attr_err != cudaSuccess) return attr_err;
   EncodeTiled encode = nullptr;
@@ -351,27 +406,30 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, uint32_t* err, int 
   // widen the frequent rows
   const uint64_t words = (uint64_t)p.n1 * p.stride;
   const uint32_t eg = (uint32_t)std::min<uint64_t>((words + 255) / 256, (uint64_t)num_sms * 16);
-  k_expand_e4m3<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
+  if (e2m1) k_expand_e2m1<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
+  else k_expand_e4m3<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  // X as a 2-D tensor of bytes: K (stride * 32 bytes) x n1 rows; boxes of 128 bytes x 128 rows, 128B swizzle;
-  // rows past n1 read as zeros
-  const uint64_t kb = (uint64_t)p.stride * 32;
+  // X as a 2-D tensor: K (stride * 32 transactions) x n1 rows; boxes of 128 transactions x 128 rows with
+  // the 128-byte swizzle (e2m1: 64 packed bytes per box row, unpacked by the TMA to 128 in shared
+  // memory); rows past n1 read as zeros
+  const uint64_t k_elems = (uint64_t)p.stride * 32;
+  const uint64_t row_bytes = e2m1 ? k_elems / 2 : k_elems;
   alignas(64) CUtensorMap map;
-  const cuuint64_t dims[2] = {kb, p.n1};
-  const cuuint64_t strides[1] = {kb};
+  const cuuint64_t dims[2] = {k_elems, p.n1};
+  const cuuint64_t strides[1] = {row_bytes};
   const cuuint32_t box[2] = {kBK, kBM};
   const cuuint32_t estr[2] = {1, 1};
-  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, X, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  if (encode(&map, e2m1 ? CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, X, dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
 
   const uint32_t nbj = (p.n1 + kBN - 1) / kBN;
   const uint32_t tiles = pair_tiles(p.n1);
-  const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-byte slices
-  // split the K range so that the items fill whole rounds of the SMs; at most 2^24 bytes per item
+  const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-element slices
+  // split the K range so that the items fill whole rounds of the SMs; at most 2^24 elements per item
   uint32_t spi = std::min(kMaxStepsPerItem, nsteps);
   double best = 1e300;
   for (uint32_t ks = 1; ks <= 256; ++ks) {
@@ -380,7 +438,7 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, uint32_t* err, int 
     const uint32_t k2 = (nsteps + c - 1) / c;
     const uint64_t items = (uint64_t)tiles * k2;
     const uint64_t rounds = (items + num_sms - 1) / num_sms;
-    const double cost = (double)rounds * (c + 12.0);  // read-back of 256 columns ~ 12 slices
+    const double cost = (double)rounds * (c + 6.0);  // read-back of the tile ~ 6 slices
     if (cost < best - 1e-9) {
       best = cost;
       spi = c;
@@ -392,7 +450,8 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, uint32_t* err, int 
     return e;
   const uint64_t items = (uint64_t)tiles * ksplit;
   const uint32_t grid = (uint32_t)std::min<uint64_t>(items, (uint64_t)num_sms);
-  k_pair_mma<<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err);
+  if (e2m1) k_pair_mma<true><<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err);
+  else k_pair_mma<false><<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err);
   note_launch();
   return cudaGetLastError();
 }

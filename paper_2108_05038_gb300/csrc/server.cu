@@ -70,9 +70,9 @@ uint64_t job_footprint(uint32_t D, uint32_t N, uint64_t nnz, uint32_t max_len, u
   b += 4ull * rows * stride;                              // bitmaps
   b += 4ull * rows * rows + 12ull * rows * rows / 2;      // pair counts, survivors, queue
   // rows widened to bytes when the engine would take the tensor-core pair kernel
-  const uint64_t xb = fim::pair_mma_buffer_bytes((uint32_t)rows, (uint32_t)stride);
+  const uint64_t xb = fim::pair_mma_buffer_bytes((uint32_t)rows, (uint32_t)stride, true);
   if (rows >= 2 && xb <= total_mem / 16 &&
-      fim::pair_mma_cost_us((uint32_t)rows, (uint32_t)stride, num_sms) <
+      fim::pair_mma_cost_us((uint32_t)rows, (uint32_t)stride, num_sms, true) <
           fim::pair_cores_cost_us((uint32_t)rows, (uint32_t)stride, num_sms))
     b += xb;
   // DFS stack: the full depth (itemsets are no longer than the longest transaction) when it fits
