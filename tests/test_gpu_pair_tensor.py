@@ -1,4 +1,5 @@
-"""Level-2 pair counts on the tensor cores (FIM_PAIR_TENSOR) against the oracle: named workloads at
+"""Level-2 pair counts on the tensor cores (FIM_PAIR_TENSOR: packed e2m1 operands; FIM_PAIR_TENSOR_E4M3:
+byte operands) against the oracle: named workloads at
 full size, ragged numbers of frequent rows around the 128 x 256 tile edges, supports past 2^24 (fp32
 exactness needs the K range split), graph replays, and the integer-pipe kernel on the same inputs."""
 import numpy as np
@@ -27,14 +28,18 @@ def csr(txs):
     return off, items
 
 
+TENSOR = [fim.FIM_PAIR_TENSOR, fim.FIM_PAIR_TENSOR_E4M3]
+
+
+@pytest.mark.parametrize("pk", TENSOR)
 @pytest.mark.parametrize("name", ["tiny", "dense_deep", "dense_exact37", "sparse_mid"])
-def test_workloads_exact_on_tensor_cores(name):
+def test_workloads_exact_on_tensor_cores(name, pk):
     w = synth.make_workload(name)
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=w["word_bits"])
     try:
-        res = db.mine(w["minsup"], pair_kernel=fim.FIM_PAIR_TENSOR)
-        assert res.stats["pair_kernel"] == fim.FIM_PAIR_TENSOR
+        res = db.mine(w["minsup"], pair_kernel=pk)
+        assert res.stats["pair_kernel"] == pk
         assert res.as_dict() == want
         cores = db.mine(w["minsup"], pair_kernel=fim.FIM_PAIR_CORES)
         assert cores.stats["pair_kernel"] == fim.FIM_PAIR_CORES
@@ -43,9 +48,10 @@ def test_workloads_exact_on_tensor_cores(name):
         db.free()
 
 
+@pytest.mark.parametrize("pk", TENSOR)
 @pytest.mark.parametrize("n1", [2, 3, 127, 128, 129, 255, 256, 257, 383, 385, 600])
 @pytest.mark.parametrize("D", [700, 4097])
-def test_ragged_frequent_rows(n1, D):
+def test_ragged_frequent_rows(n1, D, pk):
     """Every item frequent (minsup 1), transactions of at most 4 items: all pairs that occur, and
     the deeper itemsets, equal the oracle; tile edges at 128 (i) and 256 (j) rows."""
     rng = np.random.default_rng(n1 * 7 + D)
@@ -55,12 +61,13 @@ def test_ragged_frequent_rows(n1, D):
     want = odict(oracle.eclat(off, items, n1, 1))
     db = fim.build_vertical_db(off, items, n1)
     try:
-        assert db.mine(1, pair_kernel=fim.FIM_PAIR_TENSOR).as_dict() == want
+        assert db.mine(1, pair_kernel=pk).as_dict() == want
     finally:
         db.free()
 
 
-def test_supports_past_fp32_integer_range():
+@pytest.mark.parametrize("pk", TENSOR)
+def test_supports_past_fp32_integer_range(pk):
     """D = 2^24 + 1 identical transactions of 12 items: every one of the 4,095 itemsets has support
     2^24 + 1, which fp32 cannot hold, so the K range must be split into exact partial sums."""
     D, N = (1 << 24) + 1, 12
@@ -69,7 +76,7 @@ def test_supports_past_fp32_integer_range():
     torch.cuda.synchronize()
     db = fim.build_vertical_db_device(d_off, d_items, D, N, 64, 0)
     try:
-        res = db.mine(D, pair_kernel=fim.FIM_PAIR_TENSOR)
+        res = db.mine(D, pair_kernel=pk)
         got = res.as_dict()
         assert len(got) == (1 << N) - 1
         assert set(got.values()) == {D}
