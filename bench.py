@@ -273,11 +273,11 @@ def run_ours(args):
                                  if stats["n_frequent_items"] * ((D + 31) // 32) * 4 > 129e6 else
                                  "the rows fit in L2 (129 MB): the DFS is bound by the latency of its dependent "
                                  "per-node steps, not by HBM; the fraction is of the HBM copy rate")}
-        elif stats.get("pair_kernel") == 2:  # level 2 on the tensor cores: the 0/1 contraction in e4m3
+        elif stats.get("pair_kernel") in (2, 3):  # level 2 on the tensor cores: the 0/1 contraction in e4m3
             flops = 2.0 * stats["n_pair_intersections"] * D  # one multiply-add per pair and transaction
             tf = flops / (pair_avg * 1e-3) / 1e12
             peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0))
-            roofline = {"kernel": "k_expand_e4m3 + k_pair_mma", "bound": "tensor", "achieved": round(tf, 1),
+            roofline = {"kernel": "k_expand_e2m1 + k_pair_mma" if stats.get("pair_kernel") == 2 else "k_expand_e4m3 + k_pair_mma", "bound": "tensor", "achieved": round(tf, 1),
                         "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(tf / peak, 4),
                         "traffic": PAIR_MMA_TRAFFIC.get(args.workload),
                         "peak_source": ("e4m3 dense = 2 x the measured bf16 burst (MEASURED_PEAKS.json bf16_tflops; "
