@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     """Compile fim_oracle.c with gcc (plain C, -O2)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -46,6 +46,8 @@ def _load():
                 f = getattr(lib, name)
                 f.restype = ctypes.c_int
                 f.argtypes = [P, P, u32, u32, u32, PP]
+            lib.oracle_eclat_mt.restype = ctypes.c_int
+            lib.oracle_eclat_mt.argtypes = [P, P, u32, u32, u32, u32, PP]
             lib.oracle_result_free.restype = None
             lib.oracle_result_free.argtypes = [P]
             lib.oracle_result_sort.restype = ctypes.c_int
@@ -83,12 +85,12 @@ def _csr(offsets, items):
     return offsets, items
 
 
-def _run(fname, offsets, items, N, minsup):
+def _run(fname, offsets, items, N, minsup, *extra):
     lib = _load()
     offsets, items = _csr(offsets, items)
     D = offsets.size - 1
     h = ctypes.c_void_p()
-    rc = getattr(lib, fname)(offsets.ctypes.data, items.ctypes.data, D, N, minsup, ctypes.byref(h))
+    rc = getattr(lib, fname)(offsets.ctypes.data, items.ctypes.data, D, N, minsup, *extra, ctypes.byref(h))
     if rc != 0:
         raise ValueError(f"{fname} failed with code {rc}")
     try:
@@ -108,6 +110,11 @@ def _run(fname, offsets, items, N, minsup):
 def eclat(offsets, items, N: int, minsup: int):
     """O1: Eclat-DFS over sorted tidlists (App. B.3.2)."""
     return _run("oracle_eclat", offsets, items, N, minsup)
+
+
+def eclat_mt(offsets, items, N: int, minsup: int, threads: int = 0):
+    """O1 with the one-item classes spread over ``threads`` host threads (0: every core); same output."""
+    return _run("oracle_eclat_mt", offsets, items, N, minsup, threads or (os.cpu_count() or 1))
 
 
 def bruteforce(offsets, items, N: int, minsup: int):

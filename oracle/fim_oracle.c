@@ -20,6 +20,10 @@
  *                           its support is >= minsupp, and recurses with the new
  *                           atoms and prefix P u {a_i}; frequent singletons are
  *                           output at the top; the empty set is never output.
+ *  O1 oracle_eclat_mt    -- the same recursion with the one-item classes [a_i | later
+ *                           atoms] handed to threads (the classes are independent,
+ *                           Sec. 2.4); each thread keeps its own output, the outputs are
+ *                           concatenated.  Used to time the oracle on every host core.
  *  O2 oracle_bruteforce  -- the definition itself (Def. "Frequent itemset",
  *                           Ch. 2): every non-empty subset of the item base,
  *                           support counted by scanning all transactions.
@@ -47,6 +51,7 @@
  * division count / total.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -232,32 +237,39 @@ typedef struct {
   uint64_t limit;   /* 0 = none */
 } eclat_ctx;
 
+static void eclat_rec(eclat_ctx* c, atom* A, uint32_t nA, uint32_t depth);
+
+/* One step of Eclat-DFS-Computation(A, P): the class of atom i, i.e. every
+ * P u {a_i, a_j} (j > i) from t(P u {a_i}) n t(P u {a_j}), output when frequent,
+ * then the recursion on the new atoms with prefix P u {a_i}. */
+static void eclat_class(eclat_ctx* c, atom* A, uint32_t nA, uint32_t i, uint32_t depth) {
+  atom* Ai = (atom*)malloc(sizeof(atom) * (nA - i > 1 ? nA - i - 1 : 1));
+  uint32_t nAi = 0;
+  if (!Ai) { c->err = -1; return; }
+  c->prefix[depth] = A[i].item;
+  for (uint32_t j = i + 1; j < nA; ++j) {
+    uint32_t cap = A[i].n < A[j].n ? A[i].n : A[j].n;
+    uint32_t* buf = (uint32_t*)malloc(sizeof(uint32_t) * (cap ? cap : 1));
+    if (!buf) { c->err = -1; break; }
+    uint32_t n = intersect(A[i].tids, A[i].n, A[j].tids, A[j].n, buf);
+    if (n >= c->minsup) {
+      Ai[nAi].item = A[j].item; Ai[nAi].n = n; Ai[nAi].tids = buf; ++nAi;
+      c->prefix[depth + 1] = A[j].item;
+      if (res_add(c->out, c->prefix, depth + 2, n) != 0) { c->err = -1; break; }
+      if (c->limit && c->out->n_sets > c->limit) { c->err = 1; break; }
+    } else {
+      free(buf);
+    }
+  }
+  if (!c->err) eclat_rec(c, Ai, nAi, depth + 1);
+  for (uint32_t k = 0; k < nAi; ++k) free(Ai[k].tids);
+  free(Ai);
+}
+
 /* Eclat-DFS-Computation(A, P): A holds atoms a with t(P u {a}); every atom is
  * itself already frequent and already output by the caller. */
 static void eclat_rec(eclat_ctx* c, atom* A, uint32_t nA, uint32_t depth) {
-  for (uint32_t i = 0; i < nA && !c->err; ++i) {
-    atom* Ai = (atom*)malloc(sizeof(atom) * (nA - i > 1 ? nA - i - 1 : 1));
-    uint32_t nAi = 0;
-    if (!Ai) { c->err = -1; return; }
-    c->prefix[depth] = A[i].item;
-    for (uint32_t j = i + 1; j < nA; ++j) {
-      uint32_t cap = A[i].n < A[j].n ? A[i].n : A[j].n;
-      uint32_t* buf = (uint32_t*)malloc(sizeof(uint32_t) * (cap ? cap : 1));
-      if (!buf) { c->err = -1; break; }
-      uint32_t n = intersect(A[i].tids, A[i].n, A[j].tids, A[j].n, buf);
-      if (n >= c->minsup) {
-        Ai[nAi].item = A[j].item; Ai[nAi].n = n; Ai[nAi].tids = buf; ++nAi;
-        c->prefix[depth + 1] = A[j].item;
-        if (res_add(c->out, c->prefix, depth + 2, n) != 0) { c->err = -1; break; }
-        if (c->limit && c->out->n_sets > c->limit) { c->err = 1; break; }
-      } else {
-        free(buf);
-      }
-    }
-    if (!c->err) eclat_rec(c, Ai, nAi, depth + 1);
-    for (uint32_t k = 0; k < nAi; ++k) free(Ai[k].tids);
-    free(Ai);
-  }
+  for (uint32_t i = 0; i < nA && !c->err; ++i) eclat_class(c, A, nA, i, depth);
 }
 
 /* Eclat-DFS(D, minsupp, F) that gives up once F holds more than `limit`
@@ -299,6 +311,96 @@ static int eclat_limited(const uint32_t* off, const uint32_t* items, uint32_t D,
 int oracle_eclat(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t minsup,
                  or_result** out) {
   return eclat_limited(off, items, D, N, minsup, 0, out);
+}
+
+/* O1 on several threads: the top-level classes are claimed one at a time
+ * (lowest unclaimed atom first) under a mutex; every thread runs the same
+ * eclat_class on its own output and prefix buffer. */
+typedef struct {
+  atom* A;
+  uint32_t nA, minsup, N;
+  uint32_t next;
+  pthread_mutex_t mu;
+  int err;
+} mt_shared;
+
+typedef struct {
+  mt_shared* sh;
+  or_result* out;
+  int err;
+} mt_worker;
+
+static void* mt_main(void* arg) {
+  mt_worker* w = (mt_worker*)arg;
+  mt_shared* sh = w->sh;
+  uint32_t* prefix = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)sh->N + 2));
+  w->out = res_new();
+  if (!prefix || !w->out) { free(prefix); w->err = -1; return NULL; }
+  eclat_ctx c = {sh->minsup, prefix, w->out, 0, 0};
+  for (;;) {
+    pthread_mutex_lock(&sh->mu);
+    const uint32_t i = sh->err ? sh->nA : sh->next++;
+    pthread_mutex_unlock(&sh->mu);
+    if (i >= sh->nA) break;
+    eclat_class(&c, sh->A, sh->nA, i, 0);
+    if (c.err) {
+      pthread_mutex_lock(&sh->mu);
+      sh->err = c.err;
+      pthread_mutex_unlock(&sh->mu);
+      break;
+    }
+  }
+  w->err = c.err;
+  free(prefix);
+  return NULL;
+}
+
+int oracle_eclat_mt(const uint32_t* off, const uint32_t* items, uint32_t D, uint32_t N, uint32_t minsup,
+                    uint32_t n_threads, or_result** out) {
+  *out = NULL;
+  if (minsup == 0) return -3;
+  if (n_threads == 0) n_threads = 1;
+  tidlists t;
+  int rc = tl_build(&t, off, items, D, N);
+  if (rc != 0) { tl_free(&t); return rc; }
+  or_result* r = res_new();
+  atom* A = (atom*)malloc(sizeof(atom) * (N ? N : 1));
+  mt_worker* ws = (mt_worker*)calloc(n_threads, sizeof(mt_worker));
+  pthread_t* th = (pthread_t*)calloc(n_threads, sizeof(pthread_t));
+  if (!r || !A || !ws || !th) { tl_free(&t); oracle_result_free(r); free(A); free(ws); free(th); return -1; }
+  uint32_t nA = 0;
+  for (uint32_t it = 0; it < N && rc == 0; ++it) {
+    uint32_t n = (uint32_t)(t.off[it + 1] - t.off[it]);
+    if (n >= minsup) {
+      A[nA].item = it; A[nA].n = n; A[nA].tids = t.tids + t.off[it]; ++nA;
+      if (res_add(r, &it, 1, n) != 0) rc = -1;
+    }
+  }
+  mt_shared sh;
+  sh.A = A; sh.nA = nA; sh.minsup = minsup; sh.N = N; sh.next = 0; sh.err = 0;
+  pthread_mutex_init(&sh.mu, NULL);
+  uint32_t started = 0;
+  if (rc == 0)
+    for (; started < n_threads; ++started) {
+      ws[started].sh = &sh;
+      if (pthread_create(&th[started], NULL, mt_main, &ws[started]) != 0) break;
+    }
+  if (rc == 0 && started == 0) rc = -1;
+  for (uint32_t k = 0; k < started; ++k) pthread_join(th[k], NULL);
+  for (uint32_t k = 0; k < started && rc == 0; ++k) {
+    if (ws[k].err) { rc = ws[k].err; break; }
+    const or_result* o = ws[k].out;
+    for (uint64_t s = 0; s < o->n_sets && rc == 0; ++s)
+      if (res_add(r, o->set_items + o->set_offsets[s], (uint32_t)(o->set_offsets[s + 1] - o->set_offsets[s]),
+                  o->supports[s]) != 0)
+        rc = -1;
+  }
+  for (uint32_t k = 0; k < n_threads; ++k) oracle_result_free(ws[k].out);
+  pthread_mutex_destroy(&sh.mu);
+  free(A); free(ws); free(th); tl_free(&t);
+  if (rc != 0) { oracle_result_free(r); return rc; }
+  *out = r;
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -447,3 +447,21 @@ def test_extension_supports_closed_forms():
         oracle.extension_supports(off2, items2, 5, [], [1])
     with pytest.raises(ValueError):
         oracle.extension_supports(off2, items2, 5, [1], [5])
+
+
+# ---------------------------------------------------------------- threaded driver
+
+@pytest.mark.parametrize("threads", [1, 2, 5, 64])
+def test_threaded_eclat_equals_sequential(threads):
+    """The threaded driver runs the same recursion per one-item class: identical canonical output,
+    also with more threads than classes."""
+    for name, D in (("tiny", 4000), ("dense_deep", 3000)):
+        w = synth.make_workload(name, D=D)
+        ms = synth.abs_minsup(w["rel_minsup"], D)
+        a = oracle.eclat(w["offsets"], w["items"], w["N"], ms)
+        b = oracle.eclat_mt(w["offsets"], w["items"], w["N"], ms, threads)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    rng = np.random.default_rng(threads)
+    txs = [list(rng.choice(15, size=rng.integers(0, 8), replace=False)) for _ in range(200)]
+    off, items = csr(txs)
+    assert as_dict(oracle.eclat_mt(off, items, 15, 2, threads)) == brute_dict(txs, 15, 2)
