@@ -79,7 +79,7 @@ typedef struct {
 } fim_mine_stats;
 
 /* Traversal of the persistent DFS (fim_mine_opts.dfs_mode). */
-enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3 };
+enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3, FIM_DFS_WARP = 4 };
 
 /* Level-2 pair counts (fim_mine_opts.pair_kernel): FIM_PAIR_CORES: AND + popcount on the integer
  * pipes (8-word carry-save adder tree); FIM_PAIR_TENSOR: the 0/1 rows widened to 4-bit values
@@ -102,8 +102,12 @@ typedef struct {
                                   words when it has at most 2,048 of them (small CTAs, several per
                                   SM), dense in its stack slot otherwise; rows of at most 65,535
                                   16-byte words, no donation (else as NODES); FIM_DFS_AUTO (2, the
-                                  default): frames when rows are at most 2,048 words (8 KB), else
-                                  sparse nodes                                                     */
+                                  default): rows of at most 2,048 words (8 KB): the warp DFS when
+                                  rows are at most 512 words and at least 1,024 rows are frequent,
+                                  else frames; wider rows: sparse nodes; FIM_DFS_WARP (4): one warp
+                                  per two-item class, the
+                                  prefix in its registers, no CTA-wide barrier; rows of at most 512
+                                  words, no donation (else as SPARSE)                              */
   uint32_t threads_per_cta;    /* persistent DFS CTA size, 128/256/512; 0 = node modes: the one with
                                   the most CTAs per SM (then warps), frames: the most warps        */
   uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece, 1/2/4/8; 0 = 8 for the

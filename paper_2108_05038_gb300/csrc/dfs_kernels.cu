@@ -1558,6 +1558,252 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
 #undef fr_tab
 }
 
+// ---------------------------------------------------------------------------
+// Warp DFS (short rows): one warp walks one two-item class at a time.
+//
+// For rows of at most 32 * WPL words a whole prefix fits in the registers of one
+// warp (lane l holds words l, l + 32, ...), so a class node needs no CTA-wide
+// barrier: the warp ANDs the prefix with the node's extension row, counts every
+// candidate against it (G candidates per round, their loads in flight
+// together, row words read only where the prefix word is nonzero), and writes
+// the survivors and their records.  The same Eclat-DFS-Computation recursion as
+// the CTA kernels (App. B.3.2), with the per-warp stack in the arena: slot s
+// holds the prefix of the frame at depth s + 1 and the survivor list (frow
+// indices and supports) its count produced.
+
+constexpr uint32_t kWarpDfsThreads = 256;  // 8 warps per CTA
+
+__host__ __device__ inline uint64_t warp_slot_words(uint32_t stride, uint32_t n1) {
+  return (uint64_t)stride + 2ull * (((uint64_t)n1 + 3) & ~3ull);
+}
+
+template <int WPL, int G>
+__global__ void __launch_bounds__(kWarpDfsThreads) k_dfs_warp(const DfsArgs A) {
+  const DfsLaunch& p = A.p;
+  if (p.cta_time && threadIdx.x == 0) p.cta_time[2 * blockIdx.x] = global_ns();
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t wpw = 2 * (A.max_len + 1) + 2 * (p.maxd + 2);  // shared words per warp
+  uint32_t* path = smem + wib * wpw;      // ids of the current prefix, in path order
+  uint32_t* xs = path + A.max_len + 1;    // the same ids ascending
+  uint32_t* f_cur = xs + A.max_len + 1;   // next survivor to expand, per frame depth
+  uint32_t* f_n = f_cur + p.maxd + 2;     // survivors, per frame depth
+  const uint64_t slot_words = warp_slot_words(p.stride, p.n1);
+  const uint64_t list_off = p.stride, supp_off = p.stride + (((uint64_t)p.n1 + 3) & ~3ull);
+  uint32_t* const arena =
+      p.arena + (size_t)blockIdx.x * p.arena_cta_words + (size_t)wib * (p.maxd + 1) * slot_words;
+  const uint32_t nwords = p.stride;  // row words (a multiple of 32)
+  unsigned long long st_inter = 0, st_nodes = 0, st_frames = 0;
+
+  // ids of path[0..len) ascending into xs (the ids are distinct)
+  auto sort_path = [&](uint32_t len) {
+    __syncwarp();
+    for (uint32_t q = lane; q < len; q += 32) {
+      const uint32_t v = path[q];
+      uint32_t r = 0;
+      for (uint32_t t = 0; t < len; ++t) r += path[t] < v;
+      xs[r] = v;
+    }
+    __syncwarp();
+  };
+
+  // counts cand[0..nc) against the prefix q (prefix ids xs[0..xlen)), writes the survivors to slot
+  // `so` (frow index, support), one record per survivor; returns the survivor count
+  auto count_node = [&](const uint32_t (&q)[WPL], const uint32_t* cand, uint32_t nc, uint32_t so, uint32_t xlen,
+                        unsigned long long& cls_sets) -> uint32_t {
+    uint32_t* lo = arena + (size_t)so * slot_words + list_off;
+    uint32_t* so_supp = arena + (size_t)so * slot_words + supp_off;
+    uint32_t nout = 0;
+    for (uint32_t k0 = 0; k0 < nc; k0 += G) {
+      uint32_t c[G], row[G], s[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        c[g] = k0 + g < nc ? cand[k0 + g] : 0xffffffffu;
+        row[g] = c[g] != 0xffffffffu ? __ldg(p.frows + c[g]) : 0u;
+        s[g] = 0;
+      }
+      uint32_t wv[G][WPL];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) {
+          const uint32_t j = (uint32_t)w * 32 + lane;
+          wv[g][w] = (j < nwords && q[w] && c[g] != 0xffffffffu) ? __ldg(p.bits + (size_t)row[g] * p.stride + j) : 0u;
+        }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) s[g] += __popc(q[w] & wv[g][w]);
+        s[g] = __reduce_add_sync(0xffffffffu, s[g]);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (c[g] != 0xffffffffu && s[g] >= p.minsup) {
+          if (lane == 0) {
+            lo[nout] = c[g];
+            so_supp[nout] = s[g];
+          }
+          ++nout;
+        }
+    }
+    st_inter += nc;
+    ++st_nodes;
+    if (nout == 0) return 0;
+    __syncwarp();  // the list written by lane 0 is read by every lane below
+    unsigned long long base = 0;
+    if (lane == 0) {
+      const unsigned long long sets = nout, items = (unsigned long long)nout * (xlen + 1);
+      base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+      atomicAdd(&p.ctrl->sets_total, sets);
+      atomicAdd(&p.ctrl->items_total, items);
+      atomicMax(&p.ctrl->max_len, xlen + 1);
+      const unsigned long long after = (base >> 32) + sets;
+      if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    cls_sets += nout;
+    if (p.out_off) {
+      for (uint32_t o = 0; o < nout; ++o) {
+        const uint32_t v = __ldg(p.rank_item + __ldg(p.frows + lo[o]));
+        const uint64_t rec = (base >> 32) + o;
+        const uint64_t it0 = (base & 0xffffffffull) + (uint64_t)o * (xlen + 1);
+        if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
+          uint32_t pos = 0;  // place of v among the prefix ids
+          for (uint32_t q0 = 0; q0 < xlen; q0 += 32)
+            pos += __popc(__ballot_sync(0xffffffffu, q0 + lane < xlen && xs[q0 + lane] < v));
+          for (uint32_t t = lane; t <= xlen; t += 32)
+            p.out_items[it0 + t] = t < pos ? xs[t] : (t == pos ? v : xs[t - 1]);
+          if (lane == 0) {
+            p.out_off[rec] = it0;
+            p.out_supp[rec] = so_supp[o];
+          }
+        } else if (lane == 0) {
+          atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
+        }
+      }
+    }
+    return nout;
+  };
+
+  for (;;) {
+    // ---------------- acquire a two-item class ----------------
+    uint32_t e = 0xffffffffu;
+    if (lane == 0) {
+      bool stop = (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED) != 0;
+      if (!stop && p.max_sets && *(volatile unsigned long long*)&p.ctrl->sets_total > p.max_sets) {
+        atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        stop = true;
+      }
+      if (!stop) {
+        e = atomicAdd(&p.ctrl->queue_head, 1u);
+        if (e >= p.ctrl->n_entries) e = 0xffffffffu;
+      }
+    }
+    e = __shfl_sync(0xffffffffu, e, 0);
+    if (e == 0xffffffffu) break;
+    const uint2 en = p.entries[e];
+    const uint32_t i = en.x, m = en.y, cls = en.x;
+    const uint32_t base = p.soff[i];
+    const uint32_t si = p.sitems[base + m];
+    const uint32_t r1 = p.frows[i], r2 = p.frows[si];
+    const uint32_t nc = p.scnt[i] - m - 1;
+    unsigned long long cls_sets = 0, cls_work = 0;
+    if (lane == 0) {
+      path[0] = p.rank_item[r1];
+      path[1] = p.rank_item[r2];
+    }
+    sort_path(2);
+
+    // root node X = {i, s_m}: prefix t(i) & t(s_m) in registers, candidates = the later survivors of i
+    uint32_t q[WPL];
+#pragma unroll
+    for (int w = 0; w < WPL; ++w) {
+      const uint32_t j = (uint32_t)w * 32 + lane;
+      q[w] = j < nwords ? __ldg(p.bits + (size_t)r1 * p.stride + j) & __ldg(p.bits + (size_t)r2 * p.stride + j) : 0u;
+    }
+    cls_work += nc;
+    uint32_t n = count_node(q, p.sitems + base + m + 1, nc, 0, 2, cls_sets);
+    int32_t depth = 0;
+    if (n >= 2) {  // the root becomes the frame at depth 1 (slot 0)
+#pragma unroll
+      for (int w = 0; w < WPL; ++w) {
+        const uint32_t j = (uint32_t)w * 32 + lane;
+        if (j < nwords) arena[j] = q[w];
+      }
+      ++st_frames;
+      if (lane == 0) {
+        f_n[1] = n;
+        f_cur[1] = 0;
+      }
+      depth = 1;
+    }
+    uint32_t since_poll = 0;
+    while (depth >= 1) {
+      __syncwarp();
+      const uint32_t k = f_cur[depth], nf = f_n[depth];
+      if (k + 1 >= nf) {  // the last survivor has no later candidates
+        --depth;
+        continue;
+      }
+      if (++since_poll == 8) {
+        since_poll = 0;
+        if (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED) break;
+      }
+      __syncwarp();
+      if (lane == 0) f_cur[depth] = k + 1;
+      uint32_t* fs = arena + (size_t)(depth - 1) * slot_words;
+      const uint32_t ce = fs[list_off + k];
+      const uint32_t re = __ldg(p.frows + ce);
+      const uint32_t xlen = (uint32_t)depth + 1;  // prefix length of the frame; the child has xlen + 1
+      if (lane == 0) path[xlen] = p.rank_item[re];
+      sort_path(xlen + 1);
+#pragma unroll
+      for (int w = 0; w < WPL; ++w) {
+        const uint32_t j = (uint32_t)w * 32 + lane;
+        q[w] = j < nwords ? fs[j] & __ldg(p.bits + (size_t)re * p.stride + j) : 0u;
+      }
+      const uint32_t ncc = nf - k - 1;
+      cls_work += ncc;
+      if ((uint32_t)depth > p.maxd) {  // no slot for the child's survivors (cannot happen: frames stop at maxd)
+        if (lane == 0) atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+        break;
+      }
+      const uint32_t n2 = count_node(q, fs + list_off + k + 1, ncc, (uint32_t)depth, xlen + 1, cls_sets);
+      if (n2 >= 2) {
+        if ((uint32_t)depth + 1 > p.maxd) {  // the stack is too shallow: the run repeats with a deeper one
+          if (lane == 0) atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+          continue;
+        }
+        uint32_t* cs = arena + (size_t)depth * slot_words;
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) {
+          const uint32_t j = (uint32_t)w * 32 + lane;
+          if (j < nwords) cs[j] = q[w];
+        }
+        ++st_frames;
+        ++depth;
+        if (lane == 0) {
+          f_n[depth] = n2;
+          f_cur[depth] = 0;
+        }
+      }
+    }
+    if (lane == 0) {
+      if (p.class_sets && cls_sets) atomicAdd(&p.class_sets[cls], cls_sets);
+      if (p.class_work && cls_work) atomicAdd(&p.class_work[cls], cls_work);
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&p.ctrl->n_intersections, st_inter);
+    atomicAdd(&p.ctrl->n_nodes, st_nodes);
+    atomicAdd(&p.ctrl->n_frames, st_frames);
+  }
+  if (p.cta_time) {
+    __syncthreads();
+    if (threadIdx.x == 0) p.cta_time[2 * blockIdx.x + 1] = global_ns();
+  }
+}
+
 // Raise a kernel's dynamic shared-memory limit to the device maximum once
 // (launches then pass their own size).  Setting it per launch to the launch's
 // size would race between threads mining concurrently.
@@ -1659,6 +1905,42 @@ cudaError_t occ_sparse_t(uint32_t threads, size_t smem, int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs_sparse<VEC>, (int)threads, smem);
 }
 
+template <int WPL, int G>
+cudaError_t launch_warp_t(const DfsArgs& a, uint32_t grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_warp<WPL, G>));
+  if (e != cudaSuccess) return e;
+  k_dfs_warp<WPL, G><<<grid, kWarpDfsThreads, smem, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// words per lane: the smallest of 1, 2, 4, 8, 16 that covers the row; candidates per round so that
+// about 8 to 16 loads per lane are in flight
+cudaError_t launch_warp(const DfsArgs& a, uint32_t grid, size_t smem, cudaStream_t st) {
+  const uint32_t wpl = a.p.stride / 32;
+  if (wpl <= 1) return launch_warp_t<1, 8>(a, grid, smem, st);
+  if (wpl <= 2) return launch_warp_t<2, 8>(a, grid, smem, st);
+  if (wpl <= 4) return launch_warp_t<4, 4>(a, grid, smem, st);
+  if (wpl <= 8) return launch_warp_t<8, 2>(a, grid, smem, st);
+  return launch_warp_t<16, 1>(a, grid, smem, st);
+}
+
+template <int WPL, int G>
+cudaError_t occ_warp_t(size_t smem, int* out) {
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_dfs_warp<WPL, G>));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dfs_warp<WPL, G>, (int)kWarpDfsThreads, smem);
+}
+
+cudaError_t occ_warp(uint32_t stride, size_t smem, int* out) {
+  const uint32_t wpl = stride / 32;
+  if (wpl <= 1) return occ_warp_t<1, 8>(smem, out);
+  if (wpl <= 2) return occ_warp_t<2, 8>(smem, out);
+  if (wpl <= 4) return occ_warp_t<4, 4>(smem, out);
+  if (wpl <= 8) return occ_warp_t<8, 2>(smem, out);
+  return occ_warp_t<16, 1>(smem, out);
+}
+
 }  // namespace
 
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
@@ -1681,6 +1963,8 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
 uint32_t dfs_sparse_cap(uint32_t stride) { return std::min<uint32_t>(kSparseCap, std::max<uint32_t>(32, stride / 4)); }
 
 size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool prefix_in_smem, uint32_t mode) {
+  if (mode == 4)  // per warp: path ids, sorted ids, frame cursors and sizes
+    return (size_t)(kWarpDfsThreads / 32) * (2ull * (max_len + 1) + 2ull * (maxd + 2)) * sizeof(uint32_t);
   if (mode == 3) {  // listed prefix: values (16 B) + indices (2 B) per entry
     const size_t cap = dfs_sparse_cap(stride);
     return (4ull * cap + kCandBatch + 2ull * (maxd + 1) + 3ull * (max_len + 1) + cap / 2 + 1) * sizeof(uint32_t);
@@ -1692,11 +1976,12 @@ size_t dfs_smem_bytes(uint32_t stride, uint32_t max_len, uint32_t maxd, bool pre
 }
 
 bool dfs_prefix_fits(uint32_t stride, size_t smem_optin, uint32_t max_len, uint32_t maxd, uint32_t mode) {
-  if (mode == 3) return false;  // the sparse node mode never holds a dense prefix in shared memory
+  if (mode == 3 || mode == 4) return false;  // sparse nodes: listed prefixes; warp DFS: prefixes in registers
   return dfs_smem_bytes(stride, max_len, maxd, true, mode) + sizeof(Ctl) + sizeof(FrameCtl) + 33 * 4 + 512 <= smem_optin;
 }
 
 uint64_t dfs_arena_cta_words(uint32_t stride, uint32_t n1, uint32_t maxd, uint32_t mode) {
+  if (mode == 4) return (uint64_t)(kWarpDfsThreads / 32) * (maxd + 1) * warp_slot_words(stride, n1);
   if (mode == 1) return frames_root_words(n1) + frames_depth_words(stride, n1) * (maxd + 1);
   return dfs_arena_depth_words(stride, n1) * (maxd + 1);
 }
@@ -1732,6 +2017,7 @@ cudaError_t dfs_max_ctas_per_sm(uint32_t threads, uint32_t vec, size_t smem, boo
 
 static cudaError_t dfs_max_ctas_per_sm_query(uint32_t threads, uint32_t vec, size_t smem, bool prefix_in_smem,
                                              uint32_t mode, int* out) {
+  if (mode == 4) return occ_warp(vec, smem, out);  // vec carries the row stride for the warp DFS
   if (mode == 3) {
     switch (vec) {
       case 1: return occ_sparse_t<1>(threads, smem, out);
@@ -1788,6 +2074,7 @@ cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint
   a.nseg = (a.stride4 + segw4 - 1) / segw4;
   a.max_len = max_len;
   a.cap = dfs_sparse_cap(p.stride);
+  if (mode == 4) return launch_warp(a, grid, smem, st);
   if (mode == 3) return launch_sparse_vec(a, grid, threads, vec, smem, st);
   if (mode == 1) {
     if (prefix_in_smem) return launch_frames_vec<true>(a, grid, threads, vec, smem, st);

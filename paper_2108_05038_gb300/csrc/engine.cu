@@ -31,9 +31,17 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // traversal: frame passes pay off on short rows (fewer dependent steps per intersection), node
   // expansion with sparse prefixes on long ones
   // (16-bit word indices: listed prefixes need rows of at most 65,535 16-byte words)
+  // (warp DFS: the prefix in the registers of one warp, rows of at most 512 words)
   const bool list_ok = in.stride / 4 <= 65535;
-  if (cfg.mode == 2) ep->mode = in.stride <= 2048 ? 1u : (list_ok && !cfg.donate ? 3u : 0u);
+  const bool warp_ok = in.stride <= 512 && !cfg.donate;
+  // automatic: short rows with many frequent rows (many classes, throughput bound) take the warp DFS
+  // (large_sparse's 1% sample: 2.38 ms against 3.64 ms in frame passes); short rows with few rows,
+  // where the largest class's chain of dependent nodes sets the time, take frame passes, which
+  // spread one frame over a whole CTA (sparse_mid's sample: 45 µs against 61 µs)
+  if (cfg.mode == 2)
+    ep->mode = in.stride <= 2048 ? (warp_ok && n1 >= 1024 ? 4u : 1u) : (list_ok && !cfg.donate ? 3u : 0u);
   else if (cfg.mode == 3) ep->mode = list_ok && !cfg.donate ? 3u : 0u;
+  else if (cfg.mode == 4) ep->mode = warp_ok ? 4u : (list_ok && !cfg.donate ? 3u : 0u);
   else ep->mode = cfg.mode == 1 ? 1u : 0u;
   ep->donate = ep->mode == 0 ? cfg.donate : 0u;  // only dense node expansion donates
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
@@ -94,7 +102,10 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full, ep->mode);
   ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem, ep->mode);
   int occ = 0;
-  if (cfg.threads == 0) {
+  if (ep->mode == 4) {  // warp DFS: CTAs of 8 warps; its occupancy query takes the row stride
+    ep->threads = 256;
+    FIM_CUDA(dfs_max_ctas_per_sm(256, in.stride, ep->smem, false, 4, &occ));
+  } else if (cfg.threads == 0) {
     // The DFS is latency bound.  Node expansion runs one class node per CTA with CTA-wide barriers
     // between its steps, so more CTAs per SM (independent nodes in flight) beat bigger CTAs: the
     // most CTAs per SM, then the most warps.  Frame passes spread one pass over the whole CTA: the

@@ -31,7 +31,8 @@ namespace fim {
 namespace {
 
 // launch shapes tried by the autotuner: CTA size x 16-byte loads per lane x
-// CTAs per SM (0 = as many as fit) x donation
+// CTAs per SM (0 = as many as fit) x donation x DFS traversal (the warp DFS runs
+// as the sparse node mode on rows wider than 512 words)
 struct Shape {
   uint32_t threads, vec, cps, donate, mode;
 };
@@ -40,7 +41,7 @@ const Shape kShapes[] = {
     {512, 4, 0, 0, 0}, {512, 8, 0, 0, 0}, {256, 4, 0, 1, 0}, {512, 4, 0, 1, 0},
     {512, 2, 0, 0, 0}, {128, 2, 0, 0, 1}, {128, 4, 0, 0, 1}, {256, 2, 0, 0, 1}, {256, 4, 0, 0, 1},
     {256, 8, 0, 0, 1}, {512, 4, 0, 0, 1}, {512, 8, 0, 0, 1}, {128, 4, 0, 0, 3}, {128, 8, 0, 0, 3},
-    {256, 4, 0, 0, 3}, {256, 8, 0, 0, 3},
+    {256, 4, 0, 0, 3}, {256, 8, 0, 0, 3}, {256, 4, 0, 0, 4},
 };
 
 struct TuneKey {

@@ -77,7 +77,7 @@ def test_random_tiny_vs_bruteforce(seed):
     for minsup in sorted({1, 2, max(1, D // 7), max(1, D // 2)}):
         want = odict(oracle.bruteforce(off, items, N, minsup))
         got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64,
-                       dfs_mode=(0, 1, 3)[(seed // 2) % 3]).as_dict()
+                       dfs_mode=(0, 1, 3, 4)[(seed // 2) % 4]).as_dict()
         assert_same(got, want)
 
 
@@ -91,7 +91,8 @@ def test_ragged_D(D):
     assert_same(gpu_mine(off, items, 12, minsup).as_dict(), odict(oracle.eclat(off, items, 12, minsup)))
 
 
-@pytest.mark.parametrize("k,mode,depth", [(11, 0, 0), (16, 0, 8), (11, 1, 4), (16, 1, 0), (11, 3, 0), (16, 3, 4)])
+@pytest.mark.parametrize("k,mode,depth", [(11, 0, 0), (16, 0, 8), (11, 1, 4), (16, 1, 0), (11, 3, 0), (16, 3, 4),
+                                          (11, 4, 0), (16, 4, 4)])
 def test_identical_transactions_closed_form(k, mode, depth):
     """2^k - 1 itemsets of support D; with a first DFS stack of 4 or 8 the depth of 9 or 14 forces the
     regrown retry, with 0 the stack has the full depth at once."""
@@ -101,7 +102,7 @@ def test_identical_transactions_closed_form(k, mode, depth):
     assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_single_and_empty_transactions(mode):
     """One transaction of 5 items: every non-empty subset (31) with support 1; only empty transactions:
     nothing is frequent (no item has support); one item in every transaction: only that singleton."""
@@ -173,7 +174,7 @@ def test_invalid_device_offsets_rejected_before_reading_items(offsets, why):
 
 # ---------------------------------------------------------------- named workloads
 
-@pytest.mark.parametrize("name,mode", [("tiny", 0), ("dense_deep", 0), ("dense_exact37", 0), ("tiny", 1),
+@pytest.mark.parametrize("name,mode", [("tiny", 0), ("dense_deep", 0), ("dense_exact37", 0), ("tiny", 1), ("tiny", 4),
                                        ("dense_deep", 1), ("tiny", 3), ("dense_deep", 3)])
 def test_workload_full_size_exact(name, mode):
     w = synth.make_workload(name)
@@ -262,7 +263,7 @@ def test_work_counters_match_output_and_modes():
     rank = np.zeros(w["N"], dtype=np.int64)
     rank[order] = np.arange(len(order))
     I, Cn, M = bench.bitmap_work(so, si, rank)
-    for mode in (0, 1, 3):
+    for mode in (0, 1, 3, 4):
         st = gpu_mine(w["offsets"], w["items"], w["N"], ms, dfs_mode=mode).stats
         assert st["n_intersections"] == I
         rb = (30000 + 63) // 64 * 8
@@ -298,7 +299,7 @@ def test_fixed_capacity_overflow_then_retry():
     assert_same(got, want)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_itemset_limit_aborts_early(mode):
     """max_itemsets stops the mine once the output passes it (FIM_ERR_OUTPUT_OVERFLOW); the db stays usable."""
     off, items = csr([list(range(20))] * 50 + [[20]])
@@ -311,7 +312,7 @@ def test_itemset_limit_aborts_early(mode):
     assert len(got) == 2 ** 20 - 1
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_output_regrowth_reuses_pair_counts(mode):
     """2^20 - 1 itemsets of length up to 20 overflow the first output buffer and a 3-deep first DFS
     stack: the repeated runs skip the pair kernel (its counts stay in the workspace) and still give
@@ -326,7 +327,7 @@ def test_output_regrowth_reuses_pair_counts(mode):
     assert st["ms_pair_kernel"] > 0 and st["ms_device_total"] >= st["ms_dfs_kernel"] > 0
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_cta_busy_times_are_consistent(mode):
     """collect_times records every persistent CTA's resident time: 0 < mean <= max <= the kernel's time."""
     w = synth.make_workload("dense_deep", D=20_000)
@@ -369,7 +370,7 @@ def _literal_class_work(txs, N, minsup):
     return work
 
 
-@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1), (4, 3), (5, 3)])
+@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1), (4, 3), (5, 3), (6, 4), (7, 4)])
 def test_class_work_matches_literal_eclat(seed, mode):
     """class_work_out: intersections per one-row class equal a literal Eclat's count, and sum to the total."""
     rng = np.random.default_rng(700 + seed)
@@ -516,3 +517,41 @@ def test_large_sparse_certificate():
     code, bad = oracle.check(w["offsets"], w["items"], w["N"], w["minsup"], res.set_offsets, res.set_items,
                              res.supports, stride=20011)
     assert code == 0, (oracle.CHECK_CODES[code], bad)
+
+
+# ---------------------------------------------------------------- warp DFS (rows of at most 512 words)
+
+@pytest.mark.parametrize("name,D,ms_scale", [("tiny", 10000, 1.0), ("sparse_mid", 16000, 1.0), ("dense_deep", 16000, 1.0),
+                                             ("large_sparse", 10000, 1.0), ("sparse_mid", 1000, 1.0),
+                                             ("dense_deep", 738, 1.0)])
+def test_warp_dfs_workload_laws(name, D, ms_scale):
+    """Every row-width class of the warp DFS (1, 2, 4, 8, 16 words per lane) on the workloads' laws at
+    sample-like sizes, against the oracle."""
+    w = synth.make_workload(name, D=D)
+    ms = max(2, int(synth.abs_minsup(w["rel_minsup"], D) * ms_scale))
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    res = gpu_mine(w["offsets"], w["items"], w["N"], ms, dfs_mode=4)
+    assert_same(res.as_dict(), want)
+    st = res.stats
+    assert st["n_frequent"] == len(want)
+
+
+@pytest.mark.parametrize("D", [32, 64, 128, 1000, 2048, 4096, 8192, 16384])
+def test_warp_dfs_words_per_lane(D):
+    """Row widths 32 ... 512 words (D up to 16,384 bits): deep dense classes through the warp stack."""
+    rng = np.random.default_rng(D + 5)
+    N = 14
+    txs = [list(np.nonzero(rng.random(N) < rng.uniform(0.3, 0.9))[0]) for _ in range(D)]
+    off, items = csr(txs)
+    minsup = max(1, D // 8)
+    want = odict(oracle.eclat(off, items, N, minsup))
+    for wb in (32, 64):
+        assert_same(gpu_mine(off, items, N, minsup, word_bits=wb, dfs_mode=4).as_dict(), want)
+
+
+def test_warp_dfs_falls_back_on_wide_rows():
+    """FIM_DFS_WARP on rows wider than 512 words runs the sparse node mode: same output."""
+    w = synth.make_workload("sparse_mid", D=30000)
+    ms = 75
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    assert_same(gpu_mine(w["offsets"], w["items"], w["N"], ms, dfs_mode=4).as_dict(), want)
