@@ -989,14 +989,15 @@ __device__ __forceinline__ uint32_t and_rows_to_list(const uint4* a4, const uint
   return *count;
 }
 
-// shared list <- (listed prefix of a stack slot) & row, zero results dropped
+// shared list <- (listed prefix of a stack slot) & row, zero results dropped; eight entries per lane
+// in flight (large_sparse: 0.5 ms less DFS time than two)
 __device__ __forceinline__ uint32_t list_from_list(const uint16_t* gl, const uint4* gv, uint32_t n,
                                                    const uint4* __restrict__ r4, uint16_t* sidx, uint4* sval,
                                                    uint32_t* count) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) *count = 0;
   __syncthreads();
-  constexpr uint32_t U = 2;
+  constexpr uint32_t U = 8;
   for (uint32_t e0 = warp * 32 * U; e0 < n; e0 += nw * 32 * U) {
     uint32_t w[U];
     uint4 v[U];
@@ -1891,6 +1892,7 @@ cudaError_t launch_sparse_t(const DfsArgs& a, uint32_t grid, uint32_t threads, s
 cudaError_t launch_sparse_vec(const DfsArgs& a, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,
                               cudaStream_t st) {
   switch (vec) {
+    case 16: return launch_sparse_t<16>(a, grid, threads, smem, st);
     case 1: return launch_sparse_t<1>(a, grid, threads, smem, st);
     case 2: return launch_sparse_t<2>(a, grid, threads, smem, st);
     case 8: return launch_sparse_t<8>(a, grid, threads, smem, st);
@@ -2020,6 +2022,7 @@ static cudaError_t dfs_max_ctas_per_sm_query(uint32_t threads, uint32_t vec, siz
   if (mode == 4) return occ_warp(vec, smem, out);  // vec carries the row stride for the warp DFS
   if (mode == 3) {
     switch (vec) {
+      case 16: return occ_sparse_t<16>(threads, smem, out);
       case 1: return occ_sparse_t<1>(threads, smem, out);
       case 2: return occ_sparse_t<2>(threads, smem, out);
       case 8: return occ_sparse_t<8>(threads, smem, out);

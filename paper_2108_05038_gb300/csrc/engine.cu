@@ -14,7 +14,9 @@
 namespace fim {
 
 static uint32_t clamp_threads(uint32_t t) { return (t == 128 || t == 256 || t == 512) ? t : 256u; }
-static uint32_t clamp_vec(uint32_t v) { return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 4u; }
+static uint32_t clamp_vec(uint32_t v, uint32_t mode) {
+  return (v == 1 || v == 2 || v == 4 || v == 8 || (v == 16 && mode == 3)) ? v : 4u;
+}
 static constexpr uint64_t kMaxCap = 0xfffffff0ull;
 
 fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg, EnginePlan* ep) {
@@ -98,13 +100,18 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->maxd_full = std::max<uint32_t>(1, ep->L - 2);
   // loads per lane: listed prefixes of wide rows have long lists, whose pieces take 8 loads per lane
   // (large_sparse: 26 ms against 32 ms with 4); 4 elsewhere
-  ep->vec = cfg.vec ? clamp_vec(cfg.vec) : (ep->mode == 3 && in.stride / 4 >= 4096 ? 8u : 4u);
+  ep->vec = cfg.vec ? clamp_vec(cfg.vec, ep->mode) : (ep->mode == 3 && in.stride / 4 >= 4096 ? 8u : 4u);
   ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full, ep->mode);
   ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem, ep->mode);
   int occ = 0;
   if (ep->mode == 4) {  // warp DFS: CTAs of 8 warps; its occupancy query takes the row stride
     ep->threads = 256;
     FIM_CUDA(dfs_max_ctas_per_sm(256, in.stride, ep->smem, false, 4, &occ));
+  } else if (cfg.threads == 0 && ep->mode == 3 && in.stride / 4 >= 4096) {
+    // sparse nodes on wide rows: 256-thread CTAs (2 per SM), whose listed child prefixes are built with
+    // twice the loads in flight (large_sparse: 24.8 ms against 26.0 ms with 128 threads, 4 per SM)
+    ep->threads = 256;
+    FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
   } else if (cfg.threads == 0) {
     // The DFS is latency bound.  Node expansion runs one class node per CTA with CTA-wide barriers
     // between its steps, so more CTAs per SM (independent nodes in flight) beat bigger CTAs: the
