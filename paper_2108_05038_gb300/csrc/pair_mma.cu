@@ -16,13 +16,13 @@
 // every integer exactly, and items of one tile are added as u32 atomics.
 //
 // Tiles: 128 rows (i) x 256 rows (j) of X, only those that hold pairs i < j.
-// A CTA (one per SM, persistent) walks (tile, K range) items; per item one
-// thread issues TMA loads of 128-byte K slices (128B swizzle) into a 4-stage
-// ring, one thread issues four 128x256x32 MMAs per slice into a 256-column TMEM
-// accumulator, and the four warps read the accumulator back (tcgen05.ld, one
-// TMEM lane quarter per warp) into shared memory (the ring is idle then), from
-// where whole 128-byte row segments are written or added (coalesced) for the
-// pairs i < j.
+// A CTA (one per SM, persistent) walks (tile, K range) items with three roles:
+// one thread issues TMA loads of 128-transaction K slices (128B swizzle) into a
+// 4-stage ring, one thread issues four 128x256x32 MMAs per slice into one of
+// two 256-column TMEM accumulators, and four warps read the other accumulator
+// back (tcgen05.ld, one TMEM lane quarter per warp) through a small transposing
+// staging area and write or add whole 128-byte row segments of C2 (coalesced)
+// for the pairs i < j, so an item's read-back overlaps the next item's MMAs.
 // Every mbarrier wait is bounded by time; on expiry the kernel sets
 // DEV_ERR_TIMEOUT, lets its copies and MMAs in flight finish, frees its TMEM and
 // returns.
@@ -41,13 +41,20 @@ constexpr uint32_t kBN = 256;       // tile rows on the j side (MMA N)
 constexpr uint32_t kBK = 128;       // K bytes per pipeline stage (one 128-byte swizzle row)
 constexpr uint32_t kMmaK = 32;      // K bytes per kind::f8f6f4 MMA
 constexpr uint32_t kStages = 4;
-constexpr uint32_t kThreads = 128;  // four warps: TMA issue (warp 0), MMA issue (warp 1), all four read back
+// six warps: TMA issue (warp 0), MMA issue and TMEM owner (warp 1), read-back (warps 2-5, one TMEM
+// lane quarter each: warp w may access lanes 32 (w mod 4) .. + 31)
+constexpr uint32_t kThreads = 192;
 constexpr uint32_t kABytes = kBM * kBK;
 constexpr uint32_t kBBytes = kBN * kBK;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
-constexpr uint32_t kBarBytes = 8 * (2 * kStages + 1) + 8;  // full[], empty[], acc, TMEM address
-constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kBarBytes;  // + slack for 1024-byte alignment
-constexpr uint32_t kTmemCols = kBN;                          // fp32 accumulator: 128 lanes x 256 columns
+constexpr uint32_t kAccBufs = 2;                     // accumulators: one read back while the next fills
+constexpr uint32_t kTmemCols = kAccBufs * kBN;       // 2 x (128 lanes x 256 fp32 columns) = all of TMEM
+constexpr uint32_t kChunk = 32;                      // columns read back per round
+constexpr uint32_t kSPitch = kChunk + 1;             // staging rows (words), conflict-free transposition
+constexpr uint32_t kStagingBytes = 4 * 32 * kSPitch * 4;  // per read-back warp 32 rows x 33 words
+// full[], empty[], acc_full[], acc_empty[], fin, TMEM address
+constexpr uint32_t kBarBytes = 8 * (2 * kStages + 2 * kAccBufs + 1) + 8;
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kStagingBytes + kBarBytes;  // + align slack
 constexpr uint32_t kMaxStepsPerItem = (1u << 24) / kBK;      // fp32 exact: at most 2^24 bytes of K per item
 constexpr uint64_t kWaitNs = 1000000000ull;                  // bound of every mbarrier wait (1 s)
 // instruction descriptor of kind::f8f6f4: D f32 (bits 4-5 = 1), A and B format in bits 7-9 and 10-12
@@ -58,8 +65,7 @@ __host__ __device__ constexpr uint32_t idesc() {
 }
 constexpr uint32_t kOneE4M3 = 0x38u;  // 1.0: exponent 7 (the bias), mantissa 0
 constexpr uint32_t kOneE2M1 = 0x2u;   // 1.0: exponent 1 (the bias), mantissa 0
-constexpr uint32_t kTPitch = kBN + 1;  // read-back tile in shared memory: u32, padded rows (conflict-free)
-static_assert((size_t)kBM * kTPitch * 4 <= (size_t)kStages * kStageBytes, "read-back tile fits in the ring");
+static_assert(kSmemBytes <= 227u * 1024u, "shared memory per CTA");
 static_assert(kBN % 16 == 0 && kBN <= 256 && kBM == 128, "MMA shape of cta_group::1");
 static_assert(kBK % kMmaK == 0, "whole MMAs per stage");
 
@@ -94,6 +100,10 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   while (!mbar_try(bar, parity))
     if (now_ns() - t0 > kWaitNs) return false;
   return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
@@ -200,21 +210,35 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // the 128-byte swizzle repeats every 1024 bytes
   const uint32_t a_st = base, b_st = base + kStages * kABytes;
-  const uint32_t bars = base + kStages * kStageBytes;
-  const uint32_t acc_bar = bars + 8 * 2 * kStages;
-  const uint32_t tslot = acc_bar + 8;
+  uint32_t* const staging = reinterpret_cast<uint32_t*>(smem_raw + (base + kStages * kStageBytes - raw));
+  const uint32_t bars = base + kStages * kStageBytes + kStagingBytes;
+  auto full = [&](uint32_t s) { return bars + 8 * s; };
+  auto empty = [&](uint32_t s) { return bars + 8 * (kStages + s); };
+  auto acc_full = [&](uint32_t b) { return bars + 8 * (2 * kStages + b); };
+  auto acc_empty = [&](uint32_t b) { return bars + 8 * (2 * kStages + kAccBufs + b); };
+  const uint32_t fin = bars + 8 * (2 * kStages + 2 * kAccBufs);
+  const uint32_t tslot = fin + 8;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile uint32_t* abort_flag = &s_abort;
+  auto abort_now = [&]() {
+    atomicOr(err, DEV_ERR_TIMEOUT);
+    *abort_flag = 1u;
+  };
 
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < kStages; ++s) {
-      mbar_init(bars + 8 * s, 1);              // full[s]: the producer's arrive + the TMA bytes
-      mbar_init(bars + 8 * (kStages + s), 1);  // empty[s]: the MMA commit that consumed stage s
+      mbar_init(full(s), 1);   // the producer's arrive + the TMA bytes
+      mbar_init(empty(s), 1);  // the MMA commit that consumed stage s
     }
-    mbar_init(acc_bar, 1);
+    for (uint32_t b = 0; b < kAccBufs; ++b) {
+      mbar_init(acc_full(b), 1);   // the MMA commit after an item's last slice
+      mbar_init(acc_empty(b), 4);  // one arrive per read-back warp
+    }
+    mbar_init(fin, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -224,115 +248,143 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + (tslot - raw));
 
-  uint32_t issued = 0, consumed = 0;  // ring position of the producer and of the MMA thread
-  uint32_t acc_parity = 0;
+  // item -> (row block bi, column block bj, first K slice, slices); items of one K range are
+  // consecutive, so the CTAs of a wave read the same K slices (L2 reuse)
   const uint32_t n_items = n_tiles * ksplit;
-  for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-    // items of one K range are consecutive, so the CTAs of a wave read the same K slices (L2 reuse)
+  auto decode = [&](uint32_t item, uint32_t& bi, uint32_t& bj, uint32_t& k0, uint32_t& ns) {
     const uint32_t split = item / n_tiles;
-    uint32_t t = item % n_tiles, bi = 0;
+    uint32_t t = item % n_tiles;
+    bi = 0;
     while (t >= nbj - bi / 2) {  // row block bi pairs with the column blocks bj >= bi / 2
       t -= nbj - bi / 2;
       ++bi;
     }
-    const uint32_t bj = bi / 2 + t;
-    const uint32_t k0 = split * steps_per_item;
-    const uint32_t ns = min(nsteps, k0 + steps_per_item) - k0;
+    bj = bi / 2 + t;
+    k0 = split * steps_per_item;
+    ns = min(nsteps, k0 + steps_per_item) - k0;
+  };
 
-    if (warp == 0) {
-      if (lane == 0) {
+  uint32_t issued = 0;  // producer: slices issued (ring position)
+  bool mma_open = false;  // MMA thread: MMAs issued since the last commit that someone waits for
+  if (warp == 0) {
+    if (lane == 0) {
+      for (uint32_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        uint32_t bi, bj, k0, ns;
+        decode(item, bi, bj, k0, ns);
         for (uint32_t s = 0; s < ns; ++s, ++issued) {
           const uint32_t st = issued % kStages;
-          if (issued >= kStages && !mbar_wait(bars + 8 * (kStages + st), ((issued / kStages) - 1) & 1)) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            s_abort = 1;
+          if (issued >= kStages && !mbar_wait(empty(st), ((issued / kStages) - 1) & 1)) {
+            abort_now();
             break;
           }
-          const uint32_t full = bars + 8 * st;
           // transaction bytes = bytes the TMA moves: e2m1 boxes carry 64 packed bytes per row (the gaps of
           // the unpacked shared-memory form are not written)
-          mbar_expect_tx(full, kE2M1 ? kStageBytes / 2 : kStageBytes);
+          mbar_expect_tx(full(st), kE2M1 ? kStageBytes / 2 : kStageBytes);
           const int32_t x = (int32_t)((k0 + s) * kBK);
-          tma_load(a_st + st * kABytes, &xmap, x, (int32_t)(bi * kBM), full);
-          tma_load(b_st + st * kBBytes, &xmap, x, (int32_t)(bj * kBN), full);
-          tma_load(b_st + st * kBBytes + kABytes, &xmap, x, (int32_t)(bj * kBN + kBM), full);
+          tma_load(a_st + st * kABytes, &xmap, x, (int32_t)(bi * kBM), full(st));
+          tma_load(b_st + st * kBBytes, &xmap, x, (int32_t)(bj * kBN), full(st));
+          tma_load(b_st + st * kBBytes + kABytes, &xmap, x, (int32_t)(bj * kBN + kBM), full(st));
         }
       }
-      __syncwarp();
-    } else if (warp == 1) {
-      if (lane == 0) {
-        for (uint32_t s = 0; s < ns; ++s) {
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t consumed = 0, it = 0;
+      for (uint32_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++it) {
+        uint32_t bi, bj, k0, ns;
+        decode(item, bi, bj, k0, ns);
+        const uint32_t b = it & 1;
+        if (it >= kAccBufs && !mbar_wait(acc_empty(b), ((it >> 1) - 1) & 1)) {  // read back, so reusable
+          abort_now();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + b * kBN;
+        bool ok = true;
+        for (uint32_t s = 0; s < ns; ++s, ++consumed) {
           const uint32_t st = consumed % kStages;
-          if (!mbar_wait(bars + 8 * st, (consumed / kStages) & 1)) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            s_abort = 1;
+          if (!mbar_wait(full(st), (consumed / kStages) & 1)) {
+            ok = false;
             break;
           }
-          ++consumed;
           tc_fence_after();
           const uint64_t ad = sw128_desc(a_st + st * kABytes), bd = sw128_desc(b_st + st * kBBytes);
 #pragma unroll
           for (uint32_t kk = 0; kk < kBK / kMmaK; ++kk)  // +32 bytes of K inside the swizzled rows: +2 in 16-byte units
-            mma_f8f6f4(tmem, ad + 2 * kk, bd + 2 * kk, idesc<kE2M1>(), (s | kk) != 0u);
-          mma_commit(bars + 8 * (kStages + st));  // stage st free once these MMAs are done
+            mma_f8f6f4(d, ad + 2 * kk, bd + 2 * kk, idesc<kE2M1>(), (s | kk) != 0u);
+          mma_commit(empty(st));  // stage st free once these MMAs are done
+          mma_open = true;
         }
-        mma_commit(acc_bar);  // accumulator complete (also after an abort: the MMAs issued finish first)
+        mma_commit(acc_full(b));  // accumulator b complete
+        mma_open = false;
+        if (!ok) {
+          abort_now();
+          mma_open = true;  // nobody may wait for acc_full(b) now
+          break;
+        }
       }
-      __syncwarp();
     }
-
-    // every thread takes the same branch below (it holds barriers): all waited successfully, or none goes on
-    const bool ok = __syncthreads_and(mbar_wait(acc_bar, acc_parity)) != 0;
-    acc_parity ^= 1u;
-    tc_fence_after();
-    if (!ok) {
-      atomicOr(err, DEV_ERR_TIMEOUT);
-      s_abort = 1;
-    } else {
-      // TMEM lane = row of the accumulator; the ring is idle (every stage consumed), so it holds the
-      // counts as a padded u32 tile: lane l of warp w writes row 32w + l (banks (l + c) mod 32)
-      uint32_t* T = reinterpret_cast<uint32_t*>(smem_raw + (base - raw));
-      const uint32_t row = warp * 32 + lane;
-      const uint32_t lane_base = tmem + ((warp * 32u) << 16);
-#pragma unroll 1
-      for (uint32_t c0 = 0; c0 < kBN; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(lane_base + c0, r);
-#pragma unroll
-        for (uint32_t c = 0; c < 16; ++c) T[row * kTPitch + c0 + c] = __float2uint_rn(__uint_as_float(r[c]));
+    __syncwarp();
+  } else {
+    // read-back: TMEM lanes -> staging (transposed) -> 128-byte row segments of C2
+    const uint32_t quarter = warp & 3;
+    uint32_t* sw = staging + (warp - 2) * 32 * kSPitch;
+    uint32_t it = 0;
+    for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x, ++it) {
+      uint32_t bi, bj, k0, ns;
+      decode(item, bi, bj, k0, ns);
+      const uint32_t b = it & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), (it >> 1) & 1));
+      if (!ok || *abort_flag) {
+        if (lane == 0 && !ok) abort_now();
+        break;
       }
-      __syncthreads();
-      // row segments of 128 consecutive j per instruction group: thread t takes columns t and t + 128
-      const uint32_t i_end = min(kBM, n1 - bi * kBM);
+      tc_fence_after();
+      const uint32_t row0 = bi * kBM + quarter * 32;
+      const uint32_t taddr = tmem + ((quarter * 32u) << 16) + b * kBN;
 #pragma unroll 1
-      for (uint32_t rr = 0; rr < i_end; ++rr) {
-        const uint32_t i = bi * kBM + rr;
+      for (uint32_t c0 = 0; c0 < kBN; c0 += kChunk) {
+        uint32_t r[16];
+        tmem_ld16(taddr + c0, r);
 #pragma unroll
-        for (uint32_t h = 0; h < kBN / kThreads; ++h) {
-          const uint32_t cc = threadIdx.x + h * kThreads, j = bj * kBN + cc;
-          if (i < j && j < n1) {
-            const uint32_t v = T[rr * kTPitch + cc];
+        for (uint32_t c = 0; c < 16; ++c) sw[lane * kSPitch + c] = __float2uint_rn(__uint_as_float(r[c]));
+        tmem_ld16(taddr + c0 + 16, r);
+#pragma unroll
+        for (uint32_t c = 0; c < 16; ++c) sw[lane * kSPitch + 16 + c] = __float2uint_rn(__uint_as_float(r[c]));
+        __syncwarp();
+        const uint32_t j = bj * kBN + c0 + lane;
+#pragma unroll 4
+        for (uint32_t rr = 0; rr < 32; ++rr) {
+          const uint32_t i = row0 + rr;
+          if (i < j && j < n1) {  // i < j < n1 also bounds i
+            const uint32_t v = sw[rr * kSPitch + lane];
             if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
             else C2[(size_t)i * n1 + j] = v;
           }
         }
+        __syncwarp();
       }
-      // the ring's next writes come from the async proxy (TMA): order these generic accesses first
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(b));
     }
-    tc_fence_before();
-    __syncthreads();
-    if (s_abort) break;
   }
 
-  // copies still in flight after an abort: wait (bounded) for every issued stage not consumed
-  if (threadIdx.x == 0 && s_abort) {
-    for (uint32_t q = consumed; q < issued; ++q) (void)mbar_wait(bars + 8 * (q % kStages), (q / kStages) & 1);
+  // teardown after an abort: the producer waits (bounded) for its last slices in flight, the MMA
+  // thread for its MMAs that nobody waits for
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (uint32_t q = issued > kStages ? issued - kStages : 0; q < issued; ++q)
+      (void)mbar_wait(full(q % kStages), (q / kStages) & 1);
+  }
+  if (warp == 1 && lane == 0 && (mma_open || *abort_flag)) {
+    mma_commit(fin);
+    (void)mbar_wait(fin, 0);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                               : "memory");
 }
 
@@ -380,7 +432,7 @@ double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1) {
     const uint32_t k2 = (nsteps + spi - 1) / spi;
     const uint64_t items = (uint64_t)tiles * k2;
     const uint64_t rounds = (items + num_sms - 1) / num_sms;
-    best = std::min(best, (double)rounds * (spi * step_us + 1.0));
+    best = std::min(best, (double)rounds * (spi + 1) * step_us + 8.0 * step_us);
   }
   return x_bytes / 5e12 * 1e6 + best + 4.0;
 }
@@ -429,16 +481,18 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t
   const uint32_t nbj = (p.n1 + kBN - 1) / kBN;
   const uint32_t tiles = pair_tiles(p.n1);
   const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-element slices
-  // split the K range so that the items fill whole rounds of the SMs; at most 2^24 elements per item
+  // split the K range so that the items fill whole rounds of the SMs; at most 2^24 elements per item.
+  // An item's read-back overlaps the next item's MMAs, so only the last one is exposed: a CTA takes
+  // about rounds x (slices + 1) + 8 slice times
   uint32_t spi = std::min(kMaxStepsPerItem, nsteps);
   double best = 1e300;
   for (uint32_t ks = 1; ks <= 256; ++ks) {
     const uint32_t c = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
-    if (c < 8 && ks > 1) break;  // at least 8 slices per item to repay its read-back
+    if (c < 8 && ks > 1) break;  // at least 8 slices per item to cover a read-back
     const uint32_t k2 = (nsteps + c - 1) / c;
     const uint64_t items = (uint64_t)tiles * k2;
     const uint64_t rounds = (items + num_sms - 1) / num_sms;
-    const double cost = (double)rounds * (c + 6.0);  // read-back of the tile ~ 6 slices
+    const double cost = (double)rounds * (c + 1.0) + 8.0;
     if (cost < best - 1e-9) {
       best = cost;
       spi = c;
