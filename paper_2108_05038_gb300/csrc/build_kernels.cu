@@ -11,12 +11,14 @@ namespace {
 
 constexpr uint32_t kSmemHistMax = 12288;  // items counted in shared memory (48 KB)
 
-// K1: item supports with set semantics.  One thread per transaction; an item
-// counts once per transaction (a repeat is detected by scanning the earlier
-// positions of the same transaction).  Also validates ids and offsets and
-// records the longest transaction (distinct items).  Only items[0, off[D]) is
-// ever read, whatever the offsets: a transaction whose range is reversed or
-// leaves [0, off[D]] is reported and skipped, and so is every transaction when
+// K1: item supports with set semantics.  One warp per transaction: the lanes
+// read 32 consecutive items at a time (coalesced), a lane's item counts unless
+// an earlier position of the same transaction holds the same id (the lowest
+// lane of its __match_any_sync group within the chunk, and no lane of an earlier
+// chunk, compared by shuffles).  Also validates ids and offsets and records the
+// longest transaction (distinct items).  Only items[0, off[D]) is ever read,
+// whatever the offsets: a transaction whose range is reversed or leaves
+// [0, off[D]] is reported and skipped, and so is every transaction when
 // off[0] != 0.  flags = [error bits, longest transaction, off[0], off[D]].
 __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
                              uint32_t N, uint32_t* __restrict__ cnt, uint32_t* flags) {
@@ -26,30 +28,46 @@ __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* _
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) hist[i] = 0;
     __syncthreads();
   }
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t first = off[0], nnz = off[D];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     flags[2] = first;
     flags[3] = nnz;
   }
   uint32_t local_max = 0, local_err = first != 0 ? DEV_ERR_OFFSETS : 0u;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D && first == 0; t += gridDim.x * blockDim.x) {
-    uint32_t b = off[t], e = off[t + 1];
-    if (e < b || e > nnz) { local_err |= DEV_ERR_OFFSETS; continue; }
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < D && first == 0; t += warps) {
+    const uint32_t b = off[t], e = off[t + 1];
+    if (e < b || e > nnz) {
+      local_err |= DEV_ERR_OFFSETS;
+      continue;
+    }
     uint32_t distinct = 0;
-    for (uint32_t k = b; k < e; ++k) {
-      uint32_t it = items[k];
-      if (it >= N) { local_err |= DEV_ERR_ITEM_RANGE; continue; }
-      bool dup = false;
-      for (uint32_t q = b; q < k && !dup; ++q) dup = items[q] == it;
-      if (dup) continue;
-      ++distinct;
-      if (use_smem) atomicAdd(&hist[it], 1u);
-      else atomicAdd(&cnt[it], 1u);
+    for (uint32_t c0 = b; c0 < e; c0 += 32) {
+      const uint32_t k = c0 + lane;
+      const bool in = k < e;
+      const uint32_t it = in ? items[k] : 0xffffffffu;
+      const bool ok = in && it < N;
+      if (in && !ok) local_err |= DEV_ERR_ITEM_RANGE;
+      // repeat within this chunk: a lower lane holds the same id
+      const uint32_t same = __match_any_sync(0xffffffffu, it);
+      bool dup = (same & ((1u << lane) - 1u)) != 0u;
+      // repeat in an earlier chunk of the same transaction
+      for (uint32_t p0 = b; p0 < c0; p0 += 32) {
+        const uint32_t prev = items[p0 + lane];  // p0 + 32 <= c0 < e: always in range
+        for (uint32_t q = 0; q < 32; ++q) dup |= __shfl_sync(0xffffffffu, prev, q) == it;
+      }
+      const bool count = ok && !dup;
+      distinct += __popc(__ballot_sync(0xffffffffu, count));
+      if (count) {
+        if (use_smem) atomicAdd(&hist[it], 1u);
+        else atomicAdd(&cnt[it], 1u);
+      }
     }
     local_max = max(local_max, distinct);
   }
   if (local_err) atomicOr(&flags[0], local_err);
-  if (local_max) atomicMax(&flags[1], local_max);
+  if (lane == 0 && local_max) atomicMax(&flags[1], local_max);
   if (use_smem) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
@@ -130,8 +148,8 @@ cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32
                               uint32_t* flags, cudaStream_t st) {
   const uint32_t threads = 256;
   size_t smem = N <= kSmemHistMax ? (size_t)N * 4 : 0;
-  // with a shared histogram every CTA flushes N counters: keep the grid modest
-  uint32_t grid = grid_for(D, threads, N <= kSmemHistMax ? 152 * 4 : 152 * 32);
+  // one warp per transaction; with a shared histogram every CTA flushes N counters: keep the grid modest
+  uint32_t grid = grid_for((uint64_t)D * 32, threads, N <= kSmemHistMax ? 152 * 4 : 152 * 32);
   k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, flags);
   note_launch();
   return cudaGetLastError();
