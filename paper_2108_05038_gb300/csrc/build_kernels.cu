@@ -76,13 +76,26 @@ __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* _
 }
 
 // K2: scatter transaction bits into the item-major bitmap rows of kept items.
+// A warp takes 32 consecutive transactions (one bitmap word of every row, lane =
+// bit); at each position j the lanes whose j-th item maps to the same row are
+// grouped by __match_any_sync, and one lane ORs the whole group's bits into the
+// word, so a popular item costs one atomic per word and position instead of one
+// per transaction.  The offsets and ids were validated by K1.
 __global__ void k_bitmap_build(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
                                const int32_t* __restrict__ item_rank, uint32_t* __restrict__ bits, uint32_t stride) {
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D; t += gridDim.x * blockDim.x) {
-    const uint32_t bit = 1u << (t & 31), word = t >> 5;
-    for (uint32_t k = off[t]; k < off[t + 1]; ++k) {
-      int32_t r = item_rank[items[k]];
-      if (r >= 0) atomicOr(&bits[(size_t)r * stride + word], bit);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t w0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32u; w0 < D; w0 += warps * 32u) {
+    const uint32_t t = w0 + lane;
+    const uint32_t b = t < D ? off[t] : 0u, e = t < D ? off[t + 1] : 0u;
+    const uint32_t len = e - b;
+    const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
+    uint32_t* const col = bits + (w0 >> 5);
+    for (uint32_t j = 0; j < maxlen; ++j) {
+      const int32_t r = j < len ? item_rank[items[b + j]] : -1;
+      const uint32_t key = r >= 0 ? (uint32_t)r : 0xffffffffu;
+      const uint32_t grp = __match_any_sync(0xffffffffu, key);
+      if (r >= 0 && lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(col + (size_t)r * stride, grp);
     }
   }
 }
@@ -158,7 +171,7 @@ cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32
 cudaError_t launch_bitmap_build(const uint32_t* off, const uint32_t* items, uint32_t D, const int32_t* item_rank,
                                 uint32_t* bits, uint32_t stride, cudaStream_t st) {
   const uint32_t threads = 256;
-  k_bitmap_build<<<grid_for(D, threads), threads, 0, st>>>(off, items, D, item_rank, bits, stride);
+  k_bitmap_build<<<grid_for(D, threads), threads, 0, st>>>(off, items, D, item_rank, bits, stride);  // 32 tx per warp
   note_launch();
   return cudaGetLastError();
 }
