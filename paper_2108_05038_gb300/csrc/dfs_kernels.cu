@@ -1019,8 +1019,9 @@ __device__ __forceinline__ uint32_t list_from_list(const uint16_t* gl, const uin
   return *count;
 }
 
+// at most 256 threads and 80 registers, so that three 256-thread CTAs (or five of 128) fit on an SM
 template <int VEC>
-__global__ void __launch_bounds__(512, 1) k_dfs_sparse(const DfsArgs A) {
+__global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
   const DfsLaunch& p = A.p;
   if (p.cta_time && threadIdx.x == 0) p.cta_time[2 * blockIdx.x] = global_ns();
   extern __shared__ __align__(16) uint32_t smem[];

@@ -98,9 +98,9 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // persistent DFS geometry: itemsets are no longer than the longest transaction
   ep->L = std::max<uint32_t>(3, std::min<uint32_t>(in.max_len_bound, n1));
   ep->maxd_full = std::max<uint32_t>(1, ep->L - 2);
-  // loads per lane: listed prefixes of wide rows have long lists, whose pieces take 8 loads per lane
-  // (large_sparse: 26 ms against 32 ms with 4); 4 elsewhere
-  ep->vec = cfg.vec ? clamp_vec(cfg.vec, ep->mode) : (ep->mode == 3 && in.stride / 4 >= 4096 ? 8u : 4u);
+  // loads per lane: 4 (with three 256-thread sparse CTAs per SM, large_sparse takes 21.7 ms with 4 and
+  // 22.5 ms with 8)
+  ep->vec = cfg.vec ? clamp_vec(cfg.vec, ep->mode) : 4u;
   ep->psmem = dfs_prefix_fits(in.stride, db->smem_optin, ep->L, ep->maxd_full, ep->mode);
   ep->smem = dfs_smem_bytes(in.stride, ep->L, ep->maxd_full, ep->psmem, ep->mode);
   int occ = 0;
@@ -108,8 +108,9 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
     ep->threads = 256;
     FIM_CUDA(dfs_max_ctas_per_sm(256, in.stride, ep->smem, false, 4, &occ));
   } else if (cfg.threads == 0 && ep->mode == 3 && in.stride / 4 >= 4096) {
-    // sparse nodes on wide rows: 256-thread CTAs (2 per SM), whose listed child prefixes are built with
-    // twice the loads in flight (large_sparse: 24.8 ms against 26.0 ms with 128 threads, 4 per SM)
+    // sparse nodes on wide rows: 256-thread CTAs (3 per SM under the kernel's 80-register bound), whose
+    // listed child prefixes are built with twice the loads in flight (large_sparse: 21.7 ms against
+    // 32.1 ms with 128-thread CTAs, 6 per SM)
     ep->threads = 256;
     FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
   } else if (cfg.threads == 0) {
@@ -122,6 +123,7 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
     uint32_t best_t = 256;
     for (uint32_t t : cand) {
       if (ep->mode == 1 && t == 128) continue;
+      if (ep->mode == 3 && t > 256) continue;  // the sparse kernel's launch bound
       int o = 0;
       FIM_CUDA(dfs_max_ctas_per_sm(t, ep->vec, ep->smem, ep->psmem, ep->mode, &o));
       if (o < 1) continue;
@@ -136,6 +138,7 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
     occ = best_occ;
   } else {
     ep->threads = clamp_threads(cfg.threads);
+    if (ep->mode == 3) ep->threads = std::min<uint32_t>(ep->threads, 256);  // the sparse kernel's launch bound
     FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
   }
   if (occ < 1) return fail(FIM_ERR_INVALID, "persistent kernel does not fit on an SM");
