@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_683_390_000}
 PAIR_MMA_TRAFFIC = {"large_sparse": 486_744_320 + 1_886_416_128 + 4_524_266_240 + 409_487_360}
 # the same for the persistent DFS kernel (profiles/k_dfs_large_sparse.md)
-DFS_KERNEL_TRAFFIC = {"large_sparse": 1_990_525_440 + 3_409_900_544}
+DFS_KERNEL_TRAFFIC = {"large_sparse": 4_444_721_920 + 5_475_868_928}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 
 
