@@ -123,7 +123,10 @@ typedef struct {
                                   repeated when an itemset is deeper                                */
   uint32_t pair_kernel;        /* FIM_PAIR_AUTO (0, default), FIM_PAIR_CORES, FIM_PAIR_TENSOR or
                                   FIM_PAIR_TENSOR_E4M3                                              */
-  uint32_t reserved_u;         /* 0                                                               */
+  uint32_t fault_pair_wait;    /* 0 (default); 1 = failure-detection test: the tensor-core pair
+                                  kernel expects 16 bytes per stage more than its copies bring, so
+                                  its bounded waits run out (about 1 s each) and the call returns
+                                  FIM_ERR_TIMEOUT with the device context intact                    */
   uint64_t out_capacity_sets;  /* 0 = automatic (grow and retry); else fixed capacity             */
   uint64_t out_capacity_items; /* idem, total items over all sets                                 */
   uint64_t spin_limit;         /* idle-CTA polling rounds without progress before FIM_ERR_TIMEOUT;

@@ -61,11 +61,14 @@ __device__ __forceinline__ uint32_t block_flag_scan(bool flag, uint32_t* wtot, u
 // ---------------------------------------------------------------------------
 // level-2 post-processing
 
+// (pair counts left incomplete by a timed-out pair kernel count as no survivors, so nothing below
+// runs on them; the call then reports the timeout)
 __global__ void k_surv_count(const uint32_t* __restrict__ C2, uint32_t n1, uint32_t minsup,
-                             uint32_t* __restrict__ scnt) {
+                             uint32_t* __restrict__ scnt, const DevCtrl* ctrl) {
   const uint32_t i = blockIdx.x;
+  const bool failed = (*(volatile const uint32_t*)&ctrl->err & DEV_ERR_TIMEOUT) != 0;
   uint32_t c = 0;
-  for (uint32_t j = i + 1 + threadIdx.x; j < n1; j += blockDim.x) c += C2[(size_t)i * n1 + j] >= minsup;
+  for (uint32_t j = i + 1 + threadIdx.x; j < n1 && !failed; j += blockDim.x) c += C2[(size_t)i * n1 + j] >= minsup;
   c = __reduce_add_sync(0xffffffffu, c);
   __shared__ uint32_t ws[32];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
@@ -1948,7 +1951,7 @@ cudaError_t occ_warp(uint32_t stride, size_t smem, int* out) {
 
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   if (p.n1 == 0) return cudaSuccess;
-  k_surv_count<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.scnt);
+  k_surv_count<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.scnt, p.ctrl);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -88,6 +88,7 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
                      pair_mma_cost_us(n1, in.stride, db->num_sms, ep->pair_e2m1) <
                          pair_cores_cost_us(n1, in.stride, db->num_sms);
     if (ep->pair_mma) FIM_TRY(ws_get(ws, WS_PAIR_X, xb, &ep->d_X));
+    ep->pair_extra_tx = cfg.fault_pair_wait ? 16u : 0u;
   }
   FIM_TRY(ws_get(ws, WS_SCNT, n1, &ep->d_scnt));
   FIM_TRY(ws_get(ws, WS_SOFF, 2ull * (n1 + 1), &ep->d_soff));
@@ -185,7 +186,8 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   if (!ep.skip_pairs) {
     uint32_t ksplit = 0;
     PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
-    ce = ep.pair_mma ? launch_pair_mma(pl, ep.d_X, ep.pair_e2m1, &ep.d_ctrl->err, ep.num_sms, st, &ksplit)
+    ce = ep.pair_mma ? launch_pair_mma(pl, ep.d_X, ep.pair_e2m1, &ep.d_ctrl->err, ep.num_sms, st, &ksplit,
+                                       ep.pair_extra_tx)
                      : launch_pair_counts(pl, ep.num_sms, st, &ksplit);
     if (ce != cudaSuccess) return ce;
   }

@@ -374,6 +374,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->mode = o->dfs_mode;
   c->depth_first = o->dfs_depth_first;
   c->pair_kernel = o->pair_kernel;
+  c->fault_pair_wait = o->fault_pair_wait;
   c->max_sets = o->max_itemsets;
   c->spin_limit = o->spin_limit;
   c->cap_sets = o->out_capacity_sets;

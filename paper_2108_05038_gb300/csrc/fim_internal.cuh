@@ -240,6 +240,7 @@ struct EngineConfig {
   uint32_t donate = 0;
   uint32_t mode = 2;  // DFS traversal: 0 node, 1 frame, 2 automatic (frames for rows of at most 2,048 words)
   uint32_t pair_kernel = 0;  // level 2: 0 automatic, 1 integer pipes, 2 tensor cores (e2m1), 3 (e4m3)
+  uint32_t fault_pair_wait = 0;  // test: the tensor pair kernel's stage waits never complete
   uint64_t spin_limit = 0;
   uint64_t cap_sets = 0, cap_items = 0;  // 0 = automatic
   bool fixed_capacity = false;
@@ -276,6 +277,7 @@ struct EnginePlan {
   bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
   bool pair_mma = false;    // level 2 on the tensor cores (rows widened into d_X)
   bool pair_e2m1 = true;    // tensor-core operands packed as e2m1 (else e4m3)
+  uint32_t pair_extra_tx = 0;  // test: bytes a stage waits for beyond its copies (0 normally)
   uint8_t* d_X = nullptr;   // widened rows (pair_mma only)
   float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
   unsigned long long* d_cta_time = nullptr;  // per-CTA [start, end] of the DFS (with timing only)
@@ -338,7 +340,7 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
 // err receives DEV_ERR_TIMEOUT if a bounded wait runs out
 // (e2m1: packed 4-bit operands, else e4m3 bytes)
 cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t* err, int num_sms, cudaStream_t st,
-                            uint32_t* ksplit_used);
+                            uint32_t* ksplit_used, uint32_t extra_tx = 0);
 uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride, bool e2m1);
 // modelled device time (µs) of each pair kernel, for the automatic choice
 double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1);

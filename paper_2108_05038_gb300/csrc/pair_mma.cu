@@ -204,7 +204,8 @@ __global__ void k_expand_e2m1(const uint32_t* __restrict__ bits, uint32_t stride
 template <bool kE2M1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pair_mma(const __grid_constant__ CUtensorMap xmap, uint32_t n1, uint32_t nbj, uint32_t n_tiles, uint32_t nsteps,
-               uint32_t steps_per_item, uint32_t ksplit, uint32_t* __restrict__ C2, uint32_t* __restrict__ err) {
+               uint32_t steps_per_item, uint32_t ksplit, uint32_t* __restrict__ C2, uint32_t* __restrict__ err,
+               uint32_t extra_tx) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_abort;
   const uint32_t raw = smem_addr(smem_raw);
@@ -279,7 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           // transaction bytes = bytes the TMA moves: e2m1 boxes carry 64 packed bytes per row (the gaps of
           // the unpacked shared-memory form are not written)
-          mbar_expect_tx(full(st), kE2M1 ? kStageBytes / 2 : kStageBytes);
+          // (extra_tx, a failure-detection test only: bytes that never arrive, so the wait runs out)
+          mbar_expect_tx(full(st), (kE2M1 ? kStageBytes / 2 : kStageBytes) + extra_tx);
           const int32_t x = (int32_t)((k0 + s) * kBK);
           tma_load(a_st + st * kABytes, &xmap, x, (int32_t)(bi * kBM), full(st));
           tma_load(b_st + st * kBBytes, &xmap, x, (int32_t)(bj * kBN), full(st));
@@ -316,13 +318,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_commit(empty(st));  // stage st free once these MMAs are done
           mma_open = true;
         }
-        mma_commit(acc_full(b));  // accumulator b complete
-        mma_open = false;
         if (!ok) {
-          abort_now();
+          abort_now();  // flagged before the commit, so the read-back sees it once acc_full(b) completes
+          mma_commit(acc_full(b));
           mma_open = true;  // nobody may wait for acc_full(b) now
           break;
         }
+        mma_commit(acc_full(b));  // accumulator b complete
+        mma_open = false;
       }
     }
     __syncwarp();
@@ -438,7 +441,7 @@ double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1) {
 }
 
 cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t* err, int num_sms, cudaStream_t st,
-                            uint32_t* ksplit_used) {
+                            uint32_t* ksplit_used, uint32_t extra_tx) {
   if (p.n1 < 2) {
     *ksplit_used = 0;
     return cudaSuccess;
@@ -504,8 +507,10 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t
     return e;
   const uint64_t items = (uint64_t)tiles * ksplit;
   const uint32_t grid = (uint32_t)std::min<uint64_t>(items, (uint64_t)num_sms);
-  if (e2m1) k_pair_mma<true><<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err);
-  else k_pair_mma<false><<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err);
+  if (e2m1)
+    k_pair_mma<true><<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err, extra_tx);
+  else
+    k_pair_mma<false><<<grid, kThreads, kSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err, extra_tx);
   note_launch();
   return cudaGetLastError();
 }

@@ -63,7 +63,7 @@ class MineOpts(ctypes.Structure):
         ("struct_size", ctypes.c_uint32), ("class_order", ctypes.c_uint32), ("dfs_mode", ctypes.c_uint32),
         ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
         ("donate", ctypes.c_uint32), ("result_on_device", ctypes.c_uint32), ("collect_times", ctypes.c_uint32),
-        ("dfs_depth_first", ctypes.c_uint32), ("pair_kernel", ctypes.c_uint32), ("reserved_u", ctypes.c_uint32),
+        ("dfs_depth_first", ctypes.c_uint32), ("pair_kernel", ctypes.c_uint32), ("fault_pair_wait", ctypes.c_uint32),
         ("out_capacity_sets", ctypes.c_uint64),
         ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("max_itemsets", ctypes.c_uint64),
         ("out_needed_sets", ctypes.c_uint64),
@@ -320,13 +320,14 @@ class Database:
              ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
              out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
              shape=None, dfs_mode: int | None = None, max_itemsets: int = 0, class_work: bool = False,
-             dfs_depth_first: int = 0, pair_kernel: int = FIM_PAIR_AUTO):
+             dfs_depth_first: int = 0, pair_kernel: int = FIM_PAIR_AUTO, fault_pair_wait: bool = False):
         """fim_mine; with ``class_work`` the result carries ``class_work`` (u64[n_rows]): the intersections
         of every one-row class, level 2 and below."""
         opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
                               collect_times, out_capacity_sets, out_capacity_items, spin_limit, stats, shape, dfs_mode,
                               max_itemsets, pair_kernel)
         opts.dfs_depth_first = dfs_depth_first
+        opts.fault_pair_wait = 1 if fault_pair_wait else 0
         cw = None
         if class_work:
             cw = np.zeros(max(1, self.info()["n_rows"]), dtype=np.uint64)

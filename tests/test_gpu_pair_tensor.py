@@ -113,3 +113,23 @@ def test_estimate_and_mine_with_automatic_choice():
         assert res.as_dict() == want
     finally:
         db.free()
+
+
+def test_pair_kernel_wait_runs_out_and_context_survives():
+    """Failure detection on the GPU: with fault_pair_wait every stage of the tensor pair kernel waits for
+    16 bytes that never arrive, so its bounded mbarrier waits (about 1 s each) run out; the kernel
+    flags the timeout, lets its copies and MMAs finish, frees its TMEM and returns, nothing below
+    level 2 runs on the incomplete counts, and the call reports FIM_ERR_TIMEOUT.  The same database
+    then mines exactly."""
+    w = synth.make_workload("sparse_mid", D=20000)
+    ms = 50
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    try:
+        with pytest.raises(fim.FimError) as e:
+            db.mine(ms, pair_kernel=fim.FIM_PAIR_TENSOR, fault_pair_wait=True)
+        assert e.value.status == fim.FIM_ERR_TIMEOUT
+        assert db.mine(ms, pair_kernel=fim.FIM_PAIR_TENSOR).as_dict() == want
+        torch.cuda.synchronize()  # the context is intact
+    finally:
+        db.free()
