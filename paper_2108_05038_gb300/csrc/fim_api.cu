@@ -103,7 +103,9 @@ static void pinned_release(void* p, size_t cap) {
 fim_status stage_get(fim_db* db, size_t bytes, void** out) {
   bytes = (bytes + 63) & ~(size_t)63;
   if (db->stage_used + bytes > db->stage_cap) {
-    FIM_CUDA(cudaStreamSynchronize(db->stream));
+    // regions handed out since the last synchronisation may still be read or written by queued
+    // copies: wait for them before reusing or replacing the buffer (nothing to wait for when none are)
+    if (db->stage_used) FIM_CUDA(cudaStreamSynchronize(db->stream));
     db->stage_used = 0;
     if (bytes > db->stage_cap) {
       pinned_release(db->stage, db->stage_cap);
@@ -272,11 +274,14 @@ static fim_status db_build_rows(fim_db* db, const uint32_t* src_off, const uint3
     if (db->nnz)
       FIM_CUDA(cudaMemcpyAsync(db->d_tx_items, src_items, db->nnz * 4ull, cudaMemcpyDeviceToDevice, st));
   }
-  std::vector<uint32_t> kept;
-  kept.reserve(N);
+  // kept items by ascending support, ties by id: one sort of (support, id) keys
+  std::vector<uint64_t> key;
+  key.reserve(N);
   for (uint32_t i = 0; i < N; ++i)
-    if (cnt[i] >= db->prefilter) kept.push_back(i);
-  std::stable_sort(kept.begin(), kept.end(), [&](uint32_t a, uint32_t b) { return cnt[a] < cnt[b]; });
+    if (cnt[i] >= db->prefilter) key.push_back(((uint64_t)cnt[i] << 32) | i);
+  std::sort(key.begin(), key.end());
+  std::vector<uint32_t> kept(key.size());
+  for (size_t k = 0; k < key.size(); ++k) kept[k] = (uint32_t)key[k];
   db->n_rows = (uint32_t)kept.size();
   db->rank_item = kept;
   db->supp.resize(db->n_rows);
@@ -438,9 +443,16 @@ fim_status make_result(cudaStream_t st, const EngineOutput& eo, bool on_dev, fim
   cudaError_t e = cudaSuccess;
   if (on_dev) {
     res->on_device = 1;
-    e = dev_malloc_async((void**)&res->d_off, (eo.n_sets + 1) * 8, st);
-    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_items, std::max<uint64_t>(1, eo.n_items) * 4, st);
-    if (e == cudaSuccess) e = dev_malloc_async((void**)&res->d_supp, std::max<uint64_t>(1, eo.n_sets) * 4, st);
+    // one block: offsets (u64) | items | supports, each part 16-byte aligned
+    const uint64_t b_off = (eo.n_sets + 1) * 8, b_items = (std::max<uint64_t>(1, eo.n_items) * 4 + 15) & ~15ull;
+    const uint64_t b_supp = std::max<uint64_t>(1, eo.n_sets) * 4;
+    void* blk = nullptr;
+    e = dev_malloc_async(&blk, ((b_off + 15) & ~15ull) + b_items + b_supp, st);
+    if (e == cudaSuccess) {
+      res->d_off = static_cast<uint64_t*>(blk);
+      res->d_items = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(blk) + ((b_off + 15) & ~15ull));
+      res->d_supp = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(res->d_items) + b_items);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(res->d_off, eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && eo.n_items)
       e = cudaMemcpyAsync(res->d_items, eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToDevice, st);
@@ -615,8 +627,11 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = total ? (double)tally[r] / (double)total : 0.0;
   db->est_order.resize(R);
   std::iota(db->est_order.begin(), db->est_order.end(), 0u);
-  std::stable_sort(db->est_order.begin(), db->est_order.end(),
-                   [&](uint32_t a, uint32_t b) { return db->est_cost[a] > db->est_cost[b]; });
+  {  // descending cost, ties by row (the order of a stable sort by cost); the tallies order the costs
+    const std::vector<unsigned long long>& t = tally;
+    std::sort(db->est_order.begin(), db->est_order.end(),
+              [&](uint32_t a, uint32_t b) { return t[a] != t[b] ? t[a] > t[b] : a < b; });
+  }
   db->has_estimate = true;
   db->est_nfs = eo.n_sets;
   db->est_m = m;
@@ -698,9 +713,7 @@ fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64
 
 void fim_result_free(fim_result* res) {
   if (!res) return;
-  if (res->d_off) cudaFreeAsync(res->d_off, res->stream);
-  if (res->d_items) cudaFreeAsync(res->d_items, res->stream);
-  if (res->d_supp) cudaFreeAsync(res->d_supp, res->stream);
+  if (res->d_off) cudaFreeAsync(res->d_off, res->stream);  // the block holding all three arrays
   delete res;
 }
 
