@@ -1051,7 +1051,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
 #define slot_supp(d) (arena + (size_t)(d) * per_depth + p.stride + lw + ((2ull * p.n1 + 3) & ~3ull))
   const uint32_t list_cap = p.n1;
   const uint4* bits4 = reinterpret_cast<const uint4*>(p.bits);
-  unsigned long long st_inter = 0, st_frames = 0;
+  unsigned long long st_inter = 0, st_frames = 0, st_nodes = 0;
 
   // the current node's prefix: listed in shared memory (n <= cap) or dense in stack slot d
   // stack slot d <- that prefix (the node has become a frame)
@@ -1144,8 +1144,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
       }
     };
     if (threadIdx.x == 0) {
-      atomicAdd(&p.ctrl->n_nodes, 1ull);
-      atomicAdd(&p.ctrl->progress, 1u);
+      ++st_nodes;  // (no CTA of this mode waits for progress)
       if (ns >= 2) { f_n[0] = ns; f_cur[0] = 0; C.depth = 0; ++st_frames; }
       else C.depth = -1;
       decide();  // (process_node ended with a barrier: nobody reads the root's step any more)
@@ -1194,8 +1193,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
                                             slot_supp(d + 1));
       if (n2 >= 2) save(d + 1, listed2, nz2);
       if (threadIdx.x == 0) {
-        atomicAdd(&p.ctrl->n_nodes, 1ull);
-        atomicAdd(&p.ctrl->progress, 1u);
+        ++st_nodes;
         if (n2 >= 2) { f_n[d + 1] = n2; f_cur[d + 1] = 0; C.depth = d + 1; ++st_frames; }
         decide();  // (the step's fields were read before process_node's barriers)
       }
@@ -1209,6 +1207,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
   if (threadIdx.x == 0) {
     atomicAdd(&p.ctrl->n_intersections, st_inter);
     atomicAdd(&p.ctrl->n_frames, st_frames);
+    atomicAdd(&p.ctrl->n_nodes, st_nodes);
     if (p.cta_time) p.cta_time[2 * blockIdx.x + 1] = global_ns();
   }
 #undef slot_pre
