@@ -455,9 +455,15 @@ def run_once(args):
         db.estimate_class_costs(SAMPLE_RATE, w["rel_minsup"], EST_SEED)
     res = db.mine(w["minsup"], result_on_device=True, collect_times=True)
     st = res.stats
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fl = res.flags()  # closed and maximal itemsets of the result (fim_result_flags)
+    t_flags = time.perf_counter() - t0
     res.free()
     db.free()
     return {"mode": "once", "config": {"workload": workload_desc(w), "estimate": not args.no_estimate},
+            "closed": int((fl & 1).sum()), "maximal": int((fl & 2).sum() // 2),
+            "ms_result_flags": round(t_flags * 1e3, 3),
             "n_frequent": st["n_frequent"], "n_intersections": st["n_intersections"],
             "ms_pair_kernel": round(st["ms_pair_kernel"], 4), "ms_dfs_kernel": round(st["ms_dfs_kernel"], 4),
             "bytes_pair_kernel": st["bytes_pair_kernel"], "bytes_dfs_kernel": st["bytes_dfs_kernel"],

@@ -376,6 +376,24 @@ fim_status fim_mine_pairs_noalloc(const fim_db* db, uint32_t minsup_abs, uint32_
 fim_status fim_extension_supports(fim_db* db, const uint32_t* prefix_items, uint32_t n_prefix,
                                   const uint32_t* cand_items, uint32_t n_cand, uint32_t* supports_out);
 
+/*
+ * Closed and maximal itemsets among a complete result (Ch. 2: Def. "Closed
+ * itemset" with its closure operator, Def. "Maximal Frequent Itemset").
+ * flags_out[k] (HOST array of n_sets bytes, the result's record order):
+ * bit 0 = itemset k is closed (no item outside it lies in every transaction
+ * that contains it, i.e. every one-item extension has a smaller support);
+ * bit 1 = itemset k is maximal (no proper superset is frequent).  Decided from
+ * the result alone: an itemset with an equal-support or a frequent superset has
+ * one with one item more, which is frequent and so in a complete result (any
+ * result of fim_mine or fim_plan_result; not a run stopped by max_itemsets).
+ * Runs on the device (a hash table of the result's itemsets, one lookup per
+ * immediate subset of every itemset) on the result's stream, which it
+ * synchronises; a host result is copied to the device for it.
+ * Errors: FIM_ERR_INVALID (NULL result or flags_out, 2^32 - 1 or more itemsets),
+ * FIM_ERR_OOM, FIM_ERR_CUDA.
+ */
+fim_status fim_result_flags(const fim_result* res, uint8_t* flags_out);
+
 void fim_result_free(fim_result* res);
 void fim_db_free(fim_db* db);
 const char* fim_status_str(fim_status s);

@@ -217,3 +217,33 @@ def extension_supports(offsets, items, N: int, prefix, candidates):
     covers_p = np.bincount(ptx[in_p], minlength=D) == prefix.size
     per_item = np.bincount(pit[covers_p[ptx]], minlength=N)
     return per_item[cand].astype(np.uint64)
+
+
+def closed_maximal(offsets, items, N: int, minsup: int):
+    """Flags of every frequent itemset (Ch. 2): bit 0 = closed (Def. "Closed itemset": the itemset equals
+    its closure, the set of items contained in every transaction that contains it), bit 1 = maximal
+    (Def. "Maximal Frequent Itemset": no proper superset is frequent).  Both follow from the counts of
+    every item over the transactions containing the itemset: closed iff no item outside it is counted
+    supp times, maximal iff no item outside it is counted at least minsup times.  Returns the O1 result
+    (canonical order) and the flags, u8 per itemset."""
+    so, si, sp = eclat(offsets, items, N, minsup)
+    offsets, items = _csr(offsets, items)
+    D = offsets.size - 1
+    tx = np.repeat(np.arange(D, dtype=np.int64), np.diff(offsets.astype(np.int64)))
+    body = items[int(offsets[0]): int(offsets[-1])].astype(np.int64)
+    pairs = np.unique(tx * N + body)  # distinct (transaction, item)
+    ptx, pit = pairs // N, pairs % N
+    tids = [ptx[pit == i] for i in range(N)]  # tidlist of every item (ascending)
+    flags = np.zeros(len(sp), dtype=np.uint8)
+    for k in range(len(sp)):
+        s = [int(v) for v in si[so[k]:so[k + 1]]]
+        t = tids[s[0]]
+        for v in s[1:]:
+            t = np.intersect1d(t, tids[v], assume_unique=True)
+        assert len(t) == int(sp[k])
+        cnt = np.bincount(pit[np.isin(ptx, t)], minlength=N)
+        cnt[s] = 0
+        closed = not np.any(cnt == len(t))
+        maximal = not np.any(cnt >= minsup)
+        flags[k] = (1 if closed else 0) | (2 if maximal else 0)
+    return so, si, sp, flags

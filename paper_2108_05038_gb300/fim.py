@@ -28,7 +28,7 @@ EXPORTED = [
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
     "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free", "fim_kernel_launches",
-    "fim_extension_supports",
+    "fim_extension_supports", "fim_result_flags",
 ]
 
 
@@ -137,6 +137,8 @@ def load(build_if_stale: bool = True):
         lib.fim_server_free.argtypes = [P]
         lib.fim_mine_pairs_noalloc.restype = i32
         lib.fim_mine_pairs_noalloc.argtypes = [P, u32, P, P, u64, ctypes.POINTER(u64)]
+        lib.fim_result_flags.restype = i32
+        lib.fim_result_flags.argtypes = [P, P]
         lib.fim_extension_supports.restype = i32
         lib.fim_extension_supports.argtypes = [P, P, u32, P, u32, P]
         lib.fim_result_view.restype = i32
@@ -186,6 +188,7 @@ class Result:
 
     def __init__(self, lib, handle, stats: MineStats | None):
         self._lib, self._h = lib, handle
+        self._flags = None
         n = ctypes.c_uint64()
         po, pi, ps = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         dev = ctypes.c_int()
@@ -207,7 +210,17 @@ class Result:
             else:
                 supp = np.zeros(0, dtype=np.uint32)
             self.set_offsets, self.set_items, self.supports = off, items, supp
-            self.free()
+            # the handle stays until free() (or collection): fim_result_flags reads it
+
+    def flags(self) -> np.ndarray:
+        """fim_result_flags: u8 per itemset (record order), bit 0 closed, bit 1 maximal (computed once)."""
+        if self._flags is None:
+            if not self._h:
+                raise FimError(FIM_ERR_INVALID, "fim_result_flags", "result already freed")
+            f = np.zeros(max(self.n_sets, 1), dtype=np.uint8)
+            _check(self._lib, self._lib.fim_result_flags(self._h, f.ctypes.data), "fim_result_flags")
+            self._flags = f[: self.n_sets]
+        return self._flags
 
     def free(self):
         if self._h:

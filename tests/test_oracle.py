@@ -465,3 +465,48 @@ def test_threaded_eclat_equals_sequential(threads):
     txs = [list(rng.choice(15, size=rng.integers(0, 8), replace=False)) for _ in range(200)]
     off, items = csr(txs)
     assert as_dict(oracle.eclat_mt(off, items, 15, 2, threads)) == brute_dict(txs, 15, 2)
+
+
+# ---------------------------------------------------------------- closed and maximal itemsets
+
+def _brute_closed_maximal(txs, N, minsup):
+    """Definitions written out over all subsets: closure = items of every transaction containing the set."""
+    sets = [frozenset(t) for t in txs]
+    d = brute_dict(txs, N, minsup)
+    out = {}
+    for s, v in d.items():
+        cover = [t for t in sets if set(s) <= t]
+        closure = frozenset.intersection(*cover) if cover else frozenset()
+        closed = closure == frozenset(s)
+        maximal = not any(set(s) < set(o) for o in d)
+        out[s] = (1 if closed else 0) | (2 if maximal else 0)
+    return out
+
+
+def _flags_dict(res):
+    so, si, sp, fl = res
+    return {tuple(int(v) for v in si[so[k]:so[k + 1]]): int(fl[k]) for k in range(len(sp))}
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_closed_maximal_equal_definitions_brute_force(seed):
+    rng = np.random.default_rng(500 + seed)
+    N = int(rng.integers(3, 11))
+    txs = [list(np.nonzero(rng.random(N) < rng.uniform(0.2, 0.8))[0]) for _ in range(int(rng.integers(5, 60)))]
+    off, items = csr(txs)
+    for minsup in (1, 2, max(1, len(txs) // 4)):
+        assert _flags_dict(oracle.closed_maximal(off, items, N, minsup)) == _brute_closed_maximal(txs, N, minsup)
+
+
+def test_closed_maximal_closed_forms():
+    """k identical transactions: only the full set is closed and maximal; nested transactions
+    {0} c {0,1} c {0,1,2}: every prefix closed (supports 3, 2, 1), only the longest maximal at minsup 1;
+    disjoint singletons: each both."""
+    off, items = csr([[0, 1, 2, 3]] * 5)
+    f = _flags_dict(oracle.closed_maximal(off, items, 4, 5))
+    assert f[(0, 1, 2, 3)] == 3 and all(v == 0 for k, v in f.items() if k != (0, 1, 2, 3))
+    off, items = csr([[0], [0, 1], [0, 1, 2]])
+    f = _flags_dict(oracle.closed_maximal(off, items, 3, 1))
+    assert f[(0,)] == 1 and f[(0, 1)] == 1 and f[(0, 1, 2)] == 3 and f[(1,)] == 0 and f[(1, 2)] == 0
+    off, items = csr([[0], [1], [2]])
+    assert set(_flags_dict(oracle.closed_maximal(off, items, 3, 1)).values()) == {3}
