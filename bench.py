@@ -40,7 +40,8 @@ L2_FLUSH_BYTES = 512 << 20
 # launch per workload: the integer-pipe k_pair_counts (profiles/k_pair_counts_sparse_mid.md) and the
 # tensor-core k_expand_e4m3 + k_pair_mma (profiles/k_pair_mma.md); None where none was taken
 PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_683_390_000}
-PAIR_MMA_TRAFFIC = {"large_sparse": 486_744_320 + 1_886_416_128 + 4_524_266_240 + 409_487_360}
+PAIR_MMA_TRAFFIC = {"large_sparse": 486_744_320 + 1_886_416_128 + 4_524_266_240 + 409_487_360,
+                    "sparse_mid": 12_403_712 + 186_112 + 51_631_616 + 0}
 # the same for the persistent DFS kernel (profiles/k_dfs_large_sparse.md)
 DFS_KERNEL_TRAFFIC = {"large_sparse": 4_444_721_920 + 5_475_868_928}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected

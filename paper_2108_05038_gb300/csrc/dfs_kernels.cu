@@ -82,13 +82,19 @@ __global__ void k_surv_count(const uint32_t* __restrict__ C2, uint32_t n1, uint3
 
 // One CTA: survivor offsets (row order), entry offsets (queue order), totals,
 // and the initial state of the control block.
+// The rows are frequent singletons, except in a count-only mine over rows not filtered by support (a
+// sample whose supports stay on the device), where rows below minsup count as nothing.
 __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t* __restrict__ row_order, uint32_t n1,
-                              uint32_t* __restrict__ soff, uint32_t* __restrict__ eoff, uint64_t cap_sets,
-                              uint64_t cap_items, DevCtrl* ctrl) {
+                              const uint32_t* __restrict__ row_supp, uint32_t minsup, uint32_t* __restrict__ soff,
+                              uint32_t* __restrict__ eoff, uint64_t cap_sets, uint64_t cap_items, DevCtrl* ctrl) {
   __shared__ uint32_t wtot[33];
+  __shared__ uint32_t n_single;
+  if (threadIdx.x == 0) n_single = 0;
+  uint32_t my_single = 0;
   uint32_t carry_s = 0, carry_e = 0;
   for (uint32_t base = 0; base < n1; base += blockDim.x) {
     uint32_t i = base + threadIdx.x;
+    if (i < n1 && row_supp[i] >= minsup) ++my_single;
     uint32_t vs = i < n1 ? scnt[i] : 0u;
     uint32_t q_row = i < n1 ? row_order[i] : 0u;
     uint32_t cq = i < n1 ? scnt[q_row] : 0u;
@@ -124,11 +130,14 @@ __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t*
     carry_e += wtot[1];
     __syncthreads();
   }
+  my_single = __reduce_add_sync(0xffffffffu, my_single);
+  if ((threadIdx.x & 31) == 0 && my_single) atomicAdd(&n_single, my_single);
+  __syncthreads();
   if (threadIdx.x == 0) {
     soff[n1] = carry_s;
     eoff[n1] = carry_e;
-    const unsigned long long P = carry_s;
-    const unsigned long long sets = n1 + P, items = n1 + 2 * P;
+    const unsigned long long P = carry_s, n1f = n_single;
+    const unsigned long long sets = n1f + P, items = n1f + 2 * P;
     ctrl->packed = (sets << 32) | items;
     ctrl->sets_total = sets;
     ctrl->items_total = items;
@@ -136,7 +145,7 @@ __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t*
     ctrl->n_entries = carry_e;
     ctrl->pending = carry_e;
     ctrl->queue_head = 0;
-    ctrl->max_len = n1 > 0 ? (P > 0 ? 2u : 1u) : 0u;
+    ctrl->max_len = n1f > 0 ? (P > 0 ? 2u : 1u) : 0u;
     if (cap_sets && (sets > cap_sets || items > cap_items)) ctrl->err |= DEV_ERR_OVERFLOW;  // 0: count only
   }
 }
@@ -157,7 +166,7 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
   const uint32_t i = row_order[q];
   const uint32_t id_i = rank_item[frows[i]];
   // sets of class i found at levels 1 and 2: {i} and its frequent pairs (the DFS adds the rest)
-  if (class_sets && threadIdx.x == 0) class_sets[i] = 1ull + scnt[i];
+  if (class_sets && threadIdx.x == 0) class_sets[i] = row_supp[i] >= minsup ? 1ull + scnt[i] : 0ull;
   if (threadIdx.x == 0 && out_off && i < cap_sets && i < cap_items) {
     out_off[i] = i;
     out_items[i] = id_i;
@@ -1954,7 +1963,8 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_level2_scan<<<1, 1024, 0, st>>>(p.scnt, p.row_order, p.n1, p.soff, p.eoff, p.cap_sets, p.cap_items, p.ctrl);
+  k_level2_scan<<<1, 1024, 0, st>>>(p.scnt, p.row_order, p.n1, p.row_supp, p.minsup, p.soff, p.eoff, p.cap_sets,
+                                    p.cap_items, p.ctrl);
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -566,16 +566,46 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   FIM_TRY(ws_get(db->ws, WS_SAMPLE_BITS, (size_t)std::max<uint32_t>(R, 1) * sstride, &d_sbits));
   FIM_TRY(ws_get(db->ws, WS_SAMPLE_SUPP, std::max<uint32_t>(R, 1), &d_ssupp));
   std::vector<uint32_t> ssupp(R);
+  // When nearly every row will be frequent in the sample (predicted from the full supports), the sample
+  // is mined over all its rows with the supports left on the device: pairs with a row below the sample
+  // minsup are not frequent anyway, and the level-2 kernels count only rows that reach it.  That saves
+  // the host round trip for the sample supports; they come back with the mine's own synchronisation.
+  uint32_t pred = 0;
+  for (uint32_t r = 0; r < R; ++r) pred += (double)db->supp[r] * (double)m / (double)db->D >= (double)minsup_s;
+  const bool all_rows = R > 0 && R <= 4096 && (uint64_t)pred * 4 >= (uint64_t)R * 3;
+  void* h_ss = nullptr;
+  size_t h_ss_cap = 0;
+  bool have_ssupp = false;
   if (R) {
     FIM_CUDA(cudaMemsetAsync(d_sbits, 0, (size_t)R * sstride * 4, st));
     FIM_CUDA(launch_sample_build(db->d_tx_off, db->d_tx_items, db->D, db->d_item_rank, seed, m, d_sbits, sstride, st));
     FIM_CUDA(launch_row_popcount(d_sbits, sstride, R, d_ssupp, st));
-    void* h = nullptr;
-    FIM_TRY(stage_get(db, (size_t)R * 4, &h));
-    FIM_CUDA(cudaMemcpyAsync(h, d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
-    FIM_TRY(stream_sync(db));
-    std::memcpy(ssupp.data(), h, (size_t)R * 4);
+    if (all_rows) {  // a pinned buffer of its own: the mine's retries may reuse the staging buffer
+      FIM_CUDA(pinned_acquire((size_t)R * 4, &h_ss, &h_ss_cap));
+      const cudaError_t ce = cudaMemcpyAsync(h_ss, d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st);
+      if (ce != cudaSuccess) {
+        pinned_release(h_ss, h_ss_cap);
+        return cuda_fail(ce, "sample supports");
+      }
+    } else {
+      void* h = nullptr;
+      FIM_TRY(stage_get(db, (size_t)R * 4, &h));
+      FIM_CUDA(cudaMemcpyAsync(h, d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+      FIM_TRY(stream_sync(db));
+      std::memcpy(ssupp.data(), h, (size_t)R * 4);
+      have_ssupp = true;
+    }
   }
+  struct PinnedGuard {  // returns the sample supports' buffer on every exit, once its copy is done
+    void* p;
+    size_t cap;
+    cudaStream_t st;
+    ~PinnedGuard() {
+      if (!p) return;
+      cudaStreamSynchronize(st);  // idle already after a mine; an early error may leave the copy queued
+      pinned_release(p, cap);
+    }
+  } guard{h_ss, h_ss_cap, st};
   EngineInput in;
   EngineOutput eo;
   unsigned long long* d_work = nullptr;
@@ -585,11 +615,18 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
     in.bits = d_sbits;
     in.stride = sstride;
     in.bytes_per_row_alg = (uint32_t)(((uint64_t)m + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
-    for (uint32_t r = 0; r < R; ++r)
-      if (ssupp[r] >= minsup_s) {
-        in.frows.push_back(r);
-        in.row_supp.push_back(ssupp[r]);
-      }
+    if (all_rows) {  // every row, supports on the device (rows below minsup_s count as nothing)
+      in.frows.resize(R);
+      std::iota(in.frows.begin(), in.frows.end(), 0u);
+      in.d_frows = db->d_iota;
+      in.d_row_supp = d_ssupp;
+    } else {
+      for (uint32_t r = 0; r < R; ++r)
+        if (ssupp[r] >= minsup_s) {
+          in.frows.push_back(r);
+          in.row_supp.push_back(ssupp[r]);
+        }
+    }
     in.n1 = (uint32_t)in.frows.size();
     in.row_order.resize(in.n1);
     std::iota(in.row_order.begin(), in.row_order.end(), 0u);
@@ -609,6 +646,11 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
     }
     eo = EngineOutput{};
     const fim_status s = engine_mine(db, db->ws, in, cfg, &eo, nullptr);
+    if (all_rows && !have_ssupp && (s == FIM_OK || s == FIM_ERR_OUTPUT_OVERFLOW)) {
+      // the copy was queued before the mine's kernels, and the mine synchronised the stream
+      std::memcpy(ssupp.data(), h_ss, (size_t)R * 4);
+      have_ssupp = true;
+    }
     if (s == FIM_OK) break;
     const bool over = max_sample_itemsets &&
                       ((eo.ctrl.err & DEV_ERR_ABORTED) || eo.ctrl.sets_total > max_sample_itemsets);
@@ -619,8 +661,12 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   // frequent sample rows) + the DFS below; itemsets = {r}, its frequent pairs and the DFS sets
   std::vector<unsigned long long> tally(R, 0ull);
   per.resize(in.n1, 0ull);
-  for (uint32_t i = 0; i < in.n1; ++i)
-    tally[in.frows[i]] = per[i] + (cost_kind == FIM_COST_INTERSECTIONS ? (in.n1 - 1 - i) : 0ull);
+  uint32_t later = 0;  // frequent sample rows after row i: its level-2 candidates
+  for (uint32_t i = in.n1; i-- > 0;) {
+    if (ssupp[in.frows[i]] < minsup_s) continue;  // (all-rows mine only) not a class of the sample
+    tally[in.frows[i]] = per[i] + (cost_kind == FIM_COST_INTERSECTIONS ? later : 0ull);
+    ++later;
+  }
   unsigned long long total = 0;
   for (uint32_t r = 0; r < R; ++r) total += tally[r];
   db->est_cost.assign(R, 0.0);
