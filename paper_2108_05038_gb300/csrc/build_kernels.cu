@@ -36,8 +36,14 @@ __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* _
   }
   uint32_t local_max = 0, local_err = first != 0 ? DEV_ERR_OFFSETS : 0u;
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-  for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < D && first == 0; t += warps) {
-    const uint32_t b = off[t], e = off[t + 1];
+  uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  uint32_t nb = t < D ? off[t] : 0u, ne = t < D ? off[t + 1] : 0u;  // the offsets of the next transaction
+  for (; t < D && first == 0; t += warps) {
+    const uint32_t b = nb, e = ne;
+    if (t + warps < D) {
+      nb = off[t + warps];
+      ne = off[t + warps + 1];
+    }
     if (e < b || e > nnz) {
       local_err |= DEV_ERR_OFFSETS;
       continue;
@@ -91,11 +97,19 @@ __global__ void k_bitmap_build(const uint32_t* __restrict__ off, const uint32_t*
     const uint32_t len = e - b;
     const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
     uint32_t* const col = bits + (w0 >> 5);
-    for (uint32_t j = 0; j < maxlen; ++j) {
-      const int32_t r = j < len ? item_rank[items[b + j]] : -1;
-      const uint32_t key = r >= 0 ? (uint32_t)r : 0xffffffffu;
-      const uint32_t grp = __match_any_sync(0xffffffffu, key);
-      if (r >= 0 && lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(col + (size_t)r * stride, grp);
+    for (uint32_t j0 = 0; j0 < maxlen; j0 += 4) {  // four positions per round: their loads in flight together
+      uint32_t it[4];
+      int32_t r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) it[u] = j0 + u < len ? items[b + j0 + u] : 0xffffffffu;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) r[u] = it[u] != 0xffffffffu ? item_rank[it[u]] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t key = r[u] >= 0 ? (uint32_t)r[u] : 0xffffffffu;
+        const uint32_t grp = __match_any_sync(0xffffffffu, key);
+        if (r[u] >= 0 && lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(col + (size_t)r[u] * stride, grp);
+      }
     }
   }
 }
@@ -161,8 +175,8 @@ cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32
                               uint32_t* flags, cudaStream_t st) {
   const uint32_t threads = 256;
   size_t smem = N <= kSmemHistMax ? (size_t)N * 4 : 0;
-  // one warp per transaction; with a shared histogram every CTA flushes N counters: keep the grid modest
-  uint32_t grid = grid_for((uint64_t)D * 32, threads, N <= kSmemHistMax ? 152 * 4 : 152 * 32);
+  // one warp per transaction; with a shared histogram every CTA flushes its nonzero counters: a modest grid
+  uint32_t grid = grid_for((uint64_t)D * 32, threads, N <= kSmemHistMax ? 152 * 8 : 152 * 32);
   k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, flags);
   note_launch();
   return cudaGetLastError();
