@@ -109,9 +109,8 @@ typedef struct {
                                   prefix in its registers, no CTA-wide barrier; rows of at most 512
                                   words, no donation (else as SPARSE)                              */
   uint32_t threads_per_cta;    /* persistent DFS CTA size, 128/256/512 (sparse nodes: at most 256;
-                                  warp DFS: 256); 0 = sparse nodes on rows of at least 4,096
-                                  16-byte words: 256; other node modes: the one with the most CTAs
-                                  per SM (then warps); frames: the most warps                      */
+                                  warp DFS: 256); 0 = sparse nodes: 256; other node modes: the one
+                                  with the most CTAs per SM (then warps); frames: the most warps   */
   uint32_t vec_per_lane;       /* 16-byte loads per lane per work piece, 1/2/4/8 (sparse nodes also
                                   16); 0 = 4                                                       */
   uint32_t ctas_per_sm;        /* 0 = as many as fit                                              */

@@ -108,10 +108,11 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   if (ep->mode == 4) {  // warp DFS: CTAs of 8 warps; its occupancy query takes the row stride
     ep->threads = 256;
     FIM_CUDA(dfs_max_ctas_per_sm(256, in.stride, ep->smem, false, 4, &occ));
-  } else if (cfg.threads == 0 && ep->mode == 3 && in.stride / 4 >= 4096) {
-    // sparse nodes on wide rows: 256-thread CTAs (3 per SM under the kernel's 80-register bound), whose
-    // listed child prefixes are built with twice the loads in flight (large_sparse: 21.7 ms against
-    // 32.1 ms with 128-thread CTAs, 6 per SM)
+  } else if (cfg.threads == 0 && ep->mode == 3) {
+    // sparse nodes: 256-thread CTAs (3 per SM under the kernel's 80-register bound), whose listed child
+    // prefixes are built with twice the loads in flight (large_sparse: 21.7 ms against 32.1 ms with
+    // 128-thread CTAs, 6 per SM; sparse_mid 0.027 against 0.029 ms; its 200,000-row variant prefers
+    // 128 threads, 7.5 against 8.7 ms)
     ep->threads = 256;
     FIM_CUDA(dfs_max_ctas_per_sm(ep->threads, ep->vec, ep->smem, ep->psmem, ep->mode, &occ));
   } else if (cfg.threads == 0) {

@@ -179,25 +179,26 @@ __global__ void k_expand_e4m3(const uint32_t* __restrict__ bits, uint32_t stride
 }
 
 // X[f][16w .. 16w+15] (bytes) = the 32 bits of word w of row frows[f] as 32 e2m1 values (1.0 or 0),
-// transaction 2k in the low nibble of byte k
+// transaction 2k in the low nibble of byte k.  Grid: x over the words of a row, y over the rows.
 __global__ void k_expand_e2m1(const uint32_t* __restrict__ bits, uint32_t stride, const uint32_t* __restrict__ frows,
                               uint32_t n1, uint4* __restrict__ X) {
-  const uint64_t total = (uint64_t)n1 * stride;
-  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t f = (uint32_t)(idx / stride), w = (uint32_t)(idx % stride);
-    const uint32_t word = __ldg(bits + (size_t)frows[f] * stride + w);
-    uint32_t o[4];
+  for (uint32_t f = blockIdx.y; f < n1; f += gridDim.y) {
+    const uint32_t* row = bits + (size_t)frows[f] * stride;
+    uint4* xrow = X + (size_t)f * stride;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < stride; w += gridDim.x * blockDim.x) {
+      const uint32_t word = __ldg(row + w);
+      uint32_t o[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      // the 8 bits of byte q to bit 0 of nibbles 0..7 (interleave with three zero bits), then x 2
-      uint32_t t = (word >> (8 * q)) & 0xFFu;
-      t = (t | (t << 12)) & 0x000F000Fu;
-      t = (t | (t << 6)) & 0x03030303u;
-      t = (t | (t << 3)) & 0x11111111u;
-      o[q] = t * kOneE2M1;
+      for (int q = 0; q < 4; ++q) {
+        // the 8 bits of byte q to bit 0 of nibbles 0..7 (interleave with three zero bits), then x 2
+        uint32_t t = (word >> (8 * q)) & 0xFFu;
+        t = (t | (t << 12)) & 0x000F000Fu;
+        t = (t | (t << 6)) & 0x03030303u;
+        t = (t | (t << 3)) & 0x11111111u;
+        o[q] = t * kOneE2M1;
+      }
+      xrow[w] = make_uint4(o[0], o[1], o[2], o[3]);
     }
-    X[idx] = make_uint4(o[0], o[1], o[2], o[3]);
   }
 }
 
@@ -461,8 +462,12 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t
   // widen the frequent rows
   const uint64_t words = (uint64_t)p.n1 * p.stride;
   const uint32_t eg = (uint32_t)std::min<uint64_t>((words + 255) / 256, (uint64_t)num_sms * 16);
-  if (e2m1) k_expand_e2m1<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
-  else k_expand_e4m3<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
+  if (e2m1) {
+    const dim3 g2(std::min<uint32_t>((p.stride + 255) / 256, 16), std::min<uint32_t>(p.n1, 65535));
+    k_expand_e2m1<<<g2, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
+  }
+  else
+    k_expand_e4m3<<<eg, 256, 0, st>>>(p.bits, p.stride, p.frows, p.n1, reinterpret_cast<uint4*>(X));
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
