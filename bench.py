@@ -8,7 +8,7 @@ every frequent itemset (pair kernel, level-2 compaction, persistent DFS),
 results left in device memory.
 
 Prints one JSON line.  `value` is the algorithmic AND+popcount throughput of
-the mining in GB/s (bytes of all tidset intersections) over the
+the mining in GB/s (bytes of all tidset intersections, the dense definition) over the
 whole step time; `itemsets_per_s` is |F| over the same time.  `e2e` repeats the
 step through the C ABI with host buffers (pinned CSR in, itemsets out).
 `--impl reference` times the CPU oracle on the same workload instead.
@@ -37,12 +37,12 @@ SAMPLE_RATE = 0.01
 EST_SEED = 1
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one launch of the level-2 pair kernel, from one ncu capture of the mine's
-# launch per workload: the integer-pipe k_pair_counts (profiles/k_pair_counts_sparse_mid.md) and the
-# tensor-core k_expand_e4m3 + k_pair_mma (profiles/k_pair_mma.md); None where none was taken
+# launch per workload (dram__bytes_read.sum + dram__bytes_write.sum): the integer-pipe k_pair_counts,
+# and the tensor-core k_expand_e2m1 + k_pair_mma; None where none was taken
 PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_683_390_000}
 PAIR_MMA_TRAFFIC = {"large_sparse": 486_744_320 + 1_886_416_128 + 4_524_266_240 + 409_487_360,
                     "sparse_mid": 12_403_712 + 186_112 + 51_631_616 + 0}
-# the same for the persistent DFS kernel (profiles/k_dfs_large_sparse.md)
+# the same for the persistent DFS kernel
 DFS_KERNEL_TRAFFIC = {"large_sparse": 4_444_721_920 + 5_475_868_928}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 
