@@ -40,10 +40,10 @@ L2_FLUSH_BYTES = 512 << 20
 # launch per workload (dram__bytes_read.sum + dram__bytes_write.sum): the integer-pipe k_pair_counts,
 # and the tensor-core k_expand_e2m1 + k_pair_mma; None where none was taken
 PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_683_390_000}
-PAIR_MMA_TRAFFIC = {"large_sparse": 486_744_320 + 1_886_416_128 + 4_524_266_240 + 409_487_360,
-                    "sparse_mid": 12_403_712 + 186_112 + 51_631_616 + 0}
+PAIR_MMA_TRAFFIC = {"large_sparse": 486_638_080 + 1_884_786_688 + 4_530_159_104 + 409_678_336,
+                    "sparse_mid": 12_402_176 + 189_952 + 51_629_056 + 0}
 # the same for the persistent DFS kernel
-DFS_KERNEL_TRAFFIC = {"large_sparse": 4_444_721_920 + 5_475_868_928}
+DFS_KERNEL_TRAFFIC = {"large_sparse": 4_454_237_440 + 5_447_404_288}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 
 
