@@ -274,18 +274,18 @@ def run_ours(args):
                                  if stats["n_frequent_items"] * ((D + 31) // 32) * 4 > 129e6 else
                                  "the rows fit in L2 (129 MB): the DFS is bound by the latency of its dependent "
                                  "per-node steps, not by HBM; the fraction is of the HBM copy rate")}
-        elif stats.get("pair_kernel") in (2, 3):  # level 2 on the tensor cores: the 0/1 contraction in e4m3
+        elif stats.get("pair_kernel") in (2, 3):  # level 2 on the tensor cores: the 0/1 contraction, kind::f8f6f4
             flops = 2.0 * stats["n_pair_intersections"] * D  # one multiply-add per pair and transaction
             tf = flops / (pair_avg * 1e-3) / 1e12
             peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0))
             roofline = {"kernel": "k_expand_e2m1 + k_pair_mma" if stats.get("pair_kernel") == 2 else "k_expand_e4m3 + k_pair_mma", "bound": "tensor", "achieved": round(tf, 1),
                         "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(tf / peak, 4),
                         "traffic": PAIR_MMA_TRAFFIC.get(args.workload),
-                        "peak_source": ("e4m3 dense = 2 x the measured bf16 burst (MEASURED_PEAKS.json bf16_tflops; "
-                                        "nominal fp8:bf16 = 4.5:2.25)" if "bf16_tflops" in peaks
+                        "peak_source": ("kind::f8f6f4 (e2m1 and e4m3 operands alike) at the fp8 dense rate = 2 x the "
+                                        "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops; nominal fp8:bf16 = 4.5:2.25)" if "bf16_tflops" in peaks
                                         else "fallback 1.9 PFLOP/s bf16 x 2"),
                         "note": "algorithmic flops: 2 x pairs i<j x transactions; the time includes widening "
-                                "the rows to bytes"}
+                                "the rows to the operand form"}
         else:
             roofline = {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                         "peak": round(alu_peak_gword, 1), "unit": "Gword/s",
