@@ -40,7 +40,10 @@ __global__ void k_flags_insert(const uint64_t* __restrict__ off, const uint32_t*
     const uint64_t b = off[i];
     const uint32_t len = (uint32_t)(off[i + 1] - b);
     uint64_t slot = set_hash(items + b, len, len) & mask;
-    while (atomicCAS(&table[slot], kEmpty, (uint32_t)i) != kEmpty) slot = (slot + 1) & mask;
+    // linear probing; the table holds at least twice as many slots as itemsets, so a free slot is
+    // met within mask + 1 probes
+    for (uint64_t probe = 0; probe <= mask; ++probe, slot = (slot + 1) & mask)
+      if (atomicCAS(&table[slot], kEmpty, (uint32_t)i) == kEmpty) break;
   }
 }
 
@@ -54,7 +57,7 @@ __global__ void k_flags_probe(const uint64_t* __restrict__ off, const uint32_t* 
     const uint32_t* y = items + b;
     for (uint32_t p = 0; p < len; ++p) {  // the subset Y without its p-th item
       uint64_t slot = set_hash(y, len, p) & mask;
-      for (;;) {
+      for (uint64_t probe = 0; probe <= mask; ++probe) {
         const uint32_t j = table[slot];
         if (j == kEmpty) break;  // every result itemset was inserted: a subset that is not found is absent
         const uint64_t bj = off[j];
