@@ -306,8 +306,10 @@ void fim_plan_free(fim_plan* plan);
  * by the caller: fim_result_free), the latency from submission and the
  * service time (either pointer may be NULL); each id can be waited once.
  * The result of a job does not depend on the other jobs in flight.
- * fim_server_free stops the workers after the jobs in flight; queued jobs
- * that never started are dropped.
+ * fim_server_submit, fim_server_wait and fim_server_stats may be called from
+ * several host threads at once.  fim_server_free stops the workers after the
+ * jobs in flight; queued jobs that never started are dropped, so no other
+ * call on the server (in particular a wait) may run during or after it.
  * Errors: FIM_ERR_INVALID (bad arguments, unknown id), FIM_ERR_CUDA, and the
  * errors of the job's own build / estimate / mine (returned by wait).
  */
