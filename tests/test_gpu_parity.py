@@ -489,6 +489,22 @@ def test_row_order_matches_oracle():
     assert np.all(np.diff(sp.astype(np.int64)) >= 0)
 
 
+@pytest.mark.parametrize("name,D,ms", [("sparse_mid", 30000, 80), ("dense_deep", 20000, 12000)])
+def test_output_independent_of_sample_rate_and_seed(name, D, ms):
+    """The estimate only orders the classes (Sec. 8.2): after estimates at different sample rates,
+    seeds, relative minsups and cost measures, every mine returns the oracle's itemsets."""
+    w = synth.make_workload(name, D=D)
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    try:
+        for rate, seed, rel, cost in [(0.005, 1, ms / D, "itemsets"), (0.05, 7, ms / D, "itemsets"),
+                                      (1.0, 2, ms / D, "intersections"), (0.01, 3, 1.5 * ms / D, "itemsets")]:
+            db.estimate_class_costs(rate, rel, seed, cost=cost)
+            assert_same(db.mine(ms).as_dict(), want)
+    finally:
+        db.free()
+
+
 # ---------------------------------------------------------------- full sizes against stored oracle digests
 
 DIGESTS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "digests.json")))
