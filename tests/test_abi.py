@@ -98,3 +98,56 @@ def test_no_oracle_import_in_product_path():
                 text = open(os.path.join(dirpath, f), errors="replace").read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "fim_oracle" not in text, f
+
+
+_SCALARS = {"uint8_t": ctypes.c_uint8, "uint32_t": ctypes.c_uint32, "uint64_t": ctypes.c_uint64,
+            "int": ctypes.c_int, "fim_status": ctypes.c_int, "double": ctypes.c_double, "float": ctypes.c_float}
+_STRUCTS = {"fim_mine_opts": "MineOpts", "fim_mine_stats": "MineStats"}
+
+
+def header_prototypes():
+    """(return type, name, [(base type, pointer depth)]) of every function declared in include/fim.h."""
+    text = open(os.path.join(ROOT, "include", "fim.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(fim_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = []
+        for p in m.group(3).split(","):
+            p = " ".join(p.replace("const", " ").split())
+            if p in ("", "void"):
+                continue
+            depth = p.count("*")
+            base = p.replace("*", " ").split()[0]
+            params.append((base, depth))
+        out.append((" ".join(m.group(1).split()), m.group(2), params))
+    return out
+
+
+def _matches(ct, base, depth):
+    if depth == 0:
+        return ct is _SCALARS[base]
+    if ct in (ctypes.c_void_p, ctypes.c_char_p):
+        return True  # an untyped pointer: buffers, opaque handles, the caller's stream
+    target = getattr(ct, "_type_", None)
+    if target is None:
+        return False
+    if depth >= 2:
+        return target is ctypes.c_void_p  # out-pointer to a handle or a buffer address
+    if base in _SCALARS:
+        return target is _SCALARS[base]
+    return base in _STRUCTS and target is getattr(fim, _STRUCTS[base])
+
+
+def test_ctypes_signatures_match_header():
+    """Every entry point's argument and return types in the binding agree with its prototype in
+    include/fim.h: the same count, the same scalar widths, pointers where the header has pointers."""
+    lib = fim.load()
+    protos = header_prototypes()
+    assert sorted(name for _, name, _ in protos) == header_functions()
+    rets = {"fim_status": ctypes.c_int, "void": None, "const char*": ctypes.c_char_p, "uint64_t": ctypes.c_uint64}
+    for ret, name, params in protos:
+        f = getattr(lib, name)
+        assert f.restype is rets[ret], name
+        assert f.argtypes is not None and len(f.argtypes) == len(params), name
+        for k, (ct, (base, depth)) in enumerate(zip(f.argtypes, params)):
+            assert _matches(ct, base, depth), f"{name} argument {k}: {ct} for {base}{'*' * depth}"
