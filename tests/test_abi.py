@@ -151,3 +151,39 @@ def test_ctypes_signatures_match_header():
         assert f.argtypes is not None and len(f.argtypes) == len(params), name
         for k, (ct, (base, depth)) in enumerate(zip(f.argtypes, params)):
             assert _matches(ct, base, depth), f"{name} argument {k}: {ct} for {base}{'*' * depth}"
+
+
+def test_plain_c_program_links_and_calls_without_gpu(tmp_path):
+    """The library is usable from plain C through include/fim.h alone: a C11 program links against it
+    and makes the calls that need no device (option defaults, argument errors, status strings)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lib_path = _build.build()
+    src = tmp_path / "use_abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "fim.h"
+int main(void) {
+  fim_mine_opts o;
+  fim_mine_opts_init(&o);
+  if (o.struct_size != sizeof(fim_mine_opts) || o.class_order != FIM_ORDER_ESTIMATE) return 1;
+  fim_db* db = (fim_db*)0;
+  if (fim_build_vertical_db(NULL, NULL, 0, 10, 64, 0, NULL, &db) != FIM_ERR_INVALID || db) return 2;
+  if (!strstr(fim_last_error(), "D == 0")) return 3;
+  fim_result* r = (fim_result*)0;
+  if (fim_mine(NULL, 5, &o, &r) != FIM_ERR_INVALID || r) return 4;
+  if (strcmp(fim_status_str(FIM_ERR_TIMEOUT), "FIM_ERR_TIMEOUT") != 0) return 5;
+  if (fim_kernel_launches() != 0) return 6;
+  fim_db_free(NULL);
+  fim_result_free(NULL);
+  puts("ok");
+  return 0;
+}
+''')
+    exe = tmp_path / "use_abi"
+    libdir = os.path.dirname(lib_path)
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe), lib_path, f"-Wl,-rpath,{libdir}"])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
