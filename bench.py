@@ -691,6 +691,23 @@ def oracle_bytes(off, items, N, D, minsup, word_bits=64):
     return (I + C + M) * ((D + word_bits - 1) // word_bits * (word_bits // 8)), len(sp)
 
 
+def host_cpu():
+    """The host CPU as a short string (architecture and model), for the CPU-baseline records."""
+    import platform
+
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                if key.strip() in ("model name", "CPU part") and val.strip():
+                    model = val.strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()} {model}".strip()
+
+
 def cpu_baseline(w, bytes_alg_per_step, name):
     """The oracle as it stands, on the host, on the same workload (one full mine; a prefix sample of large
     databases): on every host core (one-item classes spread over threads) and on one core."""
@@ -707,7 +724,7 @@ def cpu_baseline(w, bytes_alg_per_step, name):
     oracle.eclat(off, items, w["N"], ms)
     dt1 = time.perf_counter() - t0
     return {"value": round(bytes_alg_per_step / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{desc} ({len(sp)} itemsets) in {dt:.2f} s on {cores} threads ({dt1:.2f} s on one); GB/s "
+            "cpu": host_cpu(), "sample": f"{desc} ({len(sp)} itemsets) in {dt:.2f} s on {cores} threads ({dt1:.2f} s on one); GB/s "
                       f"counts the bitmap path's algorithmic bytes for the same answer",
             "itemsets_per_s": round(len(sp) / dt, 1),
             "single_core": {"value": round(bytes_alg_per_step / dt1 / 1e9, 4), "unit": "GB/s", "cores": 1,
@@ -740,7 +757,7 @@ def run_reference(args):
             "config": {"workload": workload_desc(w)},
             "itemsets_per_s": round(n_sets * args.steps / dt, 1),
             "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{desc} per step ({n_sets} itemsets), one-item classes over {cores} "
+                             "cpu": host_cpu(), "sample": f"{desc} per step ({n_sets} itemsets), one-item classes over {cores} "
                                        f"threads"},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -25,6 +25,7 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"] is True
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) and cb["value"] == d["value"]
+    assert isinstance(cb["cpu"], str) and cb["cpu"]
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "tiny" in d["config"]["workload"]
 
