@@ -191,6 +191,24 @@ def test_singletons_equal_histogram():
     assert single == {i: int(c) for i, c in enumerate(hist) if c >= 30}
 
 
+@pytest.mark.parametrize("seed,prefilter", [(0, 0), (1, 5), (2, 40), (3, 10 ** 6)])
+def test_item_order_is_ascending_support_then_id(seed, prefilter):
+    """The row order (reading 3: ascending support, ties by id; items below the prefilter dropped), as
+    properties: a permutation of exactly the items whose support (library histogram of each
+    transaction's distinct items) reaches the prefilter, supports non-decreasing, ties by id."""
+    rng = np.random.default_rng(seed)
+    N = 60
+    txs = [list(rng.integers(0, N, size=rng.integers(0, 12))) for _ in range(800)]  # repeats inside allowed
+    off = np.cumsum([0] + [len(t) for t in txs]).astype(np.uint32)  # raw CSR, repeats kept
+    items = np.array([v for t in txs for v in t], dtype=np.uint32)
+    supp = np.bincount(np.concatenate([np.unique(t) for t in txs if len(t)]), minlength=N)
+    order = oracle.item_order(off, items, N, prefilter)
+    assert sorted(order.tolist()) == [i for i in range(N) if supp[i] >= prefilter]
+    s = supp[order]
+    assert np.all(np.diff(s) >= 0)
+    assert all(order[k] < order[k + 1] for k in range(len(order) - 1) if s[k] == s[k + 1])
+
+
 def test_anti_monotone_along_prefixes():
     """Thm. 2.1 on an Eclat output: every set's prefix (minus last item) is output with >= support."""
     w = synth.make_workload("tiny", D=4000)
