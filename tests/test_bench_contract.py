@@ -34,3 +34,65 @@ def test_reference_arm_other_ranks_are_silent():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def _literal_bitmap_work(off, items, N, minsup):
+    """Runs the bitmap Eclat literally, in row order (ascending support, ties by id), counting every
+    support test (intersection), every class node that tests at least one candidate, and every prefix
+    of two or more items whose bitmap is formed because it has at least two frequent extensions."""
+    import numpy as np
+
+    D = len(off) - 1
+    supp = np.zeros(N, dtype=np.int64)
+    tids = [set() for _ in range(N)]
+    for t in range(D):
+        for i in set(int(v) for v in items[off[t]:off[t + 1]]):
+            tids[i].add(t)
+            supp[i] += 1
+    order = sorted(range(N), key=lambda i: (supp[i], i))  # row r holds item order[r]
+    rows = [tids[i] for i in order]
+    freq = [r for r in range(N) if len(rows[r]) >= minsup]
+    count = {"I": 0, "C": 0, "M": 0}
+
+    def node(X, tX, cands):
+        if not cands:
+            return
+        count["C"] += 1
+        surv = []
+        for e in cands:
+            count["I"] += 1
+            t = tX & rows[e]
+            if len(t) >= minsup:
+                surv.append((e, t))
+        if len(X) >= 2 and len(surv) >= 2:
+            count["M"] += 1
+        for k, (e, t) in enumerate(surv):
+            node(X + (e,), t, [f for f, _ in surv[k + 1:]])
+
+    for p, r in enumerate(freq):
+        node((r,), rows[r], freq[p + 1:])
+    return count["I"], count["C"], count["M"]
+
+
+def test_algorithmic_work_counts_equal_a_literal_run():
+    """The bench's unit of work (intersections, class nodes with candidates, materialised prefixes),
+    recomputed from an oracle output alone, equals what a literal bitmap Eclat performs."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        N, D = int(rng.integers(3, 14)), int(rng.integers(20, 300))
+        dens = rng.uniform(0.15, 0.7)
+        txs = [np.nonzero(rng.random(N) < dens)[0] for _ in range(D)]
+        off = np.cumsum([0] + [len(t) for t in txs]).astype(np.uint32)
+        items = np.concatenate([t for t in txs] + [np.zeros(0, dtype=np.int64)]).astype(np.uint32)
+        for minsup in (1, max(1, D // 6), max(1, D // 3)):
+            so, si, _ = oracle.eclat(off, items, N, minsup)
+            order = oracle.item_order(off, items, N, 0)
+            rank = np.zeros(N, dtype=np.int64)
+            rank[order] = np.arange(len(order))
+            assert bench.bitmap_work(so, si, rank) == _literal_bitmap_work(off, items, N, minsup), (trial, minsup)
