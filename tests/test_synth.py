@@ -100,3 +100,16 @@ def test_serving_request_law():
     gaps = np.diff(np.concatenate([[0.0], arr]))
     assert np.all(gaps >= 0)
     assert abs(gaps.mean() - 0.05) < 5 * 0.05 / math.sqrt(n)  # exponential gaps: sd = mean
+
+
+def test_relative_minsup_is_exact_decimal_ceiling():
+    """Reading 8: minsup = ceil(rel D) computed on the decimal value of rel, at least 1: the workloads'
+    absolute minsups (100, 250, 30,000, 500), and cases where binary floating point would round wrong
+    (0.07 x 100 = 7.000000000000001 in doubles, whose ceiling is 8)."""
+    assert [synth.make_workload(n)["minsup"] for n in ("tiny", "sparse_mid", "dense_deep", "large_sparse")] == \
+        [100, 250, 30_000, 500]
+    assert synth.abs_minsup(0.07, 100) == 7
+    assert synth.abs_minsup(0.29, 100) == 29
+    assert synth.abs_minsup(0.071, 100) == 8
+    assert synth.abs_minsup(0.0001, 100) == 1
+    assert synth.abs_minsup(0.0, 100) == 1
