@@ -717,15 +717,21 @@ def cpu_baseline(w, bytes_alg_per_step, name):
     if D != w["D"]:
         bytes_alg_per_step, _ = oracle_bytes(off, items, w["N"], D, ms, w["word_bits"])
     cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    so, si, sp = oracle.eclat_mt(off, items, w["N"], ms, cores)
-    dt = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.eclat(off, items, w["N"], ms)
-    dt1 = time.perf_counter() - t0
+
+    def median_time(fn, budget_s):  # up to 5 runs within the time budget (at least one): their median
+        times = []
+        while len(times) < 5 and (not times or sum(times) + times[-1] <= budget_s):
+            t0 = time.perf_counter()
+            out = fn()
+            times.append(time.perf_counter() - t0)
+        return sorted(times)[len(times) // 2], len(times), out
+
+    dt, n_mt, (so, si, sp) = median_time(lambda: oracle.eclat_mt(off, items, w["N"], ms, cores), 5.0)
+    dt1, n_1, _ = median_time(lambda: oracle.eclat(off, items, w["N"], ms), 10.0)
     return {"value": round(bytes_alg_per_step / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "cpu": host_cpu(), "sample": f"{desc} ({len(sp)} itemsets) in {dt:.2f} s on {cores} threads ({dt1:.2f} s on one); GB/s "
-                      f"counts the bitmap path's algorithmic bytes for the same answer",
+            "cpu": host_cpu(), "sample": f"{desc} ({len(sp)} itemsets) in {dt:.2f} s on {cores} threads ({dt1:.2f} s on one); "
+                      f"medians of {n_mt} and {n_1} runs; GB/s counts the bitmap path's algorithmic bytes for the "
+                      f"same answer",
             "itemsets_per_s": round(len(sp) / dt, 1),
             "single_core": {"value": round(bytes_alg_per_step / dt1 / 1e9, 4), "unit": "GB/s", "cores": 1,
                             "itemsets_per_s": round(len(sp) / dt1, 1)}}

@@ -96,3 +96,19 @@ def test_algorithmic_work_counts_equal_a_literal_run():
             rank = np.zeros(N, dtype=np.int64)
             rank[order] = np.arange(len(order))
             assert bench.bitmap_work(so, si, rank) == _literal_bitmap_work(off, items, N, minsup), (trial, minsup)
+
+
+def test_cpu_baseline_record():
+    """The main arm's cpu_baseline: the oracle on every host core and on one, medians of up to 5 runs,
+    the host CPU named, in the metric's units."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2108_05038_gb300 import synth
+
+    w = synth.make_workload("tiny")
+    w["name"] = "tiny"
+    bytes_alg, _ = bench.oracle_bytes(w["offsets"], w["items"], w["N"], w["D"], w["minsup"], w["word_bits"])
+    cb = bench.cpu_baseline(w, bytes_alg, "tiny")
+    assert cb["kind"] == "oracle" and cb["unit"] == "GB/s" and cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] > 0 and cb["single_core"]["value"] > 0 and cb["single_core"]["cores"] == 1
+    assert "medians of" in cb["sample"] and "2624 itemsets" in cb["sample"] and cb["cpu"]
