@@ -187,3 +187,19 @@ int main(void) {
                            "-o", str(exe), lib_path, f"-Wl,-rpath,{libdir}"])
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def test_stored_expected_values_come_from_the_oracle_only():
+    """The script that writes tests/golden/digests.json imports the oracle, the input generator and the
+    canonical-form helper, and nothing of the CUDA path (no expected value comes from the GPU)."""
+    import ast
+
+    for rel in ("tests/golden/make_digests.py", "tests/canon.py"):
+        tree = ast.parse(open(os.path.join(ROOT, rel)).read())
+        names = set()
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                names |= {a.name for a in node.names}
+            elif isinstance(node, ast.ImportFrom):
+                names |= {f"{node.module}.{a.name}" for a in node.names}
+        assert not any("fim" in n.split(".")[-1] or "torch" in n or "_build" in n for n in names), (rel, names)
