@@ -32,19 +32,41 @@ import numpy as np  # noqa: E402
 from paper_2108_05038_gb300 import synth  # noqa: E402
 
 METRIC = "tidset AND+popc GB/s"
-WORKLOAD = "sparse_mid"  # the configuration the headline metric is quoted on; --workload picks another
+WORKLOAD = "large_sparse"  # the largest configuration (1M transactions, 1.25 GB of rows); --workload picks another
 SAMPLE_RATE = 0.01
 EST_SEED = 1
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one launch of the level-2 pair kernel, from one ncu capture of the mine's
-# launch per workload (dram__bytes_read.sum + dram__bytes_write.sum): the integer-pipe k_pair_counts,
-# and the tensor-core k_expand_e2m1 + k_pair_mma; None where none was taken
-PAIR_KERNEL_TRAFFIC = {"sparse_mid": 14_443_008, "large_sparse": 5_683_390_000}
-PAIR_MMA_TRAFFIC = {"large_sparse": 486_638_080 + 1_884_786_688 + 4_530_159_104 + 409_678_336,
-                    "sparse_mid": 12_402_176 + 189_952 + 51_629_056 + 0}
-# the same for the persistent DFS kernel
-DFS_KERNEL_TRAFFIC = {"large_sparse": 4_454_237_440 + 5_447_404_288}
+# DRAM traffic from one ncu launch-list capture of `bench.py --workload <w> --mode once` with the metrics
+# gpu__time_duration.sum, dram__bytes_read.sum and dram__bytes_write.sum (one pass; the summary under
+# profiles/ gives the command and the per-kernel figures): per launch of the pair step and of the DFS
+# stage, and for the whole step (build, estimate, mine).  A record is used only while the CUDA sources
+# hash to the SHA-256 it was captured with; otherwise the line reports no traffic and says why.
+CAPTURES = {}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
+
+
+def sources_sha256() -> str:
+    """SHA-256 over the CUDA sources and the ABI header (file names and contents, in name order)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    base = os.path.join(ROOT, "paper_2108_05038_gb300", "csrc")
+    files = sorted(f for f in os.listdir(base) if f.endswith((".cu", ".cuh")))
+    for f in files + ["../../include/fim.h"]:
+        h.update(f.encode())
+        with open(os.path.join(base, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured(workload):
+    """The DRAM-traffic record of a workload when it matches the current sources, else (None, reason)."""
+    rec = CAPTURES.get(workload)
+    if rec is None:
+        return None, f"no ncu capture of {workload}"
+    if rec["sources_sha256"] != sources_sha256():
+        return None, f"the CUDA sources changed since the ncu capture of {rec['date']} ({rec['summary']})"
+    return rec, f"ncu capture of {rec['date']} ({rec['summary']}), sources sha256 {rec['sources_sha256'][:12]}"
 
 
 def workload_desc(w):

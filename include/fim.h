@@ -76,10 +76,19 @@ typedef struct {
   float dfs_cta_busy_max_ms;     /* longest time a persistent DFS CTA was resident (collect_times)  */
   float dfs_cta_busy_mean_ms;    /* mean over the CTAs; max / mean is the load imbalance           */
   uint32_t pair_kernel;          /* level-2 kernel that ran: FIM_PAIR_CORES / _TENSOR / _TENSOR_E4M3 */
+  uint32_t n_proj_classes;       /* FIM_DFS_PROJECTED: one-item classes given their database part   */
+  uint64_t n_proj_splits;        /* frames handed to other warps with their own database part       */
+  uint64_t n_fallback_entries;   /* two-item classes mined by the sparse node mode instead           */
+  uint64_t bytes_projected;      /* FIM_DFS_PROJECTED: operand bytes in its own representation: the
+                                    class database parts built (each row read, one word gathered per
+                                    survivor and transaction, the bitmaps written), per class node its
+                                    prefix and candidates over its region's width, per compacted or
+                                    handed-out frame its gathered words and region                  */
 } fim_mine_stats;
 
 /* Traversal of the persistent DFS (fim_mine_opts.dfs_mode). */
-enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3, FIM_DFS_WARP = 4 };
+enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3, FIM_DFS_WARP = 4,
+       FIM_DFS_PROJECTED = 5 };
 
 /* Level-2 pair counts (fim_mine_opts.pair_kernel): FIM_PAIR_CORES: AND + popcount on the integer
  * pipes (8-word carry-save adder tree); FIM_PAIR_TENSOR: the 0/1 rows widened to 4-bit values
@@ -104,10 +113,17 @@ typedef struct {
                                   16-byte words, no donation (else as NODES); FIM_DFS_AUTO (2, the
                                   default): rows of at most 2,048 words (8 KB): the warp DFS when
                                   rows are at most 512 words and at least 1,024 rows are frequent,
-                                  else frames; wider rows: sparse nodes; FIM_DFS_WARP (4): one warp
+                                  else frames; wider rows: projected; FIM_DFS_WARP (4): one warp
                                   per two-item class, the
                                   prefix in its registers, no CTA-wide barrier; rows of at most 512
-                                  words, no donation (else as SPARSE)                              */
+                                  words, no donation (else as SPARSE); FIM_DFS_PROJECTED (5): the
+                                  database part of every one-item class [i | S_i] (the transactions
+                                  of i, and each survivor's bitmap over them: Phase 3 of Sec. 8.3
+                                  on the device) is built once, then one warp per two-item class
+                                  runs Eclat on those short bitmaps; classes beyond its budgets
+                                  (bitmaps of at most 1/4 of the frequent rows' bytes, stacks of
+                                  64K words per warp, doubled and the run repeated when too small)
+                                  are mined as SPARSE; same row limit and no donation as SPARSE  */
   uint32_t threads_per_cta;    /* persistent DFS CTA size, 128/256/512 (sparse nodes: at most 256;
                                   warp DFS: 256); 0 = sparse nodes: 256; other node modes: the one
                                   with the most CTAs per SM (then warps); frames: the most warps   */
@@ -133,6 +149,14 @@ typedef struct {
   uint64_t max_itemsets;       /* 0 = no limit; else mining stops as soon as more itemsets are found
                                   and the call returns FIM_ERR_OUTPUT_OVERFLOW (bounds the work of
                                   requests whose output explodes combinatorially)                  */
+  uint64_t proj_bitmap_words;  /* FIM_DFS_PROJECTED budgets (0 = automatic): the class bitmaps, in
+                                  32-bit words (classes past it, in queue order, are mined as SPARSE) */
+  uint64_t proj_stack_words;   /* first stack of one warp, in 32-bit words                         */
+  uint32_t proj_max_row_words; /* widest class bitmap (words) that is projected (default: 1/4 of the
+                                  stack)                                                            */
+  uint32_t proj_split_words;   /* a frame whose next level would read more 32-bit words than this is
+                                  handed to the other warps with its own database part (0 = automatic,
+                                  16,384)                                                           */
   /* outputs */
   uint64_t out_needed_sets;    /* on FIM_ERR_OUTPUT_OVERFLOW: capacities that would have sufficed */
   uint64_t out_needed_items;
@@ -336,7 +360,9 @@ void fim_server_free(fim_server* srv);
  * DEVICE buffers owned by the caller with room for `capacity` pairs; the
  * order of the pairs is unspecified.  *n_pairs (host) receives the number of
  * frequent pairs, also when it exceeds capacity (then FIM_ERR_OUTPUT_OVERFLOW
- * and only `capacity` of them are written).  The call synchronises db's stream.
+ * and only `capacity` of them are written).  The call makes db's device
+ * current while it runs (the caller's current device is restored on return)
+ * and synchronises db's stream.
  *
  * Scratch: one fixed array inside the library (4 MiB plus a little), held by
  * every GPU that loads the library until the process exits.  At most 1024
@@ -406,6 +432,16 @@ const char* fim_last_error(void);
  * each fim_plan_launch (the launches recorded while capturing it do not
  * count).  Kernels run by other libraries (memsets, copies) are not counted. */
 uint64_t fim_kernel_launches(void);
+
+/* Device memory of the library's stream-ordered pool on `device` (the pool
+ * every database, workspace and device result is carved from): *used_bytes =
+ * bytes handed out and not yet freed, *reserved_bytes = bytes the pool holds
+ * from the driver (freed blocks stay reserved for reuse).  Either pointer may
+ * be NULL.  A device whose pool was never created reports 0 and 0.  Not part
+ * of the thesis's method: it lets a serving process account for the memory
+ * of its mining jobs, and lets a test see that a call allocated nothing.
+ * Errors: FIM_ERR_INVALID (device ordinal out of range), FIM_ERR_CUDA. */
+fim_status fim_pool_memory(int device, uint64_t* used_bytes, uint64_t* reserved_bytes);
 
 #ifdef __cplusplus
 }

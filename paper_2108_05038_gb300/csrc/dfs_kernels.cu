@@ -160,7 +160,8 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
                               const uint32_t* __restrict__ eoff, uint32_t* __restrict__ sitems,
                               uint2* __restrict__ entries, uint64_t* __restrict__ out_off,
                               uint32_t* __restrict__ out_items, uint32_t* __restrict__ out_supp, uint64_t cap_sets,
-                              uint64_t cap_items, unsigned long long* __restrict__ class_sets) {
+                              uint64_t cap_items, unsigned long long* __restrict__ class_sets,
+                              const uint32_t* __restrict__ eoffx, uint2* __restrict__ entries_f) {
   __shared__ uint32_t wtot[33];
   const uint32_t q = blockIdx.x;
   const uint32_t i = row_order[q];
@@ -173,7 +174,11 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
     out_supp[i] = row_supp[i];
   }
   const uint32_t ne = scnt[i] > 0 ? scnt[i] - 1 : 0u;
-  for (uint32_t m = threadIdx.x; m < ne; m += blockDim.x) entries[eoff[q] + m] = make_uint2(i, m);
+  // the projected DFS splits the entries into its own queue and the fallback queue (bit 31 of eoffx)
+  const uint32_t ex = eoffx ? eoffx[q] : eoff[q];
+  uint2* const dst = (eoffx && (ex & 0x80000000u)) ? entries_f : entries;
+  const uint32_t e0 = eoffx ? (ex & 0x7fffffffu) : ex;
+  for (uint32_t m = threadIdx.x; m < ne; m += blockDim.x) dst[e0 + m] = make_uint2(i, m);
   uint32_t pos0 = 0;
   for (uint32_t base = i + 1; base < n1; base += blockDim.x) {
     uint32_t j = base + threadIdx.x;
@@ -1088,8 +1093,11 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
         atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
         stop = true;
       }
-      const uint32_t e = stop ? 0xffffffffu : atomicAdd(&p.ctrl->queue_head, 1u);
-      if (e < p.ctrl->n_entries) {
+      // (the projected mode's fallback queue when queue_sel is set)
+      uint32_t* const qhead = p.queue_sel ? &p.ctrl->queue_head_f : &p.ctrl->queue_head;
+      const uint32_t qlen = p.queue_sel ? p.ctrl->n_entries_f : p.ctrl->n_entries;
+      const uint32_t e = stop ? 0xffffffffu : atomicAdd(qhead, 1u);
+      if (e < qlen) {
         const uint2 en = p.entries[e];
         C.kind = 1; C.a = en.x; C.b = en.y; C.cls = en.x;
       }
@@ -1817,26 +1825,10 @@ __global__ void __launch_bounds__(kWarpDfsThreads) k_dfs_warp(const DfsArgs A) {
   }
 }
 
-// Raise a kernel's dynamic shared-memory limit to the device maximum once
-// (launches then pass their own size).  Setting it per launch to the launch's
-// size would race between threads mining concurrently.
-cudaError_t allow_max_smem(const void* func) {
-  static std::mutex mu;
-  static std::vector<const void*> done;
-  std::lock_guard<std::mutex> lock(mu);
-  for (const void* f : done)
-    if (f == func) return cudaSuccess;
-  int dev = 0, optin = 0;
-  cudaFuncAttributes fa{};
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
-  // static shared memory counts against the same per-block limit
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess) done.push_back(func);
-  return e;
-}
+// Raise a kernel's dynamic shared-memory limit to the device maximum once per device (launches then
+// pass their own size).  Setting it per launch to the launch's size would race between threads
+// mining concurrently.
+cudaError_t allow_max_smem(const void* func) { return kernel_smem_limit(func, -1); }
 
 template <int VEC, bool PSMEM>
 cudaError_t launch_dfs_t(const DfsArgs& a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
@@ -1957,7 +1949,7 @@ cudaError_t occ_warp(uint32_t stride, size_t smem, int* out) {
 
 }  // namespace
 
-cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
+cudaError_t launch_level2_counts(const LevelLaunch& p, cudaStream_t st) {
   if (p.n1 == 0) return cudaSuccess;
   k_surv_count<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.scnt, p.ctrl);
   note_launch();
@@ -1966,13 +1958,22 @@ cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
   k_level2_scan<<<1, 1024, 0, st>>>(p.scnt, p.row_order, p.n1, p.row_supp, p.minsup, p.soff, p.eoff, p.cap_sets,
                                     p.cap_items, p.ctrl);
   note_launch();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level2_fill(const LevelLaunch& p, cudaStream_t st) {
+  if (p.n1 == 0) return cudaSuccess;
   k_level2_fill<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.frows, p.row_supp, p.rank_item, p.row_order, p.scnt,
                                       p.soff, p.eoff, p.sitems, p.entries, p.out_off, p.out_items, p.out_supp,
-                                      p.cap_sets, p.cap_items, p.class_sets);
+                                      p.cap_sets, p.cap_items, p.class_sets, p.eoffx, p.entries_f);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st) {
+  cudaError_t e = launch_level2_counts(p, st);
+  if (e != cudaSuccess) return e;
+  return launch_level2_fill(p, st);
 }
 
 uint32_t dfs_sparse_cap(uint32_t stride) { return std::min<uint32_t>(kSparseCap, std::max<uint32_t>(32, stride / 4)); }

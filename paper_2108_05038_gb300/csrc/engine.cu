@@ -40,11 +40,14 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // (large_sparse's 1% sample: 2.38 ms against 3.64 ms in frame passes); short rows with few rows,
   // where the largest class's chain of dependent nodes sets the time, take frame passes, which
   // spread one frame over a whole CTA (sparse_mid's sample: 45 µs against 61 µs)
+  // wide rows (automatic) or FIM_DFS_PROJECTED: the projected DFS, with the sparse node mode (whose
+  // geometry ep->mode = 3 describes) mining the classes left out of the projection
   if (cfg.mode == 2)
     ep->mode = in.stride <= 2048 ? (warp_ok && n1 >= 1024 ? 4u : 1u) : (list_ok && !cfg.donate ? 3u : 0u);
-  else if (cfg.mode == 3) ep->mode = list_ok && !cfg.donate ? 3u : 0u;
+  else if (cfg.mode == 3 || cfg.mode == 5) ep->mode = list_ok && !cfg.donate ? 3u : 0u;
   else if (cfg.mode == 4) ep->mode = warp_ok ? 4u : (list_ok && !cfg.donate ? 3u : 0u);
   else ep->mode = cfg.mode == 1 ? 1u : 0u;
+  ep->proj = ep->mode == 3 && (cfg.mode == 5 || (cfg.mode == 2 && in.stride > 2048));
   ep->donate = ep->mode == 0 ? cfg.donate : 0u;  // only dense node expansion donates
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
@@ -155,6 +158,37 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   ep->pool_slots = ep->donate ? std::max<uint32_t>(8, ep->grid) : 0;
   ep->pool_slot_words = dfs_pool_slot_words(in.stride, ep->L, n1);
   if (ep->pool_slots) FIM_TRY(ws_get(ws, WS_POOL, ep->pool_slot_words * ep->pool_slots, &ep->d_pool));
+  if (ep->proj) {
+    // budgets of the class database parts: bitmaps up to a quarter of the frequent rows' bytes (at least
+    // 64 MB, at most 1/32 of device memory); transactions: every frequent row's support (the exact bound);
+    // a warp's stack takes eight prefixes of the widest projected class
+    ep->proj_y_cap = std::min<uint64_t>(db->total_mem / 128,
+                                        std::max<uint64_t>((uint64_t)n1 * in.stride / 4, 16ull << 20));
+    ep->proj_t_cap = 0;
+    for (uint32_t s : in.row_supp) ep->proj_t_cap += ((uint64_t)s + 3) & ~3ull;
+    ep->pstack_words = ((cfg.pstack_words ? cfg.pstack_words : kProjStackWords) + 31) & ~31ull;
+    ep->proj_w_cap = cfg.proj_w_cap ? cfg.proj_w_cap : (uint32_t)std::min<uint64_t>(ep->pstack_words / 4, 1u << 20);
+    if (cfg.proj_y_cap) ep->proj_y_cap = cfg.proj_y_cap;
+    ep->proj_smem = dfs_proj_smem_bytes(ep->L);
+    int pocc = 0;
+    FIM_CUDA(dfs_proj_ctas_per_sm(ep->proj_smem, &pocc));
+    if (pocc < 1) return fail(FIM_ERR_INVALID, "projected DFS kernel does not fit on an SM");
+    ep->proj_grid = (uint32_t)db->num_sms * (uint32_t)pocc;
+    uint32_t* meta = nullptr;
+    FIM_TRY(ws_get(ws, WS_PROJ_META, 6ull * n1 + 2, &meta));
+    ep->d_yoff = reinterpret_cast<uint64_t*>(meta);
+    ep->d_toff = ep->d_yoff + n1;
+    ep->d_itemoff = meta + 4ull * n1;
+    ep->d_eoffx = ep->d_itemoff + n1 + 1;
+    FIM_TRY(ws_get(ws, WS_ENTRIES_F, ep->npairs_max + 1, &ep->d_entries_f));
+    // the arena holds the class regions (within proj_y_cap), then the regions of split frames
+    ep->proj_arena_words = ep->proj_y_cap + std::max<uint64_t>(ep->proj_y_cap, 16ull << 20);
+    ep->split_words = cfg.split_words ? cfg.split_words : kProjSplitWords;
+    ep->dq_cap = kProjDqCap;
+    FIM_TRY(ws_get(ws, WS_PROJ_Y, ep->proj_arena_words, &ep->d_Y));
+    FIM_TRY(ws_get(ws, WS_PROJ_DQ, ep->dq_cap, &ep->d_dq));
+    FIM_TRY(ws_get(ws, WS_PROJ_T, std::max<uint64_t>(4, ep->proj_t_cap), &ep->d_T));
+  }
   if (cfg.collect_times)
     for (auto& e : ep->ev) FIM_CUDA(cudaEventCreate(&e));
   return FIM_OK;
@@ -168,7 +202,10 @@ fim_status engine_alloc(Workspace& ws, EnginePlan* ep) {
   }
   if (ep->n1 >= 3)
     FIM_TRY(ws_get(ws, WS_ARENA, dfs_arena_cta_words(ep->stride, ep->n1, ep->maxd, ep->mode) * ep->grid, &ep->d_arena));
-  if (ep->n1 >= 3 && ep->ev[0]) FIM_TRY(ws_get(ws, WS_CTATIME, 2ull * ep->grid, &ep->d_cta_time));
+  if (ep->n1 >= 3 && ep->proj)
+    FIM_TRY(ws_get(ws, WS_PSTACK, (uint64_t)ep->proj_grid * (kProjThreads / 32) * ep->pstack_words, &ep->d_pstack));
+  if (ep->n1 >= 3 && ep->ev[0])
+    FIM_TRY(ws_get(ws, WS_CTATIME, 2ull * std::max(ep->grid, ep->proj_grid), &ep->d_cta_time));
   return FIM_OK;
 }
 
@@ -197,7 +234,23 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
                  ep.d_soff, ep.d_eoff, ep.d_sitems, ep.d_entries, ep.d_off, ep.d_items, ep.d_supp,
                  ep.count_only ? 0ull : ep.cap_sets, ep.count_only ? 0ull : ep.cap_items, ep.d_ctrl,
                  ep.d_class_sets};
-  ce = launch_level2(ll, st);
+  ProjLaunch pj{};
+  if (ep.proj && ep.n1 >= 3) {
+    // level-2 counts, the projection plan (which classes get their database part, and the split of the
+    // queue), then the queue fill
+    pj = ProjLaunch{ep.bits, ep.stride, ep.d_frows, ep.d_rsupp, ep.d_order, ep.d_scnt, ep.d_soff, ep.d_sitems,
+                    ep.d_rank_item, ep.n1, ep.proj_y_cap, ep.proj_t_cap, ep.proj_w_cap, ep.d_yoff, ep.d_toff,
+                    ep.d_itemoff, ep.d_eoffx, ep.d_Y, ep.d_T, ep.d_ctrl};
+    ce = launch_level2_counts(ll, st);
+    if (ce != cudaSuccess) return ce;
+    ce = launch_proj_plan(pj, st);
+    if (ce != cudaSuccess) return ce;
+    ll.eoffx = ep.d_eoffx;
+    ll.entries_f = ep.d_entries_f;
+    ce = launch_level2_fill(ll, st);
+  } else {
+    ce = launch_level2(ll, st);
+  }
   if (ce != cudaSuccess) return ce;
   if (ep.ev[2]) cudaEventRecord(ep.ev[2], st);
   if (ep.n1 >= 3) {
@@ -231,6 +284,29 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.class_work = ep.d_class_work;
     dl.max_sets = ep.max_sets;
     dl.cta_time = ep.d_cta_time;
+    if (ep.proj) {
+      // Phase 3 (the classes' database parts), Phase 4 (one warp per two-item class), then the sparse
+      // node mode on the classes left out
+      ce = launch_proj_build(pj, ep.num_sms, st);
+      if (ce != cudaSuccess) return ce;
+      ce = cudaMemsetAsync(ep.d_dq, 0, (size_t)ep.dq_cap * sizeof(uint4), st);  // no slot published yet
+      if (ce != cudaSuccess) return ce;
+      DfsLaunch dp = dl;
+      dp.row_supp = ep.d_rsupp;
+      dp.yoff = ep.d_yoff;
+      dp.Y = ep.d_Y;
+      dp.pstack = ep.d_pstack;
+      dp.pstack_words = ep.pstack_words;
+      dp.dq = ep.d_dq;
+      dp.dq_cap = ep.dq_cap;
+      dp.arena_words = ep.proj_arena_words;
+      dp.split_words = ep.split_words;
+      ce = launch_dfs_proj(dp, ep.proj_grid, ep.L, st);
+      if (ce != cudaSuccess) return ce;
+      dl.entries = ep.d_entries_f;
+      dl.queue_sel = 1;
+      dl.cta_time = nullptr;
+    }
     ce = launch_dfs(dl, ep.grid, ep.threads, ep.vec, ep.smem, ep.psmem, ep.L, ep.mode, st);
     if (ce != cudaSuccess) return ce;
   }
@@ -278,6 +354,16 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
   if (h.err & DEV_ERR_TIMEOUT) return fail(FIM_ERR_TIMEOUT, "persistent kernel: bounded wait ran out without progress");
   if ((h.err & DEV_ERR_ABORTED) || (ep->max_sets && h.sets_total > ep->max_sets))
     return fail(FIM_ERR_OUTPUT_OVERFLOW, "more frequent itemsets than the limit: mining stopped early (counts are lower bounds)");
+  if (h.err & DEV_ERR_PSTACK) {  // a warp's stack of the projected DFS was too small: double it and repeat
+    // (at least twice the largest stack a class asked for before the warps stopped)
+    // (a multiple of 32 words, so every warp's stack starts on a 128-byte line)
+    const uint64_t next = (std::max<uint64_t>(ep->pstack_words * 2, 2ull * h.pstack_need) + 31) & ~31ull;
+    if (next * ep->proj_grid * (kProjThreads / 32) * 4 > db->total_mem / 8)
+      return fail(FIM_ERR_OOM, "projected DFS: the warps' stacks would exceed 1/8 of device memory");
+    ep->pstack_words = next;
+    *retry = true;
+    return FIM_OK;
+  }
   if (h.err & DEV_ERR_DEPTH) {
     if (ep->maxd >= ep->maxd_full) return fail(FIM_ERR_INVALID, "itemset longer than the depth bound of the DFS stack");
     ep->maxd = ep->maxd_full;  // deeper than the first stack: repeat with the full bound
@@ -315,7 +401,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     stats->n_pair_intersections = ep->npairs_max;
     stats->n_intersections = ep->npairs_max + h.n_intersections;
     stats->n_classes = h.n_nodes;
-    stats->n_queue_entries = h.n_entries;
+    stats->n_queue_entries = h.n_entries + (ep->proj ? h.n_entries_f : 0u);
     stats->n_donations = h.n_donations;
     // sibling operand per intersection + one prefix read per class node + materialised prefixes
     stats->bytes_pair_kernel = ep->npairs_max * rb + (uint64_t)(n1 > 0 ? n1 - 1 : 0) * rb;
@@ -325,23 +411,28 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     stats->threads_per_cta = ep->threads;
     stats->vec_per_lane = ep->vec;
     stats->pair_kernel = !ep->pair_mma ? FIM_PAIR_CORES : ep->pair_e2m1 ? FIM_PAIR_TENSOR : FIM_PAIR_TENSOR_E4M3;
+    stats->n_proj_classes = ep->proj ? h.n_proj_classes : 0u;
+    stats->n_proj_splits = ep->proj ? h.proj_splits : 0u;
+    stats->n_fallback_entries = ep->proj ? h.n_entries_f : 0u;
+    stats->bytes_projected = ep->proj ? h.proj_bytes : 0u;
     if (ep->ev[0] && n1 > 0) {
       stats->ms_pair_kernel = ep->ms_pair;  // the one pair-kernel launch of this mine
       cudaEventElapsedTime(&stats->ms_dfs_kernel, ep->ev[2], ep->ev[3]);  // the last DFS run
       stats->ms_device_total = ep->ms_total;  // every launch, repeated runs included
     }
-    if (ep->d_cta_time && ep->grid) {  // load balance of the persistent DFS: busy time per CTA
-      std::vector<unsigned long long> t(2ull * ep->grid);
+    const uint32_t tgrid = ep->proj ? ep->proj_grid : ep->grid;  // CTAs whose times were recorded
+    if (ep->d_cta_time && tgrid) {  // load balance of the persistent DFS: busy time per CTA
+      std::vector<unsigned long long> t(2ull * tgrid);
       FIM_CUDA(cudaMemcpyAsync(t.data(), ep->d_cta_time, t.size() * 8, cudaMemcpyDeviceToHost, st));
       FIM_CUDA(cudaStreamSynchronize(st));
       double sum = 0.0, mx = 0.0;
-      for (uint32_t c = 0; c < ep->grid; ++c) {
+      for (uint32_t c = 0; c < tgrid; ++c) {
         const double b = t[2 * c + 1] > t[2 * c] ? (double)(t[2 * c + 1] - t[2 * c]) * 1e-6 : 0.0;
         sum += b;
         mx = std::max(mx, b);
       }
       stats->dfs_cta_busy_max_ms = (float)mx;
-      stats->dfs_cta_busy_mean_ms = (float)(sum / ep->grid);
+      stats->dfs_cta_busy_mean_ms = (float)(sum / tgrid);
     }
   }
   return FIM_OK;
@@ -356,7 +447,7 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
   ep.count_only = cfg.count_only;
   ep.class_out = cfg.class_out;
   ep.max_sets = cfg.max_sets;
-  for (int attempt = 0; s == FIM_OK && attempt < 4; ++attempt) {
+  for (int attempt = 0; s == FIM_OK && attempt < 8; ++attempt) {
     if ((s = engine_alloc(ws, &ep)) != FIM_OK) break;
     cudaError_t ce = engine_launch(ep, ws.stream);
     if (ce != cudaSuccess) {
@@ -366,7 +457,7 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
     bool retry = false;
     s = engine_finish(db, ws.stream, &ep, out, stats, &retry);
     if (s != FIM_OK || !retry) break;
-    if (attempt == 3) s = fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity still exceeded after regrowth");
+    if (attempt == 7) s = fail(FIM_ERR_OUTPUT_OVERFLOW, "output capacity still exceeded after regrowth");
     ep.skip_pairs = true;  // the pair counts in the workspace stay valid: only the later stages repeat
   }
   ep.skip_pairs = false;

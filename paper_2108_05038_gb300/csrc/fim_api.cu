@@ -17,6 +17,30 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void note_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Function attributes belong to the device that is current when they are set, so they are set once
+// per (device, kernel).
+cudaError_t kernel_smem_limit(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& d : done)
+    if (d.first == dev && d.second == func) return cudaSuccess;
+  if (bytes < 0) {  // the device maximum, less the kernel's static shared memory
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    bytes = optin - (int)fa.sharedSizeBytes;
+  }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.emplace_back(dev, func);
+  return e;
+}
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -381,6 +405,10 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->pair_kernel = o->pair_kernel;
   c->fault_pair_wait = o->fault_pair_wait;
   c->max_sets = o->max_itemsets;
+  c->proj_y_cap = o->proj_bitmap_words;
+  c->pstack_words = o->proj_stack_words;
+  c->proj_w_cap = o->proj_max_row_words;
+  c->split_words = o->proj_split_words;
   c->spin_limit = o->spin_limit;
   c->cap_sets = o->out_capacity_sets;
   c->cap_items = o->out_capacity_items;
@@ -507,6 +535,24 @@ const char* fim_status_str(fim_status s) {
 const char* fim_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t fim_kernel_launches(void) { return launches_so_far(); }
+
+fim_status fim_pool_memory(int device, uint64_t* used_bytes, uint64_t* reserved_bytes) {
+  if (used_bytes) *used_bytes = 0;
+  if (reserved_bytes) *reserved_bytes = 0;
+  if (device < 0 || device >= 64) return fail(FIM_ERR_INVALID, "device ordinal out of range");
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    pool = g_pools[device];
+  }
+  if (!pool) return FIM_OK;
+  uint64_t used = 0, reserved = 0;
+  FIM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  FIM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  if (used_bytes) *used_bytes = used;
+  if (reserved_bytes) *reserved_bytes = reserved;
+  return FIM_OK;
+}
 
 fim_status fim_build_vertical_db(const uint32_t* tx_offsets, const uint32_t* tx_items, uint32_t D, uint32_t N,
                                  uint32_t word_bits, uint32_t prefilter_minsup, void* cuda_stream, fim_db** out) {

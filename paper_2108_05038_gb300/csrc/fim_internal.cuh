@@ -15,6 +15,9 @@ namespace fim {
 // kernels put on a stream by this library (fim_kernel_launches)
 void note_launch(uint64_t n = 1);
 uint64_t launches_so_far();
+// raise a kernel's dynamic shared-memory limit on the current device, once per (device, kernel);
+// bytes < 0: the device's opt-in maximum less the kernel's static shared memory
+cudaError_t kernel_smem_limit(const void* func, int bytes);
 
 // ---------------------------------------------------------------------------
 // error reporting
@@ -48,6 +51,7 @@ enum : uint32_t {
   DEV_ERR_OVERFLOW = 1u << 4,     // output capacity exceeded (counts keep going)
   DEV_ERR_POOL = 1u << 5,         // donation pool protocol violated
   DEV_ERR_ABORTED = 1u << 6,      // more itemsets than the caller's limit: mining stopped early
+  DEV_ERR_PSTACK = 1u << 7,       // projected DFS: a warp's stack was too small (grown and repeated)
 };
 
 // ---------------------------------------------------------------------------
@@ -105,6 +109,13 @@ enum WsSlot {
   WS_DB_TXITEMS,
   WS_DB_BITS,
   WS_DB_SMALL,  // item_rank (N) | rank_item (rows) | supp (rows) | iota (rows), each 16-byte aligned
+  // projected DFS: per-class database parts and the warps' stacks
+  WS_PROJ_META,  // yoff (n1 u64) | toff (n1 u64) | itemoff (n1 + 1 u32) | eoffx (n1 u32)
+  WS_PROJ_Y,     // bitmaps of every class's survivors over the class's transactions
+  WS_PROJ_T,     // the transactions (tids) of every projected class
+  WS_PSTACK,     // per-warp DFS stacks
+  WS_ENTRIES_F,  // queue of the two-item classes whose class was not projected
+  WS_PROJ_DQ,    // queue of the children of split frames
   WS_COUNT
 };
 
@@ -126,7 +137,12 @@ struct alignas(128) DevCtrl {
   // line 1: static queue
   alignas(128) uint32_t queue_head;  // next static queue entry
   uint32_t n_entries;                // static queue length (written by the scan kernel)
-  uint32_t pad1[30];
+  uint32_t queue_head_f;             // projected DFS: next entry of the fallback queue
+  uint32_t n_entries_f;              // its length
+  uint32_t n_proj_classes;           // classes whose database part was built
+  uint32_t n_proj_items;             // work items of the projection
+  uint32_t pstack_need;              // largest warp stack (words) a projected class asked for
+  uint32_t pad1[25];
   // line 2: termination and progress (polled)
   alignas(128) uint32_t pending;     // unfinished queue entries
   uint32_t progress;                 // nodes finished (any CTA), the no-progress timer's clock
@@ -140,6 +156,15 @@ struct alignas(128) DevCtrl {
   // line 4: node count (stats)
   alignas(128) unsigned long long n_nodes;
   uint32_t pad4[30];
+  // line 5: projected DFS work sharing: the queue of split frames' children, unfinished items, and the
+  // bump pointer of the region arena
+  alignas(128) uint32_t dq_head;     // next item to take
+  uint32_t dq_tail;                  // items reserved by producers
+  uint32_t proj_pending;             // items (static or split) not yet finished
+  uint32_t proj_splits;              // frames split into regions (stats)
+  unsigned long long arena_top;      // words of the region arena in use
+  unsigned long long proj_bytes;     // operand bytes of the projected DFS (stats)
+  uint32_t pad5[24];
 };
 
 // ---------------------------------------------------------------------------
@@ -250,6 +275,12 @@ struct EngineConfig {
   bool count_only = false;                   // count itemsets, write no records (no output buffers)
   std::vector<unsigned long long>* class_out = nullptr;  // host copy of class_sets / class_work (n1 entries)
   uint64_t max_sets = 0;                     // 0 = no limit; else stop early past this many itemsets
+  // projected DFS (0 = automatic): a warp's first stack (words), the widest projected class bitmap
+  // (words), the budget of the class bitmaps (words)
+  uint64_t pstack_words = 0;
+  uint32_t proj_w_cap = 0;
+  uint64_t proj_y_cap = 0;
+  uint64_t split_words = 0;  // 0 = automatic; else a frame whose next level reads more words is split
 };
 
 // Everything one mining call launches, with its geometry and buffers.  The
@@ -279,6 +310,18 @@ struct EnginePlan {
   bool pair_e2m1 = true;    // tensor-core operands packed as e2m1 (else e4m3)
   uint32_t pair_extra_tx = 0;  // test: bytes a stage waits for beyond its copies (0 normally)
   uint8_t* d_X = nullptr;   // widened rows (pair_mma only)
+  // projected DFS (mode 5): budgets, geometry and buffers; the fallback runs the sparse node mode with
+  // the geometry above
+  bool proj = false;
+  uint64_t proj_y_cap = 0, proj_t_cap = 0, pstack_words = 0;
+  uint32_t proj_w_cap = 0, proj_grid = 0;
+  size_t proj_smem = 0;
+  uint64_t *d_yoff = nullptr, *d_toff = nullptr;
+  uint32_t *d_itemoff = nullptr, *d_eoffx = nullptr, *d_Y = nullptr, *d_T = nullptr, *d_pstack = nullptr;
+  uint2* d_entries_f = nullptr;
+  uint4* d_dq = nullptr;
+  uint32_t dq_cap = 0;
+  uint64_t proj_arena_words = 0, split_words = 0;
   float ms_pair = 0.f, ms_total = 0.f;  // device time of the pair kernel / of all launches so far
   unsigned long long* d_cta_time = nullptr;  // per-CTA [start, end] of the DFS (with timing only)
   // buffers
@@ -365,8 +408,16 @@ struct LevelLaunch {
   uint64_t cap_sets, cap_items;
   DevCtrl* ctrl;
   unsigned long long* class_sets;  // optional: frequent itemsets per top class
+  const uint32_t* eoffx;           // optional (projected DFS): entry offset per queue position, bit 31 =
+                                   // the class's entries go to the fallback queue entries_f
+  uint2* entries_f;
 };
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st);
+// the level-2 kernels up to the entry offsets, and the fill kernel alone (the projected DFS plans its
+// classes between the two)
+cudaError_t launch_level2_counts(const LevelLaunch& p, cudaStream_t st);
+cudaError_t launch_level2_fill(const LevelLaunch& p, cudaStream_t st);
+
 
 struct DfsLaunch {
   const uint32_t* bits;
@@ -397,7 +448,57 @@ struct DfsLaunch {
   unsigned long long* cta_time;    // optional: [start, end] global time (ns) of every CTA
   unsigned long long* class_sets;  // optional: frequent itemsets per top class
   const uint32_t* C2;              // level-2 pair counts (n1 x n1): supports of the root prefixes
+  uint32_t queue_sel;              // 0: the main queue; 1: the projected mode's fallback queue
+  // projected DFS (mode 5) only
+  const uint32_t* row_supp;        // support of every frequent row (n1)
+  const uint64_t* yoff;            // word offset of class i's bitmaps in Y (~0 = not projected)
+  const uint32_t* Y;               // the classes' bitmaps
+  uint32_t* pstack;                // per-warp stacks
+  uint64_t pstack_words;           // words of one warp's stack
+  uint4* dq;                       // queue of split frames' children: (region offset, m, ready) per slot
+  uint32_t dq_cap;                 // its slots
+  uint64_t arena_words;            // words of Y (class regions, then split regions)
+  uint64_t split_words;            // a frame whose next level reads more words than this is split
 };
+
+// Projected DFS (mode 5): the database part of every one-item class (its transactions and its
+// survivors' bitmaps over them), then one warp per two-item class running Eclat on those bitmaps.
+struct ProjLaunch {
+  const uint32_t* bits;
+  uint32_t stride;
+  const uint32_t* frows;
+  const uint32_t* row_supp;
+  const uint32_t* row_order;  // queue position -> class
+  const uint32_t* scnt;
+  const uint32_t* soff;
+  const uint32_t* sitems;
+  const uint32_t* rank_item;  // row -> original item id
+  uint32_t n1;
+  uint64_t y_cap_words;  // budget of Y (words)
+  uint64_t t_cap;        // budget of T (tids)
+  uint32_t w_cap;        // widest bitmap of a projected class (words)
+  uint64_t* yoff;        // n1, by class
+  uint64_t* toff;        // n1, by class
+  uint32_t* itemoff;     // n1 + 1, by queue position
+  uint32_t* eoffx;       // n1, by queue position
+  uint32_t* Y;
+  uint32_t* T;
+  DevCtrl* ctrl;
+};
+cudaError_t launch_proj_plan(const ProjLaunch& q, cudaStream_t st);
+cudaError_t launch_proj_build(const ProjLaunch& q, int num_sms, cudaStream_t st);
+cudaError_t launch_dfs_proj(const DfsLaunch& p, uint32_t grid, uint32_t max_len, cudaStream_t st);
+size_t dfs_proj_smem_bytes(uint32_t max_len);
+cudaError_t dfs_proj_ctas_per_sm(size_t smem, int* out);
+constexpr uint32_t kProjThreads = 256;     // projected DFS: 8 warps per CTA
+constexpr uint32_t kProjCtasPerSm = 4;     // at most 32 warps per SM (their stacks take device memory)
+constexpr uint64_t kProjStackWords = 65536;  // first stack of one warp (doubled when a run needs more)
+constexpr uint32_t kProjDqCap = 1u << 18;     // items of split frames the queue holds
+constexpr uint64_t kProjSplitWords = 1u << 14;  // next-level words above which a frame is handed out
+// words of a class region's header, prefix ids and row ids (its rows start there)
+__host__ __device__ inline uint64_t region_rows_off(uint32_t xlen, uint32_t k) {
+  return 8ull + (((uint64_t)xlen + 3) & ~3ull) + (((uint64_t)k + 3) & ~3ull);
+}
 // grid: number of persistent CTAs; threads: CTA size; vec: 16-byte loads per lane per piece
 // mode 0: node at a time (optionally with donation); mode 1: frame passes (all children of a frame together)
 cudaError_t launch_dfs(const DfsLaunch& p, uint32_t grid, uint32_t threads, uint32_t vec, size_t smem,

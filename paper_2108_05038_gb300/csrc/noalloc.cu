@@ -28,16 +28,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 uint32_t* g_scratch_ptr[kMaxDevices] = {};
 
+// (called with `dev` current)
 fim_status scratch_on_device(int dev, uint32_t** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(FIM_ERR_INVALID, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
-    int cur = -1;
-    FIM_CUDA(cudaGetDevice(&cur));
-    if (cur != dev) FIM_CUDA(cudaSetDevice(dev));
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_pair_scratch);
-    if (cur != dev) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_pair_scratch)");
     g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
   }
@@ -89,6 +86,17 @@ extern "C" fim_status fim_mine_pairs_noalloc(const fim_db* db, uint32_t minsup_a
                                      " frequent items exceed its fixed scratch of " +
                                      std::to_string(kNoAllocMaxRows) + " items; use fim_mine");
   if (n1 < 2) return FIM_OK;
+  // the whole call runs on db's device, which is made current for it; the caller's current device
+  // comes back on return
+  int caller_dev = -1;
+  FIM_CUDA(cudaGetDevice(&caller_dev));
+  struct Restore {
+    int dev, cur;
+    ~Restore() {
+      if (dev != cur) cudaSetDevice(dev);
+    }
+  } restore{caller_dev, db->device};
+  if (caller_dev != db->device) FIM_CUDA(cudaSetDevice(db->device));
   uint32_t* scratch = nullptr;
   FIM_TRY(scratch_on_device(db->device, &scratch));
   uint32_t* C2 = scratch;

@@ -175,16 +175,15 @@ double pair_cores_cost_us(uint32_t n1, uint32_t stride, int num_sms) {
 
 cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used) {
   if (p.n1 < 2) { *ksplit_used = 0; return cudaSuccess; }
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
+  cudaError_t attr_err = kernel_smem_limit(reinterpret_cast<const void*>(k_pair_counts), (int)kSmemBytes);
+  if (attr_err != cudaSuccess) return attr_err;
+  static std::once_flag once;  // resident CTAs per SM: the same on every GB300 of the process
   static int occ = 0;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_pair_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_counts, kThreads, kSmemBytes);
-    if (occ < 1) occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_counts, kThreads, kSmemBytes) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
   });
-  if (attr_err != cudaSuccess) return attr_err;
   const uint32_t nb = (p.n1 + kTile - 1) / kTile;
   const uint32_t tiles = nb * (nb + 1) / 2;
   const uint32_t nchunks = p.stride / kChunk;  // stride is a multiple of 32 words

@@ -447,13 +447,9 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t
     *ksplit_used = 0;
     return cudaSuccess;
   }
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_pair_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(k_pair_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  });
+  cudaError_t attr_err = kernel_smem_limit(reinterpret_cast<const void*>(k_pair_mma<false>), (int)kSmemBytes);
+  if (attr_err == cudaSuccess)
+    attr_err = kernel_smem_limit(reinterpret_cast<const void*>(k_pair_mma<true>), (int)kSmemBytes);
   if (attr_err != cudaSuccess) return attr_err;
   EncodeTiled encode = nullptr;
   cudaError_t e = encoder(&encode);

@@ -28,7 +28,7 @@ EXPORTED = [
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
     "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free", "fim_kernel_launches",
-    "fim_extension_supports", "fim_result_flags",
+    "fim_extension_supports", "fim_result_flags", "fim_pool_memory",
 ]
 
 
@@ -52,6 +52,8 @@ class MineStats(ctypes.Structure):
         ("threads_per_cta", ctypes.c_uint32), ("vec_per_lane", ctypes.c_uint32), ("ms_pair_kernel", ctypes.c_float),
         ("ms_dfs_kernel", ctypes.c_float), ("ms_device_total", ctypes.c_float),
         ("dfs_cta_busy_max_ms", ctypes.c_float), ("dfs_cta_busy_mean_ms", ctypes.c_float), ("pair_kernel", ctypes.c_uint32),
+        ("n_proj_classes", ctypes.c_uint32), ("n_proj_splits", ctypes.c_uint64), ("n_fallback_entries", ctypes.c_uint64),
+        ("bytes_projected", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -66,6 +68,8 @@ class MineOpts(ctypes.Structure):
         ("dfs_depth_first", ctypes.c_uint32), ("pair_kernel", ctypes.c_uint32), ("fault_pair_wait", ctypes.c_uint32),
         ("out_capacity_sets", ctypes.c_uint64),
         ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("max_itemsets", ctypes.c_uint64),
+        ("proj_bitmap_words", ctypes.c_uint64), ("proj_stack_words", ctypes.c_uint64),
+        ("proj_max_row_words", ctypes.c_uint32), ("proj_split_words", ctypes.c_uint32),
         ("out_needed_sets", ctypes.c_uint64),
         ("out_needed_items", ctypes.c_uint64), ("stats", ctypes.POINTER(MineStats)),
         ("class_work_out", ctypes.c_void_p),
@@ -153,6 +157,8 @@ def load(build_if_stale: bool = True):
         lib.fim_last_error.argtypes = []
         lib.fim_kernel_launches.restype = u64
         lib.fim_kernel_launches.argtypes = []
+        lib.fim_pool_memory.restype = i32
+        lib.fim_pool_memory.argtypes = [i32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         _lib = lib
         return lib
 
@@ -333,7 +339,9 @@ class Database:
              ctas_per_sm: int = 0, donate: bool = False, result_on_device: bool = False, collect_times: bool = False,
              out_capacity_sets: int = 0, out_capacity_items: int = 0, spin_limit: int = 0, stats: bool = True,
              shape=None, dfs_mode: int | None = None, max_itemsets: int = 0, class_work: bool = False,
-             dfs_depth_first: int = 0, pair_kernel: int = FIM_PAIR_AUTO, fault_pair_wait: bool = False):
+             dfs_depth_first: int = 0, pair_kernel: int = FIM_PAIR_AUTO, fault_pair_wait: bool = False,
+             proj_bitmap_words: int = 0, proj_stack_words: int = 0, proj_max_row_words: int = 0,
+             proj_split_words: int = 0):
         """fim_mine; with ``class_work`` the result carries ``class_work`` (u64[n_rows]): the intersections
         of every one-row class, level 2 and below."""
         opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
@@ -341,6 +349,10 @@ class Database:
                               max_itemsets, pair_kernel)
         opts.dfs_depth_first = dfs_depth_first
         opts.fault_pair_wait = 1 if fault_pair_wait else 0
+        opts.proj_bitmap_words = proj_bitmap_words
+        opts.proj_stack_words = proj_stack_words
+        opts.proj_max_row_words = proj_max_row_words
+        opts.proj_split_words = proj_split_words
         cw = None
         if class_work:
             cw = np.zeros(max(1, self.info()["n_rows"]), dtype=np.uint64)
@@ -454,6 +466,14 @@ def build_vertical_db_device(d_tx_offsets, d_tx_items, D: int, N: int, word_bits
 def kernel_launches() -> int:
     """fim_kernel_launches: kernels this library has put on a stream so far (graph replays included)."""
     return int(load().fim_kernel_launches())
+
+
+def pool_memory(device: int = 0):
+    """fim_pool_memory: (bytes in use, bytes reserved) of the library's device memory pool."""
+    lib = load()
+    used, reserved = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib, lib.fim_pool_memory(device, ctypes.byref(used), ctypes.byref(reserved)), "fim_pool_memory")
+    return used.value, reserved.value
 
 
 def status_str(status: int) -> str:

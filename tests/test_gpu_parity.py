@@ -77,7 +77,7 @@ def test_random_tiny_vs_bruteforce(seed):
     for minsup in sorted({1, 2, max(1, D // 7), max(1, D // 2)}):
         want = odict(oracle.bruteforce(off, items, N, minsup))
         got = gpu_mine(off, items, N, minsup, word_bits=32 if seed % 2 else 64,
-                       dfs_mode=(0, 1, 3, 4)[(seed // 2) % 4]).as_dict()
+                       dfs_mode=(0, 1, 3, 4, 5)[(seed // 2) % 5]).as_dict()
         assert_same(got, want)
 
 
@@ -92,7 +92,7 @@ def test_ragged_D(D):
 
 
 @pytest.mark.parametrize("k,mode,depth", [(11, 0, 0), (16, 0, 8), (11, 1, 4), (16, 1, 0), (11, 3, 0), (16, 3, 4),
-                                          (11, 4, 0), (16, 4, 4)])
+                                          (11, 4, 0), (16, 4, 4), (11, 5, 0), (16, 5, 4)])
 def test_identical_transactions_closed_form(k, mode, depth):
     """2^k - 1 itemsets of support D; with a first DFS stack of 4 or 8 the depth of 9 or 14 forces the
     regrown retry, with 0 the stack has the full depth at once."""
@@ -102,7 +102,7 @@ def test_identical_transactions_closed_form(k, mode, depth):
     assert len(got) == 2 ** k - 1 and set(got.values()) == {D}
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
 def test_single_and_empty_transactions(mode):
     """One transaction of 5 items: every non-empty subset (31) with support 1; only empty transactions:
     nothing is frequent (no item has support); one item in every transaction: only that singleton."""
@@ -175,7 +175,8 @@ def test_invalid_device_offsets_rejected_before_reading_items(offsets, why):
 # ---------------------------------------------------------------- named workloads
 
 @pytest.mark.parametrize("name,mode", [("tiny", 0), ("dense_deep", 0), ("dense_exact37", 0), ("tiny", 1), ("tiny", 4),
-                                       ("dense_deep", 1), ("tiny", 3), ("dense_deep", 3)])
+                                       ("dense_deep", 1), ("tiny", 3), ("dense_deep", 3), ("tiny", 5),
+                                       ("dense_deep", 5)])
 def test_workload_full_size_exact(name, mode):
     w = synth.make_workload(name)
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
@@ -183,7 +184,7 @@ def test_workload_full_size_exact(name, mode):
     assert_same(got, want)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("mode", [0, 1, 3, 5])
 def test_sparse_mid_full_size_exact(mode):
     w = synth.make_workload("sparse_mid")
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
@@ -299,7 +300,7 @@ def test_fixed_capacity_overflow_then_retry():
     assert_same(got, want)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
 def test_itemset_limit_aborts_early(mode):
     """max_itemsets stops the mine once the output passes it (FIM_ERR_OUTPUT_OVERFLOW); the db stays usable."""
     off, items = csr([list(range(20))] * 50 + [[20]])
@@ -312,7 +313,7 @@ def test_itemset_limit_aborts_early(mode):
     assert len(got) == 2 ** 20 - 1
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
 def test_output_regrowth_reuses_pair_counts(mode):
     """2^20 - 1 itemsets of length up to 20 overflow the first output buffer and a 3-deep first DFS
     stack: the repeated runs skip the pair kernel (its counts stay in the workspace) and still give
@@ -327,7 +328,7 @@ def test_output_regrowth_reuses_pair_counts(mode):
     assert st["ms_pair_kernel"] > 0 and st["ms_device_total"] >= st["ms_dfs_kernel"] > 0
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4, 5])
 def test_cta_busy_times_are_consistent(mode):
     """collect_times records every persistent CTA's resident time: 0 < mean <= max <= the kernel's time."""
     w = synth.make_workload("dense_deep", D=20_000)
@@ -370,7 +371,8 @@ def _literal_class_work(txs, N, minsup):
     return work
 
 
-@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1), (4, 3), (5, 3), (6, 4), (7, 4)])
+@pytest.mark.parametrize("seed,mode", [(0, 0), (1, 1), (2, 0), (3, 1), (4, 3), (5, 3), (6, 4), (7, 4), (8, 5),
+                                       (9, 5)])
 def test_class_work_matches_literal_eclat(seed, mode):
     """class_work_out: intersections per one-row class equal a literal Eclat's count, and sum to the total."""
     rng = np.random.default_rng(700 + seed)
