@@ -283,26 +283,33 @@ def run_ours(args):
         alu_peak_gword = 128.0 / 3.0 * num_sms * sm_max_mhz * 1e6 / 1e9
         words = stats["n_pair_intersections"] * ((D + 31) // 32)  # algorithmic 32-bit word pairs
         achieved_gword = words / (pair_avg * 1e-3) / 1e9
-        if dfs_avg > pair_avg:  # the persistent DFS dominates: its bytes against the measured copy rate
-            hbm = float(peaks.get("hbm_gbs", 6800.0))
-            dfs_gbs = stats["bytes_dfs_kernel"] / (dfs_avg * 1e-3) / 1e9
-            roofline = {"kernel": "k_dfs", "bound": "hbm", "achieved": round(dfs_gbs, 1), "peak": round(hbm, 1),
+        rec, rec_note = captured(args.workload)
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        hbm_src = "measured copy rate (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+        if dfs_avg > pair_avg:  # the DFS stage dominates: its operand bytes against the measured copy rate
+            proj = stats.get("bytes_projected", 0) > 0
+            alg = stats["bytes_projected"] if proj else stats["bytes_dfs_kernel"]
+            dfs_gbs = alg / (dfs_avg * 1e-3) / 1e9
+            roofline = {"kernel": ("k_proj_tids + k_proj_bits + k_dfs_proj (+ k_dfs_sparse on the classes left out)"
+                                   if proj else "k_dfs"),
+                        "bound": "hbm", "achieved": round(dfs_gbs, 1), "peak": round(hbm, 1),
                         "unit": "GB/s", "frac": round(dfs_gbs / hbm, 4),
-                        "traffic": DFS_KERNEL_TRAFFIC.get(args.workload),
-                        "peak_source": "measured copy rate (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
-                        else "fallback 6.8 TB/s",
-                        "note": ("algorithmic bytes count every candidate row in full; the kernel reads row words "
-                                 "only under nonzero prefix words, so traffic is far below them"
-                                 if stats["n_frequent_items"] * ((D + 31) // 32) * 4 > 129e6 else
-                                 "the rows fit in L2 (129 MB): the DFS is bound by the latency of its dependent "
-                                 "per-node steps, not by HBM; the fraction is of the HBM copy rate")}
+                        "traffic": rec["kernels"]["dfs"] if rec else None, "traffic_source": rec_note,
+                        "peak_source": hbm_src,
+                        "note": ("algorithmic bytes of the projected DFS in its own representation (stats "
+                                 "bytes_projected): each class database part built (row read, one word gathered "
+                                 "per survivor and transaction, bitmaps written) and per class node its prefix and "
+                                 "candidates over its region's width; the regions (tens of MB) stay in the 129 MB L2"
+                                 if proj else
+                                 "algorithmic bytes count every candidate row in full (the dense definition); the "
+                                 "kernel reads row words only under nonzero prefix words")}
         elif stats.get("pair_kernel") in (2, 3):  # level 2 on the tensor cores: the 0/1 contraction, kind::f8f6f4
             flops = 2.0 * stats["n_pair_intersections"] * D  # one multiply-add per pair and transaction
             tf = flops / (pair_avg * 1e-3) / 1e12
             peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0))
             roofline = {"kernel": "k_expand_e2m1 + k_pair_mma" if stats.get("pair_kernel") == 2 else "k_expand_e4m3 + k_pair_mma", "bound": "tensor", "achieved": round(tf, 1),
                         "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(tf / peak, 4),
-                        "traffic": PAIR_MMA_TRAFFIC.get(args.workload),
+                        "traffic": rec["kernels"]["pair"] if rec else None, "traffic_source": rec_note,
                         "peak_source": ("kind::f8f6f4 (e2m1 and e4m3 operands alike) at the fp8 dense rate = 2 x the "
                                         "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops; nominal fp8:bf16 = 4.5:2.25)" if "bf16_tflops" in peaks
                                         else "fallback 1.9 PFLOP/s bf16 x 2"),
@@ -312,9 +319,15 @@ def run_ours(args):
             roofline = {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                         "peak": round(alu_peak_gword, 1), "unit": "Gword/s",
                         "frac": round(achieved_gword / alu_peak_gword, 4),
-                        "traffic": PAIR_KERNEL_TRAFFIC.get(args.workload),
+                        "traffic": rec["kernels"]["pair"] if rec else None, "traffic_source": rec_note,
                         "peak_source": "derived: (64 LOP3 + 32 POPC lanes/clk/SM) -> 42.67 word pairs/clk/SM x SMs "
                                        "x max SM clock"}
+        ms_step = max_ms / args.steps
+        dram = {"bytes_per_step": rec["step"] if rec else None, "source": rec_note}
+        if rec:
+            dram["gbs"] = round(rec["step"] / (ms_step * 1e-3) / 1e9, 1)
+            dram["frac_of_hbm"] = round(dram["gbs"] / hbm, 4)
+            dram["note"] = "DRAM bytes of one step's launches (ncu) over this run's ms_per_step"
         out = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
@@ -332,6 +345,10 @@ def run_ours(args):
                              "step_min": round(min(step_ms), 4), "step_median": round(statistics.median(step_ms), 4),
                              "step_max": round(max(step_ms), 4)},
             "roofline": roofline,
+            "dram": dram,
+            "value_note": "value counts the dense-definition bytes of every intersection (a work rate: words that "
+                          "the kernels skip or read from projected bitmaps count in full); dram gives the HBM "
+                          "fraction of the step",
             "e2e": {"value": round(tot_bytes / max_e2e / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": round(max_e2e / args.steps * 1e3, 3)},
             "gpu_launches": int(launches),
@@ -343,18 +360,26 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    if out is not None and world == 1 and not args.no_legs:
+        # the two systems forms, measured in the same run: one mine of the deep dense workload captured in a
+        # CUDA graph and replayed, and the served request loop against the plain loop (a prefix of the
+        # 2,000-request serving workload, same laws and arrival rate)
+        out["legs"] = {"plan": run_plan(args, workload="dense_deep", steps=max(args.steps, 20)),
+                       "serve": run_serve(args, n_requests=args.serve_requests)}
     return out
 
 
-def run_plan(args):
+def run_plan(args, workload=None, steps=None):
     """Graph replays of one captured mine (batched mode): all prefix classes in one persistent launch."""
     import torch
 
     from paper_2108_05038_gb300 import fim
 
     torch.cuda.set_device(0)
-    w = synth.make_workload(args.workload)
-    w["name"] = args.workload
+    workload = workload or args.workload
+    w = synth.make_workload(workload)
+    w["name"] = workload
+    args_steps = steps or args.steps
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     s = torch.cuda.Stream()
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], w["word_bits"], 0, stream=s)
@@ -369,7 +394,7 @@ def run_plan(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     total = 0.0
     launches0 = fim.kernel_launches()
-    for _ in range(args.steps):
+    for _ in range(args_steps):
         with torch.cuda.stream(s):
             flush.fill_(1)
             e0.record(s)
@@ -377,12 +402,12 @@ def run_plan(args):
         e1.record(s)
         e1.synchronize()
         total += e0.elapsed_time(e1)
-    ms = total / args.steps
+    ms = total / args_steps
     launches = fim.kernel_launches() - launches0
     plan.free()
     db.free()
     return {"metric": METRIC, "value": round(st["bytes_algorithmic"] / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "n_gpus": 1, "steps": args_steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "mode": "plan (CUDA-graph replay of one mine; build and estimate once before timing)",
             "config": {"workload": workload_desc(w), "shape": shape, "autotuned_ms": round(tuned_ms, 4),
@@ -580,54 +605,56 @@ def _gen_request(r):
     return off, items
 
 
-def run_serve(args):
-    """Serving: Poisson arrivals of mining requests on their own databases; p50/p99 latency and
-    itemsets/s of the continuous-batching server against the plain one-job-at-a-time loop."""
-    import multiprocessing as mp
+def result_digest(res):
+    """Order-independent digest of a host result: (itemsets, sum over itemsets of a 64-bit mix of the
+    itemset's items and support).  Equal results give equal digests whatever their record order."""
+    n = res.n_sets
+    if n == 0:
+        return (0, 0)
+    so = res.set_offsets.astype(np.int64)
+    it = res.set_items.astype(np.uint64)
+    m = np.uint64(0xbf58476d1ce4e5b9)
+    with np.errstate(over="ignore"):
+        h = (it + np.uint64(0x9e3779b97f4a7c15)) * m
+        h ^= h >> np.uint64(31)
+        h *= np.uint64(0x94d049bb133111eb)
+        per_set = np.add.reduceat(h, so[:-1]) if len(it) else np.zeros(n, dtype=np.uint64)
+        per_set = (per_set ^ (res.supports.astype(np.uint64) * m)) * np.uint64(0x94d049bb133111eb)
+        per_set ^= per_set >> np.uint64(29)
+        return (int(n), int(per_set.sum(dtype=np.uint64)))
 
-    reqs = synth.serving_requests(args.requests, rate=args.rate)
-    with mp.get_context("spawn").Pool(max(1, (os.cpu_count() or 4) - 2)) as pool:  # before any CUDA call
-        dbs = pool.map(_gen_request, reqs, chunksize=4)
-    import torch
+
+def serve_arm(reqs, dbs, slots):
+    """Requests submitted at their arrival times to a server with `slots` slots; results collected in a
+    second thread.  Returns latencies (s), per-request digests (None = rejected over the itemset limit),
+    the makespan, the peak of jobs in flight and the service times."""
+    import threading
 
     from paper_2108_05038_gb300 import fim
 
-    torch.cuda.set_device(0)
-    # warm the library (kernels loaded, pools primed)
-    srv = fim.Server(slots=args.slots, ctas_per_sm=1, max_itemsets=MAX_ITEMSETS_PER_JOB)
-    for k in range(min(4, len(reqs))):
+    srv = fim.Server(slots=slots, ctas_per_sm=1, max_itemsets=MAX_ITEMSETS_PER_JOB)
+    for k in range(min(4, len(reqs))):  # warm the library (kernels loaded, pools primed)
         srv.wait(srv.submit(dbs[k][0], dbs[k][1], reqs[k]["N"], reqs[k]["minsup"], SAMPLE_RATE))[0].free()
-
-    def pct(v, q):
-        v = sorted(v)
-        return v[min(len(v) - 1, int(round(q / 100 * (len(v) - 1))))]
-
-    # continuous batching: submit at the arrival times, collect in a second thread
-    import threading
-    lat, sets = [None] * len(reqs), [0] * len(reqs)
-    svc = [0.0] * len(reqs)
+    lat, dig, svc = [None] * len(reqs), [None] * len(reqs), [0.0] * len(reqs)
     ids = [None] * len(reqs)
     ready = threading.Semaphore(0)
-
-    rejected = [0]
 
     def collector():
         for k in range(len(reqs)):
             ready.acquire()
             try:
                 res, l, sv = srv.wait(ids[k])
-                sets[k] = res.n_sets
+                dig[k] = result_digest(res)
                 svc[k] = sv
                 res.free()
             except fim.FimError as e:
                 if e.status != fim.FIM_ERR_OUTPUT_OVERFLOW:
                     raise
-                rejected[0] += 1
-                sets[k] = -1
                 l = time.perf_counter() - t0 - reqs[k]["arrival_s"]
             lat[k] = l
-            if (k + 1) % 50 == 0:
-                print(f"served {k + 1}/{len(reqs)} at {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+            if (k + 1) % 100 == 0:
+                print(f"slots={slots}: served {k + 1}/{len(reqs)} at {time.perf_counter() - t0:.1f} s",
+                      file=sys.stderr, flush=True)
 
     th = threading.Thread(target=collector)
     th.start()
@@ -642,38 +669,39 @@ def run_serve(args):
     span = time.perf_counter() - t0
     peak = srv.stats()["peak_in_flight"]
     srv.free()
-    slow = sorted(range(len(reqs)), key=lambda k: -svc[k])[:5]
-    served = {"p50_ms": round(pct(lat, 50) * 1e3, 2), "p99_ms": round(pct(lat, 99) * 1e3, 2),
-              "itemsets_per_s": round(sum(max(0, x) for x in sets) / span, 1), "makespan_s": round(span, 2),
-              "peak_in_flight": peak, "rejected_over_limit": rejected[0],
-              "slowest_service": [{"k": k, "D": reqs[k]["D"], "N": reqs[k]["N"], "TL": round(reqs[k]["TL"], 1),
-                                   "minsup": reqs[k]["minsup"], "service_ms": round(svc[k] * 1e3, 1),
-                                   "itemsets": sets[k]} for k in slow]}
+    return lat, dig, span, peak, svc
 
-    # plain loop: one job at a time, in arrival order, on the default stream
-    lat2, sets2, rej2 = [], 0, 0
-    t0 = time.perf_counter()
-    for k, r in enumerate(reqs):
-        now = time.perf_counter() - t0
-        if now < r["arrival_s"]:
-            time.sleep(r["arrival_s"] - now)
-        db = fim.build_vertical_db(dbs[k][0], dbs[k][1], r["N"], 64, r["minsup"])
-        db.estimate_class_costs(SAMPLE_RATE, r["minsup"] / r["D"], 1000 + k)
-        try:
-            res = db.mine(r["minsup"], ctas_per_sm=1, max_itemsets=MAX_ITEMSETS_PER_JOB)
-            sets2 += res.n_sets
-        except fim.FimError as e:
-            if e.status != fim.FIM_ERR_OUTPUT_OVERFLOW:
-                raise
-            rej2 += 1
-        db.free()
-        lat2.append(time.perf_counter() - t0 - r["arrival_s"])
-        if (k + 1) % 50 == 0:
-            print(f"plain {k + 1}/{len(reqs)} at {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
-    span2 = time.perf_counter() - t0
-    plain = {"p50_ms": round(pct(lat2, 50) * 1e3, 2), "p99_ms": round(pct(lat2, 99) * 1e3, 2),
-             "itemsets_per_s": round(sets2 / span2, 1), "makespan_s": round(span2, 2), "rejected_over_limit": rej2}
-    assert sets2 == sum(max(0, x) for x in sets), "served and plain results differ in size"
+
+def run_serve(args, n_requests=None):
+    """Serving: Poisson arrivals of mining requests on their own databases; p50/p99 latency and itemsets/s of
+    the continuous-batching server (`--slots` slots) against the plain one-job-at-a-time loop, which is the
+    same server with one slot, so both arms run the same C++ worker code and differ only in batching."""
+    import multiprocessing as mp
+
+    reqs = synth.serving_requests(n_requests or args.requests, rate=args.rate)
+    with mp.get_context("spawn").Pool(max(1, (os.cpu_count() or 4) - 2)) as pool:  # before any CUDA call
+        dbs = pool.map(_gen_request, reqs, chunksize=4)
+    import torch
+
+    torch.cuda.set_device(0)
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(q / 100 * (len(v) - 1))))]
+
+    def summary(lat, dig, span, peak, svc, slots):
+        sets = sum(d[0] for d in dig if d is not None)
+        slow = sorted(range(len(reqs)), key=lambda k: -svc[k])[:3]
+        return {"slots": slots, "p50_ms": round(pct(lat, 50) * 1e3, 2), "p99_ms": round(pct(lat, 99) * 1e3, 2),
+                "itemsets_per_s": round(sets / span, 1), "makespan_s": round(span, 2), "peak_in_flight": peak,
+                "rejected_over_limit": sum(1 for d in dig if d is None),
+                "slowest_service": [{"k": k, "D": reqs[k]["D"], "N": reqs[k]["N"], "minsup": reqs[k]["minsup"],
+                                     "service_ms": round(svc[k] * 1e3, 1)} for k in slow]}
+
+    served_raw = serve_arm(reqs, dbs, args.slots)
+    plain_raw = serve_arm(reqs, dbs, 1)
+    same = [a == b for a, b in zip(served_raw[1], plain_raw[1])]
+    served, plain = summary(*served_raw, args.slots), summary(*plain_raw, 1)
     return {"metric": "served p50/p99 latency vs plain loop", "value": served["p99_ms"], "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "mode": "serve", "data": "synthetic",
             "config": {"requests": len(reqs), "rate_per_s": args.rate, "slots": args.slots,
@@ -681,7 +709,9 @@ def run_serve(args):
                        "workload": "pattern-embedded, D log-uniform [1e4, 5e5], N uniform [100, 5000], "
                                    "TL uniform [5, 30], PL 4, npat 2N, minsup log-uniform [0.1%, 5%], "
                                    "request seed 1000+k, Poisson arrivals"},
-            "served": served, "plain_loop": plain, "n_frequent_total": int(sets2)}
+            "served": served, "plain_loop": plain,
+            "per_request_equal": all(same), "requests_differing": [k for k, x in enumerate(same) if not x][:10],
+            "n_frequent_total": int(sum(d[0] for d in served_raw[1] if d is not None))}
 
 
 ORACLE_MAX_D = 200_000  # larger workloads: the oracle mines a prefix sample (its full mine takes many minutes)
@@ -829,6 +859,9 @@ def main():
                          "build + mine (profiler captures); stream: the counting step alone over 4 GiB of "
                          "bitmap rows")
     ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving leg of the default run (the first ones of the serving workload)")
+    ap.add_argument("--no-legs", action="store_true", help="default run: skip the plan and serving legs")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()

@@ -111,9 +111,9 @@ typedef struct {
                                   words when it has at most 2,048 of them (small CTAs, several per
                                   SM), dense in its stack slot otherwise; rows of at most 65,535
                                   16-byte words, no donation (else as NODES); FIM_DFS_AUTO (2, the
-                                  default): rows of at most 2,048 words (8 KB): the warp DFS when
-                                  rows are at most 512 words and at least 1,024 rows are frequent,
-                                  else frames; wider rows: projected; FIM_DFS_WARP (4): one warp
+                                  default): projected for rows of more than 2,048 words (8 KB) and
+                                  for rows of at most 512 words with at least 1,024 frequent rows,
+                                  else frames; FIM_DFS_WARP (4): one warp
                                   per two-item class, the
                                   prefix in its registers, no CTA-wide barrier; rows of at most 512
                                   words, no donation (else as SPARSE); FIM_DFS_PROJECTED (5): the
@@ -122,7 +122,7 @@ typedef struct {
                                   on the device) is built once, then one warp per two-item class
                                   runs Eclat on those short bitmaps; classes beyond its budgets
                                   (bitmaps of at most 1/4 of the frequent rows' bytes, stacks of
-                                  64K words per warp, doubled and the run repeated when too small)
+                                  128K words per warp, doubled and the run repeated when too small)
                                   are mined as SPARSE; same row limit and no donation as SPARSE  */
   uint32_t threads_per_cta;    /* persistent DFS CTA size, 128/256/512 (sparse nodes: at most 256;
                                   warp DFS: 256); 0 = sparse nodes: 256; other node modes: the one
@@ -152,11 +152,12 @@ typedef struct {
   uint64_t proj_bitmap_words;  /* FIM_DFS_PROJECTED budgets (0 = automatic): the class bitmaps, in
                                   32-bit words (classes past it, in queue order, are mined as SPARSE) */
   uint64_t proj_stack_words;   /* first stack of one warp, in 32-bit words                         */
-  uint32_t proj_max_row_words; /* widest class bitmap (words) that is projected (default: 1/4 of the
-                                  stack)                                                            */
+  uint32_t proj_max_row_words; /* widest class bitmap (words) that is projected (default: 1/8 of the
+                                  first stack)                                                      */
   uint32_t proj_split_words;   /* a frame whose next level would read more 32-bit words than this is
-                                  handed to the other warps with its own database part (0 = automatic,
-                                  16,384)                                                           */
+                                  handed to the other warps with its own database part (0 = automatic:
+                                  64 x the mean bitmap width of the class regions, at least 128 and
+                                  at most 65,536)                                                   */
   /* outputs */
   uint64_t out_needed_sets;    /* on FIM_ERR_OUTPUT_OVERFLOW: capacities that would have sufficed */
   uint64_t out_needed_items;
@@ -343,6 +344,12 @@ fim_status fim_server_submit(fim_server* srv, const uint32_t* tx_offsets, const 
                              uint32_t N, uint32_t minsup_abs, double sample_rate, uint64_t* job_id);
 fim_status fim_server_wait(fim_server* srv, uint64_t job_id, fim_result** out, double* latency_s,
                            double* service_s);
+/* As fim_server_wait, and the job's device interval: milliseconds from the
+ * server's creation to CUDA events recorded on the job's stream just before its
+ * first and just after its last device work (-1 when they could not be read).
+ * Jobs whose intervals intersect had device work in flight at the same time. */
+fim_status fim_server_wait_ex(fim_server* srv, uint64_t job_id, fim_result** out, double* latency_s,
+                              double* service_s, double* device_start_ms, double* device_end_ms);
 fim_status fim_server_stats(fim_server* srv, uint64_t* in_use_bytes, uint32_t* in_flight, uint32_t* peak_in_flight,
                             uint64_t* queued);
 void fim_server_free(fim_server* srv);

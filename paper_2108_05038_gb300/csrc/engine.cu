@@ -40,14 +40,20 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // (large_sparse's 1% sample: 2.38 ms against 3.64 ms in frame passes); short rows with few rows,
   // where the largest class's chain of dependent nodes sets the time, take frame passes, which
   // spread one frame over a whole CTA (sparse_mid's sample: 45 µs against 61 µs)
-  // wide rows (automatic) or FIM_DFS_PROJECTED: the projected DFS, with the sparse node mode (whose
-  // geometry ep->mode = 3 describes) mining the classes left out of the projection
+  // The projected DFS (FIM_DFS_PROJECTED, automatic on wide rows and on short rows with many classes)
+  // runs with the sparse node mode, whose geometry ep->mode = 3 describes, mining the classes left out
+  // of the projection.  Automatic: wide rows and short rows with at least 1,024 frequent rows (many
+  // classes, throughput bound: large_sparse's 1% sample, DFS 2.4 ms in the warp DFS, 2.1 ms projected;
+  // its 20,000-row variant 11.1 against 3.8 ms) take it; other short rows take frame passes, which spread
+  // one frame over a whole CTA where the largest class's chain of dependent nodes sets the time
+  // (sparse_mid: 0.022 ms against 0.080 ms projected).
+  const bool auto_proj = cfg.mode == 2 && list_ok && !cfg.donate && (in.stride > 2048 || (warp_ok && n1 >= 1024));
   if (cfg.mode == 2)
-    ep->mode = in.stride <= 2048 ? (warp_ok && n1 >= 1024 ? 4u : 1u) : (list_ok && !cfg.donate ? 3u : 0u);
+    ep->mode = auto_proj ? 3u : (in.stride <= 2048 ? 1u : 0u);
   else if (cfg.mode == 3 || cfg.mode == 5) ep->mode = list_ok && !cfg.donate ? 3u : 0u;
   else if (cfg.mode == 4) ep->mode = warp_ok ? 4u : (list_ok && !cfg.donate ? 3u : 0u);
   else ep->mode = cfg.mode == 1 ? 1u : 0u;
-  ep->proj = ep->mode == 3 && (cfg.mode == 5 || (cfg.mode == 2 && in.stride > 2048));
+  ep->proj = ep->mode == 3 && (cfg.mode == 5 || auto_proj);
   ep->donate = ep->mode == 0 ? cfg.donate : 0u;  // only dense node expansion donates
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
@@ -166,13 +172,22 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
                                         std::max<uint64_t>((uint64_t)n1 * in.stride / 4, 16ull << 20));
     ep->proj_t_cap = 0;
     for (uint32_t s : in.row_supp) ep->proj_t_cap += ((uint64_t)s + 3) & ~3ull;
-    ep->pstack_words = ((cfg.pstack_words ? cfg.pstack_words : kProjStackWords) + 31) & ~31ull;
-    ep->proj_w_cap = cfg.proj_w_cap ? cfg.proj_w_cap : (uint32_t)std::min<uint64_t>(ep->pstack_words / 4, 1u << 20);
+    // (a database remembers the stack its earlier mines grew to, so that a mine is not repeated for it)
+    ep->pstack_words = ((cfg.pstack_words ? cfg.pstack_words : std::max<uint64_t>(kProjStackWords, db->proj_stack_words)) +
+                        31) & ~31ull;
+    // widest projected class: eight prefixes of it fit the first stack (a frame that keeps its class's width
+    // materialises one prefix per level)
+    const uint64_t base_stack = cfg.pstack_words ? cfg.pstack_words : kProjStackWords;
+    ep->proj_w_cap = cfg.proj_w_cap ? cfg.proj_w_cap : (uint32_t)std::min<uint64_t>(base_stack / 8, 1u << 20);
     if (cfg.proj_y_cap) ep->proj_y_cap = cfg.proj_y_cap;
     ep->proj_smem = dfs_proj_smem_bytes(ep->L);
     int pocc = 0;
     FIM_CUDA(dfs_proj_ctas_per_sm(ep->proj_smem, &pocc));
     if (pocc < 1) return fail(FIM_ERR_INVALID, "projected DFS kernel does not fit on an SM");
+    // a capped CTA count (the server's concurrent jobs) also turns the work sharing off: warps then leave as
+    // soon as the static queue is empty instead of waiting for handed-out frames
+    const bool share = cfg.ctas_per_sm == 0;
+    if (!share) pocc = std::min<int>(pocc, (int)cfg.ctas_per_sm);
     ep->proj_grid = (uint32_t)db->num_sms * (uint32_t)pocc;
     uint32_t* meta = nullptr;
     FIM_TRY(ws_get(ws, WS_PROJ_META, 6ull * n1 + 2, &meta));
@@ -182,11 +197,11 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
     ep->d_eoffx = ep->d_itemoff + n1 + 1;
     FIM_TRY(ws_get(ws, WS_ENTRIES_F, ep->npairs_max + 1, &ep->d_entries_f));
     // the arena holds the class regions (within proj_y_cap), then the regions of split frames
-    ep->proj_arena_words = ep->proj_y_cap + std::max<uint64_t>(ep->proj_y_cap, 16ull << 20);
-    ep->split_words = cfg.split_words ? cfg.split_words : kProjSplitWords;
-    ep->dq_cap = kProjDqCap;
+    ep->proj_arena_words = ep->proj_y_cap + (share ? std::max<uint64_t>(ep->proj_y_cap, 16ull << 20) : 0ull);
+    ep->split_words = cfg.split_words;  // 0: chosen on the device from the class regions' mean width
+    ep->dq_cap = share ? kProjDqCap : 0u;
     FIM_TRY(ws_get(ws, WS_PROJ_Y, ep->proj_arena_words, &ep->d_Y));
-    FIM_TRY(ws_get(ws, WS_PROJ_DQ, ep->dq_cap, &ep->d_dq));
+    FIM_TRY(ws_get(ws, WS_PROJ_DQ, std::max<uint32_t>(1, ep->dq_cap), &ep->d_dq));
     FIM_TRY(ws_get(ws, WS_PROJ_T, std::max<uint64_t>(4, ep->proj_t_cap), &ep->d_T));
   }
   if (cfg.collect_times)
@@ -289,8 +304,10 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
       // node mode on the classes left out
       ce = launch_proj_build(pj, ep.num_sms, st);
       if (ce != cudaSuccess) return ce;
-      ce = cudaMemsetAsync(ep.d_dq, 0, (size_t)ep.dq_cap * sizeof(uint4), st);  // no slot published yet
-      if (ce != cudaSuccess) return ce;
+      if (ep.dq_cap) {
+        ce = cudaMemsetAsync(ep.d_dq, 0, (size_t)ep.dq_cap * sizeof(uint4), st);  // no slot published yet
+        if (ce != cudaSuccess) return ce;
+      }
       DfsLaunch dp = dl;
       dp.row_supp = ep.d_rsupp;
       dp.yoff = ep.d_yoff;
@@ -312,6 +329,12 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   }
   if (ep.ev[3]) cudaEventRecord(ep.ev[3], st);
   return cudaSuccess;
+}
+
+uint64_t proj_footprint_bytes(uint32_t rows, uint32_t stride, uint64_t nnz, uint32_t grid) {
+  const uint64_t y = std::max<uint64_t>((uint64_t)rows * stride / 4, 16ull << 20);  // class bitmaps (words)
+  return 4ull * y + 4ull * nnz + 4ull * (uint64_t)grid * (kProjThreads / 32) * kProjStackWords +
+         64ull * rows + (1ull << 20);
 }
 
 void engine_release_events(EnginePlan* ep) {
@@ -361,6 +384,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     if (next * ep->proj_grid * (kProjThreads / 32) * 4 > db->total_mem / 8)
       return fail(FIM_ERR_OOM, "projected DFS: the warps' stacks would exceed 1/8 of device memory");
     ep->pstack_words = next;
+    db->proj_stack_words = std::max(db->proj_stack_words, next);
     *retry = true;
     return FIM_OK;
   }

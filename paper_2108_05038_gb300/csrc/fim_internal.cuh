@@ -164,7 +164,8 @@ struct alignas(128) DevCtrl {
   uint32_t proj_splits;              // frames split into regions (stats)
   unsigned long long arena_top;      // words of the region arena in use
   unsigned long long proj_bytes;     // operand bytes of the projected DFS (stats)
-  uint32_t pad5[24];
+  unsigned long long proj_split_words;  // hand-out threshold chosen by the planning kernel
+  uint32_t pad5[22];
 };
 
 // ---------------------------------------------------------------------------
@@ -210,6 +211,7 @@ struct fim_db {
   fim::Workspace ws;
 
   uint32_t* d_iota = nullptr;  // 0 .. n_rows-1 (frequent-row lists of the full database point into it)
+  uint64_t proj_stack_words = 0;  // largest warp stack a projected mine of this database needed (0 = none yet)
   // pinned host staging for small copies; regions are handed out by a bump
   // pointer that is reset whenever the stream has been synchronised
   uint8_t* stage = nullptr;
@@ -492,9 +494,11 @@ size_t dfs_proj_smem_bytes(uint32_t max_len);
 cudaError_t dfs_proj_ctas_per_sm(size_t smem, int* out);
 constexpr uint32_t kProjThreads = 256;     // projected DFS: 8 warps per CTA
 constexpr uint32_t kProjCtasPerSm = 4;     // at most 32 warps per SM (their stacks take device memory)
-constexpr uint64_t kProjStackWords = 65536;  // first stack of one warp (doubled when a run needs more)
+constexpr uint64_t kProjStackWords = 131072;  // first stack of one warp (doubled when a run needs more)
 constexpr uint32_t kProjDqCap = 1u << 18;     // items of split frames the queue holds
-constexpr uint64_t kProjSplitWords = 1u << 14;  // next-level words above which a frame is handed out
+// device bytes the projected DFS adds to a mine of `rows` frequent rows of `stride` words over a database
+// of nnz items run on `grid` persistent CTAs (for the server's admission)
+uint64_t proj_footprint_bytes(uint32_t rows, uint32_t stride, uint64_t nnz, uint32_t grid);
 // words of a class region's header, prefix ids and row ids (its rows start there)
 __host__ __device__ inline uint64_t region_rows_off(uint32_t xlen, uint32_t k) {
   return 8ull + (((uint64_t)xlen + 3) & ~3ull) + (((uint64_t)k + 3) & ~3ull);

@@ -95,12 +95,12 @@ __host__ __device__ inline uint32_t padded_words(uint32_t supp) { return (words_
 // budgets go to the classes that start first.
 __global__ void __launch_bounds__(1024) k_proj_plan(const ProjLaunch P) {
   __shared__ unsigned long long sy[33], st[33], sbytes[33];
-  __shared__ uint32_t sa[33], sb[33], sc[33], sd[33];
+  __shared__ uint32_t sa[33], sb[33], sc[33], sd[33], se[33];
   __shared__ unsigned long long carry_y, carry_t, carry_b;
-  __shared__ uint32_t carry_p, carry_f, carry_i, carry_c;
+  __shared__ uint32_t carry_p, carry_f, carry_i, carry_c, carry_n;
   if (threadIdx.x == 0) {
     carry_y = carry_t = carry_b = 0;
-    carry_p = carry_f = carry_i = carry_c = 0;
+    carry_p = carry_f = carry_i = carry_c = carry_n = 0;
   }
   __syncthreads();
   for (uint32_t base = 0; base < P.n1; base += blockDim.x) {
@@ -123,8 +123,10 @@ __global__ void __launch_bounds__(1024) k_proj_plan(const ProjLaunch P) {
     const uint32_t pex = block_excl_scan<uint32_t>(neP, sa);
     const uint32_t fex = block_excl_scan<uint32_t>(neF, sb);
     const uint32_t iex = block_excl_scan<uint32_t>(nit, sc);
-    const uint32_t cex = block_excl_scan<uint32_t>(proj ? 1u : 0u, sd);
+    const uint32_t cex = block_excl_scan<uint32_t>(proj ? k : 0u, sd);  // rows of the projected classes
+    const uint32_t nex = block_excl_scan<uint32_t>(proj ? 1u : 0u, se);   // projected classes
     (void)cex;
+    (void)nex;
     // Phase 3's operand bytes: the row read once, its transactions written and read, one word gathered per
     // (survivor, transaction), the bitmaps written
     const unsigned long long pb = proj ? 4ull * P.stride + 8ull * s + 4ull * k * s + 4ull * k * Wp : 0ull;
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(1024) k_proj_plan(const ProjLaunch P) {
       carry_f += sb[32];
       carry_i += sc[32];
       carry_c += sd[32];
+      carry_n += se[32];
       carry_b += sbytes[32];
     }
     __syncthreads();
@@ -156,7 +159,10 @@ __global__ void __launch_bounds__(1024) k_proj_plan(const ProjLaunch P) {
     P.ctrl->n_entries_f = carry_f;
     P.ctrl->queue_head = 0;
     P.ctrl->queue_head_f = 0;
-    P.ctrl->n_proj_classes = carry_c;
+    // hand-out threshold: 64 x the mean width of a projected row, within [128, 65536] words
+    const unsigned long long mean_w = carry_c ? carry_y / carry_c : 1ull;
+    P.ctrl->proj_split_words = min(max(64ull * mean_w, 128ull), 65536ull);
+    P.ctrl->n_proj_classes = carry_n;
     P.ctrl->n_proj_items = carry_i;
   }
 }
@@ -349,6 +355,8 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
   // operand bytes: per node the prefix and the candidates' bitmaps over the region's width; per compacted or
   // handed-out frame one gathered word per (survivor, transaction) and the region written
   unsigned long long st_bytes = 0;
+  unsigned long long st_sets = 0, st_items = 0;
+  uint32_t st_maxlen = 0;
   bool static_done = false;
   constexpr uint32_t kStop = DEV_ERR_ABORTED | DEV_ERR_PSTACK | DEV_ERR_TIMEOUT;
 
@@ -369,7 +377,8 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
     uint32_t m = 0;
     if (lane == 0) {
       bool stop = (ld_volatile(&p.ctrl->err) & kStop) != 0;
-      if (!stop && p.max_sets && *(volatile unsigned long long*)&p.ctrl->sets_total > p.max_sets) {
+      // (records reserved so far: the high half of the reservation word)
+      if (!stop && p.max_sets && (*(volatile unsigned long long*)&p.ctrl->packed >> 32) > p.max_sets) {
         atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
         stop = true;
       }
@@ -428,6 +437,7 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
     }
 
     const RegionView R0 = region_view(p.Y + roff);
+    const unsigned long long split_words = p.split_words ? p.split_words : p.ctrl->proj_split_words;
     const uint32_t cls = R0.cls;
     unsigned long long cls_sets = 0, cls_work = 0;
     for (uint32_t q = lane; q < R0.xlen; q += 32) path[q] = R0.R[8 + q];
@@ -483,16 +493,18 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       if (nout == 0) return 0;
       __syncwarp();  // the list written by lane 0 is read by every lane below
       unsigned long long base = 0;
+      // one atomic per node reserves its records; the exact totals and the longest length are added once per
+      // warp at the end (nothing reads them while the kernel runs)
       if (lane == 0) {
         const unsigned long long sets = nout, items = (unsigned long long)nout * (xlen + 1);
         base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
-        atomicAdd(&p.ctrl->sets_total, sets);
-        atomicAdd(&p.ctrl->items_total, items);
-        atomicMax(&p.ctrl->max_len, xlen + 1);
         const unsigned long long after = (base >> 32) + sets;
         if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
       }
       base = __shfl_sync(kFull, base, 0);
+      st_sets += nout;
+      st_items += (unsigned long long)nout * (xlen + 1);
+      st_maxlen = max(st_maxlen, xlen + 1);
       cls_sets += nout;
       if (p.out_off) {
         for (uint32_t o = 0; o < nout; ++o) {
@@ -723,8 +735,10 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       const uint32_t W2 = words_of(supp);
       // (stack allocations are whole 16-byte units: a compacted region's rows are written as 16-byte vectors)
       const uint64_t after_list = ((uint64_t)top + used + 2ull * n2 + 3) & ~3ull;
+      // hand the frame out when its next level is large: more words than split_words (given, or 64 x the mean
+      // bitmap width of the class regions, set by the planning kernel)
       const unsigned long long work = (unsigned long long)n2 * (n2 - 1) / 2 * W2;
-      if (n2 >= 3 && work > p.split_words && after_list + supp <= p.pstack_words &&
+      if (p.dq_cap && n2 >= 3 && work > split_words && after_list + supp <= p.pstack_words &&
           hand_out(V, cpre, lst, n2, plen + 1, supp, stk + after_list))
         continue;
       if ((uint64_t)W2 * 4 <= V.W) {  // compact: X's own database part on the stack
@@ -776,6 +790,11 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
     atomicAdd(&p.ctrl->n_frames, st_frames);
     if (st_splits) atomicAdd(&p.ctrl->proj_splits, (uint32_t)st_splits);
     atomicAdd(&p.ctrl->proj_bytes, st_bytes);
+    if (st_sets) {
+      atomicAdd(&p.ctrl->sets_total, st_sets);
+      atomicAdd(&p.ctrl->items_total, st_items);
+      atomicMax(&p.ctrl->max_len, st_maxlen);
+    }
   }
   if (p.cta_time) {
     __syncthreads();

@@ -31,6 +31,7 @@ struct Job {
   double sample_rate = 0.0;
   uint64_t footprint = 0;
   Clock::time_point t_submit, t_start, t_end;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // the job's device work on its slot's stream
   fim_status status = FIM_OK;
   std::string error;
   fim_result* result = nullptr;
@@ -55,6 +56,7 @@ struct fim_server {
   uint64_t total_mem = 0;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
+  cudaEvent_t ev_origin = nullptr;  // recorded at creation: device times of jobs are measured from it
 };
 
 namespace {
@@ -80,6 +82,8 @@ uint64_t job_footprint(uint32_t D, uint32_t N, uint64_t nnz, uint32_t max_len, u
   const uint64_t depth = std::max<uint32_t>(3, std::min<uint64_t>(max_len, rows)) - 1;
   const uint64_t full = 4ull * (stride + 2 * rows + 8) * depth * grid;
   b += full <= total_mem / 32 ? full : 4ull * (stride + 2 * rows + 8) * (fim::kDfsDepthHint + 1) * grid;
+  // the projected DFS of wide rows: class database parts, transactions, the warps' stacks
+  if (stride > 2048) b += fim::proj_footprint_bytes((uint32_t)rows, (uint32_t)stride, nnz, (uint32_t)grid);
   b += 64ull << 20;                                       // output, sample, small buffers
   return b;
 }
@@ -127,7 +131,10 @@ void worker_main(fim_server* srv, size_t slot) {
       srv->peak_in_flight = std::max(srv->peak_in_flight, srv->in_flight);
     }
     j->t_start = Clock::now();
+    // (events on the slot's stream bracket the job's device work; timing only, no synchronisation)
+    if (cudaEventCreate(&j->ev_start) == cudaSuccess) cudaEventRecord(j->ev_start, st);
     run_job(srv, j, st);
+    if (cudaEventCreate(&j->ev_end) == cudaSuccess) cudaEventRecord(j->ev_end, st);
     j->t_end = Clock::now();
     {
       std::lock_guard<std::mutex> lock(srv->mu);
@@ -181,6 +188,7 @@ fim_status fim_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint32_t
     }
     srv->streams.push_back(s);
   }
+  if (cudaEventCreate(&srv->ev_origin) == cudaSuccess) cudaEventRecord(srv->ev_origin, srv->streams[0]);
   for (uint32_t k = 0; k < slots; ++k) srv->workers.emplace_back(worker_main, srv, (size_t)k);
   *out = srv;
   return FIM_OK;
@@ -219,6 +227,13 @@ fim_status fim_server_submit(fim_server* srv, const uint32_t* tx_offsets, const 
 
 fim_status fim_server_wait(fim_server* srv, uint64_t job_id, fim_result** out, double* latency_s,
                            double* service_s) {
+  return fim_server_wait_ex(srv, job_id, out, latency_s, service_s, nullptr, nullptr);
+}
+
+fim_status fim_server_wait_ex(fim_server* srv, uint64_t job_id, fim_result** out, double* latency_s,
+                              double* service_s, double* device_start_ms, double* device_end_ms) {
+  if (device_start_ms) *device_start_ms = -1.0;
+  if (device_end_ms) *device_end_ms = -1.0;
   if (!srv || !out) return fail(FIM_ERR_INVALID, "server or out is NULL");
   *out = nullptr;
   Job* j = nullptr;
@@ -233,6 +248,17 @@ fim_status fim_server_wait(fim_server* srv, uint64_t job_id, fim_result** out, d
   }
   if (latency_s) *latency_s = std::chrono::duration<double>(j->t_end - j->t_submit).count();
   if (service_s) *service_s = std::chrono::duration<double>(j->t_end - j->t_start).count();
+  // the job's device interval from the server's origin event (both events completed: the job's result
+  // was synchronised on its stream before the worker marked it done)
+  float t0 = -1.f, t1 = -1.f;
+  if (srv->ev_origin && j->ev_start && j->ev_end && cudaEventSynchronize(j->ev_end) == cudaSuccess &&
+      cudaEventElapsedTime(&t0, srv->ev_origin, j->ev_start) == cudaSuccess &&
+      cudaEventElapsedTime(&t1, srv->ev_origin, j->ev_end) == cudaSuccess) {
+    if (device_start_ms) *device_start_ms = t0;
+    if (device_end_ms) *device_end_ms = t1;
+  }
+  if (j->ev_start) cudaEventDestroy(j->ev_start);
+  if (j->ev_end) cudaEventDestroy(j->ev_end);
   fim_status s = j->status;
   if (s == FIM_OK) *out = j->result;
   else set_error(j->error);
@@ -261,11 +287,14 @@ void fim_server_free(fim_server* srv) {
   for (auto& t : srv->workers) t.join();
   for (auto& kv : srv->jobs) {
     if (kv.second->result) fim_result_free(kv.second->result);
+    if (kv.second->ev_start) cudaEventDestroy(kv.second->ev_start);
+    if (kv.second->ev_end) cudaEventDestroy(kv.second->ev_end);
     delete kv.second;
   }
   for (Job* j : srv->queue)
     if (srv->jobs.find(j->id) == srv->jobs.end()) delete j;
   for (auto s : srv->streams) cudaStreamDestroy(s);
+  if (srv->ev_origin) cudaEventDestroy(srv->ev_origin);
   delete srv;
 }
 

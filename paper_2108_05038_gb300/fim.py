@@ -28,7 +28,7 @@ EXPORTED = [
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
     "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free", "fim_kernel_launches",
-    "fim_extension_supports", "fim_result_flags", "fim_pool_memory",
+    "fim_extension_supports", "fim_result_flags", "fim_pool_memory", "fim_server_wait_ex",
 ]
 
 
@@ -134,6 +134,9 @@ def load(build_if_stale: bool = True):
         lib.fim_server_submit.argtypes = [P, P, P, u32, u32, u32, dbl, ctypes.POINTER(u64)]
         lib.fim_server_wait.restype = i32
         lib.fim_server_wait.argtypes = [P, u64, PP, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        lib.fim_server_wait_ex.restype = i32
+        lib.fim_server_wait_ex.argtypes = [P, u64, PP, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                           ctypes.POINTER(dbl)]
         lib.fim_server_stats.restype = i32
         lib.fim_server_stats.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32),
                                          ctypes.POINTER(u64)]
@@ -502,11 +505,18 @@ class Server:
 
     def wait(self, job_id: int):
         """Returns (Result, latency seconds, service seconds)."""
+        res, lat, svc, _ = self.wait_ex(job_id)
+        return res, lat, svc
+
+    def wait_ex(self, job_id: int):
+        """fim_server_wait_ex: (Result, latency s, service s, (device start ms, device end ms) from the
+        server's creation)."""
         h = ctypes.c_void_p()
-        lat, svc = ctypes.c_double(), ctypes.c_double()
-        _check(self._lib, self._lib.fim_server_wait(self._h, job_id, ctypes.byref(h), ctypes.byref(lat),
-                                                    ctypes.byref(svc)), "fim_server_wait")
-        return Result(self._lib, h.value, None), lat.value, svc.value
+        lat, svc, t0, t1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib, self._lib.fim_server_wait_ex(self._h, job_id, ctypes.byref(h), ctypes.byref(lat),
+                                                       ctypes.byref(svc), ctypes.byref(t0), ctypes.byref(t1)),
+               "fim_server_wait_ex")
+        return Result(self._lib, h.value, None), lat.value, svc.value, (t0.value, t1.value)
 
     def stats(self):
         a, b, c, d = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()

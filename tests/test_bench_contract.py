@@ -112,3 +112,51 @@ def test_cpu_baseline_record():
     assert cb["kind"] == "oracle" and cb["unit"] == "GB/s" and cb["cores"] == (os.cpu_count() or 1)
     assert cb["value"] > 0 and cb["single_core"]["value"] > 0 and cb["single_core"]["cores"] == 1
     assert "medians of" in cb["sample"] and "2624 itemsets" in cb["sample"] and cb["cpu"]
+
+
+def test_result_digest_is_order_free_and_separates_results():
+    """The serving comparison's per-request digest: the same itemsets and supports in any record order give
+    the same digest; one support or one item changed gives another."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class R:
+        def __init__(self, sets):
+            self.n_sets = len(sets)
+            self.set_offsets = np.cumsum([0] + [len(s) for s, _ in sets]).astype(np.uint64)
+            self.set_items = np.array([v for s, _ in sets for v in s], dtype=np.uint32)
+            self.supports = np.array([c for _, c in sets], dtype=np.uint32)
+
+    sets = [((1,), 50), ((2,), 40), ((1, 2), 30), ((1, 2, 7), 12), ((3,), 40)]
+    d = bench.result_digest(R(sets))
+    assert d[0] == 5
+    assert bench.result_digest(R(sets[::-1])) == d
+    assert bench.result_digest(R(sets[:3] + [((1, 2, 7), 13)] + sets[4:])) != d
+    assert bench.result_digest(R(sets[:3] + [((1, 2, 8), 12)] + sets[4:])) != d
+    assert bench.result_digest(R([])) == (0, 0)
+
+
+def test_traffic_records_follow_the_sources():
+    """A DRAM-traffic record is reported only while the CUDA sources hash to the value it was captured with."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.sources_sha256()
+    assert len(h) == 64 and h == bench.sources_sha256()
+    for name, rec in bench.CAPTURES.items():
+        assert set(rec) >= {"sources_sha256", "date", "summary", "kernels", "step"}
+        assert os.path.exists(os.path.join(ROOT, rec["summary"]))
+    saved = dict(bench.CAPTURES)
+    try:
+        bench.CAPTURES["x"] = {"sources_sha256": "0" * 64, "date": "d", "summary": "s", "kernels": {}, "step": 1}
+        rec, why = bench.captured("x")
+        assert rec is None and "changed" in why
+        bench.CAPTURES["x"]["sources_sha256"] = h
+        rec, why = bench.captured("x")
+        assert rec is not None and h[:12] in why
+        assert bench.captured("nothing")[0] is None
+    finally:
+        bench.CAPTURES.clear()
+        bench.CAPTURES.update(saved)

@@ -103,3 +103,34 @@ def test_itemset_limit_stops_exploding_job():
     off2, items2, N2, ms2 = good_req
     assert res.as_dict() == odict(oracle.eclat(off2, items2, N2, ms2))
     srv.free()
+
+
+def test_long_jobs_overlap_on_the_device_and_stay_exact():
+    """Continuous batching, not a queue alone: two long jobs submitted together run on the device at the
+    same time (their device intervals, from CUDA events on their slots' streams, intersect), and each
+    result equals the job's result alone and the oracle's."""
+    jobs = []
+    for seed, D in ((11, 60_000), (12, 60_000)):
+        w = synth.make_workload("sparse_mid", D=D, seed=seed)
+        ms = synth.abs_minsup(w["rel_minsup"], D)
+        jobs.append((w["offsets"], w["items"], w["N"], ms))
+    alone = []
+    for off, items, N, ms in jobs:
+        db = fim.build_vertical_db(off, items, N, prefilter_minsup=ms)
+        alone.append(db.mine(ms).as_dict())
+        db.free()
+    srv = fim.Server(slots=2, ctas_per_sm=1)
+    ids = [srv.submit(off, items, N, ms, sample_rate=0.01) for off, items, N, ms in jobs]
+    spans = []
+    for k, jid in enumerate(ids):
+        res, lat, svc, (t0, t1) = srv.wait_ex(jid)
+        assert 0 <= t0 < t1
+        spans.append((t0, t1))
+        got = res.as_dict()
+        assert got == alone[k]
+        off, items, N, ms = jobs[k]
+        assert got == odict(oracle.eclat(off, items, N, ms))
+    assert srv.stats()["peak_in_flight"] == 2
+    srv.free()
+    (a0, a1), (b0, b1) = spans
+    assert max(a0, b0) < min(a1, b1), spans  # the two device intervals intersect
