@@ -90,6 +90,9 @@ typedef struct {
 enum { FIM_DFS_NODES = 0, FIM_DFS_FRAMES = 1, FIM_DFS_AUTO = 2, FIM_DFS_SPARSE = 3, FIM_DFS_WARP = 4,
        FIM_DFS_PROJECTED = 5 };
 
+/* Which itemsets fim_mine returns (fim_mine_opts.output). */
+enum { FIM_OUTPUT_ALL = 0, FIM_OUTPUT_CLOSED = 1, FIM_OUTPUT_MAXIMAL = 2 };
+
 /* Level-2 pair counts (fim_mine_opts.pair_kernel): FIM_PAIR_CORES: AND + popcount on the integer
  * pipes (8-word carry-save adder tree); FIM_PAIR_TENSOR: the 0/1 rows widened to 4-bit values
  * (1.0 in e2m1, two transactions per byte) and multiplied on the tensor cores (tcgen05
@@ -154,6 +157,19 @@ typedef struct {
   uint64_t proj_stack_words;   /* first stack of one warp, in 32-bit words                         */
   uint32_t proj_max_row_words; /* widest class bitmap (words) that is projected (default: 1/8 of the
                                   first stack)                                                      */
+  uint32_t output;             /* FIM_OUTPUT_ALL (0, default): every frequent itemset;
+                                  FIM_OUTPUT_MAXIMAL: only the maximal ones (Def. "Maximal Frequent
+                                  Itemset"); the DFS writes only its leaves (itemsets with no
+                                  frequent extension by a later item: the candidates on an MFI of
+                                  the DFS-MFI-Schema, Ch. 7), and a pass drops every leaf that has
+                                  a one-item-larger superset among the leaves (a non-maximal leaf
+                                  always has one, so this is the schema's superset check); it takes
+                                  the projected DFS (rows of at most 65,535 16-byte words);
+                                  FIM_OUTPUT_CLOSED: only the closed ones (Def. "Closed itemset"):
+                                  the whole result, then a pass that drops every itemset with a
+                                  one-item-larger superset of equal support.  Supports are exact in
+                                  every mode; stats.n_frequent counts the itemsets returned      */
+  uint32_t output_reserved;    /* 0                                                                 */
   uint32_t proj_split_words;   /* a frame whose next level would read more 32-bit words than this is
                                   handed to the other warps with its own database part (0 = automatic:
                                   64 x the mean bitmap width of the class regions, at least 128 and

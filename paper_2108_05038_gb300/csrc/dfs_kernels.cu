@@ -86,7 +86,8 @@ __global__ void k_surv_count(const uint32_t* __restrict__ C2, uint32_t n1, uint3
 // sample whose supports stay on the device), where rows below minsup count as nothing.
 __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t* __restrict__ row_order, uint32_t n1,
                               const uint32_t* __restrict__ row_supp, uint32_t minsup, uint32_t* __restrict__ soff,
-                              uint32_t* __restrict__ eoff, uint64_t cap_sets, uint64_t cap_items, DevCtrl* ctrl) {
+                              uint32_t* __restrict__ eoff, uint64_t cap_sets, uint64_t cap_items, DevCtrl* ctrl,
+                              uint32_t leaves) {
   __shared__ uint32_t wtot[33];
   __shared__ uint32_t n_single;
   if (threadIdx.x == 0) n_single = 0;
@@ -137,7 +138,8 @@ __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t*
     soff[n1] = carry_s;
     eoff[n1] = carry_e;
     const unsigned long long P = carry_s, n1f = n_single;
-    const unsigned long long sets = n1f + P, items = n1f + 2 * P;
+    // (leaves only: the records of levels 1 and 2 are reserved one by one by k_level2_leaves)
+    const unsigned long long sets = leaves ? 0ull : n1f + P, items = leaves ? 0ull : n1f + 2 * P;
     ctrl->packed = (sets << 32) | items;
     ctrl->sets_total = sets;
     ctrl->items_total = items;
@@ -145,7 +147,7 @@ __global__ void k_level2_scan(const uint32_t* __restrict__ scnt, const uint32_t*
     ctrl->n_entries = carry_e;
     ctrl->pending = carry_e;
     ctrl->queue_head = 0;
-    ctrl->max_len = n1f > 0 ? (P > 0 ? 2u : 1u) : 0u;
+    ctrl->max_len = leaves ? 0u : (n1f > 0 ? (P > 0 ? 2u : 1u) : 0u);
     if (cap_sets && (sets > cap_sets || items > cap_items)) ctrl->err |= DEV_ERR_OVERFLOW;  // 0: count only
   }
 }
@@ -200,6 +202,45 @@ __global__ void k_level2_fill(const uint32_t* __restrict__ C2, uint32_t n1, uint
     }
     pos0 += tot;
     __syncthreads();
+  }
+}
+
+// Leaves of levels 1 and 2 (maximal output): one warp per row i that is frequent.  {i} is a leaf when no
+// pair {i, j} is frequent; otherwise {i, s_last} (its last survivor, which has no later candidate) is one,
+// while the other pairs are the DFS's class nodes and write their own leaves.
+__global__ void k_level2_leaves(const uint32_t* __restrict__ C2, uint32_t n1, uint32_t minsup,
+                                const uint32_t* __restrict__ frows, const uint32_t* __restrict__ row_supp,
+                                const uint32_t* __restrict__ rank_item, const uint32_t* __restrict__ scnt,
+                                const uint32_t* __restrict__ soff, const uint32_t* __restrict__ sitems,
+                                uint64_t* __restrict__ out_off, uint32_t* __restrict__ out_items,
+                                uint32_t* __restrict__ out_supp, uint64_t cap_sets, uint64_t cap_items, DevCtrl* ctrl) {
+  const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n1 || (threadIdx.x & 31) != 0) return;
+  if (row_supp[i] < minsup) return;  // (a count-only mine over rows not filtered by support)
+  const uint32_t k = scnt[i];
+  const uint32_t id_i = rank_item[frows[i]];
+  uint32_t len = 1, a = id_i, b = 0, sp = row_supp[i];
+  if (k > 0) {
+    const uint32_t j = sitems[soff[i] + k - 1];
+    const uint32_t id_j = rank_item[frows[j]];
+    len = 2;
+    a = min(id_i, id_j);
+    b = max(id_i, id_j);
+    sp = C2[(size_t)i * n1 + j];
+  }
+  const unsigned long long base = atomicAdd(&ctrl->packed, (1ull << 32) | len);
+  atomicAdd(&ctrl->sets_total, 1ull);
+  atomicAdd(&ctrl->items_total, (unsigned long long)len);
+  atomicMax(&ctrl->max_len, len);
+  const uint64_t rec = base >> 32, it0 = base & 0xffffffffull;
+  if (!out_off) return;
+  if (rec < cap_sets && it0 + len <= cap_items) {
+    out_items[it0] = a;
+    if (len == 2) out_items[it0 + 1] = b;
+    out_off[rec] = it0;
+    out_supp[rec] = sp;
+  } else {
+    atomicOr(&ctrl->err, DEV_ERR_OVERFLOW);
   }
 }
 
@@ -380,7 +421,7 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
                                                  const uint32_t* cand, uint32_t mode, uint32_t nc, uint32_t* out_list,
                                                  uint32_t out_cap, uint32_t xlen, const uint16_t* nzl = nullptr,
                                                  uint32_t nnz = 0, const uint4* vals = nullptr,
-                                                 uint32_t* out_supp = nullptr) {
+                                                 uint32_t* out_supp = nullptr, uint32_t xsupp = 0) {
   const DfsLaunch& p = A.p;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint4* pre4 = reinterpret_cast<const uint4*>(pre);
@@ -408,7 +449,7 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
       const bool f = k < nb && ck >= p.minsup;
       uint32_t tot;
       const uint32_t pos = block_flag_scan(f, wtot, &tot);
-      if (threadIdx.x == 0 && tot) {
+      if (threadIdx.x == 0 && tot && !p.leaves) {
         const unsigned long long sets = tot, items = (unsigned long long)tot * (xlen + 1);
         C.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
         atomicAdd(&p.ctrl->sets_total, sets);
@@ -433,8 +474,8 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
         }
         const uint64_t rec = (C.base >> 32) + pos;
         const uint64_t it0 = (C.base & 0xffffffffull) + (uint64_t)pos * (xlen + 1);
-        if (!p.out_off) {
-          // count only: no records
+        if (!p.out_off || p.leaves) {
+          // count only, or leaves only (the node's one record follows): no records here
         } else if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
           uint32_t* dst = p.out_items + it0;
           uint32_t q = 0;
@@ -453,6 +494,33 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
       }
       nsurv += tot;
       __syncthreads();
+    }
+  }
+  // leaves only (maximal output): one record, X itself when no candidate survives, else X with its last
+  // survivor, which has no later candidate
+  if (p.leaves && threadIdx.x == 0) {
+    const uint32_t len = nsurv ? xlen + 1 : xlen;
+    const uint32_t v = nsurv ? out_list[2 * (nsurv - 1) + 1] : 0xffffffffu;
+    const uint32_t sp = nsurv ? out_supp[nsurv - 1] : xsupp;
+    const unsigned long long base = atomicAdd(&p.ctrl->packed, (1ull << 32) | len);
+    atomicAdd(&p.ctrl->sets_total, 1ull);
+    atomicAdd(&p.ctrl->items_total, (unsigned long long)len);
+    atomicMax(&p.ctrl->max_len, len);
+    const uint64_t rec = base >> 32, it0 = base & 0xffffffffull;
+    if (p.out_off && rec < p.cap_sets && it0 + len <= p.cap_items) {
+      uint32_t* dst = p.out_items + it0;
+      uint32_t q = 0;
+      bool placed = v == 0xffffffffu;
+      for (uint32_t x = 0; x < xlen; ++x) {
+        const uint32_t u = xid[x];
+        if (!placed && v < u) { dst[q++] = v; placed = true; }
+        dst[q++] = u;
+      }
+      if (!placed) dst[q] = v;
+      p.out_off[rec] = it0;
+      p.out_supp[rec] = sp;
+    } else if (p.out_off) {
+      atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
     }
   }
   return nsurv;
@@ -1130,7 +1198,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
     }
     const uint32_t ns = process_node<VEC>(A, C, cnt, wtot, xid, slot_pre(0), !listed, p.sitems + base + m + 1,
                                           CAND_FROW, nc, slot_list(0), list_cap, 2, listed ? sidx : nullptr, nz,
-                                          listed ? sval : nullptr, slot_supp(0));
+                                          listed ? sval : nullptr, slot_supp(0), supp0);
     if (ns >= 2) save(0, listed, nz);
     // the next step of the DFS (thread 0): expand the next child of the top frame, pop the frame, or
     // finish the class; every thread has read the previous step when thread 0 runs this
@@ -1207,7 +1275,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
       const uint32_t n2 = process_node<VEC>(A, C, cnt, wtot, xid, slot_pre(d + 1), !listed2,
                                             slot_list(d) + 2 * coff, CAND_PAIR, ncc, slot_list(d + 1), list_cap, xl,
                                             listed2 ? sidx : nullptr, nz2, listed2 ? sval : nullptr,
-                                            slot_supp(d + 1));
+                                            slot_supp(d + 1), C.s_supp);
       if (n2 >= 2) save(d + 1, listed2, nz2);
       if (threadIdx.x == 0) {
         ++st_nodes;
@@ -1956,16 +2024,24 @@ cudaError_t launch_level2_counts(const LevelLaunch& p, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_level2_scan<<<1, 1024, 0, st>>>(p.scnt, p.row_order, p.n1, p.row_supp, p.minsup, p.soff, p.eoff, p.cap_sets,
-                                    p.cap_items, p.ctrl);
+                                    p.cap_items, p.ctrl, p.leaves);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_level2_fill(const LevelLaunch& p, cudaStream_t st) {
   if (p.n1 == 0) return cudaSuccess;
+  // (leaves only: the fill writes the queue and survivor lists, no records)
   k_level2_fill<<<p.n1, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.frows, p.row_supp, p.rank_item, p.row_order, p.scnt,
-                                      p.soff, p.eoff, p.sitems, p.entries, p.out_off, p.out_items, p.out_supp,
-                                      p.cap_sets, p.cap_items, p.class_sets, p.eoffx, p.entries_f);
+                                      p.soff, p.eoff, p.sitems, p.entries, p.leaves ? nullptr : p.out_off,
+                                      p.out_items, p.out_supp, p.cap_sets, p.cap_items, p.class_sets, p.eoffx,
+                                      p.entries_f);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !p.leaves) return e;
+  k_level2_leaves<<<(p.n1 + 7) / 8, 256, 0, st>>>(p.C2, p.n1, p.minsup, p.frows, p.row_supp, p.rank_item, p.scnt,
+                                                  p.soff, p.sitems, p.out_off, p.out_items, p.out_supp, p.cap_sets,
+                                                  p.cap_items, p.ctrl);
   note_launch();
   return cudaGetLastError();
 }

@@ -54,6 +54,7 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   else if (cfg.mode == 4) ep->mode = warp_ok ? 4u : (list_ok && !cfg.donate ? 3u : 0u);
   else ep->mode = cfg.mode == 1 ? 1u : 0u;
   ep->proj = ep->mode == 3 && (cfg.mode == 5 || auto_proj);
+  ep->leaves = cfg.output == FIM_OUTPUT_MAXIMAL;  // (mine_input made such a mine projected)
   ep->donate = ep->mode == 0 ? cfg.donate : 0u;  // only dense node expansion donates
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
@@ -249,6 +250,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
                  ep.d_soff, ep.d_eoff, ep.d_sitems, ep.d_entries, ep.d_off, ep.d_items, ep.d_supp,
                  ep.count_only ? 0ull : ep.cap_sets, ep.count_only ? 0ull : ep.cap_items, ep.d_ctrl,
                  ep.d_class_sets};
+  ll.leaves = ep.leaves ? 1u : 0u;
   ProjLaunch pj{};
   if (ep.proj && ep.n1 >= 3) {
     // level-2 counts, the projection plan (which classes get their database part, and the split of the
@@ -299,6 +301,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.class_work = ep.d_class_work;
     dl.max_sets = ep.max_sets;
     dl.cta_time = ep.d_cta_time;
+    dl.leaves = ep.leaves ? 1u : 0u;
     if (ep.proj) {
       // Phase 3 (the classes' database parts), Phase 4 (one warp per two-item class), then the sparse
       // node mode on the classes left out

@@ -409,6 +409,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->pstack_words = o->proj_stack_words;
   c->proj_w_cap = o->proj_max_row_words;
   c->split_words = o->proj_split_words;
+  c->output = o->output;
   c->spin_limit = o->spin_limit;
   c->cap_sets = o->out_capacity_sets;
   c->cap_items = o->out_capacity_items;
@@ -450,6 +451,13 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
     in->identity_order = true;
   }
   engine_config_from_opts(opts, cfg);
+  if (cfg->output > FIM_OUTPUT_MAXIMAL) return fail(FIM_ERR_INVALID, "unknown output kind");
+  if (cfg->output == FIM_OUTPUT_MAXIMAL) {
+    // the leaves are written by the projected DFS (and its sparse fallback)
+    if (db->stride / 4 > 65535) return fail(FIM_ERR_INVALID, "maximal output needs rows of at most 65,535 16-byte words");
+    cfg->mode = FIM_DFS_PROJECTED;
+    cfg->donate = 0;
+  }
   // first output capacity: |F| of the whole database at about the same relative minsup is of
   // the order of the sample's |F_s|, so a few times |F_s| usually avoids a second DFS run
   // (when the sample's minsup had to be raised, its count at the requested minsup passed the
@@ -768,6 +776,11 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
     opts->out_needed_items = eo.ctrl.items_total;
   }
   if (s != FIM_OK) return s;
+  if (cfg.output != FIM_OUTPUT_ALL) {  // closed or maximal: the pass over the output's own supersets
+    FIM_TRY(filter_output(db->ws, db->stream, cfg.output == FIM_OUTPUT_CLOSED ? 1 : 2, &eo, db->num_sms));
+    stats->n_frequent = eo.n_sets;
+    stats->n_items_out = eo.n_items;
+  }
   if (work_out) {  // per row: level-2 candidates (the later frequent rows) + the DFS below the class
     std::fill(work_out, work_out + db->n_rows, 0ull);
     if (in.n1) {

@@ -116,6 +116,11 @@ enum WsSlot {
   WS_PSTACK,     // per-warp DFS stacks
   WS_ENTRIES_F,  // queue of the two-item classes whose class was not projected
   WS_PROJ_DQ,    // queue of the children of split frames
+  WS_FILT_TABLE, // closed / maximal output: hash table and flags
+  WS_FILT_OFF,   // the kept itemsets: offsets
+  WS_FILT_ITEMS, // items
+  WS_FILT_SUPP,  // supports
+  WS_FILT_SCAN,  // block sums of the compaction
   WS_COUNT
 };
 
@@ -283,6 +288,7 @@ struct EngineConfig {
   uint32_t proj_w_cap = 0;
   uint64_t proj_y_cap = 0;
   uint64_t split_words = 0;  // 0 = automatic; else a frame whose next level reads more words is split
+  uint32_t output = 0;       // FIM_OUTPUT_*: maximal makes the DFS write its leaves only
 };
 
 // Everything one mining call launches, with its geometry and buffers.  The
@@ -314,6 +320,7 @@ struct EnginePlan {
   uint8_t* d_X = nullptr;   // widened rows (pair_mma only)
   // projected DFS (mode 5): budgets, geometry and buffers; the fallback runs the sparse node mode with
   // the geometry above
+  bool leaves = false;  // write only the DFS's leaves (itemsets without a frequent later extension)
   bool proj = false;
   uint64_t proj_y_cap = 0, proj_t_cap = 0, pstack_words = 0;
   uint32_t proj_w_cap = 0, proj_grid = 0;
@@ -349,6 +356,10 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
                          bool* retry);
 // the EngineInput / EngineConfig of a fim_mine call (validation included)
 fim_status mine_input(fim_db* db, uint32_t minsup, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg);
+// keeps the itemsets of an engine output whose closed (keep = 1) or maximal (keep = 2) flag is set, decided
+// by the immediate supersets within the output itself (result_flags.cu); the output's buffers are replaced
+// by workspace buffers holding the kept itemsets in their original order
+fim_status filter_output(Workspace& ws, cudaStream_t st, uint8_t keep, EngineOutput* eo, int num_sms);
 // fim_result from an engine output (device copy or host copy per on_device)
 fim_status make_result(cudaStream_t st, const EngineOutput& eo, bool on_device, fim_result** out);
 fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg,
@@ -413,6 +424,7 @@ struct LevelLaunch {
   const uint32_t* eoffx;           // optional (projected DFS): entry offset per queue position, bit 31 =
                                    // the class's entries go to the fallback queue entries_f
   uint2* entries_f;
+  uint32_t leaves;                 // 1: records only for the leaves of levels 1 and 2 (k_level2_leaves)
 };
 cudaError_t launch_level2(const LevelLaunch& p, cudaStream_t st);
 // the level-2 kernels up to the entry offsets, and the fill kernel alone (the projected DFS plans its
@@ -451,6 +463,8 @@ struct DfsLaunch {
   unsigned long long* class_sets;  // optional: frequent itemsets per top class
   const uint32_t* C2;              // level-2 pair counts (n1 x n1): supports of the root prefixes
   uint32_t queue_sel;              // 0: the main queue; 1: the projected mode's fallback queue
+  uint32_t leaves;                 // 1: a node writes one record: itself when no candidate survives, else
+                                   // itself with its last survivor (the DFS's leaves; maximal output)
   // projected DFS (mode 5) only
   const uint32_t* row_supp;        // support of every frequent row (n1)
   const uint64_t* yoff;            // word offset of class i's bitmaps in Y (~0 = not projected)

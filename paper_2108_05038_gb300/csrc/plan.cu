@@ -121,6 +121,7 @@ fim_status fim_plan_create(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts,
   EngineInput in;
   EngineConfig cfg;
   FIM_TRY(mine_input(db, minsup_abs, opts, &in, &cfg));
+  if (cfg.output != FIM_OUTPUT_ALL) return fail(FIM_ERR_INVALID, "a plan returns every frequent itemset (output 0)");
   cfg.collect_times = false;
   fim_plan* plan = new (std::nothrow) fim_plan();
   if (!plan) return fail(FIM_ERR_OOM, "host allocation");

@@ -490,6 +490,45 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       cls_work += nc;
       ++st_nodes;
       st_bytes += 4ull * (nc + 1) * V.W;
+      if (p.leaves) {  // maximal output: one record, X alone or X with its last survivor (a leaf either way)
+        __syncwarp();
+        uint32_t sp = 0, v = kFull;
+        if (nout) {
+          v = V.rids[out[2 * (nout - 1)]];
+          sp = out[2 * (nout - 1) + 1];
+        } else {
+          for (uint32_t w = lane; w < V.W; w += 32) sp += __popc(pre[w]);
+          sp = __reduce_add_sync(kFull, sp);
+        }
+        const uint32_t len = nout ? xlen + 1 : xlen;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctrl->packed, (1ull << 32) | len);
+        base = __shfl_sync(kFull, base, 0);
+        st_sets += 1;
+        st_items += len;
+        st_maxlen = max(st_maxlen, len);
+        cls_sets += 1;
+        const uint64_t rec = base >> 32, it0 = base & 0xffffffffull;
+        if (p.out_off) {
+          if (rec < p.cap_sets && it0 + len <= p.cap_items) {
+            uint32_t pos = xlen;  // place of v among the prefix ids (none: v absent)
+            if (v != kFull) {
+              pos = 0;
+              for (uint32_t q0 = 0; q0 < xlen; q0 += 32)
+                pos += __popc(__ballot_sync(kFull, q0 + lane < xlen && xs[q0 + lane] < v));
+            }
+            for (uint32_t t = lane; t < len; t += 32)
+              p.out_items[it0 + t] = t < pos ? xs[t] : (t == pos ? v : xs[t - 1]);
+            if (lane == 0) {
+              p.out_off[rec] = it0;
+              p.out_supp[rec] = sp;
+            }
+          } else if (lane == 0) {
+            atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
+          }
+        }
+        return nout;
+      }
       if (nout == 0) return 0;
       __syncwarp();  // the list written by lane 0 is read by every lane below
       unsigned long long base = 0;
