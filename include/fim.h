@@ -169,7 +169,10 @@ typedef struct {
                                   the whole result, then a pass that drops every itemset with a
                                   one-item-larger superset of equal support.  Supports are exact in
                                   every mode; stats.n_frequent counts the itemsets returned      */
-  uint32_t output_reserved;    /* 0                                                                 */
+  uint32_t diffsets;           /* FIM_DFS_PROJECTED frames as diffsets (dEclat, App. B.4.3): 0 never
+                                  (default), 1 where the lists of their nonzero words are at most a
+                                  quarter of the bitmaps, 2 every frame; d(PXY) = d(PY) \ d(PX) and
+                                  supp(PXY) = supp(PX) - |d(PXY)|, exact                          */
   uint32_t proj_split_words;   /* a frame whose next level would read more 32-bit words than this is
                                   handed to the other warps with its own database part (0 = automatic:
                                   64 x the mean bitmap width of the class regions, at least 128 and

@@ -55,6 +55,7 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   else ep->mode = cfg.mode == 1 ? 1u : 0u;
   ep->proj = ep->mode == 3 && (cfg.mode == 5 || auto_proj);
   ep->leaves = cfg.output == FIM_OUTPUT_MAXIMAL;  // (mine_input made such a mine projected)
+  ep->diffsets = cfg.diffsets;
   ep->donate = ep->mode == 0 ? cfg.donate : 0u;  // only dense node expansion donates
   ep->spin_limit = cfg.spin_limit ? cfg.spin_limit : 2000000ull;
   ep->fixed_capacity = cfg.fixed_capacity;
@@ -302,6 +303,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     dl.max_sets = ep.max_sets;
     dl.cta_time = ep.d_cta_time;
     dl.leaves = ep.leaves ? 1u : 0u;
+    dl.diffsets = ep.diffsets;
     if (ep.proj) {
       // Phase 3 (the classes' database parts), Phase 4 (one warp per two-item class), then the sparse
       // node mode on the classes left out

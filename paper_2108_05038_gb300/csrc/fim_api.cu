@@ -410,6 +410,7 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
   c->proj_w_cap = o->proj_max_row_words;
   c->split_words = o->proj_split_words;
   c->output = o->output;
+  c->diffsets = o->diffsets;
   c->spin_limit = o->spin_limit;
   c->cap_sets = o->out_capacity_sets;
   c->cap_items = o->out_capacity_items;
@@ -452,6 +453,7 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
   }
   engine_config_from_opts(opts, cfg);
   if (cfg->output > FIM_OUTPUT_MAXIMAL) return fail(FIM_ERR_INVALID, "unknown output kind");
+  if (cfg->diffsets > 2) return fail(FIM_ERR_INVALID, "diffsets must be 0, 1 or 2");
   if (cfg->output == FIM_OUTPUT_MAXIMAL) {
     // the leaves are written by the projected DFS (and its sparse fallback)
     if (db->stride / 4 > 65535) return fail(FIM_ERR_INVALID, "maximal output needs rows of at most 65,535 16-byte words");

@@ -289,6 +289,7 @@ struct EngineConfig {
   uint64_t proj_y_cap = 0;
   uint64_t split_words = 0;  // 0 = automatic; else a frame whose next level reads more words is split
   uint32_t output = 0;       // FIM_OUTPUT_*: maximal makes the DFS write its leaves only
+  uint32_t diffsets = 0;     // projected DFS: 0 never, 1 where smaller than bitmaps, 2 always
 };
 
 // Everything one mining call launches, with its geometry and buffers.  The
@@ -321,6 +322,7 @@ struct EnginePlan {
   // projected DFS (mode 5): budgets, geometry and buffers; the fallback runs the sparse node mode with
   // the geometry above
   bool leaves = false;  // write only the DFS's leaves (itemsets without a frequent later extension)
+  uint32_t diffsets = 0;
   bool proj = false;
   uint64_t proj_y_cap = 0, proj_t_cap = 0, pstack_words = 0;
   uint32_t proj_w_cap = 0, proj_grid = 0;
@@ -463,6 +465,8 @@ struct DfsLaunch {
   unsigned long long* class_sets;  // optional: frequent itemsets per top class
   const uint32_t* C2;              // level-2 pair counts (n1 x n1): supports of the root prefixes
   uint32_t queue_sel;              // 0: the main queue; 1: the projected mode's fallback queue
+  uint32_t diffsets;               // projected DFS: 0 bitmaps only, 1 diffset frames where they are small,
+                                   // 2 every frame as diffsets
   uint32_t leaves;                 // 1: a node writes one record: itself when no candidate survives, else
                                    // itself with its last survivor (the DFS's leaves; maximal output)
   // projected DFS (mode 5) only

@@ -311,6 +311,7 @@ constexpr int kG = 8;   // candidates counted per round
 constexpr int kPR = 2;  // prefix words per lane per chunk (64 words)
 constexpr unsigned long long kIdleNs = 2000000000ull;  // no item finished anywhere for 2 s: give up
 constexpr uint32_t kIdentity = 0xffffffffu;  // frame list: every row of the region, in order
+constexpr unsigned long long kDiffFrame = 1ull;  // frame prefix marker: the survivors are held as diffsets
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* a) { return *(volatile const uint32_t*)a; }
 
@@ -442,6 +443,81 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
     unsigned long long cls_sets = 0, cls_work = 0;
     for (uint32_t q = lane; q < R0.xlen; q += 32) path[q] = R0.R[8 + q];
 
+    // Records of a node X (ids xs[0, xlen)) whose survivors are the rows out[0], out[st], out[2 st], ... with
+    // supports out[1], out[st + 1], ...: one record X u {s} per survivor, or, when only the leaves are written
+    // (maximal output), one record: X with its last survivor, or X alone (support xsupp) when none survived.
+    auto emit = [&](const RegionView& V, const uint32_t* out, uint32_t st, uint32_t nout, uint32_t xlen,
+                    uint32_t xsupp) {
+      __syncwarp();  // the list written by lane 0 is read by every lane below
+      if (p.leaves) {
+        const uint32_t v = nout ? V.rids[out[st * (nout - 1)]] : kFull;
+        const uint32_t sp = nout ? out[st * (nout - 1) + 1] : xsupp;
+        const uint32_t len = nout ? xlen + 1 : xlen;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctrl->packed, (1ull << 32) | len);
+        base = __shfl_sync(kFull, base, 0);
+        st_sets += 1;
+        st_items += len;
+        st_maxlen = max(st_maxlen, len);
+        cls_sets += 1;
+        const uint64_t rec = base >> 32, it0 = base & 0xffffffffull;
+        if (p.out_off) {
+          if (rec < p.cap_sets && it0 + len <= p.cap_items) {
+            uint32_t pos = xlen;  // place of v among the prefix ids (none: v absent)
+            if (v != kFull) {
+              pos = 0;
+              for (uint32_t q0 = 0; q0 < xlen; q0 += 32)
+                pos += __popc(__ballot_sync(kFull, q0 + lane < xlen && xs[q0 + lane] < v));
+            }
+            for (uint32_t t = lane; t < len; t += 32)
+              p.out_items[it0 + t] = t < pos ? xs[t] : (t == pos ? v : xs[t - 1]);
+            if (lane == 0) {
+              p.out_off[rec] = it0;
+              p.out_supp[rec] = sp;
+            }
+          } else if (lane == 0) {
+            atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
+          }
+        }
+        return;
+      }
+      if (nout == 0) return;
+      unsigned long long base = 0;
+      // one atomic per node reserves its records; the exact totals and the longest length are added once per
+      // warp at the end (nothing reads them while the kernel runs)
+      if (lane == 0) {
+        const unsigned long long sets = nout, items = (unsigned long long)nout * (xlen + 1);
+        base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+        const unsigned long long after = (base >> 32) + sets;
+        if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+      }
+      base = __shfl_sync(kFull, base, 0);
+      st_sets += nout;
+      st_items += (unsigned long long)nout * (xlen + 1);
+      st_maxlen = max(st_maxlen, xlen + 1);
+      cls_sets += nout;
+      if (p.out_off) {
+        for (uint32_t o = 0; o < nout; ++o) {
+          const uint32_t v = V.rids[out[st * o]];
+          const uint64_t rec = (base >> 32) + o;
+          const uint64_t it0 = (base & 0xffffffffull) + (uint64_t)o * (xlen + 1);
+          if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
+            uint32_t pos = 0;  // place of v among the prefix ids
+            for (uint32_t q0 = 0; q0 < xlen; q0 += 32)
+              pos += __popc(__ballot_sync(kFull, q0 + lane < xlen && xs[q0 + lane] < v));
+            for (uint32_t t = lane; t <= xlen; t += 32)
+              p.out_items[it0 + t] = t < pos ? xs[t] : (t == pos ? v : xs[t - 1]);
+            if (lane == 0) {
+              p.out_off[rec] = it0;
+              p.out_supp[rec] = out[st * o + 1];
+            }
+          } else if (lane == 0) {
+            atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
+          }
+        }
+      }
+    };
+
     // Counts candidates (rows of region V: c0, c0 + 1, ... when clist is NULL, else clist[0], clist[2], ...)
     // against prefix `pre` (V.W words), writes the survivors as (row, support) pairs to out and one record
     // per survivor; returns the survivor count.  Candidate words are read only under nonzero prefix words.
@@ -490,81 +566,12 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       cls_work += nc;
       ++st_nodes;
       st_bytes += 4ull * (nc + 1) * V.W;
-      if (p.leaves) {  // maximal output: one record, X alone or X with its last survivor (a leaf either way)
-        __syncwarp();
-        uint32_t sp = 0, v = kFull;
-        if (nout) {
-          v = V.rids[out[2 * (nout - 1)]];
-          sp = out[2 * (nout - 1) + 1];
-        } else {
-          for (uint32_t w = lane; w < V.W; w += 32) sp += __popc(pre[w]);
-          sp = __reduce_add_sync(kFull, sp);
-        }
-        const uint32_t len = nout ? xlen + 1 : xlen;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctrl->packed, (1ull << 32) | len);
-        base = __shfl_sync(kFull, base, 0);
-        st_sets += 1;
-        st_items += len;
-        st_maxlen = max(st_maxlen, len);
-        cls_sets += 1;
-        const uint64_t rec = base >> 32, it0 = base & 0xffffffffull;
-        if (p.out_off) {
-          if (rec < p.cap_sets && it0 + len <= p.cap_items) {
-            uint32_t pos = xlen;  // place of v among the prefix ids (none: v absent)
-            if (v != kFull) {
-              pos = 0;
-              for (uint32_t q0 = 0; q0 < xlen; q0 += 32)
-                pos += __popc(__ballot_sync(kFull, q0 + lane < xlen && xs[q0 + lane] < v));
-            }
-            for (uint32_t t = lane; t < len; t += 32)
-              p.out_items[it0 + t] = t < pos ? xs[t] : (t == pos ? v : xs[t - 1]);
-            if (lane == 0) {
-              p.out_off[rec] = it0;
-              p.out_supp[rec] = sp;
-            }
-          } else if (lane == 0) {
-            atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
-          }
-        }
-        return nout;
+      uint32_t xsupp = 0;
+      if (p.leaves && nout == 0) {  // a leaf's own support: the popcount of its prefix
+        for (uint32_t w = lane; w < V.W; w += 32) xsupp += __popc(pre[w]);
+        xsupp = __reduce_add_sync(kFull, xsupp);
       }
-      if (nout == 0) return 0;
-      __syncwarp();  // the list written by lane 0 is read by every lane below
-      unsigned long long base = 0;
-      // one atomic per node reserves its records; the exact totals and the longest length are added once per
-      // warp at the end (nothing reads them while the kernel runs)
-      if (lane == 0) {
-        const unsigned long long sets = nout, items = (unsigned long long)nout * (xlen + 1);
-        base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
-        const unsigned long long after = (base >> 32) + sets;
-        if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
-      }
-      base = __shfl_sync(kFull, base, 0);
-      st_sets += nout;
-      st_items += (unsigned long long)nout * (xlen + 1);
-      st_maxlen = max(st_maxlen, xlen + 1);
-      cls_sets += nout;
-      if (p.out_off) {
-        for (uint32_t o = 0; o < nout; ++o) {
-          const uint32_t v = V.rids[out[2 * o]];
-          const uint64_t rec = (base >> 32) + o;
-          const uint64_t it0 = (base & 0xffffffffull) + (uint64_t)o * (xlen + 1);
-          if (rec < p.cap_sets && it0 + xlen + 1 <= p.cap_items) {
-            uint32_t pos = 0;  // place of v among the prefix ids
-            for (uint32_t q0 = 0; q0 < xlen; q0 += 32)
-              pos += __popc(__ballot_sync(kFull, q0 + lane < xlen && xs[q0 + lane] < v));
-            for (uint32_t t = lane; t <= xlen; t += 32)
-              p.out_items[it0 + t] = t < pos ? xs[t] : (t == pos ? v : xs[t - 1]);
-            if (lane == 0) {
-              p.out_off[rec] = it0;
-              p.out_supp[rec] = out[2 * o + 1];
-            }
-          } else if (lane == 0) {
-            atomicOr(&p.ctrl->err, DEV_ERR_OVERFLOW);
-          }
-        }
-      }
+      emit(V, out, 2, nout, xlen, xsupp);
       return nout;
     };
 
@@ -726,6 +733,101 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       __syncwarp();
       if (lane == 0) fr_cur[depth] = kk + 1;
       const RegionView V = region_view(reinterpret_cast<const uint32_t*>(fr_R[depth]));
+      if (fr_P[depth] == kDiffFrame) {
+        // A frame [X | S] held as diffsets (dEclat, App. B.4.3): survivor s has the list of the nonzero words
+        // of d(X u {s}) = t(X) \ t(X u {s}) over the region's words.  Child X' = X u {s_k}: its diffset is
+        // scattered into a dense W-word bitmap dK; for every later survivor s_j, d(X' u {s_j}) = d(X u {s_j}) \
+        // d(X') (the list filtered by dK) and supp(X' u {s_j}) = supp(X') - |d(X' u {s_j})|.
+        const uint32_t* ent = stk + fr_L[depth];  // per survivor: row, support, list offset, list entries
+        const uint32_t sj = ent[4 * kk], supp_k = ent[4 * kk + 1];
+        const uint32_t* Lk = stk + ent[4 * kk + 2];
+        const uint32_t lenk = ent[4 * kk + 3];
+        const uint32_t plen = (uint32_t)(R0.xlen + depth);
+        const uint32_t ncc = nf - kk - 1;
+        if (plen + 1 >= L1) {
+          if (lane == 0) atomicOr(&p.ctrl->err, DEV_ERR_DEPTH);
+          break;
+        }
+        if (lane == 0) path[plen] = V.rids[sj];
+        sort_path(plen + 1);
+        uint32_t sumlen = 0;  // list entries of the candidates: the filtered lists take at most as many
+        for (uint32_t t = lane; t < ncc; t += 32) sumlen += ent[4 * (kk + 1 + t) + 3];
+        sumlen = __reduce_add_sync(kFull, sumlen);
+        const uint64_t words = (uint64_t)V.Wp + 4ull * ncc + 2ull * sumlen;
+        if ((uint64_t)top + words + 3 > p.pstack_words) {
+          need = (uint64_t)top + words + 3;
+          overflow = true;
+          break;
+        }
+        uint32_t* dK = stk + top;
+        for (uint32_t w = lane; w < V.W; w += 32) dK[w] = 0u;
+        __syncwarp();
+        for (uint32_t e = lane; e < lenk; e += 32) dK[Lk[2 * e]] = Lk[2 * e + 1];
+        __syncwarp();
+        uint32_t* ent2 = dK + V.Wp;
+        const uint32_t lists2 = top + V.Wp + 4 * ncc;  // stack offset of the filtered lists
+        uint32_t nout = 0, carry = 0;
+        for (uint32_t t0 = 0; t0 < ncc; t0 += 32) {
+          const uint32_t t = t0 + lane;
+          const bool ok = t < ncc;
+          const uint32_t* ej = ent + 4 * (kk + 1 + (ok ? t : 0));
+          const uint32_t len = ok ? ej[3] : 0u;
+          // this lane's filtered list goes after the lists of the lanes before it (old lengths: an upper bound)
+          uint32_t incl = len;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+          }
+          const uint32_t doff = lists2 + 2 * (carry + incl - len);
+          carry += __shfl_sync(kFull, incl, 31);
+          uint32_t cnt = 0, dsz = 0;
+          if (ok) {
+            const uint32_t* Lj = stk + ej[2];
+            uint32_t* dst = stk + doff;
+            for (uint32_t e = 0; e < len; ++e) {
+              const uint32_t w = Lj[2 * e];
+              const uint32_t r = Lj[2 * e + 1] & ~dK[w];
+              dsz += __popc(r);
+              if (r) {
+                dst[2 * cnt] = w;
+                dst[2 * cnt + 1] = r;
+                ++cnt;
+              }
+            }
+          }
+          const uint32_t sn = ok ? supp_k - dsz : 0u;
+          const bool f = ok && sn >= p.minsup;
+          const uint32_t bal = __ballot_sync(kFull, f);
+          if (f) {
+            uint32_t* e2 = ent2 + 4 * (nout + __popc(bal & ((1u << lane) - 1u)));
+            e2[0] = ej[0];
+            e2[1] = sn;
+            e2[2] = doff;
+            e2[3] = cnt;
+          }
+          nout += __popc(bal);
+        }
+        st_inter += ncc;
+        cls_work += ncc;
+        ++st_nodes;
+        st_bytes += 8ull * (lenk + sumlen) + 4ull * V.W;
+        emit(V, ent2, 4, nout, plen + 1, supp_k);
+        if (nout >= 2) {
+          ++st_frames;
+          ++depth;
+          if (lane == 0) {
+            fr_R[depth] = fr_R[depth - 1];
+            fr_P[depth] = kDiffFrame;
+            fr_L[depth] = top + V.Wp;
+            fr_n[depth] = nout;
+            fr_cur[depth] = 0;
+            fr_top[depth] = top;
+          }
+          top = (uint32_t)(((uint64_t)top + words + 3) & ~3ull);
+        }
+        continue;
+      }
       const uint32_t* P = reinterpret_cast<const uint32_t*>(fr_P[depth]);
       const uint32_t lo = fr_L[depth];
       const uint32_t* list = lo == kIdentity ? nullptr : stk + lo;
@@ -774,6 +876,61 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       const uint32_t W2 = words_of(supp);
       // (stack allocations are whole 16-byte units: a compacted region's rows are written as 16-byte vectors)
       const uint64_t after_list = ((uint64_t)top + used + 2ull * n2 + 3) & ~3ull;
+      // diffsets (dEclat) when asked, or when they are at most a quarter of the bitmaps: every survivor s gets
+      // the list of the nonzero words of t(X) \ t(X u {s}) = cpre & ~Y[s] over the region's words
+      bool diff = p.diffsets == 2;
+      if (p.diffsets == 1) {
+        uint64_t dtids = 0;  // sum of the diffset sizes (an upper bound of their nonzero words)
+        for (uint32_t q = lane; q < n2; q += 32) dtids += supp - lst[2 * q + 1];
+        for (int o = 16; o > 0; o >>= 1) dtids += __shfl_xor_sync(kFull, dtids, o);
+        diff = 8 * dtids <= (uint64_t)n2 * V.W;
+      }
+      if (diff) {
+        const uint64_t ent0 = ((uint64_t)top + used + 2ull * n2 + 3) & ~3ull;  // entries after the survivor list
+        uint64_t lp = ent0 + 4ull * n2;                                       // lists after the entries
+        for (uint32_t q = 0; q < n2 && !overflow; ++q) {
+          if (lp + 2ull * V.W > p.pstack_words) {
+            need = lp + 2ull * V.W;
+            overflow = true;
+            break;
+          }
+          const uint32_t* ys = V.Y + (uint64_t)lst[2 * q] * V.Wp;
+          uint32_t cnt = 0;
+          for (uint32_t w0 = 0; w0 < V.W; w0 += 32) {
+            const uint32_t w = w0 + lane;
+            const uint32_t r = w < V.W ? cpre[w] & ~ys[w] : 0u;
+            const uint32_t bal = __ballot_sync(kFull, r != 0u);
+            if (r) {
+              uint32_t* d = stk + lp + 2 * (cnt + __popc(bal & ((1u << lane) - 1u)));
+              d[0] = w;
+              d[1] = r;
+            }
+            cnt += __popc(bal);
+          }
+          if (lane == 0) {
+            uint32_t* e = stk + ent0 + 4 * q;
+            e[0] = lst[2 * q];
+            e[1] = lst[2 * q + 1];
+            e[2] = (uint32_t)lp;
+            e[3] = cnt;
+          }
+          st_bytes += 8ull * V.W;
+          lp += 2ull * cnt;
+        }
+        if (overflow) break;
+        __syncwarp();
+        ++depth;
+        if (lane == 0) {
+          fr_R[depth] = fr_R[depth - 1];
+          fr_P[depth] = kDiffFrame;
+          fr_L[depth] = (uint32_t)ent0;
+          fr_n[depth] = n2;
+          fr_cur[depth] = 0;
+          fr_top[depth] = top;
+        }
+        top = (uint32_t)((lp + 3) & ~3ull);
+        continue;
+      }
       // hand the frame out when its next level is large: more words than split_words (given, or 64 x the mean
       // bitmap width of the class regions, set by the planning kernel)
       const unsigned long long work = (unsigned long long)n2 * (n2 - 1) / 2 * W2;

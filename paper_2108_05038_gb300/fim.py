@@ -70,7 +70,7 @@ class MineOpts(ctypes.Structure):
         ("out_capacity_sets", ctypes.c_uint64),
         ("out_capacity_items", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64), ("max_itemsets", ctypes.c_uint64),
         ("proj_bitmap_words", ctypes.c_uint64), ("proj_stack_words", ctypes.c_uint64),
-        ("proj_max_row_words", ctypes.c_uint32), ("output", ctypes.c_uint32), ("output_reserved", ctypes.c_uint32),
+        ("proj_max_row_words", ctypes.c_uint32), ("output", ctypes.c_uint32), ("diffsets", ctypes.c_uint32),
         ("proj_split_words", ctypes.c_uint32),
         ("out_needed_sets", ctypes.c_uint64),
         ("out_needed_items", ctypes.c_uint64), ("stats", ctypes.POINTER(MineStats)),
@@ -346,7 +346,7 @@ class Database:
              shape=None, dfs_mode: int | None = None, max_itemsets: int = 0, class_work: bool = False,
              dfs_depth_first: int = 0, pair_kernel: int = FIM_PAIR_AUTO, fault_pair_wait: bool = False,
              proj_bitmap_words: int = 0, proj_stack_words: int = 0, proj_max_row_words: int = 0,
-             proj_split_words: int = 0, output: str = "all"):
+             proj_split_words: int = 0, output: str = "all", diffsets: int = 0):
         """fim_mine; with ``class_work`` the result carries ``class_work`` (u64[n_rows]): the intersections
         of every one-row class, level 2 and below."""
         opts, st = self._opts(class_order, threads_per_cta, vec_per_lane, ctas_per_sm, donate, result_on_device,
@@ -359,6 +359,7 @@ class Database:
         opts.proj_max_row_words = proj_max_row_words
         opts.proj_split_words = proj_split_words
         opts.output = {"all": FIM_OUTPUT_ALL, "closed": FIM_OUTPUT_CLOSED, "maximal": FIM_OUTPUT_MAXIMAL}[output]
+        opts.diffsets = diffsets
         cw = None
         if class_work:
             cw = np.zeros(max(1, self.info()["n_rows"]), dtype=np.uint64)

@@ -140,3 +140,40 @@ def test_result_on_device_and_itemset_limit(wants):
     res.free()
     assert_same(db.mine(case[2], dfs_mode=PROJ).as_dict(), want)
     db.free()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_diffset_frames_random_vs_bruteforce(seed):
+    """Every frame of the projected DFS held as diffsets (dEclat: d(PXY) = d(PY) minus d(PX), supp(PXY) =
+    supp(PX) - |d(PXY)|): the same itemsets and supports as brute force, dense and sparse databases alike."""
+    rng = np.random.default_rng(5300 + seed)
+    N = int(rng.integers(3, 14))
+    D = int(rng.integers(1, 900))
+    dens = rng.uniform(0.05, 0.95)
+    txs = [list(np.nonzero(rng.random(N) < dens)[0]) for _ in range(D)]
+    off, items = csr(txs)
+    minsup = int(rng.integers(1, max(2, D // 3)))
+    want = odict(oracle.bruteforce(off, items, N, minsup))
+    db = fim.build_vertical_db(off, items, N, word_bits=64)
+    for mode in (1, 2):
+        assert_same(db.mine(minsup, dfs_mode=PROJ, diffsets=mode).as_dict(), want)
+    db.free()
+
+
+@pytest.mark.parametrize("name,D,minsup", [("dense_deep", 50_000, 30_000), ("dense_deep", 200_000, 120_000),
+                                           ("large_sparse", 70_000, 40), ("sparse_mid", 100_000, 250)])
+def test_diffset_frames_workloads(name, D, minsup):
+    """The deep dense workload, its law at 200,000 transactions (rows of 6,250 words), and two sparse ones:
+    tidset and diffset frames give the oracle's output, with the same class nodes and intersections; the
+    operand bytes per node of both forms are reported by the stats."""
+    w = synth.make_workload(name, D=D)
+    want = odict(oracle.eclat_mt(w["offsets"], w["items"], w["N"], minsup, 0))
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=64)
+    ref = db.mine(minsup, dfs_mode=PROJ, diffsets=0)
+    assert_same(ref.as_dict(), want)
+    for mode in (1, 2):
+        res = db.mine(minsup, dfs_mode=PROJ, diffsets=mode)
+        assert_same(res.as_dict(), want)
+        for key in ("n_intersections", "n_classes", "n_frequent"):
+            assert res.stats[key] == ref.stats[key], key
+    db.free()
