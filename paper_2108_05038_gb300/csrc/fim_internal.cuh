@@ -511,7 +511,8 @@ cudaError_t launch_dfs_proj(const DfsLaunch& p, uint32_t grid, uint32_t max_len,
 size_t dfs_proj_smem_bytes(uint32_t max_len);
 cudaError_t dfs_proj_ctas_per_sm(size_t smem, int* out);
 constexpr uint32_t kProjThreads = 256;     // projected DFS: 8 warps per CTA
-constexpr uint32_t kProjCtasPerSm = 4;     // at most 32 warps per SM (their stacks take device memory)
+constexpr uint32_t kProjCtasPerSm = 2;     // 16 warps per SM with up to 128 registers each (large_sparse's DFS:
+                                           // 5.1 ms against 7.3 ms with four CTAs at 64 registers, which spill)
 constexpr uint64_t kProjStackWords = 131072;  // first stack of one warp (doubled when a run needs more)
 constexpr uint32_t kProjDqCap = 1u << 18;     // items of split frames the queue holds
 // device bytes the projected DFS adds to a mine of `rows` frequent rows of `stride` words over a database
