@@ -303,18 +303,20 @@ def run_ours(args):
                                  if proj else
                                  "algorithmic bytes count every candidate row in full (the dense definition); the "
                                  "kernel reads row words only under nonzero prefix words")}
-        elif stats.get("pair_kernel") in (2, 3):  # level 2 on the tensor cores: the 0/1 contraction, kind::f8f6f4
+        elif stats.get("pair_kernel") in (2, 3, 4):  # level 2 on the tensor cores: the 0/1 contraction, kind::f8f6f4
             flops = 2.0 * stats["n_pair_intersections"] * D  # one multiply-add per pair and transaction
             tf = flops / (pair_avg * 1e-3) / 1e12
             peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0))
-            roofline = {"kernel": "k_expand_e2m1 + k_pair_mma" if stats.get("pair_kernel") == 2 else "k_expand_e4m3 + k_pair_mma", "bound": "tensor", "achieved": round(tf, 1),
+            kname = {2: "k_expand_e2m1 + k_pair_mma", 3: "k_expand_e4m3 + k_pair_mma",
+                     4: "k_pair_mma_fused"}[stats["pair_kernel"]]
+            roofline = {"kernel": kname, "bound": "tensor", "achieved": round(tf, 1),
                         "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(tf / peak, 4),
                         "traffic": rec["kernels"]["pair"] if rec else None, "traffic_source": rec_note,
                         "peak_source": ("kind::f8f6f4 (e2m1 and e4m3 operands alike) at the fp8 dense rate = 2 x the "
                                         "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops; nominal fp8:bf16 = 4.5:2.25)" if "bf16_tflops" in peaks
                                         else "fallback 1.9 PFLOP/s bf16 x 2"),
                         "note": "algorithmic flops: 2 x pairs i<j x transactions; the time includes widening "
-                                "the rows to the operand form"}
+                                "the rows to the operand form (inside the kernel when fused)"}
         else:
             roofline = {"kernel": "k_pair_counts", "bound": "alu", "achieved": round(achieved_gword, 1),
                         "peak": round(alu_peak_gword, 1), "unit": "Gword/s",
@@ -333,7 +335,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {1: "u32", 2: "u32 + e2m1 (level-2 0/1 products, f32 sums)",
-                      3: "u32 + e4m3 (level-2 0/1 products, f32 sums)"}.get(stats.get("pair_kernel", 1), "u32"),
+                      3: "u32 + e4m3 (level-2 0/1 products, f32 sums)",
+                      4: "u32 + e4m3 (level-2 0/1 products widened in shared memory, f32 sums)"}.get(
+                          stats.get("pair_kernel", 1), "u32"),
             "data": "synthetic",
             "config": {"workload": workload_desc(w), "sample_rate": SAMPLE_RATE,
                        "parallelism": "replicas" if world > 1 else "single GPU",

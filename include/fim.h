@@ -75,7 +75,8 @@ typedef struct {
   float ms_device_total;         /* CUDA-event time from the first to the last mining kernel       */
   float dfs_cta_busy_max_ms;     /* longest time a persistent DFS CTA was resident (collect_times)  */
   float dfs_cta_busy_mean_ms;    /* mean over the CTAs; max / mean is the load imbalance           */
-  uint32_t pair_kernel;          /* level-2 kernel that ran: FIM_PAIR_CORES / _TENSOR / _TENSOR_E4M3 */
+  uint32_t pair_kernel;          /* level-2 kernel that ran: FIM_PAIR_CORES / _TENSOR / _TENSOR_E4M3 /
+                                    _TENSOR_FUSED                                                      */
   uint32_t n_proj_classes;       /* FIM_DFS_PROJECTED: one-item classes given their database part   */
   uint64_t n_proj_splits;        /* frames handed to other warps with their own database part       */
   uint64_t n_fallback_entries;   /* two-item classes mined by the sparse node mode instead           */
@@ -99,9 +100,15 @@ enum { FIM_OUTPUT_ALL = 0, FIM_OUTPUT_CLOSED = 1, FIM_OUTPUT_MAXIMAL = 2 };
  * kind::f8f6f4, fp32 accumulators, at most 2^24 transactions per partial sum, so exact), which
  * needs a scratch of frequent rows x padded row bytes x 4 in the database's workspace;
  * FIM_PAIR_TENSOR_E4M3: the same with one byte per transaction (1.0 in e4m3, twice the scratch);
- * FIM_PAIR_AUTO: integer pipes or FIM_PAIR_TENSOR, whichever has the smaller modelled time, the
- * tensor cores only while their scratch is at most 1/16 of device memory. */
-enum { FIM_PAIR_AUTO = 0, FIM_PAIR_CORES = 1, FIM_PAIR_TENSOR = 2, FIM_PAIR_TENSOR_E4M3 = 3 };
+ * FIM_PAIR_TENSOR_FUSED: the widening done inside the tensor-core kernel (the raw bits brought to
+ * shared memory by TMA, spread to e4m3 there), no scratch and no widened copy in device memory;
+ * needs the frequent rows to be consecutive rows of the bitmap, which they are in every fim_mine
+ * (FIM_ERR_INVALID otherwise);
+ * FIM_PAIR_AUTO: integer pipes or a tensor-core kernel, whichever has the smaller modelled time:
+ * FIM_PAIR_TENSOR_FUSED for consecutive rows, else FIM_PAIR_TENSOR while its scratch is at most 1/16
+ * of device memory. */
+enum { FIM_PAIR_AUTO = 0, FIM_PAIR_CORES = 1, FIM_PAIR_TENSOR = 2, FIM_PAIR_TENSOR_E4M3 = 3,
+       FIM_PAIR_TENSOR_FUSED = 4 };
 
 typedef struct {
   uint32_t struct_size;        /* set to sizeof(fim_mine_opts); 0 = treat as defaults            */
@@ -139,8 +146,8 @@ typedef struct {
   uint32_t dfs_depth_first;    /* 0 = automatic (the full depth bound when its stack fits in 1/32 of
                                   device memory); else the first DFS stack depth, grown and the run
                                   repeated when an itemset is deeper                                */
-  uint32_t pair_kernel;        /* FIM_PAIR_AUTO (0, default), FIM_PAIR_CORES, FIM_PAIR_TENSOR or
-                                  FIM_PAIR_TENSOR_E4M3                                              */
+  uint32_t pair_kernel;        /* FIM_PAIR_AUTO (0, default), FIM_PAIR_CORES, FIM_PAIR_TENSOR,
+                                  FIM_PAIR_TENSOR_E4M3 or FIM_PAIR_TENSOR_FUSED                     */
   uint32_t fault_pair_wait;    /* 0 (default); 1 = failure-detection test: the tensor-core pair
                                   kernel expects 16 bytes per stage more than its copies bring, so
                                   its bounded waits run out (about 1 s each) and the call returns

@@ -86,19 +86,31 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
 
   ep->npairs_max = (uint64_t)n1 * (n1 - 1) / 2;
   FIM_TRY(ws_get(ws, WS_C2, (size_t)n1 * n1, &ep->d_C2));
-  // level 2 on the tensor cores when asked, or when its modelled time is lower and the widened rows
-  // (one byte per transaction) take at most 1/16 of the device memory; TMA coordinates are signed
-  // 32-bit, so widened rows of less than 2^31 bytes
+  // level 2 on the tensor cores when asked, or when its modelled time is lower: fused with the widening
+  // when the rows are consecutive, else through widened rows (at most 1/16 of the device memory; TMA
+  // coordinates are signed 32-bit, so widened rows of less than 2^31 bytes)
   if (n1 >= 2) {
-    ep->pair_e2m1 = cfg.pair_kernel != 3;
+    // the fused kernel reads the raw rows by TMA, so they must be consecutive rows of the bitmap: every mine
+    // of a whole database (the frequent rows are a suffix), and the estimate's sample when it takes all rows
+    const bool consecutive = in.frows.size() == n1 && in.frows.back() - in.frows.front() == n1 - 1;
+    ep->rows_base = consecutive ? in.bits + (size_t)in.frows.front() * in.stride : nullptr;
+    ep->pair_e2m1 = cfg.pair_kernel != FIM_PAIR_TENSOR_E4M3;
     const uint64_t xb = pair_mma_buffer_bytes(n1, in.stride, ep->pair_e2m1);
     const bool coords_ok = (uint64_t)in.stride * 32 < (1ull << 31);
-    if (cfg.pair_kernel >= 2) ep->pair_mma = coords_ok;
-    else if (cfg.pair_kernel == 0)
-      ep->pair_mma = coords_ok && xb <= db->total_mem / 16 &&
-                     pair_mma_cost_us(n1, in.stride, db->num_sms, ep->pair_e2m1) <
-                         pair_cores_cost_us(n1, in.stride, db->num_sms);
-    if (ep->pair_mma) FIM_TRY(ws_get(ws, WS_PAIR_X, xb, &ep->d_X));
+    const double cores_us = pair_cores_cost_us(n1, in.stride, db->num_sms);
+    if (cfg.pair_kernel == FIM_PAIR_TENSOR_FUSED) {
+      if (!consecutive) return fail(FIM_ERR_INVALID, "the fused tensor-core pair kernel needs consecutive rows");
+      ep->pair_mma = ep->pair_fused = true;
+    } else if (cfg.pair_kernel >= FIM_PAIR_TENSOR) {
+      ep->pair_mma = coords_ok;
+    } else if (cfg.pair_kernel == FIM_PAIR_AUTO) {
+      if (consecutive)
+        ep->pair_mma = ep->pair_fused = pair_mma_cost_us(n1, in.stride, db->num_sms, false, true) < cores_us;
+      else
+        ep->pair_mma = coords_ok && xb <= db->total_mem / 16 &&
+                       pair_mma_cost_us(n1, in.stride, db->num_sms, ep->pair_e2m1) < cores_us;
+    }
+    if (ep->pair_mma && !ep->pair_fused) FIM_TRY(ws_get(ws, WS_PAIR_X, xb, &ep->d_X));
     ep->pair_extra_tx = cfg.fault_pair_wait ? 16u : 0u;
   }
   FIM_TRY(ws_get(ws, WS_SCNT, n1, &ep->d_scnt));
@@ -240,10 +252,11 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
   if (ep.ev[0]) cudaEventRecord(ep.ev[0], st);
   if (!ep.skip_pairs) {
     uint32_t ksplit = 0;
-    PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0};
-    ce = ep.pair_mma ? launch_pair_mma(pl, ep.d_X, ep.pair_e2m1, &ep.d_ctrl->err, ep.num_sms, st, &ksplit,
-                                       ep.pair_extra_tx)
-                     : launch_pair_counts(pl, ep.num_sms, st, &ksplit);
+    PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0, ep.rows_base};
+    ce = ep.pair_fused ? launch_pair_mma_fused(pl, &ep.d_ctrl->err, ep.num_sms, st, &ksplit, ep.pair_extra_tx)
+         : ep.pair_mma ? launch_pair_mma(pl, ep.d_X, ep.pair_e2m1, &ep.d_ctrl->err, ep.num_sms, st, &ksplit,
+                                         ep.pair_extra_tx)
+                       : launch_pair_counts(pl, ep.num_sms, st, &ksplit);
     if (ce != cudaSuccess) return ce;
   }
   if (ep.ev[1]) cudaEventRecord(ep.ev[1], st);
@@ -439,7 +452,10 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
     stats->grid_ctas = n1 >= 3 ? ep->grid : 0;
     stats->threads_per_cta = ep->threads;
     stats->vec_per_lane = ep->vec;
-    stats->pair_kernel = !ep->pair_mma ? FIM_PAIR_CORES : ep->pair_e2m1 ? FIM_PAIR_TENSOR : FIM_PAIR_TENSOR_E4M3;
+    stats->pair_kernel = !ep->pair_mma   ? FIM_PAIR_CORES
+                         : ep->pair_fused ? FIM_PAIR_TENSOR_FUSED
+                         : ep->pair_e2m1  ? FIM_PAIR_TENSOR
+                                          : FIM_PAIR_TENSOR_E4M3;
     stats->n_proj_classes = ep->proj ? h.n_proj_classes : 0u;
     stats->n_proj_splits = ep->proj ? h.proj_splits : 0u;
     stats->n_fallback_entries = ep->proj ? h.n_entries_f : 0u;

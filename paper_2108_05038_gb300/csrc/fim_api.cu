@@ -454,6 +454,7 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
   engine_config_from_opts(opts, cfg);
   if (cfg->output > FIM_OUTPUT_MAXIMAL) return fail(FIM_ERR_INVALID, "unknown output kind");
   if (cfg->diffsets > 2) return fail(FIM_ERR_INVALID, "diffsets must be 0, 1 or 2");
+  if (cfg->pair_kernel > FIM_PAIR_TENSOR_FUSED) return fail(FIM_ERR_INVALID, "unknown pair kernel");
   if (cfg->output == FIM_OUTPUT_MAXIMAL) {
     // the leaves are written by the projected DFS (and its sparse fallback)
     if (db->stride / 4 > 65535) return fail(FIM_ERR_INVALID, "maximal output needs rows of at most 65,535 16-byte words");

@@ -271,7 +271,7 @@ struct EngineConfig {
   uint32_t ctas_per_sm = 0;
   uint32_t donate = 0;
   uint32_t mode = 2;  // DFS traversal: 0 node, 1 frame, 2 automatic (frames for rows of at most 2,048 words)
-  uint32_t pair_kernel = 0;  // level 2: 0 automatic, 1 integer pipes, 2 tensor cores (e2m1), 3 (e4m3)
+  uint32_t pair_kernel = 0;  // level 2: 0 automatic, 1 integer pipes, 2 tensor cores (e2m1), 3 (e4m3), 4 (fused)
   uint32_t fault_pair_wait = 0;  // test: the tensor pair kernel's stage waits never complete
   uint64_t spin_limit = 0;
   uint64_t cap_sets = 0, cap_items = 0;  // 0 = automatic
@@ -317,6 +317,8 @@ struct EnginePlan {
   bool skip_pairs = false;  // a repeated launch reuses the pair counts of the previous one
   bool pair_mma = false;    // level 2 on the tensor cores (rows widened into d_X)
   bool pair_e2m1 = true;    // tensor-core operands packed as e2m1 (else e4m3)
+  bool pair_fused = false;  // widening fused into the tensor-core product (consecutive rows, no widened copy)
+  const uint32_t* rows_base = nullptr;  // the frequent rows when consecutive
   uint32_t pair_extra_tx = 0;  // test: bytes a stage waits for beyond its copies (0 normally)
   uint8_t* d_X = nullptr;   // widened rows (pair_mma only)
   // projected DFS (mode 5): budgets, geometry and buffers; the fallback runs the sparse node mode with
@@ -392,6 +394,7 @@ struct PairLaunch {
   uint32_t n1;
   uint32_t* C2;  // n1 * n1
   uint32_t ksplit;
+  const uint32_t* rows_base = nullptr;  // the frequent rows when they are consecutive rows of `bits` (else NULL)
 };
 cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st, uint32_t* ksplit_used);
 // the same counts on the tensor cores: rows widened into X (pair_mma_buffer_bytes), then C2 = X X^T;
@@ -400,8 +403,12 @@ cudaError_t launch_pair_counts(const PairLaunch& p, int num_sms, cudaStream_t st
 cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t* err, int num_sms, cudaStream_t st,
                             uint32_t* ksplit_used, uint32_t extra_tx = 0);
 uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride, bool e2m1);
+// the same with the widening fused into the product (e4m3 operands written to shared memory from the raw
+// bits, no widened copy); needs p.rows_base
+cudaError_t launch_pair_mma_fused(const PairLaunch& p, uint32_t* err, int num_sms, cudaStream_t st,
+                                  uint32_t* ksplit_used, uint32_t extra_tx = 0);
 // modelled device time (µs) of each pair kernel, for the automatic choice
-double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1);
+double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1, bool fused = false);
 double pair_cores_cost_us(uint32_t n1, uint32_t stride, int num_sms);
 
 struct LevelLaunch {

@@ -392,6 +392,301 @@ __global__ void __launch_bounds__(kThreads, 1)
                               : "memory");
 }
 
+// ---- the widening fused into the product ----------------------------------------------------------------
+// The TMA brings the raw bits (4 words = one 128-transaction slice of 384 rows: 6 KB) into a ring of small
+// stages; twelve expander warps in two groups, which take alternate slices, turn each raw stage into the
+// e4m3 operand stage (48 KB, in the 128-byte swizzle layout the MMA descriptors read), make those
+// generic-proxy writes visible to the tensor cores (fence.proxy.async) and arrive on the stage's barrier.
+// No widened copy of the rows exists, so the DRAM traffic is that of the raw bits.
+// A set bit becomes 2.0 (0x40, one bit of its byte); every product is then 4, a partial sum is 4 x an
+// integer of at most 2^24 (exact in fp32: multiples of 4 up to 2^26), and the read-back divides by 4.
+// The order of the transactions inside a slice is free as long as every row uses the same one: byte k of
+// output word t of raw word w is bit 8k + t of w, i.e. output word t = (w << (6 - t)) & 0x40404040, one
+// multiply and one mask.  The multipliers are kernel arguments, so the shifts run as integer multiplies on
+// the FMA pipe and the ALU pipe, which bounds the expansion, only takes the masks.
+constexpr uint32_t kFStages = 3;                   // operand stages (48 KB each)
+constexpr uint32_t kRStages = 8;                   // raw stages (6 KB each): several TMA latencies in flight
+constexpr uint32_t kRawRows = kBM + kBN;           // 384 rows per slice (A rows, then B rows)
+constexpr uint32_t kRawStageBytes = kRawRows * 16;  // 4 words per row
+constexpr uint32_t kExpGroups = 2;                 // groups of expander warps, alternate slices
+constexpr uint32_t kGroupWarps = 6;
+constexpr uint32_t kGroupThreads = kGroupWarps * 32;
+constexpr uint32_t kRowsPerExp = kRawRows / kGroupThreads;  // rows of a slice per expander thread
+constexpr uint32_t kExpThreads = kExpGroups * kGroupThreads;
+constexpr uint32_t kFThreads = kThreads + kExpThreads;  // warps 0-5 as above, 6-17 expand
+constexpr uint32_t kTwoE4M3 = 0x40u;                // 2.0: exponent 8 (bias 7), mantissa 0
+// rfull[], rempty[], ofull[], oempty[], acc_full[], acc_empty[], fin, TMEM address
+constexpr uint32_t kFBarBytes = 8 * (2 * kRStages + 2 * kFStages + 2 * kAccBufs + 1) + 8;
+constexpr size_t kFSmemBytes =
+    1024 + (size_t)kFStages * kStageBytes + (size_t)kRStages * kRawStageBytes + kStagingBytes + kFBarBytes;
+static_assert(kFSmemBytes <= 227u * 1024u, "shared memory per CTA");
+static_assert(kFThreads <= 1024 && kRawRows % kGroupThreads == 0, "whole rows per expander thread");
+static_assert(kRStages % kExpGroups == 0, "a raw stage's slices all belong to one group");
+static_assert(kABytes == kBM * 128 && kBK == 128, "operand rows of 128 bytes, A rows then B rows");
+
+// the 32 transactions of raw word w as output words t = 0..7 (two 16-byte chunks): (w << (6 - t)) & keep,
+// with mul[t] = 2^(6 - t) given at run time and t = 7 as the high half of w x 2^31 (w >> 1)
+__device__ __forceinline__ void spread32_two(uint32_t w, const uint32_t (&mul)[6], uint32_t hi31, uint4& lo,
+                                             uint4& hi) {
+  constexpr uint32_t kKeep = kTwoE4M3 * 0x01010101u;
+  lo = make_uint4((w * mul[0]) & kKeep, (w * mul[1]) & kKeep, (w * mul[2]) & kKeep, (w * mul[3]) & kKeep);
+  hi = make_uint4((w * mul[4]) & kKeep, (w * mul[5]) & kKeep, w & kKeep, __umulhi(w, hi31) & kKeep);
+}
+
+// orders this thread's generic-proxy writes to shared memory before later async-proxy reads (the MMA)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    k_pair_mma_fused(const __grid_constant__ CUtensorMap rmap, uint32_t n1, uint32_t nbj, uint32_t n_tiles,
+                     uint32_t nsteps, uint32_t steps_per_item, uint32_t ksplit, uint32_t* __restrict__ C2,
+                     uint32_t* __restrict__ err, uint32_t extra_tx, uint32_t unit) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint32_t s_abort;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // the 128-byte swizzle repeats every 1024 bytes
+  const uint32_t op_st = base;                   // operand stage: 128 A rows then 256 B rows of 128 bytes
+  const uint32_t raw_st = base + kFStages * kStageBytes;
+  uint32_t* const staging =
+      reinterpret_cast<uint32_t*>(smem_raw + (raw_st + kRStages * kRawStageBytes - raw));
+  const uint32_t bars = raw_st + kRStages * kRawStageBytes + kStagingBytes;
+  auto rfull = [&](uint32_t s) { return bars + 8 * s; };
+  auto rempty = [&](uint32_t s) { return bars + 8 * (kRStages + s); };
+  auto ofull = [&](uint32_t s) { return bars + 8 * (2 * kRStages + s); };
+  auto oempty = [&](uint32_t s) { return bars + 8 * (2 * kRStages + kFStages + s); };
+  auto acc_full = [&](uint32_t b) { return bars + 8 * (2 * kRStages + 2 * kFStages + b); };
+  auto acc_empty = [&](uint32_t b) { return bars + 8 * (2 * kRStages + 2 * kFStages + kAccBufs + b); };
+  const uint32_t fin = bars + 8 * (2 * kRStages + 2 * kFStages + 2 * kAccBufs);
+  const uint32_t tslot = fin + 8;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile uint32_t* abort_flag = &s_abort;
+  auto abort_now = [&]() {
+    atomicOr(err, DEV_ERR_TIMEOUT);
+    *abort_flag = 1u;
+  };
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < kRStages; ++s) {
+      mbar_init(rfull(s), 1);           // the producer's arrive + the TMA bytes
+      mbar_init(rempty(s), kGroupWarps);  // one arrive per warp of the group that expands the slice
+    }
+    for (uint32_t s = 0; s < kFStages; ++s) {
+      mbar_init(ofull(s), kGroupWarps);  // one arrive per warp of the group, after its proxy fence
+      mbar_init(oempty(s), 1);         // the MMA commit that consumed the stage
+    }
+    for (uint32_t b = 0; b < kAccBufs; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 4);
+    }
+    mbar_init(fin, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + (tslot - raw));
+
+  // item -> (row block bi, column block bj, first K slice, slices); items of one K range are consecutive, so
+  // the CTAs of a round read the same K slices of the rows (L2 reuse)
+  const uint32_t n_items = n_tiles * ksplit;
+  auto decode = [&](uint32_t item, uint32_t& bi, uint32_t& bj, uint32_t& k0, uint32_t& ns) {
+    const uint32_t split = item / n_tiles;
+    uint32_t t = item % n_tiles;
+    bi = 0;
+    while (t >= nbj - bi / 2) {  // row block bi pairs with the column blocks bj >= bi / 2
+      t -= nbj - bi / 2;
+      ++bi;
+    }
+    bj = bi / 2 + t;
+    k0 = split * steps_per_item;
+    ns = min(nsteps, k0 + steps_per_item) - k0;
+  };
+
+  uint32_t issued = 0;
+  bool mma_open = false;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (uint32_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        uint32_t bi, bj, k0, ns;
+        decode(item, bi, bj, k0, ns);
+        bool ok = true;
+        for (uint32_t s = 0; s < ns; ++s, ++issued) {
+          const uint32_t st = issued % kRStages;
+          if (issued >= kRStages && !mbar_wait(rempty(st), ((issued / kRStages) - 1) & 1)) {
+            abort_now();
+            ok = false;
+            break;
+          }
+          // (extra_tx, a failure-detection test only: bytes that never arrive, so the wait runs out)
+          mbar_expect_tx(rfull(st), kRawStageBytes + extra_tx);
+          const int32_t x = (int32_t)((k0 + s) * 4);  // words: x * 4 bytes is a multiple of 16
+          const uint32_t d = raw_st + st * kRawStageBytes;
+          tma_load(d, &rmap, x, (int32_t)(bi * kBM), rfull(st));
+          tma_load(d + kBM * 16, &rmap, x, (int32_t)(bj * kBN), rfull(st));
+          tma_load(d + 2 * kBM * 16, &rmap, x, (int32_t)(bj * kBN + kBM), rfull(st));
+        }
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t consumed = 0, it = 0;
+      for (uint32_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++it) {
+        uint32_t bi, bj, k0, ns;
+        decode(item, bi, bj, k0, ns);
+        const uint32_t b = it & 1;
+        if (it >= kAccBufs && !mbar_wait(acc_empty(b), ((it >> 1) - 1) & 1)) {
+          abort_now();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + b * kBN;
+        bool ok = true;
+        for (uint32_t s = 0; s < ns; ++s, ++consumed) {
+          const uint32_t st = consumed % kFStages;
+          if (!mbar_wait(ofull(st), (consumed / kFStages) & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = sw128_desc(op_st + st * kStageBytes), bd = sw128_desc(op_st + st * kStageBytes + kABytes);
+#pragma unroll
+          for (uint32_t kk = 0; kk < kBK / kMmaK; ++kk)
+            mma_f8f6f4(d, ad + 2 * kk, bd + 2 * kk, idesc<false>(), (s | kk) != 0u);
+          mma_commit(oempty(st));
+          mma_open = true;
+        }
+        if (!ok) {
+          abort_now();
+          mma_commit(acc_full(b));
+          mma_open = true;
+          break;
+        }
+        mma_commit(acc_full(b));
+        mma_open = false;
+      }
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    // read-back, as in the widened kernel (sums of products of 4)
+    const uint32_t quarter = warp & 3;
+    uint32_t* sw = staging + (warp - 2) * 32 * kSPitch;
+    uint32_t it = 0;
+    for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x, ++it) {
+      uint32_t bi, bj, k0, ns;
+      decode(item, bi, bj, k0, ns);
+      const uint32_t b = it & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), (it >> 1) & 1));
+      if (!ok || *abort_flag) {
+        if (lane == 0 && !ok) abort_now();
+        break;
+      }
+      tc_fence_after();
+      const uint32_t row0 = bi * kBM + quarter * 32;
+      const uint32_t taddr = tmem + ((quarter * 32u) << 16) + b * kBN;
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < kBN; c0 += kChunk) {
+        uint32_t r[16];
+        tmem_ld16(taddr + c0, r);
+#pragma unroll
+        for (uint32_t c = 0; c < 16; ++c)
+          sw[lane * kSPitch + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);  // exact: a power of 2
+        tmem_ld16(taddr + c0 + 16, r);
+#pragma unroll
+        for (uint32_t c = 0; c < 16; ++c) sw[lane * kSPitch + 16 + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);
+        __syncwarp();
+        const uint32_t j = bj * kBN + c0 + lane;
+#pragma unroll 4
+        for (uint32_t rr = 0; rr < 32; ++rr) {
+          const uint32_t i = row0 + rr;
+          if (i < j && j < n1) {
+            const uint32_t v = sw[rr * kSPitch + lane];
+            if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
+            else C2[(size_t)i * n1 + j] = v;
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(b));
+    }
+  } else {
+    // expanders: raw stage -> operand stage.  Group g takes the slices c with c mod 2 = g; its thread e owns
+    // rows e and e + 192 of the slice (A rows 0-127, B rows 128-383: consecutive 128-byte rows of the operand
+    // stage): one 16-byte load of the row's 4 raw words, then 8 chunks of 16 bytes, chunk c stored at
+    // c ^ (row mod 8) (the 128-byte swizzle; the 8 lanes of a store phase are 8 consecutive rows, so they
+    // hit 8 distinct chunk positions: no bank conflict)
+    const uint32_t grp = (threadIdx.x - kThreads) / kGroupThreads, e = (threadIdx.x - kThreads) % kGroupThreads;
+    uint32_t mul[6];
+#pragma unroll
+    for (uint32_t t = 0; t < 6; ++t) mul[t] = unit << (6 - t);
+    const uint32_t hi31 = unit << 31;
+    uint32_t c = 0;  // slices of this CTA so far (both groups)
+    bool ok = true;
+    for (uint32_t item = blockIdx.x; item < n_items && ok && !*abort_flag; item += gridDim.x) {
+      uint32_t bi, bj, k0, ns;
+      decode(item, bi, bj, k0, ns);
+      for (uint32_t s = 0; s < ns; ++s, ++c) {
+        if (c % kExpGroups != grp) continue;
+        const uint32_t rs = c % kRStages, os = c % kFStages;
+        ok = __all_sync(0xffffffffu, mbar_wait(rfull(rs), (c / kRStages) & 1));
+        if (ok && c >= kFStages) ok = __all_sync(0xffffffffu, mbar_wait(oempty(os), ((c / kFStages) - 1) & 1));
+        if (!ok) {
+          if (lane == 0) abort_now();
+          break;
+        }
+        const uint8_t* rsrc = smem_raw + (raw_st + rs * kRawStageBytes - raw);
+        uint8_t* odst = smem_raw + (op_st + os * kStageBytes - raw);
+#pragma unroll
+        for (uint32_t h = 0; h < kRowsPerExp; ++h) {
+          const uint32_t row = e + h * kGroupThreads, sw7 = row & 7u;
+          const uint4 w = *reinterpret_cast<const uint4*>(rsrc + row * 16u);
+          uint8_t* drow = odst + row * 128u;
+          const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (uint32_t q = 0; q < 4; ++q) {
+            uint4 lo, hi;
+            spread32_two(wv[q], mul, hi31, lo, hi);
+            *reinterpret_cast<uint4*>(drow + (((2u * q) ^ sw7) << 4)) = lo;
+            *reinterpret_cast<uint4*>(drow + (((2u * q + 1u) ^ sw7) << 4)) = hi;
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(ofull(os));
+          mbar_arrive(rempty(rs));
+        }
+      }
+    }
+  }
+
+  // teardown after an abort: the producer waits (bounded, and no longer once one wait ran out) for its last
+  // raw stages in flight, the MMA thread for its MMAs that nobody waits for
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (uint32_t q = issued > kRStages ? issued - kRStages : 0; q < issued; ++q)
+      if (!mbar_wait(rfull(q % kRStages), (q / kRStages) & 1)) break;
+  }
+  if (warp == 1 && lane == 0 && (mma_open || *abort_flag)) {
+    mma_commit(fin);
+    (void)mbar_wait(fin, 0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                              : "memory");
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -424,9 +719,9 @@ uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride, bool e2m1) {
   return (uint64_t)n1 * stride * (e2m1 ? 16ull : 32ull);
 }
 
-double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1) {
+double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1, bool fused) {
   // widening (bytes written at ~5 TB/s) + tile rounds at ~1.5 PFLOP/s of kind::f8f6f4 per 152 SMs
-  const double x_bytes = (double)pair_mma_buffer_bytes(n1, stride, e2m1);
+  const double x_bytes = fused ? 0.0 : (double)pair_mma_buffer_bytes(n1, stride, e2m1);
   const uint32_t tiles = pair_tiles(n1);
   const uint32_t nsteps = stride / 4;
   const double step_us = 2.0 * kBM * kBN * kBK / (1.5e15 / 152.0) * 1e6;  // one 128-element K slice of a tile
@@ -439,6 +734,65 @@ double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1) {
     best = std::min(best, (double)rounds * (spi + 1) * step_us + 8.0 * step_us);
   }
   return x_bytes / 5e12 * 1e6 + best + 4.0;
+}
+
+// the split of the K range: items fill whole rounds of the SMs, at most 2^24 elements per item, at least 8
+// slices per item to cover a read-back; an item's read-back overlaps the next item's MMAs, so only the last
+// one is exposed and a CTA takes about rounds x (slices + 1) + 8 slice times
+static uint32_t pair_split(uint32_t tiles, uint32_t nsteps, int num_sms) {
+  uint32_t spi = std::min(kMaxStepsPerItem, nsteps);
+  double best = 1e300;
+  for (uint32_t ks = 1; ks <= 256; ++ks) {
+    const uint32_t c = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
+    if (c < 8 && ks > 1) break;
+    const uint32_t k2 = (nsteps + c - 1) / c;
+    const uint64_t items = (uint64_t)tiles * k2;
+    const uint64_t rounds = (items + num_sms - 1) / num_sms;
+    const double cost = (double)rounds * (c + 1.0) + 8.0;
+    if (cost < best - 1e-9) {
+      best = cost;
+      spi = c;
+    }
+  }
+  return spi;
+}
+
+cudaError_t launch_pair_mma_fused(const PairLaunch& p, uint32_t* err, int num_sms, cudaStream_t st,
+                                  uint32_t* ksplit_used, uint32_t extra_tx) {
+  if (p.n1 < 2) {
+    *ksplit_used = 0;
+    return cudaSuccess;
+  }
+  if (!p.rows_base) return cudaErrorInvalidValue;
+  cudaError_t e = kernel_smem_limit(reinterpret_cast<const void*>(k_pair_mma_fused), (int)kFSmemBytes);
+  if (e != cudaSuccess) return e;
+  EncodeTiled encode = nullptr;
+  if ((e = encoder(&encode)) != cudaSuccess) return e;
+  // the frequent rows' raw bits as a 2-D tensor: stride words x n1 rows; boxes of 4 words (one slice of 128
+  // transactions) x 128 rows, no swizzle; rows past n1 read as zeros
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[2] = {p.stride, p.n1};
+  const cuuint64_t strides[1] = {(cuuint64_t)p.stride * 4};
+  const cuuint32_t box[2] = {4, kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(p.rows_base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const uint32_t nbj = (p.n1 + kBN - 1) / kBN;
+  const uint32_t tiles = pair_tiles(p.n1);
+  const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-transaction slices
+  const uint32_t spi = pair_split(tiles, nsteps, num_sms);
+  const uint32_t ksplit = (nsteps + spi - 1) / spi;
+  *ksplit_used = ksplit;
+  if (ksplit > 1 && (e = cudaMemsetAsync(p.C2, 0, (size_t)p.n1 * p.n1 * sizeof(uint32_t), st)) != cudaSuccess)
+    return e;
+  const uint64_t items = (uint64_t)tiles * ksplit;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(items, (uint64_t)num_sms);
+  k_pair_mma_fused<<<grid, kFThreads, kFSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err,
+                                                         extra_tx, 1u);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t* err, int num_sms, cudaStream_t st,
@@ -485,23 +839,7 @@ cudaError_t launch_pair_mma(const PairLaunch& p, uint8_t* X, bool e2m1, uint32_t
   const uint32_t nbj = (p.n1 + kBN - 1) / kBN;
   const uint32_t tiles = pair_tiles(p.n1);
   const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-element slices
-  // split the K range so that the items fill whole rounds of the SMs; at most 2^24 elements per item.
-  // An item's read-back overlaps the next item's MMAs, so only the last one is exposed: a CTA takes
-  // about rounds x (slices + 1) + 8 slice times
-  uint32_t spi = std::min(kMaxStepsPerItem, nsteps);
-  double best = 1e300;
-  for (uint32_t ks = 1; ks <= 256; ++ks) {
-    const uint32_t c = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
-    if (c < 8 && ks > 1) break;  // at least 8 slices per item to cover a read-back
-    const uint32_t k2 = (nsteps + c - 1) / c;
-    const uint64_t items = (uint64_t)tiles * k2;
-    const uint64_t rounds = (items + num_sms - 1) / num_sms;
-    const double cost = (double)rounds * (c + 1.0) + 8.0;
-    if (cost < best - 1e-9) {
-      best = cost;
-      spi = c;
-    }
-  }
+  const uint32_t spi = pair_split(tiles, nsteps, num_sms);
   const uint32_t ksplit = (nsteps + spi - 1) / spi;
   *ksplit_used = ksplit;
   if (ksplit > 1 && (e = cudaMemsetAsync(p.C2, 0, (size_t)p.n1 * p.n1 * sizeof(uint32_t), st)) != cudaSuccess)

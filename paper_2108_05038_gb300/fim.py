@@ -19,7 +19,7 @@ FIM_OK, FIM_ERR_INVALID, FIM_ERR_OOM, FIM_ERR_OUTPUT_OVERFLOW, FIM_ERR_CUDA, FIM
 FIM_ORDER_ESTIMATE, FIM_ORDER_UNIFORM = 0, 1
 FIM_DFS_NODES, FIM_DFS_FRAMES, FIM_DFS_AUTO, FIM_DFS_SPARSE, FIM_DFS_WARP, FIM_DFS_PROJECTED = 0, 1, 2, 3, 4, 5
 FIM_OUTPUT_ALL, FIM_OUTPUT_CLOSED, FIM_OUTPUT_MAXIMAL = 0, 1, 2
-FIM_PAIR_AUTO, FIM_PAIR_CORES, FIM_PAIR_TENSOR, FIM_PAIR_TENSOR_E4M3 = 0, 1, 2, 3
+FIM_PAIR_AUTO, FIM_PAIR_CORES, FIM_PAIR_TENSOR, FIM_PAIR_TENSOR_E4M3, FIM_PAIR_TENSOR_FUSED = 0, 1, 2, 3, 4
 SAMPLE_ITEMSET_LIMIT = 1 << 20  # FIM_SAMPLE_ITEMSET_LIMIT
 
 # every symbol declared in include/fim.h

@@ -1,5 +1,6 @@
 """Level-2 pair counts on the tensor cores (FIM_PAIR_TENSOR: packed e2m1 operands; FIM_PAIR_TENSOR_E4M3:
-byte operands) against the oracle: named workloads at
+byte operands; FIM_PAIR_TENSOR_FUSED: the raw bits widened to e4m3 in shared memory inside the kernel)
+against the oracle: named workloads at
 full size, ragged numbers of frequent rows around the 128 x 256 tile edges, supports past 2^24 (fp32
 exactness needs the K range split), graph replays, and the integer-pipe kernel on the same inputs."""
 import numpy as np
@@ -28,7 +29,7 @@ def csr(txs):
     return off, items
 
 
-TENSOR = [fim.FIM_PAIR_TENSOR, fim.FIM_PAIR_TENSOR_E4M3]
+TENSOR = [fim.FIM_PAIR_TENSOR, fim.FIM_PAIR_TENSOR_E4M3, fim.FIM_PAIR_TENSOR_FUSED]
 
 
 @pytest.mark.parametrize("pk", TENSOR)
@@ -85,13 +86,14 @@ def test_supports_past_fp32_integer_range(pk):
         del d_off, d_items
 
 
-def test_graph_replay_on_tensor_cores():
+@pytest.mark.parametrize("pk", [fim.FIM_PAIR_TENSOR, fim.FIM_PAIR_TENSOR_FUSED])
+def test_graph_replay_on_tensor_cores(pk):
     w = synth.make_workload("sparse_mid", D=30000)
     ms = 80
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
     try:
-        plan = db.plan(ms, pair_kernel=fim.FIM_PAIR_TENSOR)
+        plan = db.plan(ms, pair_kernel=pk)
         for _ in range(3):
             plan.launch()
             assert plan.result().as_dict() == want
@@ -101,21 +103,22 @@ def test_graph_replay_on_tensor_cores():
 
 
 def test_estimate_and_mine_with_automatic_choice():
-    """The automatic choice (tensor cores on sparse_mid's 988 rows of 12.5 KB) keeps the output exact
-    through the sample estimate and the mine."""
+    """The automatic choice (tensor cores on sparse_mid's 988 rows of 12.5 KB; fused, since a mine's
+    frequent rows are consecutive) keeps the output exact through the sample estimate and the mine."""
     w = synth.make_workload("sparse_mid")
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], w["minsup"]))
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
     try:
         db.estimate_class_costs(0.01, w["rel_minsup"], 1)
         res = db.mine(w["minsup"])
-        assert res.stats["pair_kernel"] in (fim.FIM_PAIR_CORES, fim.FIM_PAIR_TENSOR)
+        assert res.stats["pair_kernel"] in (fim.FIM_PAIR_CORES, fim.FIM_PAIR_TENSOR_FUSED)
         assert res.as_dict() == want
     finally:
         db.free()
 
 
-def test_pair_kernel_wait_runs_out_and_context_survives():
+@pytest.mark.parametrize("pk", [fim.FIM_PAIR_TENSOR, fim.FIM_PAIR_TENSOR_FUSED])
+def test_pair_kernel_wait_runs_out_and_context_survives(pk):
     """Failure detection on the GPU: with fault_pair_wait every stage of the tensor pair kernel waits for
     16 bytes that never arrive, so its bounded mbarrier waits (about 1 s each) run out; the kernel
     flags the timeout, lets its copies and MMAs finish, frees its TMEM and returns, nothing below
@@ -127,9 +130,27 @@ def test_pair_kernel_wait_runs_out_and_context_survives():
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
     try:
         with pytest.raises(fim.FimError) as e:
-            db.mine(ms, pair_kernel=fim.FIM_PAIR_TENSOR, fault_pair_wait=True)
+            db.mine(ms, pair_kernel=pk, fault_pair_wait=True)
         assert e.value.status == fim.FIM_ERR_TIMEOUT
-        assert db.mine(ms, pair_kernel=fim.FIM_PAIR_TENSOR).as_dict() == want
+        assert db.mine(ms, pair_kernel=pk).as_dict() == want
         torch.cuda.synchronize()  # the context is intact
+    finally:
+        db.free()
+
+
+def test_fused_kernel_needs_no_widened_rows():
+    """The fused kernel takes no scratch for widened rows: the database's device bytes (its bitmaps and
+    workspace) grow by nothing on a fused mine after an integer-pipe mine of the same minsup, while the
+    widened kernel's scratch (rows x padded words x 16 bytes) adds to them."""
+    w = synth.make_workload("sparse_mid")
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    try:
+        db.mine(w["minsup"], pair_kernel=fim.FIM_PAIR_CORES)
+        base = db.info()["device_bytes"]
+        res = db.mine(w["minsup"], pair_kernel=fim.FIM_PAIR_TENSOR_FUSED)
+        assert res.stats["pair_kernel"] == fim.FIM_PAIR_TENSOR_FUSED
+        assert db.info()["device_bytes"] == base
+        db.mine(w["minsup"], pair_kernel=fim.FIM_PAIR_TENSOR)
+        assert db.info()["device_bytes"] > base
     finally:
         db.free()
