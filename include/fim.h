@@ -121,9 +121,9 @@ typedef struct {
                                   words when it has at most 2,048 of them (small CTAs, several per
                                   SM), dense in its stack slot otherwise; rows of at most 65,535
                                   16-byte words, no donation (else as NODES); FIM_DFS_AUTO (2, the
-                                  default): projected for rows of more than 2,048 words (8 KB) and
-                                  for rows of at most 512 words with at least 1,024 frequent rows,
-                                  else frames; FIM_DFS_WARP (4): one warp
+                                  default): projected with at least 1,024 frequent rows, else
+                                  frames for rows of at most 16,384 words (64 KB), else SPARSE;
+                                  FIM_DFS_WARP (4): one warp
                                   per two-item class, the
                                   prefix in its registers, no CTA-wide barrier; rows of at most 512
                                   words, no donation (else as SPARSE); FIM_DFS_PROJECTED (5): the

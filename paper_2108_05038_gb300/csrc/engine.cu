@@ -36,20 +36,17 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // (warp DFS: the prefix in the registers of one warp, rows of at most 512 words)
   const bool list_ok = in.stride / 4 <= 65535;
   const bool warp_ok = in.stride <= 512 && !cfg.donate;
-  // automatic: short rows with many frequent rows (many classes, throughput bound) take the warp DFS
-  // (large_sparse's 1% sample: 2.38 ms against 3.64 ms in frame passes); short rows with few rows,
-  // where the largest class's chain of dependent nodes sets the time, take frame passes, which
-  // spread one frame over a whole CTA (sparse_mid's sample: 45 µs against 61 µs)
-  // The projected DFS (FIM_DFS_PROJECTED, automatic on wide rows and on short rows with many classes)
-  // runs with the sparse node mode, whose geometry ep->mode = 3 describes, mining the classes left out
-  // of the projection.  Automatic: wide rows and short rows with at least 1,024 frequent rows (many
-  // classes, throughput bound: large_sparse's 1% sample, DFS 2.4 ms in the warp DFS, 2.1 ms projected;
-  // its 20,000-row variant 11.1 against 3.8 ms) take it; other short rows take frame passes, which spread
-  // one frame over a whole CTA where the largest class's chain of dependent nodes sets the time
-  // (sparse_mid: 0.022 ms against 0.080 ms projected).
-  const bool auto_proj = cfg.mode == 2 && list_ok && !cfg.donate && (in.stride > 2048 || (warp_ok && n1 >= 1024));
+  // Automatic: the number of classes decides, not the row width.  At least 1,024 frequent rows (many
+  // classes, throughput bound) take the projected DFS (FIM_DFS_PROJECTED), which runs with the sparse node
+  // mode (ep->mode = 3) mining the classes left out of the projection: large_sparse 5.1 ms; its laws at
+  // 50,000 transactions (rows of 1,568 words) 2.0 ms against 8.6 ms in frame passes and 7.4 in sparse
+  // nodes.  Fewer rows, where the largest class's chain of dependent nodes sets the time, take frame
+  // passes, which spread one frame over a whole CTA: sparse_mid (988 rows of 3,136 words) 0.021 ms against
+  // 0.064 projected, 0.027 in sparse nodes and 0.033 in dense node expansion; at 300,000 transactions
+  // (9,376 words) 0.033 against 0.084 projected; rows past 16,384 words take the sparse node mode.
+  const bool auto_proj = cfg.mode == 2 && list_ok && !cfg.donate && n1 >= 1024;
   if (cfg.mode == 2)
-    ep->mode = auto_proj ? 3u : (in.stride <= 2048 ? 1u : 0u);
+    ep->mode = auto_proj ? 3u : (in.stride <= 16384 ? 1u : (list_ok && !cfg.donate ? 3u : 0u));
   else if (cfg.mode == 3 || cfg.mode == 5) ep->mode = list_ok && !cfg.donate ? 3u : 0u;
   else if (cfg.mode == 4) ep->mode = warp_ok ? 4u : (list_ok && !cfg.donate ? 3u : 0u);
   else ep->mode = cfg.mode == 1 ? 1u : 0u;

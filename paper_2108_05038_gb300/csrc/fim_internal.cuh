@@ -270,7 +270,7 @@ struct EngineConfig {
   uint32_t vec = 0;          // 0 = automatic
   uint32_t ctas_per_sm = 0;
   uint32_t donate = 0;
-  uint32_t mode = 2;  // DFS traversal: 0 node, 1 frame, 2 automatic (frames for rows of at most 2,048 words)
+  uint32_t mode = 2;  // DFS traversal: 0 node, 1 frame, 2 automatic, 3 sparse node, 4 warp, 5 projected
   uint32_t pair_kernel = 0;  // level 2: 0 automatic, 1 integer pipes, 2 tensor cores (e2m1), 3 (e4m3), 4 (fused)
   uint32_t fault_pair_wait = 0;  // test: the tensor pair kernel's stage waits never complete
   uint64_t spin_limit = 0;

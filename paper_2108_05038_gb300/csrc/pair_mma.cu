@@ -393,36 +393,46 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---- the widening fused into the product ----------------------------------------------------------------
-// The TMA brings the raw bits (4 words = one 128-transaction slice of 384 rows: 6 KB) into a ring of small
-// stages; twelve expander warps in two groups, which take alternate slices, turn each raw stage into the
-// e4m3 operand stage (48 KB, in the 128-byte swizzle layout the MMA descriptors read), make those
-// generic-proxy writes visible to the tensor cores (fence.proxy.async) and arrive on the stage's barrier.
-// No widened copy of the rows exists, so the DRAM traffic is that of the raw bits.
+// Tiles of 256 x 256 rows: two M 128 MMAs per K step share the B operand, and the two accumulators fill all
+// of TMEM (512 columns), so a tile's read-back runs between its item and the next one while the expanders
+// already fill the next item's stages.  Per 128-transaction slice the TMA brings the raw bits (16 bytes per
+// row, 512 rows: 8 KB) into a ring of three stages; 24 expander warps in three groups, which take the
+// slices in turn, turn a raw stage into the e4m3 operand stage (64 KB: 256 A rows, then 256 B rows, in
+// the 128-byte swizzle layout the MMA descriptors read), make those generic-proxy writes visible to the
+// tensor cores (fence.proxy.async) and arrive on the stage's barrier.  No widened copy of the rows exists,
+// so the DRAM traffic is that of the raw bits, and per flop the expansion is two thirds of that of a
+// 128 x 256 tile (512 rows per two MMA steps instead of 384 per one).
 // A set bit becomes 2.0 (0x40, one bit of its byte); every product is then 4, a partial sum is 4 x an
 // integer of at most 2^24 (exact in fp32: multiples of 4 up to 2^26), and the read-back divides by 4.
 // The order of the transactions inside a slice is free as long as every row uses the same one: byte k of
 // output word t of raw word w is bit 8k + t of w, i.e. output word t = (w << (6 - t)) & 0x40404040, one
 // multiply and one mask.  The multipliers are kernel arguments, so the shifts run as integer multiplies on
 // the FMA pipe and the ALU pipe, which bounds the expansion, only takes the masks.
-constexpr uint32_t kFStages = 3;                   // operand stages (48 KB each)
-constexpr uint32_t kRStages = 8;                   // raw stages (6 KB each): several TMA latencies in flight
-constexpr uint32_t kRawRows = kBM + kBN;           // 384 rows per slice (A rows, then B rows)
-constexpr uint32_t kRawStageBytes = kRawRows * 16;  // 4 words per row
-constexpr uint32_t kExpGroups = 2;                 // groups of expander warps, alternate slices
-constexpr uint32_t kGroupWarps = 6;
+constexpr uint32_t kFM = 256;                        // tile rows on the i side (two MMAs of M 128)
+constexpr uint32_t kFN = kBN;                        // tile rows on the j side (MMA N)
+constexpr uint32_t kFStages = 3;                     // operand stages (64 KB each), one per expander group
+constexpr uint32_t kFStageBytes = (kFM + kFN) * kBK;
+constexpr uint32_t kRStages = 3;                     // raw stages (8 KB each), one per expander group
+constexpr uint32_t kRawRows = kFM + kFN;             // 512 rows per slice (A rows, then B rows)
+constexpr uint32_t kRawStageBytes = kRawRows * 16;   // 4 words per row
+constexpr uint32_t kExpGroups = 3;                   // groups of expander warps, slices in turn
+constexpr uint32_t kGroupWarps = 8;
 constexpr uint32_t kGroupThreads = kGroupWarps * 32;
 constexpr uint32_t kRowsPerExp = kRawRows / kGroupThreads;  // rows of a slice per expander thread
 constexpr uint32_t kExpThreads = kExpGroups * kGroupThreads;
-constexpr uint32_t kFThreads = kThreads + kExpThreads;  // warps 0-5 as above, 6-17 expand
+constexpr uint32_t kFThreads = kThreads + kExpThreads;  // warps 0-5 as in the widened kernel, 6-29 expand
+constexpr uint32_t kFChunk = 16;                     // columns read back per round
+constexpr uint32_t kFPitch = kFChunk + 1;            // staging rows (words): conflict-free transposition
+constexpr uint32_t kFStagingBytes = 4 * 32 * kFPitch * 4;
 constexpr uint32_t kTwoE4M3 = 0x40u;                // 2.0: exponent 8 (bias 7), mantissa 0
-// rfull[], rempty[], ofull[], oempty[], acc_full[], acc_empty[], fin, TMEM address
-constexpr uint32_t kFBarBytes = 8 * (2 * kRStages + 2 * kFStages + 2 * kAccBufs + 1) + 8;
+// rfull[], rempty[], ofull[], oempty[], acc_full, acc_empty, fin, TMEM address
+constexpr uint32_t kFBarBytes = 8 * (2 * kRStages + 2 * kFStages + 3) + 8;
 constexpr size_t kFSmemBytes =
-    1024 + (size_t)kFStages * kStageBytes + (size_t)kRStages * kRawStageBytes + kStagingBytes + kFBarBytes;
+    1024 + (size_t)kFStages * kFStageBytes + (size_t)kRStages * kRawStageBytes + kFStagingBytes + kFBarBytes;
 static_assert(kFSmemBytes <= 227u * 1024u, "shared memory per CTA");
 static_assert(kFThreads <= 1024 && kRawRows % kGroupThreads == 0, "whole rows per expander thread");
-static_assert(kRStages % kExpGroups == 0, "a raw stage's slices all belong to one group");
-static_assert(kABytes == kBM * 128 && kBK == 128, "operand rows of 128 bytes, A rows then B rows");
+static_assert(kRStages == kExpGroups && kFStages == kExpGroups, "group g owns raw stage g and operand stage g");
+static_assert(kBK == 128 && kFM == 2 * kBM && 2 * kBN == kTmemCols, "128-byte operand rows; two accumulators");
 
 // the 32 transactions of raw word w as output words t = 0..7 (two 16-byte chunks): (w << (6 - t)) & keep,
 // with mul[t] = 2^(6 - t) given at run time and t = 7 as the high half of w x 2^31 (w >> 1)
@@ -439,25 +449,25 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 __global__ void __launch_bounds__(kFThreads, 1)
-    k_pair_mma_fused(const __grid_constant__ CUtensorMap rmap, uint32_t n1, uint32_t nbj, uint32_t n_tiles,
+    k_pair_mma_fused(const __grid_constant__ CUtensorMap rmap, uint32_t n1, uint32_t nb, uint32_t n_tiles,
                      uint32_t nsteps, uint32_t steps_per_item, uint32_t ksplit, uint32_t* __restrict__ C2,
                      uint32_t* __restrict__ err, uint32_t extra_tx, uint32_t unit) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_abort;
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // the 128-byte swizzle repeats every 1024 bytes
-  const uint32_t op_st = base;                   // operand stage: 128 A rows then 256 B rows of 128 bytes
-  const uint32_t raw_st = base + kFStages * kStageBytes;
+  const uint32_t op_st = base;                   // operand stage: 256 A rows then 256 B rows of 128 bytes
+  const uint32_t raw_st = base + kFStages * kFStageBytes;
   uint32_t* const staging =
       reinterpret_cast<uint32_t*>(smem_raw + (raw_st + kRStages * kRawStageBytes - raw));
-  const uint32_t bars = raw_st + kRStages * kRawStageBytes + kStagingBytes;
+  const uint32_t bars = raw_st + kRStages * kRawStageBytes + kFStagingBytes;
   auto rfull = [&](uint32_t s) { return bars + 8 * s; };
   auto rempty = [&](uint32_t s) { return bars + 8 * (kRStages + s); };
   auto ofull = [&](uint32_t s) { return bars + 8 * (2 * kRStages + s); };
   auto oempty = [&](uint32_t s) { return bars + 8 * (2 * kRStages + kFStages + s); };
-  auto acc_full = [&](uint32_t b) { return bars + 8 * (2 * kRStages + 2 * kFStages + b); };
-  auto acc_empty = [&](uint32_t b) { return bars + 8 * (2 * kRStages + 2 * kFStages + kAccBufs + b); };
-  const uint32_t fin = bars + 8 * (2 * kRStages + 2 * kFStages + 2 * kAccBufs);
+  const uint32_t acc_full = bars + 8 * (2 * kRStages + 2 * kFStages);
+  const uint32_t acc_empty = acc_full + 8;
+  const uint32_t fin = acc_full + 16;
   const uint32_t tslot = fin + 8;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile uint32_t* abort_flag = &s_abort;
@@ -468,17 +478,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
 
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < kRStages; ++s) {
-      mbar_init(rfull(s), 1);           // the producer's arrive + the TMA bytes
+      mbar_init(rfull(s), 1);             // the producer's arrive + the TMA bytes
       mbar_init(rempty(s), kGroupWarps);  // one arrive per warp of the group that expands the slice
     }
     for (uint32_t s = 0; s < kFStages; ++s) {
       mbar_init(ofull(s), kGroupWarps);  // one arrive per warp of the group, after its proxy fence
-      mbar_init(oempty(s), 1);         // the MMA commit that consumed the stage
+      mbar_init(oempty(s), 1);           // the MMA commit that consumed the stage
     }
-    for (uint32_t b = 0; b < kAccBufs; ++b) {
-      mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), 4);
-    }
+    mbar_init(acc_full, 1);   // the MMA commit after an item's last slice
+    mbar_init(acc_empty, 4);  // one arrive per read-back warp
     mbar_init(fin, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -493,18 +501,18 @@ __global__ void __launch_bounds__(kFThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + (tslot - raw));
 
-  // item -> (row block bi, column block bj, first K slice, slices); items of one K range are consecutive, so
-  // the CTAs of a round read the same K slices of the rows (L2 reuse)
+  // item -> (row block bi, column block bj >= bi, first K slice, slices); items of one K range are
+  // consecutive, so the CTAs of a round read the same K slices of the rows (L2 reuse)
   const uint32_t n_items = n_tiles * ksplit;
   auto decode = [&](uint32_t item, uint32_t& bi, uint32_t& bj, uint32_t& k0, uint32_t& ns) {
     const uint32_t split = item / n_tiles;
     uint32_t t = item % n_tiles;
     bi = 0;
-    while (t >= nbj - bi / 2) {  // row block bi pairs with the column blocks bj >= bi / 2
-      t -= nbj - bi / 2;
+    while (t >= nb - bi) {  // row block bi pairs with the column blocks bj >= bi
+      t -= nb - bi;
       ++bi;
     }
-    bj = bi / 2 + t;
+    bj = bi + t;
     k0 = split * steps_per_item;
     ns = min(nsteps, k0 + steps_per_item) - k0;
   };
@@ -528,9 +536,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
           mbar_expect_tx(rfull(st), kRawStageBytes + extra_tx);
           const int32_t x = (int32_t)((k0 + s) * 4);  // words: x * 4 bytes is a multiple of 16
           const uint32_t d = raw_st + st * kRawStageBytes;
-          tma_load(d, &rmap, x, (int32_t)(bi * kBM), rfull(st));
-          tma_load(d + kBM * 16, &rmap, x, (int32_t)(bj * kBN), rfull(st));
-          tma_load(d + 2 * kBM * 16, &rmap, x, (int32_t)(bj * kBN + kBM), rfull(st));
+          tma_load(d, &rmap, x, (int32_t)(bi * kFM), rfull(st));
+          tma_load(d + kBM * 16, &rmap, x, (int32_t)(bi * kFM + kBM), rfull(st));
+          tma_load(d + 2 * kBM * 16, &rmap, x, (int32_t)(bj * kFN), rfull(st));
+          tma_load(d + 3 * kBM * 16, &rmap, x, (int32_t)(bj * kFN + kBM), rfull(st));
         }
         if (!ok) break;
       }
@@ -542,13 +551,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (uint32_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++it) {
         uint32_t bi, bj, k0, ns;
         decode(item, bi, bj, k0, ns);
-        const uint32_t b = it & 1;
-        if (it >= kAccBufs && !mbar_wait(acc_empty(b), ((it >> 1) - 1) & 1)) {
+        if (it >= 1 && !mbar_wait(acc_empty, (it - 1) & 1)) {  // the previous tile read back
           abort_now();
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + b * kBN;
         bool ok = true;
         for (uint32_t s = 0; s < ns; ++s, ++consumed) {
           const uint32_t st = consumed % kFStages;
@@ -557,74 +564,77 @@ __global__ void __launch_bounds__(kFThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint64_t ad = sw128_desc(op_st + st * kStageBytes), bd = sw128_desc(op_st + st * kStageBytes + kABytes);
+          const uint32_t a = op_st + st * kFStageBytes;
+          const uint64_t a0 = sw128_desc(a), a1 = sw128_desc(a + kABytes), bd = sw128_desc(a + 2 * kABytes);
 #pragma unroll
-          for (uint32_t kk = 0; kk < kBK / kMmaK; ++kk)
-            mma_f8f6f4(d, ad + 2 * kk, bd + 2 * kk, idesc<false>(), (s | kk) != 0u);
+          for (uint32_t kk = 0; kk < kBK / kMmaK; ++kk) {
+            mma_f8f6f4(tmem, a0 + 2 * kk, bd + 2 * kk, idesc<false>(), (s | kk) != 0u);
+            mma_f8f6f4(tmem + kBN, a1 + 2 * kk, bd + 2 * kk, idesc<false>(), (s | kk) != 0u);
+          }
           mma_commit(oempty(st));
           mma_open = true;
         }
         if (!ok) {
           abort_now();
-          mma_commit(acc_full(b));
+          mma_commit(acc_full);
           mma_open = true;
           break;
         }
-        mma_commit(acc_full(b));
+        mma_commit(acc_full);
         mma_open = false;
       }
     }
     __syncwarp();
   } else if (warp < 6) {
-    // read-back, as in the widened kernel (sums of products of 4)
+    // read-back: TMEM lanes -> staging (transposed) -> 64-byte row segments of C2, for both halves; rounds of
+    // 16 columns, lanes 0-15 and 16-31 writing rows rr and rr + 16
     const uint32_t quarter = warp & 3;
-    uint32_t* sw = staging + (warp - 2) * 32 * kSPitch;
+    uint32_t* sw = staging + (warp - 2) * 32 * kFPitch;
     uint32_t it = 0;
     for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x, ++it) {
       uint32_t bi, bj, k0, ns;
       decode(item, bi, bj, k0, ns);
-      const uint32_t b = it & 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), (it >> 1) & 1));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, it & 1));
       if (!ok || *abort_flag) {
         if (lane == 0 && !ok) abort_now();
         break;
       }
       tc_fence_after();
-      const uint32_t row0 = bi * kBM + quarter * 32;
-      const uint32_t taddr = tmem + ((quarter * 32u) << 16) + b * kBN;
 #pragma unroll 1
-      for (uint32_t c0 = 0; c0 < kBN; c0 += kChunk) {
-        uint32_t r[16];
-        tmem_ld16(taddr + c0, r);
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t row0 = bi * kFM + h * kBM + quarter * 32;
+        const uint32_t taddr = tmem + ((quarter * 32u) << 16) + h * kBN;
+#pragma unroll 1
+        for (uint32_t c0 = 0; c0 < kFN; c0 += kFChunk) {
+          uint32_t r[16];
+          tmem_ld16(taddr + c0, r);
 #pragma unroll
-        for (uint32_t c = 0; c < 16; ++c)
-          sw[lane * kSPitch + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);  // exact: a power of 2
-        tmem_ld16(taddr + c0 + 16, r);
-#pragma unroll
-        for (uint32_t c = 0; c < 16; ++c) sw[lane * kSPitch + 16 + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);
-        __syncwarp();
-        const uint32_t j = bj * kBN + c0 + lane;
+          for (uint32_t c = 0; c < 16; ++c)
+            sw[lane * kFPitch + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);  // exact: a power of 2
+          __syncwarp();
+          const uint32_t j = bj * kFN + c0 + (lane & 15u);
 #pragma unroll 4
-        for (uint32_t rr = 0; rr < 32; ++rr) {
-          const uint32_t i = row0 + rr;
-          if (i < j && j < n1) {
-            const uint32_t v = sw[rr * kSPitch + lane];
-            if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
-            else C2[(size_t)i * n1 + j] = v;
+          for (uint32_t rr = 0; rr < 16; ++rr) {
+            const uint32_t rl = rr + (lane >> 4) * 16u, i = row0 + rl;
+            if (i < j && j < n1) {  // i < j < n1 also bounds i
+              const uint32_t v = sw[rl * kFPitch + (lane & 15u)];
+              if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
+              else C2[(size_t)i * n1 + j] = v;
+            }
           }
+          __syncwarp();
         }
-        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty(b));
+      if (lane == 0) mbar_arrive(acc_empty);
     }
   } else {
-    // expanders: raw stage -> operand stage.  Group g takes the slices c with c mod 2 = g; its thread e owns
-    // rows e and e + 192 of the slice (A rows 0-127, B rows 128-383: consecutive 128-byte rows of the operand
-    // stage): one 16-byte load of the row's 4 raw words, then 8 chunks of 16 bytes, chunk c stored at
-    // c ^ (row mod 8) (the 128-byte swizzle; the 8 lanes of a store phase are 8 consecutive rows, so they
-    // hit 8 distinct chunk positions: no bank conflict)
+    // expanders: raw stage -> operand stage.  Group g takes the slices c with c mod 3 = g (and so always raw
+    // stage g and operand stage g); its thread e owns rows e and e + 256 of the slice (A rows 0-255, B rows 256-511:
+    // consecutive 128-byte rows of the operand stage): one 16-byte load of the row's 4 raw words, then 8
+    // chunks of 16 bytes, chunk c stored at c ^ (row mod 8) (the 128-byte swizzle; the 8 lanes of a store
+    // phase are 8 consecutive rows, so they hit 8 distinct chunk positions: no bank conflict)
     const uint32_t grp = (threadIdx.x - kThreads) / kGroupThreads, e = (threadIdx.x - kThreads) % kGroupThreads;
     uint32_t mul[6];
 #pragma unroll
@@ -645,7 +655,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
           break;
         }
         const uint8_t* rsrc = smem_raw + (raw_st + rs * kRawStageBytes - raw);
-        uint8_t* odst = smem_raw + (op_st + os * kStageBytes - raw);
+        uint8_t* odst = smem_raw + (op_st + os * kFStageBytes - raw);
 #pragma unroll
         for (uint32_t h = 0; h < kRowsPerExp; ++h) {
           const uint32_t row = e + h * kGroupThreads, sw7 = row & 7u;
@@ -687,6 +697,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
                               : "memory");
 }
 
+// tiles of the fused kernel: 256-row blocks bi <= bj
+uint32_t fused_tiles(uint32_t n1) {
+  const uint32_t nb = (n1 + kFM - 1) / kFM;
+  return nb * (nb + 1) / 2;
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -722,9 +738,10 @@ uint64_t pair_mma_buffer_bytes(uint32_t n1, uint32_t stride, bool e2m1) {
 double pair_mma_cost_us(uint32_t n1, uint32_t stride, int num_sms, bool e2m1, bool fused) {
   // widening (bytes written at ~5 TB/s) + tile rounds at ~1.5 PFLOP/s of kind::f8f6f4 per 152 SMs
   const double x_bytes = fused ? 0.0 : (double)pair_mma_buffer_bytes(n1, stride, e2m1);
-  const uint32_t tiles = pair_tiles(n1);
+  // (fused: 256 x 256 tiles, twice the MMAs per slice)
+  const uint32_t tiles = fused ? fused_tiles(n1) : pair_tiles(n1);
   const uint32_t nsteps = stride / 4;
-  const double step_us = 2.0 * kBM * kBN * kBK / (1.5e15 / 152.0) * 1e6;  // one 128-element K slice of a tile
+  const double step_us = (fused ? 2.0 : 1.0) * 2.0 * kBM * kBN * kBK / (1.5e15 / 152.0) * 1e6;  // one K slice of a tile
   double best = 1e300;
   for (uint32_t ks = 1; ks <= 256; ++ks) {
     const uint32_t spi = std::min(kMaxStepsPerItem, (nsteps + ks - 1) / ks);
@@ -779,8 +796,8 @@ cudaError_t launch_pair_mma_fused(const PairLaunch& p, uint32_t* err, int num_sm
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const uint32_t nbj = (p.n1 + kBN - 1) / kBN;
-  const uint32_t tiles = pair_tiles(p.n1);
+  const uint32_t nb = (p.n1 + kFM - 1) / kFM;
+  const uint32_t tiles = fused_tiles(p.n1);
   const uint32_t nsteps = p.stride / 4;  // stride is a multiple of 32 words: whole 128-transaction slices
   const uint32_t spi = pair_split(tiles, nsteps, num_sms);
   const uint32_t ksplit = (nsteps + spi - 1) / spi;
@@ -789,7 +806,7 @@ cudaError_t launch_pair_mma_fused(const PairLaunch& p, uint32_t* err, int num_sm
     return e;
   const uint64_t items = (uint64_t)tiles * ksplit;
   const uint32_t grid = (uint32_t)std::min<uint64_t>(items, (uint64_t)num_sms);
-  k_pair_mma_fused<<<grid, kFThreads, kFSmemBytes, st>>>(map, p.n1, nbj, tiles, nsteps, spi, ksplit, p.C2, err,
+  k_pair_mma_fused<<<grid, kFThreads, kFSmemBytes, st>>>(map, p.n1, nb, tiles, nsteps, spi, ksplit, p.C2, err,
                                                          extra_tx, 1u);
   note_launch();
   return cudaGetLastError();

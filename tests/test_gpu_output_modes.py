@@ -97,7 +97,7 @@ def test_closed_forms():
 
 
 def test_maximal_of_a_wide_database_equals_the_full_result_flags():
-    """On 70,000 transactions of the large-sparse laws (rows of 2,188 words: the automatic projected DFS)
+    """On 70,000 transactions of the large-sparse laws (about 3,900 frequent rows: the automatic projected DFS)
     the maximal output equals the maximal itemsets that the flags pass finds in the complete result,
     itself pinned to the oracle's definitions on the smaller cases (tests/test_gpu_flags.py)."""
     w = synth.make_workload("large_sparse", D=70_000)

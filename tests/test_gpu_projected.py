@@ -63,8 +63,8 @@ def test_random_small_vs_bruteforce(seed):
     assert_same(got, want)
 
 
-# (workload, D, minsup): rows of up to 200,000 transactions, so the automatic mode takes the projected
-# traversal itself on the wide ones
+# (workload, D, minsup): rows of up to 200,000 transactions; the large-sparse laws have about 3,900 frequent
+# rows, so the automatic mode takes the projected traversal itself there
 CASES = [("large_sparse", 200_000, 100), ("large_sparse", 70_000, 40), ("sparse_mid", 100_000, 250),
          ("dense_deep", 50_000, 30_000), ("tiny", 10_000, 100)]
 
@@ -83,7 +83,7 @@ def test_workloads_exact(case, wants):
     w, want = wants[case]
     db = fim.build_vertical_db(w["offsets"], w["items"], w["N"], word_bits=w["word_bits"])
     db.estimate_class_costs(0.01, case[2] / case[1], 1)
-    mode = None if case[1] > 65_536 else PROJ  # the automatic choice on rows wider than 2,048 words
+    mode = None if case[0] == "large_sparse" else PROJ  # the automatic choice with 1,024 or more frequent rows
     res = db.mine(case[2], dfs_mode=mode)
     db.free()
     assert_same(res.as_dict(), want)
