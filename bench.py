@@ -189,7 +189,7 @@ def run_ours(args):
 
     def step(collect_times=False):
         db = fim.build_vertical_db_device(d_off, d_items, D, N, wb, 0, stream=stream)
-        db.estimate_class_costs(SAMPLE_RATE, rel, EST_SEED)
+        db.estimate_class_costs(SAMPLE_RATE, rel, EST_SEED, outputs=False)
         res = db.mine(minsup, result_on_device=True, collect_times=collect_times)
         st = res.stats
         res.free()
@@ -255,7 +255,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         db = fim.build_vertical_db(h_off.numpy(), h_items.numpy(), N, wb, 0, stream=stream)
-        db.estimate_class_costs(SAMPLE_RATE, rel, EST_SEED)
+        db.estimate_class_costs(SAMPLE_RATE, rel, EST_SEED, outputs=False)
         res = db.mine(minsup)
         t1 = time.perf_counter()
         if k >= args.warmup:
@@ -504,7 +504,7 @@ def run_once(args):
     d_items = torch.from_numpy(w["items"].astype(np.int32)).cuda()
     db = fim.build_vertical_db_device(d_off, d_items, w["D"], w["N"], w["word_bits"], 0)
     if not args.no_estimate:
-        db.estimate_class_costs(SAMPLE_RATE, w["rel_minsup"], EST_SEED)
+        db.estimate_class_costs(SAMPLE_RATE, w["rel_minsup"], EST_SEED, outputs=False)
     res = db.mine(w["minsup"], result_on_device=True, collect_times=True)
     st = res.stats
     torch.cuda.synchronize()

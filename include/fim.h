@@ -254,8 +254,18 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
  * LPT order, Sec. 8.2).  Both arrays have n_rows entries (host memory).
  * The estimate is kept in the db and orders the classes of later fim_mine
  * calls (FIM_ORDER_ESTIMATE); it never changes their output.
- * Errors: FIM_ERR_INVALID (sample_rate not in (0,1], rel_minsup not in [0,1],
- * NULL outputs), FIM_ERR_OOM, FIM_ERR_CUDA, FIM_ERR_TIMEOUT.
+ * cost_out and order_out may be NULL.  When both are NULL and the sample is
+ * mined over all its rows (the db has at most 4,096 rows and at least 3/4 of
+ * them have supp * m / D >= minsup_s), the call does not wait for the device: the sample's mine,
+ * its per-class counts and the LPT order stay on the device (a one-CTA sort),
+ * and the next fim_mine takes its class order from there and reads the
+ * sample's itemset count (its first output capacity) only after launching its
+ * pair kernel.  A sample that passed the itemset limit is then mined again by
+ * the synchronous path after that mine (whose output is the same either way).
+ * Errors of such a deferred estimate are reported by the call that reads it
+ * (fim_mine, fim_estimate_result, fim_estimate_sample_size).
+ * Errors: FIM_ERR_INVALID (sample_rate not in (0,1], rel_minsup not in
+ * [0,1]), FIM_ERR_OOM, FIM_ERR_CUDA, FIM_ERR_TIMEOUT.
  */
 fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
                                     double* cost_out, uint32_t* order_out);
@@ -281,9 +291,18 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
                                        uint32_t* order_out);
 
 /* Number of frequent itemsets found in the sample by the last estimate, the
- * sample's size and the sample minsup it was mined at (after any doubling). */
+ * sample's size and the sample minsup it was mined at (after any doubling).
+ * Waits for a deferred estimate. */
 fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, uint32_t* sample_rows,
                                     uint32_t* sample_minsup);
+
+/* The last estimate's class costs and LPT order (n_rows entries each, host
+ * memory, either may be NULL), as fim_estimate_class_costs_ex returns them;
+ * waits for a deferred estimate (and runs its synchronous redo if it needs
+ * one).  The thesis's counterpart is the schedule that Sec. 8.2 computes from
+ * the sample.  Errors: FIM_ERR_INVALID (no estimate), FIM_ERR_CUDA,
+ * FIM_ERR_TIMEOUT. */
+fim_status fim_estimate_result(fim_db* db, double* cost_out, uint32_t* order_out);
 
 /*
  * Mine every frequent itemset F = { X != {} : supp(X) >= minsup_abs }

@@ -158,6 +158,118 @@ __global__ void k_row_popcount(const uint32_t* __restrict__ bits, uint32_t strid
   }
 }
 
+// Exclusive prefix sum over the 1024 threads of a CTA of each thread's total v (thread order); returns the
+// sum of all threads through *total.  Every thread of the CTA calls it.
+__device__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < (blockDim.x >> 5) ? wsum[lane] : 0u;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    wsum[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  const uint32_t before_warp = warp ? wsum[warp - 1] : 0u;
+  *total = wsum[(blockDim.x >> 5) - 1];
+  __syncthreads();  // wsum is reused by the next call
+  return before_warp + x - v;
+}
+
+// The class costs of an estimate and their LPT order, on the device (one CTA of 1024 threads, at most
+// kEstDeviceRows rows, shared memory P x 12 bytes for P the power of two >= R).  For row i of the sample,
+// mined over all its rows: a class of the sample when ssupp[i] >= minsup_s, its cost per[i] (the sample's
+// itemsets whose lowest row is i, or the DFS intersections below it) plus, for the intersection measure, its
+// level-2 candidates (the frequent sample rows after i); 0 for the other rows.  order = the rows by
+// descending cost, ties by row (what a stable sort by cost gives), by a bitonic sort of (cost, row) keys.
+__global__ void __launch_bounds__(1024) k_est_order(const unsigned long long* __restrict__ per,
+                                                    const uint32_t* __restrict__ ssupp, uint32_t minsup_s,
+                                                    uint32_t intersections, uint32_t R, uint32_t P,
+                                                    unsigned long long* __restrict__ tally,
+                                                    uint32_t* __restrict__ order) {
+  extern __shared__ unsigned long long skey[];
+  uint32_t* srow = reinterpret_cast<uint32_t*>(skey + P);
+  // frequent sample rows before each of this thread's four rows (rows 4t .. 4t + 3)
+  uint32_t f[4], cnt = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    const uint32_t i = 4 * threadIdx.x + q;
+    f[q] = i < R && ssupp[i] >= minsup_s;
+    cnt += f[q];
+  }
+  uint32_t n_freq = 0;
+  uint32_t before = cta_exclusive_scan(cnt, &n_freq);
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    const uint32_t i = 4 * threadIdx.x + q;
+    before += f[q];  // frequent rows up to and including i
+    if (i < R) {
+      const unsigned long long t = f[q] ? per[i] + (intersections ? (unsigned long long)(n_freq - before) : 0ull) : 0ull;
+      tally[i] = t;
+      skey[i] = t;
+      srow[i] = i;
+    }
+  }
+  for (uint32_t i = R + threadIdx.x; i < P; i += blockDim.x) {  // padding: sorts after every row
+    skey[i] = 0ull;
+    srow[i] = 0xffffffffu;
+  }
+  __syncthreads();
+  // a before b: larger cost, or equal cost and smaller row
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const unsigned long long ta = skey[i], tb = skey[l];
+          const uint32_t ra = srow[i], rb = srow[l];
+          const bool b_before_a = tb > ta || (tb == ta && rb < ra);
+          const bool a_before_b = ta > tb || (ta == tb && ra < rb);
+          if ((i & k) == 0 ? b_before_a : a_before_b) {
+            skey[i] = tb;
+            skey[l] = ta;
+            srow[i] = rb;
+            srow[l] = ra;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < R; i += blockDim.x) order[i] = srow[i];
+}
+
+// The queue order of a mine's frequent rows r0 .. r0 + n1 - 1 from an estimate's order over all R rows:
+// the order's entries >= r0, in their order, minus r0 (one CTA of 1024 threads, R <= kEstDeviceRows).
+__global__ void __launch_bounds__(1024) k_order_suffix(const uint32_t* __restrict__ order, uint32_t R, uint32_t r0,
+                                                       uint32_t* __restrict__ out) {
+  uint32_t v[4], cnt = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    const uint32_t i = 4 * threadIdx.x + q;
+    v[q] = i < R ? order[i] : 0u;
+    cnt += i < R && v[q] >= r0;
+  }
+  uint32_t total = 0;
+  uint32_t pos = cta_exclusive_scan(cnt, &total);
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    const uint32_t i = 4 * threadIdx.x + q;
+    if (i < R && v[q] >= r0) out[pos++] = v[q] - r0;
+  }
+}
+
 __global__ void k_iota(uint32_t* out, uint32_t n) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
 }
@@ -201,6 +313,26 @@ cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint
 cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_iota<<<grid_for(n, 256), 256, 0, st>>>(out, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_est_order(const unsigned long long* per, const uint32_t* ssupp, uint32_t minsup_s,
+                             bool intersections, uint32_t R, unsigned long long* tally, uint32_t* order,
+                             cudaStream_t st) {
+  if (R == 0) return cudaSuccess;
+  if (R > kEstDeviceRows) return cudaErrorInvalidValue;
+  uint32_t P = 2;
+  while (P < R) P <<= 1;
+  k_est_order<<<1, 1024, (size_t)P * 12, st>>>(per, ssupp, minsup_s, intersections ? 1u : 0u, R, P, tally, order);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order_suffix(const uint32_t* order, uint32_t R, uint32_t r0, uint32_t* out, cudaStream_t st) {
+  if (R == 0) return cudaSuccess;
+  if (R > kEstDeviceRows) return cudaErrorInvalidValue;
+  k_order_suffix<<<1, 1024, 0, st>>>(order, R, r0, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -66,7 +66,7 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // row lists (pinned-staged uploads unless the caller already has them on the device)
   ep->d_frows = in.d_frows;
   ep->d_rsupp = in.d_row_supp;
-  ep->d_order = in.identity_order ? db->d_iota : nullptr;
+  ep->d_order = in.identity_order ? db->d_iota : in.d_row_order;
   auto upload = [&](int slot, const std::vector<uint32_t>& v, const uint32_t** dst) -> fim_status {
     uint32_t* d = nullptr;
     void* h = nullptr;
@@ -236,6 +236,11 @@ fim_status engine_alloc(Workspace& ws, EnginePlan* ep) {
 }
 
 cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
+  cudaError_t ce = engine_launch_front(ep, st, !ep.skip_pairs);
+  return ce != cudaSuccess ? ce : engine_launch_back(ep, st);
+}
+
+cudaError_t engine_launch_front(const EnginePlan& ep, cudaStream_t st, bool pairs) {
   cudaError_t ce = cudaMemsetAsync(ep.d_ctrl, 0, sizeof(DevCtrl), st);
   if (ce != cudaSuccess || ep.n1 == 0) return ce;
   if (ep.d_class_work) {
@@ -247,7 +252,7 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     if (ce != cudaSuccess) return ce;
   }
   if (ep.ev[0]) cudaEventRecord(ep.ev[0], st);
-  if (!ep.skip_pairs) {
+  if (pairs) {
     uint32_t ksplit = 0;
     PairLaunch pl{ep.bits, ep.stride, ep.d_frows, ep.n1, ep.d_C2, 0, ep.rows_base};
     ce = ep.pair_fused ? launch_pair_mma_fused(pl, &ep.d_ctrl->err, ep.num_sms, st, &ksplit, ep.pair_extra_tx)
@@ -257,6 +262,12 @@ cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st) {
     if (ce != cudaSuccess) return ce;
   }
   if (ep.ev[1]) cudaEventRecord(ep.ev[1], st);
+  return cudaSuccess;
+}
+
+cudaError_t engine_launch_back(const EnginePlan& ep, cudaStream_t st) {
+  if (ep.n1 == 0) return cudaSuccess;
+  cudaError_t ce = cudaSuccess;
   LevelLaunch ll{ep.d_C2, ep.n1, ep.minsup, ep.d_frows, ep.d_rsupp, ep.d_rank_item, ep.d_order, ep.d_scnt,
                  ep.d_soff, ep.d_eoff, ep.d_sitems, ep.d_entries, ep.d_off, ep.d_items, ep.d_supp,
                  ep.count_only ? 0ull : ep.cap_sets, ep.count_only ? 0ull : ep.cap_items, ep.d_ctrl,
@@ -481,7 +492,7 @@ fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutp
 }
 
 fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg, EngineOutput* out,
-                       fim_mine_stats* stats, EnginePlan* plan_out) {
+                       fim_mine_stats* stats, EnginePlan* plan_out, const std::function<fim_status(EnginePlan*)>& after_pairs) {
   EnginePlan ep;
   fim_status s = engine_prepare(db, ws, in, cfg, &ep);
   if (s == FIM_OK && cfg.class_work) ep.d_class_work = cfg.class_work;
@@ -489,9 +500,17 @@ fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const E
   ep.count_only = cfg.count_only;
   ep.class_out = cfg.class_out;
   ep.max_sets = cfg.max_sets;
+  // the pair kernel first: it needs no output buffer, so whatever the hook waits for (a deferred estimate's
+  // class costs and itemset count) overlaps with it
+  if (s == FIM_OK) {
+    const cudaError_t ce = engine_launch_front(ep, ws.stream, true);
+    if (ce != cudaSuccess) s = cuda_fail(ce, "mining kernels");
+  }
+  if (s == FIM_OK && after_pairs) s = after_pairs(&ep);
   for (int attempt = 0; s == FIM_OK && attempt < 8; ++attempt) {
     if ((s = engine_alloc(ws, &ep)) != FIM_OK) break;
-    cudaError_t ce = engine_launch(ep, ws.stream);
+    cudaError_t ce = attempt ? engine_launch_front(ep, ws.stream, false) : cudaSuccess;
+    if (ce == cudaSuccess) ce = engine_launch_back(ep, ws.stream);
     if (ce != cudaSuccess) {
       s = cuda_fail(ce, "mining kernels");
       break;

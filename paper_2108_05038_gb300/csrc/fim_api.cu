@@ -423,7 +423,19 @@ static void engine_config_from_opts(const fim_mine_opts* o, EngineConfig* c) {
 }
 
 
-fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg) {
+uint64_t estimate_capacity(const fim_db* db, uint32_t minsup_abs) {
+  // first output capacity: |F| of the whole database at about the same relative minsup is of the order of
+  // the sample's |F_s|, so a few times |F_s| usually avoids a second DFS run (when the sample's minsup had
+  // to be raised, its count at the requested minsup passed the limit, so the limit is the better lower bound)
+  if (!db->has_estimate || db->est_pending || !db->est_nfs || !(db->est_rel > 0.0)) return 0;
+  const double rel = (double)minsup_abs / (double)db->D;
+  if (std::fabs(rel - db->est_rel) > 0.1 * db->est_rel) return 0;
+  const uint64_t f = db->est_doubled ? std::max<uint64_t>(db->est_nfs, db->est_limit) : db->est_nfs;
+  return std::min<uint64_t>(4ull * f, 1ull << 28);
+}
+
+fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg,
+                      bool defer_ok) {
   if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
   if (minsup_abs == 0) return fail(FIM_ERR_INVALID, "minsup 0 makes every subset frequent");
   if (minsup_abs < db->prefilter) return fail(FIM_ERR_INVALID, "minsup below the prefilter support of the database");
@@ -443,7 +455,17 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
   const uint32_t order = opts && opts->struct_size ? opts->class_order : (uint32_t)FIM_ORDER_ESTIMATE;
   in->row_order.clear();
   in->row_order.reserve(in->n1);
-  if (order == FIM_ORDER_ESTIMATE && db->has_estimate && in->n1) {
+  if (!defer_ok || order != FIM_ORDER_ESTIMATE) {  // the host copies of a deferred estimate are needed now
+    FIM_TRY(est_resolve(db));
+    FIM_TRY(est_redo(db));
+  }
+  if (order == FIM_ORDER_ESTIMATE && db->has_estimate && db->est_pending && in->n1) {
+    // the deferred estimate's order, restricted to this minsup's rows on the device
+    uint32_t* d = nullptr;
+    FIM_TRY(ws_get(db->ws, WS_ROWORDER, in->n1, &d));
+    FIM_CUDA(launch_order_suffix(db->d_est_order, db->n_rows, db->n_rows - in->n1, d, db->stream));
+    in->d_row_order = d;
+  } else if (order == FIM_ORDER_ESTIMATE && db->has_estimate && in->n1) {
     const uint32_t r0 = db->n_rows - in->n1;
     for (uint32_t r : db->est_order)
       if (r >= r0) in->row_order.push_back(r - r0);
@@ -461,14 +483,9 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
     cfg->mode = FIM_DFS_PROJECTED;
     cfg->donate = 0;
   }
-  // first output capacity: |F| of the whole database at about the same relative minsup is of
-  // the order of the sample's |F_s|, so a few times |F_s| usually avoids a second DFS run
-  // (when the sample's minsup had to be raised, its count at the requested minsup passed the
-  // limit, so the limit is the better lower bound)
-  if (!cfg->cap_sets && db->has_estimate && db->est_nfs && db->est_rel > 0.0) {
-    const double rel = (double)minsup_abs / (double)db->D;
-    const uint64_t f = db->est_doubled ? std::max<uint64_t>(db->est_nfs, db->est_limit) : db->est_nfs;
-    if (std::fabs(rel - db->est_rel) <= 0.1 * db->est_rel) cfg->cap_sets = std::min<uint64_t>(4ull * f, 1ull << 28);
+  if (!cfg->cap_sets) {
+    const uint64_t c = estimate_capacity(db, minsup_abs);
+    if (c) cfg->cap_sets = c;
   }
   return FIM_OK;
 }
@@ -604,6 +621,22 @@ fim_status fim_estimate_class_costs(fim_db* db, double sample_rate, double rel_m
 fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed,
                                        uint32_t cost_kind, uint64_t max_sample_itemsets, double* cost_out,
                                        uint32_t* order_out) {
+  return fim::estimate_impl(db, sample_rate, rel_minsup, seed, cost_kind, max_sample_itemsets, cost_out, order_out,
+                            true);
+}
+
+}  // extern "C"
+
+namespace fim {
+
+// The estimate itself.  With allow_defer, no host output asked for, and a sample mined over all its rows
+// (at most kEstDeviceRows), nothing waits for the device: the sample's count-only mine is only launched, a
+// one-CTA kernel turns its per-class counts into the class costs and their LPT order on the device, and the
+// control block, costs and order travel to a pinned block behind an event; est_resolve reads them when a
+// caller needs them (fim_mine only after its pair kernel is on its way).  A deferred sample that ran into
+// the itemset limit (or needed a retry) is mined again by the synchronous path after the mine that used it.
+fim_status estimate_impl(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed, uint32_t cost_kind,
+                         uint64_t max_sample_itemsets, double* cost_out, uint32_t* order_out, bool allow_defer) {
   if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
   if (cost_kind != FIM_COST_ITEMSETS && cost_kind != FIM_COST_INTERSECTIONS)
     return fail(FIM_ERR_INVALID, "unknown cost kind");
@@ -637,6 +670,66 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
     FIM_CUDA(cudaMemsetAsync(d_sbits, 0, (size_t)R * sstride * 4, st));
     FIM_CUDA(launch_sample_build(db->d_tx_off, db->d_tx_items, db->D, db->d_item_rank, seed, m, d_sbits, sstride, st));
     FIM_CUDA(launch_row_popcount(d_sbits, sstride, R, d_ssupp, st));
+    if (allow_defer && all_rows && !cost_out && !order_out && R <= kEstDeviceRows) {
+      db->est_pending = false;  // (a pending earlier estimate is replaced)
+      db->has_estimate = false;
+      EngineInput in;
+      in.bits = d_sbits;
+      in.stride = sstride;
+      in.bytes_per_row_alg = (uint32_t)(((uint64_t)m + db->word_bits - 1) / db->word_bits * (db->word_bits / 8));
+      in.frows.resize(R);
+      std::iota(in.frows.begin(), in.frows.end(), 0u);
+      in.d_frows = db->d_iota;
+      in.d_row_supp = d_ssupp;
+      in.n1 = R;
+      in.identity_order = true;
+      in.d_rank_item = db->d_rank_item;
+      in.minsup = minsup_s;
+      in.max_len_bound = db->max_tx_len;
+      EngineConfig cfg;
+      cfg.donate = 0;
+      unsigned long long* d_work = nullptr;
+      FIM_TRY(ws_get(db->ws, WS_CLASSWORK, R, &d_work));
+      EnginePlan ep;
+      FIM_TRY(engine_prepare(db, db->ws, in, cfg, &ep));
+      if (cost_kind == FIM_COST_INTERSECTIONS) ep.d_class_work = d_work;
+      else ep.d_class_sets = d_work;
+      ep.count_only = true;  // per-class counts, no itemset records
+      ep.max_sets = max_sample_itemsets;
+      FIM_TRY(engine_alloc(db->ws, &ep));
+      FIM_CUDA(engine_launch(ep, st));
+      uint32_t* d_est = nullptr;  // costs (R u64), then the order (R u32)
+      FIM_TRY(ws_get(db->ws, WS_EST, 3ull * R, &d_est));
+      unsigned long long* d_tally = reinterpret_cast<unsigned long long*>(d_est);
+      uint32_t* d_order = d_est + 2ull * R;
+      FIM_CUDA(launch_est_order(d_work, d_ssupp, minsup_s, cost_kind == FIM_COST_INTERSECTIONS, R, d_tally, d_order, st));
+      const size_t ctrl_bytes = (sizeof(DevCtrl) + 63) & ~(size_t)63;
+      const size_t need = ctrl_bytes + 12ull * R;
+      if (db->est_pin_cap < need) {
+        if (db->est_pin) FIM_CUDA(cudaStreamSynchronize(st));  // an earlier copy may still target the old block
+        pinned_release(db->est_pin, db->est_pin_cap);
+        db->est_pin = nullptr;
+        db->est_pin_cap = 0;
+        FIM_CUDA(pinned_acquire(need, &db->est_pin, &db->est_pin_cap));
+      }
+      uint8_t* pin = static_cast<uint8_t*>(db->est_pin);
+      FIM_CUDA(cudaMemcpyAsync(pin, ep.d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+      FIM_CUDA(cudaMemcpyAsync(pin + ctrl_bytes, d_est, 12ull * R, cudaMemcpyDeviceToHost, st));
+      if (!db->est_done) FIM_CUDA(cudaEventCreateWithFlags(&db->est_done, cudaEventDisableTiming));
+      FIM_CUDA(cudaEventRecord(db->est_done, st));
+      db->d_est_order = d_order;
+      db->est_pending = true;
+      db->est_redo = false;
+      db->has_estimate = true;
+      db->est_nfs = 0;  // known once resolved
+      db->est_m = m;
+      db->est_minsup = minsup_s;
+      db->est_rel = rel_minsup;
+      db->est_limit = max_sample_itemsets;
+      db->est_doubled = false;
+      db->est_args = {sample_rate, rel_minsup, seed, max_sample_itemsets, cost_kind};
+      return FIM_OK;
+    }
     if (all_rows) {  // a pinned buffer of its own: the mine's retries may reuse the staging buffer
       FIM_CUDA(pinned_acquire((size_t)R * 4, &h_ss, &h_ss_cap));
       const cudaError_t ce = cudaMemcpyAsync(h_ss, d_ssupp, (size_t)R * 4, cudaMemcpyDeviceToHost, st);
@@ -744,6 +837,57 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
   db->est_doubled = minsup_s != (msd < 1.0 ? 1u : (uint32_t)msd);
   if (cost_out && R) std::memcpy(cost_out, db->est_cost.data(), R * sizeof(double));
   if (order_out && R) std::memcpy(order_out, db->est_order.data(), R * sizeof(uint32_t));
+  db->est_pending = false;
+  db->est_redo = false;
+  return FIM_OK;
+}
+
+// Waits for a deferred estimate and reads its control block, costs and order from the pinned block into the
+// database's host copies; a sample past the itemset limit (or one that needed a retry) leaves the order of
+// its partial counts and asks for the synchronous redo.
+fim_status est_resolve(fim_db* db) {
+  if (!db->est_pending) return FIM_OK;
+  FIM_CUDA(cudaEventSynchronize(db->est_done));
+  db->est_pending = false;
+  const uint32_t R = db->n_rows;
+  const size_t ctrl_bytes = (sizeof(DevCtrl) + 63) & ~(size_t)63;
+  const uint8_t* pin = static_cast<const uint8_t*>(db->est_pin);
+  DevCtrl h;
+  std::memcpy(&h, pin, sizeof(DevCtrl));
+  std::vector<unsigned long long> tally(R);
+  std::memcpy(tally.data(), pin + ctrl_bytes, 8ull * R);
+  db->est_order.resize(R);
+  std::memcpy(db->est_order.data(), pin + ctrl_bytes + 8ull * R, 4ull * R);
+  unsigned long long total = 0;
+  for (uint32_t r = 0; r < R; ++r) total += tally[r];
+  db->est_cost.assign(R, 0.0);
+  for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = total ? (double)tally[r] / (double)total : 0.0;
+  db->est_nfs = h.sets_total;
+  db->est_redo = (h.err & (DEV_ERR_TIMEOUT | DEV_ERR_ABORTED | DEV_ERR_PSTACK | DEV_ERR_DEPTH)) != 0 ||
+                 (db->est_limit && h.sets_total > db->est_limit);
+  return FIM_OK;
+}
+
+// The synchronous estimate of a deferred one that est_resolve found incomplete.
+fim_status est_redo(fim_db* db) {
+  if (!db->est_redo) return FIM_OK;
+  db->est_redo = false;
+  const auto a = db->est_args;
+  return estimate_impl(db, a.rate, a.rel, a.seed, a.kind, a.limit, nullptr, nullptr, false);
+}
+
+}  // namespace fim
+
+extern "C" {
+
+fim_status fim_estimate_result(fim_db* db, double* cost_out, uint32_t* order_out) {
+  if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
+  if (!db->has_estimate) return fail(FIM_ERR_INVALID, "no estimate computed");
+  FIM_TRY(est_resolve(db));
+  FIM_TRY(est_redo(db));
+  const uint32_t R = db->n_rows;
+  if (cost_out && R) std::memcpy(cost_out, db->est_cost.data(), R * sizeof(double));
+  if (order_out && R) std::memcpy(order_out, db->est_order.data(), R * sizeof(uint32_t));
   return FIM_OK;
 }
 
@@ -751,6 +895,8 @@ fim_status fim_estimate_sample_size(const fim_db* db, uint64_t* n_sample_fis, ui
                                     uint32_t* sample_minsup) {
   if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
   if (!db->has_estimate) return fail(FIM_ERR_INVALID, "no estimate computed");
+  FIM_TRY(est_resolve(const_cast<fim_db*>(db)));
+  FIM_TRY(est_redo(const_cast<fim_db*>(db)));
   if (n_sample_fis) *n_sample_fis = db->est_nfs;
   if (sample_rows) *sample_rows = db->est_m;
   if (sample_minsup) *sample_minsup = db->est_minsup;
@@ -762,7 +908,19 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
   *out = nullptr;
   EngineInput in;
   EngineConfig cfg;
-  FIM_TRY(mine_input(db, minsup_abs, opts, &in, &cfg));
+  FIM_TRY(mine_input(db, minsup_abs, opts, &in, &cfg, true));
+  // a deferred estimate is read only once the pair kernel is launched: its output capacity comes from the
+  // sample's itemset count
+  auto after_pairs = [&](EnginePlan* ep) -> fim_status {
+    if (!db->est_pending) return FIM_OK;
+    FIM_TRY(est_resolve(db));
+    const uint64_t c = cfg.cap_sets ? 0ull : estimate_capacity(db, minsup_abs);
+    if (c) {
+      ep->cap_sets = std::min<uint64_t>(c, 0xfffffff0ull);
+      if (!cfg.cap_items) ep->cap_items = std::min<uint64_t>(ep->cap_sets * 6, 0xfffffff0ull);
+    }
+    return FIM_OK;
+  };
   fim_mine_stats local_stats{};
   fim_mine_stats* stats = opts && opts->struct_size && opts->stats ? opts->stats : &local_stats;
   std::memset(stats, 0, sizeof(*stats));
@@ -773,7 +931,7 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
     cfg.class_work = d_work;
   }
   EngineOutput eo;
-  fim_status s = engine_mine(db, db->ws, in, cfg, &eo, stats);
+  fim_status s = engine_mine(db, db->ws, in, cfg, &eo, stats, nullptr, after_pairs);
   if (s == FIM_ERR_OUTPUT_OVERFLOW && opts && opts->struct_size) {
     opts->out_needed_sets = eo.ctrl.sets_total;
     opts->out_needed_items = eo.ctrl.items_total;
@@ -799,7 +957,15 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
       for (uint32_t i = 0; i < in.n1; ++i) work_out[r0 + i] = w[i] + (in.n1 - 1 - i);
     }
   }
-  return make_result(db->stream, eo, opts && opts->struct_size && opts->result_on_device, out);
+  FIM_TRY(make_result(db->stream, eo, opts && opts->struct_size && opts->result_on_device, out));
+  // a deferred estimate that this mine found incomplete: the synchronous estimate now (after the result's
+  // copies in stream order), for the later mines and queries of the database
+  const fim_status r = est_redo(db);
+  if (r != FIM_OK) {
+    fim_result_free(*out);
+    *out = nullptr;
+  }
+  return r;
 }
 
 fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,
@@ -834,6 +1000,8 @@ void fim_db_free(fim_db* db) {
     db->ws.release();
   }
   fim::pinned_release(db->stage, db->stage_cap);
+  fim::pinned_release(db->est_pin, db->est_pin_cap);
+  if (db->est_done) cudaEventDestroy(db->est_done);
   delete db;
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "../../include/fim.h"
@@ -99,6 +100,7 @@ enum WsSlot {
   WS_SAMPLE_SUPP,
   WS_TALLY,
   WS_CLASSWORK,
+  WS_EST,  // a deferred estimate's class costs (u64) and order (u32)
   WS_CTATIME,
   WS_PAIR_X,        // rows widened to bytes for the tensor-core pair kernel
   WS_QUERY_ROWS,    // fim_extension_supports: prefix rows | candidate rows
@@ -212,6 +214,19 @@ struct fim_db {
   double est_rel = 0.0;      // relative minsup the estimate was asked for
   bool est_doubled = false;  // the sample minsup was raised by the itemset limit
   uint64_t est_limit = 0;    // that limit
+  // a deferred estimate (no host outputs asked for): costs and order on the device (d_est_order, R rows),
+  // the sample's control block, costs and order copied to est_pin behind est_done; est_pending until read
+  bool est_pending = false;
+  bool est_redo = false;  // the deferred sample needs the synchronous path (itemset limit or a retry)
+  cudaEvent_t est_done = nullptr;
+  void* est_pin = nullptr;
+  size_t est_pin_cap = 0;
+  const uint32_t* d_est_order = nullptr;
+  struct {
+    double rate, rel;
+    uint64_t seed, limit;
+    uint32_t kind;
+  } est_args{};
 
   fim::Workspace ws;
 
@@ -251,6 +266,7 @@ struct EngineInput {
   std::vector<uint32_t> frows;     // ascending row ids (host), n1 entries
   std::vector<uint32_t> row_supp;  // support of each frequent row, n1 entries
   std::vector<uint32_t> row_order; // queue order of the top classes (permutation of 0..n1-1)
+  const uint32_t* d_row_order = nullptr;  // optional device copy of row_order (else uploaded)
   const uint32_t* d_rank_item = nullptr;  // row -> original item id
   uint32_t minsup = 1;
   uint32_t max_len_bound = 2;      // upper bound on the length of a frequent itemset
@@ -354,20 +370,38 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
 fim_status engine_alloc(Workspace& ws, EnginePlan* ep);
 // all device work of one mine: no host synchronisation, no allocation (graph capturable)
 cudaError_t engine_launch(const EnginePlan& ep, cudaStream_t st);
+// its two parts: the control block reset and (when `pairs`) the pair kernel, which needs no output buffer;
+// then level 2, the DFS and the timing events
+cudaError_t engine_launch_front(const EnginePlan& ep, cudaStream_t st, bool pairs);
+cudaError_t engine_launch_back(const EnginePlan& ep, cudaStream_t st);
 // wait, read the control block, check errors; *retry = true when the buffers must grow and the
 // launch be repeated (output capacity or DFS depth)
 fim_status engine_finish(fim_db* db, cudaStream_t st, EnginePlan* ep, EngineOutput* out, fim_mine_stats* stats,
                          bool* retry);
-// the EngineInput / EngineConfig of a fim_mine call (validation included)
-fim_status mine_input(fim_db* db, uint32_t minsup, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg);
+// the EngineInput / EngineConfig of a fim_mine call (validation included); with defer_ok a pending estimate
+// stays pending (the queue order is derived on the device, the output capacity left to the caller)
+fim_status mine_input(fim_db* db, uint32_t minsup, const fim_mine_opts* opts, EngineInput* in, EngineConfig* cfg,
+                      bool defer_ok = false);
+// the first output capacity that the database's estimate suggests for a minsup (0: none)
+uint64_t estimate_capacity(const fim_db* db, uint32_t minsup);
+// fim_estimate_class_costs_ex, allowed to leave its result on the device (see fim_api.cu)
+fim_status estimate_impl(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed, uint32_t cost_kind,
+                         uint64_t max_sample_itemsets, double* cost_out, uint32_t* order_out, bool allow_defer);
+// a deferred estimate read into the database's host copies (no-op when none is pending)
+fim_status est_resolve(fim_db* db);
+// the synchronous estimate that a deferred one found incomplete asks for (no-op otherwise)
+fim_status est_redo(fim_db* db);
 // keeps the itemsets of an engine output whose closed (keep = 1) or maximal (keep = 2) flag is set, decided
 // by the immediate supersets within the output itself (result_flags.cu); the output's buffers are replaced
 // by workspace buffers holding the kept itemsets in their original order
 fim_status filter_output(Workspace& ws, cudaStream_t st, uint8_t keep, EngineOutput* eo, int num_sms);
 // fim_result from an engine output (device copy or host copy per on_device)
 fim_status make_result(cudaStream_t st, const EngineOutput& eo, bool on_device, fim_result** out);
+// prepare, launch the pair kernel, call `after_pairs` (may change the output capacity), then allocate,
+// launch the rest and finish, repeating the later stages while the buffers must grow
 fim_status engine_mine(fim_db* db, Workspace& ws, const EngineInput& in, const EngineConfig& cfg,
-                       EngineOutput* out, fim_mine_stats* stats, EnginePlan* plan_out = nullptr);
+                       EngineOutput* out, fim_mine_stats* stats, EnginePlan* plan_out = nullptr,
+                       const std::function<fim_status(EnginePlan*)>& after_pairs = {});
 void engine_release_events(EnginePlan* ep);
 // pinned staging of a database (see fim_api.cu)
 fim_status stage_get(fim_db* db, size_t bytes, void** out);
@@ -386,6 +420,14 @@ cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint
 cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t n_rows, uint32_t* supp,
                                 cudaStream_t st);
+// rows of a database whose estimate may stay on the device (one-CTA tally, sort and suffix kernels)
+constexpr uint32_t kEstDeviceRows = 4096;
+// class costs (tally, R u64) and their LPT order (R u32) of a sample mined over all its R rows
+cudaError_t launch_est_order(const unsigned long long* per, const uint32_t* ssupp, uint32_t minsup_s,
+                             bool intersections, uint32_t R, unsigned long long* tally, uint32_t* order,
+                             cudaStream_t st);
+// the queue order of the rows r0 .. of a mine from an estimate's order over all R rows
+cudaError_t launch_order_suffix(const uint32_t* order, uint32_t R, uint32_t r0, uint32_t* out, cudaStream_t st);
 
 struct PairLaunch {
   const uint32_t* bits;

@@ -25,7 +25,7 @@ SAMPLE_ITEMSET_LIMIT = 1 << 20  # FIM_SAMPLE_ITEMSET_LIMIT
 # every symbol declared in include/fim.h
 EXPORTED = [
     "fim_mine_opts_init", "fim_build_vertical_db", "fim_build_vertical_db_device", "fim_db_info", "fim_db_rows",
-    "fim_estimate_class_costs", "fim_estimate_class_costs_ex", "fim_estimate_sample_size", "fim_mine", "fim_result_view", "fim_result_free",
+    "fim_estimate_class_costs", "fim_estimate_class_costs_ex", "fim_estimate_sample_size", "fim_estimate_result", "fim_mine", "fim_result_view", "fim_result_free",
     "fim_db_free", "fim_status_str", "fim_last_error", "fim_mine_pairs_noalloc", "fim_autotune", "fim_plan_create",
     "fim_plan_launch", "fim_plan_result", "fim_plan_stream", "fim_plan_free", "fim_server_create",
     "fim_server_submit", "fim_server_wait", "fim_server_stats", "fim_server_free", "fim_kernel_launches",
@@ -116,6 +116,8 @@ def load(build_if_stale: bool = True):
         lib.fim_estimate_class_costs_ex.argtypes = [P, dbl, dbl, u64, u32, u64, P, P]
         lib.fim_estimate_sample_size.restype = i32
         lib.fim_estimate_sample_size.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.fim_estimate_result.restype = i32
+        lib.fim_estimate_result.argtypes = [P, P, P]
         lib.fim_mine.restype = i32
         lib.fim_mine.argtypes = [P, u32, ctypes.POINTER(MineOpts), PP]
         lib.fim_autotune.restype = i32
@@ -277,17 +279,33 @@ class Database:
         return ri[:n], sp[:n]
 
     def estimate_class_costs(self, sample_rate: float, rel_minsup: float, seed: int, cost: str = "itemsets",
-                             max_sample_itemsets: int = SAMPLE_ITEMSET_LIMIT):
+                             max_sample_itemsets: int = SAMPLE_ITEMSET_LIMIT, outputs: bool = True):
         """fim_estimate_class_costs_ex: cost "itemsets" (the thesis's measure) or "intersections"; the sample
-        minsup doubles while the sample has more than ``max_sample_itemsets`` frequent itemsets (0: never)."""
+        minsup doubles while the sample has more than ``max_sample_itemsets`` frequent itemsets (0: never).
+        outputs=False passes NULL outputs (the estimate may then stay on the device until the next mine) and
+        returns None."""
+        kind = {"itemsets": 0, "intersections": 1}[cost]
+        if not outputs:
+            _check(self._lib, self._lib.fim_estimate_class_costs_ex(self._h, sample_rate, rel_minsup, seed, kind,
+                                                                    max_sample_itemsets, None, None),
+                   "fim_estimate_class_costs_ex")
+            return None
         n = self.info()["n_rows"]
         c = np.zeros(max(n, 1), dtype=np.float64)
         order = np.zeros(max(n, 1), dtype=np.uint32)
-        kind = {"itemsets": 0, "intersections": 1}[cost]
         _check(self._lib, self._lib.fim_estimate_class_costs_ex(self._h, sample_rate, rel_minsup, seed, kind,
                                                                 max_sample_itemsets, c.ctypes.data,
                                                                 order.ctypes.data),
                "fim_estimate_class_costs_ex")
+        return c[:n], order[:n]
+
+    def estimate_result(self):
+        """fim_estimate_result: the last estimate's (costs, order), waiting for a deferred one."""
+        n = self.info()["n_rows"]
+        c = np.zeros(max(n, 1), dtype=np.float64)
+        order = np.zeros(max(n, 1), dtype=np.uint32)
+        _check(self._lib, self._lib.fim_estimate_result(self._h, c.ctypes.data, order.ctypes.data),
+               "fim_estimate_result")
         return c[:n], order[:n]
 
     def estimate_sample_size(self):
