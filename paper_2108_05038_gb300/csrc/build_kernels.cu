@@ -187,67 +187,44 @@ __device__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t* total) {
   return before_warp + x - v;
 }
 
-// The class costs of an estimate and their LPT order, on the device (one CTA of 1024 threads, at most
-// kEstDeviceRows rows, shared memory P x 12 bytes for P the power of two >= R).  For row i of the sample,
-// mined over all its rows: a class of the sample when ssupp[i] >= minsup_s, its cost per[i] (the sample's
-// itemsets whose lowest row is i, or the DFS intersections below it) plus, for the intersection measure, its
-// level-2 candidates (the frequent sample rows after i); 0 for the other rows.  order = the rows by
-// descending cost, ties by row (what a stable sort by cost gives), by a bitonic sort of (cost, row) keys.
-__global__ void __launch_bounds__(1024) k_est_order(const unsigned long long* __restrict__ per,
-                                                    const uint32_t* __restrict__ ssupp, uint32_t minsup_s,
-                                                    uint32_t intersections, uint32_t R, uint32_t P,
-                                                    unsigned long long* __restrict__ tally,
-                                                    uint32_t* __restrict__ order) {
-  extern __shared__ unsigned long long skey[];
-  uint32_t* srow = reinterpret_cast<uint32_t*>(skey + P);
-  // frequent sample rows before each of this thread's four rows (rows 4t .. 4t + 3)
-  uint32_t f[4], cnt = 0;
-#pragma unroll
-  for (uint32_t q = 0; q < 4; ++q) {
-    const uint32_t i = 4 * threadIdx.x + q;
-    f[q] = i < R && ssupp[i] >= minsup_s;
-    cnt += f[q];
+// The class costs of an estimate and their LPT order, on the device: one warp per row i of a sample mined
+// over all its R rows.  Row i is a class of the sample when ssupp[i] >= minsup_s; its cost is per[i] (the
+// sample's itemsets whose lowest row is i, or the DFS intersections below it) plus, for the intersection
+// measure, its level-2 candidates (the frequent sample rows after i); 0 for the other rows.  The order is the
+// rows by descending cost, ties by row (what a stable sort by cost gives): row i goes to position
+// rank(i) = #{j : cost_j > cost_i, or cost_j = cost_i and j < i}.  The warp recomputes the costs of all rows
+// (32 at a time, the frequent-row counts by ballot) instead of waiting for another kernel to store them.
+__global__ void k_est_order(const unsigned long long* __restrict__ per, const uint32_t* __restrict__ ssupp,
+                            uint32_t minsup_s, uint32_t intersections, uint32_t R,
+                            unsigned long long* __restrict__ tally, uint32_t* __restrict__ order) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= R) return;  // (whole warps leave together)
+  // frequent sample rows in all, and up to and including row i
+  uint32_t n_freq = 0, upto_i = 0;
+  for (uint32_t j0 = 0; j0 < R; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const uint32_t b = __ballot_sync(0xffffffffu, j < R && __ldg(ssupp + j) >= minsup_s);
+    n_freq += __popc(b);
+    if (j0 <= i) upto_i += __popc(i - j0 >= 31 ? b : b & ((2u << (i - j0)) - 1u));
   }
-  uint32_t n_freq = 0;
-  uint32_t before = cta_exclusive_scan(cnt, &n_freq);
-#pragma unroll
-  for (uint32_t q = 0; q < 4; ++q) {
-    const uint32_t i = 4 * threadIdx.x + q;
-    before += f[q];  // frequent rows up to and including i
-    if (i < R) {
-      const unsigned long long t = f[q] ? per[i] + (intersections ? (unsigned long long)(n_freq - before) : 0ull) : 0ull;
-      tally[i] = t;
-      skey[i] = t;
-      srow[i] = i;
-    }
+  const bool fi = __ldg(ssupp + i) >= minsup_s;
+  const unsigned long long ti = fi ? __ldg(per + i) + (intersections ? (unsigned long long)(n_freq - upto_i) : 0ull) : 0ull;
+  // rows before row i in the order
+  uint32_t rank = 0, upto = 0;
+  for (uint32_t j0 = 0; j0 < R; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const bool fj = j < R && __ldg(ssupp + j) >= minsup_s;
+    const uint32_t b = __ballot_sync(0xffffffffu, fj);
+    const uint32_t incl = upto + __popc(b & ((2u << lane) - 1u));  // frequent rows up to and including j
+    upto += __popc(b);
+    const unsigned long long tj = fj ? __ldg(per + j) + (intersections ? (unsigned long long)(n_freq - incl) : 0ull) : 0ull;
+    rank += __popc(__ballot_sync(0xffffffffu, j < R && (tj > ti || (tj == ti && j < i))));
   }
-  for (uint32_t i = R + threadIdx.x; i < P; i += blockDim.x) {  // padding: sorts after every row
-    skey[i] = 0ull;
-    srow[i] = 0xffffffffu;
+  if (lane == 0) {
+    tally[i] = ti;
+    order[rank] = i;
   }
-  __syncthreads();
-  // a before b: larger cost, or equal cost and smaller row
-  for (uint32_t k = 2; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-        const uint32_t l = i ^ j;
-        if (l > i) {
-          const unsigned long long ta = skey[i], tb = skey[l];
-          const uint32_t ra = srow[i], rb = srow[l];
-          const bool b_before_a = tb > ta || (tb == ta && rb < ra);
-          const bool a_before_b = ta > tb || (ta == tb && ra < rb);
-          if ((i & k) == 0 ? b_before_a : a_before_b) {
-            skey[i] = tb;
-            skey[l] = ta;
-            srow[i] = rb;
-            srow[l] = ra;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (uint32_t i = threadIdx.x; i < R; i += blockDim.x) order[i] = srow[i];
 }
 
 // The queue order of a mine's frequent rows r0 .. r0 + n1 - 1 from an estimate's order over all R rows:
@@ -322,9 +299,7 @@ cudaError_t launch_est_order(const unsigned long long* per, const uint32_t* ssup
                              cudaStream_t st) {
   if (R == 0) return cudaSuccess;
   if (R > kEstDeviceRows) return cudaErrorInvalidValue;
-  uint32_t P = 2;
-  while (P < R) P <<= 1;
-  k_est_order<<<1, 1024, (size_t)P * 12, st>>>(per, ssupp, minsup_s, intersections ? 1u : 0u, R, P, tally, order);
+  k_est_order<<<(R + 7) / 8, 256, 0, st>>>(per, ssupp, minsup_s, intersections ? 1u : 0u, R, tally, order);
   note_launch();
   return cudaGetLastError();
 }

@@ -420,7 +420,7 @@ cudaError_t launch_sample_build(const uint32_t* off, const uint32_t* items, uint
 cudaError_t launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 cudaError_t launch_row_popcount(const uint32_t* bits, uint32_t stride, uint32_t n_rows, uint32_t* supp,
                                 cudaStream_t st);
-// rows of a database whose estimate may stay on the device (one-CTA tally, sort and suffix kernels)
+// rows of a database whose estimate may stay on the device (the one-CTA suffix kernel)
 constexpr uint32_t kEstDeviceRows = 4096;
 // class costs (tally, R u64) and their LPT order (R u32) of a sample mined over all its R rows
 cudaError_t launch_est_order(const unsigned long long* per, const uint32_t* ssupp, uint32_t minsup_s,
