@@ -515,14 +515,19 @@ fim_status make_result(cudaStream_t st, const EngineOutput& eo, bool on_dev, fim
     if (e == cudaSuccess && eo.n_sets)
       e = cudaMemcpyAsync(res->d_supp, eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToDevice, st);
   } else {
-    res->h_off.resize(eo.n_sets + 1);
-    res->h_items.resize(eo.n_items);
-    res->h_supp.resize(eo.n_sets);
-    e = cudaMemcpyAsync(res->h_off.data(), eo.d_off, (eo.n_sets + 1) * 8, cudaMemcpyDeviceToHost, st);
+    // pinned host memory (pooled): the copies run at the link's rate instead of through staging buffers
+    const uint64_t b_off = (eo.n_sets + 1) * 8, b_items = (eo.n_items * 4 + 15) & ~15ull;
+    e = pinned_acquire(b_off + b_items + std::max<uint64_t>(1, eo.n_sets) * 4, &res->h_block, &res->h_cap);
+    if (e == cudaSuccess) {
+      res->h_off = static_cast<uint64_t*>(res->h_block);
+      res->h_items = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(res->h_block) + b_off);
+      res->h_supp = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(res->h_block) + b_off + b_items);
+      e = cudaMemcpyAsync(res->h_off, eo.d_off, b_off, cudaMemcpyDeviceToHost, st);
+    }
     if (e == cudaSuccess && eo.n_items)
-      e = cudaMemcpyAsync(res->h_items.data(), eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(res->h_items, eo.d_items, eo.n_items * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && eo.n_sets)
-      e = cudaMemcpyAsync(res->h_supp.data(), eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(res->h_supp, eo.d_supp, eo.n_sets * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
   if (e != cudaSuccess) {
@@ -978,9 +983,9 @@ fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64
     if (set_items) *set_items = res->d_items;
     if (supports) *supports = res->d_supp;
   } else {
-    if (set_offsets) *set_offsets = res->h_off.data();
-    if (set_items) *set_items = res->h_items.data();
-    if (supports) *supports = res->h_supp.data();
+    if (set_offsets) *set_offsets = res->h_off;
+    if (set_items) *set_items = res->h_items;
+    if (supports) *supports = res->h_supp;
   }
   return FIM_OK;
 }
@@ -988,6 +993,7 @@ fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64
 void fim_result_free(fim_result* res) {
   if (!res) return;
   if (res->d_off) cudaFreeAsync(res->d_off, res->stream);  // the block holding all three arrays
+  fim::pinned_release(res->h_block, res->h_cap);            // (host result: back to the pool)
   delete res;
 }
 

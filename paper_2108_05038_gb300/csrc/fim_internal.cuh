@@ -242,8 +242,12 @@ struct fim_result {
   uint64_t n_sets = 0;
   uint64_t n_items = 0;
   int on_device = 0;
-  std::vector<uint64_t> h_off;
-  std::vector<uint32_t> h_items, h_supp;
+  // host result: offsets | items | supports in one pinned block of the library's pool (returned on free)
+  uint64_t* h_off = nullptr;
+  uint32_t* h_items = nullptr;
+  uint32_t* h_supp = nullptr;
+  void* h_block = nullptr;
+  size_t h_cap = 0;
   uint64_t* d_off = nullptr;
   uint32_t* d_items = nullptr;
   uint32_t* d_supp = nullptr;

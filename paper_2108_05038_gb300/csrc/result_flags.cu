@@ -290,9 +290,9 @@ fim_status fim_result_flags(const fim_result* res, uint8_t* flags_out) {
     uint64_t* o = reinterpret_cast<uint64_t*>(base);
     uint32_t* it = reinterpret_cast<uint32_t*>(base + ((b_off + 15) & ~15ull));
     uint32_t* sp = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(it) + b_items);
-    FIM_CUDA(cudaMemcpyAsync(o, res->h_off.data(), b_off, cudaMemcpyHostToDevice, st));
-    if (n_items) FIM_CUDA(cudaMemcpyAsync(it, res->h_items.data(), n_items * 4, cudaMemcpyHostToDevice, st));
-    FIM_CUDA(cudaMemcpyAsync(sp, res->h_supp.data(), b_supp, cudaMemcpyHostToDevice, st));
+    FIM_CUDA(cudaMemcpyAsync(o, res->h_off, b_off, cudaMemcpyHostToDevice, st));
+    if (n_items) FIM_CUDA(cudaMemcpyAsync(it, res->h_items, n_items * 4, cudaMemcpyHostToDevice, st));
+    FIM_CUDA(cudaMemcpyAsync(sp, res->h_supp, b_supp, cudaMemcpyHostToDevice, st));
     d_off = o;
     d_items = it;
     d_supp = sp;

@@ -196,11 +196,32 @@ def _stream_handle(stream):
     return stream.cuda_stream  # torch.cuda.Stream
 
 
+class _HostResult:
+    """Owns the C result of a host result: its arrays are views of the result's pinned memory, which is
+    released (fim_result_free) only when the last of them, and the Result, are gone."""
+
+    def __init__(self, lib, handle):
+        self.lib, self.h = lib, handle
+
+    def view(self, ctype, addr, n):
+        buf = (ctype * n).from_address(addr)
+        buf._owner = self  # the buffer, and so every array made from it, keeps the result alive
+        return np.frombuffer(buf, dtype=np.dtype(ctype))
+
+    def __del__(self):
+        try:
+            self.lib.fim_result_free(self.h)
+        except Exception:
+            pass
+
+
 class Result:
-    """Frequent itemsets in CSR form; numpy arrays for host results."""
+    """Frequent itemsets in CSR form; numpy arrays for host results (views of the result's own pinned
+    host memory, valid for as long as they are referenced)."""
 
     def __init__(self, lib, handle, stats: MineStats | None):
         self._lib, self._h = lib, handle
+        self._owner = None
         self._flags = None
         n = ctypes.c_uint64()
         po, pi, ps = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
@@ -212,18 +233,13 @@ class Result:
         self.stats = stats.as_dict() if stats is not None else None
         self.device_ptrs = (po.value, pi.value, ps.value) if self.on_device else None
         if not self.on_device:
-            off = np.ctypeslib.as_array((ctypes.c_uint64 * (self.n_sets + 1)).from_address(po.value)).copy()
+            own = _HostResult(lib, handle)
+            off = own.view(ctypes.c_uint64, po.value, self.n_sets + 1)
             n_items = int(off[-1]) if self.n_sets else 0
-            if n_items:
-                items = np.ctypeslib.as_array((ctypes.c_uint32 * n_items).from_address(pi.value)).copy()
-            else:
-                items = np.zeros(0, dtype=np.uint32)
-            if self.n_sets:
-                supp = np.ctypeslib.as_array((ctypes.c_uint32 * self.n_sets).from_address(ps.value)).copy()
-            else:
-                supp = np.zeros(0, dtype=np.uint32)
+            items = own.view(ctypes.c_uint32, pi.value, n_items) if n_items else np.zeros(0, dtype=np.uint32)
+            supp = own.view(ctypes.c_uint32, ps.value, self.n_sets) if self.n_sets else np.zeros(0, dtype=np.uint32)
             self.set_offsets, self.set_items, self.supports = off, items, supp
-            # the handle stays until free() (or collection): fim_result_flags reads it
+            self._owner = own  # fim_result_flags reads the handle until free() (or collection)
 
     def flags(self) -> np.ndarray:
         """fim_result_flags: u8 per itemset (record order), bit 0 closed, bit 1 maximal (computed once)."""
@@ -236,8 +252,12 @@ class Result:
         return self._flags
 
     def free(self):
+        """Device result: freed now.  Host result: the Result lets go of it; its memory is released once no
+        array of it is referenced any more."""
         if self._h:
-            self._lib.fim_result_free(self._h)
+            if self._owner is None:
+                self._lib.fim_result_free(self._h)
+            self._owner = None
             self._h = None
 
     def __del__(self):
