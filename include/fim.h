@@ -121,8 +121,9 @@ typedef struct {
                                   words when it has at most 2,048 of them (small CTAs, several per
                                   SM), dense in its stack slot otherwise; rows of at most 65,535
                                   16-byte words, no donation (else as NODES); FIM_DFS_AUTO (2, the
-                                  default): projected with at least 1,024 frequent rows, else
-                                  frames for rows of at most 16,384 words (64 KB), else SPARSE;
+                                  default): projected with at least 1,024 frequent rows (and no
+                                  cap on the CTAs per SM), else frames for rows of at most 16,384
+                                  words (64 KB), else SPARSE;
                                   FIM_DFS_WARP (4): one warp
                                   per two-item class, the
                                   prefix in its registers, no CTA-wide barrier; rows of at most 512
@@ -250,7 +251,9 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
  * cost_out[r] = |{X in F_s : the lowest row of X is r}| / |F_s| (0 when F_s is
  * empty).  While D_s has more than FIM_SAMPLE_ITEMSET_LIMIT frequent itemsets
  * at minsup_s, minsup_s doubles (the thesis does not treat a sample whose
- * itemsets explode; this keeps the estimate's cost bounded).  order_out = rows by descending cost, ties by ascending row (the
+ * itemsets explode; this keeps the estimate's cost bounded: the count-only
+ * mine of a sample stops once it passes the limit, so an exploding sample
+ * costs about limit itemsets per doubling).  order_out = rows by descending cost, ties by ascending row (the
  * LPT order, Sec. 8.2).  Both arrays have n_rows entries (host memory).
  * The estimate is kept in the db and orders the classes of later fim_mine
  * calls (FIM_ORDER_ESTIMATE); it never changes their output.

@@ -44,7 +44,10 @@ fim_status engine_prepare(fim_db* db, Workspace& ws, const EngineInput& in, cons
   // passes, which spread one frame over a whole CTA: sparse_mid (988 rows of 3,136 words) 0.021 ms against
   // 0.064 projected, 0.027 in sparse nodes and 0.033 in dense node expansion; at 300,000 transactions
   // (9,376 words) 0.033 against 0.084 projected; rows past 16,384 words take the sparse node mode.
-  const bool auto_proj = cfg.mode == 2 && list_ok && !cfg.donate && n1 >= 1024;
+  // A capped CTA count (the server's concurrent jobs) turns the projection's hand-out of large frames off,
+  // and without it every class's whole subtree runs on one warp (the tail the hand-out removes), so such
+  // mines keep the traversals that spread a class over a CTA.
+  const bool auto_proj = cfg.mode == 2 && list_ok && !cfg.donate && n1 >= 1024 && cfg.ctas_per_sm == 0;
   if (cfg.mode == 2)
     ep->mode = auto_proj ? 3u : (in.stride <= 16384 ? 1u : (list_ok && !cfg.donate ? 3u : 0u));
   else if (cfg.mode == 3 || cfg.mode == 5) ep->mode = list_ok && !cfg.donate ? 3u : 0u;

@@ -457,8 +457,8 @@ fim_status mine_input(fim_db* db, uint32_t minsup_abs, const fim_mine_opts* opts
   in->row_order.reserve(in->n1);
   if (!defer_ok || order != FIM_ORDER_ESTIMATE) {  // the host copies of a deferred estimate are needed now
     FIM_TRY(est_resolve(db));
-    FIM_TRY(est_redo(db));
   }
+  if (order == FIM_ORDER_ESTIMATE) FIM_TRY(est_redo(db));  // an incomplete deferred sample, found by an earlier mine
   if (order == FIM_ORDER_ESTIMATE && db->has_estimate && db->est_pending && in->n1) {
     // the deferred estimate's order, restricted to this minsup's rows on the device
     uint32_t* d = nullptr;
@@ -627,7 +627,7 @@ fim_status fim_estimate_class_costs_ex(fim_db* db, double sample_rate, double re
                                        uint32_t cost_kind, uint64_t max_sample_itemsets, double* cost_out,
                                        uint32_t* order_out) {
   return fim::estimate_impl(db, sample_rate, rel_minsup, seed, cost_kind, max_sample_itemsets, cost_out, order_out,
-                            true);
+                            true, 0);
 }
 
 }  // extern "C"
@@ -641,7 +641,8 @@ namespace fim {
 // caller needs them (fim_mine only after its pair kernel is on its way).  A deferred sample that ran into
 // the itemset limit (or needed a retry) is mined again by the synchronous path after the mine that used it.
 fim_status estimate_impl(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed, uint32_t cost_kind,
-                         uint64_t max_sample_itemsets, double* cost_out, uint32_t* order_out, bool allow_defer) {
+                         uint64_t max_sample_itemsets, double* cost_out, uint32_t* order_out, bool allow_defer,
+                         uint32_t first_minsup_s) {
   if (!db) return fail(FIM_ERR_INVALID, "db is NULL");
   if (cost_kind != FIM_COST_ITEMSETS && cost_kind != FIM_COST_INTERSECTIONS)
     return fail(FIM_ERR_INVALID, "unknown cost kind");
@@ -655,6 +656,8 @@ fim_status estimate_impl(fim_db* db, double sample_rate, double rel_minsup, uint
   const uint32_t m = md < 1.0 ? 1u : (uint32_t)md;
   const double msd = std::ceil(rel_minsup * (double)m);
   uint32_t minsup_s = msd < 1.0 ? 1u : (uint32_t)msd;
+  // (a redo of a deferred sample that passed the itemset limit starts where the doubling continues)
+  if (first_minsup_s > minsup_s) minsup_s = first_minsup_s;
   const uint32_t sw = (m + 31) / 32, sstride = ((sw + 31) / 32) * 32;
   const uint32_t R = db->n_rows;
   uint32_t *d_sbits = nullptr, *d_ssupp = nullptr;
@@ -868,17 +871,22 @@ fim_status est_resolve(fim_db* db) {
   db->est_cost.assign(R, 0.0);
   for (uint32_t r = 0; r < R; ++r) db->est_cost[r] = total ? (double)tally[r] / (double)total : 0.0;
   db->est_nfs = h.sets_total;
-  db->est_redo = (h.err & (DEV_ERR_TIMEOUT | DEV_ERR_ABORTED | DEV_ERR_PSTACK | DEV_ERR_DEPTH)) != 0 ||
-                 (db->est_limit && h.sets_total > db->est_limit);
+  const bool over = (h.err & DEV_ERR_ABORTED) || (db->est_limit && h.sets_total > db->est_limit);
+  db->est_redo = over || (h.err & (DEV_ERR_TIMEOUT | DEV_ERR_PSTACK | DEV_ERR_DEPTH)) != 0;
+  // past the itemset limit: the synchronous path continues the doubling from twice this minsup (and until
+  // then the first output capacity is bounded by the limit, as after a doubling)
+  db->est_redo_minsup = over ? (db->est_minsup > UINT32_MAX / 2 ? UINT32_MAX : 2 * db->est_minsup) : 0u;
+  db->est_doubled = over;
   return FIM_OK;
 }
 
-// The synchronous estimate of a deferred one that est_resolve found incomplete.
+// The synchronous estimate of a deferred one that est_resolve found incomplete.  It runs when a later mine
+// or query needs the estimate (not at the end of the mine that found it: a served job mines once).
 fim_status est_redo(fim_db* db) {
   if (!db->est_redo) return FIM_OK;
   db->est_redo = false;
   const auto a = db->est_args;
-  return estimate_impl(db, a.rate, a.rel, a.seed, a.kind, a.limit, nullptr, nullptr, false);
+  return estimate_impl(db, a.rate, a.rel, a.seed, a.kind, a.limit, nullptr, nullptr, false, db->est_redo_minsup);
 }
 
 }  // namespace fim
@@ -962,15 +970,7 @@ fim_status fim_mine(fim_db* db, uint32_t minsup_abs, fim_mine_opts* opts, fim_re
       for (uint32_t i = 0; i < in.n1; ++i) work_out[r0 + i] = w[i] + (in.n1 - 1 - i);
     }
   }
-  FIM_TRY(make_result(db->stream, eo, opts && opts->struct_size && opts->result_on_device, out));
-  // a deferred estimate that this mine found incomplete: the synchronous estimate now (after the result's
-  // copies in stream order), for the later mines and queries of the database
-  const fim_status r = est_redo(db);
-  if (r != FIM_OK) {
-    fim_result_free(*out);
-    *out = nullptr;
-  }
-  return r;
+  return make_result(db->stream, eo, opts && opts->struct_size && opts->result_on_device, out);
 }
 
 fim_status fim_result_view(const fim_result* res, uint64_t* n_sets, const uint64_t** set_offsets,

@@ -218,6 +218,7 @@ struct fim_db {
   // the sample's control block, costs and order copied to est_pin behind est_done; est_pending until read
   bool est_pending = false;
   bool est_redo = false;  // the deferred sample needs the synchronous path (itemset limit or a retry)
+  uint32_t est_redo_minsup = 0;  // the sample minsup that redo starts at (0: the estimate's own)
   cudaEvent_t est_done = nullptr;
   void* est_pin = nullptr;
   size_t est_pin_cap = 0;
@@ -390,7 +391,8 @@ fim_status mine_input(fim_db* db, uint32_t minsup, const fim_mine_opts* opts, En
 uint64_t estimate_capacity(const fim_db* db, uint32_t minsup);
 // fim_estimate_class_costs_ex, allowed to leave its result on the device (see fim_api.cu)
 fim_status estimate_impl(fim_db* db, double sample_rate, double rel_minsup, uint64_t seed, uint32_t cost_kind,
-                         uint64_t max_sample_itemsets, double* cost_out, uint32_t* order_out, bool allow_defer);
+                         uint64_t max_sample_itemsets, double* cost_out, uint32_t* order_out, bool allow_defer,
+                         uint32_t first_minsup_s);
 // a deferred estimate read into the database's host copies (no-op when none is pending)
 fim_status est_resolve(fim_db* db);
 // the synchronous estimate that a deferred one found incomplete asks for (no-op otherwise)
