@@ -41,7 +41,19 @@ L2_FLUSH_BYTES = 512 << 20
 # profiles/ gives the command and the per-kernel figures): per launch of the pair step and of the DFS
 # stage, and for the whole step (build, estimate, mine).  A record is used only while the CUDA sources
 # hash to the SHA-256 it was captured with; otherwise the line reports no traffic and says why.
-CAPTURES = {}
+# DRAM bytes (read + written) of one `bench.py --workload <w> --mode once` process's launches, from the ncu
+# launch lists summarised in profiles/ (one-pass metrics gpu__time_duration, dram__bytes_read/write); a
+# record applies only while the CUDA sources hash to the value it was captured with.  "pair": the mine's
+# pair kernel; "dfs": the mine's DFS stage (projection + DFS + fallback, or the one DFS launch); "step": the
+# build, estimate and mine launches (the closed/maximal flags pass of --mode once excluded).
+CAPTURES = {
+    "large_sparse": {"sources_sha256": "1fc47c1a3c5b602730715d976cb9892090f7a70bc3949463cfab159a675f45b2",
+                     "date": "2026-12-03", "summary": "profiles/launches_large_sparse.md",
+                     "kernels": {"pair": 701891072, "dfs": 1015687424}, "step": 2680594432},
+    "sparse_mid": {"sources_sha256": "1fc47c1a3c5b602730715d976cb9892090f7a70bc3949463cfab159a675f45b2",
+                   "date": "2026-12-03", "summary": "profiles/launches_sparse_mid.md",
+                   "kernels": {"pair": 14436864, "dfs": 4326400}, "step": 48653056},
+}
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 
 
