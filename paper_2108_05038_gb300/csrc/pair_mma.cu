@@ -425,8 +425,13 @@ constexpr uint32_t kFChunk = 16;                     // columns read back per ro
 constexpr uint32_t kFPitch = kFChunk + 1;            // staging rows (words): conflict-free transposition
 constexpr uint32_t kFStagingBytes = 4 * 32 * kFPitch * 4;
 constexpr uint32_t kTwoE4M3 = 0x40u;                // 2.0: exponent 8 (bias 7), mantissa 0
-// rfull[], rempty[], ofull[], oempty[], acc_full, acc_empty, fin, TMEM address
-constexpr uint32_t kFBarBytes = 8 * (2 * kRStages + 2 * kFStages + 3) + 8;
+// rfull[], rempty[], ofull[], oempty[], acc_full, acc_empty, fin, acc_last, TMEM address
+constexpr uint32_t kFBarBytes = 8 * (2 * kRStages + 2 * kFStages + 4) + 8;
+// the read-back of a CTA's last tile is shared by the read-back warp of each TMEM lane quarter and the six
+// expander warps of the same quarter (their slices done, the operand stages free for their staging)
+constexpr uint32_t kLastWorkers = 1 + kExpThreads / 32 / 4;
+static_assert(kExpThreads / 32 % 4 == 0 && kExpThreads / 32 * 32 * kFPitch * 4 <= kFStageBytes,
+              "expander warps cover the four quarters evenly; their staging fits one operand stage");
 constexpr size_t kFSmemBytes =
     1024 + (size_t)kFStages * kFStageBytes + (size_t)kRStages * kRawStageBytes + kFStagingBytes + kFBarBytes;
 static_assert(kFSmemBytes <= 227u * 1024u, "shared memory per CTA");
@@ -468,7 +473,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   const uint32_t acc_full = bars + 8 * (2 * kRStages + 2 * kFStages);
   const uint32_t acc_empty = acc_full + 8;
   const uint32_t fin = acc_full + 16;
-  const uint32_t tslot = fin + 8;
+  const uint32_t acc_last = fin + 8;  // the last tile's MMAs done (single use: expander warps wait on it)
+  const uint32_t tslot = acc_last + 8;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile uint32_t* abort_flag = &s_abort;
   auto abort_now = [&]() {
@@ -488,6 +494,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     mbar_init(acc_full, 1);   // the MMA commit after an item's last slice
     mbar_init(acc_empty, 4);  // one arrive per read-back warp
     mbar_init(fin, 1);
+    mbar_init(acc_last, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -515,6 +522,30 @@ __global__ void __launch_bounds__(kFThreads, 1)
     bj = bi + t;
     k0 = split * steps_per_item;
     ns = min(nsteps, k0 + steps_per_item) - k0;
+  };
+
+  // read-back round rd (0-31) of tile (bi, bj) by one warp for TMEM lane quarter `quarter`: half rd / 16, 16
+  // columns from (rd mod 16) x 16, through the warp's staging area sw (32 x kFPitch words)
+  auto readback_round = [&](uint32_t rd, uint32_t* sw, uint32_t bi, uint32_t bj, uint32_t quarter) {
+    const uint32_t h = rd / (kFN / kFChunk), c0 = (rd % (kFN / kFChunk)) * kFChunk;
+    const uint32_t row0 = bi * kFM + h * kBM + quarter * 32;
+    uint32_t r[16];
+    tmem_ld16(tmem + ((quarter * 32u) << 16) + h * kBN + c0, r);
+#pragma unroll
+    for (uint32_t c = 0; c < 16; ++c)
+      sw[lane * kFPitch + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);  // exact: a power of 2
+    __syncwarp();
+    const uint32_t j = bj * kFN + c0 + (lane & 15u);
+#pragma unroll 4
+    for (uint32_t rr = 0; rr < 16; ++rr) {
+      const uint32_t rl = rr + (lane >> 4) * 16u, i = row0 + rl;
+      if (i < j && j < n1) {  // i < j < n1 also bounds i
+        const uint32_t v = sw[rl * kFPitch + (lane & 15u)];
+        if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
+        else C2[(size_t)i * n1 + j] = v;
+      }
+    }
+    __syncwarp();
   };
 
   uint32_t issued = 0;
@@ -581,13 +612,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
           break;
         }
         mma_commit(acc_full);
+        if (item + gridDim.x >= n_items) mma_commit(acc_last);  // the CTA's last tile
         mma_open = false;
       }
     }
     __syncwarp();
   } else if (warp < 6) {
     // read-back: TMEM lanes -> staging (transposed) -> 64-byte row segments of C2, for both halves; rounds of
-    // 16 columns, lanes 0-15 and 16-31 writing rows rr and rr + 16
+    // 16 columns, lanes 0-15 and 16-31 writing rows rr and rr + 16; the last tile's 32 rounds are shared with
+    // the expander warps of the same quarter (this warp takes every kLastWorkers-th)
     const uint32_t quarter = warp & 3;
     uint32_t* sw = staging + (warp - 2) * 32 * kFPitch;
     uint32_t it = 0;
@@ -600,31 +633,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
         break;
       }
       tc_fence_after();
+      const uint32_t step = item + gridDim.x >= n_items ? kLastWorkers : 1u;
 #pragma unroll 1
-      for (uint32_t h = 0; h < 2; ++h) {
-        const uint32_t row0 = bi * kFM + h * kBM + quarter * 32;
-        const uint32_t taddr = tmem + ((quarter * 32u) << 16) + h * kBN;
-#pragma unroll 1
-        for (uint32_t c0 = 0; c0 < kFN; c0 += kFChunk) {
-          uint32_t r[16];
-          tmem_ld16(taddr + c0, r);
-#pragma unroll
-          for (uint32_t c = 0; c < 16; ++c)
-            sw[lane * kFPitch + c] = __float2uint_rn(__uint_as_float(r[c]) * 0.25f);  // exact: a power of 2
-          __syncwarp();
-          const uint32_t j = bj * kFN + c0 + (lane & 15u);
-#pragma unroll 4
-          for (uint32_t rr = 0; rr < 16; ++rr) {
-            const uint32_t rl = rr + (lane >> 4) * 16u, i = row0 + rl;
-            if (i < j && j < n1) {  // i < j < n1 also bounds i
-              const uint32_t v = sw[rl * kFPitch + (lane & 15u)];
-              if (ksplit > 1) atomicAdd(&C2[(size_t)i * n1 + j], v);
-              else C2[(size_t)i * n1 + j] = v;
-            }
-          }
-          __syncwarp();
-        }
-      }
+      for (uint32_t rd = 0; rd < 2 * kFN / kFChunk; rd += step) readback_round(rd, sw, bi, bj, quarter);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
@@ -676,6 +687,24 @@ __global__ void __launch_bounds__(kFThreads, 1)
           mbar_arrive(ofull(os));
           mbar_arrive(rempty(rs));
         }
+      }
+    }
+    // the last tile's read-back, shared with the read-back warp of this warp's quarter once its MMAs are
+    // done (acc_last: every MMA has read its operand stage, so stage 0 holds the staging areas)
+    if (ok && !*abort_flag) {
+      const bool done = __all_sync(0xffffffffu, mbar_wait(acc_last, 0));
+      if (done && !*abort_flag) {
+        tc_fence_after();
+        const uint32_t last = blockIdx.x + (n_items - 1 - blockIdx.x) / gridDim.x * gridDim.x;
+        uint32_t bi, bj, k0, ns;
+        decode(last, bi, bj, k0, ns);
+        const uint32_t ew = warp - kThreads / 32;  // expander warp 0-23
+        uint32_t* sw = reinterpret_cast<uint32_t*>(smem_raw + (op_st - raw)) + ew * 32 * kFPitch;
+        for (uint32_t rd = 1 + ew / 4; rd < 2 * kFN / kFChunk; rd += kLastWorkers)
+          readback_round(rd, sw, bi, bj, warp & 3);
+        tc_fence_before();
+      } else if (!done && lane == 0) {
+        abort_now();
       }
     }
   }
