@@ -47,12 +47,12 @@ L2_FLUSH_BYTES = 512 << 20
 # pair kernel; "dfs": the mine's DFS stage (projection + DFS + fallback, or the one DFS launch); "step": the
 # build, estimate and mine launches (the closed/maximal flags pass of --mode once excluded).
 CAPTURES = {
-    "large_sparse": {"sources_sha256": "1fc47c1a3c5b602730715d976cb9892090f7a70bc3949463cfab159a675f45b2",
+    "large_sparse": {"sources_sha256": "02f67a4529354026b95fcd919e5fa8b9eccb0d0609afcbe08883fa65a753ba40",
                      "date": "2026-12-03", "summary": "profiles/launches_large_sparse.md",
-                     "kernels": {"pair": 701891072, "dfs": 1015687424}, "step": 2680594432},
-    "sparse_mid": {"sources_sha256": "1fc47c1a3c5b602730715d976cb9892090f7a70bc3949463cfab159a675f45b2",
+                     "kernels": {"pair": 699948800, "dfs": 1013662720}, "step": 2677619712},
+    "sparse_mid": {"sources_sha256": "02f67a4529354026b95fcd919e5fa8b9eccb0d0609afcbe08883fa65a753ba40",
                    "date": "2026-12-03", "summary": "profiles/launches_sparse_mid.md",
-                   "kernels": {"pair": 14436864, "dfs": 4326400}, "step": 48653056},
+                   "kernels": {"pair": 14441984, "dfs": 4326144}, "step": 48668672},
 }
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 
@@ -875,8 +875,8 @@ def main():
                          "build + mine (profiler captures); stream: the counting step alone over 4 GiB of "
                          "bitmap rows")
     ap.add_argument("--requests", type=int, default=2000)
-    ap.add_argument("--serve-requests", type=int, default=200,
-                    help="requests of the serving leg of the default run (the first ones of the serving workload)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving leg of the default run (config 4 in full: about 100 s per arm)")
     ap.add_argument("--no-legs", action="store_true", help="default run: skip the plan and serving legs")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--slots", type=int, default=4)
