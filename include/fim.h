@@ -263,8 +263,10 @@ fim_status fim_db_rows(const fim_db* db, uint32_t* rank_item, uint32_t* supports
  * its per-class counts and the LPT order stay on the device (a one-CTA sort),
  * and the next fim_mine takes its class order from there and reads the
  * sample's itemset count (its first output capacity) only after launching its
- * pair kernel.  A sample that passed the itemset limit is then mined again by
- * the synchronous path after that mine (whose output is the same either way).
+ * pair kernel.  A sample that passed the itemset limit orders that mine by its
+ * partial counts (the output is the same for every order), and is mined again
+ * by the synchronous path, from the doubled sample minsup, when a later mine
+ * or query of the estimate needs it.
  * Errors of such a deferred estimate are reported by the call that reads it
  * (fim_mine, fim_estimate_result, fim_estimate_sample_size).
  * Errors: FIM_ERR_INVALID (sample_rate not in (0,1], rel_minsup not in
