@@ -573,3 +573,27 @@ def test_warp_dfs_falls_back_on_wide_rows():
     ms = 75
     want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], ms))
     assert_same(gpu_mine(w["offsets"], w["items"], w["N"], ms, dfs_mode=4).as_dict(), want)
+
+
+def test_host_result_arrays_outlive_the_result():
+    """A host result's arrays view the result's own pinned memory: they stay valid after Result.free() and
+    after the Result object is gone (the memory goes back to the pool only when the last array does), and
+    results made meanwhile reuse pooled blocks without touching them."""
+    import gc
+
+    w = synth.make_workload("tiny", D=6000)
+    want = odict(oracle.eclat(w["offsets"], w["items"], w["N"], 60))
+    db = fim.build_vertical_db(w["offsets"], w["items"], w["N"])
+    res = db.mine(60)
+    off, items, supp = res.set_offsets, res.set_items, res.supports
+    res.free()
+    del res
+    gc.collect()
+    for _ in range(3):  # more results while the arrays above are alive
+        other = db.mine(90)
+        assert other.n_sets < len(want)
+        del other
+        gc.collect()
+    got = {tuple(int(v) for v in items[off[k]:off[k + 1]]): int(supp[k]) for k in range(len(supp))}
+    assert got == want
+    db.free()
