@@ -47,12 +47,12 @@ L2_FLUSH_BYTES = 512 << 20
 # pair kernel; "dfs": the mine's DFS stage (projection + DFS + fallback, or the one DFS launch); "step": the
 # build, estimate and mine launches (the closed/maximal flags pass of --mode once excluded).
 CAPTURES = {
-    "large_sparse": {"sources_sha256": "1f38089f610e9b0c31190abdc211f788bc9f594f7bfbd02e7586a684a0105753",
+    "large_sparse": {"sources_sha256": "1bc65d4d04f2e31da824a427c53561cbbbe8c516b750cf8d0d036c5981cb197d",
                      "date": "2026-12-03", "summary": "profiles/launches_large_sparse.md",
-                     "kernels": {"pair": 694163712, "dfs": 1013348352}, "step": 2671792640},
-    "sparse_mid": {"sources_sha256": "1f38089f610e9b0c31190abdc211f788bc9f594f7bfbd02e7586a684a0105753",
+                     "kernels": {"pair": 784721664, "dfs": 1013350400}, "step": 2764478464},
+    "sparse_mid": {"sources_sha256": "1bc65d4d04f2e31da824a427c53561cbbbe8c516b750cf8d0d036c5981cb197d",
                    "date": "2026-12-03", "summary": "profiles/launches_sparse_mid.md",
-                   "kernels": {"pair": 14442240, "dfs": 4327168}, "step": 48660224},
+                   "kernels": {"pair": 14442496, "dfs": 4329984}, "step": 48665088},
 }
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 

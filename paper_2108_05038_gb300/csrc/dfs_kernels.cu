@@ -282,6 +282,20 @@ enum : uint32_t { CAND_FROW = 0, CAND_PAIR = 1, CAND_PAIR_RING = 2 };
 
 __device__ __forceinline__ bool any4(const uint4& v) { return (v.x | v.y | v.z | v.w) != 0u; }
 
+// Whether a traversal unwinds: a flagged abort, or (a count-only mine, which reserves no record positions and
+// so checks its itemset limit here instead of at every node) a running total past the limit or the 32-bit
+// record range, which is flagged here.  Both words are loaded before either is looked at.
+__device__ __forceinline__ bool traversal_stopped(const DfsLaunch& p) {
+  const unsigned long long t = p.out_off ? 0ull : *(volatile const unsigned long long*)&p.ctrl->sets_total;
+  const uint32_t e = *(volatile const uint32_t*)&p.ctrl->err;
+  if (e & DEV_ERR_ABORTED) return true;
+  if ((p.max_sets && t > p.max_sets) || t > 0xfffffff0ull) {
+    atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+    return true;
+  }
+  return false;
+}
+
 // Sparse skipping: a prefix bitmap of support s over D transactions has at most
 // s nonzero words, so wherever its 16 bytes are zero the candidate row is not
 // read at all (its AND is zero there).  Prefixes deep in the DFS are much
@@ -451,12 +465,14 @@ __device__ __forceinline__ uint32_t process_node(const DfsArgs& A, Ctl& C, uint3
       const uint32_t pos = block_flag_scan(f, wtot, &tot);
       if (threadIdx.x == 0 && tot && !p.leaves) {
         const unsigned long long sets = tot, items = (unsigned long long)tot * (xlen + 1);
-        C.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+        if (p.out_off) {  // record positions (a count-only mine checks the itemset limit at its polls)
+          C.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+          const unsigned long long after = (C.base >> 32) + sets;
+          if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+        }
         atomicAdd(&p.ctrl->sets_total, sets);
         atomicAdd(&p.ctrl->items_total, items);
         atomicMax(&p.ctrl->max_len, xlen + 1);
-        const unsigned long long after = (C.base >> 32) + sets;
-        if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
         if (p.class_sets) atomicAdd(&p.class_sets[C.cls], sets);
       }
       __syncthreads();
@@ -806,7 +822,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs(const DfsArgs A) {
       __syncthreads();  // every thread has read the previous decision
       if (threadIdx.x == 0) {
         // a run past the itemset limit unwinds at once (every 8th node looks at the flag)
-        if (C.depth >= 0 && (++poll & 7) == 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
+        if (C.depth >= 0 && (++poll & 7) == 0 && traversal_stopped(p)) C.depth = -1;
         const int32_t d = C.depth;
         C.action = 0;
         if (d < 0) {
@@ -1204,7 +1220,7 @@ __global__ void __launch_bounds__(256, 3) k_dfs_sparse(const DfsArgs A) {
     // finish the class; every thread has read the previous step when thread 0 runs this
     uint32_t poll = 0;
     auto decide = [&]() {
-      if (C.depth >= 0 && (++poll & 7) == 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
+      if (C.depth >= 0 && (++poll & 7) == 0 && traversal_stopped(p)) C.depth = -1;
       const int32_t d = C.depth;
       if (d < 0) {
         C.action = 4;
@@ -1437,7 +1453,7 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
     for (;;) {
       __syncthreads();
       if (threadIdx.x == 0) {
-        if (C.depth >= 0 && (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED)) C.depth = -1;
+        if (C.depth >= 0 && traversal_stopped(p)) C.depth = -1;
         const int32_t d = C.depth;
         if (d < 0) {
           F.action = 4;
@@ -1568,12 +1584,14 @@ __global__ void __launch_bounds__(512, 1) k_dfs_frames(const DfsArgs A) {
         const uint32_t pos = block_flag_scan(f, wtot, &tot);
         if (threadIdx.x == 0 && tot) {
           const unsigned long long sets = tot, items = (unsigned long long)tot * (xl + 2);
-          F.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+          if (p.out_off) {  // record positions (a count-only mine checks the itemset limit at its polls)
+            F.base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+            const unsigned long long after = (F.base >> 32) + sets;
+            if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+          }
           atomicAdd(&p.ctrl->sets_total, sets);
           atomicAdd(&p.ctrl->items_total, items);
           atomicMax(&p.ctrl->max_len, xl + 2);
-          const unsigned long long after = (F.base >> 32) + sets;
-          if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
           if (p.class_sets) atomicAdd(&p.class_sets[C.cls], sets);
         }
         __syncthreads();
@@ -1742,14 +1760,16 @@ __global__ void __launch_bounds__(kWarpDfsThreads) k_dfs_warp(const DfsArgs A) {
     unsigned long long base = 0;
     if (lane == 0) {
       const unsigned long long sets = nout, items = (unsigned long long)nout * (xlen + 1);
-      base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+      if (p.out_off) {  // record positions (a count-only mine checks the itemset limit at its polls)
+        base = atomicAdd(&p.ctrl->packed, (sets << 32) | items);
+        const unsigned long long after = (base >> 32) + sets;
+        if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+      }
       atomicAdd(&p.ctrl->sets_total, sets);
       atomicAdd(&p.ctrl->items_total, items);
       atomicMax(&p.ctrl->max_len, xlen + 1);
-      const unsigned long long after = (base >> 32) + sets;
-      if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
     }
-    base = __shfl_sync(0xffffffffu, base, 0);
+    if (p.out_off) base = __shfl_sync(0xffffffffu, base, 0);
     cls_sets += nout;
     if (p.out_off) {
       for (uint32_t o = 0; o < nout; ++o) {
@@ -1836,7 +1856,9 @@ __global__ void __launch_bounds__(kWarpDfsThreads) k_dfs_warp(const DfsArgs A) {
       }
       if (++since_poll == 8) {
         since_poll = 0;
-        if (*(volatile uint32_t*)&p.ctrl->err & DEV_ERR_ABORTED) break;
+        uint32_t stop = 0;
+        if (lane == 0) stop = traversal_stopped(p);
+        if (__shfl_sync(0xffffffffu, stop, 0)) break;
       }
       __syncwarp();
       if (lane == 0) f_cur[depth] = k + 1;

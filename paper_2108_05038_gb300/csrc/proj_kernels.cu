@@ -357,6 +357,9 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
   // handed-out frame one gathered word per (survivor, transaction) and the region written
   unsigned long long st_bytes = 0;
   unsigned long long st_sets = 0, st_items = 0;
+  // count only (no records): itemsets not yet added to the reservation word, which then feeds nothing but the
+  // itemset limit; added every 8 nodes and at the end of an item instead of one returning atomic per node
+  unsigned long long pend_sets = 0;
   uint32_t st_maxlen = 0;
   bool static_done = false;
   constexpr uint32_t kStop = DEV_ERR_ABORTED | DEV_ERR_PSTACK | DEV_ERR_TIMEOUT;
@@ -482,6 +485,14 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
         return;
       }
       if (nout == 0) return;
+      if (!p.out_off) {  // count only: nothing to reserve
+        pend_sets += nout;
+        st_sets += nout;
+        st_items += (unsigned long long)nout * (xlen + 1);
+        st_maxlen = max(st_maxlen, xlen + 1);
+        cls_sets += nout;
+        return;
+      }
       unsigned long long base = 0;
       // one atomic per node reserves its records; the exact totals and the longest length are added once per
       // warp at the end (nothing reads them while the kernel runs)
@@ -733,7 +744,20 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       first = false;
       if (++since_poll == 8) {
         since_poll = 0;
-        if (ld_volatile(&p.ctrl->err) & kStop) break;
+        uint32_t stop = 0;
+        if (lane == 0) {
+          const uint32_t e = ld_volatile(&p.ctrl->err);  // (in flight with the add below)
+          if (pend_sets) {
+            const unsigned long long after = (atomicAdd(&p.ctrl->packed, pend_sets << 32) >> 32) + pend_sets;
+            if ((p.max_sets && after > p.max_sets) || after > 0xfffffff0ull) {
+              atomicOr(&p.ctrl->err, DEV_ERR_ABORTED);
+              stop = 1;
+            }
+          }
+          stop |= e & kStop;
+        }
+        pend_sets = 0;
+        if (__shfl_sync(kFull, stop, 0)) break;
       }
       __syncwarp();
       if (lane == 0) fr_cur[depth] = kk + 1;
@@ -982,11 +1006,13 @@ __global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_dfs_proj(const
       atomicOr(&p.ctrl->err, DEV_ERR_PSTACK);
     }
     if (lane == 0) {
+      if (pend_sets) atomicAdd(&p.ctrl->packed, pend_sets << 32);  // (read at the next acquire)
       if (p.class_sets && cls_sets) atomicAdd(&p.class_sets[cls], cls_sets);
       if (p.class_work && cls_work) atomicAdd(&p.class_work[cls], cls_work);
       __threadfence();  // the item's records and published children before its completion
       atomicSub(&p.ctrl->proj_pending, 1u);
     }
+    pend_sets = 0;
   }
   if (lane == 0) {
     atomicAdd(&p.ctrl->n_intersections, st_inter);

@@ -112,3 +112,41 @@ def test_replaced_estimate_uniform_mine_and_plan():
         res.free()
     finally:
         db.free()
+
+
+# Samples with more than 1,024 frequent rows: the automatic DFS mines them with the projected DFS (and the
+# sparse node mode for the classes left out), whose count-only mines check the itemset limit at their polls.
+# (12,000 x 1,400: 1,079 of the 1,400 rows predicted frequent in the 6,000-transaction sample, so the sample is
+# mined over all rows; start minsup 9 gives 26,822 itemsets, past a limit of 20,000: 18 gives 10,538.
+# 20,000 x 1,500 at rate 1/4: 73% predicted, so the sample is mined over its frequent rows; 11,480 itemsets at
+# minsup 10, past 5,000: 3,476 at 20.)
+PROJ_CASES = [(12000, 1400, 12.0, 0.5, 0.0015, 0, 0, False), (12000, 1400, 12.0, 0.5, 0.0015, 20000, 0, False),
+              (12000, 1400, 12.0, 0.5, 0.0015, 20000, 1, True), (20000, 1500, 10.0, 0.25, 0.002, 5000, 0, True)]
+
+
+@pytest.mark.parametrize("D,N,TL,rate,rel,limit,kind,outputs", PROJ_CASES)
+def test_sample_mined_by_the_projected_dfs_matches_oracle(D, N, TL, rate, rel, limit, kind, outputs):
+    off, items = synth.pattern_db(7, D, N, TL, 5.0, 500 if D == 12000 else 600)
+    w = {"offsets": off, "items": items, "N": N}
+    assert deferred(w, rate, rel) == (D == 12000)
+    ocost, oorder, onfs, oms = oracle.class_costs(off, items, N, 0, rate, rel, 5, kind=kind, limit=limit,
+                                                  return_minsup=True)
+    assert onfs > 1024 and (limit == 0 or oms > max(1, math.ceil(rel * math.ceil(rate * D))))
+    minsup = math.ceil(rel * D)
+    want = odict(oracle.eclat(off, items, N, minsup))
+    db = fim.build_vertical_db(off, items, N)
+    try:
+        costk = ("itemsets", "intersections")[kind]
+        if outputs:
+            cost, order = db.estimate_class_costs(rate, rel, 5, cost=costk, max_sample_itemsets=limit)
+        else:
+            assert db.estimate_class_costs(rate, rel, 5, cost=costk, max_sample_itemsets=limit, outputs=False) is None
+            assert db.mine(minsup).as_dict() == want
+            cost, order = db.estimate_result()
+        nfs, m, ms = db.estimate_sample_size()
+        assert (nfs, ms, m) == (onfs, oms, math.ceil(rate * D))
+        assert np.array_equal(cost, ocost)
+        assert np.array_equal(order, oorder)
+        assert db.mine(minsup).as_dict() == want
+    finally:
+        db.free()
