@@ -11,15 +11,23 @@ namespace {
 
 constexpr uint32_t kSmemHistMax = 12288;  // items counted in shared memory (48 KB)
 
-// K1: item supports with set semantics.  One warp per transaction: the lanes
-// read 32 consecutive items at a time (coalesced), a lane's item counts unless
-// an earlier position of the same transaction holds the same id (the lowest
-// lane of its __match_any_sync group within the chunk, and no lane of an earlier
-// chunk, compared by shuffles).  Also validates ids and offsets and records the
-// longest transaction (distinct items).  Only items[0, off[D]) is ever read,
-// whatever the offsets: a transaction whose range is reversed or leaves
-// [0, off[D]] is reported and skipped, and so is every transaction when
-// off[0] != 0.  flags = [error bits, longest transaction, off[0], off[D]].
+// K1: item supports with set semantics.  One thread per transaction of at most
+// kShortTx items: it reads its items in order, and an item counts unless an
+// earlier position of the same transaction holds the same id; while the ids
+// seen so far are strictly ascending (the usual layout) a new id above the last
+// one needs no comparison, otherwise it is compared with every earlier position.
+// Longer transactions are taken by the whole warp, one after the other: the
+// lanes read 32 consecutive items at a time (coalesced), a lane's item counts
+// unless the same id sits at a lower lane of the chunk (__match_any_sync) or in
+// an earlier chunk (compared by shuffles).  Counts go to a shared histogram per
+// CTA when N is small, flushed with one global atomic per nonzero counter.  Also
+// validates ids and offsets and records the longest transaction (distinct
+// items).  Only items[0, off[D]) is ever read, whatever the offsets: a
+// transaction whose range is reversed or leaves [0, off[D]] is reported and
+// skipped, and so is every transaction when off[0] != 0.
+// flags = [error bits, longest transaction, off[0], off[D]].
+constexpr uint32_t kShortTx = 64;
+
 __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* __restrict__ items, uint32_t D,
                              uint32_t N, uint32_t* __restrict__ cnt, uint32_t* flags) {
   extern __shared__ uint32_t hist[];
@@ -35,44 +43,78 @@ __global__ void k_item_count(const uint32_t* __restrict__ off, const uint32_t* _
     flags[3] = nnz;
   }
   uint32_t local_max = 0, local_err = first != 0 ? DEV_ERR_OFFSETS : 0u;
-  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-  uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  uint32_t nb = t < D ? off[t] : 0u, ne = t < D ? off[t + 1] : 0u;  // the offsets of the next transaction
-  for (; t < D && first == 0; t += warps) {
-    const uint32_t b = nb, e = ne;
-    if (t + warps < D) {
-      nb = off[t + warps];
-      ne = off[t + warps + 1];
+  auto bump = [&](uint32_t it) {
+    if (use_smem) atomicAdd(&hist[it], 1u);
+    else atomicAdd(&cnt[it], 1u);
+  };
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  // (warp-uniform loop: lane l of the warp takes transaction base + l)
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); first == 0 && base < D; base += nthreads) {
+    const uint32_t t = base + lane;
+    uint32_t b = 0, e = 0;
+    bool valid = false;
+    if (t < D) {
+      b = off[t];
+      e = off[t + 1];
+      valid = e >= b && e <= nnz;
+      if (!valid) local_err |= DEV_ERR_OFFSETS;
     }
-    if (e < b || e > nnz) {
-      local_err |= DEV_ERR_OFFSETS;
-      continue;
-    }
-    uint32_t distinct = 0;
-    for (uint32_t c0 = b; c0 < e; c0 += 32) {
-      const uint32_t k = c0 + lane;
-      const bool in = k < e;
-      const uint32_t it = in ? items[k] : 0xffffffffu;
-      const bool ok = in && it < N;
-      if (in && !ok) local_err |= DEV_ERR_ITEM_RANGE;
-      // repeat within this chunk: a lower lane holds the same id
-      const uint32_t same = __match_any_sync(0xffffffffu, it);
-      bool dup = (same & ((1u << lane) - 1u)) != 0u;
-      // repeat in an earlier chunk of the same transaction
-      for (uint32_t p0 = b; p0 < c0; p0 += 32) {
-        const uint32_t prev = items[p0 + lane];  // p0 + 32 <= c0 < e: always in range
-        for (uint32_t q = 0; q < 32; ++q) dup |= __shfl_sync(0xffffffffu, prev, q) == it;
+    const bool wide = valid && e - b > kShortTx;
+    if (valid && !wide) {
+      uint32_t distinct = 0, prev = 0;
+      bool asc = true;  // the ids so far strictly ascending, prev the last of them
+      for (uint32_t k0 = b; k0 < e; k0 += 4) {
+        uint32_t v[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) v[u] = k0 + u < e ? items[k0 + u] : 0u;  // (loads in flight together)
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+          const uint32_t k = k0 + u;
+          if (k >= e) break;
+          const uint32_t it = v[u];
+          bool dup = false;
+          if (k > b && !(asc && it > prev)) {
+            asc = false;
+            for (uint32_t q = b; q < k && !dup; ++q) dup = items[q] == it;
+          }
+          prev = it;
+          if (it >= N) {
+            local_err |= DEV_ERR_ITEM_RANGE;
+          } else if (!dup) {
+            ++distinct;
+            bump(it);
+          }
+        }
       }
-      const bool count = ok && !dup;
-      distinct += __popc(__ballot_sync(0xffffffffu, count));
-      if (count) {
-        if (use_smem) atomicAdd(&hist[it], 1u);
-        else atomicAdd(&cnt[it], 1u);
-      }
+      local_max = max(local_max, distinct);
     }
-    local_max = max(local_max, distinct);
+    for (uint32_t pend = __ballot_sync(0xffffffffu, wide); pend; pend &= pend - 1) {
+      const uint32_t src = __ffs(pend) - 1;
+      const uint32_t wb = __shfl_sync(0xffffffffu, b, src), we = __shfl_sync(0xffffffffu, e, src);
+      uint32_t distinct = 0;
+      for (uint32_t c0 = wb; c0 < we; c0 += 32) {
+        const uint32_t k = c0 + lane;
+        const bool in = k < we;
+        const uint32_t it = in ? items[k] : 0xffffffffu;
+        const bool ok = in && it < N;
+        if (in && !ok) local_err |= DEV_ERR_ITEM_RANGE;
+        // repeat within this chunk: a lower lane holds the same id
+        const uint32_t same = __match_any_sync(0xffffffffu, it);
+        bool dup = (same & ((1u << lane) - 1u)) != 0u;
+        // repeat in an earlier chunk of the same transaction
+        for (uint32_t p0 = wb; p0 < c0; p0 += 32) {
+          const uint32_t prv = items[p0 + lane];  // p0 + 32 <= c0 < we: always in range
+          for (uint32_t q = 0; q < 32; ++q) dup |= __shfl_sync(0xffffffffu, prv, q) == it;
+        }
+        const bool count = ok && !dup;
+        distinct += __popc(__ballot_sync(0xffffffffu, count));
+        if (count) bump(it);
+      }
+      local_max = max(local_max, distinct);
+    }
   }
   if (local_err) atomicOr(&flags[0], local_err);
+  local_max = __reduce_max_sync(0xffffffffu, local_max);
   if (lane == 0 && local_max) atomicMax(&flags[1], local_max);
   if (use_smem) {
     __syncthreads();
@@ -264,8 +306,9 @@ cudaError_t launch_item_count(const uint32_t* off, const uint32_t* items, uint32
                               uint32_t* flags, cudaStream_t st) {
   const uint32_t threads = 256;
   size_t smem = N <= kSmemHistMax ? (size_t)N * 4 : 0;
-  // one warp per transaction; with a shared histogram every CTA flushes its nonzero counters: a modest grid
-  uint32_t grid = grid_for((uint64_t)D * 32, threads, N <= kSmemHistMax ? 152 * 8 : 152 * 32);
+  // one thread per transaction; with a shared histogram every CTA flushes its nonzero counters: two CTAs per
+  // SM, each thread taking several transactions
+  uint32_t grid = grid_for((uint64_t)D, threads, N <= kSmemHistMax ? 152 * 2 : 152 * 8);
   k_item_count<<<grid, threads, smem, st>>>(off, items, D, N, cnt, flags);
   note_launch();
   return cudaGetLastError();

@@ -142,6 +142,24 @@ def test_duplicate_items_count_once():
     assert gpu_mine(off, items, 3, 1).as_dict() == {(1,): 2, (2,): 1, (1, 2): 1}
 
 
+def test_item_supports_with_repeats_in_any_order():
+    """Set semantics of the item count (Ch. 2: a transaction supports an item once) on 2,000 transactions of
+    0-200 ids drawn with replacement: short ones (counted by one thread each) sorted or not, with repeats,
+    and long ones (more than 64 ids, counted by a warp) with repeats across 32-id chunks.  Minsup 60 keeps
+    the 1,500 singletons (about 133 transactions each) and no pair (about 9 on average)."""
+    rng = np.random.default_rng(12)
+    N, D = 1500, 2000
+    lens = rng.integers(0, 201, D)
+    off = np.zeros(D + 1, dtype=np.uint32)
+    off[1:] = np.cumsum(lens)
+    items = rng.integers(0, N, int(off[-1])).astype(np.uint32)
+    for d in range(0, D, 3):
+        items[off[d]:off[d + 1]].sort()
+    want = odict(oracle.eclat(off, items, N, 60))
+    assert len(want) == N and all(len(k) == 1 for k in want)
+    assert_same(gpu_mine(off, items, N, 60).as_dict(), want)
+
+
 def test_invalid_inputs():
     off, items = csr([[1, 7]])
     with pytest.raises(fim.FimError) as e:
