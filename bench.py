@@ -47,12 +47,12 @@ L2_FLUSH_BYTES = 512 << 20
 # pair kernel; "dfs": the mine's DFS stage (projection + DFS + fallback, or the one DFS launch); "step": the
 # build, estimate and mine launches (the closed/maximal flags pass of --mode once excluded).
 CAPTURES = {
-    "large_sparse": {"sources_sha256": "92fede2e8f9da05ec990ee3792d01dee78dda85b0855d1f30a63c9a7b248eb3f",
+    "large_sparse": {"sources_sha256": "b7fa302ba7ee8f829e4355c71eb6aa41ed99fd4654012ab5e226a54ec7557371",
                      "date": "2026-12-03", "summary": "profiles/launches_large_sparse.md",
-                     "kernels": {"pair": 779835136, "dfs": 1015812608}, "step": 2758285056},
-    "sparse_mid": {"sources_sha256": "92fede2e8f9da05ec990ee3792d01dee78dda85b0855d1f30a63c9a7b248eb3f",
+                     "kernels": {"pair": 781809664, "dfs": 1014534400}, "step": 2760817152},
+    "sparse_mid": {"sources_sha256": "b7fa302ba7ee8f829e4355c71eb6aa41ed99fd4654012ab5e226a54ec7557371",
                    "date": "2026-12-03", "summary": "profiles/launches_sparse_mid.md",
-                   "kernels": {"pair": 14442240, "dfs": 4326912}, "step": 48670720},
+                   "kernels": {"pair": 14441984, "dfs": 4328704}, "step": 48670464},
 }
 MAX_ITEMSETS_PER_JOB = 4_000_000  # serving: jobs whose output passes this are stopped and counted as rejected
 

@@ -283,7 +283,19 @@ static fim_status db_build_rows(fim_db* db, const uint32_t* src_off, const uint3
   void* hcnt = nullptr;
   FIM_TRY(stage_get(db, ((size_t)N + 4) * 4, &hcnt));
   FIM_CUDA(cudaMemcpyAsync(hcnt, d_cnt, ((size_t)N + 4) * 4, cudaMemcpyDeviceToHost, st));
-  FIM_TRY(stream_sync(db));
+  // Without a prefilter every item gets a row (n_rows = N), so the bitmap block is known before the counts:
+  // it is cleared behind the counts' copy, while the host waits for that copy alone and relabels the rows.
+  const bool early_bits = db->prefilter == 0 && (size_t)N * db->stride > 0;
+  if (early_bits) {
+    if (!db->cnt_done) FIM_CUDA(cudaEventCreateWithFlags(&db->cnt_done, cudaEventDisableTiming));
+    FIM_CUDA(cudaEventRecord(db->cnt_done, st));
+    FIM_TRY(ws_get(db->ws, WS_DB_BITS, (size_t)N * db->stride, &db->d_bits));
+    FIM_CUDA(cudaMemsetAsync(db->d_bits, 0, (size_t)N * db->stride * 4, st));
+    FIM_CUDA(cudaEventSynchronize(db->cnt_done));
+    db->stage_used = 0;
+  } else {
+    FIM_TRY(stream_sync(db));
+  }
   std::vector<uint32_t> cnt(static_cast<uint32_t*>(hcnt), static_cast<uint32_t*>(hcnt) + N + 4);
   const uint32_t err = cnt[N];
   if (cnt[N + 2] != 0) return fail(FIM_ERR_INVALID, "tx_offsets[0] must be 0");
@@ -336,7 +348,7 @@ static fim_status db_build_rows(fim_db* db, const uint32_t* src_off, const uint3
   }
   FIM_CUDA(launch_iota(db->d_iota, db->n_rows, st));
   if (db->n_rows) {
-    FIM_CUDA(cudaMemsetAsync(db->d_bits, 0, (size_t)db->n_rows * db->stride * 4, st));
+    if (!early_bits) FIM_CUDA(cudaMemsetAsync(db->d_bits, 0, (size_t)db->n_rows * db->stride * 4, st));
     FIM_CUDA(launch_bitmap_build(db->d_tx_off, db->d_tx_items, D, db->d_item_rank, db->d_bits, db->stride, st));
   }
   return FIM_OK;
@@ -1008,6 +1020,7 @@ void fim_db_free(fim_db* db) {
   fim::pinned_release(db->stage, db->stage_cap);
   fim::pinned_release(db->est_pin, db->est_pin_cap);
   if (db->est_done) cudaEventDestroy(db->est_done);
+  if (db->cnt_done) cudaEventDestroy(db->cnt_done);
   delete db;
 }
 

@@ -220,6 +220,7 @@ struct fim_db {
   bool est_redo = false;  // the deferred sample needs the synchronous path (itemset limit or a retry)
   uint32_t est_redo_minsup = 0;  // the sample minsup that redo starts at (0: the estimate's own)
   cudaEvent_t est_done = nullptr;
+  cudaEvent_t cnt_done = nullptr;  // the build's item counts copied to the host (the bitmap clearing behind them)
   void* est_pin = nullptr;
   size_t est_pin_cap = 0;
   const uint32_t* d_est_order = nullptr;
