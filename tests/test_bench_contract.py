@@ -148,6 +148,9 @@ def test_traffic_records_follow_the_sources():
     for name, rec in bench.CAPTURES.items():
         assert set(rec) >= {"sources_sha256", "date", "summary", "kernels", "step"}
         assert os.path.exists(os.path.join(ROOT, rec["summary"]))
+        # the summary the record cites is the one of the same capture (it names the sources' hash)
+        with open(os.path.join(ROOT, rec["summary"])) as f:
+            assert rec["sources_sha256"][:12] in f.read(), (name, rec["summary"])
     saved = dict(bench.CAPTURES)
     try:
         bench.CAPTURES["x"] = {"sources_sha256": "0" * 64, "date": "d", "summary": "s", "kernels": {}, "step": 1}
